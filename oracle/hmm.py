@@ -1,0 +1,155 @@
+"""Oracle for the HMM workloads (test infrastructure only).
+
+The paper (Expression Acceleration, arXiv 2211.00621) does not mention hidden Markov
+models.  The HMM forward recursion is used as a synthetic program built from its pattern
+vocabulary: for every time step t (a sequential loop, as the foldl of Listing 1), the new
+forward vector is a ``map`` over states j of a ``reduce`` over states i (Appendix A,
+Fig. "pmexpr-extension").  The arithmetic below is the textbook forward algorithm and
+forward-backward expected counts, in float64, with these readings:
+
+* natural logarithms; logL = log P(o_1 .. o_T);
+* the first emission is included: alpha_1(j) = pi_j b_j(o_1);
+* parameters enter as log-probabilities that are treated as free parameters (no row
+  renormalisation inside the function), so d logL / d logA_ij is the expected number of
+  i->j transitions and d logL / d logB_jk the expected number of times state j emits k.
+
+Layouts: A[i, j] = P(z_{t+1}=j | z_t=i); B[j, k] = P(o_t=k | z_t=j); pi[j] = P(z_1=j).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _lse(v: np.ndarray, axis=None):
+    m = np.max(v, axis=axis, keepdims=True)
+    r = m + np.log(np.sum(np.exp(v - m), axis=axis, keepdims=True))
+    return np.squeeze(r, axis=axis) if axis is not None else float(r.reshape(()))
+
+
+def forward_log(logA: np.ndarray, logB: np.ndarray, logpi: np.ndarray, obs: np.ndarray) -> float:
+    """Log-space forward recursion.
+
+    la_1(j) = log pi_j + log B[j, o_1]
+    la_t(j) = LSE_i( la_{t-1}(i) + log A[i, j] ) + log B[j, o_t]
+    logL    = LSE_j la_T(j)
+    """
+    la = logpi + logB[:, obs[0]]
+    for t in range(1, len(obs)):
+        la = _lse(la[:, None] + logA, axis=0) + logB[:, obs[t]]
+    return _lse(la)
+
+
+def forward_scaled(A: np.ndarray, B: np.ndarray, pi: np.ndarray, obs: np.ndarray,
+                   return_all: bool = False):
+    """Scaled forward recursion.
+
+    a~_1 = pi o b(o_1);  a~_t = (a^_{t-1} A) o b(o_t);  c_t = sum_j a~_t(j);
+    a^_t = a~_t / c_t;   logL = sum_t log c_t.
+    With ``return_all`` also returns the normalised alphas [T, K] and the c_t [T].
+    """
+    T = len(obs)
+    K = len(pi)
+    ahat = np.empty((T, K)) if return_all else None
+    c = np.empty(T)
+    a = pi * B[:, obs[0]]
+    c[0] = a.sum()
+    a = a / c[0]
+    if return_all:
+        ahat[0] = a
+    for t in range(1, T):
+        a = (a @ A) * B[:, obs[t]]
+        c[t] = a.sum()
+        a = a / c[t]
+        if return_all:
+            ahat[t] = a
+    logL = float(np.sum(np.log(c)))
+    if return_all:
+        return logL, ahat, c
+    return logL
+
+
+def backward_scaled(A: np.ndarray, B: np.ndarray, obs: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """Scaled backward recursion matching :func:`forward_scaled`'s c_t.
+
+    b^_T = 1;  b^_t = A ( b(o_{t+1}) o b^_{t+1} ) / c_{t+1}.   Returns [T, K].
+    """
+    T = len(obs)
+    K = A.shape[0]
+    bhat = np.empty((T, K))
+    bhat[T - 1] = 1.0
+    for t in range(T - 2, -1, -1):
+        bhat[t] = A @ (B[:, obs[t + 1]] * bhat[t + 1]) / c[t + 1]
+    return bhat
+
+
+def expected_counts(A: np.ndarray, B: np.ndarray, pi: np.ndarray, obs: np.ndarray):
+    """Forward-backward expected counts for one sequence.
+
+    gamma_t(j)  = a^_t(j) b^_t(j)                              (posterior of z_t = j)
+    xi(i, j)    = sum_{t<T} a^_t(i) A_ij b_j(o_{t+1}) b^_{t+1}(j) / c_{t+1}
+    counts(j,k) = sum_t gamma_t(j) [o_t = k]
+    Returns (logL, xi [K,K], counts [K,M], gamma_1 [K]); these are the gradients of logL
+    with respect to log A, log B and log pi under the free-parameter reading.
+    """
+    logL, ahat, c = forward_scaled(A, B, pi, obs, return_all=True)
+    bhat = backward_scaled(A, B, obs, c)
+    T = len(obs)
+    K, M = B.shape
+    xi = np.zeros((K, K))
+    for t in range(T - 1):
+        w = B[:, obs[t + 1]] * bhat[t + 1] / c[t + 1]
+        xi += np.outer(ahat[t], w)
+    xi *= A
+    gamma = ahat * bhat
+    counts = np.zeros((K, M))
+    for t in range(T):
+        counts[:, obs[t]] += gamma[t]
+    return logL, xi, counts, gamma[0].copy()
+
+
+# ------------------------------------------------------------------------ batches
+def loglik_batch(p: dict, seqs=None, log_space: bool = False, params: dict | None = None) -> np.ndarray:
+    """logL for each sequence (or the listed subset) of a workload dict from synth.
+
+    ``params`` overrides the float64 parameters (A, B, pi), e.g. with float32-rounded
+    ones converted to float64.
+    """
+    q = params if params is not None else p
+    obs, off = p["obs"], p["offsets"]
+    idx = range(len(off) - 1) if seqs is None else seqs
+    out = []
+    for s in idx:
+        o = obs[off[s]:off[s + 1]]
+        if log_space:
+            out.append(forward_log(np.log(q["A"]), np.log(q["B"]), np.log(q["pi"]), o))
+        else:
+            out.append(forward_scaled(q["A"], q["B"], q["pi"], o))
+    return np.array(out)
+
+
+def gradients_batch(p: dict, seqs=None, weights=None, params: dict | None = None):
+    """Summed (optionally weighted) gradients of sum_s w_s logL_s over the sequences.
+
+    Returns (logL [n], grad_logA [K,K], grad_logB [K,M], grad_logpi [K]).
+    """
+    q = params if params is not None else p
+    obs, off = p["obs"], p["offsets"]
+    idx = list(range(len(off) - 1)) if seqs is None else list(seqs)
+    K, M = q["B"].shape
+    gA, gB, gpi = np.zeros((K, K)), np.zeros((K, M)), np.zeros(K)
+    lls = []
+    for n, s in enumerate(idx):
+        w = 1.0 if weights is None else float(weights[n])
+        ll, xi, cnt, g1 = expected_counts(q["A"], q["B"], q["pi"], obs[off[s]:off[s + 1]])
+        lls.append(ll)
+        gA += w * xi
+        gB += w * cnt
+        gpi += w * g1
+    return np.array(lls), gA, gB, gpi
+
+
+def params_from_f32_logs(logs: dict) -> dict:
+    """float64 parameters equal to exp of the float32 log inputs (the kernel's inputs)."""
+    return {"A": np.exp(logs["log_A"].astype(np.float64)),
+            "B": np.exp(logs["log_B"].astype(np.float64)),
+            "pi": np.exp(logs["log_pi"].astype(np.float64))}

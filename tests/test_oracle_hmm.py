@@ -1,0 +1,151 @@
+"""Pins for oracle.hmm: brute force over all state paths, closed forms, invariants and
+central finite differences (CPU only)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import brute, hmm
+from paper_2211_00621_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name + ".json")) as f:
+        c = json.load(f)
+    return {k: np.array(v) if k not in ("source",) else v for k, v in c.items()}
+
+
+@pytest.mark.parametrize("name", ["hmm_k2_t5", "hmm_k3_t4"])
+def test_forward_matches_bruteforce_fixture(name):
+    c = _load(name)
+    obs = c["obs"].astype(np.int64)
+    ll_s = hmm.forward_scaled(c["A"], c["B"], c["pi"], obs)
+    ll_l = hmm.forward_log(np.log(c["A"]), np.log(c["B"]), np.log(c["pi"]), obs)
+    assert ll_s == pytest.approx(float(c["loglik"]), rel=1e-13)
+    assert ll_l == pytest.approx(float(c["loglik"]), rel=1e-13)
+
+
+@pytest.mark.parametrize("name", ["hmm_k2_t5", "hmm_k3_t4"])
+def test_expected_counts_match_bruteforce_fixture(name):
+    c = _load(name)
+    ll, xi, cnt, g1 = hmm.expected_counts(c["A"], c["B"], c["pi"], c["obs"].astype(np.int64))
+    np.testing.assert_allclose(xi, c["xi"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(cnt, c["counts"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(g1, c["gamma1"], rtol=1e-12, atol=1e-14)
+
+
+def test_bruteforce_random_k2_t5():
+    p = synth.hmm_workload(11, 2, 4, 3, "fixed", 5, 5)
+    for s in range(3):
+        o = p["obs"][p["offsets"][s]:p["offsets"][s + 1]]
+        ref = brute.loglik(p["A"], p["B"], p["pi"], o)
+        assert hmm.forward_scaled(p["A"], p["B"], p["pi"], o) == pytest.approx(ref, rel=1e-14)
+        assert hmm.forward_log(np.log(p["A"]), np.log(p["B"]), np.log(p["pi"]), o) == pytest.approx(ref, rel=1e-14)
+
+
+def test_closed_form_uniform_emissions():
+    # b_j(o) = 1/M for all j, o: logL = -T log M whatever A and pi are.
+    K, M, T = 5, 7, 40
+    g = synth.rng(1)
+    A = synth.dirichlet1_rows(g, K, K)
+    pi = synth.dirichlet1_rows(g, 1, K)[0]
+    B = np.full((K, M), 1.0 / M)
+    o = g.integers(0, M, T)
+    assert hmm.forward_scaled(A, B, pi, o) == pytest.approx(-T * math.log(M), rel=1e-13)
+    assert hmm.forward_log(np.log(A), np.log(B), np.log(pi), o) == pytest.approx(-T * math.log(M), rel=1e-13)
+
+
+def test_closed_form_single_state():
+    # K = 1: logL = sum_t log B(o_t).
+    B = np.array([[0.1, 0.2, 0.3, 0.4]])
+    o = np.array([3, 0, 0, 2, 1, 3])
+    ref = sum(math.log(B[0, k]) for k in o)
+    assert hmm.forward_scaled(np.ones((1, 1)), B, np.ones(1), o) == pytest.approx(ref, rel=1e-14)
+
+
+def test_closed_form_identity_transitions():
+    # A = I: the state never changes, logL = log sum_j pi_j prod_t b_j(o_t).
+    K, M, T = 4, 3, 12
+    g = synth.rng(2)
+    B = synth.dirichlet1_rows(g, K, M)
+    pi = synth.dirichlet1_rows(g, 1, K)[0]
+    o = g.integers(0, M, T)
+    ref = math.log(sum(pi[j] * math.prod(B[j, k] for k in o) for j in range(K)))
+    assert hmm.forward_scaled(np.eye(K), B, pi, o) == pytest.approx(ref, rel=1e-13)
+
+
+def test_closed_form_rows_equal_pi():
+    # Every row of A equal to pi: the z_t are i.i.d. pi, logL = sum_t log sum_j pi_j b_j(o_t).
+    K, M, T = 6, 5, 30
+    g = synth.rng(3)
+    B = synth.dirichlet1_rows(g, K, M)
+    pi = synth.dirichlet1_rows(g, 1, K)[0]
+    A = np.tile(pi, (K, 1))
+    o = g.integers(0, M, T)
+    ref = sum(math.log(float(np.dot(pi, B[:, k]))) for k in o)
+    assert hmm.forward_scaled(A, B, pi, o) == pytest.approx(ref, rel=1e-13)
+
+
+def test_scaled_equals_logspace_medium():
+    p = synth.hmm_workload(0, 64, 32, 2, "fixed", 300, 300)
+    a = hmm.loglik_batch(p)
+    b = hmm.loglik_batch(p, log_space=True)
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
+def test_expected_counts_invariants():
+    p = synth.hmm_workload(5, 8, 6, 4, "uniform", 5, 30)
+    lls, gA, gB, gpi = hmm.gradients_batch(p)
+    L = p["lengths"]
+    assert gA.sum() == pytest.approx(float(np.sum(L - 1)), rel=1e-12)
+    assert gB.sum() == pytest.approx(float(np.sum(L)), rel=1e-12)
+    assert gpi.sum() == pytest.approx(4.0, rel=1e-12)
+    assert (gA >= 0).all() and (gB >= 0).all() and (gpi >= 0).all()
+    # counts of symbol k over states equal the number of times k was observed
+    np.testing.assert_allclose(gB.sum(axis=0), np.bincount(p["obs"], minlength=6), rtol=1e-12)
+
+
+def test_gradients_equal_central_finite_differences():
+    # d logL / d logA_ij (free log parameters) by central differences, h = 1e-6, float64.
+    p = synth.hmm_workload(8, 4, 3, 2, "fixed", 12, 12)
+    _, gA, gB, gpi = hmm.gradients_batch(p)
+    lA, lB, lpi = np.log(p["A"]), np.log(p["B"]), np.log(p["pi"])
+    obs, off = p["obs"], p["offsets"]
+
+    def total(lA_, lB_, lpi_):
+        return sum(hmm.forward_log(lA_, lB_, lpi_, obs[off[s]:off[s + 1]]) for s in range(2))
+
+    h = 1e-6
+    for (i, j) in [(0, 0), (1, 3), (3, 2), (2, 1)]:
+        a, b = lA.copy(), lA.copy()
+        a[i, j] += h
+        b[i, j] -= h
+        fd = (total(a, lB, lpi) - total(b, lB, lpi)) / (2 * h)
+        assert fd == pytest.approx(gA[i, j], rel=1e-6, abs=1e-6)
+    for (j, k) in [(0, 0), (2, 1), (3, 2)]:
+        a, b = lB.copy(), lB.copy()
+        a[j, k] += h
+        b[j, k] -= h
+        fd = (total(lA, a, lpi) - total(lA, b, lpi)) / (2 * h)
+        assert fd == pytest.approx(gB[j, k], rel=1e-6, abs=1e-6)
+    for j in range(4):
+        a, b = lpi.copy(), lpi.copy()
+        a[j] += h
+        b[j] -= h
+        fd = (total(lA, lB, a) - total(lA, lB, b)) / (2 * h)
+        assert fd == pytest.approx(gpi[j], rel=1e-6, abs=1e-6)
+
+
+def test_bruteforce_expected_counts_random():
+    p = synth.hmm_workload(21, 2, 3, 1, "fixed", 5, 5)
+    o = p["obs"]
+    ll, xi, cnt, g1 = brute.expected_counts(p["A"], p["B"], p["pi"], o)
+    ll2, xi2, cnt2, g12 = hmm.expected_counts(p["A"], p["B"], p["pi"], o)
+    assert ll2 == pytest.approx(ll, rel=1e-14)
+    np.testing.assert_allclose(xi2, xi, rtol=1e-12)
+    np.testing.assert_allclose(cnt2, cnt, rtol=1e-12)
+    np.testing.assert_allclose(g12, g1, rtol=1e-12)
