@@ -1,0 +1,271 @@
+/*
+ * accel.h -- C ABI of libaccel, a GB300 (sm_103a) library for the data-parallel hot path
+ * of expression acceleration (Expression Acceleration: Seamless Parallelization of Typed
+ * High-Level Languages, arXiv 2211.00621).
+ *
+ * One call = one accelerated expression (Sec. 3.1 "Key Idea": `accelerate e` runs e on the
+ * GPU, its free variables passed in).  Arguments arrive already in the backend format or
+ * are marshaled by the library (Sec. 3.3 "Marshaling").  There are no function-valued
+ * arguments (Sec. 3.4 and Appendix B, rules WF-BC-1/2 forbid higher-order functions in
+ * accelerated code), so every pattern takes an operator from a FIXED enumeration.  Tensor
+ * elements are integers or floats (Appendix B, WF-TC-Ten) and tensors have rank <= 3
+ * (Appendix B, "Dynamic Assumptions": the CUDA backend's maximum rank, default 3).
+ *
+ * Conventions (all entry points)
+ * ------------------------------
+ *  - Every call returns accel_status; ACCEL_OK (0) on success.  On failure nothing has
+ *    been launched unless the code is ACCEL_ERR_CUDA / ACCEL_ERR_TIMEOUT, and
+ *    accel_last_error() returns a message (thread-local, valid until the next call on the
+ *    same thread).
+ *  - Pointers named d_* are device pointers (or host pointers the device can address, where
+ *    stated); h_* are host pointers read before the call returns.  The caller owns ALL
+ *    memory: the library never allocates device memory.  Scratch space is passed as
+ *    (d_ws, ws_bytes); the matching *_workspace_size() reports how much is needed
+ *    (256-byte aligned pointer required).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every call is
+ *    asynchronous on that stream unless debug mode is on.
+ *  - Debug mode (accel_set_debug(1)) follows the paper's debug mode (Sec. 3.2 "Recommended
+ *    Workflow" and Appendix B "Dynamic Assumptions"): arguments are validated on the host
+ *    and on the device (offsets monotone and in range, symbols < M, rank <= 3, lengths),
+ *    the stream is synchronized after the call and device-side errors are returned as
+ *    status codes.  With debug mode off ("accelerate mode") only O(1) host checks run.
+ *  - Integers are 64-bit wherever the paper's compiler would use its single int type
+ *    (Sec. 5: the compiler always uses 64-bit integers): offsets, sizes, integer results of
+ *    maps and reductions computed from int32 data.
+ */
+#ifndef ACCEL_H
+#define ACCEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+typedef int32_t accel_status;
+#define ACCEL_OK                 0
+#define ACCEL_ERR_INVALID_ARG    1  /* null pointer, bad enum, negative size            */
+#define ACCEL_ERR_SHAPE          2  /* rank > 3, offsets not monotone, symbol >= M, ... */
+#define ACCEL_ERR_DTYPE          3  /* dtype combination not supported by the operator  */
+#define ACCEL_ERR_WORKSPACE      4  /* ws_bytes smaller than *_workspace_size()         */
+#define ACCEL_ERR_CUDA           5  /* a CUDA runtime call failed                        */
+#define ACCEL_ERR_TIMEOUT        6  /* a bounded device-side wait gave up                */
+#define ACCEL_ERR_UNSUPPORTED    7  /* size outside the kernels' limits (e.g. K > 256)   */
+
+/* ------------------------------------------------------------------ element types */
+#define ACCEL_I32 0
+#define ACCEL_I64 1
+#define ACCEL_F32 2
+#define ACCEL_F64 3
+
+/* ----------------------------------------------------------- fixed operator sets */
+/* map / map2 operators g (Appendix A: map f s, map2 f s1 s2).  For integer outputs the
+ * arithmetic is int64 narrowed to the output type; for float outputs it is done in the
+ * output type.  SCALE multiplies by `scalar`; ADD2/MUL2 are map2 operators.           */
+#define ACCEL_MAP_IDENTITY     0  /* g(x) = x          */
+#define ACCEL_MAP_SQ_PLUS_ONE  1  /* g(x) = x*x + 1    */
+#define ACCEL_MAP_NEG          2  /* g(x) = -x         */
+#define ACCEL_MAP_ABS          3  /* g(x) = |x|        */
+#define ACCEL_MAP_SCALE        4  /* g(x) = scalar*x   */
+#define ACCEL_MAP_ADD2         5  /* g(x,y) = x + y    */
+#define ACCEL_MAP_MUL2         6  /* g(x,y) = x * y    */
+
+/* reduce operators f with neutral element ne (Appendix A: reduce f ne s; Appendix B:
+ * f must be associative and ne its neutral element).                                  */
+#define ACCEL_RED_ADD 0  /* ne = 0                         */
+#define ACCEL_RED_MUL 1  /* ne = 1                         */
+#define ACCEL_RED_MIN 2  /* ne = max of type / +inf        */
+#define ACCEL_RED_MAX 3  /* ne = min of type / -inf        */
+
+/* loop bodies (Appendix A: loop n f calls f i for i in [0,n) in undefined order).     */
+#define ACCEL_LOOP_AXPY  0  /* t0[i] = t0[i] + scalar*t1[i]   (Listing 1, axpy)      */
+#define ACCEL_LOOP_SCALE 1  /* t0[i] = scalar*t1[i]           (Appendix A, b = 2a)   */
+
+/* all-pairs operators */
+#define ACCEL_PAIR_GRAVITY_SOFTENED 0
+
+/* HMM forward precisions */
+#define ACCEL_HMM_FP32_LOG    0  /* log-space forward in FP32 SIMT                     */
+#define ACCEL_HMM_BF16_SCALED 1  /* scaled forward, BF16 tcgen05 step, FP32 accumulate */
+
+#define ACCEL_MAX_RANK   3
+#define ACCEL_MAX_FIELDS 8
+#define ACCEL_HMM_MAX_K  256
+
+/* ------------------------------------------------------------------- housekeeping */
+const char* accel_version(void);
+/* Message of the last failing call on the calling thread ("" if none). */
+const char* accel_last_error(void);
+/* Debug mode on (1) / off (0); process-wide, default off. */
+void accel_set_debug(int32_t on);
+int32_t accel_get_debug(void);
+
+/* =========================================================== marshaling (Sec. 3.3) */
+/*
+ * accel_marshal_ragged -- flatten a host list of S sequences (Appendix A `flatten`,
+ * Sec. 3.3 marshaling of a [[T]] argument) into the backend format:
+ *     d_offsets[0] = 0, d_offsets[s+1] = d_offsets[s] + h_lengths[s]   (int64, S+1)
+ *     d_flat[d_offsets[s] + k] = h_ptrs[s][k]                           (k < h_lengths[s])
+ *  h_ptrs    host array of S element pointers; each points to device memory or to
+ *            page-locked host memory mapped for the device (UVA); may be NULL where the
+ *            length is 0.  Read before the call returns.
+ *  h_lengths host array of S lengths >= 0.  Read before the call returns.
+ *  dtype     element type of every sequence (4- or 8-byte).
+ *  d_flat    device output, sum(lengths) elements; d_offsets device output, S+1 int64.
+ *  d_ws      scratch of accel_marshal_ragged_workspace_size(S) bytes (pointer + length
+ *            tables and scan partials).
+ * Errors: INVALID_ARG (null/negative), DTYPE, WORKSPACE, CUDA.
+ */
+size_t accel_marshal_ragged_workspace_size(int64_t S);
+accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_lengths, int64_t S,
+                                  int32_t dtype, void* d_flat, int64_t* d_offsets,
+                                  void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * accel_marshal_records -- a sequence of n records {l_i = e_i} (Fig. mexpr-ast) stored as
+ * an array of structures of `record_bytes` bytes each, converted to one array per field
+ * (structure of arrays) (Sec. 3.3), or back when `inverse` != 0.
+ *  d_aos            device, n * record_bytes bytes (input, or output when inverse).
+ *  nfields          1..ACCEL_MAX_FIELDS; h_field_offsets[f] byte offset of field f inside
+ *                   the record; h_field_dtypes[f] its element type (4- or 8-byte scalar,
+ *                   naturally aligned).
+ *  h_soa            host array of nfields device pointers, field f is n elements.
+ *  With inverse, bytes of d_aos not covered by a field are left untouched.
+ * Errors: INVALID_ARG, DTYPE (unaligned field or bad type), SHAPE (field outside record).
+ */
+accel_status accel_marshal_records(void* d_aos, int64_t n, int32_t record_bytes, int32_t nfields,
+                                   const int32_t* h_field_offsets, const int32_t* h_field_dtypes,
+                                   void* const* h_soa, int32_t inverse, void* stream);
+
+/* ================================================== map / map2 (Appendix A, Fig. pmexpr) */
+/*
+ * accel_map -- d_out[k] = g(d_in[k])  or  g(d_in[k], d_in2[k]) for map2 operators, k < n.
+ *  d_in2 must be non-NULL exactly for ACCEL_MAP_ADD2 / ACCEL_MAP_MUL2 and has in_dtype.
+ *  Integer output: computed in int64, narrowed (two's complement) to out_dtype.
+ *  Float output: computed in out_dtype.  Integer input with float output is converted.
+ *  Float input with integer output is rejected (DTYPE).
+ */
+accel_status accel_map(int32_t op, int32_t in_dtype, const void* d_in, const void* d_in2,
+                       int32_t out_dtype, void* d_out, int64_t n, double scalar, void* stream);
+
+/* ============================================================ reduce (Appendix A) */
+/*
+ * accel_reduce -- *d_out = reduce f ne d_in[0..n)  (one element of `dtype`, device).
+ *  Deterministic two-pass reduction: per-CTA partials in d_ws, then one combining CTA.
+ *  n == 0 gives ne.  Integer results are exact (wrapping), float results depend on the
+ *  (fixed) combination order.
+ */
+size_t accel_reduce_workspace_size(int64_t n, int32_t dtype);
+accel_status accel_reduce(int32_t op, int32_t dtype, const void* d_in, int64_t n, void* d_out,
+                          void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * accel_segreduce -- segmented reduce with a fused map, i.e. the nested pattern
+ *     map (lam s. reduce f ne (map g s)) over a flattened [[T]] (Appendix A):
+ *     d_out[s] = f-fold of g(d_data[k]) over k in [d_offsets[s], d_offsets[s+1]),
+ *     ne for an empty segment.
+ *  d_data     device, N elements of in_dtype (the flat data of accel_marshal_ragged).
+ *  d_offsets  device, S+1 non-decreasing int64, d_offsets[0] = 0, d_offsets[S] = N.
+ *  g          fused map (any single-operand ACCEL_MAP_*), applied in out_dtype
+ *             (int64 for integer data: Sec. 5); `scalar` is used by ACCEL_MAP_SCALE.
+ *  d_out      device, S elements of out_dtype.
+ *  d_ws       accel_segreduce_workspace_size(N, S) bytes.
+ * Errors: INVALID_ARG, DTYPE, WORKSPACE, SHAPE (debug mode: offsets not monotone / not
+ * matching N), CUDA.
+ */
+size_t accel_segreduce_workspace_size(int64_t N, int64_t S);
+accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, int32_t out_dtype,
+                             const void* d_data, int64_t N, const int64_t* d_offsets, int64_t S,
+                             double scalar, void* d_out, void* d_ws, size_t ws_bytes, void* stream);
+
+/* ============================================================== loop (Appendix A) */
+/* A tensor argument (Tensor[Int] / Tensor[Float], rank <= 3, dense row-major). */
+typedef struct accel_tensor {
+    void*   data;                 /* device pointer                               */
+    int32_t dtype;                /* ACCEL_I32 .. ACCEL_F64                        */
+    int32_t rank;                 /* 0..ACCEL_MAX_RANK                             */
+    int64_t dims[ACCEL_MAX_RANK]; /* dims[0..rank) used                            */
+} accel_tensor;
+
+/*
+ * accel_loop -- `loop n f` with a fixed body over tensors args[0] (written) and args[1]
+ * (read), both of the same dtype and with >= n elements; i in [0, n) in undefined order.
+ *  ACCEL_LOOP_AXPY : t0[i] += scalar * t1[i];   ACCEL_LOOP_SCALE: t0[i] = scalar * t1[i].
+ *  Integer tensors use (int64)scalar.
+ * Errors: INVALID_ARG (nargs != 2, null), SHAPE (rank > 3 or fewer than n elements),
+ * DTYPE (dtypes differ).
+ */
+accel_status accel_loop(int32_t body, int64_t n, const accel_tensor* args, int32_t nargs,
+                        double scalar, void* stream);
+
+/* ====================================================================== HMM */
+/* Model parameters, float32 log-probabilities, device memory owned by the caller. */
+typedef struct accel_hmm_model {
+    int32_t K;             /* states, 1..ACCEL_HMM_MAX_K                                   */
+    int32_t M;             /* observation symbols, 1..1024                                 */
+    const float* log_A;    /* [K*K] row-major: log P(z_{t+1}=j | z_t=i) at i*K + j          */
+    const float* log_B;    /* [K*M] row-major: log P(o_t=k | z_t=j)     at j*M + k          */
+    const float* log_pi;   /* [K]:             log P(z_1=j)                                 */
+} accel_hmm_model;
+
+/*
+ * hmm_forward -- per-sequence log-likelihood logL_s = log P(o_1..o_T_s) of S observation
+ * sequences of uneven lengths, by the forward recursion: a map over states j of a reduce
+ * over states i inside a sequential loop over t (Appendix A patterns; HMM arithmetic is
+ * the textbook forward algorithm, which the paper does not discuss).
+ *  precision  ACCEL_HMM_FP32_LOG: log-space recursion in FP32 (max-shifted sum of exp).
+ *             ACCEL_HMM_BF16_SCALED: scaled recursion, alpha and A in BF16 on the tensor
+ *             cores (tcgen05, FP32 accumulation in TMEM), per-step power-of-two rescaling,
+ *             log-scale sum in FP64; one persistent launch for all sequences.
+ *  d_obs      device int32 [total_T], symbols in [0, M); d_offsets device int64 [S+1].
+ *  d_loglik   device float64 [S].
+ *  d_ws       hmm_forward_workspace_size(...) bytes.
+ * Every sequence must have length >= 1.  Errors: INVALID_ARG, SHAPE (debug mode: bad
+ * offsets, symbol >= M, empty sequence), UNSUPPORTED (K or M beyond the limits of the
+ * chosen precision), WORKSPACE, CUDA, TIMEOUT.
+ */
+size_t hmm_forward_workspace_size(const accel_hmm_model* m, int64_t S, int64_t total_T,
+                                  int32_t precision);
+accel_status hmm_forward(const accel_hmm_model* m, int32_t precision, const int32_t* d_obs,
+                         const int64_t* d_offsets, int64_t S, int64_t total_T, double* d_loglik,
+                         void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * hmm_adjoint -- gradients of L = sum_s w_s logL_s with respect to the log parameters,
+ * treated as free parameters:
+ *   d_grad_log_A[i*K+j]  = sum_s w_s sum_{t<T_s} P(z_t=i, z_{t+1}=j | o^s)  (expected transitions)
+ *   d_grad_log_B[j*M+k]  = sum_s w_s sum_t P(z_t=j | o^s) [o^s_t = k]      (expected emissions)
+ *   d_grad_log_pi[j]     = sum_s w_s P(z_1=j | o^s)
+ * computed by a hand-written adjoint of the scaled forward recursion: a forward pass that
+ * keeps alpha only every ceil(sqrt(T_s)) steps, then, segment by segment in reverse, a
+ * recomputation of alpha from its checkpoint and the backward (beta) recursion.
+ *  d_weights  device float64 [S] or NULL (all ones).
+ *  d_loglik   device float64 [S] or NULL: the forward's logL_s.
+ *  max_T      the largest sequence length (sizes the checkpoint storage).
+ *  Outputs are overwritten (not accumulated); d_grad_log_pi may be NULL.
+ */
+size_t hmm_adjoint_workspace_size(const accel_hmm_model* m, int64_t S, int64_t total_T, int64_t max_T);
+accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets,
+                         int64_t S, int64_t total_T, int64_t max_T, const double* d_weights,
+                         double* d_loglik, float* d_grad_log_A, float* d_grad_log_B,
+                         float* d_grad_log_pi, void* d_ws, size_t ws_bytes, void* stream);
+
+/* =========================================================== all-pairs map-of-reduce */
+/*
+ * pairwise_mapreduce -- for every body i, a reduce over all bodies j (a map of a reduce,
+ * Appendix A; the shape of the paper's tpacf / mri-q workloads, Table 1):
+ *   ACCEL_PAIR_GRAVITY_SOFTENED:
+ *     a_i = sum_j m_j (p_j - p_i) / (|p_j - p_i|^2 + eps^2)^(3/2)      (G = 1, FP32)
+ *  d_x, d_y, d_z, d_m  device float32 [n] (structure of arrays, e.g. from
+ *                      accel_marshal_records); outputs d_ax, d_ay, d_az float32 [n].
+ */
+accel_status pairwise_mapreduce(int32_t op, const float* d_x, const float* d_y, const float* d_z,
+                                const float* d_m, int64_t n, float eps, float* d_ax, float* d_ay,
+                                float* d_az, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACCEL_H */

@@ -1,0 +1,246 @@
+"""Thin PyTorch binding of the C ABI (include/accel.h): argument marshalling only.
+
+Each function has the name of the C entry point it calls.  Tensors are CUDA tensors
+unless stated; device memory (outputs and workspaces) is allocated with PyTorch, and every
+call is issued on ``torch.cuda.current_stream()``.  No computation of the path happens
+here: every step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.int32: L.I32, torch.int64: L.I64, torch.float32: L.F32, torch.float64: L.F64}
+_TORCH = {v: k for k, v in _DT.items()}
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _dt(t_or_dtype):
+    d = t_or_dtype.dtype if isinstance(t_or_dtype, torch.Tensor) else t_or_dtype
+    if d not in _DT:
+        raise TypeError(f"unsupported dtype {d}")
+    return _DT[d]
+
+
+def _ws(nbytes: int, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libaccel operates on CUDA tensors")
+
+
+def set_debug(on: bool):
+    """Debug mode: the library validates arguments on host and device and synchronizes."""
+    L.load().accel_set_debug(1 if on else 0)
+
+
+def version() -> str:
+    return L.load().accel_version().decode()
+
+
+# ------------------------------------------------------------------------ marshaling
+def accel_marshal_ragged(seqs, dtype=torch.int32, device="cuda"):
+    """Flatten a list of 1-D tensors (CUDA, or pinned CPU readable by the device) into
+    (flat data, int64 offsets) on ``device``."""
+    lib = L.load()
+    S = len(seqs)
+    lengths = (C.c_int64 * max(S, 1))(*[int(s.numel()) for s in seqs])
+    ptrs = (C.c_void_p * max(S, 1))(*[s.data_ptr() if s.numel() else 0 for s in seqs])
+    for s in seqs:
+        if s.dtype != dtype:
+            raise TypeError("all sequences must have the given dtype")
+        if not s.is_cuda and s.numel() and not s.is_pinned():
+            raise ValueError("host sequences must be in pinned memory")
+    total = sum(int(s.numel()) for s in seqs)
+    flat = torch.empty(total, dtype=dtype, device=device)
+    offsets = torch.empty(S + 1, dtype=torch.int64, device=device)
+    ws = _ws(lib.accel_marshal_ragged_workspace_size(S), device)
+    L.check("accel_marshal_ragged", lib.accel_marshal_ragged(ptrs, lengths, S, _dt(dtype), _ptr(flat),
+                                                             _ptr(offsets), _ptr(ws), ws.numel(), _stream()))
+    return flat, offsets
+
+
+def accel_marshal_records(aos: torch.Tensor, fields, inverse_from=None):
+    """Records -> structure of arrays.  ``aos`` is a CUDA tensor whose rows are records
+    (any dtype; the record size is its row size in bytes); ``fields`` = [(byte offset,
+    torch dtype)].  With ``inverse_from`` (list of per-field tensors), writes them back into
+    ``aos`` instead and returns ``aos``."""
+    lib = L.load()
+    _need_cuda(aos)
+    n = aos.shape[0]
+    rb = aos[0].numel() * aos.element_size() if n else aos.stride(0) * aos.element_size()
+    nf = len(fields)
+    offs = (C.c_int32 * nf)(*[int(o) for o, _ in fields])
+    dts = (C.c_int32 * nf)(*[_dt(d) for _, d in fields])
+    if inverse_from is None:
+        cols = [torch.empty(n, dtype=d, device=aos.device) for _, d in fields]
+    else:
+        cols = list(inverse_from)
+    ptrs = (C.c_void_p * nf)(*[c.data_ptr() for c in cols])
+    L.check("accel_marshal_records", lib.accel_marshal_records(_ptr(aos), n, rb, nf, offs, dts, ptrs,
+                                                               1 if inverse_from is not None else 0, _stream()))
+    return aos if inverse_from is not None else cols
+
+
+# ---------------------------------------------------------------------- map / reduce
+def accel_map(op: int, x: torch.Tensor, out_dtype=None, y: torch.Tensor | None = None, scalar: float = 0.0):
+    lib = L.load()
+    _need_cuda(x, y)
+    out_dtype = out_dtype or x.dtype
+    out = torch.empty(x.numel(), dtype=out_dtype, device=x.device)
+    L.check("accel_map", lib.accel_map(op, _dt(x), _ptr(x), _ptr(y), _dt(out_dtype), _ptr(out), x.numel(),
+                                       float(scalar), _stream()))
+    return out
+
+
+def accel_reduce(op: int, x: torch.Tensor):
+    lib = L.load()
+    _need_cuda(x)
+    out = torch.empty(1, dtype=x.dtype, device=x.device)
+    ws = _ws(lib.accel_reduce_workspace_size(x.numel(), _dt(x)), x.device)
+    L.check("accel_reduce", lib.accel_reduce(op, _dt(x), _ptr(x), x.numel(), _ptr(out), _ptr(ws), ws.numel(),
+                                             _stream()))
+    return out
+
+
+def accel_segreduce(op: int, fused_map: int, data: torch.Tensor, offsets: torch.Tensor, out_dtype=None,
+                    scalar: float = 0.0, out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    lib = L.load()
+    _need_cuda(data, offsets)
+    S = offsets.numel() - 1
+    N = data.numel()
+    out_dtype = out_dtype or (torch.int64 if data.dtype in (torch.int32, torch.int64) else data.dtype)
+    if out is None:
+        out = torch.empty(S, dtype=out_dtype, device=data.device)
+    need = lib.accel_segreduce_workspace_size(N, S)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, data.device)
+    L.check("accel_segreduce", lib.accel_segreduce(op, fused_map, _dt(data), _dt(out), _ptr(data), N,
+                                                   _ptr(offsets), S, float(scalar), _ptr(out), _ptr(ws),
+                                                   ws.numel(), _stream()))
+    return out
+
+
+def _tensor_desc(t: torch.Tensor):
+    d = L.accel_tensor()
+    d.data = t.data_ptr()
+    d.dtype = _dt(t)
+    d.rank = t.dim()
+    for i in range(min(t.dim(), L.MAX_RANK)):
+        d.dims[i] = t.shape[i]
+    return d
+
+
+def accel_loop(body: int, t0: torch.Tensor, t1: torch.Tensor, scalar: float, n: int | None = None):
+    """loop n f with a fixed body, in place on t0 (t0, t1 contiguous)."""
+    lib = L.load()
+    _need_cuda(t0, t1)
+    args = (L.accel_tensor * 2)(_tensor_desc(t0), _tensor_desc(t1))
+    n = t0.numel() if n is None else n
+    L.check("accel_loop", lib.accel_loop(body, n, args, 2, float(scalar), _stream()))
+    return t0
+
+
+# ------------------------------------------------------------------------------- HMM
+def _model(log_A, log_B, log_pi):
+    m = L.accel_hmm_model()
+    m.K = log_A.shape[0]
+    m.M = log_B.shape[1]
+    m.log_A = log_A.data_ptr()
+    m.log_B = log_B.data_ptr()
+    m.log_pi = log_pi.data_ptr()
+    return m
+
+
+def hmm_forward(log_A, log_B, log_pi, obs, offsets, precision=L.HMM_FP32_LOG, total_T: int | None = None,
+                out=None, ws=None):
+    """Per-sequence log-likelihoods (float64 [S]).  log_A [K,K], log_B [K,M], log_pi [K]
+    float32; obs int32 flat; offsets int64 [S+1]."""
+    lib = L.load()
+    _need_cuda(log_A, log_B, log_pi, obs, offsets)
+    for t in (log_A, log_B, log_pi):
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError("HMM parameters must be contiguous float32")
+    m = _model(log_A, log_B, log_pi)
+    S = offsets.numel() - 1
+    total_T = obs.numel() if total_T is None else total_T
+    if out is None:
+        out = torch.empty(S, dtype=torch.float64, device=obs.device)
+    need = lib.hmm_forward_workspace_size(C.byref(m), S, total_T, precision)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, obs.device)
+    L.check("hmm_forward", lib.hmm_forward(C.byref(m), precision, _ptr(obs), _ptr(offsets), S, total_T, _ptr(out),
+                                           _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | None = None, want_loglik=True,
+                ws=None):
+    """Gradients of sum_s w_s logL_s w.r.t. (log_A, log_B, log_pi) (float32) and logL
+    (float64 [S])."""
+    lib = L.load()
+    _need_cuda(log_A, log_B, log_pi, obs, offsets, weights)
+    m = _model(log_A, log_B, log_pi)
+    S = offsets.numel() - 1
+    K, M = m.K, m.M
+    if max_T is None:
+        max_T = int((offsets[1:] - offsets[:-1]).max().item()) if S else 0
+    gA = torch.empty(K, K, dtype=torch.float32, device=obs.device)
+    gB = torch.empty(K, M, dtype=torch.float32, device=obs.device)
+    gpi = torch.empty(K, dtype=torch.float32, device=obs.device)
+    ll = torch.empty(S, dtype=torch.float64, device=obs.device) if want_loglik else None
+    need = lib.hmm_adjoint_workspace_size(C.byref(m), S, obs.numel(), max_T)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, obs.device)
+    if weights is not None and weights.dtype != torch.float64:
+        weights = weights.to(torch.float64)
+    L.check("hmm_adjoint", lib.hmm_adjoint(C.byref(m), _ptr(obs), _ptr(offsets), S, obs.numel(), max_T,
+                                           _ptr(weights), _ptr(ll), _ptr(gA), _ptr(gB), _ptr(gpi), _ptr(ws),
+                                           ws.numel(), _stream()))
+    return gA, gB, gpi, ll
+
+
+class HMMLogLik(torch.autograd.Function):
+    """logL[S] = HMMLogLik.apply(log_A, log_B, log_pi, obs, offsets, precision).
+
+    Backward calls hmm_adjoint with the incoming gradient as per-sequence weights (the
+    gradient of sum_s w_s logL_s is linear in w), giving d/d log_A, d/d log_B, d/d log_pi.
+    """
+
+    @staticmethod
+    def forward(ctx, log_A, log_B, log_pi, obs, offsets, precision=L.HMM_FP32_LOG):
+        ctx.save_for_backward(log_A, log_B, log_pi, obs, offsets)
+        return hmm_forward(log_A, log_B, log_pi, obs, offsets, precision)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        log_A, log_B, log_pi, obs, offsets = ctx.saved_tensors
+        gA, gB, gpi, _ = hmm_adjoint(log_A, log_B, log_pi, obs, offsets,
+                                     weights=grad_out.contiguous().to(torch.float64), want_loglik=False)
+        return gA, gB, gpi, None, None, None
+
+
+# ------------------------------------------------------------------------- all-pairs
+def pairwise_mapreduce(x, y, z, m, eps: float, op: int = L.PAIR_GRAVITY_SOFTENED, out=None):
+    lib = L.load()
+    _need_cuda(x, y, z, m)
+    n = x.numel()
+    if out is None:
+        out = tuple(torch.empty(n, dtype=torch.float32, device=x.device) for _ in range(3))
+    ax, ay, az = out
+    L.check("pairwise_mapreduce", lib.pairwise_mapreduce(op, _ptr(x), _ptr(y), _ptr(z), _ptr(m), n, float(eps),
+                                                         _ptr(ax), _ptr(ay), _ptr(az), _stream()))
+    return ax, ay, az

@@ -1,0 +1,32 @@
+// Internal interfaces shared by the HMM kernels and the hmm_forward / hmm_adjoint entry
+// points (not part of the C ABI).
+#pragma once
+#include "common.cuh"
+
+namespace accel {
+namespace hmm {
+
+// Layout of the status block at the start of every HMM workspace.
+constexpr size_t kDebugScratchOff = 0;   // 8 bytes for debug-mode checks
+constexpr size_t kStatusOff = 8;         // int32 device status (ACCEL_OK or an error code)
+constexpr size_t kQueueOff = 16;         // uint64 sequence-queue counter
+
+// Sequence order by decreasing length (approximate: 1024 logarithmic length buckets), so
+// that long sequences start first and groups of consecutive sequences have similar
+// lengths.  order[q] = sequence index.  Scratch: order_ws_bytes(S) - S*4 bytes after order.
+size_t order_ws_bytes(int64_t S);
+accel_status order_by_length(const int64_t* d_off, int64_t S, int32_t* d_order, char* scratch, cudaStream_t st);
+
+// FP32 log-space forward (k_hmm_plain.cu).
+size_t plain_ws_bytes(int K, int M, int64_t S);
+accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const int64_t* off, int64_t S,
+                           double* loglik, char* ws, cudaStream_t st);
+
+// BF16 tensor-core scaled forward (k_hmm_tc.cu).
+size_t tc_ws_bytes(int K, int M, int64_t S);
+accel_status tc_forward(const accel_hmm_model* m, const int32_t* obs, const int64_t* off, int64_t S,
+                        double* loglik, char* ws, int32_t* d_status, cudaStream_t st);
+bool tc_supported(int K, int M);
+
+}  // namespace hmm
+}  // namespace accel

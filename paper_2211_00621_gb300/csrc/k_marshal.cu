@@ -1,0 +1,259 @@
+// Marshaling (Sec. 3.3): converting the sequential representation of an accelerated
+// binding's arguments into the backend format.
+//  K1 accel_marshal_ragged  -- [[T]] as a host list of S separately stored sequences ->
+//                              flat data + int64 offsets (flatten, Appendix A).
+//  K2 accel_marshal_records -- a sequence of records {l_i = e_i} stored as an array of
+//                              structures -> one array per field, or back.
+#include "common.cuh"
+
+namespace accel {
+namespace marshal {
+
+constexpr int kScanThreads = 1024;   // elements scanned per block = kScanThreads
+
+// ---------------------------------------------------------------- exclusive scan
+// Block-local inclusive scan of int64 (warp shuffles + one shared level).
+__device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t* s_warp) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) s_warp[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int64_t x = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int64_t o = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += o;
+        }
+        s_warp[lane] = x;  // inclusive warp prefix
+    }
+    __syncthreads();
+    if (w > 0) v += s_warp[w - 1];
+    return v;
+}
+
+// pass 1: per-block totals of the lengths
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const int64_t* __restrict__ len, int64_t S,
+                                                               int64_t* __restrict__ bsum) {
+    __shared__ int64_t s_warp[32];
+    int64_t i = blockIdx.x * (int64_t)kScanThreads + threadIdx.x;
+    int64_t v = i < S ? len[i] : 0;
+    v = block_incl_scan(v, s_warp);
+    if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = v;
+}
+
+// pass 2: exclusive scan of the block totals, in place, by one block (chunks with carry)
+__global__ void __launch_bounds__(kScanThreads) k_scan_totals(int64_t* __restrict__ bsum, int64_t nb) {
+    __shared__ int64_t s_warp[32];
+    __shared__ int64_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < nb ? bsum[i] : 0;
+        int64_t inc = block_incl_scan(v, s_warp);
+        int64_t carry = s_carry;
+        if (i < nb) bsum[i] = carry + inc - v;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) s_carry = carry + inc;
+        __syncthreads();
+    }
+}
+
+// pass 3: offsets[i] = block prefix + exclusive in-block prefix; offsets[S] = total
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(const int64_t* __restrict__ len, int64_t S,
+                                                              const int64_t* __restrict__ bpre,
+                                                              int64_t* __restrict__ off) {
+    __shared__ int64_t s_warp[32];
+    int64_t i = blockIdx.x * (int64_t)kScanThreads + threadIdx.x;
+    int64_t v = i < S ? len[i] : 0;
+    int64_t inc = block_incl_scan(v, s_warp);
+    int64_t p = bpre[blockIdx.x];
+    if (i < S) off[i] = p + inc - v;
+    if (i == S - 1) off[S] = p + inc;
+}
+
+// ---------------------------------------------------------------- ragged gather
+// One warp per sequence (grid-stride over sequences); each lane moves up to 8 elements
+// per round with all loads issued before the stores.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather(const T* const* __restrict__ ptrs, const int64_t* __restrict__ off,
+                                               int64_t S, T* __restrict__ flat) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < S; s += nwarps) {
+        const int64_t o = off[s];
+        const int64_t n = off[s + 1] - o;
+        const T* src = ptrs[s];
+        T* dst = flat + o;
+        for (int64_t base = 0; base < n; base += 32 * 8) {
+            T v[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                int64_t k = base + r * 32 + lane;
+                if (k < n) v[r] = src[k];
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                int64_t k = base + r * 32 + lane;
+                if (k < n) dst[k] = v[r];
+            }
+        }
+    }
+}
+
+size_t ws_layout(int64_t S, size_t* ptr_off, size_t* len_off, size_t* bsum_off) {
+    int64_t nb = (S + kScanThreads - 1) / kScanThreads;
+    *ptr_off = kStatusBytes;
+    *len_off = align_up(*ptr_off + (size_t)S * 8, 256);
+    *bsum_off = align_up(*len_off + (size_t)S * 8, 256);
+    return align_up(*bsum_off + (size_t)(nb > 0 ? nb : 1) * 8, 256);
+}
+
+// ---------------------------------------------------------------- records
+struct FieldDesc {
+    int32_t nfields;
+    int32_t record_bytes;
+    int32_t off[ACCEL_MAX_FIELDS];
+    int32_t size[ACCEL_MAX_FIELDS];
+    void* soa[ACCEL_MAX_FIELDS];
+};
+
+// Fast path: 16-byte records of four 4-byte fields at offsets 0, 4, 8, 12.
+template <bool INV>
+__global__ void __launch_bounds__(256) k_records16(int4* __restrict__ aos, int64_t n, FieldDesc fd) {
+    int32_t* f0 = (int32_t*)fd.soa[0];
+    int32_t* f1 = (int32_t*)fd.soa[1];
+    int32_t* f2 = (int32_t*)fd.soa[2];
+    int32_t* f3 = (int32_t*)fd.soa[3];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (!INV) {
+            int4 r = aos[i];
+            f0[i] = r.x; f1[i] = r.y; f2[i] = r.z; f3[i] = r.w;
+        } else {
+            aos[i] = make_int4(f0[i], f1[i], f2[i], f3[i]);
+        }
+    }
+}
+
+// General path: one thread per (record, field) pair, 4- or 8-byte scalars.
+template <bool INV>
+__global__ void __launch_bounds__(256) k_records(char* __restrict__ aos, int64_t n, FieldDesc fd) {
+    int64_t total = n * fd.nfields;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / fd.nfields;
+        int f = (int)(q - i * fd.nfields);
+        char* rec = aos + i * fd.record_bytes + fd.off[f];
+        if (fd.size[f] == 4) {
+            int32_t* col = (int32_t*)fd.soa[f];
+            if constexpr (!INV) col[i] = *(const int32_t*)rec; else *(int32_t*)rec = col[i];
+        } else {
+            int64_t* col = (int64_t*)fd.soa[f];
+            if constexpr (!INV) col[i] = *(const int64_t*)rec; else *(int64_t*)rec = col[i];
+        }
+    }
+}
+
+}  // namespace marshal
+}  // namespace accel
+
+using namespace accel;
+using namespace accel::marshal;
+
+extern "C" {
+
+size_t accel_marshal_ragged_workspace_size(int64_t S) {
+    size_t a, b, c;
+    return ws_layout(S < 0 ? 0 : S, &a, &b, &c);
+}
+
+accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_lengths, int64_t S, int32_t dtype,
+                                  void* d_flat, int64_t* d_offsets, void* d_ws, size_t ws_bytes, void* stream) {
+    ACCEL_REQUIRE(S >= 0, ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: S < 0");
+    ACCEL_REQUIRE(dtype_valid(dtype), ACCEL_ERR_DTYPE, "accel_marshal_ragged: bad dtype");
+    ACCEL_REQUIRE(d_offsets && d_ws && (S == 0 || (h_ptrs && h_lengths)), ACCEL_ERR_INVALID_ARG,
+                  "accel_marshal_ragged: null pointer");
+    ACCEL_REQUIRE(((uintptr_t)d_ws % 256) == 0, ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: d_ws must be 256-byte aligned");
+    size_t po, lo, bo;
+    size_t need = ws_layout(S, &po, &lo, &bo);
+    ACCEL_REQUIRE(ws_bytes >= need, ACCEL_ERR_WORKSPACE, "accel_marshal_ragged: workspace %zu < %zu bytes", ws_bytes, need);
+    int64_t total = 0;
+    for (int64_t s = 0; s < S; ++s) {
+        ACCEL_REQUIRE(h_lengths[s] >= 0, ACCEL_ERR_SHAPE, "accel_marshal_ragged: length[%lld] < 0", (long long)s);
+        ACCEL_REQUIRE(h_lengths[s] == 0 || h_ptrs[s], ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: ptr[%lld] is null", (long long)s);
+        total += h_lengths[s];
+    }
+    ACCEL_REQUIRE(total == 0 || d_flat, ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: d_flat is null");
+    cudaStream_t st = as_stream(stream);
+    if (S == 0) {
+        ACCEL_CUDA_TRY(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), st));
+        return after_launch(st, "accel_marshal_ragged");
+    }
+    char* ws = (char*)d_ws;
+    int64_t* d_len = (int64_t*)(ws + lo);
+    int64_t* d_bsum = (int64_t*)(ws + bo);
+    const void** d_ptrs = (const void**)(ws + po);
+    ACCEL_CUDA_TRY(cudaMemcpyAsync(d_ptrs, h_ptrs, (size_t)S * sizeof(void*), cudaMemcpyHostToDevice, st));
+    ACCEL_CUDA_TRY(cudaMemcpyAsync(d_len, h_lengths, (size_t)S * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    int64_t nb = (S + kScanThreads - 1) / kScanThreads;
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum);
+    k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
+    k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum, d_offsets);
+    int64_t warps_needed = S;
+    int64_t blocks = (warps_needed + 7) / 8;
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (dtype_size(dtype) == 4)
+        k_gather<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t* const*)d_ptrs, d_offsets, S, (int32_t*)d_flat);
+    else
+        k_gather<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t* const*)d_ptrs, d_offsets, S, (int64_t*)d_flat);
+    return after_launch(st, "accel_marshal_ragged");
+}
+
+accel_status accel_marshal_records(void* d_aos, int64_t n, int32_t record_bytes, int32_t nfields,
+                                   const int32_t* h_field_offsets, const int32_t* h_field_dtypes, void* const* h_soa,
+                                   int32_t inverse, void* stream) {
+    ACCEL_REQUIRE(n >= 0 && record_bytes > 0, ACCEL_ERR_INVALID_ARG, "accel_marshal_records: bad size");
+    ACCEL_REQUIRE(nfields >= 1 && nfields <= ACCEL_MAX_FIELDS, ACCEL_ERR_INVALID_ARG,
+                  "accel_marshal_records: nfields must be 1..%d", ACCEL_MAX_FIELDS);
+    ACCEL_REQUIRE(h_field_offsets && h_field_dtypes && h_soa, ACCEL_ERR_INVALID_ARG, "accel_marshal_records: null pointer");
+    FieldDesc fd{};
+    fd.nfields = nfields;
+    fd.record_bytes = record_bytes;
+    for (int f = 0; f < nfields; ++f) {
+        ACCEL_REQUIRE(dtype_valid(h_field_dtypes[f]), ACCEL_ERR_DTYPE, "accel_marshal_records: bad dtype of field %d", f);
+        int sz = (int)dtype_size(h_field_dtypes[f]);
+        ACCEL_REQUIRE(h_field_offsets[f] >= 0 && h_field_offsets[f] + sz <= record_bytes, ACCEL_ERR_SHAPE,
+                      "accel_marshal_records: field %d outside the record", f);
+        ACCEL_REQUIRE(h_field_offsets[f] % sz == 0 && record_bytes % sz == 0, ACCEL_ERR_DTYPE,
+                      "accel_marshal_records: field %d not naturally aligned", f);
+        ACCEL_REQUIRE(n == 0 || h_soa[f], ACCEL_ERR_INVALID_ARG, "accel_marshal_records: field %d array is null", f);
+        fd.off[f] = h_field_offsets[f];
+        fd.size[f] = sz;
+        fd.soa[f] = h_soa[f];
+    }
+    if (n == 0) return ok();
+    ACCEL_REQUIRE(d_aos, ACCEL_ERR_INVALID_ARG, "accel_marshal_records: d_aos is null");
+    cudaStream_t st = as_stream(stream);
+    bool fast = record_bytes == 16 && nfields == 4 && ((uintptr_t)d_aos % 16) == 0;
+    for (int f = 0; fast && f < 4; ++f) fast = fd.off[f] == 4 * f && fd.size[f] == 4;
+    int64_t work = fast ? n : n * nfields;
+    int64_t blocks = (work + 255) / 256;
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (fast) {
+        if (inverse) k_records16<true><<<(unsigned)blocks, 256, 0, st>>>((int4*)d_aos, n, fd);
+        else k_records16<false><<<(unsigned)blocks, 256, 0, st>>>((int4*)d_aos, n, fd);
+    } else {
+        if (inverse) k_records<true><<<(unsigned)blocks, 256, 0, st>>>((char*)d_aos, n, fd);
+        else k_records<false><<<(unsigned)blocks, 256, 0, st>>>((char*)d_aos, n, fd);
+    }
+    return after_launch(st, "accel_marshal_records");
+}
+
+}  // extern "C"

@@ -1,0 +1,354 @@
+// Segmented reduce with a fused map (K5): the nested pattern
+//     map (lam s. reduce f ne (map g s))   over a flattened [[T]]     (Appendix A)
+// d_out[s] = f-fold of g(data[k]) over k in [off[s], off[s+1]), ne for an empty segment.
+//
+// Design (HBM-bound streaming):
+//  * The flat data is cut into fixed tiles of 16 KB (4096 4-byte or 2048 8-byte
+//    elements), one CTA of 256 threads per tile, so the load is balanced whatever the
+//    segment lengths are.  A segment is OWNED by the tile holding its last element (an
+//    empty segment by the tile holding its position, clamped to N-1).  Owned segments of
+//    tile b are the contiguous range [lo[b], lo[b+1]) found by a small partition kernel
+//    (binary search of the monotone key).
+//  * Loads are 16-byte vectors, coalesced across the CTA, staged through shared memory
+//    with an XOR swizzle so that each thread then reads its 16 contiguous elements
+//    conflict-free.  The tile's offsets are cached in shared memory too.
+//  * Each thread folds its elements in order, writing every segment that starts and
+//    ends inside it.  Partial segments crossing thread boundaries are combined by a
+//    CTA-wide key-segmented scan; segments crossing tile boundaries by a deterministic
+//    fixup kernel that folds the preceding tiles' carry-outs in tile order.
+#include "common.cuh"
+
+namespace accel {
+namespace segred {
+
+constexpr int kThreads = 256;
+constexpr int kTileBytes = 16384;
+constexpr int kVecs = kTileBytes / 16;            // 1024 16-byte vectors per tile
+constexpr int kVecPerThread = kVecs / kThreads;   // 4
+constexpr int kOffCap = 1024;                     // offsets cached in shared memory
+
+template <typename Tin> constexpr int items() { return kTileBytes / kThreads / (int)sizeof(Tin); }
+template <typename Tin> constexpr int tile_elems() { return kTileBytes / (int)sizeof(Tin); }
+
+__device__ __forceinline__ int swz(int v) { return v ^ ((v >> 3) & 7); }
+
+template <typename C> __device__ __forceinline__ C map_rt(int op, C x, C s) {
+    switch (op) {
+        case ACCEL_MAP_SQ_PLUS_ONE: return map_apply<ACCEL_MAP_SQ_PLUS_ONE, C>(x, C(0), s);
+        case ACCEL_MAP_NEG: return map_apply<ACCEL_MAP_NEG, C>(x, C(0), s);
+        case ACCEL_MAP_ABS: return map_apply<ACCEL_MAP_ABS, C>(x, C(0), s);
+        case ACCEL_MAP_SCALE: return map_apply<ACCEL_MAP_SCALE, C>(x, C(0), s);
+        default: return x;
+    }
+}
+
+// key(s): last element of a non-empty segment, position of an empty one, clamped to N-1.
+__device__ __forceinline__ int64_t seg_key(const int64_t* __restrict__ off, int64_t s, int64_t N) {
+    int64_t a = off[s], b = off[s + 1];
+    int64_t k = b > a ? b - 1 : a;
+    return k < N - 1 ? k : N - 1;
+}
+
+// lo[b] = first segment with key >= b * TILE, for b in [0, ntiles]; lo[ntiles] = S.
+__global__ void k_partition(const int64_t* __restrict__ off, int64_t S, int64_t N, int64_t tile,
+                            int64_t ntiles, int64_t* __restrict__ lo) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b > ntiles) return;
+    if (b == ntiles) { lo[b] = S; return; }
+    int64_t target = b * tile;
+    int64_t a = 0, z = S;
+    while (a < z) {
+        int64_t mid = (a + z) >> 1;
+        if (seg_key(off, mid, N) >= target) z = mid; else a = mid + 1;
+    }
+    lo[b] = a;
+}
+
+template <typename C> struct KV { int64_t k; C v; };
+
+template <int OP, typename C>
+__device__ __forceinline__ KV<C> seg_combine(KV<C> a, KV<C> b) {
+    // (k1, v1) + (k2, v2) = (k2, k1 == k2 ? v1 f v2 : v2); associative for monotone keys.
+    KV<C> r;
+    r.k = b.k;
+    r.v = (a.k == b.k) ? red_combine<OP, C>(a.v, b.v) : b.v;
+    return r;
+}
+
+template <typename C> __device__ __forceinline__ C shfl_up_val(C v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+
+template <typename Tin, typename Tout, int OP>
+__global__ void __launch_bounds__(kThreads)
+k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
+            const int64_t* __restrict__ lo_arr, int map_op, double scalar, Tout* __restrict__ out,
+            int64_t* __restrict__ tail_seg, typename compute_of<Tout>::type* __restrict__ tail_val) {
+    using C = typename compute_of<Tout>::type;
+    constexpr int IT = items<Tin>();
+    constexpr int TE = tile_elems<Tin>();
+    __shared__ int4 s_data[kVecs];
+    __shared__ int64_t s_off[kOffCap];
+    __shared__ KV<C> s_warp[kThreads / 32];
+
+    const int t = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    const int64_t e0 = b * TE;
+    const int64_t e1 = (e0 + TE < N) ? e0 + TE : N;
+    const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
+    const C nel = red_neutral<C>(OP);
+    const C sc = (C)scalar;
+
+    // ---- stage the tile (16-byte vectors, coalesced) and the tile's offsets
+    const bool full = (e1 - e0) == TE;
+    if (full) {
+        const int4* src = reinterpret_cast<const int4*>(data + e0);
+#pragma unroll
+        for (int r = 0; r < kVecPerThread; ++r) {
+            int v = r * kThreads + t;
+            s_data[swz(v)] = __ldg(src + v);
+        }
+    } else {
+        Tin* sd = reinterpret_cast<Tin*>(s_data);
+        constexpr int per_vec = 16 / (int)sizeof(Tin);
+        for (int e = t; e < TE; e += kThreads) {
+            int v = e / per_vec, w = e % per_vec;
+            Tin x = (e0 + e < e1) ? data[e0 + e] : Tin(0);
+            sd[swz(v) * per_vec + w] = x;
+        }
+    }
+    // offsets off[lo_b .. last] with last = min(hi_b + 1, S)
+    const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
+    const int64_t cnt = last - lo_b + 1;
+    const bool off_in_smem = cnt <= kOffCap;
+    if (off_in_smem)
+        for (int64_t i = t; i < cnt; i += kThreads) s_off[i] = off[lo_b + i];
+    __syncthreads();
+
+    auto getoff = [&](int64_t s) -> int64_t {
+        return off_in_smem ? s_off[s - lo_b] : off[s];
+    };
+    // end of segment s (exclusive); "infinite" for a segment past the cached range
+    auto seg_end = [&](int64_t s) -> int64_t { return (s + 1 <= last) ? getoff(s + 1) : INT64_MAX; };
+
+    // ---- this thread's elements [k0, k1)
+    const int64_t k0 = e0 + (int64_t)t * IT;
+    const int64_t k1r = k0 + IT;
+    const int64_t k1 = k1r < e1 ? k1r : e1;
+    const bool active = k0 < e1;
+
+    C x[IT];
+    {
+        int4 raw[kVecPerThread];
+#pragma unroll
+        for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
+        const Tin* xs = reinterpret_cast<const Tin*>(raw);
+#pragma unroll
+        for (int i = 0; i < IT; ++i) x[i] = map_rt<C>(map_op, (C)xs[i], sc);
+    }
+
+    KV<C> tail;           // (key, partial) handed to the scan
+    bool tail_open = false;  // elements accumulated after the last segment end
+    bool has_head = false;
+    int64_t head_seg = 0;
+    C head_val = nel;
+
+    if (active) {
+        // segment containing k0: largest s in [lo_b, hi_b] with off[s] <= k0
+        int64_t a = lo_b, z = hi_b;
+        while (a < z) {
+            int64_t mid = (a + z + 1) >> 1;
+            if (getoff(mid) <= k0) a = mid; else z = mid - 1;
+        }
+        int64_t s = a;
+        // empty segments positioned at k0 precede s: they are owned here
+        for (int64_t q = s - 1; q >= lo_b && getoff(q) == k0 && getoff(q + 1) == k0; --q) out[q] = (Tout)nel;
+        bool started_here = getoff(s) >= k0;
+        int64_t nend = seg_end(s);
+        C acc = nel;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            int64_t k = k0 + i;
+            if (k < k1) {
+                acc = red_combine<OP, C>(acc, x[i]);
+                tail_open = true;
+                if (k == nend - 1) {
+                    tail_open = false;
+                    if (started_here) out[s] = (Tout)acc;
+                    else { has_head = true; head_seg = s; head_val = acc; }
+                    acc = nel;
+                    started_here = true;
+                    ++s;
+                    // empty segments at position k+1 belong to this thread if k+1 < k1, or
+                    // if this is the end of the data (their key is clamped to N-1)
+                    while (s < S && (k + 1 < k1 || k + 1 == N)) {
+                        int64_t so = getoff(s), se = seg_end(s);
+                        if (!(so == k + 1 && se == k + 1)) break;
+                        out[s] = (Tout)nel;
+                        ++s;
+                    }
+                    nend = (s < S) ? seg_end(s) : INT64_MAX;
+                }
+            }
+        }
+        // elements after the last boundary form this thread's tail partial of segment s
+        tail.k = s;
+        tail.v = acc;
+    } else {
+        tail.k = INT64_MAX;
+        tail.v = nel;
+    }
+
+    // ---- CTA-wide inclusive key-segmented scan of the tails
+    const int lane = t & 31, warp = t >> 5;
+    KV<C> q = tail;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        KV<C> o;
+        o.k = __shfl_up_sync(0xffffffffu, q.k, d);
+        o.v = shfl_up_val<C>(q.v, d);
+        if (lane >= d) q = seg_combine<OP, C>(o, q);
+    }
+    if (lane == 31) s_warp[warp] = q;
+    __syncthreads();
+    KV<C> wpre;  // fold of warps 0..warp-1
+    wpre.k = INT64_MIN;
+    wpre.v = nel;
+    for (int w = 0; w < warp; ++w) wpre = (w == 0) ? s_warp[0] : seg_combine<OP, C>(wpre, s_warp[w]);
+    if (warp > 0) q = seg_combine<OP, C>(wpre, q);
+    // exclusive value for this thread = inclusive value of thread t-1
+    KV<C> ex;
+    ex.k = __shfl_up_sync(0xffffffffu, q.k, 1);
+    ex.v = shfl_up_val<C>(q.v, 1);
+    if (lane == 0) ex = wpre;
+
+    if (has_head) {
+        C carry = (t > 0 && ex.k == head_seg) ? ex.v : nel;
+        out[head_seg] = (Tout)red_combine<OP, C>(carry, head_val);
+    }
+    // tile carry-out: the last active thread
+    const int t_last = (int)((e1 - e0 - 1) / IT);
+    if (t == t_last) {
+        if (tail_open) { tail_seg[b] = tail.k; tail_val[b] = q.v; }
+        else tail_seg[b] = -1;
+    }
+}
+
+// Folds the carry-outs of the tiles preceding b into the first segment b owns, when that
+// segment started in an earlier tile.  Tile order is kept, so float results are
+// deterministic.
+template <typename Tout, int OP>
+__global__ void k_fixup(const int64_t* __restrict__ off, const int64_t* __restrict__ lo_arr, int64_t ntiles,
+                        int64_t tile, const int64_t* __restrict__ tail_seg,
+                        const typename compute_of<Tout>::type* __restrict__ tail_val, Tout* __restrict__ out) {
+    using C = typename compute_of<Tout>::type;
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= ntiles || b == 0) return;
+    int64_t s = lo_arr[b];
+    if (s >= lo_arr[b + 1]) return;            // owns nothing
+    if (off[s] >= b * tile) return;            // first owned segment starts in this tile
+    if (off[s + 1] == off[s]) return;          // empty (cannot cross)
+    int64_t a = b - 1;
+    while (a >= 0 && tail_seg[a] == s) --a;
+    C carry = red_neutral<C>(OP);
+    for (int64_t i = a + 1; i < b; ++i) carry = red_combine<OP, C>(carry, tail_val[i]);
+    out[s] = (Tout)red_combine<OP, C>(carry, (C)out[s]);
+}
+
+template <typename Tout>
+__global__ void k_fill(Tout* __restrict__ out, int64_t S, Tout v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) out[i] = v;
+}
+
+struct Layout {
+    int64_t ntiles;
+    size_t lo_off, seg_off, val_off, total;
+};
+
+static Layout layout(int64_t N, int64_t S, size_t in_size) {
+    Layout L;
+    int64_t te = kTileBytes / (int64_t)in_size;
+    L.ntiles = (N + te - 1) / te;
+    L.lo_off = kStatusBytes;
+    L.seg_off = align_up(L.lo_off + (size_t)(L.ntiles + 1) * 8, 256);
+    L.val_off = align_up(L.seg_off + (size_t)L.ntiles * 8, 256);
+    L.total = align_up(L.val_off + (size_t)L.ntiles * 8, 256);
+    (void)S;
+    return L;
+}
+
+template <typename Tin, typename Tout>
+static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t N, const int64_t* d_off,
+                        int64_t S, double scalar, void* d_out, void* d_ws, cudaStream_t st) {
+    using C = typename compute_of<Tout>::type;
+    Layout L = layout(N, S, sizeof(Tin));
+    char* ws = (char*)d_ws;
+    int64_t* lo = (int64_t*)(ws + L.lo_off);
+    int64_t* tseg = (int64_t*)(ws + L.seg_off);
+    C* tval = (C*)(ws + L.val_off);
+    Tout* out = (Tout*)d_out;
+    if (N == 0) {
+        Tout nel = 0;
+        ACCEL_DISPATCH_RED(op, OPC, (nel = (Tout)red_neutral<C>(OPC)));
+        int g = (int)((S + 255) / 256);
+        if (g > 8 * num_sms()) g = 8 * num_sms();
+        k_fill<Tout><<<g, 256, 0, st>>>(out, S, nel);
+        return after_launch(st, "accel_segreduce(fill)");
+    }
+    int64_t te = tile_elems<Tin>();
+    k_partition<<<(unsigned)((L.ntiles + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);
+    ACCEL_DISPATCH_RED(op, OPC, {
+        k_segreduce<Tin, Tout, OPC><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
+            (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, tval);
+        k_fixup<Tout, OPC><<<(unsigned)((L.ntiles + 255) / 256), 256, 0, st>>>(d_off, lo, L.ntiles, te, tseg, tval, out);
+    });
+    return after_launch(st, "accel_segreduce");
+}
+
+}  // namespace segred
+}  // namespace accel
+
+using namespace accel;
+
+extern "C" {
+
+size_t accel_segreduce_workspace_size(int64_t N, int64_t S) {
+    // sized for the smallest element (most tiles)
+    return segred::layout(N < 0 ? 0 : N, S, 4).total;
+}
+
+accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, int32_t out_dtype, const void* d_data,
+                             int64_t N, const int64_t* d_offsets, int64_t S, double scalar, void* d_out, void* d_ws,
+                             size_t ws_bytes, void* stream) {
+    ACCEL_REQUIRE(op >= ACCEL_RED_ADD && op <= ACCEL_RED_MAX, ACCEL_ERR_INVALID_ARG, "accel_segreduce: bad op %d", op);
+    ACCEL_REQUIRE(fused_map >= ACCEL_MAP_IDENTITY && fused_map <= ACCEL_MAP_SCALE, ACCEL_ERR_INVALID_ARG,
+                  "accel_segreduce: fused map must be a single-operand map (got %d)", fused_map);
+    ACCEL_REQUIRE(dtype_valid(in_dtype) && dtype_valid(out_dtype), ACCEL_ERR_DTYPE, "accel_segreduce: bad dtype");
+    ACCEL_REQUIRE(dtype_is_int(in_dtype) == dtype_is_int(out_dtype), ACCEL_ERR_DTYPE,
+                  "accel_segreduce: input and output must both be integer or both float");
+    ACCEL_REQUIRE(N >= 0 && S >= 0, ACCEL_ERR_INVALID_ARG, "accel_segreduce: negative size");
+    ACCEL_REQUIRE(d_offsets && d_ws && (S == 0 || d_out) && (N == 0 || d_data), ACCEL_ERR_INVALID_ARG,
+                  "accel_segreduce: null pointer");
+    ACCEL_REQUIRE(((uintptr_t)d_data % 16) == 0, ACCEL_ERR_INVALID_ARG, "accel_segreduce: d_data must be 16-byte aligned");
+    ACCEL_REQUIRE(((uintptr_t)d_ws % 256) == 0, ACCEL_ERR_INVALID_ARG, "accel_segreduce: d_ws must be 256-byte aligned");
+    ACCEL_REQUIRE(ws_bytes >= accel_segreduce_workspace_size(N, S), ACCEL_ERR_WORKSPACE,
+                  "accel_segreduce: workspace %zu < %zu bytes", ws_bytes, accel_segreduce_workspace_size(N, S));
+    if (S == 0) return ok();
+    cudaStream_t st = as_stream(stream);
+    if (debug_mode()) {
+        accel_status r = debug_check_offsets(d_offsets, S, N, 0, d_ws, st);
+        if (r != ACCEL_OK) return r;
+    }
+    accel_status r = ACCEL_OK;
+    switch (in_dtype * 4 + out_dtype) {
+        case ACCEL_I32 * 4 + ACCEL_I32: r = segred::run<int32_t, int32_t>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+        case ACCEL_I32 * 4 + ACCEL_I64: r = segred::run<int32_t, int64_t>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+        case ACCEL_I64 * 4 + ACCEL_I64: r = segred::run<int64_t, int64_t>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+        case ACCEL_I64 * 4 + ACCEL_I32: r = segred::run<int64_t, int32_t>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+        case ACCEL_F32 * 4 + ACCEL_F32: r = segred::run<float, float>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+        case ACCEL_F32 * 4 + ACCEL_F64: r = segred::run<float, double>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+        case ACCEL_F64 * 4 + ACCEL_F64: r = segred::run<double, double>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+        default: r = segred::run<double, float>(op, fused_map, d_data, N, d_offsets, S, scalar, d_out, d_ws, st); break;
+    }
+    return r;
+}
+
+}  // extern "C"
