@@ -30,8 +30,8 @@ k_plain_warp(const float* __restrict__ logA, const float* __restrict__ logB, con
              int K, int M, const int32_t* __restrict__ obs, const int64_t* __restrict__ off, int64_t S,
              double* __restrict__ loglik) {
     extern __shared__ float smem[];
-    float* sB = smem;                        // [M][K]  log B^T
-    float* sP = smem + (size_t)M * K;        // [4][32 J] per-warp exp-shifted alphas
+    float* sB = smem;                                  // [M][K]  log B^T
+    float* sP = smem + (((size_t)M * K + 3) & ~(size_t)3);   // [4][32 J] per-warp, 16-byte aligned
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int idx = threadIdx.x; idx < M * K; idx += blockDim.x) {
         int j = idx / M, k = idx - j * M;
@@ -126,8 +126,9 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
             int K, int M, const int32_t* __restrict__ obs, const int64_t* __restrict__ off, int64_t S,
             const int32_t* __restrict__ order, double* __restrict__ loglik) {
     extern __shared__ float smem[];
+    const int Kp = (K + 3) & ~3;                // padded row stride of sP (16-byte rows)
     float* sB = smem;                           // [M][K]
-    float* sP = smem + (size_t)M * K;           // [kG][K]
+    float* sP = smem + (((size_t)M * K + 3) & ~(size_t)3);   // [kG][Kp], 16-byte aligned
     __shared__ float s_red[kG][kCtaThreads / 32];
     __shared__ int64_t s_T[kG], s_o0[kG];
     const int j = threadIdx.x, lane = j & 31, w = j >> 5;
@@ -174,7 +175,7 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
             float v = s_red[g][0];
             for (int q = 1; q < kCtaThreads / 32; ++q) v = fmaxf(v, s_red[g][q]);
             m[g] = v;
-            if (jv) sP[g * K + j] = (t < T[g]) ? __expf(r[g] - v) : 0.f;
+            if (jv) sP[g * Kp + j] = (t < T[g]) ? __expf(r[g] - v) : 0.f;
         }
         __syncthreads();
         float acc[kG];
@@ -188,7 +189,7 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
                 float a2 = __ldg(Ac + (int64_t)(i + 2) * K), a3 = __ldg(Ac + (int64_t)(i + 3) * K);
 #pragma unroll
                 for (int g = 0; g < kG; ++g) {
-                    float4 p = *reinterpret_cast<const float4*>(sP + g * K + i);
+                    float4 p = *reinterpret_cast<const float4*>(sP + g * Kp + i);
                     acc[g] = fmaf(p.x, a0, acc[g]);
                     acc[g] = fmaf(p.y, a1, acc[g]);
                     acc[g] = fmaf(p.z, a2, acc[g]);
@@ -198,7 +199,7 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
             for (; i < K; ++i) {
                 float a0 = __ldg(Ac + (int64_t)i * K);
 #pragma unroll
-                for (int g = 0; g < kG; ++g) acc[g] = fmaf(sP[g * K + i], a0, acc[g]);
+                for (int g = 0; g < kG; ++g) acc[g] = fmaf(sP[g * Kp + i], a0, acc[g]);
             }
         }
 #pragma unroll
@@ -254,7 +255,7 @@ accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const i
                            double* loglik, char* ws, cudaStream_t st) {
     const int K = m->K, M = m->M;
     if (K <= 64) {
-        size_t smem = ((size_t)M * K + 4 * 64) * sizeof(float);
+        size_t smem = ((((size_t)M * K + 3) & ~(size_t)3) + 4 * 64) * sizeof(float);
         ACCEL_REQUIRE(smem <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_forward: M*K too large for the FP32 kernel");
         unsigned grid = (unsigned)((S + 3) / 4);
         if (K <= 32) {
@@ -266,7 +267,7 @@ accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const i
         }
         return after_launch(st, "hmm_forward(fp32 warp)");
     }
-    size_t smem = ((size_t)M * K + (size_t)kG * K) * sizeof(float);
+    size_t smem = ((((size_t)M * K + 3) & ~(size_t)3) + (size_t)kG * ((K + 3) & ~3)) * sizeof(float);
     ACCEL_REQUIRE(smem <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_forward: M*K too large for the FP32 kernel");
     float* Aexp = (float*)ws;
     int32_t* order = (int32_t*)(ws + align_up((size_t)K * K * 4, 256));

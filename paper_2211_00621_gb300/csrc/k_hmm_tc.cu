@@ -193,9 +193,12 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
             if (m == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
             break;
         }
-        // ---- epilogue of step `pos` for the row's current sequence
-        if (iter > 0 && seq >= 0) {
-            const int ob = o[pos];
+        // ---- epilogue of step `pos` for the row's current sequence.  tcgen05.ld is
+        // warp-collective (.sync.aligned): every thread of a warp executes the loads, and
+        // rows without a sequence ignore what they read.
+        if (iter > 0 && __any_sync(0xffffffffu, seq >= 0)) {
+            const bool act = seq >= 0;
+            const int ob = act ? o[pos] : 0;
             float csum = 0.f;
             for (int jc = 0; jc < K; jc += 32) {
                 uint32_t d[32];
@@ -205,25 +208,34 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
 #pragma unroll
                 for (int u = 0; u < 32; ++u) csum = fmaf(__uint_as_float(d[u]), b[u], csum);
             }
-            if (pos == T - 1) {
-                loglik[seq] = 0.6931471805599453 * (double)E + log((double)csum);
-                seq = -1;
-            } else {
-                int e;
-                frexpf(csum, &e);
-                const float scale = ldexpf(1.0f, -e);
-                E += e;
+            bool cont = false;
+            float scale = 1.f;
+            if (act) {
+                if (pos == T - 1) {
+                    loglik[seq] = 0.6931471805599453 * (double)E + log((double)csum);
+                    seq = -1;
+                } else {
+                    int e;
+                    frexpf(csum, &e);
+                    scale = ldexpf(1.0f, -e);
+                    E += e;
+                    cont = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, cont)) {
                 for (int jc = 0; jc < K; jc += 32) {
                     uint32_t d[32];
-                    float b[32], v[32];
                     tc::tmem_ld32(trow + jc, d);
-                    load_emis(ob, jc, b);
+                    if (cont) {
+                        float b[32], v[32];
+                        load_emis(ob, jc, b);
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) v[u] = __uint_as_float(d[u]) * b[u];
-                    store_chunk(jc, v, scale);
+                        for (int u = 0; u < 32; ++u) v[u] = __uint_as_float(d[u]) * b[u];
+                        store_chunk(jc, v, scale);
+                    }
                 }
-                ++pos;
             }
+            if (cont) ++pos;
         }
         // ---- idle row: start the next sequence of the queue (alpha~_1 = pi o b(o_1))
         while (seq < 0 && !queue_empty) {
