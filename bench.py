@@ -1,0 +1,506 @@
+"""Benchmark of the accelerated hot path on GB300.
+
+One step = one pass of every hot-path row over its synthetic workload, inputs resident in
+HBM when the timed region starts:
+  segreduce   4,096 int32 sequences (lengths U{0..256}, values U{-1000..1000}): ragged
+              marshal -> fused map x*x+1 + int64 segmented sum -> int64 max; plus the loop
+              body b = 2a over the flat data
+  hmm_plain   FP32 log-space HMM forward, K=64, M=32, 512 sequences x 1000 steps
+  hmm_bf16    BF16 tensor-core scaled forward, K=256, M=64, 4,096 sequences, lengths
+              log-uniform in [50, 5000], one persistent launch
+  hmm_adjoint forward + adjoint, K=256, M=64, 1,024 sequences, lengths U{200..2000}
+  allpairs    records {pos: float3, mass: float} -> SoA, all-pairs softened gravity, N=65,536
+
+Metric: HMM state-steps per second (K x sum of lengths, counted once for every forward
+pass and once for every adjoint pass) over the whole step; per-row times, the segmented
+reduce's GB/s and every kernel's roofline fraction are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_00621_gb300 import synth  # noqa: E402
+
+METRIC = "HMM fwd+adjoint state-steps/s & seg-reduce GB/s vs plain form, 1 GB300"
+UNIT = "state-steps/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------ workloads
+def hmm_inputs(cfg, torch, dev):
+    p = synth.hmm_workload(cfg["seed"], cfg["K"], cfg["M"], cfg["S"], cfg["kind"], cfg["lo"], cfg["hi"])
+    logs = synth.hmm_log_inputs_f32(p)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in logs.items()}
+    d["obs"] = torch.from_numpy(p["obs"]).to(dev)
+    d["offsets"] = torch.from_numpy(p["offsets"]).to(dev)
+    d["host"] = {"obs": p["obs"], "offsets": p["offsets"], **logs}
+    d["K"], d["S"], d["sumT"], d["maxT"] = cfg["K"], cfg["S"], int(p["lengths"].sum()), int(p["lengths"].max())
+    return d
+
+
+class Workload:
+    def __init__(self, torch, dev, with_adjoint: bool):
+        from paper_2211_00621_gb300 import api
+        self.torch, self.dev, self.api = torch, dev, api
+        c = synth.CFG_SEGREDUCE
+        seqs = synth.ragged_int32(c["seed"], c["S"], c["len_lo"], c["len_hi"], c["val_lo"], c["val_hi"])
+        self.seq_host = seqs
+        self.seq_dev = [torch.from_numpy(s).to(dev) for s in seqs]
+        self.seg_N = int(sum(len(s) for s in seqs))
+        self.seg_S = c["S"]
+        self.table_dev = api.ragged_table(self.seq_dev)
+        self.seq_pinned = [torch.from_numpy(s).pin_memory() for s in seqs]
+        self.table_pinned = api.ragged_table(self.seq_pinned)
+        self.plain = hmm_inputs(synth.CFG_HMM_PLAIN, torch, dev)
+        self.bf16 = hmm_inputs(synth.CFG_HMM_BATCHED, torch, dev)
+        self.adj = hmm_inputs(synth.CFG_HMM_ADJOINT, torch, dev) if with_adjoint else None
+        b = synth.bodies(synth.CFG_ALLPAIRS["seed"], synth.CFG_ALLPAIRS["N"])
+        self.aos_host = b["aos"]
+        self.aos = torch.from_numpy(b["aos"]).to(dev)
+        self.N = synth.CFG_ALLPAIRS["N"]
+        self.eps = synth.CFG_ALLPAIRS["eps"]
+        f32 = torch.float32
+        self.fields = [(0, f32), (4, f32), (8, f32), (12, f32)]
+        self.with_adjoint = with_adjoint
+
+    def state_steps(self):
+        n = self.plain["K"] * self.plain["sumT"] + self.bf16["K"] * self.bf16["sumT"]
+        if self.adj is not None:
+            n += 2 * self.adj["K"] * self.adj["sumT"]
+        return n
+
+    # one step, device-resident inputs; `ev` collects per-row (start, end) events
+    def step(self, ev=None):
+        api, torch = self.api, self.torch
+
+        def mark(name, fn):
+            if ev is None:
+                return fn()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            r = fn()
+            b.record()
+            ev.setdefault(name, []).append((a, b))
+            return r
+
+        def seg():
+            flat, off = api.accel_marshal_ragged_table(self.table_dev)
+            s = api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, flat, off, torch.int64)
+            m = api.accel_reduce(api.RED_MAX, s)
+            twice = torch.empty_like(flat)
+            api.accel_loop(api.LOOP_SCALE, twice, flat, 2.0)
+            return s, m
+
+        out = {}
+        out["seg"] = mark("segreduce", seg)
+        p = self.plain
+        out["plain"] = mark("hmm_plain", lambda: api.hmm_forward(p["log_A"], p["log_B"], p["log_pi"], p["obs"],
+                                                                 p["offsets"], api.HMM_FP32_LOG))
+        q = self.bf16
+        out["bf16"] = mark("hmm_bf16", lambda: api.hmm_forward(q["log_A"], q["log_B"], q["log_pi"], q["obs"],
+                                                               q["offsets"], api.HMM_BF16_SCALED))
+        if self.adj is not None:
+            a = self.adj
+
+            def adjoint():
+                ll = api.hmm_forward(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"],
+                                     api.HMM_FP32_LOG)
+                g = api.hmm_adjoint(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"],
+                                    max_T=a["maxT"], want_loglik=False)
+                return ll, g
+            out["adj"] = mark("hmm_adjoint", adjoint)
+
+        def allpairs():
+            x, y, z, m = api.accel_marshal_records(self.aos, self.fields)
+            return api.pairwise_mapreduce(x, y, z, m, self.eps)
+        out["allpairs"] = mark("allpairs", allpairs)
+        return out
+
+    # end-to-end step: inputs copied from pinned host memory, results read back
+    def e2e_step(self, host):
+        api, torch, dev = self.api, self.torch, self.dev
+        st = torch.cuda.current_stream()
+        res = []
+        # ragged pieces are read by the marshal kernel straight from pinned host memory
+        flat, off = api.accel_marshal_ragged_table(self.table_pinned)
+        s = api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, flat, off, torch.int64)
+        m = api.accel_reduce(api.RED_MAX, s)
+        res += [s, m]
+        for name, prec in (("plain", api.HMM_FP32_LOG), ("bf16", api.HMM_BF16_SCALED)):
+            h = host[name]
+            d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
+            res.append(api.hmm_forward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"], prec))
+        if self.adj is not None:
+            h = host["adj"]
+            d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
+            res.append(api.hmm_forward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"],
+                                       api.HMM_FP32_LOG))
+            gA, gB, gpi, _ = api.hmm_adjoint(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"],
+                                             max_T=self.adj["maxT"], want_loglik=False)
+            res += [gA, gB, gpi]
+        aos = host["aos"].to(dev, non_blocking=True)
+        x, y, z, mm = api.accel_marshal_records(aos, self.fields)
+        res += list(api.pairwise_mapreduce(x, y, z, mm, self.eps))
+        outs = [torch.empty(r.shape, dtype=r.dtype, pin_memory=True) for r in res]
+        for o, r in zip(outs, res):
+            o.copy_(r, non_blocking=True)
+        st.synchronize()
+        return sum(o.numel() * o.element_size() for o in outs)
+
+    def host_inputs(self):
+        torch = self.torch
+        h = {}
+        for name, d in (("plain", self.plain), ("bf16", self.bf16), ("adj", self.adj)):
+            if d is None:
+                continue
+            h[name] = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in d["host"].items()}
+        h["aos"] = torch.from_numpy(self.aos_host).pin_memory()
+        nb = sum(t.numel() * t.element_size() for name in h if name != "aos" for t in h[name].values())
+        nb += h["aos"].numel() * 4
+        nb += 4 * self.seg_N + 16 * self.seg_S          # ragged pieces + pointer/length tables
+        return h, nb
+
+
+# ------------------------------------------------------------------------ rooflines
+def source_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def traffic_for(kernel_src: str):
+    """dram bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_src)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2211_00621_gb300", "csrc", kernel_src)
+    if not os.path.exists(src) or source_hash(src) != e.get("source_sha1"):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def rooflines(W, row_ms, peaks, sm_mhz_max):
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
+    r = {}
+    seg_bytes = 4 * W.seg_N * 3 + 8 * (W.seg_S + 1) * 3 + 8 * W.seg_S * 2 + 16 * W.seg_S
+    r["segreduce"] = {"bound": "hbm", "achieved": seg_bytes / (row_ms["segreduce"] * 1e-3) / 1e9,
+                      "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    p = W.plain
+    r["hmm_plain"] = {"bound": "alu", "achieved": 2 * p["K"] ** 2 * p["sumT"] / (row_ms["hmm_plain"] * 1e-3) / 1e12,
+                      "peak": fp32_peak, "unit": "TFLOP/s"}
+    q = W.bf16
+    r["hmm_bf16"] = {"bound": "tensor", "achieved": 2 * q["K"] ** 2 * q["sumT"] / (row_ms["hmm_bf16"] * 1e-3) / 1e12,
+                     "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+    if W.adj is not None and "hmm_adjoint" in row_ms:
+        a = W.adj
+        r["hmm_adjoint"] = {"bound": "alu", "achieved": 6 * a["K"] ** 2 * a["sumT"] / (row_ms["hmm_adjoint"] * 1e-3)
+                            / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
+    r["allpairs"] = {"bound": "alu", "achieved": 20.0 * W.N * W.N / (row_ms["allpairs"] * 1e-3) / 1e12,
+                     "peak": fp32_peak, "unit": "TFLOP/s"}
+    for v in r.values():
+        v["frac"] = v["achieved"] / v["peak"]
+    return r
+
+
+# ---------------------------------------------------------------------- CPU oracle
+def oracle_sample(seconds: float, seed: int = 0):
+    """Times the oracle (as it stands) on a bounded sample of the HMM rows; returns
+    (state-steps, seconds, description)."""
+    from oracle import hmm as ohmm
+    g = synth.rng(seed)
+    work, t_total, n_fwd, n_fb = 0, 0.0, 0, 0
+    pl = synth.hmm_workload(**{k: v for k, v in synth.CFG_HMM_PLAIN.items()})
+    bf = synth.hmm_workload(**{k: v for k, v in synth.CFG_HMM_BATCHED.items()})
+    ad = synth.hmm_workload(**{k: v for k, v in synth.CFG_HMM_ADJOINT.items()})
+    pl_par = ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(pl))
+    bf_par = ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(bf))
+    ad_par = ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(ad))
+    t_end = time.perf_counter() + seconds
+    while time.perf_counter() < t_end:
+        for p, par, fb in ((pl, pl_par, False), (bf, bf_par, False), (ad, ad_par, True)):
+            s = int(g.integers(0, p["S"]))
+            t0 = time.perf_counter()
+            if fb:
+                ohmm.gradients_batch(p, seqs=[s], params=par)
+                work += 2 * p["K"] * int(p["lengths"][s])
+                n_fb += 1
+            else:
+                ohmm.loglik_batch(p, seqs=[s], params=par)
+                work += p["K"] * int(p["lengths"][s])
+                n_fwd += 1
+            t_total += time.perf_counter() - t0
+    desc = (f"float64 numpy oracle: {n_fwd} forward passes (random sequences of the K=64 and K=256 configs) and "
+            f"{n_fb} forward-backward passes (K=256 adjoint config), {t_total:.1f} s")
+    return work, t_total, desc
+
+
+def oracle_threads():
+    # numpy matrix-vector products at K <= 256 run on one thread in the BLAS builds used here;
+    # report the process's allowed cores as the upper bound only if BLAS threading is on.
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return 1
+
+
+# ---------------------------------------------------------------------------- main
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    # the reference arm is the oracle, timed as it stands on the host cores
+    for _ in range(args.warmup):
+        oracle_sample(args.ref_step_seconds, seed=1000)
+    work, secs = 0, 0.0
+    desc = ""
+    for k in range(args.steps):
+        w, s, desc = oracle_sample(args.ref_step_seconds, seed=k)
+        work += w
+        secs += s
+    value = work / secs
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "HMM rows of the hot path (K=64 plain, K=256 batched, K=256 adjoint), "
+                                   "bounded random sample of sequences per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                             "sample": desc + f" per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--no-adjoint", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2211_00621_gb300 import _lib, api
+    from paper_2211_00621_gb300 import build as _build
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if not _build.up_to_date():
+        if rank == 0:
+            _build.build()
+        if world > 1:
+            dist.barrier()
+    lib = _lib.load()
+
+    with_adj = not args.no_adjoint
+    if with_adj:
+        try:
+            W0 = hmm_inputs(dict(seed=0, K=8, M=4, S=2, kind="fixed", lo=3, hi=3), torch, dev)
+            api.hmm_adjoint(W0["log_A"], W0["log_B"], W0["log_pi"], W0["obs"], W0["offsets"])
+        except _lib.AccelError:
+            with_adj = False
+    W = Workload(torch, dev, with_adj)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        W.step()
+    barrier()
+
+    # ---------------- timed region: K steps, L2 flushed (untimed) before each
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = {}
+    step_ms = []
+    launches0 = lib.accel_launch_count()
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        W.step(ev)
+        e.record()
+        e.synchronize()
+        step_ms.append(s.elapsed_time(e))
+    barrier()
+    launches = lib.accel_launch_count() - launches0
+    clk = clocks.stop()
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    row_ms = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+    work = W.state_steps()
+    value = work * world / (ms * 1e-3)
+
+    # ---------------- end to end through the public API with host buffers
+    host, h2d = W.host_inputs()
+    for _ in range(2):
+        W.e2e_step(host)
+    barrier()
+    e2e_ms = []
+    d2h = 0
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = W.e2e_step(host)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = statistics.median(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    # ---------------- rooflines
+    peaks, peak_src = load_peaks()
+    rl = rooflines(W, row_ms, peaks, float(peaks.get("sm_max_mhz", 2070.0)))
+    dom = max((k for k in rl), key=lambda k: row_ms.get(k, 0.0))
+    dom_src = {"segreduce": "k_segreduce.cu", "hmm_plain": "k_hmm_plain.cu", "hmm_bf16": "k_hmm_tc.cu",
+               "hmm_adjoint": "hmm_adjoint.cu", "allpairs": "k_pairwise.cu"}[dom]
+    roof = dict(rl[dom])
+    roof["kernel"] = dom
+    roof["traffic"] = traffic_for(dom_src)
+    roof["peak_source"] = f"{peak_src} ({'sustained bf16' if roof['bound'] == 'tensor' else roof['bound']})"
+
+    rows = {k: {"ms": row_ms[k], "frac": rl[k]["frac"], "achieved": rl[k]["achieved"], "unit": rl[k]["unit"],
+                "bound": rl[k]["bound"]} for k in rl}
+    seg_gbs = rl["segreduce"]["achieved"]
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+fp32 (HMM), int64 (seg-reduce), fp32 (all-pairs)",
+            "data": "synthetic",
+            "config": {"workload": "all hot-path rows once per step: seg-reduce 4096 seqs; HMM plain K=64 S=512 T=1000;"
+                                   " HMM batched BF16 K=256 S=4096 T log-U[50,5000]; HMM adjoint K=256 S=1024 "
+                                   "T U[200,2000]" + ("" if with_adj else " (adjoint not built: skipped)") +
+                                   "; all-pairs N=65536",
+                       "l2": "flushed before every timed step (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
+            "seg_reduce_gbs": seg_gbs, "rows": rows, "roofline": roof,
+            "e2e": {"value": work * world / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+            "gpu_launches": int(launches), "clocks": clk}
+
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        w, s, desc = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": w / s, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -101,6 +101,9 @@ const char* accel_last_error(void);
 /* Debug mode on (1) / off (0); process-wide, default off. */
 void accel_set_debug(int32_t on);
 int32_t accel_get_debug(void);
+/* Number of CUDA kernels this library has launched in the process so far (diagnostic;
+ * used to count the launches inside a timed region). */
+uint64_t accel_launch_count(void);
 
 /* =========================================================== marshaling (Sec. 3.3) */
 /*

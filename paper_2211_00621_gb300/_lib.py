@@ -49,6 +49,7 @@ SIGNATURES = {
     "accel_last_error": (C.c_char_p, []),
     "accel_set_debug": (None, [i32]),
     "accel_get_debug": (i32, []),
+    "accel_launch_count": (C.c_uint64, []),
     "accel_marshal_ragged_workspace_size": (sz, [i64]),
     "accel_marshal_ragged": (i32, [vp, vp, i64, i32, vp, vp, vp, sz, vp]),
     "accel_marshal_records": (i32, [vp, i64, i32, i32, vp, vp, vp, i32, vp]),

@@ -12,6 +12,10 @@ import ctypes as C
 import torch
 
 from . import _lib as L
+from ._lib import (  # noqa: F401  (operator ids, re-exported for callers of this module)
+    HMM_BF16_SCALED, HMM_FP32_LOG, LOOP_AXPY, LOOP_SCALE, MAP_ABS, MAP_ADD2, MAP_IDENTITY, MAP_MUL2, MAP_NEG,
+    MAP_SCALE, MAP_SQ_PLUS_ONE, PAIR_GRAVITY_SOFTENED, RED_ADD, RED_MAX, RED_MIN, RED_MUL,
+)
 
 _DT = {torch.int32: L.I32, torch.int64: L.I64, torch.float32: L.F32, torch.float64: L.F64}
 _TORCH = {v: k for k, v in _DT.items()}
@@ -52,25 +56,50 @@ def version() -> str:
 
 
 # ------------------------------------------------------------------------ marshaling
+class RaggedTable:
+    """Host-side description of a list of sequences: pinned tables of element pointers and
+    lengths (what accel_marshal_ragged reads), built once per list."""
+
+    def __init__(self, seqs, dtype):
+        self.seqs = list(seqs)          # keeps the pieces alive
+        self.dtype = dtype
+        self.S = len(self.seqs)
+        for s in self.seqs:
+            if s.dtype != dtype:
+                raise TypeError("all sequences must have the same dtype")
+            if not s.is_cuda and s.numel() and not s.is_pinned():
+                raise ValueError("host sequences must be in pinned memory")
+        self.ptrs = torch.tensor([s.data_ptr() if s.numel() else 0 for s in self.seqs] or [0],
+                                 dtype=torch.int64).pin_memory()
+        self.lengths = torch.tensor([int(s.numel()) for s in self.seqs] or [0], dtype=torch.int64).pin_memory()
+        self.total = int(self.lengths[:self.S].sum().item()) if self.S else 0
+
+
+def ragged_table(seqs, dtype=None):
+    dtype = dtype or (seqs[0].dtype if len(seqs) else torch.int32)
+    return RaggedTable(seqs, dtype)
+
+
+def accel_marshal_ragged_table(table: RaggedTable, device="cuda", out=None):
+    """Flatten the sequences of a RaggedTable into (flat data, int64 offsets) on device."""
+    lib = L.load()
+    if out is None:
+        flat = torch.empty(table.total, dtype=table.dtype, device=device)
+        offsets = torch.empty(table.S + 1, dtype=torch.int64, device=device)
+    else:
+        flat, offsets = out
+    ws = _ws(lib.accel_marshal_ragged_workspace_size(table.S), flat.device if table.total else offsets.device)
+    L.check("accel_marshal_ragged", lib.accel_marshal_ragged(C.c_void_p(table.ptrs.data_ptr()),
+                                                             C.c_void_p(table.lengths.data_ptr()), table.S,
+                                                             _dt(table.dtype), _ptr(flat), _ptr(offsets), _ptr(ws),
+                                                             ws.numel(), _stream()))
+    return flat, offsets
+
+
 def accel_marshal_ragged(seqs, dtype=torch.int32, device="cuda"):
     """Flatten a list of 1-D tensors (CUDA, or pinned CPU readable by the device) into
     (flat data, int64 offsets) on ``device``."""
-    lib = L.load()
-    S = len(seqs)
-    lengths = (C.c_int64 * max(S, 1))(*[int(s.numel()) for s in seqs])
-    ptrs = (C.c_void_p * max(S, 1))(*[s.data_ptr() if s.numel() else 0 for s in seqs])
-    for s in seqs:
-        if s.dtype != dtype:
-            raise TypeError("all sequences must have the given dtype")
-        if not s.is_cuda and s.numel() and not s.is_pinned():
-            raise ValueError("host sequences must be in pinned memory")
-    total = sum(int(s.numel()) for s in seqs)
-    flat = torch.empty(total, dtype=dtype, device=device)
-    offsets = torch.empty(S + 1, dtype=torch.int64, device=device)
-    ws = _ws(lib.accel_marshal_ragged_workspace_size(S), device)
-    L.check("accel_marshal_ragged", lib.accel_marshal_ragged(ptrs, lengths, S, _dt(dtype), _ptr(flat),
-                                                             _ptr(offsets), _ptr(ws), ws.numel(), _stream()))
-    return flat, offsets
+    return accel_marshal_ragged_table(RaggedTable(seqs, dtype), device)
 
 
 def accel_marshal_records(aos: torch.Tensor, fields, inverse_from=None):

@@ -10,6 +10,9 @@ namespace accel {
 
 static thread_local char g_last_error[512] = {0};
 static std::atomic<int> g_debug{0};
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 accel_status set_error(accel_status st, const char* fmt, ...) {
     va_list ap;
@@ -26,7 +29,8 @@ accel_status ok() {
 
 bool debug_mode() { return g_debug.load(std::memory_order_relaxed) != 0; }
 
-accel_status after_launch(cudaStream_t stream, const char* what) {
+accel_status after_launch(cudaStream_t stream, const char* what, int nkernels) {
+    count_launches(nkernels);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(ACCEL_ERR_CUDA, "%s: launch failed: %s", what, cudaGetErrorString(e));
     if (debug_mode()) {
@@ -85,6 +89,7 @@ accel_status debug_check_offsets(const int64_t* d_offsets, int64_t S, int64_t N,
     int blocks = (int)((S + 1 + 255) / 256);
     if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
     k_check_offsets<<<blocks, 256, 0, stream>>>(d_offsets, S, N, min_len, (unsigned long long*)d_scratch);
+    count_launches(1);
     ACCEL_CUDA_TRY(cudaGetLastError());
     unsigned long long bad = 0;
     accel_status st = read_bad(d_scratch, stream, &bad);
@@ -103,6 +108,7 @@ accel_status debug_check_symbols(const int32_t* d_obs, int64_t n, int32_t M, voi
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
     k_check_symbols<<<blocks, 256, 0, stream>>>(d_obs, n, M, (unsigned long long*)d_scratch);
+    count_launches(1);
     ACCEL_CUDA_TRY(cudaGetLastError());
     unsigned long long bad = 0;
     accel_status st = read_bad(d_scratch, stream, &bad);
@@ -119,5 +125,6 @@ const char* accel_version(void) { return "libaccel 0.1 (sm_103a)"; }
 const char* accel_last_error(void) { return accel::g_last_error; }
 void accel_set_debug(int32_t on) { accel::g_debug.store(on ? 1 : 0); }
 int32_t accel_get_debug(void) { return accel::g_debug.load(); }
+uint64_t accel_launch_count(void) { return accel::g_launches.load(); }
 
 }  // extern "C"

@@ -31,9 +31,11 @@ bool debug_mode();
         if (!(cond)) return ::accel::set_error((st), __VA_ARGS__);                   \
     } while (0)
 
-// After a launch: report launch errors; in debug mode also synchronize the stream so
-// asynchronous faults surface as ACCEL_ERR_CUDA from the call that caused them.
-accel_status after_launch(cudaStream_t stream, const char* what);
+// After the launches of one call: count them (accel_launch_count), report launch errors,
+// and in debug mode synchronize the stream so asynchronous faults surface as
+// ACCEL_ERR_CUDA from the call that caused them.
+accel_status after_launch(cudaStream_t stream, const char* what, int nkernels);
+void count_launches(int n);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

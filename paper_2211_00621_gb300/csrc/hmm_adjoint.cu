@@ -1,22 +1,583 @@
-// hmm_adjoint entry point (K9).
+// Hand-written adjoint of the scaled HMM forward recursion (K9), with sqrt(T)
+// checkpointing.
+//
+// Gradients of L = sum_s w_s logL_s with respect to log A, log B, log pi taken as free
+// parameters are the (weighted) forward-backward expected counts.  The HMM is not in the
+// paper; the recursion is its pattern vocabulary (a map of a reduce inside a sequential
+// loop, Appendix A) and the adjoint is the textbook backward recursion, arranged so that
+// the power-of-two scaling of the forward pass carries over without logarithms:
+//
+//   forward (0-based t):  S_t = alpha~_t 2^-e_t, alpha~_0 = pi o b(o_0),
+//                         alpha~_t = (S_{t-1} A) o b(o_t),  c'_t = sum_j alpha~_t(j) = f 2^e_t
+//   logL = ln2 sum_{t<T-1} e_t + ln c'_{T-1}
+//   backward:             R_{T-1} = 1 / c'_{T-1}
+//                         R_t     = 2^-e_t  A (b(o_{t+1}) o R_{t+1})
+//   expected counts:      xi(i,j)  = A_ij sum_t S_t(i) b_j(o_{t+1}) R_{t+1}(j)
+//                         gamma_t  = S_t o R_t 2^e_t,   counts(j,k) = sum_t gamma_t(j)[o_t = k]
+// (R_t equals beta_t 2^{E_{t-1}} / P(o) with E the running exponent sum, so every product
+// above equals the textbook alpha, beta, P(o) expression.)
+//
+// Memory: the forward keeps S_t only every C_s = ceil(sqrt(T_s)) steps (plus e_t).  The
+// backward runs in rounds r = 0, 1, ...: round r takes segment n_s - 1 - r of every
+// sequence (n_s = ceil(T_s / C_s)), recomputes its S_t from the checkpoint into a row
+// buffer P, runs the backward recursion across it writing the matching rows
+// Q = w_s b(o_{t+1}) o R_{t+1}, and a split-K GEMM accumulates U += P^T Q, so that
+// xi = A o U at the end.  Storage is O(S sqrt(T_max) K) instead of O(sum_s T_s K).
+//
+// All kernels are FP32 SIMT; the groups of 8 sequences per CTA are taken in order of
+// decreasing length.  Every accumulation has a fixed order, so results are deterministic.
 #include "hmm_internal.cuh"
 
+#include <math.h>
+
+namespace accel {
+namespace hmm {
+namespace adj {
+
+constexpr int kT = 256;     // threads per CTA; thread j <-> state j
+constexpr int kG = 8;       // sequences per CTA
+constexpr int kTile = 64;   // GEMM tile of U
+constexpr int kSplit = 16;  // GEMM split over rows
+
+struct Prm {
+    int K, M, Cmax;
+    int64_t S;
+    const float* A;     // exp(log A) [K][K]
+    const float* At;    // its transpose
+    const float* BT;    // exp(log B)^T [M][K]
+    const float* pi;    // exp(log pi) [K]
+    const int32_t* obs;
+    const int64_t* off;
+    const int32_t* order;
+    const double* w;    // weights or null
+    float* cp;          // checkpoints [S][Cmax][K]
+    int32_t* cp_e;      // their exponents [S][Cmax]
+    float* clast;       // c'_{T-1} [S]
+    double* loglik;     // [S] or null
+    float* P;           // rows [S][Cmax][K]
+    float* Q;           // rows [S][Cmax][K]
+    float* Rc;          // carried R [S][K]
+    float* cnt;         // per group [ngroups][K][M]
+    float* pig;         // per group [ngroups][K]
+    int32_t* status;    // device status word (ACCEL_ERR_SHAPE if a length exceeds max_T)
+    int Kp;             // padded row stride of the shared-memory vectors (multiple of 4)
+};
+
+__host__ __device__ __forceinline__ int seg_len(int64_t T) {
+    int c = (int)ceil(sqrt((double)T));
+    while ((int64_t)c * c < T) ++c;
+    while (c > 1 && (int64_t)(c - 1) * (c - 1) >= T) --c;
+    return c < 1 ? 1 : c;
+}
+
+struct GroupInfo {
+    int64_t seq[kG], T[kG], o0[kG];
+    int C[kG];
+};
+
+__device__ void load_group(const Prm& p, GroupInfo& gi) {
+    for (int g = 0; g < kG; ++g) {
+        int64_t q = blockIdx.x * (int64_t)kG + g;
+        int64_t s = q < p.S ? p.order[q] : -1;
+        gi.seq[g] = s;
+        gi.T[g] = s >= 0 ? p.off[s + 1] - p.off[s] : 0;
+        gi.o0[g] = s >= 0 ? p.off[s] : 0;
+        gi.C[g] = s >= 0 ? seg_len(gi.T[g]) : 1;
+        if (s >= 0 && gi.C[g] > p.Cmax) {   // longer than max_T: skip, report
+            if (threadIdx.x == 0) atomicExch(p.status, ACCEL_ERR_SHAPE);
+            gi.seq[g] = -1;
+            gi.T[g] = 0;
+            gi.C[g] = 1;
+        }
+    }
+}
+
+// Block-wide sums of kG per-thread values (deterministic order); result in all threads.
+__device__ __forceinline__ void block_sum_g(float (&v)[kG], float (*s_red)[kT / 32]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        float x = v[g];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+        if (lane == 0) s_red[g][w] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        float x = 0.f;
+#pragma unroll
+        for (int q = 0; q < kT / 32; ++q) x += s_red[g][q];
+        v[g] = x;
+    }
+    __syncthreads();
+}
+
+// acc_g(j) = sum_i X[g][i] Mat[i][j] for the active g (Mat row-major K x K, read by columns)
+__device__ __forceinline__ void matvec_g(const float* __restrict__ Mat, const float* __restrict__ X, int K, int ld,
+                                         const bool (&act)[kG], float (&acc)[kG]) {
+    const int j = threadIdx.x;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) acc[g] = 0.f;
+    if (j >= K) return;
+    const float* col = Mat + j;
+    int i = 0;
+    for (; i + 4 <= K; i += 4) {
+        float a0 = __ldg(col + (int64_t)(i + 0) * K), a1 = __ldg(col + (int64_t)(i + 1) * K);
+        float a2 = __ldg(col + (int64_t)(i + 2) * K), a3 = __ldg(col + (int64_t)(i + 3) * K);
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (!act[g]) continue;
+            float4 x = *reinterpret_cast<const float4*>(X + g * ld + i);
+            acc[g] = fmaf(x.x, a0, acc[g]);
+            acc[g] = fmaf(x.y, a1, acc[g]);
+            acc[g] = fmaf(x.z, a2, acc[g]);
+            acc[g] = fmaf(x.w, a3, acc[g]);
+        }
+    }
+    for (; i < K; ++i) {
+        float a0 = __ldg(col + (int64_t)i * K);
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+            if (act[g]) acc[g] = fmaf(X[g * ld + i], a0, acc[g]);
+    }
+}
+
+// One forward step for the active sequences: sS holds S_{t-1} on entry and S_t on exit;
+// returns e_t and c'_t per sequence.  obs_t[g] is o_t of sequence g.
+__device__ __forceinline__ void fwd_step(const Prm& p, float* sS, const float* sBT, float (*s_red)[kT / 32],
+                                         const bool (&act)[kG], const int (&obs_t)[kG], int (&e)[kG],
+                                         float (&c)[kG]) {
+    const int j = threadIdx.x, K = p.K, Kp = p.Kp;
+    float acc[kG];
+    matvec_g(p.A, sS, K, Kp, act, acc);
+    float v[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        acc[g] = (act[g] && j < K) ? acc[g] * sBT[obs_t[g] * K + j] : 0.f;
+        v[g] = acc[g];
+    }
+    block_sum_g(v, s_red);   // includes a barrier after all reads of sS
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        c[g] = v[g];
+        int ex = 0;
+        frexpf(v[g], &ex);
+        e[g] = ex;
+        if (act[g] && j < K) sS[g * Kp + j] = acc[g] * ldexpf(1.0f, -ex);
+    }
+    __syncthreads();
+}
+
+__global__ void k_prep(const float* __restrict__ logA, const float* __restrict__ logB, const float* __restrict__ logpi,
+                       int K, int M, float* __restrict__ A, float* __restrict__ At, float* __restrict__ BT,
+                       float* __restrict__ pi) {
+    int64_t nA = (int64_t)K * K, nB = (int64_t)K * M;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * nA + nB + K;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        if (idx < nA) {
+            A[idx] = __expf(logA[idx]);
+        } else if (idx < 2 * nA) {
+            int64_t q = idx - nA;
+            int i = (int)(q / K), j = (int)(q % K);
+            At[(int64_t)j * K + i] = __expf(logA[q]);
+        } else if (idx < 2 * nA + nB) {
+            int64_t q = idx - 2 * nA;
+            int j = (int)(q / M), k = (int)(q % M);
+            BT[(int64_t)k * K + j] = __expf(logB[q]);
+        } else {
+            int j = (int)(idx - 2 * nA - nB);
+            pi[j] = __expf(logpi[j]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- forward + checkpoints
+__global__ void __launch_bounds__(kT) k_forward_cp(Prm p) {
+    extern __shared__ float smem[];
+    const int K = p.K, M = p.M, Kp = p.Kp, j = threadIdx.x;
+    float* sBT = smem;                                       // [M][K]
+    float* sS = smem + (((size_t)M * K + 3) & ~(size_t)3);   // [kG][K]
+    __shared__ float s_red[kG][kT / 32];
+    for (int idx = j; idx < M * K; idx += kT) sBT[idx] = p.BT[idx];
+    GroupInfo gi;
+    load_group(p, gi);
+    int64_t Tmax = 0;
+    for (int g = 0; g < kG; ++g) Tmax = gi.T[g] > Tmax ? gi.T[g] : Tmax;
+    __syncthreads();
+    // t = 0: alpha~_0 = pi o b(o_0)
+    bool act[kG];
+    int ob[kG], e[kG];
+    float c[kG], v[kG], a0[kG];
+    int64_t E[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        act[g] = gi.T[g] > 0;
+        ob[g] = act[g] ? p.obs[gi.o0[g]] : 0;
+        a0[g] = (act[g] && j < K) ? p.pi[j] * sBT[ob[g] * K + j] : 0.f;
+        v[g] = a0[g];
+        E[g] = 0;
+    }
+    block_sum_g(v, s_red);
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        int ex = 0;
+        frexpf(v[g], &ex);
+        e[g] = ex;
+        c[g] = v[g];
+        if (act[g] && j < K) {
+            float sv = a0[g] * ldexpf(1.0f, -ex);
+            sS[g * Kp + j] = sv;
+            p.cp[((int64_t)gi.seq[g] * p.Cmax) * K + j] = sv;
+        }
+        if (act[g] && j == 0) p.cp_e[(int64_t)gi.seq[g] * p.Cmax] = ex;
+        if (act[g] && gi.T[g] == 1 && j == 0) {
+            p.clast[gi.seq[g]] = c[g];
+            if (p.loglik) p.loglik[gi.seq[g]] = log((double)c[g]);
+        }
+        E[g] = ex;
+    }
+    __syncthreads();
+    for (int64_t t = 1; t < Tmax; ++t) {
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            act[g] = t < gi.T[g];
+            ob[g] = act[g] ? p.obs[gi.o0[g] + t] : 0;
+        }
+        fwd_step(p, sS, sBT, s_red, act, ob, e, c);
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (!act[g]) continue;
+            if (t == gi.T[g] - 1 && j == 0) {
+                p.clast[gi.seq[g]] = c[g];
+                if (p.loglik) p.loglik[gi.seq[g]] = 0.6931471805599453 * (double)E[g] + log((double)c[g]);
+            }
+            E[g] += e[g];
+            if (t % gi.C[g] == 0) {
+                int64_t k = t / gi.C[g];
+                if (j < K) p.cp[((int64_t)gi.seq[g] * p.Cmax + k) * K + j] = sS[g * Kp + j];
+                if (j == 0) p.cp_e[(int64_t)gi.seq[g] * p.Cmax + k] = e[g];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- one backward round
+__global__ void __launch_bounds__(kT) k_backward_round(Prm p, int r) {
+    extern __shared__ float smem[];
+    const int K = p.K, M = p.M, Kp = p.Kp, j = threadIdx.x;
+    float* sBT = smem;                                             // [M][K]
+    float* sS = smem + (((size_t)M * K + 3) & ~(size_t)3);         // [kG][Kp] recompute state / v
+    float* sR = sS + (size_t)kG * Kp;                              // [kG][Kp] R_{t+1}
+    int* sE = reinterpret_cast<int*>(sR + (size_t)kG * Kp);        // [kG][Cmax] exponents of the segment
+    __shared__ float s_red[kG][kT / 32];
+    for (int idx = j; idx < M * K; idx += kT) sBT[idx] = p.BT[idx];
+    GroupInfo gi;
+    load_group(p, gi);
+    int64_t t0[kG], L[kG];
+    int maxL = 0;
+    float wgt[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        t0[g] = 0;
+        L[g] = 0;
+        wgt[g] = 0.f;
+        if (gi.seq[g] < 0) continue;
+        int64_t n = (gi.T[g] + gi.C[g] - 1) / gi.C[g];
+        int64_t k = n - 1 - r;
+        if (k < 0) continue;
+        t0[g] = k * gi.C[g];
+        int64_t t1 = t0[g] + gi.C[g] < gi.T[g] ? t0[g] + gi.C[g] : gi.T[g];
+        L[g] = t1 - t0[g];
+        maxL = L[g] > maxL ? (int)L[g] : maxL;
+        wgt[g] = p.w ? (float)p.w[gi.seq[g]] : 1.0f;
+    }
+    // ---- recompute S_t for t in [t0, t0 + L) into the P rows (and e_t into sE)
+    bool act[kG];
+    int ob[kG], e[kG];
+    float c[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        act[g] = L[g] > 0;
+        if (!act[g]) continue;
+        int64_t base = (int64_t)gi.seq[g] * p.Cmax;
+        int64_t k = t0[g] / gi.C[g];
+        if (j < K) {
+            float sv = p.cp[(base + k) * K + j];
+            sS[g * Kp + j] = sv;
+            p.P[base * K + j] = sv;
+        }
+        if (j == 0) sE[g * p.Cmax] = p.cp_e[base + k];
+    }
+    __syncthreads();
+    for (int tt = 1; tt < maxL; ++tt) {
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            act[g] = tt < L[g];
+            ob[g] = act[g] ? p.obs[gi.o0[g] + t0[g] + tt] : 0;
+        }
+        fwd_step(p, sS, sBT, s_red, act, ob, e, c);
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (!act[g]) continue;
+            int64_t row = (int64_t)gi.seq[g] * p.Cmax + tt;
+            if (j < K) p.P[row * K + j] = sS[g * Kp + j];
+            if (j == 0) sE[g * p.Cmax + tt] = e[g];
+        }
+    }
+    // ---- backward across the segment: R_{t+1} in sR, v = b(o_{t+1}) o R_{t+1} in sS
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        if (L[g] == 0 || j >= K) continue;
+        bool last_seg = t0[g] + L[g] == gi.T[g];
+        sR[g * Kp + j] = last_seg ? 0.f : p.Rc[(int64_t)gi.seq[g] * K + j];
+    }
+    __syncthreads();
+    for (int tt = maxL - 1; tt >= 0; --tt) {
+        bool trans[kG];
+        int ob1[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            act[g] = tt < L[g];
+            int64_t t = t0[g] + tt;
+            trans[g] = act[g] && t < gi.T[g] - 1;          // transition t -> t+1 exists
+            ob1[g] = trans[g] ? p.obs[gi.o0[g] + t + 1] : 0;
+            if (act[g] && j < K) {
+                int64_t row = (int64_t)gi.seq[g] * p.Cmax + tt;
+                float vv = trans[g] ? sBT[ob1[g] * K + j] * sR[g * Kp + j] : 0.f;
+                sS[g * Kp + j] = vv;
+                p.Q[row * K + j] = wgt[g] * vv;
+            }
+        }
+        __syncthreads();
+        float acc[kG];
+        matvec_g(p.At, sS, K, Kp, trans, acc);
+        __syncthreads();
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (!act[g]) continue;
+            int64_t t = t0[g] + tt;
+            const int et = sE[g * p.Cmax + tt];
+            float Rt = trans[g] ? acc[g] * ldexpf(1.0f, -et) : 1.0f / p.clast[gi.seq[g]];
+            if (j < K) {
+                int64_t row = (int64_t)gi.seq[g] * p.Cmax + tt;
+                float St = p.P[row * K + j];
+                float gam = wgt[g] * St * Rt * ldexpf(1.0f, et);
+                int ot = p.obs[gi.o0[g] + t];
+                float* cnt = p.cnt + (int64_t)blockIdx.x * K * M;
+                cnt[(int64_t)j * M + ot] += gam;
+                if (t == 0) p.pig[(int64_t)blockIdx.x * K + j] += gam;
+                sR[g * Kp + j] = Rt;
+            }
+        }
+        __syncthreads();
+    }
+    // carry R_{t0} to the next round; zero the unused rows of Q
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        if (gi.seq[g] < 0) continue;
+        int64_t base = (int64_t)gi.seq[g] * p.Cmax;
+        if (L[g] > 0 && j < K) p.Rc[(int64_t)gi.seq[g] * K + j] = sR[g * Kp + j];
+        for (int64_t tt = L[g]; tt < p.Cmax; ++tt)
+            if (j < K) p.Q[(base + tt) * K + j] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------- U += P^T Q (split-K)
+// CTA (tile i-block, j-block, split): rows [split*rows/kSplit, ...) of P and Q.
+__global__ void __launch_bounds__(256) k_gemm_ptq(const float* __restrict__ P, const float* __restrict__ Q, int64_t rows,
+                                                 int K, float* __restrict__ Upart) {
+    __shared__ float sP[32][kTile + 4];
+    __shared__ float sQ[32][kTile + 4];
+    const int nb = (K + kTile - 1) / kTile;
+    const int bi = blockIdx.x % nb, bj = (blockIdx.x / nb) % nb, sp = blockIdx.x / (nb * nb);
+    const int64_t r0 = rows * sp / kSplit, r1 = rows * (sp + 1) / kSplit;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
+    float acc[4][4] = {};
+    for (int64_t rb = r0; rb < r1; rb += 32) {
+        for (int q = threadIdx.x; q < 32 * kTile; q += 256) {
+            int rr = q / kTile, cc = q % kTile;
+            int64_t row = rb + rr;
+            int ci = bi * kTile + cc, cj = bj * kTile + cc;
+            sP[rr][cc] = (row < r1 && ci < K) ? P[row * K + ci] : 0.f;
+            sQ[rr][cc] = (row < r1 && cj < K) ? Q[row * K + cj] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = sP[rr][ty * 4 + u]; b[u] = sQ[rr][tx * 4 + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+    float* U = Upart + (int64_t)sp * K * K;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int i = bi * kTile + ty * 4 + u, jj = bj * kTile + tx * 4 + v;
+            if (i < K && jj < K) U[(int64_t)i * K + jj] += acc[u][v];
+        }
+}
+
+// grad_log_A = A o sum_split U, grad_log_B = sum_groups counts, grad_log_pi = sum_groups pig
+__global__ void k_finish(const float* __restrict__ A, const float* __restrict__ Upart, const float* __restrict__ cnt,
+                         const float* __restrict__ pig, int K, int M, int64_t ngroups, float* __restrict__ gA,
+                         float* __restrict__ gB, float* __restrict__ gpi) {
+    int64_t nA = (int64_t)K * K, nB = (int64_t)K * M;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nA + nB + K;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        if (idx < nA) {
+            float u = 0.f;
+            for (int s = 0; s < kSplit; ++s) u += Upart[(int64_t)s * nA + idx];
+            gA[idx] = A[idx] * u;
+        } else if (idx < nA + nB) {
+            int64_t q = idx - nA;
+            float x = 0.f;
+            for (int64_t b = 0; b < ngroups; ++b) x += cnt[b * nB + q];
+            gB[q] = x;
+        } else {
+            int64_t q = idx - nA - nB;
+            float x = 0.f;
+            for (int64_t b = 0; b < ngroups; ++b) x += pig[b * K + q];
+            if (gpi) gpi[q] = x;
+        }
+    }
+}
+
+struct Layout {
+    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, order, total;
+    int Cmax;
+    int64_t ngroups;
+};
+
+static Layout layout(int K, int M, int64_t S, int64_t max_T) {
+    Layout L;
+    L.Cmax = seg_len(max_T < 1 ? 1 : max_T);
+    L.ngroups = (S + kG - 1) / kG;
+    size_t o = kStatusBytes;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    L.A = take((size_t)K * K * 4);
+    L.At = take((size_t)K * K * 4);
+    L.BT = take((size_t)M * K * 4);
+    L.pi = take((size_t)K * 4);
+    L.cp = take((size_t)S * L.Cmax * K * 4);
+    L.cp_e = take((size_t)S * L.Cmax * 4);
+    L.clast = take((size_t)S * 4);
+    L.P = take((size_t)S * L.Cmax * K * 4);
+    L.Q = take((size_t)S * L.Cmax * K * 4);
+    L.Rc = take((size_t)S * K * 4);
+    L.cnt = take((size_t)L.ngroups * K * M * 4);
+    L.pig = take((size_t)L.ngroups * K * 4);
+    L.Upart = take((size_t)kSplit * K * K * 4);
+    L.order = o;
+    L.total = o + order_ws_bytes(S);
+    return L;
+}
+
+static int padK(int K) { return (K + 3) & ~3; }
+static size_t smem_fwd(int K, int M) { return ((((size_t)M * K + 3) & ~(size_t)3) + (size_t)kG * padK(K)) * 4; }
+static size_t smem_bwd(int K, int M, int Cmax) {
+    return ((((size_t)M * K + 3) & ~(size_t)3) + 2 * (size_t)kG * padK(K)) * 4 + (size_t)kG * Cmax * 4;
+}
+
+}  // namespace adj
+}  // namespace hmm
+}  // namespace accel
+
 using namespace accel;
+using namespace accel::hmm;
+
+namespace accel {
+namespace hmm {
+accel_status check_model(const accel_hmm_model* m, const char* who);
+}
+}  // namespace accel
 
 extern "C" {
 
 size_t hmm_adjoint_workspace_size(const accel_hmm_model* m, int64_t S, int64_t total_T, int64_t max_T) {
-    (void)m; (void)S; (void)total_T; (void)max_T;
-    return kStatusBytes;
+    (void)total_T;
+    if (!m || S < 0) return 0;
+    return adj::layout(m->K, m->M, S, max_T).total;
 }
 
 accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets, int64_t S,
                          int64_t total_T, int64_t max_T, const double* d_weights, double* d_loglik,
                          float* d_grad_log_A, float* d_grad_log_B, float* d_grad_log_pi, void* d_ws, size_t ws_bytes,
                          void* stream) {
-    (void)m; (void)d_obs; (void)d_offsets; (void)S; (void)total_T; (void)max_T; (void)d_weights; (void)d_loglik;
-    (void)d_grad_log_A; (void)d_grad_log_B; (void)d_grad_log_pi; (void)d_ws; (void)ws_bytes; (void)stream;
-    return set_error(ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: not built yet");
+    accel_status r = check_model(m, "hmm_adjoint");
+    if (r != ACCEL_OK) return r;
+    ACCEL_REQUIRE(S >= 0 && total_T >= 0 && max_T >= 0, ACCEL_ERR_INVALID_ARG, "hmm_adjoint: negative size");
+    ACCEL_REQUIRE(d_offsets && d_ws && d_grad_log_A && d_grad_log_B && (total_T == 0 || d_obs), ACCEL_ERR_INVALID_ARG,
+                  "hmm_adjoint: null pointer");
+    ACCEL_REQUIRE(((uintptr_t)d_ws % 256) == 0, ACCEL_ERR_INVALID_ARG, "hmm_adjoint: d_ws must be 256-byte aligned");
+    const int K = m->K, M = m->M;
+    adj::Layout L = adj::layout(K, M, S, max_T);
+    ACCEL_REQUIRE(ws_bytes >= L.total, ACCEL_ERR_WORKSPACE, "hmm_adjoint: workspace %zu < %zu bytes", ws_bytes, L.total);
+    size_t sm_b = adj::smem_bwd(K, M, L.Cmax);
+    ACCEL_REQUIRE(sm_b <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED,
+                  "hmm_adjoint: emission table too large for shared memory (K=%d, M=%d)", K, M);
+    cudaStream_t st = as_stream(stream);
+    char* ws = (char*)d_ws;
+    if (debug_mode() && S > 0) {
+        r = debug_check_offsets(d_offsets, S, total_T, 1, ws + kDebugScratchOff, st);
+        if (r != ACCEL_OK) return r;
+        r = debug_check_symbols(d_obs, total_T, M, ws + kDebugScratchOff, st);
+        if (r != ACCEL_OK) return r;
+    }
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + kStatusOff, 0, 4, st));
+    adj::Prm p;
+    p.K = K; p.M = M; p.Cmax = L.Cmax; p.S = S; p.Kp = adj::padK(K);
+    p.status = (int32_t*)(ws + kStatusOff);
+    p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
+    p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = d_weights;
+    p.cp = (float*)(ws + L.cp); p.cp_e = (int32_t*)(ws + L.cp_e); p.clast = (float*)(ws + L.clast);
+    p.loglik = d_loglik; p.P = (float*)(ws + L.P); p.Q = (float*)(ws + L.Q); p.Rc = (float*)(ws + L.Rc);
+    p.cnt = (float*)(ws + L.cnt); p.pig = (float*)(ws + L.pig);
+    float* Upart = (float*)(ws + L.Upart);
+    int nlaunch = 0;
+    int pg = num_sms() * 4;
+    adj::k_prep<<<pg, 256, 0, st>>>(m->log_A, m->log_B, m->log_pi, K, M, (float*)p.A, (float*)p.At, (float*)p.BT,
+                                    (float*)p.pi);
+    ++nlaunch;
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cnt, 0, (size_t)L.ngroups * K * M * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.pig, 0, (size_t)L.ngroups * K * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)adj::kSplit * K * K * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
+    if (S > 0) {
+        r = order_by_length(d_offsets, S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)S * 4, 256), st);
+        if (r != ACCEL_OK) return r;
+        nlaunch += 3;
+        size_t sm_f = adj::smem_fwd(K, M);
+        ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_forward_cp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f));
+        ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
+        adj::k_forward_cp<<<(unsigned)L.ngroups, adj::kT, sm_f, st>>>(p);
+        ++nlaunch;
+        const int nb = (K + adj::kTile - 1) / adj::kTile;
+        for (int round = 0; round < L.Cmax; ++round) {
+            adj::k_backward_round<<<(unsigned)L.ngroups, adj::kT, sm_b, st>>>(p, round);
+            adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, S * (int64_t)L.Cmax, K, Upart);
+            nlaunch += 2;
+        }
+    }
+    adj::k_finish<<<pg, 256, 0, st>>>(p.A, Upart, p.cnt, p.pig, K, M, L.ngroups, d_grad_log_A, d_grad_log_B,
+                                      d_grad_log_pi);
+    ++nlaunch;
+    r = after_launch(st, "hmm_adjoint", nlaunch);
+    if (r != ACCEL_OK) return r;
+    if (debug_mode()) {
+        int32_t h = 0;
+        ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, ws + kStatusOff, 4, cudaMemcpyDeviceToHost, st));
+        ACCEL_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h != ACCEL_OK) return set_error(h, "hmm_adjoint: a sequence is longer than max_T=%lld", (long long)max_T);
+    }
+    return ok();
 }
 
 }  // extern "C"

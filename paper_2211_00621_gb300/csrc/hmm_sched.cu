@@ -60,6 +60,7 @@ accel_status order_by_length(const int64_t* d_off, int64_t S, int32_t* d_order, 
     k_len_hist<<<g, 256, 0, st>>>(d_off, S, count);
     k_len_scan<<<1, kBuckets, 0, st>>>(count, cursor);
     k_len_scatter<<<g, 256, 0, st>>>(d_off, S, cursor, d_order);
+    // these three are counted by the calling entry point
     ACCEL_CUDA_TRY(cudaGetLastError());
     return ACCEL_OK;
 }

@@ -265,7 +265,7 @@ accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const i
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_plain_warp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_plain_warp<2><<<grid, 128, smem, st>>>(m->log_A, m->log_B, m->log_pi, K, M, obs, off, S, loglik);
         }
-        return after_launch(st, "hmm_forward(fp32 warp)");
+        return after_launch(st, "hmm_forward(fp32 warp)", 1);
     }
     size_t smem = ((((size_t)M * K + 3) & ~(size_t)3) + (size_t)kG * ((K + 3) & ~3)) * sizeof(float);
     ACCEL_REQUIRE(smem <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_forward: M*K too large for the FP32 kernel");
@@ -278,7 +278,7 @@ accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const i
     ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_plain_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = (unsigned)((S + kG - 1) / kG);
     k_plain_cta<<<grid, kCtaThreads, smem, st>>>(Aexp, m->log_B, m->log_pi, K, M, obs, off, S, order, loglik);
-    return after_launch(st, "hmm_forward(fp32 cta)");
+    return after_launch(st, "hmm_forward(fp32 cta)", 5);
 }
 
 }  // namespace hmm

@@ -323,7 +323,7 @@ accel_status tc_forward(const accel_hmm_model* mdl, const int32_t* obs, const in
     int64_t tiles = (S + kRows - 1) / kRows;
     int grid = (int)(tiles < num_sms() ? tiles : num_sms());
     k_hmm_tc<<<grid, kTcThreads, L.smem_bytes, st>>>(K, M, at, et, pi, obs, off, S, order, next, loglik, d_status, L);
-    return after_launch(st, "hmm_forward(bf16 tcgen05)");
+    return after_launch(st, "hmm_forward(bf16 tcgen05)", 5);
 }
 
 }  // namespace hmm

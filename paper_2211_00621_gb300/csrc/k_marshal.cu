@@ -192,7 +192,7 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
     cudaStream_t st = as_stream(stream);
     if (S == 0) {
         ACCEL_CUDA_TRY(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), st));
-        return after_launch(st, "accel_marshal_ragged");
+        return after_launch(st, "accel_marshal_ragged", 0);
     }
     char* ws = (char*)d_ws;
     int64_t* d_len = (int64_t*)(ws + lo);
@@ -212,7 +212,7 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
         k_gather<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t* const*)d_ptrs, d_offsets, S, (int32_t*)d_flat);
     else
         k_gather<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t* const*)d_ptrs, d_offsets, S, (int64_t*)d_flat);
-    return after_launch(st, "accel_marshal_ragged");
+    return after_launch(st, "accel_marshal_ragged", 4);
 }
 
 accel_status accel_marshal_records(void* d_aos, int64_t n, int32_t record_bytes, int32_t nfields,
@@ -253,7 +253,7 @@ accel_status accel_marshal_records(void* d_aos, int64_t n, int32_t record_bytes,
         if (inverse) k_records<true><<<(unsigned)blocks, 256, 0, st>>>((char*)d_aos, n, fd);
         else k_records<false><<<(unsigned)blocks, 256, 0, st>>>((char*)d_aos, n, fd);
     }
-    return after_launch(st, "accel_marshal_records");
+    return after_launch(st, "accel_marshal_records", 1);
 }
 
 }  // extern "C"

@@ -106,7 +106,7 @@ accel_status pairwise_mapreduce(int32_t op, const float* d_x, const float* d_y, 
     cudaStream_t st = as_stream(stream);
     unsigned grid = (unsigned)((n + pair::kBodies - 1) / pair::kBodies);
     pair::k_gravity<<<grid, pair::kThreads, 0, st>>>(d_x, d_y, d_z, d_m, n, eps * eps, d_ax, d_ay, d_az);
-    return after_launch(st, "pairwise_mapreduce");
+    return after_launch(st, "pairwise_mapreduce", 1);
 }
 
 }  // extern "C"

@@ -68,7 +68,7 @@ static accel_status launch_map(int32_t op, const void* in, const void* in2, void
         case ACCEL_MAP_MUL2: k_map<Tin, Tout, ACCEL_MAP_MUL2, true><<<grid, kThreads, 0, st>>>(a, b, o, n, scalar, vec_ok); break;
         default: ACCEL_DISPATCH_MAP1(op, OPC, (k_map<Tin, Tout, OPC, false><<<grid, kThreads, 0, st>>>(a, nullptr, o, n, scalar, vec_ok)));
     }
-    return after_launch(st, "accel_map");
+    return after_launch(st, "accel_map", 1);
 }
 
 // ------------------------------------------------------------------------ loop
@@ -183,7 +183,7 @@ accel_status accel_loop(int32_t body, int64_t n, const accel_tensor* args, int32
     ACCEL_DISPATCH_DTYPE(args[0].dtype, T,
         if (body == ACCEL_LOOP_AXPY) k_loop<T, ACCEL_LOOP_AXPY><<<grid, kThreads, 0, st>>>((T*)args[0].data, (const T*)args[1].data, n, scalar);
         else k_loop<T, ACCEL_LOOP_SCALE><<<grid, kThreads, 0, st>>>((T*)args[0].data, (const T*)args[1].data, n, scalar));
-    return after_launch(st, "accel_loop");
+    return after_launch(st, "accel_loop", 1);
 }
 
 size_t accel_reduce_workspace_size(int64_t n, int32_t dtype) {
@@ -205,7 +205,7 @@ accel_status accel_reduce(int32_t op, int32_t dtype, const void* d_in, int64_t n
         k_reduce_partial<T, OPC><<<grid, kThreads, 0, st>>>((const T*)d_in, n, (C*)partials);
         k_reduce_final<T, OPC><<<1, kThreads, 0, st>>>((const C*)partials, grid, (T*)d_out);
     }));
-    return after_launch(st, "accel_reduce");
+    return after_launch(st, "accel_reduce", 2);
 }
 
 }  // extern "C"

@@ -291,7 +291,7 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
         int g = (int)((S + 255) / 256);
         if (g > 8 * num_sms()) g = 8 * num_sms();
         k_fill<Tout><<<g, 256, 0, st>>>(out, S, nel);
-        return after_launch(st, "accel_segreduce(fill)");
+        return after_launch(st, "accel_segreduce(fill)", 1);
     }
     int64_t te = tile_elems<Tin>();
     k_partition<<<(unsigned)((L.ntiles + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);
@@ -300,7 +300,7 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
             (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, tval);
         k_fixup<Tout, OPC><<<(unsigned)((L.ntiles + 255) / 256), 256, 0, st>>>(d_off, lo, L.ntiles, te, tseg, tval, out);
     });
-    return after_launch(st, "accel_segreduce");
+    return after_launch(st, "accel_segreduce", 3);
 }
 
 }  // namespace segred

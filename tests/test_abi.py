@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "accel.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?(?:accel_status|size_t|char\s*\*|void|int32_t)\s*\*?\s*(\w+)\s*\(", src,
+    names = re.findall(r"^\s*(?:const\s+)?(?:accel_status|size_t|char\s*\*|void|int32_t|uint64_t)\s*\*?\s*(\w+)\s*\(", src,
                        flags=re.M)
     return sorted(set(names))
 

@@ -1,0 +1,164 @@
+"""GPU parity of the HMM adjoint (hmm_adjoint and the HMMLogLik autograd function) with
+the float64 oracle's forward-backward expected counts, brute-force enumeration and central
+finite differences of the float64 forward.
+
+Tolerance: relative Frobenius 1e-4 per gradient (FP32 arithmetic), against the oracle on
+the same float32-rounded log parameters the kernels receive.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2211_00621_gb300 import _lib, api, synth
+from oracle import hmm as ohmm
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dev(p):
+    logs = synth.hmm_log_inputs_f32(p)
+    t = {k: torch.from_numpy(v).to(DEV) for k, v in logs.items()}
+    return logs, t, torch.from_numpy(p["obs"]).to(DEV), torch.from_numpy(p["offsets"]).to(DEV)
+
+
+def _rel_fro(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _check_grads(got, ref, tol=1e-4):
+    for g, r, name in zip(got, ref, ("log_A", "log_B", "log_pi")):
+        e = _rel_fro(g, r)
+        assert e <= tol, f"{name}: relative Frobenius error {e:.3e}"
+
+
+@pytest.mark.parametrize("name", ["hmm_k2_t5", "hmm_k3_t4"])
+def test_bruteforce_fixture(name):
+    with open(os.path.join(GOLD, name + ".json")) as f:
+        c = json.load(f)
+    lA = torch.tensor(np.log(c["A"]), dtype=torch.float32, device=DEV)
+    lB = torch.tensor(np.log(c["B"]), dtype=torch.float32, device=DEV)
+    lpi = torch.tensor(np.log(c["pi"]), dtype=torch.float32, device=DEV)
+    obs = torch.tensor(c["obs"], dtype=torch.int32, device=DEV)
+    off = torch.tensor([0, len(c["obs"])], dtype=torch.int64, device=DEV)
+    gA, gB, gpi, ll = api.hmm_adjoint(lA, lB, lpi, obs, off)
+    np.testing.assert_allclose(gA.cpu().numpy(), c["xi"], rtol=2e-5, atol=1e-6)
+    np.testing.assert_allclose(gB.cpu().numpy(), c["counts"], rtol=2e-5, atol=1e-6)
+    np.testing.assert_allclose(gpi.cpu().numpy(), c["gamma1"], rtol=2e-5, atol=1e-6)
+    assert abs(ll.item() - c["loglik"]) <= 1e-5 * abs(c["loglik"])
+
+
+@pytest.mark.parametrize("K,M,S,lo,hi", [(8, 5, 20, 1, 50), (37, 11, 13, 1, 130), (64, 32, 9, 100, 400)])
+def test_small_models_against_oracle(K, M, S, lo, hi):
+    p = synth.hmm_workload(K * 3 + S, K, M, S, "uniform", lo, hi)
+    logs, t, obs, off = _dev(p)
+    w = synth.rng(5).uniform(0.5, 2.0, size=S)
+    gA, gB, gpi, ll = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off,
+                                      weights=torch.from_numpy(w).to(DEV))
+    par = ohmm.params_from_f32_logs(logs)
+    lls, rA, rB, rpi = ohmm.gradients_batch(p, weights=w, params=par)
+    _check_grads((gA.cpu().numpy(), gB.cpu().numpy(), gpi.cpu().numpy()), (rA, rB, rpi))
+    assert np.max(np.abs(ll.cpu().numpy() - lls) / np.abs(lls)) <= 1e-5
+
+
+def test_config_shapes_subset_against_oracle():
+    c = synth.CFG_HMM_ADJOINT
+    p = synth.hmm_workload(c["seed"] + 7, c["K"], c["M"], 24, c["kind"], c["lo"], c["hi"])
+    logs, t, obs, off = _dev(p)
+    gA, gB, gpi, ll = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off)
+    lls, rA, rB, rpi = ohmm.gradients_batch(p, params=ohmm.params_from_f32_logs(logs))
+    _check_grads((gA.cpu().numpy(), gB.cpu().numpy(), gpi.cpu().numpy()), (rA, rB, rpi))
+
+
+def test_config_full_size_invariants_and_weighted_subset():
+    c = synth.CFG_HMM_ADJOINT
+    p = synth.hmm_workload(c["seed"], c["K"], c["M"], c["S"], c["kind"], c["lo"], c["hi"])
+    logs, t, obs, off = _dev(p)
+    L = p["lengths"]
+    gA, gB, gpi, ll = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off)
+    gA, gB, gpi = gA.cpu().numpy().astype(np.float64), gB.cpu().numpy().astype(np.float64), gpi.cpu().numpy()
+    # one transition per step, one emission per step, one initial state per sequence
+    assert abs(gA.sum() - np.sum(L - 1)) <= 1e-4 * np.sum(L - 1)
+    assert abs(gB.sum() - np.sum(L)) <= 1e-4 * np.sum(L)
+    assert abs(gpi.sum() - c["S"]) <= 1e-4 * c["S"]
+    np.testing.assert_allclose(gB.sum(axis=0), np.bincount(p["obs"], minlength=c["M"]), rtol=1e-4)
+    assert (gA >= 0).all() and (gB >= 0).all() and (gpi >= 0).all()
+    # linearity in the weights: 0/1 weights select a subset, compared with the oracle
+    sub = sorted(set(synth.rng(3).choice(c["S"], size=6, replace=False).tolist() + [int(np.argmax(L))]))
+    w = np.zeros(c["S"])
+    w[sub] = 1.0
+    sA, sB, spi, _ = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off,
+                                     weights=torch.from_numpy(w).to(DEV))
+    _, rA, rB, rpi = ohmm.gradients_batch(p, seqs=sub, params=ohmm.params_from_f32_logs(logs))
+    _check_grads((sA.cpu().numpy(), sB.cpu().numpy(), spi.cpu().numpy()), (rA, rB, rpi))
+    # the forward's logL agrees with the FP32 log-space kernel
+    ll2 = api.hmm_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off).cpu().numpy()
+    assert np.max(np.abs(ll.cpu().numpy() - ll2) / np.abs(ll2)) <= 1e-5
+
+
+def test_central_finite_differences_fp64():
+    # d/d log A_ij and d/d log B_jk of sum_s logL_s by central differences (h = 1e-6) of the
+    # float64 forward, on a few sequences of the adjoint configuration's model.
+    c = synth.CFG_HMM_ADJOINT
+    p = synth.hmm_workload(c["seed"], c["K"], c["M"], 3, "uniform", 200, 400)
+    logs, t, obs, off = _dev(p)
+    gA, gB, gpi, _ = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off)
+    gA, gB = gA.cpu().numpy(), gB.cpu().numpy()
+    lA = logs["log_A"].astype(np.float64)
+    lB = logs["log_B"].astype(np.float64)
+    lpi = logs["log_pi"].astype(np.float64)
+    o, of = p["obs"], p["offsets"]
+
+    def total(a, b):
+        return sum(ohmm.forward_log(a, b, lpi, o[of[s]:of[s + 1]]) for s in range(3))
+
+    h = 1e-6
+    g = synth.rng(1)
+    for _ in range(4):
+        i, j = (int(x) for x in g.integers(0, c["K"], 2))
+        a1, a2 = lA.copy(), lA.copy()
+        a1[i, j] += h
+        a2[i, j] -= h
+        fd = (total(a1, lB) - total(a2, lB)) / (2 * h)
+        assert abs(gA[i, j] - fd) <= 1e-4 * abs(fd) + 2e-5
+    for _ in range(3):
+        j, k = int(g.integers(0, c["K"])), int(g.integers(0, c["M"]))
+        b1, b2 = lB.copy(), lB.copy()
+        b1[j, k] += h
+        b2[j, k] -= h
+        fd = (total(lA, b1) - total(lA, b2)) / (2 * h)
+        assert abs(gB[j, k] - fd) <= 1e-4 * abs(fd) + 2e-5
+
+
+def test_autograd_function():
+    p = synth.hmm_workload(4, 16, 6, 11, "uniform", 5, 80)
+    logs, t, obs, off = _dev(p)
+    lA = t["log_A"].clone().requires_grad_(True)
+    lB = t["log_B"].clone().requires_grad_(True)
+    lpi = t["log_pi"].clone().requires_grad_(True)
+    ll = api.HMMLogLik.apply(lA, lB, lpi, obs, off)
+    w = torch.linspace(0.5, 1.5, 11, dtype=torch.float64, device=DEV)
+    (ll * w).sum().backward()
+    _, rA, rB, rpi = ohmm.gradients_batch(p, weights=w.cpu().numpy(), params=ohmm.params_from_f32_logs(logs))
+    _check_grads((lA.grad.cpu().numpy(), lB.grad.cpu().numpy(), lpi.grad.cpu().numpy()), (rA, rB, rpi))
+
+
+def test_single_step_sequences_and_debug_max_T():
+    p = synth.hmm_workload(2, 8, 4, 10, "uniform", 1, 3)
+    logs, t, obs, off = _dev(p)
+    gA, gB, gpi, _ = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off)
+    _, rA, rB, rpi = ohmm.gradients_batch(p, params=ohmm.params_from_f32_logs(logs))
+    np.testing.assert_allclose(gB.cpu().numpy(), rB, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(gpi.cpu().numpy(), rpi, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(gA.cpu().numpy(), rA, rtol=1e-5, atol=1e-6)
+    api.set_debug(True)
+    try:
+        with pytest.raises(_lib.AccelError) as e:
+            api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, max_T=1)
+        assert e.value.status == 2
+    finally:
+        api.set_debug(False)
