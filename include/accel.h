@@ -183,6 +183,29 @@ accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, in
                              const void* d_data, int64_t N, const int64_t* d_offsets, int64_t S,
                              double scalar, void* d_out, void* d_ws, size_t ws_bytes, void* stream);
 
+/*
+ * accel_segreduce_noalloc -- accel_segreduce for callers that cannot allocate device
+ * memory (code that runs where cudaMalloc is unavailable or not allowed: inside an
+ * allocator's own hooks, under a host framework that owns every allocation, or in a loop
+ * that must never enter the allocator).  The paper has no counterpart: it is a property of
+ * this library, not of expression acceleration.  Same arguments and results as
+ * accel_segreduce, without (d_ws, ws_bytes): the scratch is a 1 MiB array inside the
+ * library, created on each device when the library is loaded there and held until the
+ * process exits.
+ *  Limit: N <= 178,909,184 flat elements (any element type); larger N returns
+ *  ACCEL_ERR_UNSUPPORTED before anything is launched.
+ *  Sharing: every call in the process uses the same array; it keeps the last call's
+ *  contents, and each call writes every byte it reads before reading it, so nothing needs
+ *  clearing between calls.  Calls that overlap on the GPU (other streams, or other host
+ *  threads without ordering) race on the array: order them.
+ *  Set-up: the first call on a device looks up the array's device address with that device
+ *  current and caches it; make that first call before any stream capture begins.
+ *  The call itself allocates nothing and frees nothing.
+ */
+accel_status accel_segreduce_noalloc(int32_t op, int32_t fused_map, int32_t in_dtype, int32_t out_dtype,
+                                     const void* d_data, int64_t N, const int64_t* d_offsets, int64_t S,
+                                     double scalar, void* d_out, void* stream);
+
 /* ============================================================== loop (Appendix A) */
 /* A tensor argument (Tensor[Int] / Tensor[Float], rank <= 3, dense row-major). */
 typedef struct accel_tensor {

@@ -58,6 +58,7 @@ SIGNATURES = {
     "accel_reduce": (i32, [i32, i32, vp, i64, vp, vp, sz, vp]),
     "accel_segreduce_workspace_size": (sz, [i64, i64]),
     "accel_segreduce": (i32, [i32, i32, i32, i32, vp, i64, vp, i64, dbl, vp, vp, sz, vp]),
+    "accel_segreduce_noalloc": (i32, [i32, i32, i32, i32, vp, i64, vp, i64, dbl, vp, vp]),
     "accel_loop": (i32, [i32, i64, C.POINTER(accel_tensor), i32, dbl, vp]),
     "hmm_forward_workspace_size": (sz, [C.POINTER(accel_hmm_model), i64, i64, i32]),
     "hmm_forward": (i32, [C.POINTER(accel_hmm_model), i32, vp, vp, i64, i64, vp, vp, sz, vp]),

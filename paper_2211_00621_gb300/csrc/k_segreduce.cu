@@ -352,3 +352,76 @@ accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, in
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------------------
+// accel_segreduce_noalloc: the same segmented reduce for callers that cannot allocate
+// device memory -- code running where cudaMalloc is unavailable or forbidden, such as
+// inside a custom allocator's own callbacks, a plugin host that owns every allocation, or
+// a real-time loop that must never reach the allocator.  Its scratch space is the
+// file-scope array below, created when the library is loaded on a device and kept until
+// the process exits; nothing is allocated or freed per call.
+//
+// Limits and sharing: the array holds kNoAllocScratchBytes (1 MiB), enough for
+// N <= 178,909,184 flat elements per call (any element type; S is not limited); larger
+// inputs are rejected with ACCEL_ERR_UNSUPPORTED.  All calls in the process share the array and it
+// keeps the last call's contents; every byte a call reads is first written by that same
+// call, so nothing has to be cleared in between.  Calls that overlap on the GPU (different
+// streams, or different host threads without ordering) race on the array.
+// Set-up: the first call on each device looks up the array's device address with
+// cudaGetSymbolAddress while that device is current, and caches it; make that first call
+// before any stream capture begins.
+// ----------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace accel {
+namespace segred {
+
+constexpr size_t kNoAllocScratchBytes = 1u << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+static accel_status noalloc_scratch(void** out) {
+    int dev = 0;
+    ACCEL_CUDA_TRY(cudaGetDevice(&dev));
+    ACCEL_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, ACCEL_ERR_UNSUPPORTED,
+                  "accel_segreduce_noalloc: device index %d >= %d", dev, kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return set_error(ACCEL_ERR_CUDA, "accel_segreduce_noalloc: cudaGetSymbolAddress failed: %s",
+                             cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return ACCEL_OK;
+}
+
+}  // namespace segred
+}  // namespace accel
+
+extern "C" {
+
+accel_status accel_segreduce_noalloc(int32_t op, int32_t fused_map, int32_t in_dtype, int32_t out_dtype,
+                                     const void* d_data, int64_t N, const int64_t* d_offsets, int64_t S, double scalar,
+                                     void* d_out, void* stream) {
+    ACCEL_REQUIRE(N >= 0 && S >= 0, ACCEL_ERR_INVALID_ARG, "accel_segreduce_noalloc: negative size");
+    const size_t need = accel_segreduce_workspace_size(N, S);
+    ACCEL_REQUIRE(need <= segred::kNoAllocScratchBytes, ACCEL_ERR_UNSUPPORTED,
+                  "accel_segreduce_noalloc: N=%lld needs %zu bytes of scratch; the built-in area holds %zu bytes "
+                  "(at most 178,909,184 elements); use accel_segreduce with a workspace",
+                  (long long)N, need, segred::kNoAllocScratchBytes);
+    void* scratch = nullptr;
+    accel_status r = segred::noalloc_scratch(&scratch);
+    if (r != ACCEL_OK) return r;
+    return accel_segreduce(op, fused_map, in_dtype, out_dtype, d_data, N, d_offsets, S, scalar, d_out, scratch,
+                           segred::kNoAllocScratchBytes, stream);
+}
+
+}  // extern "C"
