@@ -331,6 +331,78 @@ def oracle_threads():
     return 1
 
 
+# ------------------------------------------------------------- single-kernel cases
+def sweep_inputs(torch, dev, S):
+    data, lengths = synth.ragged_flat_int32(1, S)
+    off = np.zeros(S + 1, np.int64)
+    np.cumsum(lengths, out=off[1:])
+    return torch.from_numpy(data).to(dev), torch.from_numpy(off).to(dev)
+
+
+def segreduce_sweep(torch, dev, api, S=1 << 20, reps=10):
+    """Fused map + segmented int64 sum at HBM scale (L2 flushed before each rep)."""
+    d, o = sweep_inputs(torch, dev, S)
+    out = torch.empty(S, dtype=torch.int64, device=dev)
+    ws = torch.empty(api.L.load().accel_segreduce_workspace_size(d.numel(), S), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    run = lambda: api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, d, o, torch.int64, out=out, ws=ws)
+    for _ in range(3):
+        run()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    nbytes = 4 * d.numel() + 16 * S + 8
+    return {"S": S, "N": int(d.numel()), "ms": ms, "GB/s": nbytes / (ms * 1e-3) / 1e9, "bytes": nbytes}
+
+
+PROFILE_CASES = ("segreduce_sweep", "step", "hmm_plain", "hmm_bf16", "hmm_bf16_small", "hmm_adjoint",
+                 "hmm_adjoint_small", "allpairs")
+
+
+def profile_case(name, reps, torch, dev):
+    """Runs one kernel case `reps` times (for ncu captures of a single kernel)."""
+    from paper_2211_00621_gb300 import api
+    if name == "segreduce_sweep":
+        d, o = sweep_inputs(torch, dev, 1 << 20)
+        fn = lambda: api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, d, o, torch.int64)
+    elif name == "step":
+        W = Workload(torch, dev, True)
+        fn = lambda: W.step()
+    elif name in ("hmm_plain", "hmm_bf16", "hmm_bf16_small", "hmm_adjoint", "hmm_adjoint_small"):
+        cfg = {"hmm_plain": synth.CFG_HMM_PLAIN, "hmm_bf16": synth.CFG_HMM_BATCHED,
+               "hmm_bf16_small": dict(synth.CFG_HMM_BATCHED, S=1024, hi=1000),
+               "hmm_adjoint": synth.CFG_HMM_ADJOINT,
+               "hmm_adjoint_small": dict(synth.CFG_HMM_ADJOINT, S=256, lo=100, hi=400)}[name]
+        h = hmm_inputs(cfg, torch, dev)
+        if name.startswith("hmm_adjoint"):
+            fn = lambda: api.hmm_adjoint(h["log_A"], h["log_B"], h["log_pi"], h["obs"], h["offsets"],
+                                         max_T=h["maxT"], want_loglik=False)
+        else:
+            prec = api.HMM_FP32_LOG if name == "hmm_plain" else api.HMM_BF16_SCALED
+            fn = lambda: api.hmm_forward(h["log_A"], h["log_B"], h["log_pi"], h["obs"], h["offsets"], prec)
+    elif name == "allpairs":
+        b = synth.bodies(0, synth.CFG_ALLPAIRS["N"])
+        aos = torch.from_numpy(b["aos"]).to(dev)
+        f32 = torch.float32
+        x, y, z, m = api.accel_marshal_records(aos, [(0, f32), (4, f32), (8, f32), (12, f32)])
+        fn = lambda: api.pairwise_mapreduce(x, y, z, m, synth.CFG_ALLPAIRS["eps"])
+    else:
+        raise ValueError(name)
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "reps": reps, "ok": True}))
+    return 0
+
+
 # ---------------------------------------------------------------------------- main
 def run_reference(args, rank, world):
     if rank != 0:
@@ -366,6 +438,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--profile-case", choices=PROFILE_CASES, default=None,
+                    help="run one kernel case --reps times and exit (for ncu captures)")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -393,6 +468,8 @@ def main():
         if world > 1:
             dist.barrier()
     lib = _lib.load()
+    if args.profile_case:
+        return profile_case(args.profile_case, args.reps, torch, dev)
 
     with_adj = not args.no_adjoint
     if with_adj:
@@ -461,8 +538,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = float(t.item())
 
+    # ---------------- seg-reduce at HBM scale (2^20 segments)
+    sweep = segreduce_sweep(torch, dev, api)
+
     # ---------------- rooflines
     peaks, peak_src = load_peaks()
+    sweep["frac"] = sweep["GB/s"] / peaks["hbm_gbs"]
     rl = rooflines(W, row_ms, peaks, float(peaks.get("sm_max_mhz", 2070.0)))
     dom = max((k for k in rl), key=lambda k: row_ms.get(k, 0.0))
     dom_src = {"segreduce": "k_segreduce.cu", "hmm_plain": "k_hmm_plain.cu", "hmm_bf16": "k_hmm_tc.cu",
@@ -474,7 +555,6 @@ def main():
 
     rows = {k: {"ms": row_ms[k], "frac": rl[k]["frac"], "achieved": rl[k]["achieved"], "unit": rl[k]["unit"],
                 "bound": rl[k]["bound"]} for k in rl}
-    seg_gbs = rl["segreduce"]["achieved"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -486,7 +566,8 @@ def main():
                                    "; all-pairs N=65536",
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
-            "seg_reduce_gbs": seg_gbs, "rows": rows, "roofline": roof,
+            "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweep,
+            "rows": rows, "roofline": roof,
             "e2e": {"value": work * world / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": int(launches), "clocks": clk}
