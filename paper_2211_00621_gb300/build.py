@@ -21,8 +21,10 @@ LIB = os.path.join(PKG, "libaccel.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host-function-from-device-code diagnostics are errors: nvcc otherwise compiles such a
+# kernel into one that does nothing
 CFLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo", "-Xcompiler", "-fPIC",
-          "-I" + INCLUDE, "-I" + CSRC]
+          "--diag-error=20011,20014", "-I" + INCLUDE, "-I" + CSRC]
 
 
 def nvcc() -> str:

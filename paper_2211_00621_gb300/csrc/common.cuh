@@ -59,7 +59,7 @@ template <> struct dtype_of<ACCEL_F64> { using type = double; };
 template <typename T> struct compute_of { using type = T; };
 template <> struct compute_of<int32_t> { using type = int64_t; };
 
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ----------------------------------------------------------------- device helpers
 template <typename T> __host__ __device__ inline T red_neutral(int op);

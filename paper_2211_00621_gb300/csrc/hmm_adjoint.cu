@@ -27,6 +27,7 @@
 // All kernels are FP32 SIMT; the groups of 8 sequences per CTA are taken in order of
 // decreasing length.  Every accumulation has a fixed order, so results are deterministic.
 #include "hmm_internal.cuh"
+#include "simt_stream.cuh"
 
 #include <math.h>
 
@@ -59,8 +60,9 @@ struct Prm {
     float* Rc;          // carried R [S][K]
     float* cnt;         // per group [ngroups][K][M]
     float* pig;         // per group [ngroups][K]
-    int32_t* status;    // device status word (ACCEL_ERR_SHAPE if a length exceeds max_T)
-    int Kp;             // padded row stride of the shared-memory vectors (multiple of 4)
+    int32_t* status;    // device status word (ACCEL_ERR_SHAPE / ACCEL_ERR_TIMEOUT)
+    int Kp;             // padded row stride (multiple of 4) of A, At and the shared vectors
+    int32_t* rows;      // per round: rows of P/Q that may be non-zero (sorted-position order)
 };
 
 __host__ __device__ __forceinline__ int seg_len(int64_t T) {
@@ -113,51 +115,22 @@ __device__ __forceinline__ void block_sum_g(float (&v)[kG], float (*s_red)[kT / 
     __syncthreads();
 }
 
-// acc_g(j) = sum_i X[g][i] Mat[i][j] for the active g (Mat row-major K x K, read by columns)
-__device__ __forceinline__ void matvec_g(const float* __restrict__ Mat, const float* __restrict__ X, int K, int ld,
-                                         const bool (&act)[kG], float (&acc)[kG]) {
-    const int j = threadIdx.x;
-#pragma unroll
-    for (int g = 0; g < kG; ++g) acc[g] = 0.f;
-    if (j >= K) return;
-    const float* col = Mat + j;
-    int i = 0;
-    for (; i + 4 <= K; i += 4) {
-        float a0 = __ldg(col + (int64_t)(i + 0) * K), a1 = __ldg(col + (int64_t)(i + 1) * K);
-        float a2 = __ldg(col + (int64_t)(i + 2) * K), a3 = __ldg(col + (int64_t)(i + 3) * K);
-#pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            if (!act[g]) continue;
-            float4 x = *reinterpret_cast<const float4*>(X + g * ld + i);
-            acc[g] = fmaf(x.x, a0, acc[g]);
-            acc[g] = fmaf(x.y, a1, acc[g]);
-            acc[g] = fmaf(x.z, a2, acc[g]);
-            acc[g] = fmaf(x.w, a3, acc[g]);
-        }
-    }
-    for (; i < K; ++i) {
-        float a0 = __ldg(col + (int64_t)i * K);
-#pragma unroll
-        for (int g = 0; g < kG; ++g)
-            if (act[g]) acc[g] = fmaf(X[g * ld + i], a0, acc[g]);
-    }
-}
-
-// One forward step for the active sequences: sS holds S_{t-1} on entry and S_t on exit;
-// returns e_t and c'_t per sequence.  obs_t[g] is o_t of sequence g.
-__device__ __forceinline__ void fwd_step(const Prm& p, float* sS, const float* sBT, float (*s_red)[kT / 32],
-                                         const bool (&act)[kG], const int (&obs_t)[kG], int (&e)[kG],
-                                         float (&c)[kG]) {
+// One forward step for the active sequences with A streamed through shared memory: sS
+// holds S_{t-1} on entry and S_t on exit; returns e_t and c'_t per sequence.  obs_t[g] is
+// o_t of sequence g.  Returns false if a bulk copy did not arrive in time.
+__device__ __forceinline__ bool fwd_step(const Prm& p, simt::AStream& as, float* sS, const float* sBT,
+                                         float (*s_red)[kT / 32], const bool (&act)[kG], const int (&obs_t)[kG],
+                                         int (&e)[kG], float (&c)[kG]) {
     const int j = threadIdx.x, K = p.K, Kp = p.Kp;
     float acc[kG];
-    matvec_g(p.A, sS, K, Kp, act, acc);
+    if (!simt::as_matvec<kG>(as, sS, Kp, act, acc)) return false;
     float v[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
         acc[g] = (act[g] && j < K) ? acc[g] * sBT[obs_t[g] * K + j] : 0.f;
         v[g] = acc[g];
     }
-    block_sum_g(v, s_red);   // includes a barrier after all reads of sS
+    block_sum_g(v, s_red);   // its barriers follow every read of sS
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
         c[g] = v[g];
@@ -167,20 +140,28 @@ __device__ __forceinline__ void fwd_step(const Prm& p, float* sS, const float* s
         if (act[g] && j < K) sS[g * Kp + j] = acc[g] * ldexpf(1.0f, -ex);
     }
     __syncthreads();
+    return true;
 }
 
+__device__ __forceinline__ void report_timeout(const Prm& p, simt::AStream& as) {
+    if (threadIdx.x == 0) atomicExch(p.status, ACCEL_ERR_TIMEOUT);
+    simt::as_drain(as);
+}
+
+// A and At with row stride Kp (padding zero), the emission table transposed, pi.
 __global__ void k_prep(const float* __restrict__ logA, const float* __restrict__ logB, const float* __restrict__ logpi,
-                       int K, int M, float* __restrict__ A, float* __restrict__ At, float* __restrict__ BT,
+                       int K, int Kp, int M, float* __restrict__ A, float* __restrict__ At, float* __restrict__ BT,
                        float* __restrict__ pi) {
-    int64_t nA = (int64_t)K * K, nB = (int64_t)K * M;
+    int64_t nA = (int64_t)K * Kp, nB = (int64_t)K * M;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * nA + nB + K;
          idx += (int64_t)gridDim.x * blockDim.x) {
         if (idx < nA) {
-            A[idx] = __expf(logA[idx]);
+            int i = (int)(idx / Kp), j = (int)(idx % Kp);
+            A[idx] = j < K ? __expf(logA[(int64_t)i * K + j]) : 0.f;
         } else if (idx < 2 * nA) {
             int64_t q = idx - nA;
-            int i = (int)(q / K), j = (int)(q % K);
-            At[(int64_t)j * K + i] = __expf(logA[q]);
+            int j = (int)(q / Kp), i = (int)(q % Kp);
+            At[q] = i < K ? __expf(logA[(int64_t)i * K + j]) : 0.f;
         } else if (idx < 2 * nA + nB) {
             int64_t q = idx - 2 * nA;
             int j = (int)(q / M), k = (int)(q % M);
@@ -192,12 +173,19 @@ __global__ void k_prep(const float* __restrict__ logA, const float* __restrict__
     }
 }
 
+// Shared-memory layout of both kernels: [A stream ring + barriers][emission table M x K]
+// [sS kG x Kp][sR kG x Kp][sE kG x Cmax ints]
+__host__ __device__ inline size_t off_bt(int Kp) { return align_up(simt::stream_smem_bytes(Kp), 16); }
+__host__ __device__ inline size_t off_ss(int K, int M, int Kp) { return align_up(off_bt(Kp) + (size_t)M * K * 4, 16); }
+
 // ---------------------------------------------------------------- forward + checkpoints
 __global__ void __launch_bounds__(kT) k_forward_cp(Prm p) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) char smem[];
     const int K = p.K, M = p.M, Kp = p.Kp, j = threadIdx.x;
-    float* sBT = smem;                                       // [M][K]
-    float* sS = smem + (((size_t)M * K + 3) & ~(size_t)3);   // [kG][K]
+    simt::AStream as;
+    simt::as_init(as, smem, K, Kp);
+    float* sBT = reinterpret_cast<float*>(smem + off_bt(Kp));          // [M][K]
+    float* sS = reinterpret_cast<float*>(smem + off_ss(K, M, Kp));     // [kG][Kp]
     __shared__ float s_red[kG][kT / 32];
     for (int idx = j; idx < M * K; idx += kT) sBT[idx] = p.BT[idx];
     GroupInfo gi;
@@ -205,6 +193,7 @@ __global__ void __launch_bounds__(kT) k_forward_cp(Prm p) {
     int64_t Tmax = 0;
     for (int g = 0; g < kG; ++g) Tmax = gi.T[g] > Tmax ? gi.T[g] : Tmax;
     __syncthreads();
+    simt::as_begin(as, p.A);
     // t = 0: alpha~_0 = pi o b(o_0)
     bool act[kG];
     int ob[kG], e[kG];
@@ -244,7 +233,7 @@ __global__ void __launch_bounds__(kT) k_forward_cp(Prm p) {
             act[g] = t < gi.T[g];
             ob[g] = act[g] ? p.obs[gi.o0[g] + t] : 0;
         }
-        fwd_step(p, sS, sBT, s_red, act, ob, e, c);
+        if (!fwd_step(p, as, sS, sBT, s_red, act, ob, e, c)) { report_timeout(p, as); return; }
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
             if (!act[g]) continue;
@@ -260,38 +249,56 @@ __global__ void __launch_bounds__(kT) k_forward_cp(Prm p) {
             }
         }
     }
+    if (!simt::as_end(as)) report_timeout(p, as);
 }
 
 // ---------------------------------------------------------------- one backward round
+// P/Q rows of the sequence at sorted position q are rows [q Cmax, (q+1) Cmax).
 __global__ void __launch_bounds__(kT) k_backward_round(Prm p, int r) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) char smem[];
     const int K = p.K, M = p.M, Kp = p.Kp, j = threadIdx.x;
-    float* sBT = smem;                                             // [M][K]
-    float* sS = smem + (((size_t)M * K + 3) & ~(size_t)3);         // [kG][Kp] recompute state / v
-    float* sR = sS + (size_t)kG * Kp;                              // [kG][Kp] R_{t+1}
-    int* sE = reinterpret_cast<int*>(sR + (size_t)kG * Kp);        // [kG][Cmax] exponents of the segment
+    simt::AStream as;
+    simt::as_init(as, smem, K, Kp);
+    float* sBT = reinterpret_cast<float*>(smem + off_bt(Kp));          // [M][K]
+    float* sS = reinterpret_cast<float*>(smem + off_ss(K, M, Kp));     // [kG][Kp] recompute state / v
+    float* sR = sS + (size_t)kG * Kp;                                  // [kG][Kp] R_{t+1}
+    int* sE = reinterpret_cast<int*>(sR + (size_t)kG * Kp);            // [kG][Cmax] exponents of the segment
     __shared__ float s_red[kG][kT / 32];
     for (int idx = j; idx < M * K; idx += kT) sBT[idx] = p.BT[idx];
     GroupInfo gi;
     load_group(p, gi);
-    int64_t t0[kG], L[kG];
+    int64_t t0[kG], L[kG], rowbase[kG];
     int maxL = 0;
     float wgt[kG];
+    bool just_done[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
         t0[g] = 0;
         L[g] = 0;
         wgt[g] = 0.f;
+        just_done[g] = false;
+        rowbase[g] = (blockIdx.x * (int64_t)kG + g) * p.Cmax;
         if (gi.seq[g] < 0) continue;
         int64_t n = (gi.T[g] + gi.C[g] - 1) / gi.C[g];
         int64_t k = n - 1 - r;
+        just_done[g] = k == -1;
         if (k < 0) continue;
         t0[g] = k * gi.C[g];
         int64_t t1 = t0[g] + gi.C[g] < gi.T[g] ? t0[g] + gi.C[g] : gi.T[g];
         L[g] = t1 - t0[g];
         maxL = L[g] > maxL ? (int)L[g] : maxL;
         wgt[g] = p.w ? (float)p.w[gi.seq[g]] : 1.0f;
+        if (j == 0) atomicMax(&p.rows[r], (int32_t)(rowbase[g] + p.Cmax));
     }
+    // rows that must read as zero: all rows of a sequence whose last segment was done in
+    // the previous round, and rows past the segment length of an active one
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        if (gi.seq[g] < 0 || !(just_done[g] || L[g] > 0)) continue;
+        for (int64_t tt = L[g]; tt < p.Cmax; ++tt)
+            if (j < K) p.Q[(rowbase[g] + tt) * K + j] = 0.f;
+    }
+    if (maxL == 0) return;
     // ---- recompute S_t for t in [t0, t0 + L) into the P rows (and e_t into sE)
     bool act[kG];
     int ob[kG], e[kG];
@@ -305,26 +312,27 @@ __global__ void __launch_bounds__(kT) k_backward_round(Prm p, int r) {
         if (j < K) {
             float sv = p.cp[(base + k) * K + j];
             sS[g * Kp + j] = sv;
-            p.P[base * K + j] = sv;
+            p.P[rowbase[g] * K + j] = sv;
         }
         if (j == 0) sE[g * p.Cmax] = p.cp_e[base + k];
     }
     __syncthreads();
+    simt::as_begin(as, p.A);
     for (int tt = 1; tt < maxL; ++tt) {
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
             act[g] = tt < L[g];
             ob[g] = act[g] ? p.obs[gi.o0[g] + t0[g] + tt] : 0;
         }
-        fwd_step(p, sS, sBT, s_red, act, ob, e, c);
+        if (!fwd_step(p, as, sS, sBT, s_red, act, ob, e, c)) { report_timeout(p, as); return; }
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
             if (!act[g]) continue;
-            int64_t row = (int64_t)gi.seq[g] * p.Cmax + tt;
-            if (j < K) p.P[row * K + j] = sS[g * Kp + j];
+            if (j < K) p.P[(rowbase[g] + tt) * K + j] = sS[g * Kp + j];
             if (j == 0) sE[g * p.Cmax + tt] = e[g];
         }
     }
+    if (!simt::as_end(as)) { report_timeout(p, as); return; }
     // ---- backward across the segment: R_{t+1} in sR, v = b(o_{t+1}) o R_{t+1} in sS
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
@@ -333,26 +341,24 @@ __global__ void __launch_bounds__(kT) k_backward_round(Prm p, int r) {
         sR[g * Kp + j] = last_seg ? 0.f : p.Rc[(int64_t)gi.seq[g] * K + j];
     }
     __syncthreads();
+    simt::as_begin(as, p.At);
+    float* cnt = p.cnt + (int64_t)blockIdx.x * K * M;
     for (int tt = maxL - 1; tt >= 0; --tt) {
         bool trans[kG];
-        int ob1[kG];
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
             act[g] = tt < L[g];
             int64_t t = t0[g] + tt;
             trans[g] = act[g] && t < gi.T[g] - 1;          // transition t -> t+1 exists
-            ob1[g] = trans[g] ? p.obs[gi.o0[g] + t + 1] : 0;
             if (act[g] && j < K) {
-                int64_t row = (int64_t)gi.seq[g] * p.Cmax + tt;
-                float vv = trans[g] ? sBT[ob1[g] * K + j] * sR[g * Kp + j] : 0.f;
+                float vv = trans[g] ? sBT[p.obs[gi.o0[g] + t + 1] * K + j] * sR[g * Kp + j] : 0.f;
                 sS[g * Kp + j] = vv;
-                p.Q[row * K + j] = wgt[g] * vv;
+                p.Q[(rowbase[g] + tt) * K + j] = wgt[g] * vv;
             }
         }
         __syncthreads();
         float acc[kG];
-        matvec_g(p.At, sS, K, Kp, trans, acc);
-        __syncthreads();
+        if (!simt::as_matvec<kG>(as, sS, Kp, trans, acc)) { report_timeout(p, as); return; }
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
             if (!act[g]) continue;
@@ -360,11 +366,9 @@ __global__ void __launch_bounds__(kT) k_backward_round(Prm p, int r) {
             const int et = sE[g * p.Cmax + tt];
             float Rt = trans[g] ? acc[g] * ldexpf(1.0f, -et) : 1.0f / p.clast[gi.seq[g]];
             if (j < K) {
-                int64_t row = (int64_t)gi.seq[g] * p.Cmax + tt;
-                float St = p.P[row * K + j];
+                float St = p.P[(rowbase[g] + tt) * K + j];
                 float gam = wgt[g] * St * Rt * ldexpf(1.0f, et);
                 int ot = p.obs[gi.o0[g] + t];
-                float* cnt = p.cnt + (int64_t)blockIdx.x * K * M;
                 cnt[(int64_t)j * M + ot] += gam;
                 if (t == 0) p.pig[(int64_t)blockIdx.x * K + j] += gam;
                 sR[g * Kp + j] = Rt;
@@ -372,26 +376,25 @@ __global__ void __launch_bounds__(kT) k_backward_round(Prm p, int r) {
         }
         __syncthreads();
     }
-    // carry R_{t0} to the next round; zero the unused rows of Q
+    if (!simt::as_end(as)) { report_timeout(p, as); return; }
+    // carry R_{t0} to the next round
 #pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        if (gi.seq[g] < 0) continue;
-        int64_t base = (int64_t)gi.seq[g] * p.Cmax;
+    for (int g = 0; g < kG; ++g)
         if (L[g] > 0 && j < K) p.Rc[(int64_t)gi.seq[g] * K + j] = sR[g * Kp + j];
-        for (int64_t tt = L[g]; tt < p.Cmax; ++tt)
-            if (j < K) p.Q[(base + tt) * K + j] = 0.f;
-    }
 }
 
 // ---------------------------------------------------------------- U += P^T Q (split-K)
-// CTA (tile i-block, j-block, split): rows [split*rows/kSplit, ...) of P and Q.
-__global__ void __launch_bounds__(256) k_gemm_ptq(const float* __restrict__ P, const float* __restrict__ Q, int64_t rows,
-                                                 int K, float* __restrict__ Upart) {
+// CTA (tile i-block, j-block, split) takes rows [split*R/kSplit, (split+1)*R/kSplit) of the
+// rows R = rows[round] that may be non-zero.
+__global__ void __launch_bounds__(256) k_gemm_ptq(const float* __restrict__ P, const float* __restrict__ Q,
+                                                 const int32_t* __restrict__ rows_r, int K, float* __restrict__ Upart) {
     __shared__ float sP[32][kTile + 4];
     __shared__ float sQ[32][kTile + 4];
+    const int64_t rows = *rows_r;
     const int nb = (K + kTile - 1) / kTile;
     const int bi = blockIdx.x % nb, bj = (blockIdx.x / nb) % nb, sp = blockIdx.x / (nb * nb);
     const int64_t r0 = rows * sp / kSplit, r1 = rows * (sp + 1) / kSplit;
+    if (r0 >= r1) return;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
     float acc[4][4] = {};
     for (int64_t rb = r0; rb < r1; rb += 32) {
@@ -451,7 +454,7 @@ __global__ void k_finish(const float* __restrict__ A, const float* __restrict__ 
 }
 
 struct Layout {
-    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, order, total;
+    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, order, total;
     int Cmax;
     int64_t ngroups;
 };
@@ -462,8 +465,9 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.ngroups = (S + kG - 1) / kG;
     size_t o = kStatusBytes;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
-    L.A = take((size_t)K * K * 4);
-    L.At = take((size_t)K * K * 4);
+    const size_t Kp = (size_t)((K + 3) & ~3);
+    L.A = take((size_t)K * Kp * 4);
+    L.At = take((size_t)K * Kp * 4);
     L.BT = take((size_t)M * K * 4);
     L.pi = take((size_t)K * 4);
     L.cp = take((size_t)S * L.Cmax * K * 4);
@@ -475,15 +479,16 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.cnt = take((size_t)L.ngroups * K * M * 4);
     L.pig = take((size_t)L.ngroups * K * 4);
     L.Upart = take((size_t)kSplit * K * K * 4);
+    L.rows = take((size_t)L.Cmax * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
     return L;
 }
 
 static int padK(int K) { return (K + 3) & ~3; }
-static size_t smem_fwd(int K, int M) { return ((((size_t)M * K + 3) & ~(size_t)3) + (size_t)kG * padK(K)) * 4; }
+static size_t smem_fwd(int K, int M) { return off_ss(K, M, padK(K)) + (size_t)kG * padK(K) * 4; }
 static size_t smem_bwd(int K, int M, int Cmax) {
-    return ((((size_t)M * K + 3) & ~(size_t)3) + 2 * (size_t)kG * padK(K)) * 4 + (size_t)kG * Cmax * 4;
+    return off_ss(K, M, padK(K)) + 2 * (size_t)kG * padK(K) * 4 + (size_t)kG * Cmax * 4;
 }
 
 }  // namespace adj
@@ -535,6 +540,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     adj::Prm p;
     p.K = K; p.M = M; p.Cmax = L.Cmax; p.S = S; p.Kp = adj::padK(K);
     p.status = (int32_t*)(ws + kStatusOff);
+    p.rows = (int32_t*)(ws + L.rows);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
     p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = d_weights;
     p.cp = (float*)(ws + L.cp); p.cp_e = (int32_t*)(ws + L.cp_e); p.clast = (float*)(ws + L.clast);
@@ -543,13 +549,15 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     float* Upart = (float*)(ws + L.Upart);
     int nlaunch = 0;
     int pg = num_sms() * 4;
-    adj::k_prep<<<pg, 256, 0, st>>>(m->log_A, m->log_B, m->log_pi, K, M, (float*)p.A, (float*)p.At, (float*)p.BT,
-                                    (float*)p.pi);
+    adj::k_prep<<<pg, 256, 0, st>>>(m->log_A, m->log_B, m->log_pi, K, p.Kp, M, (float*)p.A, (float*)p.At,
+                                    (float*)p.BT, (float*)p.pi);
     ++nlaunch;
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cnt, 0, (size_t)L.ngroups * K * M * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.pig, 0, (size_t)L.ngroups * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)adj::kSplit * K * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.rows, 0, (size_t)L.Cmax * 4, st));
     if (S > 0) {
         r = order_by_length(d_offsets, S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)S * 4, 256), st);
         if (r != ACCEL_OK) return r;
@@ -562,7 +570,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
         const int nb = (K + adj::kTile - 1) / adj::kTile;
         for (int round = 0; round < L.Cmax; ++round) {
             adj::k_backward_round<<<(unsigned)L.ngroups, adj::kT, sm_b, st>>>(p, round);
-            adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, S * (int64_t)L.Cmax, K, Upart);
+            adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
             nlaunch += 2;
         }
     }
@@ -575,7 +583,8 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
         int32_t h = 0;
         ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, ws + kStatusOff, 4, cudaMemcpyDeviceToHost, st));
         ACCEL_CUDA_TRY(cudaStreamSynchronize(st));
-        if (h != ACCEL_OK) return set_error(h, "hmm_adjoint: a sequence is longer than max_T=%lld", (long long)max_T);
+        if (h == ACCEL_ERR_SHAPE) return set_error(h, "hmm_adjoint: a sequence is longer than max_T=%lld", (long long)max_T);
+        if (h != ACCEL_OK) return set_error(h, "hmm_adjoint: device status %d (a bounded wait gave up)", h);
     }
     return ok();
 }

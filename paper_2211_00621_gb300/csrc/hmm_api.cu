@@ -61,7 +61,7 @@ accel_status hmm_forward(const accel_hmm_model* m, int32_t precision, const int3
     }
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + kStatusOff, 0, 4, st));
     if (precision == ACCEL_HMM_FP32_LOG) {
-        r = plain_forward(m, d_obs, d_offsets, S, d_loglik, ws + kStatusBytes, st);
+        r = plain_forward(m, d_obs, d_offsets, S, d_loglik, ws + kStatusBytes, (int32_t*)(ws + kStatusOff), st);
     } else {
         r = tc_forward(m, d_obs, d_offsets, S, d_loglik, ws, (int32_t*)(ws + kStatusOff), st);
     }

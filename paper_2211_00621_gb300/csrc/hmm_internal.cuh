@@ -20,7 +20,7 @@ accel_status order_by_length(const int64_t* d_off, int64_t S, int32_t* d_order, 
 // FP32 log-space forward (k_hmm_plain.cu).
 size_t plain_ws_bytes(int K, int M, int64_t S);
 accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const int64_t* off, int64_t S,
-                           double* loglik, char* ws, cudaStream_t st);
+                           double* loglik, char* ws, int32_t* d_status, cudaStream_t st);
 
 // BF16 tensor-core scaled forward (k_hmm_tc.cu).
 size_t tc_ws_bytes(int K, int M, int64_t S);

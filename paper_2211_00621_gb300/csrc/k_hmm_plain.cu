@@ -19,6 +19,7 @@
 //    column j from L2, reusing each element G times.
 #include "common.cuh"
 #include "hmm_internal.cuh"
+#include "simt_stream.cuh"
 
 namespace accel {
 namespace hmm {
@@ -116,19 +117,28 @@ k_plain_warp(const float* __restrict__ logA, const float* __restrict__ logB, con
 constexpr int kCtaThreads = 256;
 constexpr int kG = 8;
 
-__global__ void k_exp_f32(const float* __restrict__ in, float* __restrict__ out, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __expf(in[i]);
+// exp(log A) with row stride Kp (padding zero)
+__global__ void k_exp_f32(const float* __restrict__ in, float* __restrict__ out, int K, int Kp) {
+    int64_t n = (int64_t)K * Kp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int r = (int)(i / Kp), c = (int)(i % Kp);
+        out[i] = c < K ? __expf(in[(int64_t)r * K + c]) : 0.f;
+    }
 }
+
+__host__ __device__ inline size_t cta_off_b(int Kp) { return align_up(simt::stream_smem_bytes(Kp), 16); }
 
 __global__ void __launch_bounds__(kCtaThreads)
 k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, const float* __restrict__ logpi,
             int K, int M, const int32_t* __restrict__ obs, const int64_t* __restrict__ off, int64_t S,
-            const int32_t* __restrict__ order, double* __restrict__ loglik) {
-    extern __shared__ float smem[];
-    const int Kp = (K + 3) & ~3;                // padded row stride of sP (16-byte rows)
-    float* sB = smem;                           // [M][K]
-    float* sP = smem + (((size_t)M * K + 3) & ~(size_t)3);   // [kG][Kp], 16-byte aligned
+            const int32_t* __restrict__ order, double* __restrict__ loglik, int32_t* __restrict__ status) {
+    extern __shared__ __align__(16) float smem_f[];
+    char* smem = reinterpret_cast<char*>(smem_f);
+    const int Kp = (K + 3) & ~3;                // padded row stride (16-byte rows)
+    simt::AStream as;
+    simt::as_init(as, smem, K, Kp);
+    float* sB = reinterpret_cast<float*>(smem + cta_off_b(Kp));                        // [M][K]
+    float* sP = sB + (((size_t)M * K + 3) & ~(size_t)3);                               // [kG][Kp]
     __shared__ float s_red[kG][kCtaThreads / 32];
     __shared__ int64_t s_T[kG], s_o0[kG];
     const int j = threadIdx.x, lane = j & 31, w = j >> 5;
@@ -159,11 +169,14 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
         c[g] = 0.0;
         r[g] = (jv && T[g] > 0) ? logpi[j] + sB[obs[o0[g]] * K + j] : -INFINITY;
     }
+    simt::as_begin(as, Aexp);
     for (int64_t t = 1; t < Tmax; ++t) {
         // per-sequence maxima over states
         float m[kG];
+        bool act[kG];
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
+            act[g] = t < T[g];
             float v = r[g];
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
@@ -175,42 +188,29 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
             float v = s_red[g][0];
             for (int q = 1; q < kCtaThreads / 32; ++q) v = fmaxf(v, s_red[g][q]);
             m[g] = v;
-            if (jv) sP[g * Kp + j] = (t < T[g]) ? __expf(r[g] - v) : 0.f;
+            if (jv) sP[g * Kp + j] = act[g] ? __expf(r[g] - v) : 0.f;
         }
         __syncthreads();
         float acc[kG];
-#pragma unroll
-        for (int g = 0; g < kG; ++g) acc[g] = 0.f;
-        if (jv) {
-            const float* Ac = Aexp + j;
-            int i = 0;
-            for (; i + 4 <= K; i += 4) {
-                float a0 = __ldg(Ac + (int64_t)(i + 0) * K), a1 = __ldg(Ac + (int64_t)(i + 1) * K);
-                float a2 = __ldg(Ac + (int64_t)(i + 2) * K), a3 = __ldg(Ac + (int64_t)(i + 3) * K);
-#pragma unroll
-                for (int g = 0; g < kG; ++g) {
-                    float4 p = *reinterpret_cast<const float4*>(sP + g * Kp + i);
-                    acc[g] = fmaf(p.x, a0, acc[g]);
-                    acc[g] = fmaf(p.y, a1, acc[g]);
-                    acc[g] = fmaf(p.z, a2, acc[g]);
-                    acc[g] = fmaf(p.w, a3, acc[g]);
-                }
-            }
-            for (; i < K; ++i) {
-                float a0 = __ldg(Ac + (int64_t)i * K);
-#pragma unroll
-                for (int g = 0; g < kG; ++g) acc[g] = fmaf(sP[g * Kp + i], a0, acc[g]);
-            }
+        if (!simt::as_matvec<kG>(as, sP, Kp, act, acc)) {
+            if (threadIdx.x == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            simt::as_drain(as);
+            return;
         }
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
-            if (t < T[g]) {
+            if (act[g]) {
                 int32_t ob = obs[o0[g] + t];
                 r[g] = jv ? __logf(acc[g]) + sB[ob * K + j] : -INFINITY;
                 c[g] += (double)m[g];
             }
         }
         __syncthreads();   // sP and s_red reuse
+    }
+    if (!simt::as_end(as)) {
+        if (threadIdx.x == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+        simt::as_drain(as);
+        return;
     }
     // logL = c + LSE_j r
 #pragma unroll
@@ -248,11 +248,11 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
 size_t plain_ws_bytes(int K, int M, int64_t S) {
     (void)M;
     if (K <= 64) return 0;
-    return align_up((size_t)K * K * 4, 256) + order_ws_bytes(S);
+    return align_up((size_t)K * ((K + 3) & ~3) * 4, 256) + order_ws_bytes(S);
 }
 
 accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const int64_t* off, int64_t S,
-                           double* loglik, char* ws, cudaStream_t st) {
+                           double* loglik, char* ws, int32_t* d_status, cudaStream_t st) {
     const int K = m->K, M = m->M;
     if (K <= 64) {
         size_t smem = ((((size_t)M * K + 3) & ~(size_t)3) + 4 * 64) * sizeof(float);
@@ -267,17 +267,18 @@ accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const i
         }
         return after_launch(st, "hmm_forward(fp32 warp)", 1);
     }
-    size_t smem = ((((size_t)M * K + 3) & ~(size_t)3) + (size_t)kG * ((K + 3) & ~3)) * sizeof(float);
+    const int Kp = (K + 3) & ~3;
+    size_t smem = cta_off_b(Kp) + ((((size_t)M * K + 3) & ~(size_t)3) + (size_t)kG * Kp) * sizeof(float);
     ACCEL_REQUIRE(smem <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_forward: M*K too large for the FP32 kernel");
     float* Aexp = (float*)ws;
-    int32_t* order = (int32_t*)(ws + align_up((size_t)K * K * 4, 256));
+    int32_t* order = (int32_t*)(ws + align_up((size_t)K * Kp * 4, 256));
     char* order_scratch = (char*)order + align_up((size_t)S * 4, 256);
-    k_exp_f32<<<num_sms() * 2, 256, 0, st>>>(m->log_A, Aexp, (int64_t)K * K);
+    k_exp_f32<<<num_sms() * 2, 256, 0, st>>>(m->log_A, Aexp, K, Kp);
     accel_status r = order_by_length(off, S, order, order_scratch, st);
     if (r != ACCEL_OK) return r;
     ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_plain_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = (unsigned)((S + kG - 1) / kG);
-    k_plain_cta<<<grid, kCtaThreads, smem, st>>>(Aexp, m->log_B, m->log_pi, K, M, obs, off, S, order, loglik);
+    k_plain_cta<<<grid, kCtaThreads, smem, st>>>(Aexp, m->log_B, m->log_pi, K, M, obs, off, S, order, loglik, d_status);
     return after_launch(st, "hmm_forward(fp32 cta)", 5);
 }
 

@@ -49,6 +49,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// ---------------------------------------------------------------- bulk copies (1-D TMA)
+// The mbarrier's current phase completes when `bytes` more bytes have arrived (and its
+// arrival count is reached): arrive once and announce the expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned),
+// completing on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
 // Make this thread's generic-proxy shared-memory writes visible to the async proxy
 // (the tensor core reads its operands through it).
 __device__ __forceinline__ void fence_proxy_async_smem() {
