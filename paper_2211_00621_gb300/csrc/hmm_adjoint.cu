@@ -429,16 +429,17 @@ __global__ void __launch_bounds__(256) k_gemm_ptq(const float* __restrict__ P, c
 }
 
 // grad_log_A = A o sum_split U, grad_log_B = sum_groups counts, grad_log_pi = sum_groups pig
-__global__ void k_finish(const float* __restrict__ A, const float* __restrict__ Upart, const float* __restrict__ cnt,
-                         const float* __restrict__ pig, int K, int M, int64_t ngroups, float* __restrict__ gA,
-                         float* __restrict__ gB, float* __restrict__ gpi) {
+// (A has row stride Kp)
+__global__ void k_finish(const float* __restrict__ A, int Kp, const float* __restrict__ Upart,
+                         const float* __restrict__ cnt, const float* __restrict__ pig, int K, int M, int64_t ngroups,
+                         float* __restrict__ gA, float* __restrict__ gB, float* __restrict__ gpi) {
     int64_t nA = (int64_t)K * K, nB = (int64_t)K * M;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nA + nB + K;
          idx += (int64_t)gridDim.x * blockDim.x) {
         if (idx < nA) {
             float u = 0.f;
             for (int s = 0; s < kSplit; ++s) u += Upart[(int64_t)s * nA + idx];
-            gA[idx] = A[idx] * u;
+            gA[idx] = A[(idx / K) * Kp + idx % K] * u;
         } else if (idx < nA + nB) {
             int64_t q = idx - nA;
             float x = 0.f;
@@ -574,7 +575,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             nlaunch += 2;
         }
     }
-    adj::k_finish<<<pg, 256, 0, st>>>(p.A, Upart, p.cnt, p.pig, K, M, L.ngroups, d_grad_log_A, d_grad_log_B,
+    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, p.pig, K, M, L.ngroups, d_grad_log_A, d_grad_log_B,
                                       d_grad_log_pi);
     ++nlaunch;
     r = after_launch(st, "hmm_adjoint", nlaunch);
