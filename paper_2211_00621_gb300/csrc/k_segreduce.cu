@@ -32,14 +32,51 @@ template <typename Tin> constexpr int tile_elems() { return kTileBytes / (int)si
 
 __device__ __forceinline__ int swz(int v) { return v ^ ((v >> 3) & 7); }
 
-template <typename C> __device__ __forceinline__ C map_rt(int op, C x, C s) {
+// g(x) applied to a thread's items, with the operator switch outside the element loop.
+template <typename C, typename Tin, int IT>
+__device__ __forceinline__ void map_items(int op, const Tin* __restrict__ xs, C (&x)[IT], C s) {
     switch (op) {
-        case ACCEL_MAP_SQ_PLUS_ONE: return map_apply<ACCEL_MAP_SQ_PLUS_ONE, C>(x, C(0), s);
-        case ACCEL_MAP_NEG: return map_apply<ACCEL_MAP_NEG, C>(x, C(0), s);
-        case ACCEL_MAP_ABS: return map_apply<ACCEL_MAP_ABS, C>(x, C(0), s);
-        case ACCEL_MAP_SCALE: return map_apply<ACCEL_MAP_SCALE, C>(x, C(0), s);
-        default: return x;
+        case ACCEL_MAP_SQ_PLUS_ONE:
+#pragma unroll
+            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_SQ_PLUS_ONE, C>((C)xs[i], C(0), s);
+            break;
+        case ACCEL_MAP_NEG:
+#pragma unroll
+            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_NEG, C>((C)xs[i], C(0), s);
+            break;
+        case ACCEL_MAP_ABS:
+#pragma unroll
+            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_ABS, C>((C)xs[i], C(0), s);
+            break;
+        case ACCEL_MAP_SCALE:
+#pragma unroll
+            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_SCALE, C>((C)xs[i], C(0), s);
+            break;
+        default:
+#pragma unroll
+            for (int i = 0; i < IT; ++i) x[i] = (C)xs[i];
+            break;
     }
+}
+
+// Fold of the first n items (n <= IT) in item order (a pairwise tree when n == IT).
+template <int OP, typename C, int IT>
+__device__ __forceinline__ C fold_items(const C (&x)[IT], int n, C nel) {
+    if (n == IT) {
+        C t[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) t[i] = x[i];
+#pragma unroll
+        for (int w = 1; w < IT; w <<= 1)
+#pragma unroll
+            for (int i = 0; i + w < IT; i += 2 * w) t[i] = red_combine<OP, C>(t[i], t[i + w]);
+        return t[0];
+    }
+    C acc = nel;
+#pragma unroll
+    for (int i = 0; i < IT; ++i)
+        if (i < n) acc = red_combine<OP, C>(acc, x[i]);
+    return acc;
 }
 
 // key(s): last element of a non-empty segment, position of an empty one, clamped to N-1.
@@ -140,9 +177,7 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
         int4 raw[kVecPerThread];
 #pragma unroll
         for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
-        const Tin* xs = reinterpret_cast<const Tin*>(raw);
-#pragma unroll
-        for (int i = 0; i < IT; ++i) x[i] = map_rt<C>(map_op, (C)xs[i], sc);
+        map_items<C, Tin, IT>(map_op, reinterpret_cast<const Tin*>(raw), x, sc);
     }
 
     KV<C> tail;           // (key, partial) handed to the scan
@@ -163,6 +198,12 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
         for (int64_t q = s - 1; q >= lo_b && getoff(q) == k0 && getoff(q + 1) == k0; --q) out[q] = (Tout)nel;
         bool started_here = getoff(s) >= k0;
         int64_t nend = seg_end(s);
+        if (nend > k1) {
+            // no segment ends among this thread's items: one fold, all of it the tail
+            tail.k = s;
+            tail.v = fold_items<OP, C, IT>(x, (int)(k1 - k0), nel);
+            tail_open = true;
+        } else {
         C acc = nel;
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
@@ -192,6 +233,7 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
         // elements after the last boundary form this thread's tail partial of segment s
         tail.k = s;
         tail.v = acc;
+        }
     } else {
         tail.k = INT64_MAX;
         tail.v = nel;

@@ -52,7 +52,7 @@ def test_fp32_cta_variant(K, M):
     _check(p, acc.HMM_FP32_LOG)
 
 
-@pytest.mark.parametrize("K,M", [(256, 64), (128, 32), (64, 32), (32, 8)])
+@pytest.mark.parametrize("K,M", [(256, 64), (192, 48), (128, 32), (64, 8)])
 def test_bf16_tc_small(K, M):
     p = synth.hmm_workload(5, K, M, 300, "loguniform", 1, 300)
     _check(p, acc.HMM_BF16_SCALED)
@@ -81,6 +81,15 @@ def test_bf16_error_against_original_parameters_reported():
     idx = list(range(0, 256, 16))
     ref = ohmm.loglik_batch(p, seqs=idx)
     assert (np.abs(ll[idx] - ref) / np.abs(ref)).max() <= 1e-3
+
+
+def test_bf16_tc_rejects_unsupported_k():
+    from paper_2211_00621_gb300 import _lib
+    p = synth.hmm_workload(1, 32, 8, 4, "fixed", 5, 5)
+    logs, t, obs, off = _prep(p)
+    with pytest.raises(_lib.AccelError) as e:
+        api.hmm_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off, acc.HMM_BF16_SCALED)
+    assert e.value.status == 7
 
 
 def test_single_step_sequences():
