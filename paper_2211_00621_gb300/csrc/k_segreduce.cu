@@ -18,6 +18,8 @@
 //    fixup kernel that folds the preceding tiles' carry-outs in tile order.
 #include "common.cuh"
 
+#include <type_traits>
+
 namespace accel {
 namespace segred {
 
@@ -31,53 +33,6 @@ template <typename Tin> constexpr int items() { return kTileBytes / kThreads / (
 template <typename Tin> constexpr int tile_elems() { return kTileBytes / (int)sizeof(Tin); }
 
 __device__ __forceinline__ int swz(int v) { return v ^ ((v >> 3) & 7); }
-
-// g(x) applied to a thread's items, with the operator switch outside the element loop.
-template <typename C, typename Tin, int IT>
-__device__ __forceinline__ void map_items(int op, const Tin* __restrict__ xs, C (&x)[IT], C s) {
-    switch (op) {
-        case ACCEL_MAP_SQ_PLUS_ONE:
-#pragma unroll
-            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_SQ_PLUS_ONE, C>((C)xs[i], C(0), s);
-            break;
-        case ACCEL_MAP_NEG:
-#pragma unroll
-            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_NEG, C>((C)xs[i], C(0), s);
-            break;
-        case ACCEL_MAP_ABS:
-#pragma unroll
-            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_ABS, C>((C)xs[i], C(0), s);
-            break;
-        case ACCEL_MAP_SCALE:
-#pragma unroll
-            for (int i = 0; i < IT; ++i) x[i] = map_apply<ACCEL_MAP_SCALE, C>((C)xs[i], C(0), s);
-            break;
-        default:
-#pragma unroll
-            for (int i = 0; i < IT; ++i) x[i] = (C)xs[i];
-            break;
-    }
-}
-
-// Fold of the first n items (n <= IT) in item order (a pairwise tree when n == IT).
-template <int OP, typename C, int IT>
-__device__ __forceinline__ C fold_items(const C (&x)[IT], int n, C nel) {
-    if (n == IT) {
-        C t[IT];
-#pragma unroll
-        for (int i = 0; i < IT; ++i) t[i] = x[i];
-#pragma unroll
-        for (int w = 1; w < IT; w <<= 1)
-#pragma unroll
-            for (int i = 0; i + w < IT; i += 2 * w) t[i] = red_combine<OP, C>(t[i], t[i + w]);
-        return t[0];
-    }
-    C acc = nel;
-#pragma unroll
-    for (int i = 0; i < IT; ++i)
-        if (i < n) acc = red_combine<OP, C>(acc, x[i]);
-    return acc;
-}
 
 // key(s): last element of a non-empty segment, position of an empty one, clamped to N-1.
 __device__ __forceinline__ int64_t seg_key(const int64_t* __restrict__ off, int64_t s, int64_t N) {
@@ -101,7 +56,7 @@ __global__ void k_partition(const int64_t* __restrict__ off, int64_t S, int64_t 
     lo[b] = a;
 }
 
-template <typename C> struct KV { int64_t k; C v; };
+template <typename C> struct KV { int32_t k; C v; };
 
 template <int OP, typename C>
 __device__ __forceinline__ KV<C> seg_combine(KV<C> a, KV<C> b) {
@@ -114,6 +69,58 @@ __device__ __forceinline__ KV<C> seg_combine(KV<C> a, KV<C> b) {
 
 template <typename C> __device__ __forceinline__ C shfl_up_val(C v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 
+__device__ __forceinline__ int64_t sq_wide(int32_t x) { return (int64_t)x * (int64_t)x; }
+__device__ __forceinline__ uint64_t sq_wide(int64_t x) { return (uint64_t)x * (uint64_t)x; }
+template <typename T> __device__ __forceinline__ T sq_wide(T x) { return x * x; }
+
+// Fold of g(x) over the first n of a thread's IT raw items, in item order: the map
+// switch sits outside the (unrolled) element loop.  For an integer sum of x*x + 1 the
+// fold is sum(x*x) + n: one widening multiply-add per element, exact in int64.
+template <int OP, typename Tin, typename C, int IT>
+__device__ __forceinline__ C fused_fold(int map_op, const Tin* __restrict__ xs, int n, C sc, C nel) {
+    C acc = nel;
+    if constexpr (OP == ACCEL_RED_ADD && std::is_integral<C>::value) {
+        if (map_op == ACCEL_MAP_SQ_PLUS_ONE) {
+            // x*x of a 32-bit x is exact in 64 bits (a widening multiply); only the running
+            // sum wraps, so accumulate unsigned
+            uint64_t u = (uint64_t)acc;
+            if (n == IT) {
+#pragma unroll
+                for (int i = 0; i < IT; ++i) u += (uint64_t)sq_wide(xs[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < IT; ++i)
+                    if (i < n) u += (uint64_t)sq_wide(xs[i]);
+            }
+            return (C)(u + (uint64_t)n);
+        }
+    }
+    switch (map_op) {
+#define ACCEL_FOLD_CASE(MAPID)                                                                   \
+        case MAPID:                                                                              \
+            _Pragma("unroll") for (int i = 0; i < IT; ++i)                                      \
+                if (i < n) acc = red_combine<OP, C>(acc, map_apply<MAPID, C>((C)xs[i], C(0), sc)); \
+            break;
+        ACCEL_FOLD_CASE(ACCEL_MAP_SQ_PLUS_ONE)
+        ACCEL_FOLD_CASE(ACCEL_MAP_NEG)
+        ACCEL_FOLD_CASE(ACCEL_MAP_ABS)
+        ACCEL_FOLD_CASE(ACCEL_MAP_SCALE)
+        ACCEL_FOLD_CASE(ACCEL_MAP_IDENTITY)
+#undef ACCEL_FOLD_CASE
+    }
+    return acc;
+}
+
+template <typename C> __device__ __forceinline__ C map_one(int op, C x, C s) {
+    switch (op) {
+        case ACCEL_MAP_SQ_PLUS_ONE: return map_apply<ACCEL_MAP_SQ_PLUS_ONE, C>(x, C(0), s);
+        case ACCEL_MAP_NEG: return map_apply<ACCEL_MAP_NEG, C>(x, C(0), s);
+        case ACCEL_MAP_ABS: return map_apply<ACCEL_MAP_ABS, C>(x, C(0), s);
+        case ACCEL_MAP_SCALE: return map_apply<ACCEL_MAP_SCALE, C>(x, C(0), s);
+        default: return x;
+    }
+}
+
 template <typename Tin, typename Tout, int OP>
 __global__ void __launch_bounds__(kThreads)
 k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
@@ -122,21 +129,21 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
     using C = typename compute_of<Tout>::type;
     constexpr int IT = items<Tin>();
     constexpr int TE = tile_elems<Tin>();
+    constexpr int PV = 16 / (int)sizeof(Tin);     // elements per 16-byte vector
     __shared__ int4 s_data[kVecs];
-    __shared__ int64_t s_off[kOffCap];
+    __shared__ int32_t s_pos[kOffCap];              // offsets relative to the tile, clamped
     __shared__ KV<C> s_warp[kThreads / 32];
 
     const int t = threadIdx.x;
     const int64_t b = blockIdx.x;
     const int64_t e0 = b * TE;
-    const int64_t e1 = (e0 + TE < N) ? e0 + TE : N;
+    const int ne = (int)((e0 + TE < N) ? TE : N - e0);   // elements in this tile
     const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
     const C nel = red_neutral<C>(OP);
     const C sc = (C)scalar;
 
     // ---- stage the tile (16-byte vectors, coalesced) and the tile's offsets
-    const bool full = (e1 - e0) == TE;
-    if (full) {
+    if (ne == TE) {
         const int4* src = reinterpret_cast<const int4*>(data + e0);
 #pragma unroll
         for (int r = 0; r < kVecPerThread; ++r) {
@@ -145,131 +152,120 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
         }
     } else {
         Tin* sd = reinterpret_cast<Tin*>(s_data);
-        constexpr int per_vec = 16 / (int)sizeof(Tin);
-        for (int e = t; e < TE; e += kThreads) {
-            int v = e / per_vec, w = e % per_vec;
-            Tin x = (e0 + e < e1) ? data[e0 + e] : Tin(0);
-            sd[swz(v) * per_vec + w] = x;
-        }
+        for (int e = t; e < TE; e += kThreads) sd[swz(e / PV) * PV + e % PV] = e < ne ? data[e0 + e] : Tin(0);
     }
-    // offsets off[lo_b .. last] with last = min(hi_b + 1, S)
+    // positions off[lo_b .. last] - e0, clamped to [-1, TE + 1]; last = min(hi_b + 1, S)
     const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
     const int64_t cnt = last - lo_b + 1;
-    const bool off_in_smem = cnt <= kOffCap;
-    if (off_in_smem)
-        for (int64_t i = t; i < cnt; i += kThreads) s_off[i] = off[lo_b + i];
-    __syncthreads();
-
-    auto getoff = [&](int64_t s) -> int64_t {
-        return off_in_smem ? s_off[s - lo_b] : off[s];
+    const bool in_smem = cnt <= kOffCap;
+    auto clamp_rel = [&](int64_t x) -> int32_t {
+        int64_t r = x - e0;
+        return (int32_t)(r < -1 ? -1 : (r > TE + 1 ? TE + 1 : r));
     };
-    // end of segment s (exclusive); "infinite" for a segment past the cached range
-    auto seg_end = [&](int64_t s) -> int64_t { return (s + 1 <= last) ? getoff(s + 1) : INT64_MAX; };
+    if (in_smem)
+        for (int i = t; i < cnt; i += kThreads) s_pos[i] = clamp_rel(off[lo_b + i]);
+    __syncthreads();
+    // start of segment lo_b + q (relative index q), and its end; past the cached range: TE+1
+    auto rel = [&](int q) -> int32_t { return in_smem ? s_pos[q] : clamp_rel(off[lo_b + q]); };
+    const int qlast = (int)(last - lo_b);
+    auto rel_end = [&](int q) -> int32_t { return q + 1 <= qlast ? rel(q + 1) : TE + 1; };
 
-    // ---- this thread's elements [k0, k1)
-    const int64_t k0 = e0 + (int64_t)t * IT;
-    const int64_t k1r = k0 + IT;
-    const int64_t k1 = k1r < e1 ? k1r : e1;
-    const bool active = k0 < e1;
+    // ---- this thread's elements [r0, r1) relative to the tile
+    const int r0 = t * IT;
+    const int r1 = min(r0 + IT, ne);
+    const bool active = r0 < ne;
+    const int rN = (int)((N - e0 < (int64_t)TE + 2) ? N - e0 : (int64_t)TE + 2);   // position of N (the end of the data)
 
-    C x[IT];
-    {
-        int4 raw[kVecPerThread];
-#pragma unroll
-        for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
-        map_items<C, Tin, IT>(map_op, reinterpret_cast<const Tin*>(raw), x, sc);
-    }
-
-    KV<C> tail;           // (key, partial) handed to the scan
-    bool tail_open = false;  // elements accumulated after the last segment end
+    KV<C> tail;                 // (relative segment index, partial) handed to the scan
+    bool tail_open = false;     // elements accumulated after the last segment end
     bool has_head = false;
-    int64_t head_seg = 0;
+    int head_q = 0;
     C head_val = nel;
 
     if (active) {
-        // segment containing k0: largest s in [lo_b, hi_b] with off[s] <= k0
-        int64_t a = lo_b, z = hi_b;
+        // segment containing r0: largest q in [0, hi_b - lo_b] with rel(q) <= r0
+        int a = 0, z = (int)(hi_b - lo_b);
         while (a < z) {
-            int64_t mid = (a + z + 1) >> 1;
-            if (getoff(mid) <= k0) a = mid; else z = mid - 1;
+            int mid = (a + z + 1) >> 1;
+            if (rel(mid) <= r0) a = mid; else z = mid - 1;
         }
-        int64_t s = a;
-        // empty segments positioned at k0 precede s: they are owned here
-        for (int64_t q = s - 1; q >= lo_b && getoff(q) == k0 && getoff(q + 1) == k0; --q) out[q] = (Tout)nel;
-        bool started_here = getoff(s) >= k0;
-        int64_t nend = seg_end(s);
-        if (nend > k1) {
-            // no segment ends among this thread's items: one fold, all of it the tail
-            tail.k = s;
-            tail.v = fold_items<OP, C, IT>(x, (int)(k1 - k0), nel);
+        int q = a;
+        // empty segments positioned at r0 precede q: they are owned here
+        for (int p = q - 1; p >= 0 && rel(p) == r0 && rel(p + 1) == r0; --p) out[lo_b + p] = (Tout)nel;
+        int nend = rel_end(q);
+        if (nend > r1) {
+            // no segment ends among this thread's items: one fused map + fold
+            int4 raw[kVecPerThread];
+#pragma unroll
+            for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
+            tail.k = q;
+            tail.v = fused_fold<OP, Tin, C, IT>(map_op, reinterpret_cast<const Tin*>(raw), r1 - r0, sc, nel);
             tail_open = true;
         } else {
-        C acc = nel;
-#pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            int64_t k = k0 + i;
-            if (k < k1) {
-                acc = red_combine<OP, C>(acc, x[i]);
+            // general path: walk the items (read from shared memory), ending segments as met
+            const Tin* sd = reinterpret_cast<const Tin*>(s_data);
+            bool started_here = rel(q) >= r0;
+            C acc = nel;
+#pragma unroll 1
+            for (int k = r0; k < r1; ++k) {
+                acc = red_combine<OP, C>(acc, map_one<C>(map_op, (C)sd[swz(k / PV) * PV + k % PV], sc));
                 tail_open = true;
                 if (k == nend - 1) {
                     tail_open = false;
-                    if (started_here) out[s] = (Tout)acc;
-                    else { has_head = true; head_seg = s; head_val = acc; }
+                    if (started_here) out[lo_b + q] = (Tout)acc;
+                    else { has_head = true; head_q = q; head_val = acc; }
                     acc = nel;
                     started_here = true;
-                    ++s;
-                    // empty segments at position k+1 belong to this thread if k+1 < k1, or
-                    // if this is the end of the data (their key is clamped to N-1)
-                    while (s < S && (k + 1 < k1 || k + 1 == N)) {
-                        int64_t so = getoff(s), se = seg_end(s);
-                        if (!(so == k + 1 && se == k + 1)) break;
-                        out[s] = (Tout)nel;
-                        ++s;
+                    ++q;
+                    // empty segments at position k+1 belong here if k+1 < r1, or if k+1 is the
+                    // end of the data (their key is clamped to N-1)
+                    while (lo_b + q < S && (k + 1 < r1 || k + 1 == rN)) {
+                        if (!(rel(q) == k + 1 && rel_end(q) == k + 1)) break;
+                        out[lo_b + q] = (Tout)nel;
+                        ++q;
                     }
-                    nend = (s < S) ? seg_end(s) : INT64_MAX;
+                    nend = (lo_b + q < S) ? rel_end(q) : TE + 2;
                 }
             }
-        }
-        // elements after the last boundary form this thread's tail partial of segment s
-        tail.k = s;
-        tail.v = acc;
+            tail.k = q;
+            tail.v = acc;
         }
     } else {
-        tail.k = INT64_MAX;
+        tail.k = INT32_MAX;
         tail.v = nel;
     }
 
-    // ---- CTA-wide inclusive key-segmented scan of the tails
+    // ---- CTA-wide inclusive key-segmented scan of the tails (keys are relative indices)
     const int lane = t & 31, warp = t >> 5;
-    KV<C> q = tail;
+    KV<C> qv = tail;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         KV<C> o;
-        o.k = __shfl_up_sync(0xffffffffu, q.k, d);
-        o.v = shfl_up_val<C>(q.v, d);
-        if (lane >= d) q = seg_combine<OP, C>(o, q);
+        o.k = __shfl_up_sync(0xffffffffu, qv.k, d);
+        o.v = shfl_up_val<C>(qv.v, d);
+        if (lane >= d) qv = seg_combine<OP, C>(o, qv);
     }
-    if (lane == 31) s_warp[warp] = q;
+    if (lane == 31) s_warp[warp] = qv;
     __syncthreads();
     KV<C> wpre;  // fold of warps 0..warp-1
-    wpre.k = INT64_MIN;
+    wpre.k = INT32_MIN;
     wpre.v = nel;
     for (int w = 0; w < warp; ++w) wpre = (w == 0) ? s_warp[0] : seg_combine<OP, C>(wpre, s_warp[w]);
-    if (warp > 0) q = seg_combine<OP, C>(wpre, q);
+    if (warp > 0) qv = seg_combine<OP, C>(wpre, qv);
     // exclusive value for this thread = inclusive value of thread t-1
     KV<C> ex;
-    ex.k = __shfl_up_sync(0xffffffffu, q.k, 1);
-    ex.v = shfl_up_val<C>(q.v, 1);
+    ex.k = __shfl_up_sync(0xffffffffu, qv.k, 1);
+    ex.v = shfl_up_val<C>(qv.v, 1);
     if (lane == 0) ex = wpre;
 
     if (has_head) {
-        C carry = (t > 0 && ex.k == head_seg) ? ex.v : nel;
-        out[head_seg] = (Tout)red_combine<OP, C>(carry, head_val);
+        C carry = (t > 0 && ex.k == head_q) ? ex.v : nel;
+        out[lo_b + head_q] = (Tout)red_combine<OP, C>(carry, head_val);
     }
     // tile carry-out: the last active thread
-    const int t_last = (int)((e1 - e0 - 1) / IT);
+    const int t_last = (ne - 1) / IT;
     if (t == t_last) {
-        if (tail_open) { tail_seg[b] = tail.k; tail_val[b] = q.v; }
+        if (tail_open) { tail_seg[b] = lo_b + tail.k; tail_val[b] = qv.v; }
         else tail_seg[b] = -1;
     }
 }
