@@ -270,6 +270,115 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
     }
 }
 
+// Integer sums: a branch-free variant.  The tile's mapped values are prefix-summed across
+// the CTA (each thread scans its 16 items, a CTA-wide scan adds the thread offsets) into
+// shared memory, and every owned segment's sum is P[end-1] - P[start-1].  Wrapping 64-bit
+// addition forms a group, so the differences are exact whatever the magnitudes.  Every
+// thread does the same work whatever the segment lengths, so no warp pays for a boundary
+// walk.  The tile's open segment (if the tile's last element does not end a segment) is
+// handed to the fixup kernel as before.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kThreads)
+k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
+         const int64_t* __restrict__ lo_arr, int map_op, double scalar, Tout* __restrict__ out,
+         int64_t* __restrict__ tail_seg, int64_t* __restrict__ tail_val) {
+    constexpr int IT = items<Tin>();
+    constexpr int TE = tile_elems<Tin>();
+    constexpr int PV = 16 / (int)sizeof(Tin);
+    // the staged tile and, once every thread holds its items, the prefix sums share storage
+    __shared__ __align__(16) uint64_t s_buf[TE];
+    int4* s_data = reinterpret_cast<int4*>(s_buf);  // kVecs 16-byte vectors (16 KB)
+    uint64_t* s_P = s_buf;                          // inclusive prefix of the mapped values
+    __shared__ int32_t s_pos[kOffCap];
+    __shared__ uint64_t s_wtot[kThreads / 32];
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t b = blockIdx.x;
+    const int64_t e0 = b * TE;
+    const int ne = (int)((e0 + TE < N) ? TE : N - e0);
+    const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
+    const int64_t sc = (int64_t)scalar;
+
+    if (ne == TE) {
+        const int4* src = reinterpret_cast<const int4*>(data + e0);
+#pragma unroll
+        for (int r = 0; r < kVecPerThread; ++r) {
+            int v = r * kThreads + t;
+            s_data[swz(v)] = __ldg(src + v);
+        }
+    } else {
+        Tin* sd = reinterpret_cast<Tin*>(s_data);
+        for (int e = t; e < TE; e += kThreads) sd[swz(e / PV) * PV + e % PV] = e < ne ? data[e0 + e] : Tin(0);
+    }
+    const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
+    const int64_t cnt = last - lo_b + 1;
+    const bool in_smem = cnt <= kOffCap;
+    auto clamp_rel = [&](int64_t x) -> int32_t {
+        int64_t r = x - e0;
+        return (int32_t)(r < -1 ? -1 : (r > TE + 1 ? TE + 1 : r));
+    };
+    if (in_smem)
+        for (int i = t; i < cnt; i += kThreads) s_pos[i] = clamp_rel(off[lo_b + i]);
+    __syncthreads();
+    auto rel = [&](int64_t q) -> int32_t { return in_smem ? s_pos[q] : clamp_rel(off[lo_b + q]); };
+
+    // ---- per-thread inclusive scan of g(x) over its items (items past ne add nothing)
+    const int r0 = t * IT;
+    const int n = max(0, min(IT, ne - r0));
+    int4 raw[kVecPerThread];
+#pragma unroll
+    for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
+    const Tin* xs = reinterpret_cast<const Tin*>(raw);
+    // g(x) of item i (0 past ne), with the map switch outside the unrolled loops
+    uint64_t run = 0;
+#define ACCEL_MAP_SWITCH(BODY)                                                                   \
+    switch (map_op) {                                                                            \
+        case ACCEL_MAP_SQ_PLUS_ONE: { auto g = [&](int64_t x) { return (uint64_t)x * (uint64_t)x + 1ull; }; BODY } break; \
+        case ACCEL_MAP_NEG: { auto g = [&](int64_t x) { return 0ull - (uint64_t)x; }; BODY } break;                     \
+        case ACCEL_MAP_ABS: { auto g = [&](int64_t x) { return x < 0 ? 0ull - (uint64_t)x : (uint64_t)x; }; BODY } break; \
+        case ACCEL_MAP_SCALE: { auto g = [&](int64_t x) { return (uint64_t)sc * (uint64_t)x; }; BODY } break;          \
+        default: { auto g = [&](int64_t x) { return (uint64_t)x; }; BODY } break;                                      \
+    }
+    ACCEL_MAP_SWITCH(
+        _Pragma("unroll") for (int i = 0; i < IT; ++i) run += (i < n) ? g((int64_t)xs[i]) : 0ull;)
+    // ---- CTA-wide exclusive scan of the thread totals
+    uint64_t inc = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) s_wtot[warp] = inc;
+    __syncthreads();   // also: every thread has read its items from the staging buffer
+    uint64_t acc = inc - run;
+    for (int w = 0; w < warp; ++w) acc += s_wtot[w];
+    ACCEL_MAP_SWITCH(
+        _Pragma("unroll") for (int i = 0; i < IT; ++i) {
+            if (i < n) { acc += g((int64_t)xs[i]); s_P[r0 + i] = acc; }
+        })
+#undef ACCEL_MAP_SWITCH
+    __syncthreads();
+
+    // ---- owned segments: sum over [max(start,0), end) = P[end-1] - P[start-1]
+    const int64_t nown = hi_b - lo_b;
+    for (int64_t q = t; q < nown; q += kThreads) {
+        const int a = rel(q), e = rel(q + 1);
+        const uint64_t hi = e > 0 ? s_P[e - 1] : 0ull;
+        const uint64_t lo = a > 0 ? s_P[a - 1] : 0ull;
+        out[lo_b + q] = (Tout)(int64_t)(hi - lo);
+    }
+    // ---- the tile's open segment: segment hi_b if it starts at or before the last element
+    if (t == 0) {
+        const int a = (hi_b < S) ? rel(nown) : TE + 1;
+        if (a <= ne - 1) {
+            tail_seg[b] = hi_b;
+            tail_val[b] = (int64_t)(s_P[ne - 1] - (a > 0 ? s_P[a - 1] : 0ull));
+        } else {
+            tail_seg[b] = -1;
+        }
+    }
+}
+
 // Folds the carry-outs of the tiles preceding b into the first segment b owns, when that
 // segment started in an earlier tile.  Tile order is kept, so float results are
 // deterministic.
@@ -333,6 +442,15 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
     }
     int64_t te = tile_elems<Tin>();
     k_partition<<<(unsigned)((L.ntiles + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);
+    if constexpr (std::is_integral<C>::value) {
+        if (op == ACCEL_RED_ADD) {
+            k_segsum<Tin, Tout><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
+                (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, (int64_t*)tval);
+            k_fixup<Tout, ACCEL_RED_ADD><<<(unsigned)((L.ntiles + 255) / 256), 256, 0, st>>>(d_off, lo, L.ntiles, te,
+                                                                                            tseg, tval, out);
+            return after_launch(st, "accel_segreduce", 3);
+        }
+    }
     ACCEL_DISPATCH_RED(op, OPC, {
         k_segreduce<Tin, Tout, OPC><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
             (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, tval);
