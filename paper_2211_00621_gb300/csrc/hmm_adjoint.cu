@@ -29,6 +29,7 @@
 #include "hmm_internal.cuh"
 #include "simt_stream.cuh"
 
+#include <cooperative_groups.h>
 #include <math.h>
 
 namespace accel {
@@ -63,6 +64,7 @@ struct Prm {
     int32_t* status;    // device status word (ACCEL_ERR_SHAPE / ACCEL_ERR_TIMEOUT)
     int Kp;             // padded row stride (multiple of 4) of A, At and the shared vectors
     int32_t* rows;      // per round: rows of P/Q that may be non-zero (sorted-position order)
+    int32_t* ebuf;      // exponents e_t of the P rows [S][Cmax] (cluster path)
 };
 
 __host__ __device__ __forceinline__ int seg_len(int64_t T) {
@@ -454,8 +456,477 @@ __global__ void k_finish(const float* __restrict__ A, int Kp, const float* __res
     }
 }
 
+
+// ============================================================================================
+// Cluster-pair path (K a multiple of 64): the matrix the step multiplies by stays resident in
+// shared memory in FP32.  A pair of CTAs (a thread-block cluster of 2) owns 16 sequences;
+// CTA r holds the K x K/2 column half r of the matrix and computes output states
+// [r K/2, (r+1) K/2) of every sequence.  After each step the two CTAs write their halves
+// of the new vectors, and their partial row sums, into both CTAs' shared memory through
+// distributed shared memory, then meet at one cluster barrier.  Vectors and partial sums are
+// double-buffered by step parity, so a CTA never overwrites what its peer may still read.
+// ============================================================================================
+namespace clu {
+namespace cg = cooperative_groups;
+
+constexpr int kG = 16;      // sequences per cluster
+constexpr int kT = 256;     // threads per CTA
+
+struct SL { size_t ah, bth, sx, spart, sr, csum, red, total; };
+
+__host__ __device__ inline SL smem_layout(int K, int M) {
+    const int Kh = K / 2;
+    SL L;
+    size_t o = 0;
+    L.ah = o;    o += (size_t)K * Kh * 4;                 // matrix column half [K][Kh]
+    L.bth = o;   o += (size_t)M * Kh * 4;                 // emission column half [M][Kh]
+    L.sx = o;    o += (size_t)2 * kG * K * 4;             // full vectors, two step parities
+    L.spart = o; o += (size_t)(kT - Kh) * kG * 4;         // partial matvec results to combine
+    L.sr = o;    o += (size_t)kG * Kh * 4;                // R (backward), own half
+    L.csum = o;  o += (size_t)2 * 2 * kG * 4;             // [parity][rank][g] partial row sums
+    L.red = o;   o += (size_t)8 * kG * 4;                 // per-warp partial sums
+    L.total = o;
+    return L;
+}
+
+struct CGroup {
+    int64_t seq[kG], T[kG], o0[kG];
+    int C[kG];
+};
+
+__device__ void load_cgroup(const Prm& p, CGroup& gi, int64_t cidx) {
+    for (int g = 0; g < kG; ++g) {
+        int64_t q = cidx * kG + g;
+        int64_t sq = q < p.S ? p.order[q] : -1;
+        gi.seq[g] = sq;
+        gi.T[g] = sq >= 0 ? p.off[sq + 1] - p.off[sq] : 0;
+        gi.o0[g] = sq >= 0 ? p.off[sq] : 0;
+        gi.C[g] = sq >= 0 ? seg_len(gi.T[g]) : 1;
+        if (sq >= 0 && gi.C[g] > p.Cmax) {
+            if (threadIdx.x == 0) atomicExch(p.status, ACCEL_ERR_SHAPE);
+            gi.seq[g] = -1;
+            gi.T[g] = 0;
+            gi.C[g] = 1;
+        }
+    }
+}
+
+// columns [r Kh, (r+1) Kh) of a K x K matrix stored with row stride Kp, into [K][Kh]
+__device__ void load_col_half(const float* __restrict__ src, int K, int Kp, int Kh, int r, float* dst) {
+    for (int idx = threadIdx.x; idx < K * Kh; idx += kT) {
+        int i = idx / Kh, jl = idx - i * Kh;
+        dst[idx] = src[(int64_t)i * Kp + r * Kh + jl];
+    }
+}
+
+// Warp reduce-scatter of 16 values: afterwards v[0] of lane l holds the warp's total of
+// value (l & 15).
+__device__ __forceinline__ float warp_sum16(float (&v)[kG]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 8; k >= 1; k >>= 1) {
+        const bool up = (lane & k) != 0;
+#pragma unroll
+        for (int i = 0; i < k; ++i) {
+            float send = up ? v[i] : v[i + k];
+            float keep = up ? v[i + k] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// acc_g = sum over this thread's i-part of X[g][i] * Ah[i][jl]; then the i-parts are
+// combined in the epilogue threads (ih == 0) in a fixed order.  Ends with a CTA barrier.
+__device__ __forceinline__ void cl_matvec(const float* __restrict__ Ah, const float* __restrict__ X, int K, int Kh,
+                                          float* spart, const bool (&act)[kG], float (&acc)[kG]) {
+    const int tid = threadIdx.x, jl = tid % Kh, ih = tid / Kh;
+    const int nih = kT / Kh, ipart = K / nih;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) acc[g] = 0.f;
+    const int i0 = ih * ipart;
+    for (int i = i0; i < i0 + ipart; i += 4) {
+        const float a0 = Ah[(i + 0) * Kh + jl], a1 = Ah[(i + 1) * Kh + jl];
+        const float a2 = Ah[(i + 2) * Kh + jl], a3 = Ah[(i + 3) * Kh + jl];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (!act[g]) continue;
+            const float4 x = *reinterpret_cast<const float4*>(X + g * K + i);
+            acc[g] = fmaf(x.x, a0, acc[g]);
+            acc[g] = fmaf(x.y, a1, acc[g]);
+            acc[g] = fmaf(x.z, a2, acc[g]);
+            acc[g] = fmaf(x.w, a3, acc[g]);
+        }
+    }
+    if (ih > 0) {
+#pragma unroll
+        for (int g = 0; g < kG; ++g) spart[((ih - 1) * kG + g) * Kh + jl] = acc[g];
+    }
+    __syncthreads();
+    if (ih == 0) {
+        for (int q = 1; q < nih; ++q)
+#pragma unroll
+            for (int g = 0; g < kG; ++g) acc[g] += spart[((q - 1) * kG + g) * Kh + jl];
+    }
+}
+
+// Sum over the epilogue threads (ih == 0, warps 0 .. Kh/32-1) of v[g]; thread g < 16 of the
+// CTA gets the CTA total of sequence g (others: unspecified).  Contains a CTA barrier.
+__device__ __forceinline__ float cta_sum16(float (&v)[kG], float* sred, int Kh) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int nwe = Kh / 32;
+    if (w < nwe) {
+        float t = warp_sum16(v);
+        if (lane < kG) sred[w * kG + lane] = t;
+    }
+    __syncthreads();
+    float tot = 0.f;
+    if (tid < kG)
+        for (int q = 0; q < nwe; ++q) tot += sred[q * kG + tid];
+    return tot;
+}
+
+// ---------------------------------------------------------------- forward + checkpoints
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm p) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank(), peer = r ^ 1;
+    const int64_t cidx = blockIdx.x >> 1;
+    const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
+    const bool epi = tid < Kh;
+    extern __shared__ __align__(16) char smem[];
+    const SL Ls = smem_layout(K, M);
+    float* Ah = reinterpret_cast<float*>(smem + Ls.ah);
+    float* BTh = reinterpret_cast<float*>(smem + Ls.bth);
+    float* sX = reinterpret_cast<float*>(smem + Ls.sx);
+    float* spart = reinterpret_cast<float*>(smem + Ls.spart);
+    float* csum = reinterpret_cast<float*>(smem + Ls.csum);
+    float* sred = reinterpret_cast<float*>(smem + Ls.red);
+    float* sX_peer = cl.map_shared_rank(sX, peer);
+    float* csum_peer = cl.map_shared_rank(csum, peer);
+    load_col_half(p.A, K, p.Kp, Kh, r, Ah);
+    for (int idx = tid; idx < M * Kh; idx += kT) {
+        int k = idx / Kh, c = idx - k * Kh;
+        BTh[idx] = p.BT[(int64_t)k * K + r * Kh + c];
+    }
+    CGroup gi;
+    load_cgroup(p, gi, cidx);
+    int64_t Tmax = 0;
+    for (int g = 0; g < kG; ++g) Tmax = gi.T[g] > Tmax ? gi.T[g] : Tmax;
+    const int j = r * Kh + jl;            // this thread's state (epilogue threads)
+    bool act[kG];
+    int e[kG];
+    int64_t E[kG];
+    float v[kG];
+    cl.sync();                            // peer's shared memory is ready before any remote write
+    // t = 0: alpha~_0 = pi o b(o_0)
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        act[g] = gi.T[g] > 0;
+        float a0 = 0.f;
+        if (act[g] && epi) a0 = p.pi[j] * BTh[p.obs[gi.o0[g]] * Kh + jl];
+        if (epi) { sX[g * K + j] = a0; sX_peer[g * K + j] = a0; }
+        v[g] = a0;
+    }
+    {
+        float tot = cta_sum16(v, sred, Kh);
+        if (tid < kG) { csum[(0 * 2 + r) * kG + tid] = tot; csum_peer[(0 * 2 + r) * kG + tid] = tot; }
+    }
+    cl.sync();
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        const float c = csum[(0 * 2 + 0) * kG + g] + csum[(0 * 2 + 1) * kG + g];
+        int ex = 0;
+        frexpf(c, &ex);
+        e[g] = ex;
+        E[g] = ex;
+        if (!act[g]) continue;
+        const int64_t sq = gi.seq[g];
+        if (epi) p.cp[(sq * p.Cmax) * K + j] = sX[g * K + j] * ldexpf(1.0f, -ex);
+        if (r == 0 && tid == g) {
+            p.cp_e[sq * p.Cmax] = ex;
+            if (gi.T[g] == 1) {
+                p.clast[sq] = c;
+                if (p.loglik) p.loglik[sq] = log((double)c);
+            }
+        }
+    }
+    for (int64_t t = 1; t < Tmax; ++t) {
+        const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
+#pragma unroll
+        for (int g = 0; g < kG; ++g) act[g] = t < gi.T[g];
+        float acc[kG];
+        cl_matvec(Ah, sX + cur * kG * K, K, Kh, spart, act, acc);
+        if (epi) {
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                float a = 0.f;
+                if (act[g]) a = acc[g] * ldexpf(1.0f, -e[g]) * BTh[p.obs[gi.o0[g] + t] * Kh + jl];
+                sX[(nxt * kG + g) * K + j] = a;
+                sX_peer[(nxt * kG + g) * K + j] = a;
+                v[g] = a;
+            }
+        }
+        {
+            float tot = cta_sum16(v, sred, Kh);
+            if (tid < kG) {
+                csum[(nxt * 2 + r) * kG + tid] = tot;
+                csum_peer[(nxt * 2 + r) * kG + tid] = tot;
+            }
+        }
+        cl.sync();
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (!act[g]) continue;
+            const float c = csum[(nxt * 2 + 0) * kG + g] + csum[(nxt * 2 + 1) * kG + g];
+            int ex = 0;
+            frexpf(c, &ex);
+            const int64_t sq = gi.seq[g];
+            if (r == 0 && tid == g && t == gi.T[g] - 1) {
+                p.clast[sq] = c;
+                if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E[g] + log((double)c);
+            }
+            E[g] += ex;
+            e[g] = ex;
+            if (t % gi.C[g] == 0) {
+                const int64_t k = t / gi.C[g];
+                if (epi) p.cp[(sq * p.Cmax + k) * K + j] = sX[(nxt * kG + g) * K + j] * ldexpf(1.0f, -ex);
+                if (r == 0 && tid == g) p.cp_e[sq * p.Cmax + k] = ex;
+            }
+        }
+    }
+    cl.sync();   // no CTA leaves while its peer may still write into its shared memory
+}
+
+// Segment bounds of round `r` for the sequences of a cluster's group.
+__device__ void round_bounds(const CGroup& gi, int r, int64_t (&t0)[kG], int64_t (&L)[kG], bool (&just_done)[kG],
+                             int& maxL) {
+    maxL = 0;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        t0[g] = 0;
+        L[g] = 0;
+        just_done[g] = false;
+        if (gi.seq[g] < 0) continue;
+        const int64_t n = (gi.T[g] + gi.C[g] - 1) / gi.C[g];
+        const int64_t k = n - 1 - r;
+        just_done[g] = k == -1;
+        if (k < 0) continue;
+        t0[g] = k * gi.C[g];
+        const int64_t t1 = t0[g] + gi.C[g] < gi.T[g] ? t0[g] + gi.C[g] : gi.T[g];
+        L[g] = t1 - t0[g];
+        maxL = L[g] > maxL ? (int)L[g] : maxL;
+    }
+}
+
+// ---------------------------------------------------------------- recompute a segment
+// S_t for t in the round's segment into the P rows (normalised), e_t into ebuf.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm p, int round) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank(), peer = r ^ 1;
+    const int64_t cidx = blockIdx.x >> 1;
+    const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
+    const bool epi = tid < Kh;
+    extern __shared__ __align__(16) char smem[];
+    const SL Ls = smem_layout(K, M);
+    float* Ah = reinterpret_cast<float*>(smem + Ls.ah);
+    float* BTh = reinterpret_cast<float*>(smem + Ls.bth);
+    float* sX = reinterpret_cast<float*>(smem + Ls.sx);
+    float* spart = reinterpret_cast<float*>(smem + Ls.spart);
+    float* csum = reinterpret_cast<float*>(smem + Ls.csum);
+    float* sred = reinterpret_cast<float*>(smem + Ls.red);
+    float* sX_peer = cl.map_shared_rank(sX, peer);
+    float* csum_peer = cl.map_shared_rank(csum, peer);
+    CGroup gi;
+    load_cgroup(p, gi, cidx);
+    int64_t t0[kG], L[kG];
+    bool just_done[kG];
+    int maxL;
+    round_bounds(gi, round, t0, L, just_done, maxL);
+    if (maxL <= 1) {
+        // only the checkpoint row itself: copy it
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (L[g] == 0) continue;
+            const int64_t sq = gi.seq[g], base = sq * p.Cmax, k = t0[g] / gi.C[g];
+            const int64_t row = (cidx * kG + g) * p.Cmax;
+            if (epi) p.P[row * K + r * Kh + jl] = p.cp[(base + k) * K + r * Kh + jl];
+            if (r == 0 && tid == g) p.ebuf[row] = p.cp_e[base + k];
+        }
+        return;   // no remote access was made: leaving early is safe for both CTAs
+    }
+    load_col_half(p.A, K, p.Kp, Kh, r, Ah);
+    for (int idx = tid; idx < M * Kh; idx += kT) {
+        int k = idx / Kh, c = idx - k * Kh;
+        BTh[idx] = p.BT[(int64_t)k * K + r * Kh + c];
+    }
+    const int j = r * Kh + jl;
+    bool act[kG];
+    int e[kG];
+    float v[kG];
+    // tt = 0: the checkpoint S_{t0} (normalised) plays alpha~ with exponent 0
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        act[g] = L[g] > 0;
+        e[g] = 0;
+        if (!act[g]) continue;
+        const int64_t sq = gi.seq[g], base = sq * p.Cmax, k = t0[g] / gi.C[g];
+        const int64_t row = (cidx * kG + g) * p.Cmax;
+        if (epi) {
+            const float sv = p.cp[(base + k) * K + j];
+            sX[g * K + j] = sv;
+            p.P[row * K + j] = sv;
+        }
+        if (r == 0 && tid == g) p.ebuf[row] = p.cp_e[base + k];
+    }
+    __syncthreads();
+    // the peer's half of the checkpoint row: read it from the checkpoint directly
+    for (int idx = tid; idx < kG * Kh; idx += kT) {
+        const int g = idx / Kh, c = idx - g * Kh;
+        if (L[g] == 0) continue;
+        const int64_t base = gi.seq[g] * p.Cmax, k = t0[g] / gi.C[g];
+        sX[g * K + peer * Kh + c] = p.cp[(base + k) * K + peer * Kh + c];
+    }
+    cl.sync();
+    for (int tt = 1; tt < maxL; ++tt) {
+        const int cur = (tt - 1) & 1, nxt = tt & 1;
+#pragma unroll
+        for (int g = 0; g < kG; ++g) act[g] = tt < L[g];
+        float acc[kG];
+        cl_matvec(Ah, sX + cur * kG * K, K, Kh, spart, act, acc);
+        if (epi) {
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                float a = 0.f;
+                if (act[g]) a = acc[g] * ldexpf(1.0f, -e[g]) * BTh[p.obs[gi.o0[g] + t0[g] + tt] * Kh + jl];
+                sX[(nxt * kG + g) * K + j] = a;
+                sX_peer[(nxt * kG + g) * K + j] = a;
+                v[g] = a;
+            }
+        }
+        {
+            float tot = cta_sum16(v, sred, Kh);
+            if (tid < kG) {
+                csum[(nxt * 2 + r) * kG + tid] = tot;
+                csum_peer[(nxt * 2 + r) * kG + tid] = tot;
+            }
+        }
+        cl.sync();
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if (!act[g]) continue;
+            const float c = csum[(nxt * 2 + 0) * kG + g] + csum[(nxt * 2 + 1) * kG + g];
+            int ex = 0;
+            frexpf(c, &ex);
+            e[g] = ex;
+            const int64_t row = (cidx * kG + g) * p.Cmax + tt;
+            if (epi) p.P[row * K + j] = sX[(nxt * kG + g) * K + j] * ldexpf(1.0f, -ex);
+            if (r == 0 && tid == g) p.ebuf[row] = ex;
+        }
+    }
+    cl.sync();
+}
+
+// ---------------------------------------------------------------- backward over a segment
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm p, int round) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank(), peer = r ^ 1;
+    const int64_t cidx = blockIdx.x >> 1;
+    const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
+    const bool epi = tid < Kh;
+    extern __shared__ __align__(16) char smem[];
+    const SL Ls = smem_layout(K, M);
+    float* Ah = reinterpret_cast<float*>(smem + Ls.ah);
+    float* BTh = reinterpret_cast<float*>(smem + Ls.bth);
+    float* sV = reinterpret_cast<float*>(smem + Ls.sx);
+    float* spart = reinterpret_cast<float*>(smem + Ls.spart);
+    float* sR = reinterpret_cast<float*>(smem + Ls.sr);
+    float* sV_peer = cl.map_shared_rank(sV, peer);
+    CGroup gi;
+    load_cgroup(p, gi, cidx);
+    int64_t t0[kG], L[kG];
+    bool just_done[kG];
+    int maxL;
+    round_bounds(gi, round, t0, L, just_done, maxL);
+    const int i = r * Kh + jl;            // this thread's state (epilogue threads)
+    float wgt[kG];
+    int64_t rowbase[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        rowbase[g] = (cidx * kG + g) * p.Cmax;
+        wgt[g] = (gi.seq[g] >= 0 && p.w) ? (float)p.w[gi.seq[g]] : 1.0f;
+        if (L[g] > 0 && r == 0 && tid == 0) atomicMax(&p.rows[round], (int32_t)(rowbase[g] + p.Cmax));
+    }
+    // rows that must read as zero (own half): the sequence's last segment was done in the
+    // previous round, or past the segment length of an active sequence
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        if (gi.seq[g] < 0 || !(just_done[g] || L[g] > 0)) continue;
+        for (int64_t tt = L[g]; tt < p.Cmax; ++tt)
+            if (epi) p.Q[(rowbase[g] + tt) * K + i] = 0.f;
+    }
+    if (maxL == 0) return;   // no remote access was made
+    load_col_half(p.At, K, p.Kp, Kh, r, Ah);
+    for (int idx = tid; idx < M * Kh; idx += kT) {
+        int k = idx / Kh, c = idx - k * Kh;
+        BTh[idx] = p.BT[(int64_t)k * K + r * Kh + c];
+    }
+    // R_{t1} from the previous round (own half); zero where this round holds T-1
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        if (L[g] == 0 || !epi) continue;
+        const bool last_seg = t0[g] + L[g] == gi.T[g];
+        sR[g * Kh + jl] = last_seg ? 0.f : p.Rc[gi.seq[g] * K + i];
+    }
+    float* cnt = p.cnt + cidx * (int64_t)K * M;
+    cl.sync();
+    for (int tt = maxL - 1; tt >= 0; --tt) {
+        const int buf = tt & 1;
+        bool act[kG], trans[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            act[g] = tt < L[g];
+            const int64_t t = t0[g] + tt;
+            trans[g] = act[g] && t < gi.T[g] - 1;
+        }
+        if (epi) {
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                float vv = 0.f;
+                if (trans[g]) vv = BTh[p.obs[gi.o0[g] + t0[g] + tt + 1] * Kh + jl] * sR[g * Kh + jl];
+                sV[(buf * kG + g) * K + i] = vv;
+                sV_peer[(buf * kG + g) * K + i] = vv;
+                if (act[g]) p.Q[(rowbase[g] + tt) * K + i] = wgt[g] * vv;
+            }
+        }
+        cl.sync();
+        float acc[kG];
+        cl_matvec(Ah, sV + buf * kG * K, K, Kh, spart, trans, acc);
+        if (epi) {
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                if (!act[g]) continue;
+                const int64_t t = t0[g] + tt;
+                const int64_t row = rowbase[g] + tt;
+                const int et = p.ebuf[row];
+                const float Rt = trans[g] ? acc[g] * ldexpf(1.0f, -et) : 1.0f / p.clast[gi.seq[g]];
+                const float St = p.P[row * K + i];
+                const float gam = wgt[g] * St * Rt * ldexpf(1.0f, et);
+                cnt[(int64_t)i * M + p.obs[gi.o0[g] + t]] += gam;
+                if (t == 0) p.pig[cidx * K + i] += gam;
+                sR[g * Kh + jl] = Rt;
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < kG; ++g)
+        if (L[g] > 0 && epi) p.Rc[gi.seq[g] * K + i] = sR[g * Kh + jl];
+    cl.sync();
+}
+
+}  // namespace clu
+
 struct Layout {
-    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, order, total;
+    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, order, total;
     int Cmax;
     int64_t ngroups;
 };
@@ -481,6 +952,7 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.pig = take((size_t)L.ngroups * K * 4);
     L.Upart = take((size_t)kSplit * K * K * 4);
     L.rows = take((size_t)L.Cmax * 4);
+    L.ebuf = take((size_t)S * L.Cmax * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
     return L;
@@ -542,6 +1014,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     p.K = K; p.M = M; p.Cmax = L.Cmax; p.S = S; p.Kp = adj::padK(K);
     p.status = (int32_t*)(ws + kStatusOff);
     p.rows = (int32_t*)(ws + L.rows);
+    p.ebuf = (int32_t*)(ws + L.ebuf);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
     p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = d_weights;
     p.cp = (float*)(ws + L.cp); p.cp_e = (int32_t*)(ws + L.cp_e); p.clast = (float*)(ws + L.clast);
@@ -563,16 +1036,33 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
         r = order_by_length(d_offsets, S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)S * 4, 256), st);
         if (r != ACCEL_OK) return r;
         nlaunch += 3;
-        size_t sm_f = adj::smem_fwd(K, M);
-        ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_forward_cp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f));
-        ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
-        adj::k_forward_cp<<<(unsigned)L.ngroups, adj::kT, sm_f, st>>>(p);
-        ++nlaunch;
         const int nb = (K + adj::kTile - 1) / adj::kTile;
-        for (int round = 0; round < L.Cmax; ++round) {
-            adj::k_backward_round<<<(unsigned)L.ngroups, adj::kT, sm_b, st>>>(p, round);
-            adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
-            nlaunch += 2;
+        const size_t sm_c = adj::clu::smem_layout(K, M).total;
+        const bool use_cluster = K % 64 == 0 && sm_c <= (size_t)max_smem_optin();
+        if (use_cluster) {
+            const unsigned grid = (unsigned)(2 * ((S + adj::clu::kG - 1) / adj::clu::kG));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::clu::k_fwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::clu::k_rec_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::clu::k_bwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
+            adj::clu::k_fwd_cl<<<grid, adj::clu::kT, sm_c, st>>>(p);
+            ++nlaunch;
+            for (int round = 0; round < L.Cmax; ++round) {
+                adj::clu::k_rec_cl<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
+                adj::clu::k_bwd_cl<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
+                adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
+                nlaunch += 3;
+            }
+        } else {
+            size_t sm_f = adj::smem_fwd(K, M);
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_forward_cp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
+            adj::k_forward_cp<<<(unsigned)L.ngroups, adj::kT, sm_f, st>>>(p);
+            ++nlaunch;
+            for (int round = 0; round < L.Cmax; ++round) {
+                adj::k_backward_round<<<(unsigned)L.ngroups, adj::kT, sm_b, st>>>(p, round);
+                adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
+                nlaunch += 2;
+            }
         }
     }
     adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, p.pig, K, M, L.ngroups, d_grad_log_A, d_grad_log_B,

@@ -291,6 +291,9 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     uint64_t* s_P = s_buf;                          // inclusive prefix of the mapped values
     __shared__ int32_t s_pos[kOffCap];
     __shared__ uint64_t s_wtot[kThreads / 32];
+    // prefix k is stored at pswz(k): the low 4 bits XOR-ed with the owning thread's low 4 bits,
+    // so a warp writing one item of each of its 32 threads' runs spreads over all banks
+    auto pswz = [](int k) { return (k & ~15) | ((k & 15) ^ ((k >> 4) & 15)); };
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t b = blockIdx.x;
@@ -354,7 +357,7 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     for (int w = 0; w < warp; ++w) acc += s_wtot[w];
     ACCEL_MAP_SWITCH(
         _Pragma("unroll") for (int i = 0; i < IT; ++i) {
-            if (i < n) { acc += g((int64_t)xs[i]); s_P[r0 + i] = acc; }
+            if (i < n) { acc += g((int64_t)xs[i]); s_P[pswz(r0 + i)] = acc; }
         })
 #undef ACCEL_MAP_SWITCH
     __syncthreads();
@@ -363,8 +366,8 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     const int64_t nown = hi_b - lo_b;
     for (int64_t q = t; q < nown; q += kThreads) {
         const int a = rel(q), e = rel(q + 1);
-        const uint64_t hi = e > 0 ? s_P[e - 1] : 0ull;
-        const uint64_t lo = a > 0 ? s_P[a - 1] : 0ull;
+        const uint64_t hi = e > 0 ? s_P[pswz(e - 1)] : 0ull;
+        const uint64_t lo = a > 0 ? s_P[pswz(a - 1)] : 0ull;
         out[lo_b + q] = (Tout)(int64_t)(hi - lo);
     }
     // ---- the tile's open segment: segment hi_b if it starts at or before the last element
@@ -372,7 +375,7 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
         const int a = (hi_b < S) ? rel(nown) : TE + 1;
         if (a <= ne - 1) {
             tail_seg[b] = hi_b;
-            tail_val[b] = (int64_t)(s_P[ne - 1] - (a > 0 ? s_P[a - 1] : 0ull));
+            tail_val[b] = (int64_t)(s_P[pswz(ne - 1)] - (a > 0 ? s_P[pswz(a - 1)] : 0ull));
         } else {
             tail_seg[b] = -1;
         }
