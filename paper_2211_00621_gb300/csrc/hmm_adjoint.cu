@@ -489,24 +489,56 @@ __host__ __device__ inline SL smem_layout(int K, int M) {
     return L;
 }
 
-struct CGroup {
+// Group state in shared memory (read as broadcasts), so the per-thread registers hold only
+// the 16 accumulators and the step's 16 scale factors.
+struct GS {
     int64_t seq[kG], T[kG], o0[kG];
     int C[kG];
+    int ob[kG];          // symbol of the step being computed (or of t+1 in the backward)
+    float scale[kG];     // 2^-e of the previous step (forward) / 2^-e_t (backward)
+    int e[kG];
+    int64_t t0[kG], L[kG];
+    int just_done[kG];
+    float w[kG];
 };
 
-__device__ void load_cgroup(const Prm& p, CGroup& gi, int64_t cidx) {
-    for (int g = 0; g < kG; ++g) {
+__device__ void load_gs(const Prm& p, GS& gs, int64_t cidx) {
+    const int g = threadIdx.x;
+    if (g < kG) {
         int64_t q = cidx * kG + g;
         int64_t sq = q < p.S ? p.order[q] : -1;
-        gi.seq[g] = sq;
-        gi.T[g] = sq >= 0 ? p.off[sq + 1] - p.off[sq] : 0;
-        gi.o0[g] = sq >= 0 ? p.off[sq] : 0;
-        gi.C[g] = sq >= 0 ? seg_len(gi.T[g]) : 1;
-        if (sq >= 0 && gi.C[g] > p.Cmax) {
-            if (threadIdx.x == 0) atomicExch(p.status, ACCEL_ERR_SHAPE);
-            gi.seq[g] = -1;
-            gi.T[g] = 0;
-            gi.C[g] = 1;
+        int64_t T = sq >= 0 ? p.off[sq + 1] - p.off[sq] : 0;
+        int C = sq >= 0 ? seg_len(T) : 1;
+        if (sq >= 0 && C > p.Cmax) {
+            atomicExch(p.status, ACCEL_ERR_SHAPE);
+            sq = -1;
+            T = 0;
+            C = 1;
+        }
+        gs.seq[g] = sq;
+        gs.T[g] = T;
+        gs.o0[g] = sq >= 0 ? p.off[sq] : 0;
+        gs.C[g] = C;
+        gs.w[g] = (sq >= 0 && p.w) ? (float)p.w[sq] : 1.0f;
+    }
+}
+
+// Segment of round `r` for sequence g (thread g < 16); returns its length (0: none).
+__device__ void round_bounds_gs(GS& gs, int r) {
+    const int g = threadIdx.x;
+    if (g < kG) {
+        gs.t0[g] = 0;
+        gs.L[g] = 0;
+        gs.just_done[g] = 0;
+        if (gs.seq[g] >= 0) {
+            const int64_t n = (gs.T[g] + gs.C[g] - 1) / gs.C[g];
+            const int64_t k = n - 1 - r;
+            gs.just_done[g] = k == -1;
+            if (k >= 0) {
+                gs.t0[g] = k * gs.C[g];
+                const int64_t t1 = gs.t0[g] + gs.C[g] < gs.T[g] ? gs.t0[g] + gs.C[g] : gs.T[g];
+                gs.L[g] = t1 - gs.t0[g];
+            }
         }
     }
 }
@@ -519,8 +551,14 @@ __device__ void load_col_half(const float* __restrict__ src, int K, int Kp, int 
     }
 }
 
-// Warp reduce-scatter of 16 values: afterwards v[0] of lane l holds the warp's total of
-// value (l & 15).
+__device__ void load_bt_half(const float* __restrict__ BT, int K, int M, int Kh, int r, float* dst) {
+    for (int idx = threadIdx.x; idx < M * Kh; idx += kT) {
+        int k = idx / Kh, c = idx - k * Kh;
+        dst[idx] = BT[(int64_t)k * K + r * Kh + c];
+    }
+}
+
+// Warp reduce-scatter of 16 values: afterwards lane l holds the warp's total of value (l & 15).
 __device__ __forceinline__ float warp_sum16(float (&v)[kG]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -536,21 +574,22 @@ __device__ __forceinline__ float warp_sum16(float (&v)[kG]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-// acc_g = sum over this thread's i-part of X[g][i] * Ah[i][jl]; then the i-parts are
-// combined in the epilogue threads (ih == 0) in a fixed order.  Ends with a CTA barrier.
+// acc_g = sum over this thread's i-part of X[g][i] * Ah[i][jl] for all 16 g (rows of
+// inactive sequences are zero); the i-parts are then combined in the epilogue threads
+// (ih == 0) in a fixed order.  Contains a CTA barrier.
 __device__ __forceinline__ void cl_matvec(const float* __restrict__ Ah, const float* __restrict__ X, int K, int Kh,
-                                          float* spart, const bool (&act)[kG], float (&acc)[kG]) {
+                                          float* spart, float (&acc)[kG]) {
     const int tid = threadIdx.x, jl = tid % Kh, ih = tid / Kh;
     const int nih = kT / Kh, ipart = K / nih;
 #pragma unroll
     for (int g = 0; g < kG; ++g) acc[g] = 0.f;
     const int i0 = ih * ipart;
+#pragma unroll 2
     for (int i = i0; i < i0 + ipart; i += 4) {
         const float a0 = Ah[(i + 0) * Kh + jl], a1 = Ah[(i + 1) * Kh + jl];
         const float a2 = Ah[(i + 2) * Kh + jl], a3 = Ah[(i + 3) * Kh + jl];
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
-            if (!act[g]) continue;
             const float4 x = *reinterpret_cast<const float4*>(X + g * K + i);
             acc[g] = fmaf(x.x, a0, acc[g]);
             acc[g] = fmaf(x.y, a1, acc[g]);
@@ -570,8 +609,7 @@ __device__ __forceinline__ void cl_matvec(const float* __restrict__ Ah, const fl
     }
 }
 
-// Sum over the epilogue threads (ih == 0, warps 0 .. Kh/32-1) of v[g]; thread g < 16 of the
-// CTA gets the CTA total of sequence g (others: unspecified).  Contains a CTA barrier.
+// CTA partial sums of v[g] over the epilogue threads; thread g < 16 gets sequence g's.
 __device__ __forceinline__ float cta_sum16(float (&v)[kG], float* sred, int Kh) {
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int nwe = Kh / 32;
@@ -586,6 +624,53 @@ __device__ __forceinline__ float cta_sum16(float (&v)[kG], float* sred, int Kh) 
     return tot;
 }
 
+struct Views {
+    float *Ah, *BTh, *sX, *spart, *sR, *csum, *sred, *sX_peer, *csum_peer;
+};
+
+__device__ __forceinline__ Views make_views(char* smem, int K, int M, cg::cluster_group& cl, int peer) {
+    const SL Ls = smem_layout(K, M);
+    Views v;
+    v.Ah = reinterpret_cast<float*>(smem + Ls.ah);
+    v.BTh = reinterpret_cast<float*>(smem + Ls.bth);
+    v.sX = reinterpret_cast<float*>(smem + Ls.sx);
+    v.spart = reinterpret_cast<float*>(smem + Ls.spart);
+    v.sR = reinterpret_cast<float*>(smem + Ls.sr);
+    v.csum = reinterpret_cast<float*>(smem + Ls.csum);
+    v.sred = reinterpret_cast<float*>(smem + Ls.red);
+    v.sX_peer = cl.map_shared_rank(v.sX, peer);
+    v.csum_peer = cl.map_shared_rank(v.csum, peer);
+    return v;
+}
+
+// One forward step of the 16 sequences: X = sX[cur] (alpha~ of the previous step, scaled by
+// gs.scale), writes alpha~ of this step into sX[nxt] of both CTAs and the partial row sums
+// into csum[nxt] of both, then meets the peer at the cluster barrier.  `active(g)`, `ob`
+// and `scale` come from gs.  Epilogue threads return alpha~ of their state in a[].
+__device__ __forceinline__ void cl_fwd_step(const Views& V, const GS& gs, int K, int Kh, int r, int cur, int nxt,
+                                            uint32_t actmask, cg::cluster_group& cl) {
+    const int tid = threadIdx.x, jl = tid % Kh;
+    const int j = r * Kh + jl;
+    float acc[kG];
+    cl_matvec(V.Ah, V.sX + cur * kG * K, K, Kh, V.spart, acc);
+    if (tid < Kh) {
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            float a = 0.f;
+            if ((actmask >> g) & 1u) a = acc[g] * gs.scale[g] * V.BTh[gs.ob[g] * Kh + jl];
+            V.sX[(nxt * kG + g) * K + j] = a;
+            V.sX_peer[(nxt * kG + g) * K + j] = a;
+            acc[g] = a;
+        }
+    }
+    const float tot = cta_sum16(acc, V.sred, Kh);
+    if (tid < kG) {
+        V.csum[(nxt * 2 + r) * kG + tid] = tot;
+        V.csum_peer[(nxt * 2 + r) * kG + tid] = tot;
+    }
+    cl.sync();
+}
+
 // ---------------------------------------------------------------- forward + checkpoints
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm p) {
     cg::cluster_group cl = cg::this_cluster();
@@ -594,128 +679,97 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
     const bool epi = tid < Kh;
     extern __shared__ __align__(16) char smem[];
-    const SL Ls = smem_layout(K, M);
-    float* Ah = reinterpret_cast<float*>(smem + Ls.ah);
-    float* BTh = reinterpret_cast<float*>(smem + Ls.bth);
-    float* sX = reinterpret_cast<float*>(smem + Ls.sx);
-    float* spart = reinterpret_cast<float*>(smem + Ls.spart);
-    float* csum = reinterpret_cast<float*>(smem + Ls.csum);
-    float* sred = reinterpret_cast<float*>(smem + Ls.red);
-    float* sX_peer = cl.map_shared_rank(sX, peer);
-    float* csum_peer = cl.map_shared_rank(csum, peer);
-    load_col_half(p.A, K, p.Kp, Kh, r, Ah);
-    for (int idx = tid; idx < M * Kh; idx += kT) {
-        int k = idx / Kh, c = idx - k * Kh;
-        BTh[idx] = p.BT[(int64_t)k * K + r * Kh + c];
+    __shared__ GS gs;
+    __shared__ int64_t s_Tmax;
+    const Views V = make_views(smem, K, M, cl, peer);
+    load_col_half(p.A, K, p.Kp, Kh, r, V.Ah);
+    load_bt_half(p.BT, K, M, Kh, r, V.BTh);
+    load_gs(p, gs, cidx);
+    __syncthreads();
+    if (tid == 0) {
+        int64_t m = 0;
+        for (int g = 0; g < kG; ++g) m = gs.T[g] > m ? gs.T[g] : m;
+        s_Tmax = m;
     }
-    CGroup gi;
-    load_cgroup(p, gi, cidx);
-    int64_t Tmax = 0;
-    for (int g = 0; g < kG; ++g) Tmax = gi.T[g] > Tmax ? gi.T[g] : Tmax;
-    const int j = r * Kh + jl;            // this thread's state (epilogue threads)
-    bool act[kG];
-    int e[kG];
-    int64_t E[kG];
-    float v[kG];
-    cl.sync();                            // peer's shared memory is ready before any remote write
+    if (tid < kG) {
+        gs.ob[tid] = gs.T[tid] > 0 ? p.obs[gs.o0[tid]] : 0;
+        gs.scale[tid] = 1.f;
+    }
+    cl.sync();                            // both CTAs started (shared memory ready) and gs visible
+    const int64_t Tmax = s_Tmax;
+    const int j = r * Kh + jl;
+    int64_t E = 0;                        // running exponent sum of sequence tid (tid < 16)
     // t = 0: alpha~_0 = pi o b(o_0)
-#pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        act[g] = gi.T[g] > 0;
-        float a0 = 0.f;
-        if (act[g] && epi) a0 = p.pi[j] * BTh[p.obs[gi.o0[g]] * Kh + jl];
-        if (epi) { sX[g * K + j] = a0; sX_peer[g * K + j] = a0; }
-        v[g] = a0;
-    }
     {
-        float tot = cta_sum16(v, sred, Kh);
-        if (tid < kG) { csum[(0 * 2 + r) * kG + tid] = tot; csum_peer[(0 * 2 + r) * kG + tid] = tot; }
+        float a[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            a[g] = 0.f;
+            if (epi && gs.T[g] > 0) a[g] = p.pi[j] * V.BTh[gs.ob[g] * Kh + jl];
+            if (epi) { V.sX[g * K + j] = a[g]; V.sX_peer[g * K + j] = a[g]; }
+        }
+        const float tot = cta_sum16(a, V.sred, Kh);
+        if (tid < kG) { V.csum[r * kG + tid] = tot; V.csum_peer[r * kG + tid] = tot; }
     }
     cl.sync();
-#pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        const float c = csum[(0 * 2 + 0) * kG + g] + csum[(0 * 2 + 1) * kG + g];
+    // bookkeeping of step 0 (thread g < 16 for sequence g), checkpoint 0
+    if (tid < kG) {
+        const int g = tid;
+        const float c = V.csum[g] + V.csum[kG + g];
         int ex = 0;
         frexpf(c, &ex);
-        e[g] = ex;
-        E[g] = ex;
-        if (!act[g]) continue;
-        const int64_t sq = gi.seq[g];
-        if (epi) p.cp[(sq * p.Cmax) * K + j] = sX[g * K + j] * ldexpf(1.0f, -ex);
-        if (r == 0 && tid == g) {
-            p.cp_e[sq * p.Cmax] = ex;
-            if (gi.T[g] == 1) {
+        gs.e[g] = ex;
+        gs.scale[g] = ldexpf(1.0f, -ex);
+        E = ex;
+        if (gs.T[g] > 0) {
+            const int64_t sq = gs.seq[g];
+            if (r == 0) p.cp_e[sq * p.Cmax] = ex;
+            if (r == 0 && gs.T[g] == 1) {
                 p.clast[sq] = c;
                 if (p.loglik) p.loglik[sq] = log((double)c);
             }
         }
+        gs.ob[g] = gs.T[g] > 1 ? p.obs[gs.o0[g] + 1] : 0;
     }
+    __syncthreads();
+    if (epi)
+        for (int g = 0; g < kG; ++g)
+            if (gs.T[g] > 0) p.cp[(gs.seq[g] * p.Cmax) * K + j] = V.sX[g * K + j] * gs.scale[g];
     for (int64_t t = 1; t < Tmax; ++t) {
         const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
+        uint32_t actmask = 0;
 #pragma unroll
-        for (int g = 0; g < kG; ++g) act[g] = t < gi.T[g];
-        float acc[kG];
-        cl_matvec(Ah, sX + cur * kG * K, K, Kh, spart, act, acc);
+        for (int g = 0; g < kG; ++g) actmask |= (t < gs.T[g] ? 1u : 0u) << g;
+        cl_fwd_step(V, gs, K, Kh, r, cur, nxt, actmask, cl);
+        // bookkeeping (thread g): exponent of this step, logL at the last step, next symbol
+        if (tid < kG) {
+            const int g = tid;
+            if ((actmask >> g) & 1u) {
+                const float c = V.csum[(nxt * 2 + 0) * kG + g] + V.csum[(nxt * 2 + 1) * kG + g];
+                int ex = 0;
+                frexpf(c, &ex);
+                const int64_t sq = gs.seq[g];
+                if (r == 0 && t == gs.T[g] - 1) {
+                    p.clast[sq] = c;
+                    if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E + log((double)c);
+                }
+                E += ex;
+                gs.e[g] = ex;
+                gs.scale[g] = ldexpf(1.0f, -ex);
+                if (r == 0 && t % gs.C[g] == 0) p.cp_e[sq * p.Cmax + t / gs.C[g]] = ex;
+                gs.ob[g] = t + 1 < gs.T[g] ? p.obs[gs.o0[g] + t + 1] : 0;
+            }
+        }
+        __syncthreads();
         if (epi) {
-#pragma unroll
+#pragma unroll 1
             for (int g = 0; g < kG; ++g) {
-                float a = 0.f;
-                if (act[g]) a = acc[g] * ldexpf(1.0f, -e[g]) * BTh[p.obs[gi.o0[g] + t] * Kh + jl];
-                sX[(nxt * kG + g) * K + j] = a;
-                sX_peer[(nxt * kG + g) * K + j] = a;
-                v[g] = a;
-            }
-        }
-        {
-            float tot = cta_sum16(v, sred, Kh);
-            if (tid < kG) {
-                csum[(nxt * 2 + r) * kG + tid] = tot;
-                csum_peer[(nxt * 2 + r) * kG + tid] = tot;
-            }
-        }
-        cl.sync();
-#pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            if (!act[g]) continue;
-            const float c = csum[(nxt * 2 + 0) * kG + g] + csum[(nxt * 2 + 1) * kG + g];
-            int ex = 0;
-            frexpf(c, &ex);
-            const int64_t sq = gi.seq[g];
-            if (r == 0 && tid == g && t == gi.T[g] - 1) {
-                p.clast[sq] = c;
-                if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E[g] + log((double)c);
-            }
-            E[g] += ex;
-            e[g] = ex;
-            if (t % gi.C[g] == 0) {
-                const int64_t k = t / gi.C[g];
-                if (epi) p.cp[(sq * p.Cmax + k) * K + j] = sX[(nxt * kG + g) * K + j] * ldexpf(1.0f, -ex);
-                if (r == 0 && tid == g) p.cp_e[sq * p.Cmax + k] = ex;
+                if (((actmask >> g) & 1u) && t % gs.C[g] == 0)
+                    p.cp[(gs.seq[g] * p.Cmax + t / gs.C[g]) * K + j] = V.sX[(nxt * kG + g) * K + j] * gs.scale[g];
             }
         }
     }
     cl.sync();   // no CTA leaves while its peer may still write into its shared memory
-}
-
-// Segment bounds of round `r` for the sequences of a cluster's group.
-__device__ void round_bounds(const CGroup& gi, int r, int64_t (&t0)[kG], int64_t (&L)[kG], bool (&just_done)[kG],
-                             int& maxL) {
-    maxL = 0;
-#pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        t0[g] = 0;
-        L[g] = 0;
-        just_done[g] = false;
-        if (gi.seq[g] < 0) continue;
-        const int64_t n = (gi.T[g] + gi.C[g] - 1) / gi.C[g];
-        const int64_t k = n - 1 - r;
-        just_done[g] = k == -1;
-        if (k < 0) continue;
-        t0[g] = k * gi.C[g];
-        const int64_t t1 = t0[g] + gi.C[g] < gi.T[g] ? t0[g] + gi.C[g] : gi.T[g];
-        L[g] = t1 - t0[g];
-        maxL = L[g] > maxL ? (int)L[g] : maxL;
-    }
 }
 
 // ---------------------------------------------------------------- recompute a segment
@@ -727,100 +781,64 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
     const bool epi = tid < Kh;
     extern __shared__ __align__(16) char smem[];
-    const SL Ls = smem_layout(K, M);
-    float* Ah = reinterpret_cast<float*>(smem + Ls.ah);
-    float* BTh = reinterpret_cast<float*>(smem + Ls.bth);
-    float* sX = reinterpret_cast<float*>(smem + Ls.sx);
-    float* spart = reinterpret_cast<float*>(smem + Ls.spart);
-    float* csum = reinterpret_cast<float*>(smem + Ls.csum);
-    float* sred = reinterpret_cast<float*>(smem + Ls.red);
-    float* sX_peer = cl.map_shared_rank(sX, peer);
-    float* csum_peer = cl.map_shared_rank(csum, peer);
-    CGroup gi;
-    load_cgroup(p, gi, cidx);
-    int64_t t0[kG], L[kG];
-    bool just_done[kG];
-    int maxL;
-    round_bounds(gi, round, t0, L, just_done, maxL);
-    if (maxL <= 1) {
-        // only the checkpoint row itself: copy it
-#pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            if (L[g] == 0) continue;
-            const int64_t sq = gi.seq[g], base = sq * p.Cmax, k = t0[g] / gi.C[g];
-            const int64_t row = (cidx * kG + g) * p.Cmax;
-            if (epi) p.P[row * K + r * Kh + jl] = p.cp[(base + k) * K + r * Kh + jl];
-            if (r == 0 && tid == g) p.ebuf[row] = p.cp_e[base + k];
-        }
-        return;   // no remote access was made: leaving early is safe for both CTAs
-    }
-    load_col_half(p.A, K, p.Kp, Kh, r, Ah);
-    for (int idx = tid; idx < M * Kh; idx += kT) {
-        int k = idx / Kh, c = idx - k * Kh;
-        BTh[idx] = p.BT[(int64_t)k * K + r * Kh + c];
-    }
-    const int j = r * Kh + jl;
-    bool act[kG];
-    int e[kG];
-    float v[kG];
-    // tt = 0: the checkpoint S_{t0} (normalised) plays alpha~ with exponent 0
-#pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        act[g] = L[g] > 0;
-        e[g] = 0;
-        if (!act[g]) continue;
-        const int64_t sq = gi.seq[g], base = sq * p.Cmax, k = t0[g] / gi.C[g];
-        const int64_t row = (cidx * kG + g) * p.Cmax;
-        if (epi) {
-            const float sv = p.cp[(base + k) * K + j];
-            sX[g * K + j] = sv;
-            p.P[row * K + j] = sv;
-        }
-        if (r == 0 && tid == g) p.ebuf[row] = p.cp_e[base + k];
+    __shared__ GS gs;
+    __shared__ int s_maxL;
+    const Views V = make_views(smem, K, M, cl, peer);
+    load_gs(p, gs, cidx);
+    __syncthreads();
+    round_bounds_gs(gs, round);
+    __syncthreads();
+    if (tid == 0) {
+        int64_t m = 0;
+        for (int g = 0; g < kG; ++g) m = gs.L[g] > m ? gs.L[g] : m;
+        s_maxL = (int)m;
     }
     __syncthreads();
-    // the peer's half of the checkpoint row: read it from the checkpoint directly
-    for (int idx = tid; idx < kG * Kh; idx += kT) {
-        const int g = idx / Kh, c = idx - g * Kh;
-        if (L[g] == 0) continue;
-        const int64_t base = gi.seq[g] * p.Cmax, k = t0[g] / gi.C[g];
-        sX[g * K + peer * Kh + c] = p.cp[(base + k) * K + peer * Kh + c];
+    const int maxL = s_maxL;
+    const int j = r * Kh + jl;
+    // tt = 0: the checkpoint row itself (both halves read from memory), exponent 0 as alpha~
+    for (int idx = tid; idx < kG * K; idx += kT) {
+        const int g = idx / K, c = idx - g * K;
+        float sv = 0.f;
+        if (gs.L[g] > 0) sv = p.cp[(gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]) * K + c];
+        V.sX[g * K + c] = sv;
     }
+    if (tid < kG && gs.L[tid] > 0) {
+        const int g = tid;
+        const int64_t row = (cidx * kG + g) * p.Cmax;
+        if (r == 0) p.ebuf[row] = p.cp_e[gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]];
+        gs.scale[g] = 1.f;
+        gs.ob[g] = gs.L[g] > 1 ? p.obs[gs.o0[g] + gs.t0[g] + 1] : 0;
+    }
+    __syncthreads();
+    if (epi)
+        for (int g = 0; g < kG; ++g)
+            if (gs.L[g] > 0) p.P[((cidx * kG + g) * p.Cmax) * K + j] = V.sX[g * K + j];
+    if (maxL <= 1) return;                // no remote access made; the peer returns here too
+    load_col_half(p.A, K, p.Kp, Kh, r, V.Ah);
+    load_bt_half(p.BT, K, M, Kh, r, V.BTh);
     cl.sync();
     for (int tt = 1; tt < maxL; ++tt) {
         const int cur = (tt - 1) & 1, nxt = tt & 1;
+        uint32_t actmask = 0;
 #pragma unroll
-        for (int g = 0; g < kG; ++g) act[g] = tt < L[g];
-        float acc[kG];
-        cl_matvec(Ah, sX + cur * kG * K, K, Kh, spart, act, acc);
-        if (epi) {
-#pragma unroll
-            for (int g = 0; g < kG; ++g) {
-                float a = 0.f;
-                if (act[g]) a = acc[g] * ldexpf(1.0f, -e[g]) * BTh[p.obs[gi.o0[g] + t0[g] + tt] * Kh + jl];
-                sX[(nxt * kG + g) * K + j] = a;
-                sX_peer[(nxt * kG + g) * K + j] = a;
-                v[g] = a;
-            }
-        }
-        {
-            float tot = cta_sum16(v, sred, Kh);
-            if (tid < kG) {
-                csum[(nxt * 2 + r) * kG + tid] = tot;
-                csum_peer[(nxt * 2 + r) * kG + tid] = tot;
-            }
-        }
-        cl.sync();
-#pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            if (!act[g]) continue;
-            const float c = csum[(nxt * 2 + 0) * kG + g] + csum[(nxt * 2 + 1) * kG + g];
+        for (int g = 0; g < kG; ++g) actmask |= (tt < gs.L[g] ? 1u : 0u) << g;
+        cl_fwd_step(V, gs, K, Kh, r, cur, nxt, actmask, cl);
+        if (tid < kG && ((actmask >> tid) & 1u)) {
+            const int g = tid;
+            const float c = V.csum[(nxt * 2 + 0) * kG + g] + V.csum[(nxt * 2 + 1) * kG + g];
             int ex = 0;
             frexpf(c, &ex);
-            e[g] = ex;
-            const int64_t row = (cidx * kG + g) * p.Cmax + tt;
-            if (epi) p.P[row * K + j] = sX[(nxt * kG + g) * K + j] * ldexpf(1.0f, -ex);
-            if (r == 0 && tid == g) p.ebuf[row] = ex;
+            gs.scale[g] = ldexpf(1.0f, -ex);
+            if (r == 0) p.ebuf[(cidx * kG + g) * p.Cmax + tt] = ex;
+            gs.ob[g] = tt + 1 < gs.L[g] ? p.obs[gs.o0[g] + gs.t0[g] + tt + 1] : 0;
+        }
+        __syncthreads();
+        if (epi) {
+#pragma unroll 1
+            for (int g = 0; g < kG; ++g)
+                if ((actmask >> g) & 1u)
+                    p.P[((cidx * kG + g) * p.Cmax + tt) * K + j] = V.sX[(nxt * kG + g) * K + j] * gs.scale[g];
         }
     }
     cl.sync();
@@ -834,92 +852,87 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
     const bool epi = tid < Kh;
     extern __shared__ __align__(16) char smem[];
-    const SL Ls = smem_layout(K, M);
-    float* Ah = reinterpret_cast<float*>(smem + Ls.ah);
-    float* BTh = reinterpret_cast<float*>(smem + Ls.bth);
-    float* sV = reinterpret_cast<float*>(smem + Ls.sx);
-    float* spart = reinterpret_cast<float*>(smem + Ls.spart);
-    float* sR = reinterpret_cast<float*>(smem + Ls.sr);
-    float* sV_peer = cl.map_shared_rank(sV, peer);
-    CGroup gi;
-    load_cgroup(p, gi, cidx);
-    int64_t t0[kG], L[kG];
-    bool just_done[kG];
-    int maxL;
-    round_bounds(gi, round, t0, L, just_done, maxL);
+    __shared__ GS gs;
+    __shared__ int s_maxL;
+    __shared__ int s_ot[kG];
+    const Views V = make_views(smem, K, M, cl, peer);
+    load_gs(p, gs, cidx);
+    __syncthreads();
+    round_bounds_gs(gs, round);
+    __syncthreads();
+    if (tid == 0) {
+        int64_t m = 0;
+        for (int g = 0; g < kG; ++g) m = gs.L[g] > m ? gs.L[g] : m;
+        s_maxL = (int)m;
+    }
     const int i = r * Kh + jl;            // this thread's state (epilogue threads)
-    float wgt[kG];
-    int64_t rowbase[kG];
-#pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        rowbase[g] = (cidx * kG + g) * p.Cmax;
-        wgt[g] = (gi.seq[g] >= 0 && p.w) ? (float)p.w[gi.seq[g]] : 1.0f;
-        if (L[g] > 0 && r == 0 && tid == 0) atomicMax(&p.rows[round], (int32_t)(rowbase[g] + p.Cmax));
-    }
-    // rows that must read as zero (own half): the sequence's last segment was done in the
-    // previous round, or past the segment length of an active sequence
-#pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        if (gi.seq[g] < 0 || !(just_done[g] || L[g] > 0)) continue;
-        for (int64_t tt = L[g]; tt < p.Cmax; ++tt)
-            if (epi) p.Q[(rowbase[g] + tt) * K + i] = 0.f;
-    }
-    if (maxL == 0) return;   // no remote access was made
-    load_col_half(p.At, K, p.Kp, Kh, r, Ah);
-    for (int idx = tid; idx < M * Kh; idx += kT) {
-        int k = idx / Kh, c = idx - k * Kh;
-        BTh[idx] = p.BT[(int64_t)k * K + r * Kh + c];
-    }
-    // R_{t1} from the previous round (own half); zero where this round holds T-1
-#pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        if (L[g] == 0 || !epi) continue;
-        const bool last_seg = t0[g] + L[g] == gi.T[g];
-        sR[g * Kh + jl] = last_seg ? 0.f : p.Rc[gi.seq[g] * K + i];
-    }
+    if (tid < kG && gs.L[tid] > 0)
+        atomicMax(&p.rows[round], (int32_t)((cidx * kG + tid + 1) * p.Cmax));
+    __syncthreads();
+    const int maxL = s_maxL;
+    // rows that must read as zero (own half): all rows of a sequence whose last segment was
+    // done in the previous round, rows past the segment length of an active one
+    if (epi)
+        for (int g = 0; g < kG; ++g) {
+            if (gs.seq[g] < 0 || !(gs.just_done[g] || gs.L[g] > 0)) continue;
+            for (int64_t tt = gs.L[g]; tt < p.Cmax; ++tt) p.Q[((cidx * kG + g) * p.Cmax + tt) * K + i] = 0.f;
+        }
+    if (maxL == 0) return;                // no remote access made; the peer returns here too
+    load_col_half(p.At, K, p.Kp, Kh, r, V.Ah);
+    load_bt_half(p.BT, K, M, Kh, r, V.BTh);
+    if (epi)
+        for (int g = 0; g < kG; ++g) {
+            if (gs.L[g] == 0) continue;
+            const bool last_seg = gs.t0[g] + gs.L[g] == gs.T[g];
+            V.sR[g * Kh + jl] = last_seg ? 0.f : p.Rc[gs.seq[g] * K + i];
+        }
     float* cnt = p.cnt + cidx * (int64_t)K * M;
     cl.sync();
     for (int tt = maxL - 1; tt >= 0; --tt) {
         const int buf = tt & 1;
-        bool act[kG], trans[kG];
-#pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            act[g] = tt < L[g];
-            const int64_t t = t0[g] + tt;
-            trans[g] = act[g] && t < gi.T[g] - 1;
+        // per-sequence scalars of this step (thread g): transition?, o_{t+1}, o_t, e_t
+        if (tid < kG) {
+            const int g = tid;
+            const bool act = tt < gs.L[g];
+            const int64_t t = gs.t0[g] + tt;
+            const bool trans = act && t < gs.T[g] - 1;
+            gs.ob[g] = trans ? p.obs[gs.o0[g] + t + 1] : -1;
+            s_ot[g] = act ? p.obs[gs.o0[g] + t] : -1;
+            gs.e[g] = act ? p.ebuf[(cidx * kG + g) * p.Cmax + tt] : 0;
+            gs.scale[g] = ldexpf(1.0f, -gs.e[g]);
         }
+        __syncthreads();
         if (epi) {
 #pragma unroll
             for (int g = 0; g < kG; ++g) {
                 float vv = 0.f;
-                if (trans[g]) vv = BTh[p.obs[gi.o0[g] + t0[g] + tt + 1] * Kh + jl] * sR[g * Kh + jl];
-                sV[(buf * kG + g) * K + i] = vv;
-                sV_peer[(buf * kG + g) * K + i] = vv;
-                if (act[g]) p.Q[(rowbase[g] + tt) * K + i] = wgt[g] * vv;
+                if (gs.ob[g] >= 0) vv = V.BTh[gs.ob[g] * Kh + jl] * V.sR[g * Kh + jl];
+                V.sX[(buf * kG + g) * K + i] = vv;
+                V.sX_peer[(buf * kG + g) * K + i] = vv;
+                if (s_ot[g] >= 0) p.Q[((cidx * kG + g) * p.Cmax + tt) * K + i] = gs.w[g] * vv;
             }
         }
         cl.sync();
         float acc[kG];
-        cl_matvec(Ah, sV + buf * kG * K, K, Kh, spart, trans, acc);
+        cl_matvec(V.Ah, V.sX + buf * kG * K, K, Kh, V.spart, acc);
         if (epi) {
-#pragma unroll
+#pragma unroll 1
             for (int g = 0; g < kG; ++g) {
-                if (!act[g]) continue;
-                const int64_t t = t0[g] + tt;
-                const int64_t row = rowbase[g] + tt;
-                const int et = p.ebuf[row];
-                const float Rt = trans[g] ? acc[g] * ldexpf(1.0f, -et) : 1.0f / p.clast[gi.seq[g]];
-                const float St = p.P[row * K + i];
-                const float gam = wgt[g] * St * Rt * ldexpf(1.0f, et);
-                cnt[(int64_t)i * M + p.obs[gi.o0[g] + t]] += gam;
+                if (s_ot[g] < 0) continue;
+                const int64_t t = gs.t0[g] + tt;
+                const int64_t row = (cidx * kG + g) * p.Cmax + tt;
+                const float Rt = gs.ob[g] >= 0 ? acc[g] * gs.scale[g] : 1.0f / p.clast[gs.seq[g]];
+                const float gam = gs.w[g] * p.P[row * K + i] * Rt * ldexpf(1.0f, gs.e[g]);
+                cnt[(int64_t)i * M + s_ot[g]] += gam;
                 if (t == 0) p.pig[cidx * K + i] += gam;
-                sR[g * Kh + jl] = Rt;
+                V.sR[g * Kh + jl] = Rt;
             }
         }
+        __syncthreads();                  // gs scalars are rewritten at the next step
     }
-#pragma unroll
-    for (int g = 0; g < kG; ++g)
-        if (L[g] > 0 && epi) p.Rc[gi.seq[g] * K + i] = sR[g * Kh + jl];
+    if (epi)
+        for (int g = 0; g < kG; ++g)
+            if (gs.L[g] > 0) p.Rc[gs.seq[g] * K + i] = V.sR[g * Kh + jl];
     cl.sync();
 }
 
