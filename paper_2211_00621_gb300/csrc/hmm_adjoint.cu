@@ -65,6 +65,8 @@ struct Prm {
     int Kp;             // padded row stride (multiple of 4) of A, At and the shared vectors
     int32_t* rows;      // per round: rows of P/Q that may be non-zero (sorted-position order)
     int32_t* ebuf;      // exponents e_t of the P rows [S][Cmax] (cluster path)
+    float* gam;         // weighted posteriors gamma_t of the rows [S][Cmax][K] (cluster path)
+    int32_t* osym;      // o_t of each row, -1 for none [S][Cmax] (cluster path)
 };
 
 __host__ __device__ __forceinline__ int seg_len(int64_t T) {
@@ -430,11 +432,37 @@ __global__ void __launch_bounds__(256) k_gemm_ptq(const float* __restrict__ P, c
         }
 }
 
+// Emission counts of one round (cluster path): cntp[split][j][k] += sum over the split's rows
+// with o(row) = k of gam[row][j].  Thread j owns column j of a shared [M][256] block, so the
+// accumulation is conflict-free and in row order (deterministic).
+constexpr int kCntSplit = 64;
+__global__ void __launch_bounds__(256) k_counts(const float* __restrict__ gam, const int32_t* __restrict__ osym,
+                                               const int32_t* __restrict__ rows_r, int K, int M,
+                                               float* __restrict__ cntp) {
+    extern __shared__ float sc[];          // [M][256]
+    const int64_t rows = *rows_r;
+    const int nb = (K + 255) / 256;
+    const int jb = blockIdx.x % nb, sp = blockIdx.x / nb;
+    const int64_t r0 = rows * sp / kCntSplit, r1 = rows * (sp + 1) / kCntSplit;
+    if (r0 >= r1) return;
+    const int j = jb * 256 + threadIdx.x;
+    for (int k = 0; k < M; ++k) sc[k * 256 + threadIdx.x] = 0.f;
+    if (j < K) {
+        for (int64_t row = r0; row < r1; ++row) {
+            const int o = osym[row];
+            if (o >= 0) sc[o * 256 + threadIdx.x] += gam[row * K + j];
+        }
+        float* dst = cntp + (int64_t)sp * K * M;
+        for (int k = 0; k < M; ++k) dst[(int64_t)j * M + k] += sc[k * 256 + threadIdx.x];
+    }
+}
+
 // grad_log_A = A o sum_split U, grad_log_B = sum_groups counts, grad_log_pi = sum_groups pig
 // (A has row stride Kp)
 __global__ void k_finish(const float* __restrict__ A, int Kp, const float* __restrict__ Upart,
-                         const float* __restrict__ cnt, const float* __restrict__ pig, int K, int M, int64_t ngroups,
-                         float* __restrict__ gA, float* __restrict__ gB, float* __restrict__ gpi) {
+                         const float* __restrict__ cnt, const float* __restrict__ cntp, const float* __restrict__ pig,
+                         int K, int M, int64_t ngroups, float* __restrict__ gA, float* __restrict__ gB,
+                         float* __restrict__ gpi) {
     int64_t nA = (int64_t)K * K, nB = (int64_t)K * M;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nA + nB + K;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -446,6 +474,7 @@ __global__ void k_finish(const float* __restrict__ A, int Kp, const float* __res
             int64_t q = idx - nA;
             float x = 0.f;
             for (int64_t b = 0; b < ngroups; ++b) x += cnt[b * nB + q];
+            for (int b = 0; b < kCntSplit; ++b) x += cntp[(int64_t)b * nB + q];
             gB[q] = x;
         } else {
             int64_t q = idx - nA - nB;
@@ -877,6 +906,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             if (gs.seq[g] < 0 || !(gs.just_done[g] || gs.L[g] > 0)) continue;
             for (int64_t tt = gs.L[g]; tt < p.Cmax; ++tt) p.Q[((cidx * kG + g) * p.Cmax + tt) * K + i] = 0.f;
         }
+    if (r == 0 && tid < kG) {
+        const int g = tid;
+        const int64_t rb = (cidx * kG + g) * p.Cmax;
+        const int64_t from = (gs.seq[g] >= 0 && (gs.just_done[g] || gs.L[g] > 0)) ? gs.L[g] : p.Cmax;
+        for (int64_t tt = from; tt < p.Cmax; ++tt) p.osym[rb + tt] = -1;
+    }
     if (maxL == 0) return;                // no remote access made; the peer returns here too
     load_col_half(p.At, K, p.Kp, Kh, r, V.Ah);
     load_bt_half(p.BT, K, M, Kh, r, V.BTh);
@@ -886,7 +921,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             const bool last_seg = gs.t0[g] + gs.L[g] == gs.T[g];
             V.sR[g * Kh + jl] = last_seg ? 0.f : p.Rc[gs.seq[g] * K + i];
         }
-    float* cnt = p.cnt + cidx * (int64_t)K * M;
     cl.sync();
     for (int tt = maxL - 1; tt >= 0; --tt) {
         const int buf = tt & 1;
@@ -898,6 +932,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             const bool trans = act && t < gs.T[g] - 1;
             gs.ob[g] = trans ? p.obs[gs.o0[g] + t + 1] : -1;
             s_ot[g] = act ? p.obs[gs.o0[g] + t] : -1;
+            if (r == 0 && act) p.osym[(cidx * kG + g) * p.Cmax + tt] = s_ot[g];
             gs.e[g] = act ? p.ebuf[(cidx * kG + g) * p.Cmax + tt] : 0;
             gs.scale[g] = ldexpf(1.0f, -gs.e[g]);
         }
@@ -916,15 +951,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         float acc[kG];
         cl_matvec(V.Ah, V.sX + buf * kG * K, K, Kh, V.spart, acc);
         if (epi) {
-#pragma unroll 1
+            float St[kG];
+#pragma unroll
+            for (int g = 0; g < kG; ++g)
+                St[g] = s_ot[g] >= 0 ? p.P[((cidx * kG + g) * p.Cmax + tt) * K + i] : 0.f;
+#pragma unroll
             for (int g = 0; g < kG; ++g) {
                 if (s_ot[g] < 0) continue;
-                const int64_t t = gs.t0[g] + tt;
                 const int64_t row = (cidx * kG + g) * p.Cmax + tt;
                 const float Rt = gs.ob[g] >= 0 ? acc[g] * gs.scale[g] : 1.0f / p.clast[gs.seq[g]];
-                const float gam = gs.w[g] * p.P[row * K + i] * Rt * ldexpf(1.0f, gs.e[g]);
-                cnt[(int64_t)i * M + s_ot[g]] += gam;
-                if (t == 0) p.pig[cidx * K + i] += gam;
+                const float gam = gs.w[g] * St[g] * Rt * ldexpf(1.0f, gs.e[g]);
+                p.gam[row * K + i] = gam;
+                if (gs.t0[g] + tt == 0) p.pig[cidx * K + i] += gam;
                 V.sR[g * Kh + jl] = Rt;
             }
         }
@@ -939,7 +977,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
 }  // namespace clu
 
 struct Layout {
-    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, order, total;
+    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, order, total;
     int Cmax;
     int64_t ngroups;
 };
@@ -966,6 +1004,9 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.Upart = take((size_t)kSplit * K * K * 4);
     L.rows = take((size_t)L.Cmax * 4);
     L.ebuf = take((size_t)S * L.Cmax * 4);
+    L.gam = take((size_t)S * L.Cmax * K * 4);
+    L.osym = take((size_t)S * L.Cmax * 4);
+    L.cntp = take((size_t)kCntSplit * K * M * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
     return L;
@@ -1028,6 +1069,9 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     p.status = (int32_t*)(ws + kStatusOff);
     p.rows = (int32_t*)(ws + L.rows);
     p.ebuf = (int32_t*)(ws + L.ebuf);
+    p.gam = (float*)(ws + L.gam);
+    p.osym = (int32_t*)(ws + L.osym);
+    float* cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
     p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = d_weights;
     p.cp = (float*)(ws + L.cp); p.cp_e = (int32_t*)(ws + L.cp_e); p.clast = (float*)(ws + L.clast);
@@ -1045,6 +1089,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.rows, 0, (size_t)L.Cmax * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cntp, 0, (size_t)adj::kCntSplit * K * M * 4, st));
     if (S > 0) {
         r = order_by_length(d_offsets, S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)S * 4, 256), st);
         if (r != ACCEL_OK) return r;
@@ -1059,11 +1104,16 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::clu::k_bwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
             adj::clu::k_fwd_cl<<<grid, adj::clu::kT, sm_c, st>>>(p);
             ++nlaunch;
+            const size_t sm_cnt = (size_t)M * 256 * 4;
+            ACCEL_REQUIRE(sm_cnt <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: M=%d too large", M);
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
+            const int nbc = (K + 255) / 256;
             for (int round = 0; round < L.Cmax; ++round) {
                 adj::clu::k_rec_cl<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
                 adj::clu::k_bwd_cl<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
                 adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
-                nlaunch += 3;
+                adj::k_counts<<<nbc * adj::kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, cntp);
+                nlaunch += 4;
             }
         } else {
             size_t sm_f = adj::smem_fwd(K, M);
@@ -1078,8 +1128,8 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             }
         }
     }
-    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, p.pig, K, M, L.ngroups, d_grad_log_A, d_grad_log_B,
-                                      d_grad_log_pi);
+    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, cntp, p.pig, K, M, L.ngroups, d_grad_log_A,
+                                      d_grad_log_B, d_grad_log_pi);
     ++nlaunch;
     r = after_launch(st, "hmm_adjoint", nlaunch);
     if (r != ACCEL_OK) return r;
