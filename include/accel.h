@@ -278,6 +278,39 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
                          double* d_loglik, float* d_grad_log_A, float* d_grad_log_B,
                          float* d_grad_log_pi, void* d_ws, size_t ws_bytes, void* stream);
 
+/*
+ * hmm_autotune -- choose the launch configuration of the BF16 tensor-core forward (column
+ * parts per row: 8 or 16 warps; sequence rows per CTA: 128, 64 or 32) by timing each
+ * candidate with CUDA events on these inputs, and remember the fastest for (device, K, M,
+ * floor(log2 S)); hmm_forward then launches with it.  `cache_path` (may be NULL) names a
+ * file of JSON lines: an entry for the same key is reused without timing, a new result is
+ * appended.  Arguments as hmm_forward (d_loglik receives the last timed run's result).
+ * Synchronizes the stream.  h_best_ms (may be NULL) receives the best time (0 when taken from
+ * the cache or when nothing is tunable, e.g. precision ACCEL_HMM_FP32_LOG).
+ */
+accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int32_t* d_obs,
+                          const int64_t* d_offsets, int64_t S, int64_t total_T, double* d_loglik,
+                          void* d_ws, size_t ws_bytes, const char* cache_path, float* h_best_ms,
+                          void* stream);
+/* The configuration hmm_forward(ACCEL_HMM_BF16_SCALED) uses for these sizes. */
+accel_status hmm_tuned_config(int32_t K, int32_t M, int64_t S, int32_t* h_split, int32_t* h_rows);
+
+/* ========================================================================= graphs */
+/*
+ * Capture a sequence of library calls made on `stream` into an executable CUDA graph and
+ * replay it (stream capture; e.g. the persistent batched HMM launch with its preparation
+ * kernels).  Between accel_graph_begin and accel_graph_end only asynchronous library calls
+ * may be made on the stream (debug mode off), with every buffer allocated beforehand: a
+ * replay reuses the captured pointers and sizes.  `stream` must not be the legacy default
+ * stream.  The graph owns only host-side CUDA objects; accel_graph_destroy frees them.
+ */
+typedef struct accel_graph_s* accel_graph;
+accel_status accel_graph_begin(void* stream);
+accel_status accel_graph_end(void* stream, accel_graph* out);
+accel_status accel_graph_launch(accel_graph g, void* stream);
+accel_status accel_graph_destroy(accel_graph g);
+accel_status accel_graph_node_count(accel_graph g, int64_t* out);
+
 /* =========================================================== all-pairs map-of-reduce */
 /*
  * pairwise_mapreduce -- for every body i, a reduce over all bodies j (a map of a reduce,

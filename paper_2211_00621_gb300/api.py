@@ -242,6 +242,66 @@ def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | N
     return gA, gB, gpi, ll
 
 
+def hmm_autotune(log_A, log_B, log_pi, obs, offsets, precision=L.HMM_BF16_SCALED, cache_path=None, ws=None):
+    """Times the BF16 forward's launch configurations on these inputs and keeps the fastest
+    for later hmm_forward calls (and in `cache_path`, JSON lines, if given).  Returns
+    (best ms or 0.0 if cached, (split, rows))."""
+    lib = L.load()
+    m = _model(log_A, log_B, log_pi)
+    S = offsets.numel() - 1
+    need = lib.hmm_forward_workspace_size(C.byref(m), S, obs.numel(), precision)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, obs.device)
+    out = torch.empty(S, dtype=torch.float64, device=obs.device)
+    best = C.c_float(0.0)
+    path = cache_path.encode() if cache_path else None
+    L.check("hmm_autotune", lib.hmm_autotune(C.byref(m), precision, _ptr(obs), _ptr(offsets), S, obs.numel(),
+                                             _ptr(out), _ptr(ws), ws.numel(), path, C.byref(best), _stream()))
+    split, rows = C.c_int32(0), C.c_int32(0)
+    L.check("hmm_tuned_config", lib.hmm_tuned_config(m.K, m.M, S, C.byref(split), C.byref(rows)))
+    return best.value, (split.value, rows.value)
+
+
+class Graph:
+    """A captured sequence of library calls on a (non-default) stream, replayed with one
+    launch.  Allocate every output and workspace before capturing."""
+
+    def __init__(self):
+        self.h = C.c_void_p(0)
+
+    def capture(self, fn, stream=None):
+        lib = L.load()
+        stream = stream or torch.cuda.current_stream()
+        s = C.c_void_p(stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            L.check("accel_graph_begin", lib.accel_graph_begin(s))
+            try:
+                result = fn()
+            finally:
+                h = C.c_void_p(0)
+                st = lib.accel_graph_end(s, C.byref(h))
+            L.check("accel_graph_end", st)
+        self.h = h
+        return result
+
+    def launch(self, stream=None):
+        lib = L.load()
+        stream = stream or torch.cuda.current_stream()
+        L.check("accel_graph_launch", lib.accel_graph_launch(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def nodes(self):
+        n = C.c_int64(0)
+        L.check("accel_graph_node_count", L.load().accel_graph_node_count(self.h, C.byref(n)))
+        return n.value
+
+    def __del__(self):
+        try:
+            if self.h and self.h.value:
+                L.load().accel_graph_destroy(self.h)
+        except Exception:
+            pass
+
+
 class HMMLogLik(torch.autograd.Function):
     """logL[S] = HMMLogLik.apply(log_A, log_B, log_pi, obs, offsets, precision).
 

@@ -128,3 +128,63 @@ int32_t accel_get_debug(void) { return accel::g_debug.load(); }
 uint64_t accel_launch_count(void) { return accel::g_launches.load(); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ CUDA graphs
+// A captured sequence of library calls (stream capture -> instantiated executable graph).
+struct accel_graph_s {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+accel_status accel_graph_begin(void* stream) {
+    using namespace accel;
+    ACCEL_REQUIRE(stream != nullptr, ACCEL_ERR_INVALID_ARG, "accel_graph_begin: capture needs a non-default stream");
+    ACCEL_REQUIRE(!debug_mode(), ACCEL_ERR_INVALID_ARG, "accel_graph_begin: debug mode synchronizes and cannot be captured");
+    ACCEL_CUDA_TRY(cudaStreamBeginCapture(as_stream(stream), cudaStreamCaptureModeRelaxed));
+    return ok();
+}
+
+accel_status accel_graph_end(void* stream, accel_graph* out) {
+    using namespace accel;
+    ACCEL_REQUIRE(stream != nullptr && out != nullptr, ACCEL_ERR_INVALID_ARG, "accel_graph_end: null argument");
+    cudaGraph_t g = nullptr;
+    ACCEL_CUDA_TRY(cudaStreamEndCapture(as_stream(stream), &g));
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_error(ACCEL_ERR_CUDA, "accel_graph_end: instantiate failed: %s", cudaGetErrorString(e));
+    }
+    accel_graph_s* h = new accel_graph_s{g, ex};
+    *out = h;
+    return ok();
+}
+
+accel_status accel_graph_launch(accel_graph g, void* stream) {
+    using namespace accel;
+    ACCEL_REQUIRE(g != nullptr, ACCEL_ERR_INVALID_ARG, "accel_graph_launch: null graph");
+    ACCEL_CUDA_TRY(cudaGraphLaunch(g->exec, as_stream(stream)));
+    return after_launch(as_stream(stream), "accel_graph_launch", 0);
+}
+
+accel_status accel_graph_destroy(accel_graph g) {
+    using namespace accel;
+    if (!g) return ok();
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return ok();
+}
+
+accel_status accel_graph_node_count(accel_graph g, int64_t* out) {
+    using namespace accel;
+    ACCEL_REQUIRE(g && out, ACCEL_ERR_INVALID_ARG, "accel_graph_node_count: null argument");
+    size_t n = 0;
+    ACCEL_CUDA_TRY(cudaGraphGetNodes(g->graph, nullptr, &n));
+    *out = (int64_t)n;
+    return ok();
+}
+
+}  // extern "C"

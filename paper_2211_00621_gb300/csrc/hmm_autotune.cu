@@ -1,0 +1,172 @@
+// Autotuner for the BF16 tensor-core HMM forward: picks the launch configuration (column
+// parts per row: 8 or 16 warps; sequence rows per CTA: 128, 64 or 32) by timing every
+// candidate on the caller's inputs with CUDA events, and remembers the winner per
+// (device, K, M, floor(log2 S)) -- in this process, and optionally in a cache file of JSON
+// lines so later processes skip the timing:
+//   {"kernel": "hmm_forward_bf16", "device": "<name>", "K": 256, "M": 64, "S_log2": 12,
+//    "split": 4, "rows": 128, "ms": 17.21}
+// hmm_forward consults the table; without an entry it uses 16 warps and 128 rows.
+#include "hmm_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+namespace accel {
+namespace hmm {
+
+namespace {
+
+using Key = std::tuple<std::string, int, int, int>;
+
+std::mutex g_mu;
+std::map<Key, TcConfig> g_table;
+
+std::string device_name() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    return prop.name;
+}
+
+int s_log2(int64_t S) {
+    int b = 0;
+    while ((int64_t(1) << (b + 1)) <= S) ++b;
+    return b;
+}
+
+TcConfig default_config(int K) { return TcConfig{(K / 4) % 32 == 0 ? 4 : 2, 128}; }
+
+bool load_from_cache(const char* path, const Key& key, TcConfig* out) {
+    if (!path || !path[0]) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char kern[64], dev[256];
+        int K, M, sl, split, rows;
+        float ms;
+        int n = sscanf(line,
+                       " {\"kernel\": \"%63[^\"]\", \"device\": \"%255[^\"]\", \"K\": %d, \"M\": %d, \"S_log2\": %d, "
+                       "\"split\": %d, \"rows\": %d, \"ms\": %f}",
+                       kern, dev, &K, &M, &sl, &split, &rows, &ms);
+        if (n != 8 || strcmp(kern, "hmm_forward_bf16") != 0) continue;
+        if (Key(dev, K, M, sl) == key) {
+            *out = TcConfig{split, rows};
+            found = true;   // the last matching line wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void append_to_cache(const char* path, const Key& key, TcConfig c, float ms) {
+    if (!path || !path[0]) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f,
+            "{\"kernel\": \"hmm_forward_bf16\", \"device\": \"%s\", \"K\": %d, \"M\": %d, \"S_log2\": %d, "
+            "\"split\": %d, \"rows\": %d, \"ms\": %.4f}\n",
+            std::get<0>(key).c_str(), std::get<1>(key), std::get<2>(key), std::get<3>(key), c.split, c.rows, ms);
+    fclose(f);
+}
+
+}  // namespace
+
+TcConfig tuned_config(int K, int M, int64_t S) {
+    Key key(device_name(), K, M, s_log2(S));
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_table.find(key);
+    return it != g_table.end() ? it->second : default_config(K);
+}
+
+accel_status check_model(const accel_hmm_model* m, const char* who);
+
+}  // namespace hmm
+}  // namespace accel
+
+using namespace accel;
+using namespace accel::hmm;
+
+extern "C" {
+
+accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int32_t* d_obs, const int64_t* d_offsets,
+                          int64_t S, int64_t total_T, double* d_loglik, void* d_ws, size_t ws_bytes,
+                          const char* cache_path, float* h_best_ms, void* stream) {
+    accel_status r = check_model(m, "hmm_autotune");
+    if (r != ACCEL_OK) return r;
+    if (h_best_ms) *h_best_ms = 0.f;
+    if (precision != ACCEL_HMM_BF16_SCALED || S == 0) return ok();   // nothing to tune
+    ACCEL_REQUIRE(d_obs && d_offsets && d_loglik && d_ws, ACCEL_ERR_INVALID_ARG, "hmm_autotune: null pointer");
+    ACCEL_REQUIRE(tc_supported(m->K, m->M), ACCEL_ERR_UNSUPPORTED, "hmm_autotune: shape not supported by the BF16 kernel");
+    const size_t need = hmm_forward_workspace_size(m, S, total_T, precision);
+    ACCEL_REQUIRE(ws_bytes >= need, ACCEL_ERR_WORKSPACE, "hmm_autotune: workspace %zu < %zu bytes", ws_bytes, need);
+    ACCEL_REQUIRE(!debug_mode(), ACCEL_ERR_INVALID_ARG, "hmm_autotune: not available in debug mode");
+    const Key key(device_name(), m->K, m->M, s_log2(S));
+    TcConfig cached;
+    if (load_from_cache(cache_path, key, &cached)) {
+        std::lock_guard<std::mutex> lock(g_mu);
+        g_table[key] = cached;
+        return ok();
+    }
+    cudaStream_t st = as_stream(stream);
+    char* ws = (char*)d_ws;
+    std::vector<TcConfig> cands;
+    for (int split : {4, 2})
+        for (int rows : {128, 64, 32}) {
+            if (split == 4 && (m->K / 4) % 32 != 0) continue;
+            if (rows < 128 && (S + rows - 1) / rows <= (S + 127) / 128) continue;   // no more CTAs than 128 rows
+            cands.push_back(TcConfig{split, rows});
+        }
+    cudaEvent_t e0, e1;
+    ACCEL_CUDA_TRY(cudaEventCreate(&e0));
+    ACCEL_CUDA_TRY(cudaEventCreate(&e1));
+    TcConfig best = default_config(m->K);
+    float best_ms = INFINITY;
+    for (const TcConfig& c : cands) {
+        ACCEL_CUDA_TRY(cudaMemsetAsync(ws + kStatusOff, 0, 4, st));
+        r = tc_forward_cfg(m, d_obs, d_offsets, S, d_loglik, ws, (int32_t*)(ws + kStatusOff), c, st);   // warm-up
+        if (r != ACCEL_OK) break;
+        float total = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            ACCEL_CUDA_TRY(cudaEventRecord(e0, st));
+            r = tc_forward_cfg(m, d_obs, d_offsets, S, d_loglik, ws, (int32_t*)(ws + kStatusOff), c, st);
+            if (r != ACCEL_OK) break;
+            ACCEL_CUDA_TRY(cudaEventRecord(e1, st));
+            ACCEL_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ACCEL_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            total += ms;
+        }
+        if (r != ACCEL_OK) break;
+        const float ms = total / 2;
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != ACCEL_OK) return r;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        g_table[key] = best;
+    }
+    append_to_cache(cache_path, key, best, best_ms);
+    if (h_best_ms) *h_best_ms = best_ms;
+    return ok();
+}
+
+// Configuration hmm_forward would use for these sizes (for tests and reports).
+accel_status hmm_tuned_config(int32_t K, int32_t M, int64_t S, int32_t* h_split, int32_t* h_rows) {
+    ACCEL_REQUIRE(h_split && h_rows, ACCEL_ERR_INVALID_ARG, "hmm_tuned_config: null pointer");
+    TcConfig c = tuned_config(K, M, S);
+    *h_split = c.split;
+    *h_rows = c.rows;
+    return ok();
+}
+
+}  // extern "C"

@@ -22,7 +22,18 @@ size_t plain_ws_bytes(int K, int M, int64_t S);
 accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const int64_t* off, int64_t S,
                            double* loglik, char* ws, int32_t* d_status, cudaStream_t st);
 
+// Launch configuration of the BF16 tensor-core forward, chosen by the autotuner
+// (hmm_autotune.cu): column parts per row (2: 8 warps, 4: 16 warps) and sequence rows used per
+// CTA (<= 128; fewer rows spread the sequences over more SMs).
+struct TcConfig {
+    int split;
+    int rows;
+};
+TcConfig tuned_config(int K, int M, int64_t S);
+
 // BF16 tensor-core scaled forward (k_hmm_tc.cu).
+accel_status tc_forward_cfg(const accel_hmm_model* m, const int32_t* obs, const int64_t* off, int64_t S,
+                            double* loglik, char* ws, int32_t* d_status, TcConfig cfg, cudaStream_t st);
 size_t tc_ws_bytes(int K, int M, int64_t S);
 accel_status tc_forward(const accel_hmm_model* m, const int32_t* obs, const int64_t* off, int64_t S,
                         double* loglik, char* ws, int32_t* d_status, cudaStream_t st);

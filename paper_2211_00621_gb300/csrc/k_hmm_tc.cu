@@ -39,7 +39,6 @@ namespace accel {
 namespace hmm {
 
 constexpr int kRows = 128;
-constexpr int kTcThreads = 256;
 constexpr uint64_t kWaitNs = 2000000000ull;   // bounded mbarrier wait: 2 s of wall clock
 
 struct TcLayout {
@@ -49,10 +48,10 @@ struct TcLayout {
     uint32_t s_at, s_x, s_e, s_rowinfo, s_psum, s_bar, s_slot, smem_bytes;
 };
 
-// Per-row values the column-half threads need (written by the row's owner thread).
+// Per-row values the column-part threads need (written by the row's owner thread).
 struct RowInfo {
-    int32_t ob;     // symbol o_t of the step being computed (-1: no sequence)
-    float mult;     // 2^-k_t for this step's X_t
+    int16_t ob;     // symbol o_t of the step being computed (-1: no sequence)
+    int16_t k;      // exponent k_t: this step's X_t is scaled by 2^-k_t
 };
 
 static TcLayout tc_layout(int K, int M, int64_t S) {
@@ -68,7 +67,7 @@ static TcLayout tc_layout(int K, int M, int64_t S) {
     L.s_e = o;  o += (uint32_t)M * K * 2;
     o = (o + 15) & ~15u;
     L.s_rowinfo = o; o += kRows * (uint32_t)sizeof(RowInfo);
-    L.s_psum = o; o += 2 * kRows * 4;
+    L.s_psum = o; o += 4 * kRows * 4;
     L.s_bar = o; o += 8;
     L.s_slot = o; o += 8;
     L.smem_bytes = o;
@@ -76,7 +75,7 @@ static TcLayout tc_layout(int K, int M, int64_t S) {
 }
 
 bool tc_supported(int K, int M) {
-    if (K < 64 || K > 256 || K % 64 != 0 || M < 1) return false;
+    if (K < 64 || K > 256 || K % 64 != 0 || M < 1 || M > 32767) return false;
     return (int)tc_layout(K, M, 0).smem_bytes <= max_smem_optin();
 }
 
@@ -120,7 +119,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+// NSPLIT = column parts per row: 2 (8 warps) or 4 (16 warps; needs K/4 a multiple of 32)
+template <int NSPLIT>
+__global__ void __launch_bounds__(128 * NSPLIT, 1)
 k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g_etab,
          const float* __restrict__ log_pi, const int32_t* __restrict__ obs, const int64_t* __restrict__ off,
          int64_t S, const int32_t* __restrict__ order, unsigned long long* __restrict__ next, int rows_active,
@@ -130,24 +131,25 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     char* sX = smem + L.s_x;
     char* sE = smem + L.s_e;
     RowInfo* rinfo = reinterpret_cast<RowInfo*>(smem + L.s_rowinfo);
-    float* psum = reinterpret_cast<float*>(smem + L.s_psum);        // [2][kRows]
+    float* psum = reinterpret_cast<float*>(smem + L.s_psum);        // [NSPLIT][kRows]
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.s_bar);
     uint32_t* slot = reinterpret_cast<uint32_t*>(smem + L.s_slot);
+    constexpr int kThreads = 128 * NSPLIT;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int quarter = w & 3, half = w >> 2;
+    const int quarter = w & 3, part = w >> 2;
     const int row = 32 * quarter + lane;          // row this thread reads and writes
-    const int KH = K >> 1;                        // columns per half
-    const int c0 = half * KH;                     // first column of this thread's half
+    const int KH = K / NSPLIT;                    // columns per part
+    const int c0 = part * KH;                     // first column of this thread's part
     const int nch = K >> 3;
 
     // ---- stage A^T and the emission table (linear copies of prepared layouts)
     {
         const int4* src = reinterpret_cast<const int4*>(g_at);
         int4* dst = reinterpret_cast<int4*>(sAT);
-        for (int i = tid; i < K * K * 2 / 16; i += kTcThreads) dst[i] = src[i];
+        for (int i = tid; i < K * K * 2 / 16; i += kThreads) dst[i] = src[i];
         src = reinterpret_cast<const int4*>(g_etab);
         dst = reinterpret_cast<int4*>(sE);
-        for (int i = tid; i < M * K * 2 / 16; i += kTcThreads) dst[i] = src[i];
+        for (int i = tid; i < M * K * 2 / 16; i += kThreads) dst[i] = src[i];
     }
     const uint32_t ncols = K <= 64 ? 64 : K <= 128 ? 128 : 256;
     if (w == 0) {
@@ -168,8 +170,8 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     const uint32_t sx_addr = tc::smem_u32(sX), sat_addr = tc::smem_u32(sAT);
     const uint32_t sbo = 16u * (uint32_t)K;
 
-    // row bookkeeping, kept by the row's owner thread (half 0)
-    const bool owner = half == 0;
+    // row bookkeeping, kept by the row's owner thread (part 0)
+    const bool owner = part == 0;
     int64_t seq = -1, T = 0, pos = 0, E = 0;
     const int32_t* o = nullptr;
     int32_t kcur = 0;            // exponent applied to this step's X
@@ -240,8 +242,8 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
             kcur = (int)rintf(uprev + ls);              // predicted exponent of s_1
             pos = 1;
         }
-        rinfo[row].ob = seq >= 0 ? o[pos] : -1;
-        rinfo[row].mult = ldexpf(1.0f, -kcur);
+        rinfo[row].ob = (int16_t)(seq >= 0 ? o[pos] : -1);
+        rinfo[row].k = (int16_t)kcur;
     };
 
     if (owner) start_next();
@@ -269,6 +271,7 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         }
         // ---- epilogue, one pass: each thread's half-row of D (tcgen05.ld is warp-collective)
         const bool act = ri.ob >= 0;
+        const float mult = ldexpf(1.0f, -(int)ri.k);
         float ps = 0.f;
         if (__any_sync(0xffffffffu, act)) {
             for (int jc = 0; jc < KH; jc += 32) {
@@ -282,15 +285,17 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
                         v[u] = __uint_as_float(d[u]) * b[u];
                         ps += v[u];
                     }
-                    store_chunk(row, c0 + jc, v, ri.mult);
+                    store_chunk(row, c0 + jc, v, mult);
                 }
             }
         }
-        psum[half * kRows + row] = ps;
+        psum[part * kRows + row] = ps;
         __syncthreads();
         // ---- row bookkeeping (owner thread of each row)
         if (owner && seq >= 0) {
-            const float s = psum[row] + psum[kRows + row];
+            float s = psum[row];
+#pragma unroll
+            for (int q = 1; q < NSPLIT; ++q) s += psum[q * kRows + row];
             if (pos == T - 1) {
                 loglik[seq] = 0.6931471805599453 * (double)E + log((double)s);
                 seq = -1;
@@ -307,8 +312,8 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         if (owner) {
             if (seq < 0) start_next();
             else {
-                rinfo[row].ob = o[pos];
-                rinfo[row].mult = ldexpf(1.0f, -kcur);
+                rinfo[row].ob = (int16_t)o[pos];
+                rinfo[row].k = (int16_t)kcur;
             }
         }
     }
@@ -317,12 +322,14 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     if (w == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
-accel_status tc_forward(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
-                        double* loglik, char* ws, int32_t* d_status, cudaStream_t st) {
+accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
+                            double* loglik, char* ws, int32_t* d_status, TcConfig cfg, cudaStream_t st) {
     const int K = mdl->K, M = mdl->M;
     ACCEL_REQUIRE(tc_supported(K, M), ACCEL_ERR_UNSUPPORTED,
                   "hmm_forward(bf16): K must be a multiple of 64 in [64, 256] and the tables must fit shared "
                   "memory (K=%d, M=%d)", K, M);
+    if (cfg.split == 4 && (K / 4) % 32 != 0) cfg.split = 2;
+    if (cfg.rows < 32 || cfg.rows > kRows) cfg.rows = kRows;
     TcLayout L = tc_layout(K, M, S);
     char* at = ws + L.at_off;
     char* et = ws + L.e_off;
@@ -335,13 +342,23 @@ accel_status tc_forward(const accel_hmm_model* mdl, const int32_t* obs, const in
     k_tc_prep<<<pg, 256, 0, st>>>(mdl->log_A, mdl->log_B, K, M, at, et);
     accel_status r = order_by_length(off, S, order, ws + L.order_scratch_off, st);
     if (r != ACCEL_OK) return r;
-    ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_hmm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
-    const int rows_active = kRows;
-    int64_t tiles = (S + rows_active - 1) / rows_active;
+    int64_t tiles = (S + cfg.rows - 1) / cfg.rows;
     int grid = (int)(tiles < num_sms() ? tiles : num_sms());
-    k_hmm_tc<<<grid, kTcThreads, L.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, rows_active,
+    if (cfg.split == 4) {
+        ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_hmm_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+        k_hmm_tc<4><<<grid, 512, L.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
                                                      loglik, d_status, L);
+    } else {
+        ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_hmm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+        k_hmm_tc<2><<<grid, 256, L.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
+                                                     loglik, d_status, L);
+    }
     return after_launch(st, "hmm_forward(bf16 tcgen05)", 5);
+}
+
+accel_status tc_forward(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
+                        double* loglik, char* ws, int32_t* d_status, cudaStream_t st) {
+    return tc_forward_cfg(mdl, obs, off, S, loglik, ws, d_status, tuned_config(mdl->K, mdl->M, S), st);
 }
 
 }  // namespace hmm

@@ -96,3 +96,63 @@ def test_single_step_sequences():
     p = synth.hmm_workload(7, 64, 32, 50, "fixed", 1, 1)
     for prec in (acc.HMM_FP32_LOG, acc.HMM_BF16_SCALED):
         _check(p, prec)
+
+
+def _force_config(tmp_path, K, M, S, split, rows, t):
+    import json as _json
+    path = str(tmp_path / "tune.jsonl")
+    sl = 0
+    while (1 << (sl + 1)) <= S:
+        sl += 1
+    with open(path, "w") as f:
+        f.write(_json.dumps({"kernel": "hmm_forward_bf16", "device": torch.cuda.get_device_name(), "K": K, "M": M,
+                             "S_log2": sl, "split": split, "rows": rows, "ms": 1.0}) + "\n")
+    ms, cfg = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], t["obs"], t["off"], cache_path=path)
+    assert ms == 0.0 and cfg == (split, rows)
+
+
+@pytest.mark.parametrize("split,rows", [(2, 128), (4, 128), (4, 32), (2, 64)])
+def test_bf16_tc_launch_configurations(tmp_path, split, rows):
+    p = synth.hmm_workload(12, 128, 32, 700, "loguniform", 1, 400)
+    logs, t, obs, off = _prep(p)
+    t["obs"], t["off"] = obs, off
+    _force_config(tmp_path, 128, 32, 700, split, rows, t)
+    _check(p, acc.HMM_BF16_SCALED)
+
+
+def test_autotune_times_candidates_and_caches(tmp_path):
+    c = synth.CFG_HMM_BATCHED
+    p = synth.hmm_workload(c["seed"], c["K"], c["M"], 512, c["kind"], c["lo"], 600)
+    logs, t, obs, off = _prep(p)
+    path = str(tmp_path / "tune.jsonl")
+    ms, cfg = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off, cache_path=path)
+    assert ms > 0.0 and cfg[0] in (2, 4) and cfg[1] in (32, 64, 128)
+    with open(path) as f:
+        assert "hmm_forward_bf16" in f.read()
+    ms2, cfg2 = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off, cache_path=path)
+    assert ms2 == 0.0 and cfg2 == cfg                      # taken from the cache file
+    _check(p, acc.HMM_BF16_SCALED, sample=list(range(0, 512, 37)))
+
+
+def test_graph_capture_replays_the_persistent_launch():
+    p = synth.hmm_workload(13, 256, 64, 600, "loguniform", 50, 800)
+    logs, t, obs, off = _prep(p)
+    direct = api.hmm_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off, acc.HMM_BF16_SCALED)
+    from paper_2211_00621_gb300 import _lib
+    import ctypes as C
+    lib = _lib.load()
+    m = api._model(t["log_A"], t["log_B"], t["log_pi"])
+    ws = torch.empty(lib.hmm_forward_workspace_size(C.byref(m), 600, obs.numel(), acc.HMM_BF16_SCALED),
+                     dtype=torch.uint8, device=DEV)
+    out = torch.full((600,), float("nan"), dtype=torch.float64, device=DEV)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = api.Graph()
+    g.capture(lambda: api.hmm_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off, acc.HMM_BF16_SCALED,
+                                      out=out, ws=ws), stream=side)
+    assert g.nodes() >= 2
+    for _ in range(2):
+        out.fill_(float("nan"))
+        g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(out, direct)
