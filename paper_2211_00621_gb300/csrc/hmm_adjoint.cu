@@ -500,35 +500,68 @@ namespace cg = cooperative_groups;
 
 constexpr int kG = 16;      // sequences per cluster
 constexpr int kT = 256;     // threads per CTA
+constexpr int kSlots = 16;  // partial row sums per sequence: 2 CTAs x 8 warps
 
-struct SL { size_t ah, bth, sx, spart, sr, csum, red, total; };
+// Work split for K in {64, 128, 256}.  Each CTA of the pair owns Kh = K/2 states.  Thread
+// tid = cs NP + p owns the CW states c_h = cs + h NCS (h < CW) of its CTA's half and the
+// i-part p of the contraction (rows p IPART .. p IPART + IPART - 1).  The NP parts of a
+// column slot are neighbouring lanes; after the contraction they are combined by a
+// reduce-scatter of xor shuffles, which leaves lane p with the sums of sequences
+// g = p GPT + u (u < GPT) -- the sequences it then handles in the epilogue.
+//
+// The contraction pairs rows, not columns: the accumulator of (g, c) is a float2 holding
+// the even-row and odd-row partial sums, so both operands of each packed FMA are natural
+// register pairs (x[g][i], x[g][i+1]) and (a[i][c], a[i+1][c]); the matrix half is kept
+// transposed (a row per owned state) for that.  Rows of both shared arrays are skewed by
+// 16 bytes per i-part so that the lanes of a warp hit distinct banks.
+struct Geo {
+    int Kh, CW, NCS, NP, IPART, GPT, XK, AS;
+};
+__host__ __device__ constexpr Geo geo(int K) {
+    return Geo{K / 2,
+               K >= 128 ? 4 : 2,
+               (K / 2) / (K >= 128 ? 4 : 2),
+               kT / ((K / 2) / (K >= 128 ? 4 : 2)),
+               K / (kT / ((K / 2) / (K >= 128 ? 4 : 2))),
+               kG / (kT / ((K / 2) / (K >= 128 ? 4 : 2))),
+               K + 4 * (kT / ((K / 2) / (K >= 128 ? 4 : 2))),
+               K + 4 * (kT / ((K / 2) / (K >= 128 ? 4 : 2))) + 4};
+}
+__host__ __device__ inline bool cluster_shape_ok(int K) { return K == 64 || K == 128 || K == 256; }
+
+template <int K>
+struct Sh {
+    static constexpr Geo G = geo(K);
+    static constexpr int Kh = G.Kh, CW = G.CW, NCS = G.NCS, NP = G.NP, IPART = G.IPART, GPT = G.GPT, XK = G.XK,
+                         AS = G.AS;
+    static_assert(IPART % 4 == 0 && NP <= 16 && GPT >= 1 && NP * GPT == kG, "unsupported split");
+    __device__ static int pos(int i) { return i + (i / IPART) * 4; }   // skewed position of element i
+};
+
+struct SL { size_t at, bth, sx, red, total; };
 
 __host__ __device__ inline SL smem_layout(int K, int M) {
-    const int Kh = K / 2;
+    const Geo G = geo(K);
     SL L;
     size_t o = 0;
-    L.ah = o;    o += (size_t)K * Kh * 4;                 // matrix column half [K][Kh]
-    L.bth = o;   o += (size_t)M * Kh * 4;                 // emission column half [M][Kh]
-    L.sx = o;    o += (size_t)2 * kG * K * 4;             // full vectors, two step parities
-    L.spart = o; o += (size_t)(kT - Kh) * kG * 4;         // partial matvec results to combine
-    L.sr = o;    o += (size_t)kG * Kh * 4;                // R (backward), own half
-    L.csum = o;  o += (size_t)2 * 2 * kG * 4;             // [parity][rank][g] partial row sums
-    L.red = o;   o += (size_t)8 * kG * 4;                 // per-warp partial sums
+    L.at = o;    o += (size_t)G.Kh * G.AS * 4;            // owned matrix columns, transposed [Kh][AS]
+    L.bth = o;   o += (size_t)M * G.Kh * 4;               // emission columns [M][Kh]
+    L.sx = o;    o += (size_t)2 * kG * G.XK * 4;          // full vectors, two step parities [2][16][XK]
+    L.red = o;   o += (size_t)2 * kSlots * kG * 4;        // partial row sums [2][16 slots][16]
     L.total = o;
     return L;
 }
 
-// Group state in shared memory (read as broadcasts), so the per-thread registers hold only
-// the 16 accumulators and the step's 16 scale factors.
+// Group state in shared memory (read as broadcasts).
 struct GS {
     int64_t seq[kG], T[kG], o0[kG];
     int C[kG];
-    int ob[kG];          // symbol of the step being computed (or of t+1 in the backward)
-    float scale[kG];     // 2^-e of the previous step (forward) / 2^-e_t (backward)
-    int e[kG];
+    float w[kG];
     int64_t t0[kG], L[kG];
     int just_done[kG];
-    float w[kG];
+    int sym[2][kG];      // per step parity: the step's symbol (see the kernels)
+    int eb[2][kG];       // per step parity: e_t (backward)
+    int sym_end[kG];     // backward: symbol after the segment, -1 if none
 };
 
 __device__ void load_gs(const Prm& p, GS& gs, int64_t cidx) {
@@ -552,7 +585,6 @@ __device__ void load_gs(const Prm& p, GS& gs, int64_t cidx) {
     }
 }
 
-// Segment of round `r` for sequence g (thread g < 16); returns its length (0: none).
 __device__ void round_bounds_gs(GS& gs, int r) {
     const int g = threadIdx.x;
     if (g < kG) {
@@ -572,340 +604,365 @@ __device__ void round_bounds_gs(GS& gs, int r) {
     }
 }
 
-// columns [r Kh, (r+1) Kh) of a K x K matrix stored with row stride Kp, into [K][Kh]
-__device__ void load_col_half(const float* __restrict__ src, int K, int Kp, int Kh, int r, float* dst) {
-    for (int idx = threadIdx.x; idx < K * Kh; idx += kT) {
-        int i = idx / Kh, jl = idx - i * Kh;
-        dst[idx] = src[(int64_t)i * Kp + r * Kh + jl];
+// dst[c][pos(i)] = src[(r Kh + c) Kp + i]: the CTA's states as rows of the contraction.
+template <int K>
+__device__ void load_mat(const float* __restrict__ src, int Kp, int r, float* dst) {
+    using S = Sh<K>;
+    for (int idx = threadIdx.x; idx < S::Kh * K; idx += kT) {
+        const int c = idx / K, i = idx - c * K;
+        dst[c * S::AS + S::pos(i)] = src[(int64_t)(r * S::Kh + c) * Kp + i];
     }
 }
 
-__device__ void load_bt_half(const float* __restrict__ BT, int K, int M, int Kh, int r, float* dst) {
-    for (int idx = threadIdx.x; idx < M * Kh; idx += kT) {
-        int k = idx / Kh, c = idx - k * Kh;
-        dst[idx] = BT[(int64_t)k * K + r * Kh + c];
+template <int K>
+__device__ void load_bt(const float* __restrict__ BT, int M, int r, float* dst) {
+    using S = Sh<K>;
+    for (int idx = threadIdx.x; idx < M * S::Kh; idx += kT) {
+        const int k = idx / S::Kh, c = idx - k * S::Kh;
+        dst[idx] = BT[(int64_t)k * K + r * S::Kh + c];
     }
 }
 
-// Warp reduce-scatter of 16 values: afterwards lane l holds the warp's total of value (l & 15).
-__device__ __forceinline__ float warp_sum16(float (&v)[kG]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 8; k >= 1; k >>= 1) {
-        const bool up = (lane & k) != 0;
-#pragma unroll
-        for (int i = 0; i < k; ++i) {
-            float send = up ? v[i] : v[i + k];
-            float keep = up ? v[i + k] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
-        }
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+template <int K>
+__device__ void zero_vectors(float* sX) {
+    using S = Sh<K>;
+    for (int idx = threadIdx.x; idx < 2 * kG * S::XK; idx += kT) sX[idx] = 0.f;
 }
 
-// acc_g = sum over this thread's i-part of X[g][i] * Ah[i][jl] for all 16 g (rows of
-// inactive sequences are zero); the i-parts are then combined in the epilogue threads
-// (ih == 0) in a fixed order.  Contains a CTA barrier.
-__device__ __forceinline__ void cl_matvec(const float* __restrict__ Ah, const float* __restrict__ X, int K, int Kh,
-                                          float* spart, float (&acc)[kG]) {
-    const int tid = threadIdx.x, jl = tid % Kh, ih = tid / Kh;
-    const int nih = kT / Kh, ipart = K / nih;
+// o[u][h] = sum_i X[p GPT + u][i] At[c_h][i] for the thread's sequences and states.
+template <int K>
+__device__ __forceinline__ void matvec(const float* __restrict__ At, const float* __restrict__ X,
+                                       float (&o)[Sh<K>::GPT][Sh<K>::CW]) {
+    using S = Sh<K>;
+    const int tid = threadIdx.x, lane = tid & 31, p = tid % S::NP, cs = tid / S::NP;
+    float2 acc[kG][S::CW];
 #pragma unroll
-    for (int g = 0; g < kG; ++g) acc[g] = 0.f;
-    const int i0 = ih * ipart;
+    for (int g = 0; g < kG; ++g)
+#pragma unroll
+        for (int h = 0; h < S::CW; ++h) acc[g][h] = make_float2(0.f, 0.f);
+    const float* xb = X + p * (S::IPART + 4);
+    const float* ab = At + cs * S::AS + p * (S::IPART + 4);
 #pragma unroll 2
-    for (int i = i0; i < i0 + ipart; i += 4) {
-        const float a0 = Ah[(i + 0) * Kh + jl], a1 = Ah[(i + 1) * Kh + jl];
-        const float a2 = Ah[(i + 2) * Kh + jl], a3 = Ah[(i + 3) * Kh + jl];
+    for (int r = 0; r < S::IPART; r += 4) {
+        float4 a[S::CW];
+#pragma unroll
+        for (int h = 0; h < S::CW; ++h) a[h] = *reinterpret_cast<const float4*>(ab + h * S::NCS * S::AS + r);
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
-            const float4 x = *reinterpret_cast<const float4*>(X + g * K + i);
-            acc[g] = fmaf(x.x, a0, acc[g]);
-            acc[g] = fmaf(x.y, a1, acc[g]);
-            acc[g] = fmaf(x.z, a2, acc[g]);
-            acc[g] = fmaf(x.w, a3, acc[g]);
+            const float4 x = *reinterpret_cast<const float4*>(xb + g * S::XK + r);
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h) {
+                acc[g][h] = __ffma2_rn(make_float2(x.x, x.y), make_float2(a[h].x, a[h].y), acc[g][h]);
+                acc[g][h] = __ffma2_rn(make_float2(x.z, x.w), make_float2(a[h].z, a[h].w), acc[g][h]);
+            }
         }
     }
-    if (ih > 0) {
+    float s[kG][S::CW];
 #pragma unroll
-        for (int g = 0; g < kG; ++g) spart[((ih - 1) * kG + g) * Kh + jl] = acc[g];
+    for (int g = 0; g < kG; ++g)
+#pragma unroll
+        for (int h = 0; h < S::CW; ++h) s[g][h] = acc[g][h].x + acc[g][h].y;
+    // reduce-scatter over the NP parts: at the stage on lane bit d, the lane with the bit set
+    // keeps the upper half of its remaining sequences and sends the lower half
+#pragma unroll
+    for (int d = S::NP / 2, half = kG / 2; d >= 1; d >>= 1, half >>= 1) {
+        const bool up = (lane & d) != 0;
+#pragma unroll
+        for (int g = 0; g < half; ++g)
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h) {
+                const float send = up ? s[g][h] : s[g + half][h];
+                const float keep = up ? s[g + half][h] : s[g][h];
+                s[g][h] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+            }
     }
-    __syncthreads();
-    if (ih == 0) {
-        for (int q = 1; q < nih; ++q)
 #pragma unroll
-            for (int g = 0; g < kG; ++g) acc[g] += spart[((q - 1) * kG + g) * Kh + jl];
+    for (int u = 0; u < S::GPT; ++u)
+#pragma unroll
+        for (int h = 0; h < S::CW; ++h) o[u][h] = s[u][h];
+}
+
+// Per-warp partial row sums of the thread's sequences -> slot (rank, warp) of parity par, in
+// both CTAs.
+template <int K>
+__device__ __forceinline__ void publish_sums(float (&ps)[Sh<K>::GPT], float* red, float* red_peer, int par, int rank) {
+    using S = Sh<K>;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, p = lane % S::NP;
+#pragma unroll
+    for (int d = S::NP; d < 32; d <<= 1)
+#pragma unroll
+        for (int u = 0; u < S::GPT; ++u) ps[u] += __shfl_xor_sync(0xffffffffu, ps[u], d);
+    if (lane < S::NP) {
+#pragma unroll
+        for (int u = 0; u < S::GPT; ++u) {
+            const int idx = (par * kSlots + rank * 8 + w) * kG + p * S::GPT + u;
+            red[idx] = ps[u];
+            red_peer[idx] = ps[u];
+        }
     }
 }
 
-// CTA partial sums of v[g] over the epilogue threads; thread g < 16 gets sequence g's.
-__device__ __forceinline__ float cta_sum16(float (&v)[kG], float* sred, int Kh) {
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int nwe = Kh / 32;
-    if (w < nwe) {
-        float t = warp_sum16(v);
-        if (lane < kG) sred[w * kG + lane] = t;
-    }
-    __syncthreads();
-    float tot = 0.f;
-    if (tid < kG)
-        for (int q = 0; q < nwe; ++q) tot += sred[q * kG + tid];
-    return tot;
+// Row sum of sequence g from the 16 slots, in a fixed order (both CTAs get the same value).
+__device__ __forceinline__ float row_sum(const float* red, int par, int g) {
+    float c = 0.f;
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) c += red[(par * kSlots + q) * kG + g];
+    return c;
 }
 
 struct Views {
-    float *Ah, *BTh, *sX, *spart, *sR, *csum, *sred, *sX_peer, *csum_peer;
+    float *At, *BTh, *sX, *red, *sX_peer, *red_peer;
 };
 
 __device__ __forceinline__ Views make_views(char* smem, int K, int M, cg::cluster_group& cl, int peer) {
     const SL Ls = smem_layout(K, M);
     Views v;
-    v.Ah = reinterpret_cast<float*>(smem + Ls.ah);
+    v.At = reinterpret_cast<float*>(smem + Ls.at);
     v.BTh = reinterpret_cast<float*>(smem + Ls.bth);
     v.sX = reinterpret_cast<float*>(smem + Ls.sx);
-    v.spart = reinterpret_cast<float*>(smem + Ls.spart);
-    v.sR = reinterpret_cast<float*>(smem + Ls.sr);
-    v.csum = reinterpret_cast<float*>(smem + Ls.csum);
-    v.sred = reinterpret_cast<float*>(smem + Ls.red);
+    v.red = reinterpret_cast<float*>(smem + Ls.red);
     v.sX_peer = cl.map_shared_rank(v.sX, peer);
-    v.csum_peer = cl.map_shared_rank(v.csum, peer);
+    v.red_peer = cl.map_shared_rank(v.red, peer);
     return v;
 }
 
-// One forward step of the 16 sequences: X = sX[cur] (alpha~ of the previous step, scaled by
-// gs.scale), writes alpha~ of this step into sX[nxt] of both CTAs and the partial row sums
-// into csum[nxt] of both, then meets the peer at the cluster barrier.  `active(g)`, `ob`
-// and `scale` come from gs.  Epilogue threads return alpha~ of their state in a[].
-__device__ __forceinline__ void cl_fwd_step(const Views& V, const GS& gs, int K, int Kh, int r, int cur, int nxt,
-                                            uint32_t actmask, cg::cluster_group& cl) {
-    const int tid = threadIdx.x, jl = tid % Kh;
-    const int j = r * Kh + jl;
-    float acc[kG];
-    cl_matvec(V.Ah, V.sX + cur * kG * K, K, Kh, V.spart, acc);
-    if (tid < Kh) {
+// X_t = (A^T-part of S_{t-1}) o b(o_t) for the thread's items: the shared epilogue of the
+// forward and the recomputation.  sc[u] = 2^-e_{t-1}; act(u) says whether the sequence is
+// still running at this step (else its vector is zero).
+template <int K, typename Act>
+__device__ __forceinline__ void fwd_epilogue(const Views& V, const GS& gs, int r, int nxt, int symbuf,
+                                             const float (&o)[Sh<K>::GPT][Sh<K>::CW], const float (&sc)[Sh<K>::GPT],
+                                             Act act) {
+    using S = Sh<K>;
+    const int p = (threadIdx.x & 31) % S::NP, cs = threadIdx.x / S::NP;
+    float ps[S::GPT];
 #pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            float a = 0.f;
-            if ((actmask >> g) & 1u) a = acc[g] * gs.scale[g] * V.BTh[gs.ob[g] * Kh + jl];
-            V.sX[(nxt * kG + g) * K + j] = a;
-            V.sX_peer[(nxt * kG + g) * K + j] = a;
-            acc[g] = a;
+    for (int u = 0; u < S::GPT; ++u) {
+        const int g = p * S::GPT + u;
+        const bool on = act(g);
+        const int ob = gs.sym[symbuf][g];
+        ps[u] = 0.f;
+#pragma unroll
+        for (int h = 0; h < S::CW; ++h) {
+            const int c = cs + h * S::NCS;
+            const float v = on ? o[u][h] * sc[u] * V.BTh[ob * S::Kh + c] : 0.f;
+            const int x = (nxt * kG + g) * S::XK + S::pos(r * S::Kh + c);
+            V.sX[x] = v;
+            V.sX_peer[x] = v;
+            ps[u] += v;
         }
     }
-    const float tot = cta_sum16(acc, V.sred, Kh);
-    if (tid < kG) {
-        V.csum[(nxt * 2 + r) * kG + tid] = tot;
-        V.csum_peer[(nxt * 2 + r) * kG + tid] = tot;
-    }
-    cl.sync();
+    publish_sums<K>(ps, V.red, V.red_peer, nxt, r);
 }
 
 // ---------------------------------------------------------------- forward + checkpoints
+// Step t (1 <= t < Tmax) reads X_{t-1} (parity cur) and the partial sums of its rows,
+// takes e_{t-1} from them, stores checkpoint t-1 where due, and writes X_t (parity nxt) to
+// both CTAs; one cluster barrier per step.  A last pass (t = Tmax) only finishes T-1.
+template <int K>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm p) {
+    using S = Sh<K>;
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
-    const bool epi = tid < Kh;
+    const int tid = threadIdx.x, pp = (tid & 31) % S::NP, cs = tid / S::NP;
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
-    __shared__ int64_t s_Tmax;
-    const Views V = make_views(smem, K, M, cl, peer);
-    load_col_half(p.A, K, p.Kp, Kh, r, V.Ah);
-    load_bt_half(p.BT, K, M, Kh, r, V.BTh);
+    const Views V = make_views(smem, K, p.M, cl, peer);
+    load_mat<K>(p.At, p.Kp, r, V.At);
+    load_bt<K>(p.BT, p.M, r, V.BTh);
     load_gs(p, gs, cidx);
     __syncthreads();
-    if (tid == 0) {
-        int64_t m = 0;
-        for (int g = 0; g < kG; ++g) m = gs.T[g] > m ? gs.T[g] : m;
-        s_Tmax = m;
-    }
+    int ob_next = 0;                      // thread g < 16: o_{t+1} for the next symbol write
     if (tid < kG) {
-        gs.ob[tid] = gs.T[tid] > 0 ? p.obs[gs.o0[tid]] : 0;
-        gs.scale[tid] = 1.f;
+        const int64_t T = gs.T[tid], o0 = gs.o0[tid];
+        gs.sym[0][tid] = T > 0 ? p.obs[o0] : 0;
+        gs.sym[1][tid] = T > 1 ? p.obs[o0 + 1] : 0;
+        ob_next = T > 2 ? p.obs[o0 + 2] : 0;
     }
-    cl.sync();                            // both CTAs started (shared memory ready) and gs visible
-    const int64_t Tmax = s_Tmax;
-    const int j = r * Kh + jl;
-    int64_t E = 0;                        // running exponent sum of sequence tid (tid < 16)
-    // t = 0: alpha~_0 = pi o b(o_0)
-    {
-        float a[kG];
+    int64_t Tmax = 0;
 #pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            a[g] = 0.f;
-            if (epi && gs.T[g] > 0) a[g] = p.pi[j] * V.BTh[gs.ob[g] * Kh + jl];
-            if (epi) { V.sX[g * K + j] = a[g]; V.sX_peer[g * K + j] = a[g]; }
+    for (int g = 0; g < kG; ++g) Tmax = gs.T[g] > Tmax ? gs.T[g] : Tmax;
+    __syncthreads();
+    cl.sync();                            // both CTAs started: shared memory may be written remotely
+    {
+        // t = 0: alpha~_0 = pi o b(o_0)
+        float o[S::GPT][S::CW], sc[S::GPT];
+#pragma unroll
+        for (int u = 0; u < S::GPT; ++u) {
+            sc[u] = 1.f;
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h) o[u][h] = p.pi[r * S::Kh + cs + h * S::NCS];
         }
-        const float tot = cta_sum16(a, V.sred, Kh);
-        if (tid < kG) { V.csum[r * kG + tid] = tot; V.csum_peer[r * kG + tid] = tot; }
+        fwd_epilogue<K>(V, gs, r, 0, 0, o, sc, [&](int g) { return gs.T[g] > 0; });
     }
     cl.sync();
-    // bookkeeping of step 0 (thread g < 16 for sequence g), checkpoint 0
-    if (tid < kG) {
-        const int g = tid;
-        const float c = V.csum[g] + V.csum[kG + g];
-        int ex = 0;
-        frexpf(c, &ex);
-        gs.e[g] = ex;
-        gs.scale[g] = ldexpf(1.0f, -ex);
-        E = ex;
-        if (gs.T[g] > 0) {
-            const int64_t sq = gs.seq[g];
-            if (r == 0) p.cp_e[sq * p.Cmax] = ex;
-            if (r == 0 && gs.T[g] == 1) {
-                p.clast[sq] = c;
-                if (p.loglik) p.loglik[sq] = log((double)c);
-            }
-        }
-        gs.ob[g] = gs.T[g] > 1 ? p.obs[gs.o0[g] + 1] : 0;
-    }
-    __syncthreads();
-    if (epi)
-        for (int g = 0; g < kG; ++g)
-            if (gs.T[g] > 0) p.cp[(gs.seq[g] * p.Cmax) * K + j] = V.sX[g * K + j] * gs.scale[g];
-    for (int64_t t = 1; t < Tmax; ++t) {
-        const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
-        uint32_t actmask = 0;
+    int64_t E[S::GPT];                    // running exponent sums (used by the cs == 0 threads)
 #pragma unroll
-        for (int g = 0; g < kG; ++g) actmask |= (t < gs.T[g] ? 1u : 0u) << g;
-        cl_fwd_step(V, gs, K, Kh, r, cur, nxt, actmask, cl);
-        // bookkeeping (thread g): exponent of this step, logL at the last step, next symbol
-        if (tid < kG) {
-            const int g = tid;
-            if ((actmask >> g) & 1u) {
-                const float c = V.csum[(nxt * 2 + 0) * kG + g] + V.csum[(nxt * 2 + 1) * kG + g];
-                int ex = 0;
-                frexpf(c, &ex);
+    for (int u = 0; u < S::GPT; ++u) E[u] = 0;
+    for (int64_t t = 1; t <= Tmax; ++t) {
+        const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
+        const int64_t tp = t - 1;
+        float sc[S::GPT];
+#pragma unroll
+        for (int u = 0; u < S::GPT; ++u) {
+            const int g = pp * S::GPT + u;
+            const float c = row_sum(V.red, cur, g);
+            int ex = 0;
+            frexpf(c, &ex);
+            sc[u] = ldexpf(1.0f, -ex);
+            const int64_t T = gs.T[g];
+            if (tp < T) {
                 const int64_t sq = gs.seq[g];
-                if (r == 0 && t == gs.T[g] - 1) {
-                    p.clast[sq] = c;
-                    if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E + log((double)c);
+                const int C = gs.C[g];
+                if (cs == 0 && r == 0) {
+                    if (tp % C == 0) p.cp_e[sq * p.Cmax + tp / C] = ex;
+                    if (tp == T - 1) {
+                        p.clast[sq] = c;
+                        if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E[u] + log((double)c);
+                    }
                 }
-                E += ex;
-                gs.e[g] = ex;
-                gs.scale[g] = ldexpf(1.0f, -ex);
-                if (r == 0 && t % gs.C[g] == 0) p.cp_e[sq * p.Cmax + t / gs.C[g]] = ex;
-                gs.ob[g] = t + 1 < gs.T[g] ? p.obs[gs.o0[g] + t + 1] : 0;
+                E[u] += ex;
+                if (tp % C == 0) {
+                    float* row = p.cp + (sq * p.Cmax + tp / C) * K;
+#pragma unroll
+                    for (int h = 0; h < S::CW; ++h) {
+                        const int j = r * S::Kh + cs + h * S::NCS;
+                        row[j] = V.sX[(cur * kG + g) * S::XK + S::pos(j)] * sc[u];
+                    }
+                }
             }
         }
-        __syncthreads();
-        if (epi) {
-#pragma unroll 1
-            for (int g = 0; g < kG; ++g) {
-                if (((actmask >> g) & 1u) && t % gs.C[g] == 0)
-                    p.cp[(gs.seq[g] * p.Cmax + t / gs.C[g]) * K + j] = V.sX[(nxt * kG + g) * K + j] * gs.scale[g];
-            }
+        if (t == Tmax) break;
+        float o[S::GPT][S::CW];
+        matvec<K>(V.At, V.sX + cur * kG * S::XK, o);
+        fwd_epilogue<K>(V, gs, r, nxt, nxt, o, sc, [&](int g) { return t < gs.T[g]; });
+        if (tid < kG) {
+            gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
+            ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
         }
+        cl.sync();
     }
-    cl.sync();   // no CTA leaves while its peer may still write into its shared memory
+    cl.sync();
 }
 
 // ---------------------------------------------------------------- recompute a segment
-// S_t for t in the round's segment into the P rows (normalised), e_t into ebuf.
+// S_t for t in the round's segment into the P rows (normalised), e_t into ebuf; the same
+// step structure as the forward, starting from the checkpoint row (e = its stored
+// exponent, scale 1).
+template <int K>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm p, int round) {
+    using S = Sh<K>;
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
-    const bool epi = tid < Kh;
+    const int tid = threadIdx.x, pp = (tid & 31) % S::NP, cs = tid / S::NP;
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
-    __shared__ int s_maxL;
-    const Views V = make_views(smem, K, M, cl, peer);
+    const Views V = make_views(smem, K, p.M, cl, peer);
     load_gs(p, gs, cidx);
     __syncthreads();
     round_bounds_gs(gs, round);
     __syncthreads();
-    if (tid == 0) {
-        int64_t m = 0;
-        for (int g = 0; g < kG; ++g) m = gs.L[g] > m ? gs.L[g] : m;
-        s_maxL = (int)m;
-    }
-    __syncthreads();
-    const int maxL = s_maxL;
-    const int j = r * Kh + jl;
-    // tt = 0: the checkpoint row itself (both halves read from memory), exponent 0 as alpha~
+    int maxL = 0;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) maxL = gs.L[g] > maxL ? (int)gs.L[g] : maxL;
+    // row 0: the checkpoint itself, into the local vector buffer and the P row
     for (int idx = tid; idx < kG * K; idx += kT) {
         const int g = idx / K, c = idx - g * K;
         float sv = 0.f;
-        if (gs.L[g] > 0) sv = p.cp[(gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]) * K + c];
-        V.sX[g * K + c] = sv;
+        if (gs.L[g] > 0) {
+            sv = p.cp[(gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]) * K + c];
+            if (c / S::Kh == r) p.P[((cidx * kG + g) * p.Cmax) * K + c] = sv;
+        }
+        V.sX[g * S::XK + S::pos(c)] = sv;
     }
-    if (tid < kG && gs.L[tid] > 0) {
+    int ob_next = 0;
+    if (tid < kG) {
         const int g = tid;
-        const int64_t row = (cidx * kG + g) * p.Cmax;
-        if (r == 0) p.ebuf[row] = p.cp_e[gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]];
-        gs.scale[g] = 1.f;
-        gs.ob[g] = gs.L[g] > 1 ? p.obs[gs.o0[g] + gs.t0[g] + 1] : 0;
+        if (gs.L[g] > 0 && r == 0) p.ebuf[(cidx * kG + g) * p.Cmax] = p.cp_e[gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]];
+        const int64_t base = gs.o0[g] + gs.t0[g];
+        gs.sym[1][g] = gs.L[g] > 1 ? p.obs[base + 1] : 0;
+        ob_next = gs.L[g] > 2 ? p.obs[base + 2] : 0;
     }
-    __syncthreads();
-    if (epi)
-        for (int g = 0; g < kG; ++g)
-            if (gs.L[g] > 0) p.P[((cidx * kG + g) * p.Cmax) * K + j] = V.sX[g * K + j];
     if (maxL <= 1) return;                // no remote access made; the peer returns here too
-    load_col_half(p.A, K, p.Kp, Kh, r, V.Ah);
-    load_bt_half(p.BT, K, M, Kh, r, V.BTh);
+    load_mat<K>(p.At, p.Kp, r, V.At);
+    load_bt<K>(p.BT, p.M, r, V.BTh);
+    __syncthreads();
     cl.sync();
-    for (int tt = 1; tt < maxL; ++tt) {
+    for (int tt = 1; tt <= maxL; ++tt) {
         const int cur = (tt - 1) & 1, nxt = tt & 1;
-        uint32_t actmask = 0;
+        float sc[S::GPT];
 #pragma unroll
-        for (int g = 0; g < kG; ++g) actmask |= (tt < gs.L[g] ? 1u : 0u) << g;
-        cl_fwd_step(V, gs, K, Kh, r, cur, nxt, actmask, cl);
-        if (tid < kG && ((actmask >> tid) & 1u)) {
-            const int g = tid;
-            const float c = V.csum[(nxt * 2 + 0) * kG + g] + V.csum[(nxt * 2 + 1) * kG + g];
+        for (int u = 0; u < S::GPT; ++u) {
+            sc[u] = 1.f;
+            if (tt < 2) continue;
+            const int g = pp * S::GPT + u;
+            const float c = row_sum(V.red, cur, g);
             int ex = 0;
             frexpf(c, &ex);
-            gs.scale[g] = ldexpf(1.0f, -ex);
-            if (r == 0) p.ebuf[(cidx * kG + g) * p.Cmax + tt] = ex;
-            gs.ob[g] = tt + 1 < gs.L[g] ? p.obs[gs.o0[g] + gs.t0[g] + tt + 1] : 0;
+            sc[u] = ldexpf(1.0f, -ex);
+            const int tp = tt - 1;
+            if (tp < gs.L[g]) {
+                const int64_t rowi = (cidx * kG + g) * p.Cmax + tp;
+                if (cs == 0 && r == 0) p.ebuf[rowi] = ex;
+#pragma unroll
+                for (int h = 0; h < S::CW; ++h) {
+                    const int j = r * S::Kh + cs + h * S::NCS;
+                    p.P[rowi * K + j] = V.sX[(cur * kG + g) * S::XK + S::pos(j)] * sc[u];
+                }
+            }
         }
-        __syncthreads();
-        if (epi) {
-#pragma unroll 1
-            for (int g = 0; g < kG; ++g)
-                if ((actmask >> g) & 1u)
-                    p.P[((cidx * kG + g) * p.Cmax + tt) * K + j] = V.sX[(nxt * kG + g) * K + j] * gs.scale[g];
+        if (tt == maxL) break;
+        float o[S::GPT][S::CW];
+        matvec<K>(V.At, V.sX + cur * kG * S::XK, o);
+        fwd_epilogue<K>(V, gs, r, nxt, nxt, o, sc, [&](int g) { return tt < gs.L[g]; });
+        if (tid < kG) {
+            gs.sym[cur][tid] = ob_next;
+            ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
         }
+        cl.sync();
     }
     cl.sync();
 }
 
 // ---------------------------------------------------------------- backward over a segment
+// Step tt (from L-1 down to 0) reads v_{t+1} = b(o_{t+1}) o R_{t+1} (parity tt), forms
+// R_t = 2^-e_t A v_{t+1} (or 1/c'_{T-1} at the last step of a sequence) and
+// gamma_t = w 2^e_t S_t o R_t, then writes v_t = b(o_t) o R_t (parity tt-1) to both CTAs
+// together with the Q row of step tt-1; one cluster barrier per step.  R_t stays in the
+// registers of the thread that owns the (sequence, state) pair.
+//   sym(tt) = o_{t0+tt} if t0+tt < T and tt <= L, else -1: the epilogue symbol o_t of an
+//   active step and the symbol of v_t; sym(tt+1) >= 0 says whether step tt is a transition.
+template <int K>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm p, int round) {
+    using S = Sh<K>;
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    const int K = p.K, M = p.M, Kh = K / 2, tid = threadIdx.x, jl = tid % Kh;
-    const bool epi = tid < Kh;
+    const int tid = threadIdx.x, pp = (tid & 31) % S::NP, cs = tid / S::NP;
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
-    __shared__ int s_maxL;
-    __shared__ int s_ot[kG];
-    const Views V = make_views(smem, K, M, cl, peer);
+    const Views V = make_views(smem, K, p.M, cl, peer);
     load_gs(p, gs, cidx);
     __syncthreads();
     round_bounds_gs(gs, round);
     __syncthreads();
-    if (tid == 0) {
-        int64_t m = 0;
-        for (int g = 0; g < kG; ++g) m = gs.L[g] > m ? gs.L[g] : m;
-        s_maxL = (int)m;
+    int maxL = 0;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) maxL = gs.L[g] > maxL ? (int)gs.L[g] : maxL;
+    if (tid < kG && gs.L[tid] > 0) atomicMax(&p.rows[round], (int32_t)((cidx * kG + tid + 1) * p.Cmax));
+    // rows that must read as zero / carry no symbol: all rows of a sequence whose last
+    // segment was done in the previous round, rows past the segment of an active one
+#pragma unroll
+    for (int u = 0; u < S::GPT; ++u) {
+        const int g = pp * S::GPT + u;
+        if (gs.seq[g] < 0 || !(gs.just_done[g] || gs.L[g] > 0)) continue;
+        for (int64_t tt = gs.L[g]; tt < p.Cmax; ++tt)
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h)
+                p.Q[((cidx * kG + g) * p.Cmax + tt) * K + r * S::Kh + cs + h * S::NCS] = 0.f;
     }
-    const int i = r * Kh + jl;            // this thread's state (epilogue threads)
-    if (tid < kG && gs.L[tid] > 0)
-        atomicMax(&p.rows[round], (int32_t)((cidx * kG + tid + 1) * p.Cmax));
-    __syncthreads();
-    const int maxL = s_maxL;
-    // rows that must read as zero (own half): all rows of a sequence whose last segment was
-    // done in the previous round, rows past the segment length of an active one
-    if (epi)
-        for (int g = 0; g < kG; ++g) {
-            if (gs.seq[g] < 0 || !(gs.just_done[g] || gs.L[g] > 0)) continue;
-            for (int64_t tt = gs.L[g]; tt < p.Cmax; ++tt) p.Q[((cidx * kG + g) * p.Cmax + tt) * K + i] = 0.f;
-        }
     if (r == 0 && tid < kG) {
         const int g = tid;
         const int64_t rb = (cidx * kG + g) * p.Cmax;
@@ -913,65 +970,141 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         for (int64_t tt = from; tt < p.Cmax; ++tt) p.osym[rb + tt] = -1;
     }
     if (maxL == 0) return;                // no remote access made; the peer returns here too
-    load_col_half(p.At, K, p.Kp, Kh, r, V.Ah);
-    load_bt_half(p.BT, K, M, Kh, r, V.BTh);
-    if (epi)
-        for (int g = 0; g < kG; ++g) {
-            if (gs.L[g] == 0) continue;
-            const bool last_seg = gs.t0[g] + gs.L[g] == gs.T[g];
-            V.sR[g * Kh + jl] = last_seg ? 0.f : p.Rc[gs.seq[g] * K + i];
+    auto sym_at = [&](int g, int tt) -> int {
+        const int64_t t = gs.t0[g] + tt;
+        return (tt <= gs.L[g] && t < gs.T[g] && gs.seq[g] >= 0) ? p.obs[gs.o0[g] + t] : -1;
+    };
+    auto e_at = [&](int g, int tt) -> int { return tt < gs.L[g] ? p.ebuf[(cidx * kG + g) * p.Cmax + tt] : 0; };
+    int nsym = -1, ne = 0;                // thread g < 16: scalars of step tt-1, loaded one step ahead
+    if (tid < kG) {
+        const int g = tid;
+        gs.sym_end[g] = sym_at(g, maxL);
+        gs.sym[(maxL - 1) & 1][g] = sym_at(g, maxL - 1);
+        gs.eb[(maxL - 1) & 1][g] = e_at(g, maxL - 1);
+        if (maxL >= 2) {
+            nsym = sym_at(g, maxL - 2);
+            ne = e_at(g, maxL - 2);
         }
+    }
+    load_mat<K>(p.A, p.Kp, r, V.At);
+    load_bt<K>(p.BT, p.M, r, V.BTh);
+    zero_vectors<K>(V.sX);
+    __syncthreads();
+    cl.sync();                            // both CTAs started and zeroed before any remote write
+    float R[S::GPT][S::CW];               // R_{t+1} of the thread's pairs
+    int prev_sym[S::GPT];
+#pragma unroll
+    for (int u = 0; u < S::GPT; ++u) {
+        const int g = pp * S::GPT + u;
+        const bool last_seg = gs.t0[g] + gs.L[g] == gs.T[g];
+        prev_sym[u] = gs.sym_end[g];
+#pragma unroll
+        for (int h = 0; h < S::CW; ++h) {
+            const int j = r * S::Kh + cs + h * S::NCS;
+            R[u][h] = (gs.L[g] > 0 && !last_seg) ? p.Rc[gs.seq[g] * K + j] : 0.f;
+        }
+    }
+    // v of step maxL-1 for the sequences whose segment has the full length
+    auto write_v = [&](int tt, int u, int s) {
+        const int g = pp * S::GPT + u;
+        const float w = gs.w[g];
+        float* qrow = p.Q + ((cidx * kG + g) * p.Cmax + tt) * K;
+#pragma unroll
+        for (int h = 0; h < S::CW; ++h) {
+            const int c = cs + h * S::NCS, j = r * S::Kh + c;
+            const float v = s >= 0 ? V.BTh[s * S::Kh + c] * R[u][h] : 0.f;
+            const int x = ((tt & 1) * kG + g) * S::XK + S::pos(j);
+            V.sX[x] = v;
+            V.sX_peer[x] = v;
+            qrow[j] = w * v;
+        }
+    };
+#pragma unroll
+    for (int u = 0; u < S::GPT; ++u)
+        if (maxL - 1 < gs.L[pp * S::GPT + u]) write_v(maxL - 1, u, prev_sym[u]);
     cl.sync();
     for (int tt = maxL - 1; tt >= 0; --tt) {
         const int buf = tt & 1;
-        // per-sequence scalars of this step (thread g): transition?, o_{t+1}, o_t, e_t
-        if (tid < kG) {
-            const int g = tid;
-            const bool act = tt < gs.L[g];
-            const int64_t t = gs.t0[g] + tt;
-            const bool trans = act && t < gs.T[g] - 1;
-            gs.ob[g] = trans ? p.obs[gs.o0[g] + t + 1] : -1;
-            s_ot[g] = act ? p.obs[gs.o0[g] + t] : -1;
-            if (r == 0 && act) p.osym[(cidx * kG + g) * p.Cmax + tt] = s_ot[g];
-            gs.e[g] = act ? p.ebuf[(cidx * kG + g) * p.Cmax + tt] : 0;
-            gs.scale[g] = ldexpf(1.0f, -gs.e[g]);
-        }
-        __syncthreads();
-        if (epi) {
+        int sym[S::GPT], e[S::GPT];
+        float St[S::GPT][S::CW];
 #pragma unroll
-            for (int g = 0; g < kG; ++g) {
-                float vv = 0.f;
-                if (gs.ob[g] >= 0) vv = V.BTh[gs.ob[g] * Kh + jl] * V.sR[g * Kh + jl];
-                V.sX[(buf * kG + g) * K + i] = vv;
-                V.sX_peer[(buf * kG + g) * K + i] = vv;
-                if (s_ot[g] >= 0) p.Q[((cidx * kG + g) * p.Cmax + tt) * K + i] = gs.w[g] * vv;
+        for (int u = 0; u < S::GPT; ++u) {
+            const int g = pp * S::GPT + u;
+            sym[u] = gs.sym[buf][g];
+            e[u] = gs.eb[buf][g];
+            const bool on = tt < gs.L[g];
+            const float* prow = p.P + ((cidx * kG + g) * p.Cmax + tt) * K;
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h) St[u][h] = on ? prow[r * S::Kh + cs + h * S::NCS] : 0.f;
+        }
+        float o[S::GPT][S::CW];
+        matvec<K>(V.At, V.sX + buf * kG * S::XK, o);
+#pragma unroll
+        for (int u = 0; u < S::GPT; ++u) {
+            const int g = pp * S::GPT + u;
+            if (tt >= gs.L[g]) continue;
+            const int64_t rowi = (cidx * kG + g) * p.Cmax + tt;
+            const bool trans = prev_sym[u] >= 0;
+            const float down = ldexpf(1.0f, -e[u]);
+            const float up = gs.w[g] * ldexpf(1.0f, e[u]);
+            const float cinv = trans ? 0.f : 1.0f / p.clast[gs.seq[g]];
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h) {
+                const int j = r * S::Kh + cs + h * S::NCS;
+                const float Rt = trans ? o[u][h] * down : cinv;
+                p.gam[rowi * K + j] = up * St[u][h] * Rt;
+                R[u][h] = Rt;
+            }
+            if (cs == 0 && r == 0) p.osym[rowi] = sym[u];
+        }
+        if (tt > 0) {
+#pragma unroll
+            for (int u = 0; u < S::GPT; ++u)
+                if (tt - 1 < gs.L[pp * S::GPT + u]) write_v(tt - 1, u, sym[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < S::GPT; ++u) prev_sym[u] = sym[u];
+        if (tid < kG && tt > 0) {
+            gs.sym[(tt - 1) & 1][tid] = nsym;
+            gs.eb[(tt - 1) & 1][tid] = ne;
+            if (tt >= 2) {
+                nsym = sym_at(tid, tt - 2);
+                ne = e_at(tid, tt - 2);
             }
         }
         cl.sync();
-        float acc[kG];
-        cl_matvec(V.Ah, V.sX + buf * kG * K, K, Kh, V.spart, acc);
-        if (epi) {
-            float St[kG];
-#pragma unroll
-            for (int g = 0; g < kG; ++g)
-                St[g] = s_ot[g] >= 0 ? p.P[((cidx * kG + g) * p.Cmax + tt) * K + i] : 0.f;
-#pragma unroll
-            for (int g = 0; g < kG; ++g) {
-                if (s_ot[g] < 0) continue;
-                const int64_t row = (cidx * kG + g) * p.Cmax + tt;
-                const float Rt = gs.ob[g] >= 0 ? acc[g] * gs.scale[g] : 1.0f / p.clast[gs.seq[g]];
-                const float gam = gs.w[g] * St[g] * Rt * ldexpf(1.0f, gs.e[g]);
-                p.gam[row * K + i] = gam;
-                if (gs.t0[g] + tt == 0) p.pig[cidx * K + i] += gam;
-                V.sR[g * Kh + jl] = Rt;
-            }
-        }
-        __syncthreads();                  // gs scalars are rewritten at the next step
     }
-    if (epi)
+#pragma unroll
+    for (int u = 0; u < S::GPT; ++u) {
+        const int g = pp * S::GPT + u;
+        if (gs.L[g] > 0)
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h) p.Rc[gs.seq[g] * K + r * S::Kh + cs + h * S::NCS] = R[u][h];
+    }
+    // gamma_0 of the sequences that started in this round, summed in a fixed order by one
+    // thread per state (the gam rows written above are visible after the barrier)
+    __syncthreads();
+    for (int c = tid; c < S::Kh; c += kT) {
+        const int j = r * S::Kh + c;
+        float s = 0.f;
         for (int g = 0; g < kG; ++g)
-            if (gs.L[g] > 0) p.Rc[gs.seq[g] * K + i] = V.sR[g * Kh + jl];
-    cl.sync();
+            if (gs.L[g] > 0 && gs.t0[g] == 0) s += p.gam[((cidx * kG + g) * p.Cmax) * K + j];
+        p.pig[cidx * K + j] += s;
+    }
+}
+
+struct Kernels {
+    void (*fwd)(Prm);
+    void (*rec)(Prm, int);
+    void (*bwd)(Prm, int);
+};
+
+inline Kernels kernels_for(int K) {
+    switch (K) {
+        case 64: return Kernels{k_fwd_cl<64>, k_rec_cl<64>, k_bwd_cl<64>};
+        case 128: return Kernels{k_fwd_cl<128>, k_rec_cl<128>, k_bwd_cl<128>};
+        default: return Kernels{k_fwd_cl<256>, k_rec_cl<256>, k_bwd_cl<256>};
+    }
 }
 
 }  // namespace clu
@@ -1096,21 +1229,22 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
         nlaunch += 3;
         const int nb = (K + adj::kTile - 1) / adj::kTile;
         const size_t sm_c = adj::clu::smem_layout(K, M).total;
-        const bool use_cluster = K % 64 == 0 && sm_c <= (size_t)max_smem_optin();
+        const bool use_cluster = adj::clu::cluster_shape_ok(K) && sm_c <= (size_t)max_smem_optin();
         if (use_cluster) {
             const unsigned grid = (unsigned)(2 * ((S + adj::clu::kG - 1) / adj::clu::kG));
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::clu::k_fwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::clu::k_rec_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::clu::k_bwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
-            adj::clu::k_fwd_cl<<<grid, adj::clu::kT, sm_c, st>>>(p);
+            const adj::clu::Kernels kc = adj::clu::kernels_for(K);
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
+            kc.fwd<<<grid, adj::clu::kT, sm_c, st>>>(p);
             ++nlaunch;
             const size_t sm_cnt = (size_t)M * 256 * 4;
             ACCEL_REQUIRE(sm_cnt <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: M=%d too large", M);
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
             const int nbc = (K + 255) / 256;
             for (int round = 0; round < L.Cmax; ++round) {
-                adj::clu::k_rec_cl<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
-                adj::clu::k_bwd_cl<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
+                kc.rec<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
+                kc.bwd<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
                 adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
                 adj::k_counts<<<nbc * adj::kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, cntp);
                 nlaunch += 4;
