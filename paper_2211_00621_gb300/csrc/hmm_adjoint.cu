@@ -461,20 +461,20 @@ __global__ void __launch_bounds__(256) k_counts(const float* __restrict__ gam, c
 // (A has row stride Kp)
 __global__ void k_finish(const float* __restrict__ A, int Kp, const float* __restrict__ Upart,
                          const float* __restrict__ cnt, const float* __restrict__ cntp, const float* __restrict__ pig,
-                         int K, int M, int64_t ngroups, float* __restrict__ gA, float* __restrict__ gB,
-                         float* __restrict__ gpi) {
+                         int K, int M, int64_t ngroups, int nsU, int nsC, float* __restrict__ gA,
+                         float* __restrict__ gB, float* __restrict__ gpi) {
     int64_t nA = (int64_t)K * K, nB = (int64_t)K * M;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nA + nB + K;
          idx += (int64_t)gridDim.x * blockDim.x) {
         if (idx < nA) {
             float u = 0.f;
-            for (int s = 0; s < kSplit; ++s) u += Upart[(int64_t)s * nA + idx];
+            for (int s = 0; s < nsU; ++s) u += Upart[(int64_t)s * nA + idx];
             gA[idx] = A[(idx / K) * Kp + idx % K] * u;
         } else if (idx < nA + nB) {
             int64_t q = idx - nA;
             float x = 0.f;
             for (int64_t b = 0; b < ngroups; ++b) x += cnt[b * nB + q];
-            for (int b = 0; b < kCntSplit; ++b) x += cntp[(int64_t)b * nB + q];
+            for (int b = 0; b < nsC; ++b) x += cntp[(int64_t)b * nB + q];
             gB[q] = x;
         } else {
             int64_t q = idx - nA - nB;
@@ -1134,12 +1134,13 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.Rc = take((size_t)S * K * 4);
     L.cnt = take((size_t)L.ngroups * K * M * 4);
     L.pig = take((size_t)L.ngroups * K * 4);
-    L.Upart = take((size_t)kSplit * K * K * 4);
+    const int ns_max = xi_tc_supported(K) ? (kXiSplitMax > kSplit ? kXiSplitMax : kSplit) : kSplit;
+    L.Upart = take((size_t)ns_max * K * K * 4);
     L.rows = take((size_t)L.Cmax * 4);
     L.ebuf = take((size_t)S * L.Cmax * 4);
     L.gam = take((size_t)S * L.Cmax * K * 4);
     L.osym = take((size_t)S * L.Cmax * 4);
-    L.cntp = take((size_t)kCntSplit * K * M * 4);
+    L.cntp = take((size_t)(ns_max > kCntSplit ? ns_max : kCntSplit) * K * M * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
     return L;
@@ -1216,20 +1217,28 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     adj::k_prep<<<pg, 256, 0, st>>>(m->log_A, m->log_B, m->log_pi, K, p.Kp, M, (float*)p.A, (float*)p.At,
                                     (float*)p.BT, (float*)p.pi);
     ++nlaunch;
+    const int nb = (K + adj::kTile - 1) / adj::kTile;
+    const size_t sm_c = adj::clu::smem_layout(K, M).total;
+    // the cluster kernels leave the emission counts to the tensor-core kernel or to k_counts
+    // (an [M][256] table in shared memory); otherwise the streaming kernels take the shape
+    const bool counts_fit = xi_tc_counts_supported(K, M) || (size_t)M * 256 * 4 <= (size_t)max_smem_optin();
+    const bool use_cluster = S > 0 && adj::clu::cluster_shape_ok(K) && sm_c <= (size_t)max_smem_optin() && counts_fit;
+    const bool xi_tc = use_cluster && xi_tc_supported(K);
+    const bool counts_tc = xi_tc && xi_tc_counts_supported(K, M);
+    const int nsU = xi_tc ? xi_tc_splits(K) : adj::kSplit;
+    const int nsC = counts_tc ? xi_tc_splits(K) : adj::kCntSplit;
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cnt, 0, (size_t)L.ngroups * K * M * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.pig, 0, (size_t)L.ngroups * K * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)adj::kSplit * K * K * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)nsU * K * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.rows, 0, (size_t)L.Cmax * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cntp, 0, (size_t)adj::kCntSplit * K * M * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cntp, 0, (size_t)nsC * K * M * 4, st));
+    if (counts_tc) ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.gam, 0, (size_t)S * L.Cmax * K * 4, st));
     if (S > 0) {
         r = order_by_length(d_offsets, S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)S * 4, 256), st);
         if (r != ACCEL_OK) return r;
         nlaunch += 3;
-        const int nb = (K + adj::kTile - 1) / adj::kTile;
-        const size_t sm_c = adj::clu::smem_layout(K, M).total;
-        const bool use_cluster = adj::clu::cluster_shape_ok(K) && sm_c <= (size_t)max_smem_optin();
         if (use_cluster) {
             const unsigned grid = (unsigned)(2 * ((S + adj::clu::kG - 1) / adj::clu::kG));
             const adj::clu::Kernels kc = adj::clu::kernels_for(K);
@@ -1239,15 +1248,28 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             kc.fwd<<<grid, adj::clu::kT, sm_c, st>>>(p);
             ++nlaunch;
             const size_t sm_cnt = (size_t)M * 256 * 4;
-            ACCEL_REQUIRE(sm_cnt <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: M=%d too large", M);
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
+            if (!counts_tc) {
+                ACCEL_REQUIRE(sm_cnt <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: M=%d too large", M);
+                ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
+            }
             const int nbc = (K + 255) / 256;
             for (int round = 0; round < L.Cmax; ++round) {
                 kc.rec<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
                 kc.bwd<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
-                adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
-                adj::k_counts<<<nbc * adj::kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, cntp);
-                nlaunch += 4;
+                nlaunch += 2;
+                if (xi_tc) {
+                    r = xi_tc_round(p.P, p.Q, p.gam, p.osym, p.rows + round, K, M, Upart, counts_tc ? cntp : nullptr,
+                                    p.status, st);
+                    if (r != ACCEL_OK) return r;
+                    ++nlaunch;
+                } else {
+                    adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
+                    ++nlaunch;
+                }
+                if (!counts_tc) {
+                    adj::k_counts<<<nbc * adj::kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, cntp);
+                    ++nlaunch;
+                }
             }
         } else {
             size_t sm_f = adj::smem_fwd(K, M);
@@ -1262,7 +1284,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             }
         }
     }
-    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, cntp, p.pig, K, M, L.ngroups, d_grad_log_A,
+    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, cntp, p.pig, K, M, L.ngroups, nsU, nsC, d_grad_log_A,
                                       d_grad_log_B, d_grad_log_pi);
     ++nlaunch;
     r = after_launch(st, "hmm_adjoint", nlaunch);
