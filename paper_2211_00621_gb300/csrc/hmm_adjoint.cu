@@ -499,55 +499,42 @@ namespace clu {
 namespace cg = cooperative_groups;
 
 constexpr int kG = 16;      // sequences per cluster
-constexpr int kT = 256;     // threads per CTA
-constexpr int kSlots = 16;  // partial row sums per sequence: 2 CTAs x 8 warps
+constexpr int kT = 256;     // threads per CTA (8 warps)
+constexpr int kNW = 8;
 
-// Work split for K in {64, 128, 256}.  Each CTA of the pair owns Kh = K/2 states.  Thread
-// tid = cs NP + p owns the CW states c_h = cs + h NCS (h < CW) of its CTA's half and the
-// i-part p of the contraction (rows p IPART .. p IPART + IPART - 1).  The NP parts of a
-// column slot are neighbouring lanes; after the contraction they are combined by a
-// reduce-scatter of xor shuffles, which leaves lane p with the sums of sequences
-// g = p GPT + u (u < GPT) -- the sequences it then handles in the epilogue.
-//
-// The contraction pairs rows, not columns: the accumulator of (g, c) is a float2 holding
-// the even-row and odd-row partial sums, so both operands of each packed FMA are natural
-// register pairs (x[g][i], x[g][i+1]) and (a[i][c], a[i+1][c]); the matrix half is kept
-// transposed (a row per owned state) for that.  Rows of both shared arrays are skewed by
-// 16 bytes per i-part so that the lanes of a warp hit distinct banks.
-struct Geo {
-    int Kh, CW, NCS, NP, IPART, GPT, XK, AS;
-};
-__host__ __device__ constexpr Geo geo(int K) {
-    return Geo{K / 2,
-               K >= 128 ? 4 : 2,
-               (K / 2) / (K >= 128 ? 4 : 2),
-               kT / ((K / 2) / (K >= 128 ? 4 : 2)),
-               K / (kT / ((K / 2) / (K >= 128 ? 4 : 2))),
-               kG / (kT / ((K / 2) / (K >= 128 ? 4 : 2))),
-               K + 4 * (kT / ((K / 2) / (K >= 128 ? 4 : 2))),
-               K + 4 * (kT / ((K / 2) / (K >= 128 ? 4 : 2))) + 4};
-}
-__host__ __device__ inline bool cluster_shape_ok(int K) { return K == 64 || K == 128 || K == 256; }
-
+// Work split for K in {64, 128, 256}.  Each CTA of the pair owns Kh = K/2 states (output
+// columns of the contraction out[g][j] = sum_i X[g][i] Mx[i][j]).
+//  * Contraction: warp w takes the i-part w (rows w IPART .. w IPART + IPART - 1) and lane l
+//    the CW = Kh/32 columns l CW .. l CW + CW - 1.  The thread's IPART x CW block of the
+//    matrix is loaded into registers once per kernel, so the step reads only the vectors
+//    from shared memory, and those as whole-warp broadcasts (every lane of a warp reads the
+//    same address).  Packed FMAs: for CW = 4 the column pairs (c, c+1) are the packed
+//    operand (the vector value is broadcast); for CW <= 2 the row pairs (i, i+1) are, with
+//    even- and odd-row partial sums added at the end.
+//  * The eight warps' partial outputs meet in shared memory (fixed order: deterministic).
+//  * Epilogue: thread t takes sequence g = t / 16 and the EC = Kh/16 consecutive states
+//    (t % 16) EC .. +EC - 1, so vector, row and parameter accesses are 8-16 byte vectors.
 template <int K>
 struct Sh {
-    static constexpr Geo G = geo(K);
-    static constexpr int Kh = G.Kh, CW = G.CW, NCS = G.NCS, NP = G.NP, IPART = G.IPART, GPT = G.GPT, XK = G.XK,
-                         AS = G.AS;
-    static_assert(IPART % 4 == 0 && NP <= 16 && GPT >= 1 && NP * GPT == kG, "unsupported split");
-    __device__ static int pos(int i) { return i + (i / IPART) * 4; }   // skewed position of element i
+    static constexpr int Kh = K / 2;
+    static constexpr int IPART = K / kNW;
+    static constexpr int CW = Kh / 32;
+    static constexpr bool RP = CW <= 2;
+    static constexpr int EC = Kh / 16;
+    static_assert(IPART % 4 == 0 && (CW == 4 || CW == 2 || CW == 1) && EC % 2 == 0, "unsupported K");
 };
+__host__ __device__ inline bool cluster_shape_ok(int K) { return K == 64 || K == 128 || K == 256; }
 
-struct SL { size_t at, bth, sx, red, total; };
+struct SL { size_t bth, sx, part, red, total; };
 
 __host__ __device__ inline SL smem_layout(int K, int M) {
-    const Geo G = geo(K);
+    const int Kh = K / 2;
     SL L;
     size_t o = 0;
-    L.at = o;    o += (size_t)G.Kh * G.AS * 4;            // owned matrix columns, transposed [Kh][AS]
-    L.bth = o;   o += (size_t)M * G.Kh * 4;               // emission columns [M][Kh]
-    L.sx = o;    o += (size_t)2 * kG * G.XK * 4;          // full vectors, two step parities [2][16][XK]
-    L.red = o;   o += (size_t)2 * kSlots * kG * 4;        // partial row sums [2][16 slots][16]
+    L.bth = o;   o += (size_t)M * Kh * 4;                 // emission columns [M][Kh]
+    L.sx = o;    o += (size_t)2 * kG * K * 4;             // full vectors, two step parities [2][16][K]
+    L.part = o;  o += (size_t)kNW * kG * Kh * 4;          // per-warp partial outputs [8][16][Kh]
+    L.red = o;   o += (size_t)2 * 2 * kG * 4;             // partial row sums [parity][rank][16]
     L.total = o;
     return L;
 }
@@ -604,172 +591,226 @@ __device__ void round_bounds_gs(GS& gs, int r) {
     }
 }
 
-// dst[c][pos(i)] = src[(r Kh + c) Kp + i]: the CTA's states as rows of the contraction.
-template <int K>
-__device__ void load_mat(const float* __restrict__ src, int Kp, int r, float* dst) {
-    using S = Sh<K>;
-    for (int idx = threadIdx.x; idx < S::Kh * K; idx += kT) {
-        const int c = idx / K, i = idx - c * K;
-        dst[c * S::AS + S::pos(i)] = src[(int64_t)(r * S::Kh + c) * Kp + i];
-    }
-}
-
+// dst[k][c] = BT[k][r Kh + c]
 template <int K>
 __device__ void load_bt(const float* __restrict__ BT, int M, int r, float* dst) {
     using S = Sh<K>;
-    for (int idx = threadIdx.x; idx < M * S::Kh; idx += kT) {
-        const int k = idx / S::Kh, c = idx - k * S::Kh;
-        dst[idx] = BT[(int64_t)k * K + r * S::Kh + c];
+    constexpr int Q = S::Kh / 4;
+    const int N = M * Q;
+    for (int b0 = threadIdx.x; b0 < N; b0 += kT * 8) {
+        float4 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = b0 + e * kT;
+            if (idx < N) v[e] = *reinterpret_cast<const float4*>(BT + (int64_t)(idx / Q) * K + r * S::Kh + 4 * (idx % Q));
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = b0 + e * kT;
+            if (idx < N) *reinterpret_cast<float4*>(dst + 4 * idx) = v[e];
+        }
     }
 }
 
+// The thread's block of the contraction matrix Mx[i][r Kh + c] (row stride Kp), i in its
+// warp's part, c in its lane's columns, as packed pairs (see Sh).
 template <int K>
-__device__ void zero_vectors(float* sX) {
+struct MatRegs {
     using S = Sh<K>;
-    for (int idx = threadIdx.x; idx < 2 * kG * S::XK; idx += kT) sX[idx] = 0.f;
-}
+    // CW = 4: a[i][0] = (Mx[i][c0], Mx[i][c0+1]), a[i][1] = (Mx[i][c0+2], Mx[i][c0+3])
+    // CW <= 2: a[q][h] = (Mx[2q][c0+h], Mx[2q+1][c0+h])
+    static constexpr int N0 = S::RP ? S::IPART / 2 : S::IPART;
+    static constexpr int N1 = S::RP ? S::CW : 2;
+    float2 a[N0][N1];
 
-// o[u][h] = sum_i X[p GPT + u][i] At[c_h][i] for the thread's sequences and states.
+    __device__ void load(const float* __restrict__ Mx, int Kp, int r) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const float* base = Mx + (int64_t)(w * S::IPART) * Kp + r * S::Kh + lane * S::CW;
+        if constexpr (!S::RP) {
+#pragma unroll
+            for (int i = 0; i < S::IPART; ++i) {
+                const float4 v = *reinterpret_cast<const float4*>(base + (int64_t)i * Kp);
+                a[i][0] = make_float2(v.x, v.y);
+                a[i][1] = make_float2(v.z, v.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < S::IPART / 2; ++q)
+#pragma unroll
+                for (int h = 0; h < S::CW; ++h)
+                    a[q][h] = make_float2(base[(int64_t)(2 * q) * Kp + h], base[(int64_t)(2 * q + 1) * Kp + h]);
+        }
+    }
+};
+
+// part[w][g][lane CW + h] = sum_{i in part w} X[g][i] Mx[i][lane CW + h], for all 16 g.
 template <int K>
-__device__ __forceinline__ void matvec(const float* __restrict__ At, const float* __restrict__ X,
-                                       float (&o)[Sh<K>::GPT][Sh<K>::CW]) {
+__device__ __forceinline__ void contract(const MatRegs<K>& m, const float* __restrict__ X, float* __restrict__ part) {
     using S = Sh<K>;
-    const int tid = threadIdx.x, lane = tid & 31, p = tid % S::NP, cs = tid / S::NP;
-    float2 acc[kG][S::CW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float* xb = X + w * S::IPART;
+    float* pb = part + (w * kG) * S::Kh + lane * S::CW;
+    if constexpr (!S::RP) {
+        float2 acc[kG][2];
 #pragma unroll
-    for (int g = 0; g < kG; ++g)
+        for (int g = 0; g < kG; ++g) acc[g][0] = acc[g][1] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int h = 0; h < S::CW; ++h) acc[g][h] = make_float2(0.f, 0.f);
-    const float* xb = X + p * (S::IPART + 4);
-    const float* ab = At + cs * S::AS + p * (S::IPART + 4);
-#pragma unroll 2
-    for (int r = 0; r < S::IPART; r += 4) {
-        float4 a[S::CW];
+        for (int q = 0; q < S::IPART / 4; ++q) {
 #pragma unroll
-        for (int h = 0; h < S::CW; ++h) a[h] = *reinterpret_cast<const float4*>(ab + h * S::NCS * S::AS + r);
+            for (int g = 0; g < kG; ++g) {
+                const float4 x = *reinterpret_cast<const float4*>(xb + g * K + 4 * q);
+                const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 xx = make_float2(xs[e], xs[e]);
+                    acc[g][0] = __ffma2_rn(xx, m.a[4 * q + e][0], acc[g][0]);
+                    acc[g][1] = __ffma2_rn(xx, m.a[4 * q + e][1], acc[g][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+            *reinterpret_cast<float4*>(pb + g * S::Kh) = make_float4(acc[g][0].x, acc[g][0].y, acc[g][1].x, acc[g][1].y);
+    } else {
+        float2 acc[kG][S::CW];
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+#pragma unroll
+            for (int h = 0; h < S::CW; ++h) acc[g][h] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < S::IPART / 4; ++q) {
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                const float4 x = *reinterpret_cast<const float4*>(xb + g * K + 4 * q);
+#pragma unroll
+                for (int h = 0; h < S::CW; ++h) {
+                    acc[g][h] = __ffma2_rn(make_float2(x.x, x.y), m.a[2 * q][h], acc[g][h]);
+                    acc[g][h] = __ffma2_rn(make_float2(x.z, x.w), m.a[2 * q + 1][h], acc[g][h]);
+                }
+            }
+        }
 #pragma unroll
         for (int g = 0; g < kG; ++g) {
-            const float4 x = *reinterpret_cast<const float4*>(xb + g * S::XK + r);
-#pragma unroll
-            for (int h = 0; h < S::CW; ++h) {
-                acc[g][h] = __ffma2_rn(make_float2(x.x, x.y), make_float2(a[h].x, a[h].y), acc[g][h]);
-                acc[g][h] = __ffma2_rn(make_float2(x.z, x.w), make_float2(a[h].z, a[h].w), acc[g][h]);
-            }
+            if constexpr (S::CW == 2)
+                *reinterpret_cast<float2*>(pb + g * S::Kh) =
+                    make_float2(acc[g][0].x + acc[g][0].y, acc[g][1].x + acc[g][1].y);
+            else
+                pb[g * S::Kh] = acc[g][0].x + acc[g][0].y;
         }
     }
-    float s[kG][S::CW];
-#pragma unroll
-    for (int g = 0; g < kG; ++g)
-#pragma unroll
-        for (int h = 0; h < S::CW; ++h) s[g][h] = acc[g][h].x + acc[g][h].y;
-    // reduce-scatter over the NP parts: at the stage on lane bit d, the lane with the bit set
-    // keeps the upper half of its remaining sequences and sends the lower half
-#pragma unroll
-    for (int d = S::NP / 2, half = kG / 2; d >= 1; d >>= 1, half >>= 1) {
-        const bool up = (lane & d) != 0;
-#pragma unroll
-        for (int g = 0; g < half; ++g)
-#pragma unroll
-            for (int h = 0; h < S::CW; ++h) {
-                const float send = up ? s[g][h] : s[g + half][h];
-                const float keep = up ? s[g + half][h] : s[g][h];
-                s[g][h] = keep + __shfl_xor_sync(0xffffffffu, send, d);
-            }
-    }
-#pragma unroll
-    for (int u = 0; u < S::GPT; ++u)
-#pragma unroll
-        for (int h = 0; h < S::CW; ++h) o[u][h] = s[u][h];
 }
 
-// Per-warp partial row sums of the thread's sequences -> slot (rank, warp) of parity par, in
-// both CTAs.
+// EC consecutive floats <-> registers (EC is a multiple of 2; 16-byte pieces where possible).
+template <int EC>
+__device__ __forceinline__ void ldv(const float* __restrict__ src, float (&v)[EC]) {
+    if constexpr (EC % 4 == 0) {
+#pragma unroll
+        for (int e = 0; e < EC; e += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(src + e);
+            v[e] = x.x; v[e + 1] = x.y; v[e + 2] = x.z; v[e + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < EC; e += 2) {
+            const float2 x = *reinterpret_cast<const float2*>(src + e);
+            v[e] = x.x; v[e + 1] = x.y;
+        }
+    }
+}
+template <int EC>
+__device__ __forceinline__ void stv(float* dst, const float (&v)[EC]) {
+    if constexpr (EC % 4 == 0) {
+#pragma unroll
+        for (int e = 0; e < EC; e += 4) *reinterpret_cast<float4*>(dst + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < EC; e += 2) *reinterpret_cast<float2*>(dst + e) = make_float2(v[e], v[e + 1]);
+    }
+}
+
+// o = sum over the 8 warps' partials of the thread's epilogue outputs (fixed order).
 template <int K>
-__device__ __forceinline__ void publish_sums(float (&ps)[Sh<K>::GPT], float* red, float* red_peer, int par, int rank) {
+__device__ __forceinline__ void gather(const float* __restrict__ part, int g, int c0, float (&o)[Sh<K>::EC]) {
     using S = Sh<K>;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, p = lane % S::NP;
+    ldv<S::EC>(part + g * S::Kh + c0, o);
 #pragma unroll
-    for (int d = S::NP; d < 32; d <<= 1)
+    for (int w = 1; w < kNW; ++w) {
+        float v[S::EC];
+        ldv<S::EC>(part + (w * kG + g) * S::Kh + c0, v);
 #pragma unroll
-        for (int u = 0; u < S::GPT; ++u) ps[u] += __shfl_xor_sync(0xffffffffu, ps[u], d);
-    if (lane < S::NP) {
-#pragma unroll
-        for (int u = 0; u < S::GPT; ++u) {
-            const int idx = (par * kSlots + rank * 8 + w) * kG + p * S::GPT + u;
-            red[idx] = ps[u];
-            red_peer[idx] = ps[u];
-        }
+        for (int e = 0; e < S::EC; ++e) o[e] += v[e];
     }
-}
-
-// Row sum of sequence g from the 16 slots, in a fixed order (both CTAs get the same value).
-__device__ __forceinline__ float row_sum(const float* red, int par, int g) {
-    float c = 0.f;
-#pragma unroll
-    for (int q = 0; q < kSlots; ++q) c += red[(par * kSlots + q) * kG + g];
-    return c;
 }
 
 struct Views {
-    float *At, *BTh, *sX, *red, *sX_peer, *red_peer;
+    float *BTh, *sX, *part, *red, *sX_peer, *red_peer;
 };
 
 __device__ __forceinline__ Views make_views(char* smem, int K, int M, cg::cluster_group& cl, int peer) {
     const SL Ls = smem_layout(K, M);
     Views v;
-    v.At = reinterpret_cast<float*>(smem + Ls.at);
     v.BTh = reinterpret_cast<float*>(smem + Ls.bth);
     v.sX = reinterpret_cast<float*>(smem + Ls.sx);
+    v.part = reinterpret_cast<float*>(smem + Ls.part);
     v.red = reinterpret_cast<float*>(smem + Ls.red);
     v.sX_peer = cl.map_shared_rank(v.sX, peer);
     v.red_peer = cl.map_shared_rank(v.red, peer);
     return v;
 }
 
-// X_t = (A^T-part of S_{t-1}) o b(o_t) for the thread's items: the shared epilogue of the
-// forward and the recomputation.  sc[u] = 2^-e_{t-1}; act(u) says whether the sequence is
-// still running at this step (else its vector is zero).
-template <int K, typename Act>
-__device__ __forceinline__ void fwd_epilogue(const Views& V, const GS& gs, int r, int nxt, int symbuf,
-                                             const float (&o)[Sh<K>::GPT][Sh<K>::CW], const float (&sc)[Sh<K>::GPT],
-                                             Act act) {
-    using S = Sh<K>;
-    const int p = (threadIdx.x & 31) % S::NP, cs = threadIdx.x / S::NP;
-    float ps[S::GPT];
+// Sum over the 16 threads of a sequence (a half warp), published as slot (rank) of parity
+// par in both CTAs.
+__device__ __forceinline__ void publish_sum(float ps, const Views& V, int par, int rank, int g) {
 #pragma unroll
-    for (int u = 0; u < S::GPT; ++u) {
-        const int g = p * S::GPT + u;
-        const bool on = act(g);
-        const int ob = gs.sym[symbuf][g];
-        ps[u] = 0.f;
-#pragma unroll
-        for (int h = 0; h < S::CW; ++h) {
-            const int c = cs + h * S::NCS;
-            const float v = on ? o[u][h] * sc[u] * V.BTh[ob * S::Kh + c] : 0.f;
-            const int x = (nxt * kG + g) * S::XK + S::pos(r * S::Kh + c);
-            V.sX[x] = v;
-            V.sX_peer[x] = v;
-            ps[u] += v;
-        }
+    for (int d = 1; d < 16; d <<= 1) ps += __shfl_xor_sync(0xffffffffu, ps, d);
+    if ((threadIdx.x & 15) == 0) {
+        const int idx = (par * 2 + rank) * kG + g;
+        V.red[idx] = ps;
+        V.red_peer[idx] = ps;
     }
-    publish_sums<K>(ps, V.red, V.red_peer, nxt, r);
+}
+
+__device__ __forceinline__ float row_sum(const float* red, int par, int g) {
+    return red[(par * 2) * kG + g] + red[(par * 2 + 1) * kG + g];
+}
+
+// X_t = o * sc o b(ob) (or zero when the sequence has ended) into parity nxt of both CTAs,
+// and its row sum.
+template <int K>
+__device__ __forceinline__ void fwd_epilogue(const Views& V, int r, int nxt, int g, int c0, bool on, int ob,
+                                             const float (&o)[Sh<K>::EC], float sc) {
+    using S = Sh<K>;
+    float b[S::EC], v[S::EC];
+    ldv<S::EC>(V.BTh + ob * S::Kh + c0, b);
+    float ps = 0.f;
+#pragma unroll
+    for (int e = 0; e < S::EC; ++e) {
+        v[e] = on ? o[e] * sc * b[e] : 0.f;
+        ps += v[e];
+    }
+    const int x = (nxt * kG + g) * K + r * S::Kh + c0;
+    stv<S::EC>(V.sX + x, v);
+    stv<S::EC>(V.sX_peer + x, v);
+    publish_sum(ps, V, nxt, r, g);
 }
 
 // ---------------------------------------------------------------- forward + checkpoints
-// Step t (1 <= t < Tmax) reads X_{t-1} (parity cur) and the partial sums of its rows,
-// takes e_{t-1} from them, stores checkpoint t-1 where due, and writes X_t (parity nxt) to
-// both CTAs; one cluster barrier per step.  A last pass (t = Tmax) only finishes T-1.
+// Step t (1 <= t < Tmax) reads X_{t-1} (parity cur) and the row sums of X_{t-1}, takes
+// e_{t-1} from them, stores checkpoint t-1 where due, and writes X_t (parity nxt) to both
+// CTAs; one cluster barrier per step.  A last pass (t = Tmax) only finishes T-1.
 template <int K>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm p) {
     using S = Sh<K>;
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    const int tid = threadIdx.x, pp = (tid & 31) % S::NP, cs = tid / S::NP;
+    const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
+    const bool lead = (tid & 15) == 0;    // one thread per sequence
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
     const Views V = make_views(smem, K, p.M, cl, peer);
-    load_mat<K>(p.At, p.Kp, r, V.At);
+    MatRegs<K> m;
+    m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
     load_gs(p, gs, cidx);
     __syncthreads();
@@ -782,61 +823,58 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     }
     int64_t Tmax = 0;
 #pragma unroll
-    for (int g = 0; g < kG; ++g) Tmax = gs.T[g] > Tmax ? gs.T[g] : Tmax;
+    for (int q = 0; q < kG; ++q) Tmax = gs.T[q] > Tmax ? gs.T[q] : Tmax;
+    const int64_t Tg = gs.T[g], base = gs.seq[g] * p.Cmax;
+    const int Cg = gs.C[g];
     __syncthreads();
     cl.sync();                            // both CTAs started: shared memory may be written remotely
     {
         // t = 0: alpha~_0 = pi o b(o_0)
-        float o[S::GPT][S::CW], sc[S::GPT];
-#pragma unroll
-        for (int u = 0; u < S::GPT; ++u) {
-            sc[u] = 1.f;
-#pragma unroll
-            for (int h = 0; h < S::CW; ++h) o[u][h] = p.pi[r * S::Kh + cs + h * S::NCS];
-        }
-        fwd_epilogue<K>(V, gs, r, 0, 0, o, sc, [&](int g) { return gs.T[g] > 0; });
+        float o[S::EC];
+        ldv<S::EC>(p.pi + r * S::Kh + c0, o);
+        fwd_epilogue<K>(V, r, 0, g, c0, Tg > 0, gs.sym[0][g], o, 1.f);
     }
     cl.sync();
-    int64_t E[S::GPT];                    // running exponent sums (used by the cs == 0 threads)
-#pragma unroll
-    for (int u = 0; u < S::GPT; ++u) E[u] = 0;
+    // the sequence's running exponent sum (used by the lead threads), steps to the next
+    // checkpoint and its index
+    int64_t E = 0;
+    int cp_left = 0, cp_idx = 0;
     for (int64_t t = 1; t <= Tmax; ++t) {
         const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
         const int64_t tp = t - 1;
-        float sc[S::GPT];
-#pragma unroll
-        for (int u = 0; u < S::GPT; ++u) {
-            const int g = pp * S::GPT + u;
-            const float c = row_sum(V.red, cur, g);
-            int ex = 0;
-            frexpf(c, &ex);
-            sc[u] = ldexpf(1.0f, -ex);
-            const int64_t T = gs.T[g];
-            if (tp < T) {
-                const int64_t sq = gs.seq[g];
-                const int C = gs.C[g];
-                if (cs == 0 && r == 0) {
-                    if (tp % C == 0) p.cp_e[sq * p.Cmax + tp / C] = ex;
-                    if (tp == T - 1) {
-                        p.clast[sq] = c;
-                        if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E[u] + log((double)c);
-                    }
+        const float c = row_sum(V.red, cur, g);
+        int ex = 0;
+        frexpf(c, &ex);
+        const float sc = ldexpf(1.0f, -ex);
+        if (tp < Tg) {
+            const bool due = cp_left == 0;
+            if (lead && r == 0) {
+                if (due) p.cp_e[base + cp_idx] = ex;
+                if (tp == Tg - 1) {
+                    const int64_t sq = gs.seq[g];
+                    p.clast[sq] = c;
+                    if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E + log((double)c);
                 }
-                E[u] += ex;
-                if (tp % C == 0) {
-                    float* row = p.cp + (sq * p.Cmax + tp / C) * K;
+            }
+            E += ex;
+            if (due) {
+                float v[S::EC];
+                ldv<S::EC>(V.sX + (cur * kG + g) * K + r * S::Kh + c0, v);
 #pragma unroll
-                    for (int h = 0; h < S::CW; ++h) {
-                        const int j = r * S::Kh + cs + h * S::NCS;
-                        row[j] = V.sX[(cur * kG + g) * S::XK + S::pos(j)] * sc[u];
-                    }
-                }
+                for (int e = 0; e < S::EC; ++e) v[e] *= sc;
+                stv<S::EC>(p.cp + (base + cp_idx) * K + r * S::Kh + c0, v);
+                ++cp_idx;
+                cp_left = Cg - 1;
+            } else {
+                --cp_left;
             }
         }
         if (t == Tmax) break;
-        float o[S::GPT][S::CW];
-        matvec<K>(V.At, V.sX + cur * kG * S::XK, o);
-        fwd_epilogue<K>(V, gs, r, nxt, nxt, o, sc, [&](int g) { return t < gs.T[g]; });
+        contract<K>(m, V.sX + cur * kG * K, V.part);
+        __syncthreads();
+        float o[S::EC];
+        gather<K>(V.part, g, c0, o);
+        fwd_epilogue<K>(V, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
         if (tid < kG) {
             gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
             ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
@@ -856,7 +894,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    const int tid = threadIdx.x, pp = (tid & 31) % S::NP, cs = tid / S::NP;
+    const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
+    const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
     const Views V = make_views(smem, K, p.M, cl, peer);
@@ -866,57 +905,57 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     __syncthreads();
     int maxL = 0;
 #pragma unroll
-    for (int g = 0; g < kG; ++g) maxL = gs.L[g] > maxL ? (int)gs.L[g] : maxL;
+    for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
+    const int Lg = (int)gs.L[g];
+    const int64_t rowb = (cidx * kG + g) * p.Cmax;
     // row 0: the checkpoint itself, into the local vector buffer and the P row
-    for (int idx = tid; idx < kG * K; idx += kT) {
-        const int g = idx / K, c = idx - g * K;
-        float sv = 0.f;
-        if (gs.L[g] > 0) {
-            sv = p.cp[(gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]) * K + c];
-            if (c / S::Kh == r) p.P[((cidx * kG + g) * p.Cmax) * K + c] = sv;
+    for (int idx = tid; idx < kG * K / 4; idx += kT) {
+        const int gg = idx / (K / 4), cc = 4 * (idx - gg * (K / 4));
+        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gs.L[gg] > 0) {
+            sv = *reinterpret_cast<const float4*>(p.cp + (gs.seq[gg] * p.Cmax + gs.t0[gg] / gs.C[gg]) * K + cc);
+            if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + ((cidx * kG + gg) * p.Cmax) * K + cc) = sv;
         }
-        V.sX[g * S::XK + S::pos(c)] = sv;
+        *reinterpret_cast<float4*>(V.sX + gg * K + cc) = sv;
     }
     int ob_next = 0;
     if (tid < kG) {
-        const int g = tid;
-        if (gs.L[g] > 0 && r == 0) p.ebuf[(cidx * kG + g) * p.Cmax] = p.cp_e[gs.seq[g] * p.Cmax + gs.t0[g] / gs.C[g]];
-        const int64_t base = gs.o0[g] + gs.t0[g];
-        gs.sym[1][g] = gs.L[g] > 1 ? p.obs[base + 1] : 0;
-        ob_next = gs.L[g] > 2 ? p.obs[base + 2] : 0;
+        const int q = tid;
+        if (gs.L[q] > 0 && r == 0) p.ebuf[(cidx * kG + q) * p.Cmax] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
+        const int64_t b0 = gs.o0[q] + gs.t0[q];
+        gs.sym[1][q] = gs.L[q] > 1 ? p.obs[b0 + 1] : 0;
+        ob_next = gs.L[q] > 2 ? p.obs[b0 + 2] : 0;
     }
     if (maxL <= 1) return;                // no remote access made; the peer returns here too
-    load_mat<K>(p.At, p.Kp, r, V.At);
+    MatRegs<K> m;
+    m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
     __syncthreads();
     cl.sync();
     for (int tt = 1; tt <= maxL; ++tt) {
         const int cur = (tt - 1) & 1, nxt = tt & 1;
-        float sc[S::GPT];
-#pragma unroll
-        for (int u = 0; u < S::GPT; ++u) {
-            sc[u] = 1.f;
-            if (tt < 2) continue;
-            const int g = pp * S::GPT + u;
+        float sc = 1.f;
+        if (tt >= 2) {
             const float c = row_sum(V.red, cur, g);
             int ex = 0;
             frexpf(c, &ex);
-            sc[u] = ldexpf(1.0f, -ex);
+            sc = ldexpf(1.0f, -ex);
             const int tp = tt - 1;
-            if (tp < gs.L[g]) {
-                const int64_t rowi = (cidx * kG + g) * p.Cmax + tp;
-                if (cs == 0 && r == 0) p.ebuf[rowi] = ex;
+            if (tp < Lg) {
+                if (lead && r == 0) p.ebuf[rowb + tp] = ex;
+                float v[S::EC];
+                ldv<S::EC>(V.sX + (cur * kG + g) * K + r * S::Kh + c0, v);
 #pragma unroll
-                for (int h = 0; h < S::CW; ++h) {
-                    const int j = r * S::Kh + cs + h * S::NCS;
-                    p.P[rowi * K + j] = V.sX[(cur * kG + g) * S::XK + S::pos(j)] * sc[u];
-                }
+                for (int e = 0; e < S::EC; ++e) v[e] *= sc;
+                stv<S::EC>(p.P + (rowb + tp) * K + r * S::Kh + c0, v);
             }
         }
         if (tt == maxL) break;
-        float o[S::GPT][S::CW];
-        matvec<K>(V.At, V.sX + cur * kG * S::XK, o);
-        fwd_epilogue<K>(V, gs, r, nxt, nxt, o, sc, [&](int g) { return tt < gs.L[g]; });
+        contract<K>(m, V.sX + cur * kG * K, V.part);
+        __syncthreads();
+        float o[S::EC];
+        gather<K>(V.part, g, c0, o);
+        fwd_epilogue<K>(V, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
         if (tid < kG) {
             gs.sym[cur][tid] = ob_next;
             ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
@@ -940,7 +979,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    const int tid = threadIdx.x, pp = (tid & 31) % S::NP, cs = tid / S::NP;
+    const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
+    const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
     const Views V = make_views(smem, K, p.M, cl, peer);
@@ -950,120 +990,106 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     __syncthreads();
     int maxL = 0;
 #pragma unroll
-    for (int g = 0; g < kG; ++g) maxL = gs.L[g] > maxL ? (int)gs.L[g] : maxL;
+    for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
+    const int Lg = (int)gs.L[g];
+    const int64_t rowb = (cidx * kG + g) * p.Cmax;
+    const int jc = r * S::Kh + c0;        // first state of the thread's epilogue block
     if (tid < kG && gs.L[tid] > 0) atomicMax(&p.rows[round], (int32_t)((cidx * kG + tid + 1) * p.Cmax));
     // rows that must read as zero / carry no symbol: all rows of a sequence whose last
     // segment was done in the previous round, rows past the segment of an active one
+    if (gs.seq[g] >= 0 && (gs.just_done[g] || Lg > 0)) {
+        float z[S::EC];
 #pragma unroll
-    for (int u = 0; u < S::GPT; ++u) {
-        const int g = pp * S::GPT + u;
-        if (gs.seq[g] < 0 || !(gs.just_done[g] || gs.L[g] > 0)) continue;
-        for (int64_t tt = gs.L[g]; tt < p.Cmax; ++tt)
-#pragma unroll
-            for (int h = 0; h < S::CW; ++h)
-                p.Q[((cidx * kG + g) * p.Cmax + tt) * K + r * S::Kh + cs + h * S::NCS] = 0.f;
+        for (int e = 0; e < S::EC; ++e) z[e] = 0.f;
+        for (int tt = Lg; tt < p.Cmax; ++tt) stv<S::EC>(p.Q + (rowb + tt) * K + jc, z);
     }
     if (r == 0 && tid < kG) {
-        const int g = tid;
-        const int64_t rb = (cidx * kG + g) * p.Cmax;
-        const int64_t from = (gs.seq[g] >= 0 && (gs.just_done[g] || gs.L[g] > 0)) ? gs.L[g] : p.Cmax;
+        const int q = tid;
+        const int64_t rb = (cidx * kG + q) * p.Cmax;
+        const int64_t from = (gs.seq[q] >= 0 && (gs.just_done[q] || gs.L[q] > 0)) ? gs.L[q] : p.Cmax;
         for (int64_t tt = from; tt < p.Cmax; ++tt) p.osym[rb + tt] = -1;
     }
     if (maxL == 0) return;                // no remote access made; the peer returns here too
-    auto sym_at = [&](int g, int tt) -> int {
-        const int64_t t = gs.t0[g] + tt;
-        return (tt <= gs.L[g] && t < gs.T[g] && gs.seq[g] >= 0) ? p.obs[gs.o0[g] + t] : -1;
+    auto sym_at = [&](int q, int tt) -> int {
+        const int64_t t = gs.t0[q] + tt;
+        return (tt <= gs.L[q] && t < gs.T[q] && gs.seq[q] >= 0) ? p.obs[gs.o0[q] + t] : -1;
     };
-    auto e_at = [&](int g, int tt) -> int { return tt < gs.L[g] ? p.ebuf[(cidx * kG + g) * p.Cmax + tt] : 0; };
-    int nsym = -1, ne = 0;                // thread g < 16: scalars of step tt-1, loaded one step ahead
+    auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(cidx * kG + q) * p.Cmax + tt] : 0; };
+    int nsym = -1, ne = 0;                // thread q < 16: scalars of step tt-1, loaded one step ahead
     if (tid < kG) {
-        const int g = tid;
-        gs.sym_end[g] = sym_at(g, maxL);
-        gs.sym[(maxL - 1) & 1][g] = sym_at(g, maxL - 1);
-        gs.eb[(maxL - 1) & 1][g] = e_at(g, maxL - 1);
+        const int q = tid;
+        gs.sym_end[q] = sym_at(q, maxL);
+        gs.sym[(maxL - 1) & 1][q] = sym_at(q, maxL - 1);
+        gs.eb[(maxL - 1) & 1][q] = e_at(q, maxL - 1);
         if (maxL >= 2) {
-            nsym = sym_at(g, maxL - 2);
-            ne = e_at(g, maxL - 2);
+            nsym = sym_at(q, maxL - 2);
+            ne = e_at(q, maxL - 2);
         }
     }
-    load_mat<K>(p.A, p.Kp, r, V.At);
+    MatRegs<K> m;
+    m.load(p.At, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
-    zero_vectors<K>(V.sX);
+    for (int idx = tid; idx < 2 * kG * K; idx += kT) V.sX[idx] = 0.f;
     __syncthreads();
     cl.sync();                            // both CTAs started and zeroed before any remote write
-    float R[S::GPT][S::CW];               // R_{t+1} of the thread's pairs
-    int prev_sym[S::GPT];
+    const float wg = gs.w[g];
+    const bool last_seg = gs.t0[g] + Lg == gs.T[g];
+    float R[S::EC];                       // R_{t+1} of the thread's (sequence, state) pairs
+    if (Lg > 0 && !last_seg) {
+        ldv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
+    } else {
 #pragma unroll
-    for (int u = 0; u < S::GPT; ++u) {
-        const int g = pp * S::GPT + u;
-        const bool last_seg = gs.t0[g] + gs.L[g] == gs.T[g];
-        prev_sym[u] = gs.sym_end[g];
-#pragma unroll
-        for (int h = 0; h < S::CW; ++h) {
-            const int j = r * S::Kh + cs + h * S::NCS;
-            R[u][h] = (gs.L[g] > 0 && !last_seg) ? p.Rc[gs.seq[g] * K + j] : 0.f;
-        }
+        for (int e = 0; e < S::EC; ++e) R[e] = 0.f;
     }
-    // v of step maxL-1 for the sequences whose segment has the full length
-    auto write_v = [&](int tt, int u, int s) {
-        const int g = pp * S::GPT + u;
-        const float w = gs.w[g];
-        float* qrow = p.Q + ((cidx * kG + g) * p.Cmax + tt) * K;
+    int prev_sym = gs.sym_end[g];
+    // v = b(s) o R for step tt into both CTAs, and the Q row of step tt
+    auto write_v = [&](int tt, int s) {
+        float v[S::EC], b[S::EC];
+        if (s >= 0) {
+            ldv<S::EC>(V.BTh + s * S::Kh + c0, b);
 #pragma unroll
-        for (int h = 0; h < S::CW; ++h) {
-            const int c = cs + h * S::NCS, j = r * S::Kh + c;
-            const float v = s >= 0 ? V.BTh[s * S::Kh + c] * R[u][h] : 0.f;
-            const int x = ((tt & 1) * kG + g) * S::XK + S::pos(j);
-            V.sX[x] = v;
-            V.sX_peer[x] = v;
-            qrow[j] = w * v;
+            for (int e = 0; e < S::EC; ++e) v[e] = b[e] * R[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < S::EC; ++e) v[e] = 0.f;
         }
-    };
+        const int x = ((tt & 1) * kG + g) * K + jc;
+        stv<S::EC>(V.sX + x, v);
+        stv<S::EC>(V.sX_peer + x, v);
 #pragma unroll
-    for (int u = 0; u < S::GPT; ++u)
-        if (maxL - 1 < gs.L[pp * S::GPT + u]) write_v(maxL - 1, u, prev_sym[u]);
+        for (int e = 0; e < S::EC; ++e) v[e] *= wg;
+        stv<S::EC>(p.Q + (rowb + tt) * K + jc, v);
+    };
+    if (maxL - 1 < Lg) write_v(maxL - 1, prev_sym);
     cl.sync();
     for (int tt = maxL - 1; tt >= 0; --tt) {
         const int buf = tt & 1;
-        int sym[S::GPT], e[S::GPT];
-        float St[S::GPT][S::CW];
-#pragma unroll
-        for (int u = 0; u < S::GPT; ++u) {
-            const int g = pp * S::GPT + u;
-            sym[u] = gs.sym[buf][g];
-            e[u] = gs.eb[buf][g];
-            const bool on = tt < gs.L[g];
-            const float* prow = p.P + ((cidx * kG + g) * p.Cmax + tt) * K;
-#pragma unroll
-            for (int h = 0; h < S::CW; ++h) St[u][h] = on ? prow[r * S::Kh + cs + h * S::NCS] : 0.f;
+        const int sym = gs.sym[buf][g], e_t = gs.eb[buf][g];
+        const bool on = tt < Lg;
+        float St[S::EC];
+        if (on) {
+            ldv<S::EC>(p.P + (rowb + tt) * K + jc, St);
         }
-        float o[S::GPT][S::CW];
-        matvec<K>(V.At, V.sX + buf * kG * S::XK, o);
-#pragma unroll
-        for (int u = 0; u < S::GPT; ++u) {
-            const int g = pp * S::GPT + u;
-            if (tt >= gs.L[g]) continue;
-            const int64_t rowi = (cidx * kG + g) * p.Cmax + tt;
-            const bool trans = prev_sym[u] >= 0;
-            const float down = ldexpf(1.0f, -e[u]);
-            const float up = gs.w[g] * ldexpf(1.0f, e[u]);
+        contract<K>(m, V.sX + buf * kG * K, V.part);
+        __syncthreads();
+        if (on) {
+            float o[S::EC];
+            gather<K>(V.part, g, c0, o);
+            const bool trans = prev_sym >= 0;
+            const float down = ldexpf(1.0f, -e_t);
+            const float up = wg * ldexpf(1.0f, e_t);
             const float cinv = trans ? 0.f : 1.0f / p.clast[gs.seq[g]];
+            float gm[S::EC];
 #pragma unroll
-            for (int h = 0; h < S::CW; ++h) {
-                const int j = r * S::Kh + cs + h * S::NCS;
-                const float Rt = trans ? o[u][h] * down : cinv;
-                p.gam[rowi * K + j] = up * St[u][h] * Rt;
-                R[u][h] = Rt;
+            for (int e = 0; e < S::EC; ++e) {
+                R[e] = trans ? o[e] * down : cinv;
+                gm[e] = up * St[e] * R[e];
             }
-            if (cs == 0 && r == 0) p.osym[rowi] = sym[u];
+            stv<S::EC>(p.gam + (rowb + tt) * K + jc, gm);
+            if (lead && r == 0) p.osym[rowb + tt] = sym;
         }
-        if (tt > 0) {
-#pragma unroll
-            for (int u = 0; u < S::GPT; ++u)
-                if (tt - 1 < gs.L[pp * S::GPT + u]) write_v(tt - 1, u, sym[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < S::GPT; ++u) prev_sym[u] = sym[u];
+        if (tt > 0 && tt - 1 < Lg) write_v(tt - 1, sym);
+        prev_sym = sym;
         if (tid < kG && tt > 0) {
             gs.sym[(tt - 1) & 1][tid] = nsym;
             gs.eb[(tt - 1) & 1][tid] = ne;
@@ -1074,21 +1100,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         }
         cl.sync();
     }
-#pragma unroll
-    for (int u = 0; u < S::GPT; ++u) {
-        const int g = pp * S::GPT + u;
-        if (gs.L[g] > 0)
-#pragma unroll
-            for (int h = 0; h < S::CW; ++h) p.Rc[gs.seq[g] * K + r * S::Kh + cs + h * S::NCS] = R[u][h];
-    }
+    if (Lg > 0) stv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
     // gamma_0 of the sequences that started in this round, summed in a fixed order by one
     // thread per state (the gam rows written above are visible after the barrier)
     __syncthreads();
-    for (int c = tid; c < S::Kh; c += kT) {
-        const int j = r * S::Kh + c;
+    for (int cc = tid; cc < S::Kh; cc += kT) {
+        const int j = r * S::Kh + cc;
         float s = 0.f;
-        for (int g = 0; g < kG; ++g)
-            if (gs.L[g] > 0 && gs.t0[g] == 0) s += p.gam[((cidx * kG + g) * p.Cmax) * K + j];
+        for (int q = 0; q < kG; ++q)
+            if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[((cidx * kG + q) * p.Cmax) * K + j];
         p.pig[cidx * K + j] += s;
     }
 }
