@@ -508,9 +508,10 @@ constexpr int kNW = 8;
 //    the CW = Kh/32 columns l CW .. l CW + CW - 1.  The thread's IPART x CW block of the
 //    matrix is loaded into registers once per kernel, so the step reads only the vectors
 //    from shared memory, and those as whole-warp broadcasts (every lane of a warp reads the
-//    same address).  Packed FMAs: for CW = 4 the column pairs (c, c+1) are the packed
-//    operand (the vector value is broadcast); for CW <= 2 the row pairs (i, i+1) are, with
-//    even- and odd-row partial sums added at the end.
+//    same address).  Packed FMAs pair rows: the accumulator of (g, c) is a float2 of the
+//    even-row and odd-row partial sums, so both operands, (x[g][i], x[g][i+1]) and
+//    (Mx[i][c], Mx[i+1][c]), are natural register pairs.  At K = 256 the 16 sequences are
+//    taken in two passes of 8 to bound the accumulator registers.
 //  * The eight warps' partial outputs meet in shared memory (fixed order: deterministic).
 //  * Epilogue: thread t takes sequence g = t / 16 and the EC = Kh/16 consecutive states
 //    (t % 16) EC .. +EC - 1, so vector, row and parameter accesses are 8-16 byte vectors.
@@ -519,8 +520,9 @@ struct Sh {
     static constexpr int Kh = K / 2;
     static constexpr int IPART = K / kNW;
     static constexpr int CW = Kh / 32;
-    static constexpr bool RP = CW <= 2;
     static constexpr int EC = Kh / 16;
+    static constexpr int NPASS = K == 256 ? 2 : 1;
+    static constexpr int GP = kG / NPASS;
     static_assert(IPART % 4 == 0 && (CW == 4 || CW == 2 || CW == 1) && EC % 2 == 0, "unsupported K");
 };
 __host__ __device__ inline bool cluster_shape_ok(int K) { return K == 64 || K == 128 || K == 256; }
@@ -613,32 +615,32 @@ __device__ void load_bt(const float* __restrict__ BT, int M, int r, float* dst) 
 }
 
 // The thread's block of the contraction matrix Mx[i][r Kh + c] (row stride Kp), i in its
-// warp's part, c in its lane's columns, as packed pairs (see Sh).
+// warp's part, c in its lane's columns: a[q][h] = (Mx[2q][c0 + h], Mx[2q + 1][c0 + h]).
 template <int K>
 struct MatRegs {
     using S = Sh<K>;
-    // CW = 4: a[i][0] = (Mx[i][c0], Mx[i][c0+1]), a[i][1] = (Mx[i][c0+2], Mx[i][c0+3])
-    // CW <= 2: a[q][h] = (Mx[2q][c0+h], Mx[2q+1][c0+h])
-    static constexpr int N0 = S::RP ? S::IPART / 2 : S::IPART;
-    static constexpr int N1 = S::RP ? S::CW : 2;
-    float2 a[N0][N1];
+    float2 a[S::IPART / 2][S::CW];
 
     __device__ void load(const float* __restrict__ Mx, int Kp, int r) {
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const float* base = Mx + (int64_t)(w * S::IPART) * Kp + r * S::Kh + lane * S::CW;
-        if constexpr (!S::RP) {
 #pragma unroll
-            for (int i = 0; i < S::IPART; ++i) {
-                const float4 v = *reinterpret_cast<const float4*>(base + (int64_t)i * Kp);
-                a[i][0] = make_float2(v.x, v.y);
-                a[i][1] = make_float2(v.z, v.w);
+        for (int q = 0; q < S::IPART / 2; ++q) {
+            float v0[S::CW], v1[S::CW];
+            if constexpr (S::CW == 4) {
+                const float4 x0 = *reinterpret_cast<const float4*>(base + (int64_t)(2 * q) * Kp);
+                const float4 x1 = *reinterpret_cast<const float4*>(base + (int64_t)(2 * q + 1) * Kp);
+                v0[0] = x0.x; v0[1] = x0.y; v0[2] = x0.z; v0[3] = x0.w;
+                v1[0] = x1.x; v1[1] = x1.y; v1[2] = x1.z; v1[3] = x1.w;
+            } else {
+#pragma unroll
+                for (int h = 0; h < S::CW; ++h) {
+                    v0[h] = base[(int64_t)(2 * q) * Kp + h];
+                    v1[h] = base[(int64_t)(2 * q + 1) * Kp + h];
+                }
             }
-        } else {
 #pragma unroll
-            for (int q = 0; q < S::IPART / 2; ++q)
-#pragma unroll
-                for (int h = 0; h < S::CW; ++h)
-                    a[q][h] = make_float2(base[(int64_t)(2 * q) * Kp + h], base[(int64_t)(2 * q + 1) * Kp + h]);
+            for (int h = 0; h < S::CW; ++h) a[q][h] = make_float2(v0[h], v1[h]);
         }
     }
 };
@@ -650,38 +652,18 @@ __device__ __forceinline__ void contract(const MatRegs<K>& m, const float* __res
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float* xb = X + w * S::IPART;
     float* pb = part + (w * kG) * S::Kh + lane * S::CW;
-    if constexpr (!S::RP) {
-        float2 acc[kG][2];
 #pragma unroll
-        for (int g = 0; g < kG; ++g) acc[g][0] = acc[g][1] = make_float2(0.f, 0.f);
+    for (int ps = 0; ps < S::NPASS; ++ps) {
+        float2 acc[S::GP][S::CW];
 #pragma unroll
-        for (int q = 0; q < S::IPART / 4; ++q) {
-#pragma unroll
-            for (int g = 0; g < kG; ++g) {
-                const float4 x = *reinterpret_cast<const float4*>(xb + g * K + 4 * q);
-                const float xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float2 xx = make_float2(xs[e], xs[e]);
-                    acc[g][0] = __ffma2_rn(xx, m.a[4 * q + e][0], acc[g][0]);
-                    acc[g][1] = __ffma2_rn(xx, m.a[4 * q + e][1], acc[g][1]);
-                }
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < kG; ++g)
-            *reinterpret_cast<float4*>(pb + g * S::Kh) = make_float4(acc[g][0].x, acc[g][0].y, acc[g][1].x, acc[g][1].y);
-    } else {
-        float2 acc[kG][S::CW];
-#pragma unroll
-        for (int g = 0; g < kG; ++g)
+        for (int g = 0; g < S::GP; ++g)
 #pragma unroll
             for (int h = 0; h < S::CW; ++h) acc[g][h] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < S::IPART / 4; ++q) {
 #pragma unroll
-            for (int g = 0; g < kG; ++g) {
-                const float4 x = *reinterpret_cast<const float4*>(xb + g * K + 4 * q);
+            for (int g = 0; g < S::GP; ++g) {
+                const float4 x = *reinterpret_cast<const float4*>(xb + (ps * S::GP + g) * K + 4 * q);
 #pragma unroll
                 for (int h = 0; h < S::CW; ++h) {
                     acc[g][h] = __ffma2_rn(make_float2(x.x, x.y), m.a[2 * q][h], acc[g][h]);
@@ -690,12 +672,15 @@ __device__ __forceinline__ void contract(const MatRegs<K>& m, const float* __res
             }
         }
 #pragma unroll
-        for (int g = 0; g < kG; ++g) {
-            if constexpr (S::CW == 2)
-                *reinterpret_cast<float2*>(pb + g * S::Kh) =
-                    make_float2(acc[g][0].x + acc[g][0].y, acc[g][1].x + acc[g][1].y);
+        for (int g = 0; g < S::GP; ++g) {
+            float* dst = pb + (ps * S::GP + g) * S::Kh;
+            if constexpr (S::CW == 4)
+                *reinterpret_cast<float4*>(dst) = make_float4(acc[g][0].x + acc[g][0].y, acc[g][1].x + acc[g][1].y,
+                                                              acc[g][2].x + acc[g][2].y, acc[g][3].x + acc[g][3].y);
+            else if constexpr (S::CW == 2)
+                *reinterpret_cast<float2*>(dst) = make_float2(acc[g][0].x + acc[g][0].y, acc[g][1].x + acc[g][1].y);
             else
-                pb[g * S::Kh] = acc[g][0].x + acc[g][0].y;
+                *dst = acc[g][0].x + acc[g][0].y;
         }
     }
 }
