@@ -19,8 +19,8 @@
 //
 // Operands are staged by all 256 threads (coalesced global loads, split, 16-byte shared
 // stores into the no-swizzle K-major canonical layout: core matrices of 8 rows x 4 values),
-// up to three stages deep; the loads of the next chunk are issued into registers before the
-// current chunk is split and stored.  One thread issues the MMAs of a stage and commits them
+// up to three stages deep; the loads of the next two chunks are in flight (in registers)
+// while the current chunk is split and stored.  One thread issues the MMAs of a stage and commits them
 // to the stage's mbarrier, which the threads wait on (bounded) before they refill it.
 #include "hmm_internal.cuh"
 #include "tc_ptx.cuh"
@@ -236,17 +236,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     const int64_t nchunks = (r1 - r0 + kKC - 1) / kKC;
     const int icol0 = ib * 128;
     bool failed = false;
-    Frag<K, CNT> cur, nxt;
-    frag_load<K, CNT>(cur, p, r0, r1, icol0, true);
-    for (int64_t c = 0; c < nchunks; ++c) {
+    // register ring of three chunks: chunk c is split and stored while the loads of chunks
+    // c+1 and c+2 are in flight
+    Frag<K, CNT> f0, f1, f2;
+    frag_load<K, CNT>(f0, p, r0, r1, icol0, true);
+    frag_load<K, CNT>(f1, p, r0 + kKC, r1, icol0, 1 < nchunks);
+    auto chunk = [&](int64_t c, const Frag<K, CNT>& cur, Frag<K, CNT>& ahead) -> bool {
         const int s = (int)(c % NS);
         char* st = smem + (size_t)s * sl.bytes;
-        // the next chunk's loads are in flight while this one is converted and multiplied
-        frag_load<K, CNT>(nxt, p, r0 + (c + 1) * kKC, r1, icol0, c + 1 < nchunks);
+        frag_load<K, CNT>(ahead, p, r0 + (c + 2) * kKC, r1, icol0, c + 2 < nchunks);
         if (c >= NS) {
             const uint32_t par = (uint32_t)((c / NS - 1) & 1);
             const bool ok = tc::mbar_wait_bounded(&s_bar[s], par, kWaitNs);
-            if (__syncthreads_or(!ok)) { failed = true; break; }
+            if (__syncthreads_or(!ok)) return false;
         }
         frag_store<K, CNT>(cur, st, sl, icol0, Mp);
         tc::fence_proxy_async_smem();
@@ -276,7 +278,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
             }
             tc::mma_commit(&s_bar[s]);
         }
-        cur = nxt;
+        return true;
+    };
+    for (int64_t c = 0; c < nchunks; c += 3) {
+        if (!chunk(c, f0, f2)) { failed = true; break; }
+        if (c + 1 >= nchunks) break;
+        if (!chunk(c + 1, f1, f0)) { failed = true; break; }
+        if (c + 2 >= nchunks) break;
+        if (!chunk(c + 2, f2, f1)) { failed = true; break; }
     }
     if (!failed) {
         // the last commit covers every MMA issued before it
