@@ -13,21 +13,23 @@
 // the accumulator: the row sum is needed only afterwards.  sum(X_t) then stays within a
 // factor of the step-to-step change of the emission scale, with no drift.
 //
-// Per CTA (one per SM, persistent, 256 threads):
+// Per CTA (one per SM, persistent, 128 x NSPLIT threads; NSPLIT = 2 or 4 column parts per
+// row, chosen by the autotuner):
 //  * shared memory holds, for the whole launch, A^T (BF16, the MMA's B operand: N = K rows
 //    of K, no-swizzle K-major canonical layout) and the emission table b(j, k) (BF16, rows
 //    rotated by the symbol so different symbols hit different banks); the X tile
 //    (BF16, 128 x K, canonical layout) is the MMA's A operand;
 //  * D (FP32, 128 lanes x K columns) accumulates in tensor memory; one thread issues the
 //    K/16 tcgen05.mma (M=128, N=K, K=16) of a step and commits them to an mbarrier;
-//  * 8 warps read D back (tcgen05.ld): warps w and w+4 share the lane quarter of rows
-//    32(w%4)..+31 and split the columns in halves; each thread multiplies its half-row by
-//    the emission, accumulates its partial row sum, scales by the predicted 2^-k, rounds to
-//    BF16 and writes its half of the next X row;
-//  * after a barrier, one thread per row combines the two partial sums, advances the row's
+//  * 4 x NSPLIT warps read D back (tcgen05.ld): warps w, w+4, ... share the lane quarter of
+//    rows 32(w%4)..+31 and split the columns in NSPLIT parts; each thread multiplies its part
+//    of the row by the emission, accumulates its partial row sum, scales by the predicted
+//    2^-k, rounds to BF16 and writes its part of the next X row;
+//  * after a barrier, one thread per row combines the partial sums, advances the row's
 //    bookkeeping and, when its sequence ends, writes logL and starts the next sequence from
 //    a global queue ordered by decreasing length (alpha~_0 = pi o b(o_0)), so uneven
-//    lengths are packed into one launch.
+//    lengths are packed into one launch.  The row's next symbol is loaded one step ahead so
+//    that no global load sits on the step's critical path.
 // All mbarrier waits are bounded (2 s); on expiry the kernel reports ACCEL_ERR_TIMEOUT.
 #include "common.cuh"
 #include "hmm_internal.cuh"
@@ -174,6 +176,7 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     const bool owner = part == 0;
     int64_t seq = -1, T = 0, pos = 0, E = 0;
     const int32_t* o = nullptr;
+    int32_t nob = 0;             // o[pos + 1], loaded one step ahead of its use
     int32_t kcur = 0;            // exponent applied to this step's X
     float uprev = 0.f;           // log2 sum(X_{t-1})
     bool queue_empty = row >= rows_active;   // rows past rows_active never take sequences
@@ -244,6 +247,7 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         }
         rinfo[row].ob = (int16_t)(seq >= 0 ? o[pos] : -1);
         rinfo[row].k = (int16_t)kcur;
+        nob = (seq >= 0 && pos + 1 < T) ? o[pos + 1] : 0;
     };
 
     if (owner) start_next();
@@ -265,11 +269,9 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         const RowInfo ri = rinfo[row];
         timed_out = !tc::mbar_wait_bounded(bar, iter & 1, kWaitNs);
         tc::tc_fence_after();
-        if (__syncthreads_or(timed_out)) {
-            if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
-            break;
-        }
-        // ---- epilogue, one pass: each thread's half-row of D (tcgen05.ld is warp-collective)
+        // ---- epilogue, one pass: each thread's part of the row of D (tcgen05.ld is
+        // warp-collective).  After a timed-out wait the values are not used: the barrier
+        // below agrees on the timeout before any bookkeeping.
         const bool act = ri.ob >= 0;
         const float mult = ldexpf(1.0f, -(int)ri.k);
         float ps = 0.f;
@@ -290,7 +292,10 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
             }
         }
         psum[part * kRows + row] = ps;
-        __syncthreads();
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            break;
+        }
         // ---- row bookkeeping (owner thread of each row)
         if (owner && seq >= 0) {
             float s = psum[row];
@@ -312,8 +317,9 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         if (owner) {
             if (seq < 0) start_next();
             else {
-                rinfo[row].ob = (int16_t)o[pos];
+                rinfo[row].ob = (int16_t)nob;
                 rinfo[row].k = (int16_t)kcur;
+                nob = pos + 1 < T ? o[pos + 1] : 0;
             }
         }
     }
