@@ -121,8 +121,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// NSPLIT = column parts per row: 2 (8 warps) or 4 (16 warps; needs K/4 a multiple of 32)
-template <int NSPLIT>
+// NSPLIT = column parts per row: 2 (8 warps) or 4 (16 warps; needs K/4 a multiple of 32).
+// MT = rows of the MMA tile: 128, or 64 when a CTA runs at most 64 sequence rows (half the
+// tensor-core work per step).  With M = 64, row r of D sits in TMEM lane 32 (r / 16) + r % 16,
+// so in each warp's lane quarter only lanes 0-15 carry a row.
+template <int NSPLIT, int MT>
 __global__ void __launch_bounds__(128 * NSPLIT, 1)
 k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g_etab,
          const float* __restrict__ log_pi, const int32_t* __restrict__ obs, const int64_t* __restrict__ off,
@@ -139,7 +142,9 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     constexpr int kThreads = 128 * NSPLIT;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int quarter = w & 3, part = w >> 2;
-    const int row = 32 * quarter + lane;          // row this thread reads and writes
+    constexpr int RPQ = MT / 4;                   // rows per lane quarter
+    const bool has_row = lane < RPQ;
+    const int row = RPQ * quarter + (has_row ? lane : 0);   // row this thread reads and writes
     const int KH = K / NSPLIT;                    // columns per part
     const int c0 = part * KH;                     // first column of this thread's part
     const int nch = K >> 3;
@@ -168,18 +173,18 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     const uint32_t tmem = *slot;
     const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
 
-    const uint32_t idesc = tc::idesc_bf16_f32(kRows, K);
+    const uint32_t idesc = tc::idesc_bf16_f32(MT, K);
     const uint32_t sx_addr = tc::smem_u32(sX), sat_addr = tc::smem_u32(sAT);
     const uint32_t sbo = 16u * (uint32_t)K;
 
     // row bookkeeping, kept by the row's owner thread (part 0)
-    const bool owner = part == 0;
+    const bool owner = part == 0 && has_row;
     int64_t seq = -1, T = 0, pos = 0, E = 0;
     const int32_t* o = nullptr;
     int32_t nob = 0;             // o[pos + 1], loaded one step ahead of its use
     int32_t kcur = 0;            // exponent applied to this step's X
     float uprev = 0.f;           // log2 sum(X_{t-1})
-    bool queue_empty = row >= rows_active;   // rows past rows_active never take sequences
+    bool queue_empty = !has_row || row >= rows_active;   // rows past rows_active never take sequences
     bool timed_out = false;
 
     // emission b(j, ob) for j in [jc, jc+32), FP32
@@ -272,7 +277,7 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         // ---- epilogue, one pass: each thread's part of the row of D (tcgen05.ld is
         // warp-collective).  After a timed-out wait the values are not used: the barrier
         // below agrees on the timeout before any bookkeeping.
-        const bool act = ri.ob >= 0;
+        const bool act = has_row && ri.ob >= 0;
         const float mult = ldexpf(1.0f, -(int)ri.k);
         float ps = 0.f;
         if (__any_sync(0xffffffffu, act)) {
@@ -291,7 +296,7 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
                 }
             }
         }
-        psum[part * kRows + row] = ps;
+        if (has_row) psum[part * kRows + row] = ps;
         if (__syncthreads_or(timed_out)) {
             if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
             break;
@@ -350,15 +355,12 @@ accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, cons
     if (r != ACCEL_OK) return r;
     int64_t tiles = (S + cfg.rows - 1) / cfg.rows;
     int grid = (int)(tiles < num_sms() ? tiles : num_sms());
-    if (cfg.split == 4) {
-        ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_hmm_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
-        k_hmm_tc<4><<<grid, 512, L.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
-                                                     loglik, d_status, L);
-    } else {
-        ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_hmm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
-        k_hmm_tc<2><<<grid, 256, L.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
-                                                     loglik, d_status, L);
-    }
+    // rows <= 64 per CTA: M = 64 tiles
+    auto kern = cfg.split == 4 ? (cfg.rows <= 64 ? k_hmm_tc<4, 64> : k_hmm_tc<4, 128>)
+                               : (cfg.rows <= 64 ? k_hmm_tc<2, 64> : k_hmm_tc<2, 128>);
+    ACCEL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+    kern<<<grid, 128 * cfg.split, L.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
+                                                      loglik, d_status, L);
     return after_launch(st, "hmm_forward(bf16 tcgen05)", 5);
 }
 

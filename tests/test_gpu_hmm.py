@@ -111,7 +111,7 @@ def _force_config(tmp_path, K, M, S, split, rows, t):
     assert ms == 0.0 and cfg == (split, rows)
 
 
-@pytest.mark.parametrize("split,rows", [(2, 128), (4, 128), (4, 32), (2, 64)])
+@pytest.mark.parametrize("split,rows", [(2, 128), (4, 128), (4, 32), (2, 64), (4, 64), (2, 32)])
 def test_bf16_tc_launch_configurations(tmp_path, split, rows):
     p = synth.hmm_workload(12, 128, 32, 700, "loguniform", 1, 400)
     logs, t, obs, off = _prep(p)
