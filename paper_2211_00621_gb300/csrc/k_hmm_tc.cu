@@ -187,18 +187,38 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     bool queue_empty = !has_row || row >= rows_active;   // rows past rows_active never take sequences
     bool timed_out = false;
 
-    // emission b(j, ob) for j in [jc, jc+32), FP32
-    auto load_emis = [&](int ob, int jc, float (&b)[32]) {
-        int q0 = (jc >> 3) + ob;
+    // emission b(j, ob) for j in [jc, jc+32), FP32, times `scale` (a power of two: exact)
+    auto load_emis = [&](int ob, int jc, float (&b)[32], float scale = 1.f) {
+        const int qb = ((jc >> 3) + ob) % nch;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            int q = (q0 + u) % nch;
+            const int q = qb + u < nch ? qb + u : qb + u - nch;
             uint4 r = *reinterpret_cast<const uint4*>(sE + ob * K * 2 + q * 16);
-            b[8 * u + 0] = bf_lo(r.x); b[8 * u + 1] = bf_hi(r.x);
-            b[8 * u + 2] = bf_lo(r.y); b[8 * u + 3] = bf_hi(r.y);
-            b[8 * u + 4] = bf_lo(r.z); b[8 * u + 5] = bf_hi(r.z);
-            b[8 * u + 6] = bf_lo(r.w); b[8 * u + 7] = bf_hi(r.w);
+            b[8 * u + 0] = bf_lo(r.x) * scale; b[8 * u + 1] = bf_hi(r.x) * scale;
+            b[8 * u + 2] = bf_lo(r.y) * scale; b[8 * u + 3] = bf_hi(r.y) * scale;
+            b[8 * u + 4] = bf_lo(r.z) * scale; b[8 * u + 5] = bf_hi(r.z) * scale;
+            b[8 * u + 6] = bf_lo(r.w) * scale; b[8 * u + 7] = bf_hi(r.w) * scale;
         }
+    };
+    // the scaled row values of columns [jc, jc+32): X = D o b 2^-k, packed to BF16 and stored;
+    // returns their sum (of the scaled values; a fixed pairwise tree)
+    auto epi_chunk = [&](const uint32_t* d, const float (&bs)[32], int jc) -> float {
+        float part8[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(d[8 * u + e]) * bs[8 * u + e];
+            uint4 pk;
+            pk.x = pack_bf16(v[0], v[1]);
+            pk.y = pack_bf16(v[2], v[3]);
+            pk.z = pack_bf16(v[4], v[5]);
+            pk.w = pack_bf16(v[6], v[7]);
+            *reinterpret_cast<uint4*>(sX + canon_off(row, jc + 8 * u, K)) = pk;
+            part8[2 * u] = (v[0] + v[1]) + (v[2] + v[3]);
+            part8[2 * u + 1] = (v[4] + v[5]) + (v[6] + v[7]);
+        }
+        return ((part8[0] + part8[1]) + (part8[2] + part8[3])) + ((part8[4] + part8[5]) + (part8[6] + part8[7]));
     };
     // write (v[u] * scale) for columns [jc, jc+32) of row `r` of X, BF16
     auto store_chunk = [&](int r, int jc, const float (&v)[32], float scale) {
@@ -272,29 +292,41 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
             tc::mma_commit(bar);
         }
         const RowInfo ri = rinfo[row];
+        const bool act = has_row && ri.ob >= 0;
+        const float mult = ldexpf(1.0f, -(int)ri.k);
+        // the first chunk's emission (scaled by 2^-k) is read while the MMAs run
+        float bs[32];
+        if (act) load_emis(ri.ob, c0, bs, mult);
         timed_out = !tc::mbar_wait_bounded(bar, iter & 1, kWaitNs);
         tc::tc_fence_after();
         // ---- epilogue, one pass: each thread's part of the row of D (tcgen05.ld is
         // warp-collective).  After a timed-out wait the values are not used: the barrier
-        // below agrees on the timeout before any bookkeeping.
-        const bool act = has_row && ri.ob >= 0;
-        const float mult = ldexpf(1.0f, -(int)ri.k);
+        // below agrees on the timeout before any bookkeeping.  The row sum is accumulated
+        // over the scaled values and unscaled by 2^k (exact) at the end.
         float ps = 0.f;
         if (__any_sync(0xffffffffu, act)) {
-            for (int jc = 0; jc < KH; jc += 32) {
-                uint32_t d[32];
-                tc::tmem_ld32(taddr + jc, d);
-                if (act) {
-                    float b[32], v[32];
-                    load_emis(ri.ob, c0 + jc, b);
-#pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        v[u] = __uint_as_float(d[u]) * b[u];
-                        ps += v[u];
+            if (KH % 64 == 0) {
+                for (int jc = 0; jc < KH; jc += 64) {
+                    uint32_t d[64];
+                    tc::tmem_ld64(taddr + jc, d);
+                    if (act) {
+                        if (jc > 0) load_emis(ri.ob, c0 + jc, bs, mult);
+                        ps += epi_chunk(d, bs, c0 + jc);
+                        load_emis(ri.ob, c0 + jc + 32, bs, mult);
+                        ps += epi_chunk(d + 32, bs, c0 + jc + 32);
                     }
-                    store_chunk(row, c0 + jc, v, mult);
+                }
+            } else {
+                for (int jc = 0; jc < KH; jc += 32) {
+                    uint32_t d[32];
+                    tc::tmem_ld32(taddr + jc, d);
+                    if (act) {
+                        if (jc > 0) load_emis(ri.ob, c0 + jc, bs, mult);
+                        ps += epi_chunk(d, bs, c0 + jc);
+                    }
                 }
             }
+            ps *= ldexpf(1.0f, (int)ri.k);
         }
         if (has_row) psum[part * kRows + row] = ps;
         if (__syncthreads_or(timed_out)) {
