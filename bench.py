@@ -431,6 +431,14 @@ def profile_case(name, reps, torch, dev):
 
 
 # ---------------------------------------------------------------------------- main
+def aggregate_ranks(ms_local: float, work_per_rank: float, world: int, allreduce_max=None):
+    """Whole-job timing of replicas: the slowest rank's step time bounds the job, and every
+    rank processes `work_per_rank` units per step (weak scaling, no data exchange).
+    Returns (ms, units per second for the whole job)."""
+    ms = ms_local if world <= 1 else float(allreduce_max(ms_local))
+    return ms, work_per_rank * world / (ms * 1e-3)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -540,14 +548,14 @@ def main():
     if W.bf16_graph is not None:
         launches += 5 * args.steps      # kernels inside each replay of the captured BF16 call
     clk = clocks.stop()
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    def allreduce_max(x):
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        return float(t.item())
+
     row_ms = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
     work = W.state_steps()
-    value = work * world / (ms * 1e-3)
+    ms, value = aggregate_ranks(sum(step_ms) / len(step_ms), work, world, allreduce_max)
 
     # ---------------- end to end through the public API with host buffers
     host, h2d = W.host_inputs()
@@ -562,11 +570,7 @@ def main():
         t0 = time.perf_counter()
         d2h = W.e2e_step(host)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = statistics.median(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e, e2e_value = aggregate_ranks(statistics.median(e2e_ms), work, world, allreduce_max)
 
     # ---------------- seg-reduce at HBM scale (2^20 segments)
     sweep = segreduce_sweep(torch, dev, api)
@@ -598,7 +602,7 @@ def main():
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
             "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweep,
             "rows": rows, "roofline": roof,
-            "e2e": {"value": work * world / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": int(launches), "clocks": clk,
             "autotune": W.tuned}
