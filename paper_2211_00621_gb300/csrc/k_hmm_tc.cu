@@ -25,11 +25,12 @@
 //    rows 32(w%4)..+31 and split the columns in NSPLIT parts; each thread multiplies its part
 //    of the row by the emission, accumulates its partial row sum, scales by the predicted
 //    2^-k, rounds to BF16 and writes its part of the next X row;
-//  * after a barrier, one thread per row combines the partial sums, advances the row's
-//    bookkeeping and, when its sequence ends, writes logL and starts the next sequence from
-//    a global queue ordered by decreasing length (alpha~_0 = pi o b(o_0)), so uneven
-//    lengths are packed into one launch.  The row's next symbol is loaded one step ahead so
-//    that no global load sits on the step's critical path.
+//  * while the next step's MMAs run, one thread per row combines the partial sums and
+//    advances the row's bookkeeping; when its sequence ends it writes logL and takes the
+//    next sequence from a global queue ordered by decreasing length, whose first vector
+//    alpha~_0 = pi o b(o_0) the row's threads write in the next epilogue (so uneven lengths
+//    are packed into one launch).  The row's next symbol is loaded one step ahead, so no
+//    global load sits on the step's critical path.
 // All mbarrier waits are bounded (2 s); on expiry the kernel reports ACCEL_ERR_TIMEOUT.
 #include "common.cuh"
 #include "hmm_internal.cuh"
@@ -52,7 +53,8 @@ struct TcLayout {
 
 // Per-row values the column-part threads need (written by the row's owner thread).
 struct RowInfo {
-    int16_t ob;     // symbol o_t of the step being computed (-1: no sequence)
+    int16_t ob;     // symbol o_t of the step being computed; -1: no sequence; -(o_0 + 2): the
+                    // row starts a sequence whose first symbol is o_0
     int16_t k;      // exponent k_t: this step's X_t is scaled by 2^-k_t
 };
 
@@ -185,10 +187,11 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     int32_t kcur = 0;            // exponent applied to this step's X
     float uprev = 0.f;           // log2 sum(X_{t-1})
     bool queue_empty = !has_row || row >= rows_active;   // rows past rows_active never take sequences
-    bool timed_out = false;
+    volatile uint32_t* s_flag = slot + 1;                 // set by a thread whose wait timed out
+    if (tid == 0) *s_flag = 0;
 
     // emission b(j, ob) for j in [jc, jc+32), FP32, times `scale` (a power of two: exact)
-    auto load_emis = [&](int ob, int jc, float (&b)[32], float scale = 1.f) {
+    auto load_emis = [&](int ob, int jc, float (&b)[32], float scale) {
         const int qb = ((jc >> 3) + ob) % nch;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -200,15 +203,15 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
             b[8 * u + 6] = bf_lo(r.w) * scale; b[8 * u + 7] = bf_hi(r.w) * scale;
         }
     };
-    // the scaled row values of columns [jc, jc+32): X = D o b 2^-k, packed to BF16 and stored;
-    // returns their sum (of the scaled values; a fixed pairwise tree)
-    auto epi_chunk = [&](const uint32_t* d, const float (&bs)[32], int jc) -> float {
+    // row values of columns [jc, jc+32): X = a o bs (a = D, or pi for a fresh row), packed to
+    // BF16 and stored; returns their sum (a fixed pairwise tree)
+    auto epi_chunk = [&](const float* a, const float (&bs)[32], int jc) -> float {
         float part8[8];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float v[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(d[8 * u + e]) * bs[8 * u + e];
+            for (int e = 0; e < 8; ++e) v[e] = a[8 * u + e] * bs[8 * u + e];
             uint4 pk;
             pk.x = pack_bf16(v[0], v[1]);
             pk.y = pack_bf16(v[2], v[3]);
@@ -220,69 +223,49 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         }
         return ((part8[0] + part8[1]) + (part8[2] + part8[3])) + ((part8[4] + part8[5]) + (part8[6] + part8[7]));
     };
-    // write (v[u] * scale) for columns [jc, jc+32) of row `r` of X, BF16
-    auto store_chunk = [&](int r, int jc, const float (&v)[32], float scale) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            uint4 pk;
-            pk.x = pack_bf16(v[8 * u + 0] * scale, v[8 * u + 1] * scale);
-            pk.y = pack_bf16(v[8 * u + 2] * scale, v[8 * u + 3] * scale);
-            pk.z = pack_bf16(v[8 * u + 4] * scale, v[8 * u + 5] * scale);
-            pk.w = pack_bf16(v[8 * u + 6] * scale, v[8 * u + 7] * scale);
-            *reinterpret_cast<uint4*>(sX + canon_off(r, jc + 8 * u, K)) = pk;
+    // take the next sequence of the queue on this row (owner thread).  Its first vector
+    // alpha~_0 = pi o b(o_0) (unscaled: k_0 = 0) is written by the row's epilogue threads in
+    // the next epilogue, flagged by rinfo.ob = -(o_0 + 2).
+    auto take_next = [&]() {
+        seq = -1;
+        if (!queue_empty) {
+            const unsigned long long q = atomicAdd(next, 1ull);
+            if (q >= (unsigned long long)S) {
+                queue_empty = true;
+            } else {
+                seq = order[q];
+                const int64_t o0 = off[seq];
+                T = off[seq + 1] - o0;
+                o = obs + o0;
+                pos = 0;
+                E = 0;
+                kcur = 0;
+                nob = T > 1 ? o[1] : 0;
+                rinfo[row].ob = (int16_t)(-(o[0] + 2));
+                rinfo[row].k = 0;
+                return;
+            }
         }
-    };
-    // start the next sequence of the queue on this row (owner thread): alpha~_0 = pi o b(o_0)
-    auto start_next = [&]() {
-        while (seq < 0 && !queue_empty) {
-            unsigned long long q = atomicAdd(next, 1ull);
-            if (q >= (unsigned long long)S) { queue_empty = true; break; }
-            seq = order[q];
-            const int64_t o0 = off[seq];
-            T = off[seq + 1] - o0;
-            o = obs + o0;
-            const int ob = o[0];
-            float s0 = 0.f;
-            for (int jc = 0; jc < K; jc += 32) {
-                float b[32];
-                load_emis(ob, jc, b);
-#pragma unroll
-                for (int u = 0; u < 32; ++u) s0 = fmaf(__expf(log_pi[jc + u]), b[u], s0);
-            }
-            if (T == 1) {
-                loglik[seq] = log((double)s0);
-                seq = -1;
-                continue;
-            }
-            int e0;
-            frexpf(s0, &e0);
-            const float sc = ldexpf(1.0f, -e0);
-            for (int jc = 0; jc < K; jc += 32) {
-                float b[32], v[32];
-                load_emis(ob, jc, b);
-#pragma unroll
-                for (int u = 0; u < 32; ++u) v[u] = __expf(log_pi[jc + u]) * b[u];
-                store_chunk(row, jc, v, sc);
-            }
-            E = e0;
-            const float ls = __log2f(s0);
-            uprev = ls - (float)e0;                     // log2 sum(X_0)
-            kcur = (int)rintf(uprev + ls);              // predicted exponent of s_1
-            pos = 1;
-        }
-        rinfo[row].ob = (int16_t)(seq >= 0 ? o[pos] : -1);
-        rinfo[row].k = (int16_t)kcur;
-        nob = (seq >= 0 && pos + 1 < T) ? o[pos + 1] : 0;
+        rinfo[row].ob = -1;
+        rinfo[row].k = 0;
     };
 
-    if (owner) start_next();
+    // Step loop.  Iteration i: (A) X is complete -> one thread issues the MMAs D = X A;
+    // meanwhile the owners process the row sums of the previous epilogue (logL at a
+    // sequence's end, the next exponent, the next symbol, or the next sequence); (B) every
+    // thread waits for the MMAs and writes the next X (or a fresh row's alpha~_0).
+    if (owner) take_next();
     for (uint32_t iter = 0;; ++iter) {
-        // ---- publish X, then issue this step's MMAs (thread 0)
+        // ---- (A) publish X; the MMAs of this iteration
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         const bool any = __syncthreads_or(owner && seq >= 0);
+        if (*s_flag != 0) {
+            if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            break;
+        }
         if (!any) break;
-        if (tid == 0) {
+        if (tid == kRows) {              // a thread of column part 1: never a row owner
             tc::tc_fence_after();
             for (int ks = 0; ks < K / 16; ++ks) {
                 uint64_t ad = tc::smem_desc_noswizzle(sx_addr + ks * 256, 128, sbo);
@@ -291,18 +274,42 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
             }
             tc::mma_commit(bar);
         }
+        // ---- bookkeeping of the previous epilogue's rows (owner threads), overlapping the MMAs
+        if (owner && seq >= 0 && iter > 0) {
+            float s = psum[row];
+#pragma unroll
+            for (int q = 1; q < NSPLIT; ++q) s += psum[q * kRows + row];
+            if (pos == T - 1) {
+                loglik[seq] = 0.6931471805599453 * (double)E + log((double)s);
+                take_next();
+            } else {
+                E += kcur;
+                const float ls = __log2f(s);
+                const float u = ls - (float)kcur;       // log2 sum(X_t)
+                const float lr = pos == 0 ? ls : ls - uprev;   // log2 of the growth sum(X_{t-1}) -> s_t
+                uprev = u;
+                kcur = (int)rintf(u + lr);
+                ++pos;
+                rinfo[row].ob = (int16_t)nob;
+                rinfo[row].k = (int16_t)kcur;
+                nob = pos + 1 < T ? o[pos + 1] : 0;
+            }
+        }
+        __syncthreads();
+        // ---- (B) epilogue
         const RowInfo ri = rinfo[row];
+        const bool fresh = has_row && ri.ob <= -2;
         const bool act = has_row && ri.ob >= 0;
+        const int ob = fresh ? -ri.ob - 2 : ri.ob;
         const float mult = ldexpf(1.0f, -(int)ri.k);
         // the first chunk's emission (scaled by 2^-k) is read while the MMAs run
         float bs[32];
-        if (act) load_emis(ri.ob, c0, bs, mult);
-        timed_out = !tc::mbar_wait_bounded(bar, iter & 1, kWaitNs);
+        if (act || fresh) load_emis(ob, c0, bs, mult);
+        const bool ok = tc::mbar_wait_bounded(bar, iter & 1, kWaitNs);
+        if (!ok) *s_flag = 1;
         tc::tc_fence_after();
-        // ---- epilogue, one pass: each thread's part of the row of D (tcgen05.ld is
-        // warp-collective).  After a timed-out wait the values are not used: the barrier
-        // below agrees on the timeout before any bookkeeping.  The row sum is accumulated
-        // over the scaled values and unscaled by 2^k (exact) at the end.
+        // each thread's part of the row of D (tcgen05.ld is warp-collective); the row sum is
+        // accumulated over the scaled values and unscaled by 2^k (exact) at the end
         float ps = 0.f;
         if (__any_sync(0xffffffffu, act)) {
             if (KH % 64 == 0) {
@@ -310,10 +317,10 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
                     uint32_t d[64];
                     tc::tmem_ld64(taddr + jc, d);
                     if (act) {
-                        if (jc > 0) load_emis(ri.ob, c0 + jc, bs, mult);
-                        ps += epi_chunk(d, bs, c0 + jc);
-                        load_emis(ri.ob, c0 + jc + 32, bs, mult);
-                        ps += epi_chunk(d + 32, bs, c0 + jc + 32);
+                        if (jc > 0) load_emis(ob, c0 + jc, bs, mult);
+                        ps += epi_chunk(reinterpret_cast<const float*>(d), bs, c0 + jc);
+                        load_emis(ob, c0 + jc + 32, bs, mult);
+                        ps += epi_chunk(reinterpret_cast<const float*>(d) + 32, bs, c0 + jc + 32);
                     }
                 }
             } else {
@@ -321,44 +328,24 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
                     uint32_t d[32];
                     tc::tmem_ld32(taddr + jc, d);
                     if (act) {
-                        if (jc > 0) load_emis(ri.ob, c0 + jc, bs, mult);
-                        ps += epi_chunk(d, bs, c0 + jc);
+                        if (jc > 0) load_emis(ob, c0 + jc, bs, mult);
+                        ps += epi_chunk(reinterpret_cast<const float*>(d), bs, c0 + jc);
                     }
                 }
             }
             ps *= ldexpf(1.0f, (int)ri.k);
         }
-        if (has_row) psum[part * kRows + row] = ps;
-        if (__syncthreads_or(timed_out)) {
-            if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
-            break;
-        }
-        // ---- row bookkeeping (owner thread of each row)
-        if (owner && seq >= 0) {
-            float s = psum[row];
+        if (fresh) {
+            // alpha~_0 = pi o b(o_0) for this thread's columns
+            for (int jc = 0; jc < KH; jc += 32) {
+                if (jc > 0) load_emis(ob, c0 + jc, bs, 1.f);
+                float pv[32];
 #pragma unroll
-            for (int q = 1; q < NSPLIT; ++q) s += psum[q * kRows + row];
-            if (pos == T - 1) {
-                loglik[seq] = 0.6931471805599453 * (double)E + log((double)s);
-                seq = -1;
-            } else {
-                E += kcur;
-                const float ls = __log2f(s);
-                const float u = ls - (float)kcur;       // log2 sum(X_t)
-                const float lr = ls - uprev;            // log2 of the growth sum(X_{t-1}) -> s_t
-                uprev = u;
-                kcur = (int)rintf(u + lr);
-                ++pos;
+                for (int u = 0; u < 32; ++u) pv[u] = __expf(log_pi[c0 + jc + u]);
+                ps += epi_chunk(pv, bs, c0 + jc);
             }
         }
-        if (owner) {
-            if (seq < 0) start_next();
-            else {
-                rinfo[row].ob = (int16_t)nob;
-                rinfo[row].k = (int16_t)kcur;
-                nob = pos + 1 < T ? o[pos + 1] : 0;
-            }
-        }
+        if (has_row) psum[part * kRows + row] = ps;
     }
     tc::tc_fence_before();
     __syncthreads();
