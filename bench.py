@@ -366,13 +366,21 @@ def sweep_inputs(torch, dev, S):
     return torch.from_numpy(data).to(dev), torch.from_numpy(off).to(dev)
 
 
-def segreduce_sweep(torch, dev, api, S=1 << 20, reps=10):
-    """Fused map + segmented int64 sum at HBM scale (L2 flushed before each rep)."""
+def segreduce_sweep(torch, dev, api, S=1 << 20, reps=10, plain=False):
+    """Fused map + segmented int64 sum at HBM scale (L2 flushed before each rep).  With
+    plain=True the same result is computed in the plain (unfused) form: the map writes an
+    int64 array, then an identity segmented sum reads it; GB/s is then still the fused
+    form's algorithmic bytes over the plain form's time."""
     d, o = sweep_inputs(torch, dev, S)
     out = torch.empty(S, dtype=torch.int64, device=dev)
     ws = torch.empty(api.L.load().accel_segreduce_workspace_size(d.numel(), S), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    run = lambda: api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, d, o, torch.int64, out=out, ws=ws)
+    if plain:
+        def run():
+            mapped = api.accel_map(api.MAP_SQ_PLUS_ONE, d, torch.int64)
+            return api.accel_segreduce(api.RED_ADD, api.MAP_IDENTITY, mapped, o, torch.int64, out=out, ws=ws)
+    else:
+        run = lambda: api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, d, o, torch.int64, out=out, ws=ws)
     for _ in range(3):
         run()
     ts = []
@@ -572,12 +580,51 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e, e2e_value = aggregate_ranks(statistics.median(e2e_ms), work, world, allreduce_max)
 
-    # ---------------- seg-reduce at HBM scale (2^20 segments)
-    sweep = segreduce_sweep(torch, dev, api)
+    # ---------------- seg-reduce at HBM scale (2^16, 2^18, 2^20 segments; plain form at 2^20)
+    sweeps = [segreduce_sweep(torch, dev, api, S=1 << e) for e in (16, 18, 20)]
+    sweep = sweeps[-1]
+    plain_form = segreduce_sweep(torch, dev, api, S=1 << 20, plain=True)
+
+    # ---------------- reported comparisons (untimed by the step): BF16 vs FP32 forward on the
+    # batched input, adjoint vs forward-only on the adjoint input, adjoint memory
+    def timed_once(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    q = W.bf16
+    fp32_on_bf16 = timed_once(lambda: api.hmm_forward(q["log_A"], q["log_B"], q["log_pi"], q["obs"], q["offsets"],
+                                                      api.HMM_FP32_LOG), reps=1)
+    compare = {"bf16_vs_fp32_forward_K256": {"fp32_ms": fp32_on_bf16, "bf16_ms": row_ms["hmm_bf16"],
+                                             "speedup": fp32_on_bf16 / row_ms["hmm_bf16"]}}
+    if W.adj is not None:
+        import ctypes as C
+        a = W.adj
+        fwd_only = timed_once(lambda: api.hmm_forward(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"],
+                                                      api.HMM_FP32_LOG))
+        m = api._model(a["log_A"], a["log_B"], a["log_pi"])
+        ws_bytes = lib.hmm_adjoint_workspace_size(C.byref(m), a["S"], a["obs"].numel(), a["maxT"])
+        compare["adjoint_vs_forward_only"] = {"adjoint_ms": row_ms["hmm_adjoint"], "fp32_forward_ms": fwd_only,
+                                              "ratio": row_ms["hmm_adjoint"] / fwd_only,
+                                              "workspace_bytes": int(ws_bytes),
+                                              "all_alphas_bytes": int(a["sumT"]) * a["K"] * 4}
+    compare["allpairs_interactions_per_s"] = W.N * W.N / (row_ms["allpairs"] * 1e-3)
+    compare["segreduce_plain_form"] = {"ms": plain_form["ms"], "GB/s_equiv": plain_form["GB/s"],
+                                       "fused_speedup": plain_form["ms"] / sweep["ms"]}
 
     # ---------------- rooflines
     peaks, peak_src = load_peaks()
-    sweep["frac"] = sweep["GB/s"] / peaks["hbm_gbs"]
+    for sw in sweeps:
+        sw["frac"] = sw["GB/s"] / peaks["hbm_gbs"]
     rl = rooflines(W, row_ms, peaks, float(peaks.get("sm_max_mhz", 2070.0)))
     dom = max((k for k in rl), key=lambda k: row_ms.get(k, 0.0))
     dom_src = {"segreduce": "k_segreduce.cu", "hmm_plain": "k_hmm_plain.cu", "hmm_bf16": "k_hmm_tc.cu",
@@ -600,7 +647,7 @@ def main():
                                    "; all-pairs N=65536",
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
-            "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweep,
+            "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweeps, "compare": compare,
             "rows": rows, "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
