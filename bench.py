@@ -278,19 +278,21 @@ def source_hash(path):
         return hashlib.sha1(f.read()).hexdigest()[:12]
 
 
-def traffic_for(kernel_src: str):
-    """dram bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+def traffic_for(row: str):
+    """DRAM bytes per launch of a row's call, from a committed ncu summary, if none of the
+    row's kernel sources has changed since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get(kernel_src)
+    e = d.get(row)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_2211_00621_gb300", "csrc", kernel_src)
-    if not os.path.exists(src) or source_hash(src) != e.get("source_sha1"):
-        return None
+    for name, sha in e.get("sources", {}).items():
+        src = os.path.join(ROOT, "paper_2211_00621_gb300", "csrc", name)
+        if not os.path.exists(src) or source_hash(src) != sha:
+            return None
     return e.get("dram_bytes_per_launch")
 
 
@@ -627,11 +629,9 @@ def main():
         sw["frac"] = sw["GB/s"] / peaks["hbm_gbs"]
     rl = rooflines(W, row_ms, peaks, float(peaks.get("sm_max_mhz", 2070.0)))
     dom = max((k for k in rl), key=lambda k: row_ms.get(k, 0.0))
-    dom_src = {"segreduce": "k_segreduce.cu", "hmm_plain": "k_hmm_plain.cu", "hmm_bf16": "k_hmm_tc.cu",
-               "hmm_adjoint": "hmm_adjoint.cu", "allpairs": "k_pairwise.cu"}[dom]
     roof = dict(rl[dom])
     roof["kernel"] = dom
-    roof["traffic"] = traffic_for(dom_src)
+    roof["traffic"] = traffic_for(dom)
     roof["peak_source"] = f"{peak_src} ({'sustained bf16' if roof['bound'] == 'tensor' else roof['bound']})"
 
     rows = {k: {"ms": row_ms[k], "frac": rl[k]["frac"], "achieved": rl[k]["achieved"], "unit": rl[k]["unit"],
