@@ -7,8 +7,8 @@
 //    elements), one CTA of 256 threads per tile, so the load is balanced whatever the
 //    segment lengths are.  A segment is OWNED by the tile holding its last element (an
 //    empty segment by the tile holding its position, clamped to N-1).  Owned segments of
-//    tile b are the contiguous range [lo[b], lo[b+1]) found by a small partition kernel
-//    (binary search of the monotone key).
+//    tile b are the contiguous range [lo[b], lo[b+1]), scattered by a small partition
+//    kernel from the monotone keys.
 //  * Loads are 16-byte vectors, coalesced across the CTA, staged through shared memory
 //    with an XOR swizzle so that each thread then reads its 16 contiguous elements
 //    conflict-free.  The tile's offsets are cached in shared memory too.
@@ -41,19 +41,18 @@ __device__ __forceinline__ int64_t seg_key(const int64_t* __restrict__ off, int6
     return k < N - 1 ? k : N - 1;
 }
 
-// lo[b] = first segment with key >= b * TILE, for b in [0, ntiles]; lo[ntiles] = S.
-__global__ void k_partition(const int64_t* __restrict__ off, int64_t S, int64_t N, int64_t tile,
-                            int64_t ntiles, int64_t* __restrict__ lo) {
-    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b > ntiles) return;
-    if (b == ntiles) { lo[b] = S; return; }
-    int64_t target = b * tile;
-    int64_t a = 0, z = S;
-    while (a < z) {
-        int64_t mid = (a + z) >> 1;
-        if (seg_key(off, mid, N) >= target) z = mid; else a = mid + 1;
-    }
-    lo[b] = a;
+// lo[b] = first segment with key >= b * TILE, for b in [0, ntiles]; lo[ntiles] = S.  Built by
+// a scatter: segment s writes lo[b] = s for every tile b
+// in (tile(key(s-1)), tile(key(s))] (keys are monotone, so each b is written exactly once),
+// and thread S writes lo[b] = S for the tiles past the last key.  One coalesced pass over
+// the offsets, with no dependent-load chain.
+__global__ void k_partition_scatter(const int64_t* __restrict__ off, int64_t S, int64_t N, int64_t tile,
+                                    int64_t ntiles, int64_t* __restrict__ lo) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s > S) return;
+    const int64_t tprev = s == 0 ? -1 : seg_key(off, s - 1, N) / tile;
+    const int64_t tcur = s == S ? ntiles : seg_key(off, s, N) / tile;
+    for (int64_t b = tprev + 1; b <= tcur; ++b) lo[b] = s;
 }
 
 template <typename C> struct KV { int32_t k; C v; };
@@ -366,8 +365,8 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     const int64_t nown = hi_b - lo_b;
     for (int64_t q = t; q < nown; q += kThreads) {
         const int a = rel(q), e = rel(q + 1);
-        const uint64_t hi = e > 0 ? s_P[pswz(e - 1)] : 0ull;
-        const uint64_t lo = a > 0 ? s_P[pswz(a - 1)] : 0ull;
+        const uint64_t hi = e > 0 ? s_P[pswz((e < ne ? e : ne) - 1)] : 0ull;
+        const uint64_t lo = a > 0 ? s_P[pswz((a < ne ? a : ne) - 1)] : 0ull;
         out[lo_b + q] = (Tout)(int64_t)(hi - lo);
     }
     // ---- the tile's open segment: segment hi_b if it starts at or before the last element
@@ -444,7 +443,7 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
         return after_launch(st, "accel_segreduce(fill)", 1);
     }
     int64_t te = tile_elems<Tin>();
-    k_partition<<<(unsigned)((L.ntiles + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);
+    k_partition_scatter<<<(unsigned)((S + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);
     if constexpr (std::is_integral<C>::value) {
         if (op == ACCEL_RED_ADD) {
             k_segsum<Tin, Tout><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
