@@ -269,13 +269,27 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
     }
 }
 
-// Integer sums: a branch-free variant.  The tile's mapped values are prefix-summed across
-// the CTA (each thread scans its 16 items, a CTA-wide scan adds the thread offsets) into
-// shared memory, and every owned segment's sum is P[end-1] - P[start-1].  Wrapping 64-bit
-// addition forms a group, so the differences are exact whatever the magnitudes.  Every
-// thread does the same work whatever the segment lengths, so no warp pays for a boundary
-// walk.  The tile's open segment (if the tile's last element does not end a segment) is
-// handed to the fixup kernel as before.
+// Integer sums: a branch-free variant with few instructions per element.  The tile's mapped
+// values are prefix-summed across the CTA (each thread scans its IT contiguous items, a
+// CTA-wide scan adds the thread offsets) into shared memory, and every owned segment's sum
+// is P[end-1] - P[start-1].  Wrapping 64-bit addition forms a group, so the differences are
+// exact whatever the magnitudes; every thread does the same work whatever the segment
+// lengths.  For the common map x*x + 1 on a full tile, P' = prefix of x*x is formed with one
+// widening multiply-add per element and P[k] = P'[k] + k + 1 is applied at lookup.  The
+// prefix array is item-major (item i of thread t at i * kThreads + t), so the stores are
+// conflict-free with constant offsets.  The tile's open segment (if its last element does
+// not end a segment) is handed to the fixup kernel.
+template <typename Tin>
+__device__ __forceinline__ uint64_t gmap(int map_op, int64_t x, int64_t sc) {
+    switch (map_op) {
+        case ACCEL_MAP_SQ_PLUS_ONE: return (uint64_t)x * (uint64_t)x + 1ull;
+        case ACCEL_MAP_NEG: return 0ull - (uint64_t)x;
+        case ACCEL_MAP_ABS: return x < 0 ? 0ull - (uint64_t)x : (uint64_t)x;
+        case ACCEL_MAP_SCALE: return (uint64_t)sc * (uint64_t)x;
+        default: return (uint64_t)x;
+    }
+}
+
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kThreads)
 k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
@@ -287,12 +301,9 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     // the staged tile and, once every thread holds its items, the prefix sums share storage
     __shared__ __align__(16) uint64_t s_buf[TE];
     int4* s_data = reinterpret_cast<int4*>(s_buf);  // kVecs 16-byte vectors (16 KB)
-    uint64_t* s_P = s_buf;                          // inclusive prefix of the mapped values
+    uint64_t* s_P = s_buf;                          // prefix of the mapped values, item-major
     __shared__ int32_t s_pos[kOffCap];
     __shared__ uint64_t s_wtot[kThreads / 32];
-    // prefix k is stored at pswz(k): the low 4 bits XOR-ed with the owning thread's low 4 bits,
-    // so a warp writing one item of each of its 32 threads' runs spreads over all banks
-    auto pswz = [](int k) { return (k & ~15) | ((k & 15) ^ ((k >> 4) & 15)); };
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t b = blockIdx.x;
@@ -300,6 +311,7 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     const int ne = (int)((e0 + TE < N) ? TE : N - e0);
     const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
     const int64_t sc = (int64_t)scalar;
+    const bool fast = map_op == ACCEL_MAP_SQ_PLUS_ONE && ne == TE;
 
     if (ne == TE) {
         const int4* src = reinterpret_cast<const int4*>(data + e0);
@@ -315,34 +327,32 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
     const int64_t cnt = last - lo_b + 1;
     const bool in_smem = cnt <= kOffCap;
+    // segment start relative to the tile, clamped to [0, ne]
     auto clamp_rel = [&](int64_t x) -> int32_t {
-        int64_t r = x - e0;
-        return (int32_t)(r < -1 ? -1 : (r > TE + 1 ? TE + 1 : r));
+        const int64_t r = x - e0;
+        return (int32_t)(r < 0 ? 0 : (r > ne ? ne : r));
     };
     if (in_smem)
         for (int i = t; i < cnt; i += kThreads) s_pos[i] = clamp_rel(off[lo_b + i]);
     __syncthreads();
     auto rel = [&](int64_t q) -> int32_t { return in_smem ? s_pos[q] : clamp_rel(off[lo_b + q]); };
 
-    // ---- per-thread inclusive scan of g(x) over its items (items past ne add nothing)
+    // ---- per-thread items and their total
     const int r0 = t * IT;
     const int n = max(0, min(IT, ne - r0));
     int4 raw[kVecPerThread];
 #pragma unroll
     for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
     const Tin* xs = reinterpret_cast<const Tin*>(raw);
-    // g(x) of item i (0 past ne), with the map switch outside the unrolled loops
     uint64_t run = 0;
-#define ACCEL_MAP_SWITCH(BODY)                                                                   \
-    switch (map_op) {                                                                            \
-        case ACCEL_MAP_SQ_PLUS_ONE: { auto g = [&](int64_t x) { return (uint64_t)x * (uint64_t)x + 1ull; }; BODY } break; \
-        case ACCEL_MAP_NEG: { auto g = [&](int64_t x) { return 0ull - (uint64_t)x; }; BODY } break;                     \
-        case ACCEL_MAP_ABS: { auto g = [&](int64_t x) { return x < 0 ? 0ull - (uint64_t)x : (uint64_t)x; }; BODY } break; \
-        case ACCEL_MAP_SCALE: { auto g = [&](int64_t x) { return (uint64_t)sc * (uint64_t)x; }; BODY } break;          \
-        default: { auto g = [&](int64_t x) { return (uint64_t)x; }; BODY } break;                                      \
+    if (fast) {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) run += (uint64_t)sq_wide(xs[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < IT; ++i)
+            if (i < n) run += gmap<Tin>(map_op, (int64_t)xs[i], sc);
     }
-    ACCEL_MAP_SWITCH(
-        _Pragma("unroll") for (int i = 0; i < IT; ++i) run += (i < n) ? g((int64_t)xs[i]) : 0ull;)
     // ---- CTA-wide exclusive scan of the thread totals
     uint64_t inc = run;
 #pragma unroll
@@ -354,27 +364,35 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     __syncthreads();   // also: every thread has read its items from the staging buffer
     uint64_t acc = inc - run;
     for (int w = 0; w < warp; ++w) acc += s_wtot[w];
-    ACCEL_MAP_SWITCH(
-        _Pragma("unroll") for (int i = 0; i < IT; ++i) {
-            if (i < n) { acc += g((int64_t)xs[i]); s_P[pswz(r0 + i)] = acc; }
-        })
-#undef ACCEL_MAP_SWITCH
+    if (fast) {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            acc += (uint64_t)sq_wide(xs[i]);
+            s_P[i * kThreads + t] = acc;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < IT; ++i)
+            if (i < n) { acc += gmap<Tin>(map_op, (int64_t)xs[i], sc); s_P[i * kThreads + t] = acc; }
+    }
     __syncthreads();
 
-    // ---- owned segments: sum over [max(start,0), end) = P[end-1] - P[start-1]
+    // ---- owned segments: sum over [start, end) of the tile = P(end) - P(start), where
+    // P(p) = sum of g over the tile's positions < p
+    auto Pb = [&](int32_t p) -> uint64_t {
+        if (p <= 0) return 0ull;
+        const int k = p - 1;
+        const uint64_t v = s_P[(k % IT) * kThreads + k / IT];
+        return fast ? v + (uint64_t)p : v;
+    };
     const int64_t nown = hi_b - lo_b;
-    for (int64_t q = t; q < nown; q += kThreads) {
-        const int a = rel(q), e = rel(q + 1);
-        const uint64_t hi = e > 0 ? s_P[pswz((e < ne ? e : ne) - 1)] : 0ull;
-        const uint64_t lo = a > 0 ? s_P[pswz((a < ne ? a : ne) - 1)] : 0ull;
-        out[lo_b + q] = (Tout)(int64_t)(hi - lo);
-    }
+    for (int64_t q = t; q < nown; q += kThreads) out[lo_b + q] = (Tout)(int64_t)(Pb(rel(q + 1)) - Pb(rel(q)));
     // ---- the tile's open segment: segment hi_b if it starts at or before the last element
     if (t == 0) {
-        const int a = (hi_b < S) ? rel(nown) : TE + 1;
+        const int32_t a = (hi_b < S) ? rel(nown) : ne;
         if (a <= ne - 1) {
             tail_seg[b] = hi_b;
-            tail_val[b] = (int64_t)(s_P[pswz(ne - 1)] - (a > 0 ? s_P[pswz(a - 1)] : 0ull));
+            tail_val[b] = (int64_t)(Pb(ne) - Pb(a));
         } else {
             tail_seg[b] = -1;
         }
