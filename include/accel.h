@@ -189,10 +189,10 @@ accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, in
  * allocator's own hooks, under a host framework that owns every allocation, or in a loop
  * that must never enter the allocator).  The paper has no counterpart: it is a property of
  * this library, not of expression acceleration.  Same arguments and results as
- * accel_segreduce, without (d_ws, ws_bytes): the scratch is a 1 MiB array inside the
+ * accel_segreduce, without (d_ws, ws_bytes): the scratch is a 2 MiB array inside the
  * library, created on each device when the library is loaded there and held until the
  * process exits.
- *  Limit: N <= 178,909,184 flat elements (any element type); larger N returns
+ *  Limit: N <= 178,913,280 flat elements (any element type); larger N returns
  *  ACCEL_ERR_UNSUPPORTED before anything is launched.
  *  Sharing: every call in the process uses the same array; it keeps the last call's
  *  contents, and each call writes every byte it reads before reading it, so nothing needs

@@ -487,8 +487,8 @@ using namespace accel;
 extern "C" {
 
 size_t accel_segreduce_workspace_size(int64_t N, int64_t S) {
-    // sized for the smallest element (most tiles)
-    return segred::layout(N < 0 ? 0 : N, S, 4).total;
+    // sized for the largest element (8 bytes: the fewest elements per tile, so the most tiles)
+    return segred::layout(N < 0 ? 0 : N, S, 8).total;
 }
 
 accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, int32_t out_dtype, const void* d_data,
@@ -537,8 +537,8 @@ accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, in
 // file-scope array below, created when the library is loaded on a device and kept until
 // the process exits; nothing is allocated or freed per call.
 //
-// Limits and sharing: the array holds kNoAllocScratchBytes (1 MiB), enough for
-// N <= 178,909,184 flat elements per call (any element type; S is not limited); larger
+// Limits and sharing: the array holds kNoAllocScratchBytes (2 MiB), enough for
+// N <= 178,913,280 flat elements per call (any element type; S is not limited); larger
 // inputs are rejected with ACCEL_ERR_UNSUPPORTED.  All calls in the process share the array and it
 // keeps the last call's contents; every byte a call reads is first written by that same
 // call, so nothing has to be cleared in between.  Calls that overlap on the GPU (different
@@ -552,7 +552,7 @@ accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, in
 namespace accel {
 namespace segred {
 
-constexpr size_t kNoAllocScratchBytes = 1u << 20;
+constexpr size_t kNoAllocScratchBytes = 2u << 20;
 constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -591,7 +591,7 @@ accel_status accel_segreduce_noalloc(int32_t op, int32_t fused_map, int32_t in_d
     const size_t need = accel_segreduce_workspace_size(N, S);
     ACCEL_REQUIRE(need <= segred::kNoAllocScratchBytes, ACCEL_ERR_UNSUPPORTED,
                   "accel_segreduce_noalloc: N=%lld needs %zu bytes of scratch; the built-in area holds %zu bytes "
-                  "(at most 178,909,184 elements); use accel_segreduce with a workspace",
+                  "(at most 178,913,280 elements); use accel_segreduce with a workspace",
                   (long long)N, need, segred::kNoAllocScratchBytes);
     void* scratch = nullptr;
     accel_status r = segred::noalloc_scratch(&scratch);

@@ -61,3 +61,11 @@ def test_host_only_calls(lib):
 def test_built_for_sm103a():
     from paper_2211_00621_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_segreduce_workspace_covers_the_most_tiles(lib):
+    # tiles hold 16 KB: 8-byte elements give the most tiles, and the workspace holds three
+    # 8-byte values per tile (partition, carry segment, carry value) after a 256-byte block
+    for n in (1, 4096, 10_000_019, 178_913_280):
+        tiles = -(-n // 2048)
+        assert lib.accel_segreduce_workspace_size(n, 7) >= 256 + 8 * (tiles + 1) + 16 * tiles

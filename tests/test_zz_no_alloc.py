@@ -54,7 +54,7 @@ def test_noalloc_rejects_inputs_beyond_its_scratch():
     out = torch.empty(8, dtype=torch.int64, device=DEV)
     st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     status = lib.accel_segreduce_noalloc(_lib.RED_ADD, _lib.MAP_IDENTITY, _lib.I32, _lib.I64,
-                                         C.c_void_p(data.data_ptr()), 178_909_185, C.c_void_p(off.data_ptr()),
+                                         C.c_void_p(data.data_ptr()), 178_913_281, C.c_void_p(off.data_ptr()),
                                          8, 0.0, C.c_void_p(out.data_ptr()), st)
     assert status == 7
     assert b"built-in area" in lib.accel_last_error()
