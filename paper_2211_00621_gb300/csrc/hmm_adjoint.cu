@@ -743,15 +743,88 @@ __device__ __forceinline__ Views make_views(char* smem, int K, int M, cg::cluste
     return v;
 }
 
+// ---- the per-step exchange between the two CTAs of a pair.  A CTA writes its half of the
+// next vectors (and its partial row sums) into its own shared memory with plain stores and
+// into its peer's with st.async, which counts the bytes on the peer's mbarrier of that step
+// parity; a CTA then waits on its own mbarrier for the peer's bytes (one arrival: its own
+// thread 0 announcing the expected byte count).  No cluster-wide memory fence per step.
+struct Xchg {
+    uint64_t* bar;           // this CTA's mbarriers, one per step parity
+    uint32_t bar_peer0, bar_peer1;   // the peer's, as shared::cluster addresses
+    uint32_t sx_peer;        // the peer's vector buffer
+    uint32_t red_peer;       // the peer's row-sum slots
+    uint32_t phase;          // bit p: parity of the next completion of bar[p]
+};
+
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_async4(uint32_t raddr, float4 v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void st_async2(uint32_t raddr, float2 v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+                 ::"r"(raddr), "f"(v.x), "f"(v.y), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void st_async1(uint32_t raddr, float v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+                 ::"r"(raddr), "r"(__float_as_uint(v)), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(tc::smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// N floats at element offset x of the peer's vector buffer (N a multiple of 2)
+template <int N>
+__device__ __forceinline__ void st_peer(const Xchg& xc, uint32_t base, int x, const float (&v)[N], uint32_t rbar) {
+    const uint32_t a = base + 4u * (uint32_t)x;
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int e = 0; e < N; e += 4) st_async4(a + 4u * e, make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]), rbar);
+    } else {
+#pragma unroll
+        for (int e = 0; e < N; e += 2) st_async2(a + 4u * e, make_float2(v[e], v[e + 1]), rbar);
+    }
+}
+
+// End of a step's writes of parity par: local visibility, then the peer's `bytes`.  A wait
+// that gives up (2 s) records ACCEL_ERR_TIMEOUT; the kernel then finishes its bounded
+// loops with unusable values, and the caller sees the status.
+__device__ __forceinline__ void xchg_finish(Xchg& xc, int par, uint32_t bytes, int32_t* status) {
+    __syncthreads();
+    uint64_t* bar = par ? &xc.bar[1] : &xc.bar[0];
+    if (threadIdx.x == 0) tc::mbar_arrive_expect_tx(bar, bytes);
+    const uint32_t ph = (xc.phase >> par) & 1u;
+    uint64_t t0 = 0;
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait_cluster(bar, ph)) break;
+        if ((i & 255) == 0) {
+            const uint64_t now = tc::globaltimer_ns();
+            if (i == 0) t0 = now;
+            else if (now - t0 > 2000000000ull) { atomicExch(status, ACCEL_ERR_TIMEOUT); break; }
+        }
+    }
+    xc.phase ^= 1u << par;
+}
+
 // Sum over the 16 threads of a sequence (a half warp), published as slot (rank) of parity
 // par in both CTAs.
-__device__ __forceinline__ void publish_sum(float ps, const Views& V, int par, int rank, int g) {
+__device__ __forceinline__ void publish_sum(float ps, const Views& V, const Xchg& xc, int par, int rank, int g) {
 #pragma unroll
     for (int d = 1; d < 16; d <<= 1) ps += __shfl_xor_sync(0xffffffffu, ps, d);
     if ((threadIdx.x & 15) == 0) {
         const int idx = (par * 2 + rank) * kG + g;
         V.red[idx] = ps;
-        V.red_peer[idx] = ps;
+        st_async1(xc.red_peer + 4u * (uint32_t)idx, ps, (par ? xc.bar_peer1 : xc.bar_peer0));
     }
 }
 
@@ -762,8 +835,8 @@ __device__ __forceinline__ float row_sum(const float* red, int par, int g) {
 // X_t = o * sc o b(ob) (or zero when the sequence has ended) into parity nxt of both CTAs,
 // and its row sum.
 template <int K>
-__device__ __forceinline__ void fwd_epilogue(const Views& V, int r, int nxt, int g, int c0, bool on, int ob,
-                                             const float (&o)[Sh<K>::EC], float sc) {
+__device__ __forceinline__ void fwd_epilogue(const Views& V, const Xchg& xc, int r, int nxt, int g, int c0, bool on,
+                                             int ob, const float (&o)[Sh<K>::EC], float sc) {
     using S = Sh<K>;
     float b[S::EC], v[S::EC];
     ldv<S::EC>(V.BTh + ob * S::Kh + c0, b);
@@ -775,14 +848,37 @@ __device__ __forceinline__ void fwd_epilogue(const Views& V, int r, int nxt, int
     }
     const int x = (nxt * kG + g) * K + r * S::Kh + c0;
     stv<S::EC>(V.sX + x, v);
-    stv<S::EC>(V.sX_peer + x, v);
-    publish_sum(ps, V, nxt, r, g);
+    st_peer<S::EC>(xc, xc.sx_peer, x, v, (nxt ? xc.bar_peer1 : xc.bar_peer0));
+    publish_sum(ps, V, xc, nxt, r, g);
+}
+
+// bytes a CTA receives from its peer per step: its half of the vectors (+ the row sums)
+template <int K>
+__host__ __device__ constexpr uint32_t xchg_bytes(bool sums) {
+    return (uint32_t)(kG * (K / 2) * 4 + (sums ? kG * 4 : 0));
+}
+
+__device__ __forceinline__ Xchg make_xchg(const Views& V, uint64_t* bar, int peer) {
+    Xchg xc;
+    xc.bar = bar;
+    xc.bar_peer0 = cluster_addr(&bar[0], (uint32_t)peer);
+    xc.bar_peer1 = cluster_addr(&bar[1], (uint32_t)peer);
+    xc.sx_peer = cluster_addr(V.sX, (uint32_t)peer);
+    xc.red_peer = cluster_addr(V.red, (uint32_t)peer);
+    xc.phase = 0;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::fence_mbar_init();
+    }
+    return xc;
 }
 
 // ---------------------------------------------------------------- forward + checkpoints
 // Step t (1 <= t < Tmax) reads X_{t-1} (parity cur) and the row sums of X_{t-1}, takes
 // e_{t-1} from them, stores checkpoint t-1 where due, and writes X_t (parity nxt) to both
-// CTAs; one cluster barrier per step.  A last pass (t = Tmax) only finishes T-1.
+// CTAs through the pair exchange (no cluster barrier per step).  A last pass (t = Tmax)
+// only finishes T-1.
 template <int K>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm p) {
     using S = Sh<K>;
@@ -793,7 +889,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     const bool lead = (tid & 15) == 0;    // one thread per sequence
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
+    __shared__ __align__(8) uint64_t s_xbar[2];
     const Views V = make_views(smem, K, p.M, cl, peer);
+    Xchg xc = make_xchg(V, s_xbar, peer);
     MatRegs<K> m;
     m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
@@ -817,9 +915,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
         // t = 0: alpha~_0 = pi o b(o_0)
         float o[S::EC];
         ldv<S::EC>(p.pi + r * S::Kh + c0, o);
-        fwd_epilogue<K>(V, r, 0, g, c0, Tg > 0, gs.sym[0][g], o, 1.f);
+        fwd_epilogue<K>(V, xc, r, 0, g, c0, Tg > 0, gs.sym[0][g], o, 1.f);
     }
-    cl.sync();
+    xchg_finish(xc, 0, xchg_bytes<K>(true), p.status);
     // the sequence's running exponent sum (used by the lead threads), steps to the next
     // checkpoint and its index
     int64_t E = 0;
@@ -859,12 +957,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
         __syncthreads();
         float o[S::EC];
         gather<K>(V.part, g, c0, o);
-        fwd_epilogue<K>(V, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
+        fwd_epilogue<K>(V, xc, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
         if (tid < kG) {
             gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
             ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
         }
-        cl.sync();
+        xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
     }
     cl.sync();
 }
@@ -883,7 +981,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
+    __shared__ __align__(8) uint64_t s_xbar[2];
     const Views V = make_views(smem, K, p.M, cl, peer);
+    Xchg xc = make_xchg(V, s_xbar, peer);
     load_gs(p, gs, cidx);
     __syncthreads();
     round_bounds_gs(gs, round);
@@ -940,12 +1040,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
         __syncthreads();
         float o[S::EC];
         gather<K>(V.part, g, c0, o);
-        fwd_epilogue<K>(V, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
+        fwd_epilogue<K>(V, xc, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
         if (tid < kG) {
             gs.sym[cur][tid] = ob_next;
             ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
         }
-        cl.sync();
+        xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
     }
     cl.sync();
 }
@@ -954,7 +1054,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
 // Step tt (from L-1 down to 0) reads v_{t+1} = b(o_{t+1}) o R_{t+1} (parity tt), forms
 // R_t = 2^-e_t A v_{t+1} (or 1/c'_{T-1} at the last step of a sequence) and
 // gamma_t = w 2^e_t S_t o R_t, then writes v_t = b(o_t) o R_t (parity tt-1) to both CTAs
-// together with the Q row of step tt-1; one cluster barrier per step.  R_t stays in the
+// together with the Q row of step tt-1 (the pair exchange, no cluster barrier).  R_t stays in the
 // registers of the thread that owns the (sequence, state) pair.
 //   sym(tt) = o_{t0+tt} if t0+tt < T and tt <= L, else -1: the epilogue symbol o_t of an
 //   active step and the symbol of v_t; sym(tt+1) >= 0 says whether step tt is a transition.
@@ -968,7 +1068,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
+    __shared__ __align__(8) uint64_t s_xbar[2];
     const Views V = make_views(smem, K, p.M, cl, peer);
+    Xchg xc = make_xchg(V, s_xbar, peer);
     load_gs(p, gs, cidx);
     __syncthreads();
     round_bounds_gs(gs, round);
@@ -1028,9 +1130,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     }
     int prev_sym = gs.sym_end[g];
     // v = b(s) o R for step tt into both CTAs, and the Q row of step tt
-    auto write_v = [&](int tt, int s) {
+    // (every thread sends its part each step -- zeros for a sequence not in step tt -- so the
+    // peer's expected byte count is constant; the Q row is written only for active steps)
+    auto write_v = [&](int tt, int s, bool active) {
         float v[S::EC], b[S::EC];
-        if (s >= 0) {
+        if (active && s >= 0) {
             ldv<S::EC>(V.BTh + s * S::Kh + c0, b);
 #pragma unroll
             for (int e = 0; e < S::EC; ++e) v[e] = b[e] * R[e];
@@ -1040,13 +1144,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         }
         const int x = ((tt & 1) * kG + g) * K + jc;
         stv<S::EC>(V.sX + x, v);
-        stv<S::EC>(V.sX_peer + x, v);
+        st_peer<S::EC>(xc, xc.sx_peer, x, v, ((tt & 1) ? xc.bar_peer1 : xc.bar_peer0));
+        if (active) {
 #pragma unroll
-        for (int e = 0; e < S::EC; ++e) v[e] *= wg;
-        stv<S::EC>(p.Q + (rowb + tt) * K + jc, v);
+            for (int e = 0; e < S::EC; ++e) v[e] *= wg;
+            stv<S::EC>(p.Q + (rowb + tt) * K + jc, v);
+        }
     };
-    if (maxL - 1 < Lg) write_v(maxL - 1, prev_sym);
-    cl.sync();
+    write_v(maxL - 1, prev_sym, maxL - 1 < Lg);
+    xchg_finish(xc, (maxL - 1) & 1, xchg_bytes<K>(false), p.status);
     for (int tt = maxL - 1; tt >= 0; --tt) {
         const int buf = tt & 1;
         const int sym = gs.sym[buf][g], e_t = gs.eb[buf][g];
@@ -1073,7 +1179,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             stv<S::EC>(p.gam + (rowb + tt) * K + jc, gm);
             if (lead && r == 0) p.osym[rowb + tt] = sym;
         }
-        if (tt > 0 && tt - 1 < Lg) write_v(tt - 1, sym);
+        if (tt > 0) write_v(tt - 1, sym, tt - 1 < Lg);
         prev_sym = sym;
         if (tid < kG && tt > 0) {
             gs.sym[(tt - 1) & 1][tid] = nsym;
@@ -1083,7 +1189,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
                 ne = e_at(tid, tt - 2);
             }
         }
-        cl.sync();
+        if (tt > 0) xchg_finish(xc, (tt - 1) & 1, xchg_bytes<K>(false), p.status);
     }
     if (Lg > 0) stv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
     // gamma_0 of the sequences that started in this round, summed in a fixed order by one
