@@ -527,7 +527,7 @@ struct Sh {
 };
 __host__ __device__ inline bool cluster_shape_ok(int K) { return K == 64 || K == 128 || K == 256; }
 
-struct SL { size_t bth, sx, part, red, total; };
+struct SL { size_t bth, sx, part, red, st, total; };
 
 __host__ __device__ inline SL smem_layout(int K, int M) {
     const int Kh = K / 2;
@@ -537,6 +537,7 @@ __host__ __device__ inline SL smem_layout(int K, int M) {
     L.sx = o;    o += (size_t)2 * kG * K * 4;             // full vectors, two step parities [2][16][K]
     L.part = o;  o += (size_t)kNW * kG * Kh * 4;          // per-warp partial outputs [8][16][Kh]
     L.red = o;   o += (size_t)2 * 2 * kG * 4;             // partial row sums [parity][rank][16]
+    L.st = o;    o += (size_t)kG * Kh * 4;                // backward: this step's S_t rows (own half)
     L.total = o;
     return L;
 }
@@ -728,7 +729,7 @@ __device__ __forceinline__ void gather(const float* __restrict__ part, int g, in
 }
 
 struct Views {
-    float *BTh, *sX, *part, *red, *sX_peer, *red_peer;
+    float *BTh, *sX, *part, *red, *sX_peer, *red_peer, *St;
 };
 
 __device__ __forceinline__ Views make_views(char* smem, int K, int M, cg::cluster_group& cl, int peer) {
@@ -738,6 +739,7 @@ __device__ __forceinline__ Views make_views(char* smem, int K, int M, cg::cluste
     v.sX = reinterpret_cast<float*>(smem + Ls.sx);
     v.part = reinterpret_cast<float*>(smem + Ls.part);
     v.red = reinterpret_cast<float*>(smem + Ls.red);
+    v.St = reinterpret_cast<float*>(smem + Ls.st);
     v.sX_peer = cl.map_shared_rank(v.sX, peer);
     v.red_peer = cl.map_shared_rank(v.red, peer);
     return v;
@@ -1157,12 +1159,29 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         const int buf = tt & 1;
         const int sym = gs.sym[buf][g], e_t = gs.eb[buf][g];
         const bool on = tt < Lg;
-        float St[S::EC];
+        // S_t of the thread's pairs, copied asynchronously into shared memory while the
+        // contraction runs (keeps registers free)
+        float* st_mine = V.St + g * S::Kh + c0;
         if (on) {
-            ldv<S::EC>(p.P + (rowb + tt) * K + jc, St);
+            const float* src = p.P + (rowb + tt) * K + jc;
+#pragma unroll
+            for (int e = 0; e < S::EC; e += 2) {
+                if constexpr (S::EC % 4 == 0) {
+                    if (e % 4 == 0)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(st_mine + e)),
+                                     "l"(src + e) : "memory");
+                } else {
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(st_mine + e)),
+                                 "l"(src + e) : "memory");
+                }
+            }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
         contract<K>(m, V.sX + buf * kG * K, V.part);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
+        float St[S::EC];
+        if (on) ldv<S::EC>(st_mine, St);
         if (on) {
             float o[S::EC];
             gather<K>(V.part, g, c0, o);
