@@ -67,6 +67,7 @@ struct Prm {
     int32_t* ebuf;      // exponents e_t of the P rows [S][Cmax] (cluster path)
     float* gam;         // weighted posteriors gamma_t of the rows [S][Cmax][K] (cluster path)
     int32_t* osym;      // o_t of each row, -1 for none [S][Cmax] (cluster path)
+    int64_t ncl;        // cluster path: number of sequence groups (2 CTAs each)
 };
 
 __host__ __device__ __forceinline__ int seg_len(int64_t T) {
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(256) k_counts(const float* __restrict__ gam, c
 // (A has row stride Kp)
 __global__ void k_finish(const float* __restrict__ A, int Kp, const float* __restrict__ Upart,
                          const float* __restrict__ cnt, const float* __restrict__ cntp, const float* __restrict__ pig,
-                         int K, int M, int64_t ngroups, int nsU, int nsC, float* __restrict__ gA,
+                         int K, int M, int64_t ngroups, int64_t npig, int nsU, int nsC, float* __restrict__ gA,
                          float* __restrict__ gB, float* __restrict__ gpi) {
     int64_t nA = (int64_t)K * K, nB = (int64_t)K * M;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nA + nB + K;
@@ -479,7 +480,7 @@ __global__ void k_finish(const float* __restrict__ A, int Kp, const float* __res
         } else {
             int64_t q = idx - nA - nB;
             float x = 0.f;
-            for (int64_t b = 0; b < ngroups; ++b) x += pig[b * K + q];
+            for (int64_t b = 0; b < npig; ++b) x += pig[b * K + q];
             if (gpi) gpi[q] = x;
         }
     }
@@ -554,11 +555,31 @@ struct GS {
     int sym_end[kG];     // backward: symbol after the segment, -1 if none
 };
 
-__device__ void load_gs(const Prm& p, GS& gs, int64_t cidx) {
+// Sorted positions [start, start + size) of group cidx: the S sequences (in order of
+// decreasing length) split into p.ncl contiguous groups of at most 16.  The critical path is
+// the group of the longest sequences, so when there is room the first groups take at most 8
+// (half the contraction work per step) and the rest share the remainder evenly.
+__device__ __forceinline__ void group_range(const Prm& p, int64_t cidx, int64_t& start, int& size) {
+    int64_t n8 = 0;                                    // leading groups of at most 8
+    if (p.S > 8 * p.ncl) {
+        n8 = (16 * p.ncl - p.S) / 8;
+        if (n8 < 0) n8 = 0;
+    }
+    if (cidx < n8) {
+        start = 8 * cidx;
+        size = 8;
+        return;
+    }
+    const int64_t rem = p.S - 8 * n8, m = p.ncl - n8, j = cidx - n8;
+    const int64_t base = rem / m, extra = rem % m, firstbig = m - extra;
+    start = 8 * n8 + j * base + (j > firstbig ? j - firstbig : 0);
+    size = (int)(base + (j >= firstbig ? 1 : 0));
+}
+
+__device__ void load_gs(const Prm& p, GS& gs, int64_t gstart, int gsize) {
     const int g = threadIdx.x;
     if (g < kG) {
-        int64_t q = cidx * kG + g;
-        int64_t sq = q < p.S ? p.order[q] : -1;
+        int64_t sq = g < gsize ? p.order[gstart + g] : -1;
         int64_t T = sq >= 0 ? p.off[sq + 1] - p.off[sq] : 0;
         int C = sq >= 0 ? seg_len(T) : 1;
         if (sq >= 0 && C > p.Cmax) {
@@ -646,15 +667,19 @@ struct MatRegs {
     }
 };
 
-// part[w][g][lane CW + h] = sum_{i in part w} X[g][i] Mx[i][lane CW + h], for all 16 g.
+// part[w][g][lane CW + h] = sum_{i in part w} X[g][i] Mx[i][lane CW + h], for the 16 g (the
+// second pass is skipped when the group has at most 8 sequences; its slots are then stale
+// and unused).
 template <int K>
-__device__ __forceinline__ void contract(const MatRegs<K>& m, const float* __restrict__ X, float* __restrict__ part) {
+__device__ __forceinline__ void contract(const MatRegs<K>& m, const float* __restrict__ X, float* __restrict__ part,
+                                         int gcount) {
     using S = Sh<K>;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float* xb = X + w * S::IPART;
     float* pb = part + (w * kG) * S::Kh + lane * S::CW;
 #pragma unroll
     for (int ps = 0; ps < S::NPASS; ++ps) {
+        if (ps > 0 && ps * S::GP >= gcount) break;   // (uniform) a group of at most GP sequences
         float2 acc[S::GP][S::CW];
 #pragma unroll
         for (int g = 0; g < S::GP; ++g)
@@ -887,6 +912,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
+    int64_t gstart;
+    int gsize;
+    group_range(p, cidx, gstart, gsize);
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;    // one thread per sequence
     extern __shared__ __align__(16) char smem[];
@@ -897,7 +925,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     MatRegs<K> m;
     m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
-    load_gs(p, gs, cidx);
+    load_gs(p, gs, gstart, gsize);
     __syncthreads();
     int ob_next = 0;                      // thread g < 16: o_{t+1} for the next symbol write
     if (tid < kG) {
@@ -955,7 +983,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
             }
         }
         if (t == Tmax) break;
-        contract<K>(m, V.sX + cur * kG * K, V.part);
+        contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
         __syncthreads();
         float o[S::EC];
         gather<K>(V.part, g, c0, o);
@@ -979,6 +1007,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
+    int64_t gstart;
+    int gsize;
+    group_range(p, cidx, gstart, gsize);
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
@@ -986,7 +1017,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     __shared__ __align__(8) uint64_t s_xbar[2];
     const Views V = make_views(smem, K, p.M, cl, peer);
     Xchg xc = make_xchg(V, s_xbar, peer);
-    load_gs(p, gs, cidx);
+    load_gs(p, gs, gstart, gsize);
     __syncthreads();
     round_bounds_gs(gs, round);
     __syncthreads();
@@ -994,21 +1025,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
 #pragma unroll
     for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
     const int Lg = (int)gs.L[g];
-    const int64_t rowb = (cidx * kG + g) * p.Cmax;
+    const int64_t rowb = (gstart + g) * p.Cmax;
     // row 0: the checkpoint itself, into the local vector buffer and the P row
     for (int idx = tid; idx < kG * K / 4; idx += kT) {
         const int gg = idx / (K / 4), cc = 4 * (idx - gg * (K / 4));
         float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (gs.L[gg] > 0) {
             sv = *reinterpret_cast<const float4*>(p.cp + (gs.seq[gg] * p.Cmax + gs.t0[gg] / gs.C[gg]) * K + cc);
-            if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + ((cidx * kG + gg) * p.Cmax) * K + cc) = sv;
+            if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + ((gstart + gg) * p.Cmax) * K + cc) = sv;
         }
         *reinterpret_cast<float4*>(V.sX + gg * K + cc) = sv;
     }
     int ob_next = 0;
     if (tid < kG) {
         const int q = tid;
-        if (gs.L[q] > 0 && r == 0) p.ebuf[(cidx * kG + q) * p.Cmax] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
+        if (gs.L[q] > 0 && r == 0) p.ebuf[(gstart + q) * p.Cmax] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
         const int64_t b0 = gs.o0[q] + gs.t0[q];
         gs.sym[1][q] = gs.L[q] > 1 ? p.obs[b0 + 1] : 0;
         ob_next = gs.L[q] > 2 ? p.obs[b0 + 2] : 0;
@@ -1038,7 +1069,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
             }
         }
         if (tt == maxL) break;
-        contract<K>(m, V.sX + cur * kG * K, V.part);
+        contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
         __syncthreads();
         float o[S::EC];
         gather<K>(V.part, g, c0, o);
@@ -1066,6 +1097,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
+    int64_t gstart;
+    int gsize;
+    group_range(p, cidx, gstart, gsize);
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
@@ -1073,7 +1107,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     __shared__ __align__(8) uint64_t s_xbar[2];
     const Views V = make_views(smem, K, p.M, cl, peer);
     Xchg xc = make_xchg(V, s_xbar, peer);
-    load_gs(p, gs, cidx);
+    load_gs(p, gs, gstart, gsize);
     __syncthreads();
     round_bounds_gs(gs, round);
     __syncthreads();
@@ -1081,9 +1115,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
 #pragma unroll
     for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
     const int Lg = (int)gs.L[g];
-    const int64_t rowb = (cidx * kG + g) * p.Cmax;
+    const int64_t rowb = (gstart + g) * p.Cmax;
     const int jc = r * S::Kh + c0;        // first state of the thread's epilogue block
-    if (tid < kG && gs.L[tid] > 0) atomicMax(&p.rows[round], (int32_t)((cidx * kG + tid + 1) * p.Cmax));
+    if (tid < kG && gs.L[tid] > 0) atomicMax(&p.rows[round], (int32_t)((gstart + tid + 1) * p.Cmax));
     // rows that must read as zero / carry no symbol: all rows of a sequence whose last
     // segment was done in the previous round, rows past the segment of an active one
     if (gs.seq[g] >= 0 && (gs.just_done[g] || Lg > 0)) {
@@ -1094,7 +1128,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     }
     if (r == 0 && tid < kG) {
         const int q = tid;
-        const int64_t rb = (cidx * kG + q) * p.Cmax;
+        const int64_t rb = (gstart + q) * p.Cmax;
         const int64_t from = (gs.seq[q] >= 0 && (gs.just_done[q] || gs.L[q] > 0)) ? gs.L[q] : p.Cmax;
         for (int64_t tt = from; tt < p.Cmax; ++tt) p.osym[rb + tt] = -1;
     }
@@ -1103,7 +1137,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         const int64_t t = gs.t0[q] + tt;
         return (tt <= gs.L[q] && t < gs.T[q] && gs.seq[q] >= 0) ? p.obs[gs.o0[q] + t] : -1;
     };
-    auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(cidx * kG + q) * p.Cmax + tt] : 0; };
+    auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(gstart + q) * p.Cmax + tt] : 0; };
     int nsym = -1, ne = 0;                // thread q < 16: scalars of step tt-1, loaded one step ahead
     if (tid < kG) {
         const int q = tid;
@@ -1177,7 +1211,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        contract<K>(m, V.sX + buf * kG * K, V.part);
+        contract<K>(m, V.sX + buf * kG * K, V.part, gsize);
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         float St[S::EC];
@@ -1218,7 +1252,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         const int j = r * S::Kh + cc;
         float s = 0.f;
         for (int q = 0; q < kG; ++q)
-            if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[((cidx * kG + q) * p.Cmax) * K + j];
+            if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[((gstart + q) * p.Cmax) * K + j];
         p.pig[cidx * K + j] += s;
     }
 }
@@ -1243,6 +1277,7 @@ struct Layout {
     size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, order, total;
     int Cmax;
     int64_t ngroups;
+    int64_t npig;       // rows of pig: one per group of either path (clusters: up to S)
 };
 
 static Layout layout(int K, int M, int64_t S, int64_t max_T) {
@@ -1263,7 +1298,8 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.Q = take((size_t)S * L.Cmax * K * 4);
     L.Rc = take((size_t)S * K * 4);
     L.cnt = take((size_t)L.ngroups * K * M * 4);
-    L.pig = take((size_t)L.ngroups * K * 4);
+    L.npig = L.ngroups > S ? L.ngroups : S;
+    L.pig = take((size_t)L.npig * K * 4);
     const int ns_max = xi_tc_supported(K) ? (kXiSplitMax > kSplit ? kXiSplitMax : kSplit) : kSplit;
     L.Upart = take((size_t)ns_max * K * K * 4);
     L.rows = take((size_t)L.Cmax * 4);
@@ -1335,6 +1371,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     p.ebuf = (int32_t*)(ws + L.ebuf);
     p.gam = (float*)(ws + L.gam);
     p.osym = (int32_t*)(ws + L.osym);
+    p.ncl = 0;
     float* cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
     p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = d_weights;
@@ -1358,7 +1395,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     const int nsU = xi_tc ? xi_tc_splits(K) : adj::kSplit;
     const int nsC = counts_tc ? xi_tc_splits(K) : adj::kCntSplit;
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cnt, 0, (size_t)L.ngroups * K * M * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.pig, 0, (size_t)L.ngroups * K * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.pig, 0, (size_t)L.npig * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)nsU * K * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
@@ -1370,7 +1407,11 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
         if (r != ACCEL_OK) return r;
         nlaunch += 3;
         if (use_cluster) {
-            const unsigned grid = (unsigned)(2 * ((S + adj::clu::kG - 1) / adj::clu::kG));
+            // groups: at most 16 sequences each, and at least one pair of CTAs per two SMs
+            const int64_t ncl_min = (S + adj::clu::kG - 1) / adj::clu::kG;
+            const int64_t ncl_sm = S < (int64_t)(num_sms() / 2) ? S : (int64_t)(num_sms() / 2);
+            p.ncl = ncl_min > ncl_sm ? ncl_min : ncl_sm;
+            const unsigned grid = (unsigned)(2 * p.ncl);
             const adj::clu::Kernels kc = adj::clu::kernels_for(K);
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
@@ -1414,7 +1455,8 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             }
         }
     }
-    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, cntp, p.pig, K, M, L.ngroups, nsU, nsC, d_grad_log_A,
+    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, cntp, p.pig, K, M, L.ngroups,
+                                      use_cluster ? p.ncl : L.ngroups, nsU, nsC, d_grad_log_A,
                                       d_grad_log_B, d_grad_log_pi);
     ++nlaunch;
     r = after_launch(st, "hmm_adjoint", nlaunch);
