@@ -156,7 +156,7 @@ class Workload:
         api, torch = self.api, self.torch
         q = self.bf16
         ms, cfg = api.hmm_autotune(q["log_A"], q["log_B"], q["log_pi"], q["obs"], q["offsets"])
-        self.tuned = {"split": cfg[0], "rows": cfg[1], "best_ms": ms}
+        self.tuned = {"split": cfg[0], "rows": cfg[1], "pair": cfg[2], "best_ms": ms}
         lib = api.L.load()
         m = api._model(q["log_A"], q["log_B"], q["log_pi"])
         nb = lib.hmm_forward_workspace_size(C.byref(m), q["S"], q["obs"].numel(), api.HMM_BF16_SCALED)

@@ -245,7 +245,8 @@ def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | N
 def hmm_autotune(log_A, log_B, log_pi, obs, offsets, precision=L.HMM_BF16_SCALED, cache_path=None, ws=None):
     """Times the BF16 forward's launch configurations on these inputs and keeps the fastest
     for later hmm_forward calls (and in `cache_path`, JSON lines, if given).  Returns
-    (best ms or 0.0 if cached, (split, rows))."""
+    (best ms or 0.0 if cached, (split, rows, pair)); pair = 1 when a tile of sequences runs
+    on a cluster of two CTAs that split the state columns."""
     lib = L.load()
     m = _model(log_A, log_B, log_pi)
     S = offsets.numel() - 1
@@ -257,9 +258,9 @@ def hmm_autotune(log_A, log_B, log_pi, obs, offsets, precision=L.HMM_BF16_SCALED
     path = cache_path.encode() if cache_path else None
     L.check("hmm_autotune", lib.hmm_autotune(C.byref(m), precision, _ptr(obs), _ptr(offsets), S, obs.numel(),
                                              _ptr(out), _ptr(ws), ws.numel(), path, C.byref(best), _stream()))
-    split, rows = C.c_int32(0), C.c_int32(0)
-    L.check("hmm_tuned_config", lib.hmm_tuned_config(m.K, m.M, S, C.byref(split), C.byref(rows)))
-    return best.value, (split.value, rows.value)
+    split, rows, pair = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    L.check("hmm_tuned_config", lib.hmm_tuned_config(m.K, m.M, S, C.byref(split), C.byref(rows), C.byref(pair)))
+    return best.value, (split.value, rows.value, pair.value)
 
 
 class Graph:

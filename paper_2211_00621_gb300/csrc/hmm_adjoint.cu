@@ -783,32 +783,11 @@ struct Xchg {
     uint32_t phase;          // bit p: parity of the next completion of bar[p]
 };
 
-__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void st_async4(uint32_t raddr, float4 v, uint32_t rbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
-                 ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar) : "memory");
-}
-__device__ __forceinline__ void st_async2(uint32_t raddr, float2 v, uint32_t rbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
-                 ::"r"(raddr), "f"(v.x), "f"(v.y), "r"(rbar) : "memory");
-}
-__device__ __forceinline__ void st_async1(uint32_t raddr, float v, uint32_t rbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
-                 ::"r"(raddr), "r"(__float_as_uint(v)), "r"(rbar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok) : "r"(tc::smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
+using tc::cluster_addr;
+using tc::mbar_try_wait_cluster;
+using tc::st_async1;
+using tc::st_async2;
+using tc::st_async4;
 
 // N floats at element offset x of the peer's vector buffer (N a multiple of 2)
 template <int N>

@@ -1,11 +1,12 @@
 // Autotuner for the BF16 tensor-core HMM forward: picks the launch configuration (column
-// parts per row: 8 or 16 warps; sequence rows per CTA: 128, 64 or 32) by timing every
-// candidate on the caller's inputs with CUDA events, and remembers the winner per
+// parts per row: 8 or 16 warps; sequence rows per tile: 128, 64 or 32; one CTA per tile or a
+// cluster pair splitting the state columns) by timing every candidate on the caller's inputs
+// with CUDA events, and remembers the winner per
 // (device, K, M, floor(log2 S)) -- in this process, and optionally in a cache file of JSON
 // lines so later processes skip the timing:
 //   {"kernel": "hmm_forward_bf16", "device": "<name>", "K": 256, "M": 64, "S_log2": 12,
-//    "split": 4, "rows": 128, "ms": 17.21}
-// hmm_forward consults the table; without an entry it uses 16 warps and 128 rows.
+//    "split": 4, "rows": 128, "pair": 0, "ms": 17.21}
+// hmm_forward consults the table; without an entry it uses 16 warps, 128 rows, one CTA.
 #include "hmm_internal.cuh"
 
 #include <cmath>
@@ -40,7 +41,7 @@ int s_log2(int64_t S) {
     return b;
 }
 
-TcConfig default_config(int K) { return TcConfig{(K / 4) % 32 == 0 ? 4 : 2, 128}; }
+TcConfig default_config(int K) { return TcConfig{(K / 4) % 32 == 0 ? 4 : 2, 128, 0}; }
 
 bool load_from_cache(const char* path, const Key& key, TcConfig* out) {
     if (!path || !path[0]) return false;
@@ -50,15 +51,15 @@ bool load_from_cache(const char* path, const Key& key, TcConfig* out) {
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char kern[64], dev[256];
-        int K, M, sl, split, rows;
+        int K, M, sl, split, rows, pair;
         float ms;
         int n = sscanf(line,
                        " {\"kernel\": \"%63[^\"]\", \"device\": \"%255[^\"]\", \"K\": %d, \"M\": %d, \"S_log2\": %d, "
-                       "\"split\": %d, \"rows\": %d, \"ms\": %f}",
-                       kern, dev, &K, &M, &sl, &split, &rows, &ms);
-        if (n != 8 || strcmp(kern, "hmm_forward_bf16") != 0) continue;
+                       "\"split\": %d, \"rows\": %d, \"pair\": %d, \"ms\": %f}",
+                       kern, dev, &K, &M, &sl, &split, &rows, &pair, &ms);
+        if (n != 9 || strcmp(kern, "hmm_forward_bf16") != 0) continue;
         if (Key(dev, K, M, sl) == key) {
-            *out = TcConfig{split, rows};
+            *out = TcConfig{split, rows, pair ? 1 : 0};
             found = true;   // the last matching line wins
         }
     }
@@ -72,8 +73,8 @@ void append_to_cache(const char* path, const Key& key, TcConfig c, float ms) {
     if (!f) return;
     fprintf(f,
             "{\"kernel\": \"hmm_forward_bf16\", \"device\": \"%s\", \"K\": %d, \"M\": %d, \"S_log2\": %d, "
-            "\"split\": %d, \"rows\": %d, \"ms\": %.4f}\n",
-            std::get<0>(key).c_str(), std::get<1>(key), std::get<2>(key), std::get<3>(key), c.split, c.rows, ms);
+            "\"split\": %d, \"rows\": %d, \"pair\": %d, \"ms\": %.4f}\n",
+            std::get<0>(key).c_str(), std::get<1>(key), std::get<2>(key), std::get<3>(key), c.split, c.rows, c.pair, ms);
     fclose(f);
 }
 
@@ -118,12 +119,14 @@ accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int
     cudaStream_t st = as_stream(stream);
     char* ws = (char*)d_ws;
     std::vector<TcConfig> cands;
-    for (int split : {4, 2})
-        for (int rows : {128, 64, 32}) {
-            if (split == 4 && (m->K / 4) % 32 != 0) continue;
-            if (rows < 128 && (S + rows - 1) / rows <= (S + 127) / 128) continue;   // no more CTAs than 128 rows
-            cands.push_back(TcConfig{split, rows});
-        }
+    for (int pair : {0, 1})
+        for (int split : {4, 2})
+            for (int rows : {128, 64, 32}) {
+                if (split == 4 && (m->K / 4) % 32 != 0) continue;
+                if (rows < 128 && (S + rows - 1) / rows <= (S + 127) / 128) continue;   // no more tiles than 128 rows
+                if (pair && !tc_pair_supported(m->K, m->M, rows, split)) continue;
+                cands.push_back(TcConfig{split, rows, pair});
+            }
     cudaEvent_t e0, e1;
     ACCEL_CUDA_TRY(cudaEventCreate(&e0));
     ACCEL_CUDA_TRY(cudaEventCreate(&e1));
@@ -161,11 +164,12 @@ accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int
 }
 
 // Configuration hmm_forward would use for these sizes (for tests and reports).
-accel_status hmm_tuned_config(int32_t K, int32_t M, int64_t S, int32_t* h_split, int32_t* h_rows) {
+accel_status hmm_tuned_config(int32_t K, int32_t M, int64_t S, int32_t* h_split, int32_t* h_rows, int32_t* h_pair) {
     ACCEL_REQUIRE(h_split && h_rows, ACCEL_ERR_INVALID_ARG, "hmm_tuned_config: null pointer");
     TcConfig c = tuned_config(K, M, S);
     *h_split = c.split;
     *h_rows = c.rows;
+    if (h_pair) *h_pair = c.pair;
     return ok();
 }
 

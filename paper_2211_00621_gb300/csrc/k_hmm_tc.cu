@@ -36,7 +36,12 @@
 #include "hmm_internal.cuh"
 #include "tc_ptx.cuh"
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace accel {
 namespace hmm {
@@ -352,6 +357,391 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     if (w == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
+// ============================================================================================
+// Cluster-pair variant.  The two CTAs of a cluster run the same tile of sequence rows and
+// split the state columns: CTA r computes D_r = X A[:, r K/2 : (r+1) K/2] (MMA N = K/2, half
+// the tensor-core time of a step), holds only its half of A^T and of the emission table, and
+// runs the epilogue of its own columns (half the per-row work).  Each CTA writes its half of
+// X_t into its own tile and, with st.async, into its peer's, together with its partial row
+// sums; the stores count their bytes on the receiver's mbarrier of that step's parity, so a
+// CTA waits for its peer's half with no cluster barrier per step.  X is double-buffered by
+// step parity: a peer can be one step ahead and must not overwrite the tile the MMA reads.
+// Both CTAs do the same row bookkeeping on the same sums (added in the same order), so they
+// agree on every exponent and on the end of every sequence; CTA 0 alone writes logL and pops
+// the sequence queue, and sends the popped index to CTA 1 in the same exchange.  A row that
+// takes a new sequence this way idles for one step while the index travels.
+// ============================================================================================
+struct PairLayout {
+    uint32_t s_at, s_x, x_bytes, s_e, s_rowinfo, s_psum, s_mail, s_bar, s_slot, smem_bytes;
+};
+
+static PairLayout pair_layout(int K, int M, int MT, int NSPLIT) {
+    PairLayout L;
+    const uint32_t KC = (uint32_t)K / 2;
+    uint32_t o = 0;
+    L.s_at = o; o += KC * (uint32_t)K * 2;                 // this CTA's half of A^T (N = K/2 rows)
+    L.x_bytes = (uint32_t)MT * (uint32_t)K * 2;
+    L.s_x = o;  o += 2 * L.x_bytes;                        // X, one buffer per step parity
+    L.s_e = o;  o += (uint32_t)M * KC * 2;                 // emission columns of this half
+    o = (o + 15) & ~15u;
+    L.s_rowinfo = o; o += (uint32_t)MT * (uint32_t)sizeof(RowInfo);
+    L.s_psum = o; o += 2 * 2 * (uint32_t)NSPLIT * (uint32_t)MT * 4;   // [parity][cta][part][row]
+    L.s_mail = o; o += 2 * (uint32_t)MT * 4;                          // [parity][row] popped index
+    o = (o + 7) & ~7u;
+    L.s_bar = o; o += 3 * 8;                                          // MMA, exchange x 2 parities
+    L.s_slot = o; o += 8;
+    L.smem_bytes = o;
+    return L;
+}
+
+bool tc_pair_supported(int K, int M, int rows, int split) {
+    if (K < 128 || K > 256 || K % 64 != 0 || M < 1 || M > 32767 || (split != 2 && split != 4)) return false;
+    if ((K / 2 / split) % 32 != 0) return false;
+    const int MT = rows <= 64 ? 64 : 128;
+    return (int)pair_layout(K, M, MT, split).smem_bytes <= max_smem_optin();
+}
+
+template <int NSPLIT, int MT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128 * NSPLIT, 1)
+k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g_etab,
+              const float* __restrict__ log_pi, const int32_t* __restrict__ obs, const int64_t* __restrict__ off,
+              int64_t S, const int32_t* __restrict__ order, unsigned long long* __restrict__ next, int rows_active,
+              double* __restrict__ loglik, int32_t* __restrict__ status, PairLayout L) {
+    extern __shared__ __align__(1024) char smem[];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), peer = rank ^ 1;
+    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+    char* sAT = smem + L.s_at;
+    char* sX = smem + L.s_x;
+    char* sE = smem + L.s_e;
+    RowInfo* rinfo = reinterpret_cast<RowInfo*>(smem + L.s_rowinfo);
+    float* psum = reinterpret_cast<float*>(smem + L.s_psum);
+    int32_t* mail = reinterpret_cast<int32_t*>(smem + L.s_mail);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.s_bar);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem + L.s_slot);
+    constexpr int kThreads = 128 * NSPLIT;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int quarter = w & 3, part = w >> 2;
+    constexpr int RPQ = MT / 4;
+    const bool has_row = lane < RPQ;
+    const int row = RPQ * quarter + (has_row ? lane : 0);
+    const int KC = K / 2;                         // columns of this CTA
+    const int KH = KC / NSPLIT;                   // columns per part
+    const int l0 = part * KH;                     // first column of the part, within the half
+    const int g0 = rank * KC + l0;                // ... and in the full row
+    const int nch = K >> 3, nchh = KC >> 3;
+
+    // ---- stage this half of A^T (rows rank*KC.. of the canonical layout are one block) and
+    // the emission columns of this half (16-byte chunks re-rotated within the half)
+    {
+        const int4* src = reinterpret_cast<const int4*>(g_at + (size_t)rank * KC * K * 2);
+        int4* dst = reinterpret_cast<int4*>(sAT);
+        for (int i = tid; i < KC * K * 2 / 16; i += kThreads) dst[i] = src[i];
+        for (int i = tid; i < M * nchh; i += kThreads) {
+            const int ob = i / nchh, c = i - ob * nchh;
+            const int qs = (rank * nchh + c + ob) % nch, qd = (c + ob) % nchh;
+            reinterpret_cast<int4*>(sE + (size_t)ob * KC * 2)[qd] =
+                reinterpret_cast<const int4*>(g_etab + (size_t)ob * K * 2)[qs];
+        }
+        for (int i = tid; i < 2 * MT; i += kThreads) mail[i] = -1;
+    }
+    if (w == 0) {
+        tc::tmem_alloc(slot, (uint32_t)KC);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::mbar_init(&bar[2], 1);
+        tc::fence_mbar_init();
+    }
+    volatile uint32_t* s_flag = slot + 1;
+    if (tid == 0) *s_flag = 0;
+    tc::tc_fence_before();
+    cl.sync();                                    // both CTAs' barriers exist before any st.async
+    tc::tc_fence_after();
+    const uint32_t tmem = *slot;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)l0;
+    const uint32_t idesc = tc::idesc_bf16_f32(MT, KC);
+    const uint32_t sx_addr = tc::smem_u32(sX), sat_addr = tc::smem_u32(sAT);
+    const uint32_t sbo = 16u * (uint32_t)K;
+    const uint32_t rx = tc::cluster_addr(sX, (uint32_t)peer);
+    const uint32_t rpsum = tc::cluster_addr(psum, (uint32_t)peer);
+    const uint32_t rmail = tc::cluster_addr(mail, (uint32_t)peer);
+    const uint32_t rbar0 = tc::cluster_addr(&bar[1], (uint32_t)peer);
+    const uint32_t rbar1 = tc::cluster_addr(&bar[2], (uint32_t)peer);
+    // bytes a CTA receives per step: the peer's half of X, its partial sums, and (CTA 1) the
+    // popped indices
+    const uint32_t xbytes = (uint32_t)(MT * KC * 2 + MT * NSPLIT * 4 + (rank == 1 ? MT * 4 : 0));
+
+    const bool owner = part == 0 && has_row;
+    int64_t seq = -1, T = 0, pos = 0, E = 0;     // seq: -1 none, -2 waiting for CTA 0's index
+    const int32_t* o = nullptr;
+    int32_t nob = 0;
+    int32_t kcur = 0;
+    float uprev = 0.f;
+    bool queue_empty = !has_row || row >= rows_active;
+    const int64_t qbase = (int64_t)rows_active * ncl;   // the first rows_active x ncl entries are dealt out
+
+    auto load_emis = [&](int ob, int jc, float (&b)[32], float scale) {
+        const int qb = ((jc >> 3) + ob) % nchh;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = qb + u < nchh ? qb + u : qb + u - nchh;
+            uint4 r = *reinterpret_cast<const uint4*>(sE + ob * KC * 2 + q * 16);
+            b[8 * u + 0] = bf_lo(r.x) * scale; b[8 * u + 1] = bf_hi(r.x) * scale;
+            b[8 * u + 2] = bf_lo(r.y) * scale; b[8 * u + 3] = bf_hi(r.y) * scale;
+            b[8 * u + 4] = bf_lo(r.z) * scale; b[8 * u + 5] = bf_hi(r.z) * scale;
+            b[8 * u + 6] = bf_lo(r.w) * scale; b[8 * u + 7] = bf_hi(r.w) * scale;
+        }
+    };
+    // columns [jc, jc+32) of this half: X = a o bs packed to BF16 into buffer xb of both CTAs;
+    // returns their sum (a fixed pairwise tree)
+    auto epi_chunk = [&](const float* a, const float (&bs)[32], int jc, uint32_t xo, uint32_t rb) -> float {
+        float part8[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = a[8 * u + e] * bs[8 * u + e];
+            uint4 pk;
+            pk.x = pack_bf16(v[0], v[1]);
+            pk.y = pack_bf16(v[2], v[3]);
+            pk.z = pack_bf16(v[4], v[5]);
+            pk.w = pack_bf16(v[6], v[7]);
+            const uint32_t co = xo + canon_off(row, rank * KC + jc + 8 * u, K);
+            *reinterpret_cast<uint4*>(sX + co) = pk;
+            tc::st_async_u4(rx + co, pk, rb);
+            part8[2 * u] = (v[0] + v[1]) + (v[2] + v[3]);
+            part8[2 * u + 1] = (v[4] + v[5]) + (v[6] + v[7]);
+        }
+        return ((part8[0] + part8[1]) + (part8[2] + part8[3])) + ((part8[4] + part8[5]) + (part8[6] + part8[7]));
+    };
+    auto start = [&](int32_t sq) {
+        seq = sq;
+        const int64_t o0 = off[sq];
+        T = off[sq + 1] - o0;
+        o = obs + o0;
+        pos = 0;
+        E = 0;
+        kcur = 0;
+        nob = T > 1 ? o[1] : 0;
+        rinfo[row].ob = (int16_t)(-(o[0] + 2));
+        rinfo[row].k = 0;
+    };
+    auto idle = [&](int64_t state) {
+        seq = state;
+        rinfo[row].ob = -1;
+        rinfo[row].k = 0;
+    };
+    if (owner) {
+        const int64_t q0 = (int64_t)row * ncl + cid;
+        if (row < rows_active && q0 < S) start(order[q0]);
+        else idle(-1);
+    }
+
+    uint32_t xph = 0;                             // bit p: parity of the next completion of exchange barrier p
+    for (uint32_t iter = 0;; ++iter) {
+        const int par = (int)(iter & 1u);
+        // ---- (A) X_{t-1} complete in buffer par^1; the MMAs of this step
+        tc::fence_proxy_async_smem();
+        tc::tc_fence_before();
+        const bool any = __syncthreads_or(owner && seq != -1);
+        if (*s_flag != 0) {
+            if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            break;
+        }
+        if (!any) break;
+        if (tid == kRows) {                       // a thread of column part 1: never a row owner
+            tc::fence_proxy_async_smem();
+            tc::tc_fence_after();
+            const uint32_t xa = sx_addr + (uint32_t)(par ^ 1) * L.x_bytes;
+            for (int ks = 0; ks < K / 16; ++ks) {
+                uint64_t ad = tc::smem_desc_noswizzle(xa + ks * 256, 128, sbo);
+                uint64_t bd = tc::smem_desc_noswizzle(sat_addr + ks * 256, 128, sbo);
+                tc::mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&bar[0]);
+        }
+        // ---- bookkeeping of the previous step's rows (both CTAs alike), overlapping the MMAs
+        if (owner && iter > 0) {
+            const int pp = par ^ 1;
+            if (seq == -2) {
+                const int32_t sq = mail[pp * MT + row];
+                if (sq >= 0) start(sq);
+                else idle(-1);
+            } else if (seq >= 0) {
+                float s = 0.f;
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int q = 0; q < NSPLIT; ++q) s += psum[((pp * 2 + c) * NSPLIT + q) * MT + row];
+                if (pos == T - 1) {
+                    if (rank == 0) {
+                        loglik[seq] = 0.6931471805599453 * (double)E + log((double)s);
+                        int32_t sq = -1;
+                        if (!queue_empty) {
+                            const int64_t q = qbase + (int64_t)atomicAdd(next, 1ull);
+                            if (q >= S) queue_empty = true;
+                            else sq = order[q];
+                        }
+                        mail[par * MT + row] = sq;
+                    }
+                    idle(-2);
+                } else {
+                    E += kcur;
+                    const float ls = __log2f(s);
+                    const float u = ls - (float)kcur;
+                    const float lr = pos == 0 ? ls : ls - uprev;
+                    uprev = u;
+                    kcur = (int)rintf(u + lr);
+                    ++pos;
+                    rinfo[row].ob = (int16_t)nob;
+                    rinfo[row].k = (int16_t)kcur;
+                    nob = pos + 1 < T ? o[pos + 1] : 0;
+                }
+            }
+        }
+        const uint32_t rb = par ? rbar1 : rbar0;
+        if (rank == 0 && owner) tc::st_async_u1(rmail + 4u * (uint32_t)(par * MT + row), (uint32_t)mail[par * MT + row], rb);
+        __syncthreads();
+        // ---- (B) epilogue of this CTA's columns into buffer par of both CTAs
+        const RowInfo ri = rinfo[row];
+        const bool fresh = has_row && ri.ob <= -2;
+        const bool act = has_row && ri.ob >= 0;
+        const int ob = fresh ? -ri.ob - 2 : ri.ob;
+        const float mult = ldexpf(1.0f, -(int)ri.k);
+        const uint32_t xo = (uint32_t)par * L.x_bytes;
+        float bs[32];
+        if (act || fresh) load_emis(ob, l0, bs, mult);
+        const bool ok = tc::mbar_wait_bounded(&bar[0], iter & 1u, kWaitNs);
+        if (!ok) *s_flag = 1;
+        tc::tc_fence_after();
+        float ps = 0.f;
+        if (__any_sync(0xffffffffu, act)) {
+            if (NSPLIT == 2 && KH % 64 == 0) {    // (4 parts of a half row are 32 columns at most)
+                for (int jc = 0; jc < KH; jc += 64) {
+                    uint32_t d[64];
+                    tc::tmem_ld64(taddr + jc, d);
+                    if (act) {
+                        if (jc > 0) load_emis(ob, l0 + jc, bs, mult);
+                        ps += epi_chunk(reinterpret_cast<const float*>(d), bs, l0 + jc, xo, rb);
+                        load_emis(ob, l0 + jc + 32, bs, mult);
+                        ps += epi_chunk(reinterpret_cast<const float*>(d) + 32, bs, l0 + jc + 32, xo, rb);
+                    }
+                }
+            } else {
+                for (int jc = 0; jc < KH; jc += 32) {
+                    uint32_t d[32];
+                    tc::tmem_ld32(taddr + jc, d);
+                    if (act) {
+                        if (jc > 0) load_emis(ob, l0 + jc, bs, mult);
+                        ps += epi_chunk(reinterpret_cast<const float*>(d), bs, l0 + jc, xo, rb);
+                    }
+                }
+            }
+            ps *= ldexpf(1.0f, (int)ri.k);
+        }
+        if (fresh) {
+            for (int jc = 0; jc < KH; jc += 32) {
+                if (jc > 0) load_emis(ob, l0 + jc, bs, 1.f);
+                float pv[32];
+#pragma unroll
+                for (int u = 0; u < 32; ++u) pv[u] = __expf(log_pi[g0 + jc + u]);
+                ps += epi_chunk(pv, bs, l0 + jc, xo, rb);
+            }
+        }
+        if (has_row && !act && !fresh) {
+            // no sequence on the row: zeros keep the peer's byte count fixed
+            for (int jc = 0; jc < KH; jc += 8) {
+                const uint32_t co = xo + canon_off(row, g0 + jc, K);
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4*>(sX + co) = z;
+                tc::st_async_u4(rx + co, z, rb);
+            }
+        }
+        if (has_row) {
+            const int idx = ((par * 2 + rank) * NSPLIT + part) * MT + row;
+            psum[idx] = ps;
+            tc::st_async1(rpsum + 4u * (uint32_t)idx, ps, rb);
+        }
+        // ---- the peer's half of X_t and its sums (bounded wait)
+        if (tid == 0) tc::mbar_arrive_expect_tx(&bar[1 + par], xbytes);
+        {
+            const uint32_t ph = (xph >> par) & 1u;
+            uint64_t t0 = 0;
+            for (uint32_t i = 0;; ++i) {
+                if (tc::mbar_try_wait_cluster(&bar[1 + par], ph)) break;
+                if ((i & 255) == 0) {
+                    const uint64_t now = tc::globaltimer_ns();
+                    if (i == 0) t0 = now;
+                    else if (now - t0 > kWaitNs) { *s_flag = 1; break; }
+                }
+            }
+            xph ^= 1u << par;
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tmem, (uint32_t)KC);
+    cl.sync();                                    // the peer no longer addresses this CTA's shared memory
+}
+
+// Clusters of the pair kernel that fit on the device at once (cached per kernel).
+template <typename Kern>
+static int pair_max_clusters(Kern kern, uint32_t smem, int threads) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, uint32_t>, int> cache;
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kern), smem);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(num_sms() & ~1), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    cache[key] = n;
+    return n;
+}
+
+static accel_status tc_forward_pair(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
+                                    double* loglik, char* ws, int32_t* d_status, TcConfig cfg, cudaStream_t st) {
+    const int K = mdl->K, M = mdl->M;
+    ACCEL_REQUIRE(tc_pair_supported(K, M, cfg.rows, cfg.split), ACCEL_ERR_UNSUPPORTED,
+                  "hmm_forward(bf16, pair): unsupported configuration (K=%d, M=%d, split=%d, rows=%d)", K, M,
+                  cfg.split, cfg.rows);
+    const int MT = cfg.rows <= 64 ? 64 : 128;
+    const PairLayout P = pair_layout(K, M, MT, cfg.split);
+    TcLayout L = tc_layout(K, M, S);
+    char* at = ws + L.at_off;
+    char* et = ws + L.e_off;
+    int32_t* order = (int32_t*)(ws + L.order_off);
+    unsigned long long* next = (unsigned long long*)(ws + kQueueOff);
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + kQueueOff, 0, 8, st));
+    int64_t nprep = (int64_t)K * K + (int64_t)K * M;
+    int pg = (int)((nprep + 255) / 256);
+    if (pg > 4 * num_sms()) pg = 4 * num_sms();
+    k_tc_prep<<<pg, 256, 0, st>>>(mdl->log_A, mdl->log_B, K, M, at, et);
+    accel_status r = order_by_length(off, S, order, ws + L.order_scratch_off, st);
+    if (r != ACCEL_OK) return r;
+    auto kern = cfg.split == 4 ? (MT == 64 ? k_hmm_tc_pair<4, 64> : k_hmm_tc_pair<4, 128>)
+                               : (MT == 64 ? k_hmm_tc_pair<2, 64> : k_hmm_tc_pair<2, 128>);
+    ACCEL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem_bytes));
+    const int maxcl = pair_max_clusters(kern, P.smem_bytes, 128 * cfg.split);
+    ACCEL_REQUIRE(maxcl > 0, ACCEL_ERR_UNSUPPORTED, "hmm_forward(bf16, pair): no cluster of two CTAs fits the device");
+    const int64_t tiles = (S + cfg.rows - 1) / cfg.rows;
+    const int ncl = (int)(tiles < maxcl ? tiles : maxcl);
+    kern<<<2 * ncl, 128 * cfg.split, P.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
+                                                         loglik, d_status, P);
+    return after_launch(st, "hmm_forward(bf16 tcgen05, cluster pair)", 5);
+}
+
 accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
                             double* loglik, char* ws, int32_t* d_status, TcConfig cfg, cudaStream_t st) {
     const int K = mdl->K, M = mdl->M;
@@ -360,6 +750,11 @@ accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, cons
                   "memory (K=%d, M=%d)", K, M);
     if (cfg.split == 4 && (K / 4) % 32 != 0) cfg.split = 2;
     if (cfg.rows < 32 || cfg.rows > kRows) cfg.rows = kRows;
+    if (cfg.pair) {
+        if (tc_pair_supported(K, M, cfg.rows, cfg.split))
+            return tc_forward_pair(mdl, obs, off, S, loglik, ws, d_status, cfg, st);
+        cfg.pair = 0;
+    }
     TcLayout L = tc_layout(K, M, S);
     char* at = ws + L.at_off;
     char* et = ws + L.e_off;

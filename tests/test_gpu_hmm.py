@@ -98,7 +98,7 @@ def test_single_step_sequences():
         _check(p, prec)
 
 
-def _force_config(tmp_path, K, M, S, split, rows, t):
+def _force_config(tmp_path, K, M, S, split, rows, t, pair=0):
     import json as _json
     path = str(tmp_path / "tune.jsonl")
     sl = 0
@@ -106,9 +106,9 @@ def _force_config(tmp_path, K, M, S, split, rows, t):
         sl += 1
     with open(path, "w") as f:
         f.write(_json.dumps({"kernel": "hmm_forward_bf16", "device": torch.cuda.get_device_name(), "K": K, "M": M,
-                             "S_log2": sl, "split": split, "rows": rows, "ms": 1.0}) + "\n")
+                             "S_log2": sl, "split": split, "rows": rows, "pair": pair, "ms": 1.0}) + "\n")
     ms, cfg = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], t["obs"], t["off"], cache_path=path)
-    assert ms == 0.0 and cfg == (split, rows)
+    assert ms == 0.0 and cfg == (split, rows, pair)
 
 
 @pytest.mark.parametrize("split,rows", [(2, 128), (4, 128), (4, 32), (2, 64), (4, 64), (2, 32)])
@@ -120,13 +120,36 @@ def test_bf16_tc_launch_configurations(tmp_path, split, rows):
     _check(p, acc.HMM_BF16_SCALED)
 
 
+# cluster pair (two CTAs split the state columns): K=128 runs 2 parts of 32 columns per
+# CTA, K=256 2 or 4 parts; 700 sequences over 32-row tiles also exercise the one-step hand-off
+# of queue indices from the first CTA of a pair to the second
+@pytest.mark.parametrize("K,split,rows", [(128, 2, 128), (128, 2, 32), (256, 4, 64), (256, 2, 128), (256, 4, 32)])
+def test_bf16_tc_cluster_pair(tmp_path, K, split, rows):
+    p = synth.hmm_workload(14, K, 40, 700, "loguniform", 1, 400)
+    logs, t, obs, off = _prep(p)
+    t["obs"], t["off"] = obs, off
+    _force_config(tmp_path, K, 40, 700, split, rows, t, pair=1)
+    _check(p, acc.HMM_BF16_SCALED)
+
+
+def test_bf16_tc_cluster_pair_batched_config_sampled(tmp_path):
+    c = synth.CFG_HMM_BATCHED
+    p = synth.hmm_workload(c["seed"], c["K"], c["M"], c["S"], c["kind"], c["lo"], c["hi"])
+    logs, t, obs, off = _prep(p)
+    t["obs"], t["off"] = obs, off
+    _force_config(tmp_path, c["K"], c["M"], c["S"], 4, 64, t, pair=1)
+    L = p["lengths"]
+    sample = sorted(set(np.argsort(L)[-6:].tolist() + np.argsort(L)[:4].tolist() + list(range(0, c["S"], 331))))
+    _check(p, acc.HMM_BF16_SCALED, sample=sample)
+
+
 def test_autotune_times_candidates_and_caches(tmp_path):
     c = synth.CFG_HMM_BATCHED
     p = synth.hmm_workload(c["seed"], c["K"], c["M"], 512, c["kind"], c["lo"], 600)
     logs, t, obs, off = _prep(p)
     path = str(tmp_path / "tune.jsonl")
     ms, cfg = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off, cache_path=path)
-    assert ms > 0.0 and cfg[0] in (2, 4) and cfg[1] in (32, 64, 128)
+    assert ms > 0.0 and cfg[0] in (2, 4) and cfg[1] in (32, 64, 128) and cfg[2] in (0, 1)
     with open(path) as f:
         assert "hmm_forward_bf16" in f.read()
     ms2, cfg2 = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off, cache_path=path)
