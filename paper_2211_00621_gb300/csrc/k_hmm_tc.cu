@@ -364,7 +364,9 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
 // runs the epilogue of its own columns (half the per-row work).  Each CTA writes its half of
 // X_t into its own tile and, with st.async, into its peer's, together with its partial row
 // sums; the stores count their bytes on the receiver's mbarrier of that step's parity, so a
-// CTA waits for its peer's half with no cluster barrier per step.  X is double-buffered by
+// CTA waits for its peer's half with no cluster barrier per step -- and only after issuing the
+// MMAs over its own half of X (half of the K/16 k-steps), which hide the exchange latency.
+// X is double-buffered by
 // step parity: a peer can be one step ahead and must not overwrite the tile the MMA reads.
 // Both CTAs do the same row bookkeeping on the same sums (added in the same order), so they
 // agree on every exponent and on the end of every sequence; CTA 0 alone writes logL and pops
@@ -423,13 +425,18 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     constexpr int kThreads = 128 * NSPLIT;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int quarter = w & 3, part = w >> 2;
-    constexpr int RPQ = MT / 4;
-    const bool has_row = lane < RPQ;
-    const int row = RPQ * quarter + (has_row ? lane : 0);
+    // MT = 128: row 32 q + lane of lane quarter q, one thread per row and part.  MT = 64: the
+    // rows sit in lanes 0-15 of each quarter, and threads t and t + 16 share row 16 q + t%16,
+    // each taking half of the part's columns (16-lane TMEM loads).
+    constexpr bool HL = MT == 64;
+    const int hsel = HL ? lane >> 4 : 0;
+    const int row = HL ? 16 * quarter + (lane & 15) : 32 * quarter + lane;
     const int KC = K / 2;                         // columns of this CTA
     const int KH = KC / NSPLIT;                   // columns per part
+    const int CPT = HL ? KH / 2 : KH;             // columns per thread
     const int l0 = part * KH;                     // first column of the part, within the half
-    const int g0 = rank * KC + l0;                // ... and in the full row
+    const int lt = l0 + hsel * CPT;               // first column of this thread, within the half
+    const int gt = rank * KC + lt;                // ... and in the full row
     const int nch = K >> 3, nchh = KC >> 3;
 
     // ---- stage this half of A^T (rows rank*KC.. of the canonical layout are one block) and
@@ -462,7 +469,7 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     cl.sync();                                    // both CTAs' barriers exist before any st.async
     tc::tc_fence_after();
     const uint32_t tmem = *slot;
-    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)l0;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(HL ? l0 : lt);
     const uint32_t idesc = tc::idesc_bf16_f32(MT, KC);
     const uint32_t sx_addr = tc::smem_u32(sX), sat_addr = tc::smem_u32(sAT);
     const uint32_t sbo = 16u * (uint32_t)K;
@@ -475,19 +482,20 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     // popped indices
     const uint32_t xbytes = (uint32_t)(MT * KC * 2 + MT * NSPLIT * 4 + (rank == 1 ? MT * 4 : 0));
 
-    const bool owner = part == 0 && has_row;
+    const bool owner = part == 0 && hsel == 0;
     int64_t seq = -1, T = 0, pos = 0, E = 0;     // seq: -1 none, -2 waiting for CTA 0's index
     const int32_t* o = nullptr;
     int32_t nob = 0;
     int32_t kcur = 0;
     float uprev = 0.f;
-    bool queue_empty = !has_row || row >= rows_active;
+    bool queue_empty = row >= rows_active;
     const int64_t qbase = (int64_t)rows_active * ncl;   // the first rows_active x ncl entries are dealt out
 
-    auto load_emis = [&](int ob, int jc, float (&b)[32], float scale) {
+    // emission b(j, ob) for the 16 columns [jc, jc+16) of this half, times `scale` (a power of two)
+    auto load_emis = [&](int ob, int jc, float (&b)[16], float scale) {
         const int qb = ((jc >> 3) + ob) % nchh;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             const int q = qb + u < nchh ? qb + u : qb + u - nchh;
             uint4 r = *reinterpret_cast<const uint4*>(sE + ob * KC * 2 + q * 16);
             b[8 * u + 0] = bf_lo(r.x) * scale; b[8 * u + 1] = bf_hi(r.x) * scale;
@@ -496,12 +504,12 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
             b[8 * u + 6] = bf_lo(r.w) * scale; b[8 * u + 7] = bf_hi(r.w) * scale;
         }
     };
-    // columns [jc, jc+32) of this half: X = a o bs packed to BF16 into buffer xb of both CTAs;
-    // returns their sum (a fixed pairwise tree)
-    auto epi_chunk = [&](const float* a, const float (&bs)[32], int jc, uint32_t xo, uint32_t rb) -> float {
-        float part8[8];
+    // columns [jc, jc+16) of this half: X = a o bs packed to BF16 into the buffer at xo of both
+    // CTAs; returns their sum (a fixed pairwise tree)
+    auto epi16 = [&](const float* a, const float (&bs)[16], int jc, uint32_t xo, uint32_t rb) -> float {
+        float part4[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             float v[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] = a[8 * u + e] * bs[8 * u + e];
@@ -513,10 +521,10 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
             const uint32_t co = xo + canon_off(row, rank * KC + jc + 8 * u, K);
             *reinterpret_cast<uint4*>(sX + co) = pk;
             tc::st_async_u4(rx + co, pk, rb);
-            part8[2 * u] = (v[0] + v[1]) + (v[2] + v[3]);
-            part8[2 * u + 1] = (v[4] + v[5]) + (v[6] + v[7]);
+            part4[2 * u] = (v[0] + v[1]) + (v[2] + v[3]);
+            part4[2 * u + 1] = (v[4] + v[5]) + (v[6] + v[7]);
         }
-        return ((part8[0] + part8[1]) + (part8[2] + part8[3])) + ((part8[4] + part8[5]) + (part8[6] + part8[7]));
+        return (part4[0] + part4[1]) + (part4[2] + part4[3]);
     };
     auto start = [&](int32_t sq) {
         seq = sq;
@@ -542,25 +550,58 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     }
 
     uint32_t xph = 0;                             // bit p: parity of the next completion of exchange barrier p
+    // bounded wait for the peer's bytes of step parity q
+    auto xchg_wait = [&](int q) {
+        const uint32_t ph = (xph >> q) & 1u;
+        uint64_t t0 = 0;
+        for (uint32_t i = 0;; ++i) {
+            if (tc::mbar_try_wait_cluster(&bar[1 + q], ph)) break;
+            if ((i & 255) == 0) {
+                const uint64_t now = tc::globaltimer_ns();
+                if (i == 0) t0 = now;
+                else if (now - t0 > kWaitNs) { *s_flag = 1; break; }
+            }
+        }
+        xph ^= 1u << q;
+    };
+    const int ks_own = rank * (KC / 16), ks_peer = (rank ^ 1) * (KC / 16);
+    // descriptors of k-step 0 of X buffer 0 and of A^T; a k-step is 256 bytes further (16 in
+    // the descriptor's address field), a buffer x_bytes
+    const uint64_t adesc0 = tc::smem_desc_noswizzle(sx_addr, 128, sbo);
+    const uint64_t bdesc0 = tc::smem_desc_noswizzle(sat_addr, 128, sbo);
+    const int nks = KC / 16;
     for (uint32_t iter = 0;; ++iter) {
         const int par = (int)(iter & 1u);
-        // ---- (A) X_{t-1} complete in buffer par^1; the MMAs of this step
+        // ---- (A) this CTA's half of X_{t-1} is complete (buffer par^1): its MMAs start while
+        // the peer's half is still in flight
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         const bool any = __syncthreads_or(owner && seq != -1);
-        if (*s_flag != 0) {
-            if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+        if (*s_flag != 0 || !any) {
+            if (*s_flag != 0 && tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            if (iter > 0) xchg_wait(par ^ 1);     // the peer's last stores have landed (bounded)
             break;
         }
-        if (!any) break;
+        const uint64_t xdesc = adesc0 + (uint64_t)((par ^ 1) * (L.x_bytes >> 4));
         if (tid == kRows) {                       // a thread of column part 1: never a row owner
-            tc::fence_proxy_async_smem();
             tc::tc_fence_after();
-            const uint32_t xa = sx_addr + (uint32_t)(par ^ 1) * L.x_bytes;
-            for (int ks = 0; ks < K / 16; ++ks) {
-                uint64_t ad = tc::smem_desc_noswizzle(xa + ks * 256, 128, sbo);
-                uint64_t bd = tc::smem_desc_noswizzle(sat_addr + ks * 256, 128, sbo);
-                tc::mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            uint64_t ad = xdesc + (uint64_t)(ks_own * 16), bd = bdesc0 + (uint64_t)(ks_own * 16);
+            tc::mma_bf16(tmem, ad, bd, idesc, 0u);
+            for (int u = 1; u < nks; ++u) {
+                ad += 16;
+                bd += 16;
+                tc::mma_bf16(tmem, ad, bd, idesc, 1u);
+            }
+        }
+        // the peer's half of X_{t-1}, its row sums and (CTA 1) the indices it popped
+        if (iter > 0) xchg_wait(par ^ 1);
+        if (tid == kRows) {
+            tc::fence_proxy_async_smem();         // the peer's stores, seen through the barrier, to the tensor core
+            uint64_t ad = xdesc + (uint64_t)(ks_peer * 16), bd = bdesc0 + (uint64_t)(ks_peer * 16);
+            for (int u = 0; u < nks; ++u) {
+                tc::mma_bf16(tmem, ad, bd, idesc, 1u);
+                ad += 16;
+                bd += 16;
             }
             tc::mma_commit(&bar[0]);
         }
@@ -608,79 +649,73 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
         __syncthreads();
         // ---- (B) epilogue of this CTA's columns into buffer par of both CTAs
         const RowInfo ri = rinfo[row];
-        const bool fresh = has_row && ri.ob <= -2;
-        const bool act = has_row && ri.ob >= 0;
+        const bool fresh = ri.ob <= -2;
+        const bool act = ri.ob >= 0;
         const int ob = fresh ? -ri.ob - 2 : ri.ob;
         const float mult = ldexpf(1.0f, -(int)ri.k);
         const uint32_t xo = (uint32_t)par * L.x_bytes;
-        float bs[32];
-        if (act || fresh) load_emis(ob, l0, bs, mult);
+        float bs[16];
+        if (act || fresh) load_emis(ob, lt, bs, mult);
         const bool ok = tc::mbar_wait_bounded(&bar[0], iter & 1u, kWaitNs);
         if (!ok) *s_flag = 1;
         tc::tc_fence_after();
         float ps = 0.f;
         if (__any_sync(0xffffffffu, act)) {
-            if (NSPLIT == 2 && KH % 64 == 0) {    // (4 parts of a half row are 32 columns at most)
-                for (int jc = 0; jc < KH; jc += 64) {
-                    uint32_t d[64];
-                    tc::tmem_ld64(taddr + jc, d);
+            if (HL) {
+                if (CPT == 16) {
+                    uint32_t d[16];
+                    tc::tmem_ld16x2_16(taddr, d);
+                    if (act) ps = epi16(reinterpret_cast<const float*>(d), bs, lt, xo, rb);
+                } else {
+                    uint32_t d[32];
+                    tc::tmem_ld16x2_32(taddr, d);
                     if (act) {
-                        if (jc > 0) load_emis(ob, l0 + jc, bs, mult);
-                        ps += epi_chunk(reinterpret_cast<const float*>(d), bs, l0 + jc, xo, rb);
-                        load_emis(ob, l0 + jc + 32, bs, mult);
-                        ps += epi_chunk(reinterpret_cast<const float*>(d) + 32, bs, l0 + jc + 32, xo, rb);
+                        ps = epi16(reinterpret_cast<const float*>(d), bs, lt, xo, rb);
+                        load_emis(ob, lt + 16, bs, mult);
+                        ps += epi16(reinterpret_cast<const float*>(d) + 16, bs, lt + 16, xo, rb);
                     }
                 }
             } else {
-                for (int jc = 0; jc < KH; jc += 32) {
+                for (int jc = 0; jc < CPT; jc += 32) {
                     uint32_t d[32];
                     tc::tmem_ld32(taddr + jc, d);
                     if (act) {
-                        if (jc > 0) load_emis(ob, l0 + jc, bs, mult);
-                        ps += epi_chunk(reinterpret_cast<const float*>(d), bs, l0 + jc, xo, rb);
+                        if (jc > 0) load_emis(ob, lt + jc, bs, mult);
+                        ps += epi16(reinterpret_cast<const float*>(d), bs, lt + jc, xo, rb);
+                        load_emis(ob, lt + jc + 16, bs, mult);
+                        ps += epi16(reinterpret_cast<const float*>(d) + 16, bs, lt + jc + 16, xo, rb);
                     }
                 }
             }
             ps *= ldexpf(1.0f, (int)ri.k);
         }
         if (fresh) {
-            for (int jc = 0; jc < KH; jc += 32) {
-                if (jc > 0) load_emis(ob, l0 + jc, bs, 1.f);
-                float pv[32];
+            // alpha~_0 = pi o b(o_0) for this thread's columns
+            for (int jc = 0; jc < CPT; jc += 16) {
+                if (jc > 0) load_emis(ob, lt + jc, bs, 1.f);
+                float pv[16];
 #pragma unroll
-                for (int u = 0; u < 32; ++u) pv[u] = __expf(log_pi[g0 + jc + u]);
-                ps += epi_chunk(pv, bs, l0 + jc, xo, rb);
+                for (int u = 0; u < 16; ++u) pv[u] = __expf(log_pi[gt + jc + u]);
+                ps += epi16(pv, bs, lt + jc, xo, rb);
             }
         }
-        if (has_row && !act && !fresh) {
+        if (!act && !fresh) {
             // no sequence on the row: zeros keep the peer's byte count fixed
-            for (int jc = 0; jc < KH; jc += 8) {
-                const uint32_t co = xo + canon_off(row, g0 + jc, K);
+            for (int jc = 0; jc < CPT; jc += 8) {
+                const uint32_t co = xo + canon_off(row, gt + jc, K);
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 *reinterpret_cast<uint4*>(sX + co) = z;
                 tc::st_async_u4(rx + co, z, rb);
             }
         }
-        if (has_row) {
+        if (HL) ps += __shfl_xor_sync(0xffffffffu, ps, 16);   // the row's two threads
+        if (hsel == 0) {
             const int idx = ((par * 2 + rank) * NSPLIT + part) * MT + row;
             psum[idx] = ps;
             tc::st_async1(rpsum + 4u * (uint32_t)idx, ps, rb);
         }
-        // ---- the peer's half of X_t and its sums (bounded wait)
+        // the peer's bytes of this step complete the barrier's phase (waited for next step)
         if (tid == 0) tc::mbar_arrive_expect_tx(&bar[1 + par], xbytes);
-        {
-            const uint32_t ph = (xph >> par) & 1u;
-            uint64_t t0 = 0;
-            for (uint32_t i = 0;; ++i) {
-                if (tc::mbar_try_wait_cluster(&bar[1 + par], ph)) break;
-                if ((i & 255) == 0) {
-                    const uint64_t now = tc::globaltimer_ns();
-                    if (i == 0) t0 = now;
-                    else if (now - t0 > kWaitNs) { *s_flag = 1; break; }
-                }
-            }
-            xph ^= 1u << par;
-        }
     }
     tc::tc_fence_before();
     __syncthreads();
