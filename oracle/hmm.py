@@ -14,6 +14,8 @@ forward-backward expected counts, in float64, with these readings:
   i->j transitions and d logL / d logB_jk the expected number of times state j emits k.
 
 Layouts: A[i, j] = P(z_{t+1}=j | z_t=i); B[j, k] = P(o_t=k | z_t=j); pi[j] = P(z_1=j).
+The re-estimation functions at the end (softmax-parameterised gradient, Baum-Welch M-step)
+are the textbook step after the expected counts.
 """
 from __future__ import annotations
 
@@ -153,3 +155,28 @@ def params_from_f32_logs(logs: dict) -> dict:
     return {"A": np.exp(logs["log_A"].astype(np.float64)),
             "B": np.exp(logs["log_B"].astype(np.float64)),
             "pi": np.exp(logs["log_pi"].astype(np.float64))}
+
+
+# ------------------------------------------------------------------------ re-estimation
+# The step after the adjoint in a training loop (textbook; not in the paper).  Each
+# parameter is a set of rows that are probability vectors: the rows of A (over j), the rows
+# of B (over k), and pi.  Both functions work on the last axis of their arguments.
+def softmax_rows_grad(logP: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Gradient with respect to unconstrained row parameters theta with P = softmax(theta)
+    along each row, given g = the gradient with respect to log P read as free parameters
+    (what expected_counts and gradients_batch return).  log P_ij = theta_ij - LSE_j' theta_ij',
+    so by the chain rule
+        dL/dtheta_ij = g_ij - P_ij * sum_j' g_ij',     P = softmax of the row of logP.
+    Rows of the result sum to zero (adding a constant to a row of theta changes nothing)."""
+    P = np.exp(logP - _lse(logP, axis=-1)[..., None])
+    return g - P * np.sum(g, axis=-1, keepdims=True)
+
+
+def mstep_rows(g: np.ndarray, logP_old: np.ndarray) -> np.ndarray:
+    """Baum-Welch re-estimation of row-stochastic parameters from their expected counts g:
+        P_new_ij = g_ij / sum_j' g_ij',   returned as log P_new.
+    A row whose counts sum to zero (no sequence visits the state) keeps log P_old."""
+    s = np.sum(g, axis=-1, keepdims=True)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        new = np.log(g) - np.log(s)
+    return np.where(s > 0, new, logP_old)

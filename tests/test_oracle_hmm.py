@@ -149,3 +149,95 @@ def test_bruteforce_expected_counts_random():
     np.testing.assert_allclose(xi2, xi, rtol=1e-12)
     np.testing.assert_allclose(cnt2, cnt, rtol=1e-12)
     np.testing.assert_allclose(g12, g1, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- re-estimation (next row)
+def _softmax(x):
+    e = np.exp(x - x.max(axis=-1, keepdims=True))
+    return e / e.sum(axis=-1, keepdims=True)
+
+
+def _small_problem(seed, K=3, M=4, lens=(5, 4, 6)):
+    rng = np.random.default_rng(seed)
+    th = {"A": rng.normal(size=(K, K)), "B": rng.normal(size=(K, M)), "pi": rng.normal(size=K)}
+    obs = [rng.integers(0, M, size=n) for n in lens]
+    return th, obs
+
+
+def _L_of_theta(th, obs):
+    A, B, pi = _softmax(th["A"]), _softmax(th["B"]), _softmax(th["pi"])
+    return sum(hmm.forward_log(np.log(A), np.log(B), np.log(pi), o) for o in obs)
+
+
+def _counts(P, obs):
+    K, M = P["B"].shape
+    gA, gB, gpi = np.zeros((K, K)), np.zeros((K, M)), np.zeros(K)
+    for o in obs:
+        _, xi, cnt, g1 = hmm.expected_counts(P["A"], P["B"], P["pi"], o)
+        gA += xi
+        gB += cnt
+        gpi += g1
+    return gA, gB, gpi
+
+
+def test_softmax_gradient_matches_central_differences():
+    # L(theta) through the log-space forward (a path that shares nothing with the counts)
+    th, obs = _small_problem(3)
+    P = {k: _softmax(v) for k, v in th.items()}
+    gA, gB, gpi = _counts(P, obs)
+    an = {"A": hmm.softmax_rows_grad(th["A"], gA), "B": hmm.softmax_rows_grad(th["B"], gB),
+          "pi": hmm.softmax_rows_grad(th["pi"], gpi)}
+    h = 1e-5
+    for name in ("A", "B", "pi"):
+        fd = np.zeros_like(th[name])
+        for idx in np.ndindex(th[name].shape):
+            tp = {k: v.copy() for k, v in th.items()}
+            tm = {k: v.copy() for k, v in th.items()}
+            tp[name][idx] += h
+            tm[name][idx] -= h
+            fd[idx] = (_L_of_theta(tp, obs) - _L_of_theta(tm, obs)) / (2 * h)
+        np.testing.assert_allclose(an[name], fd, rtol=1e-6, atol=1e-8)
+        np.testing.assert_allclose(an[name].sum(axis=-1), 0.0, atol=1e-12)   # row-shift invariance
+
+
+def test_mstep_single_state_is_empirical_symbol_frequencies():
+    # K = 1: the maximum-likelihood emission row is the symbol histogram, A and pi are 1
+    rng = np.random.default_rng(5)
+    M = 6
+    obs = [rng.integers(0, M, size=n) for n in (7, 3, 11)]
+    P = {"A": np.ones((1, 1)), "B": _softmax(rng.normal(size=(1, M))), "pi": np.ones(1)}
+    gA, gB, gpi = _counts(P, obs)
+    allobs = np.concatenate(obs)
+    hist = np.bincount(allobs, minlength=M) / len(allobs)
+    with np.errstate(divide="ignore"):
+        np.testing.assert_allclose(hmm.mstep_rows(gB, np.log(P["B"])), np.log(hist)[None, :], rtol=1e-13)
+    np.testing.assert_allclose(hmm.mstep_rows(gA, np.zeros((1, 1))), 0.0, atol=1e-15)
+    np.testing.assert_allclose(hmm.mstep_rows(gpi, np.zeros(1)), 0.0, atol=1e-15)
+    assert gA[0, 0] == pytest.approx(sum(len(o) - 1 for o in obs), rel=1e-13)
+
+
+def test_mstep_does_not_decrease_the_likelihood():
+    # Baum-Welch is an EM algorithm: every re-estimation step keeps or raises sum logL
+    th, obs = _small_problem(11, K=4, M=5, lens=(9, 6, 12, 5))
+    logP = {k: np.log(_softmax(v)) for k, v in th.items()}
+    prev = None
+    for _ in range(4):
+        P = {k: np.exp(v) for k, v in logP.items()}
+        L = sum(hmm.forward_log(logP["A"], logP["B"], logP["pi"], o) for o in obs)
+        if prev is not None:
+            assert L >= prev - 1e-10
+        prev = L
+        gA, gB, gpi = _counts(P, obs)
+        logP = {"A": hmm.mstep_rows(gA, logP["A"]), "B": hmm.mstep_rows(gB, logP["B"]),
+                "pi": hmm.mstep_rows(gpi, logP["pi"])}
+        for v in logP.values():
+            np.testing.assert_allclose(np.exp(v).sum(axis=-1), 1.0, rtol=1e-13)
+
+
+def test_mstep_row_without_counts_keeps_its_parameters():
+    g = np.array([[1.0, 3.0, 0.0], [0.0, 0.0, 0.0]])
+    old = np.log(np.array([[0.2, 0.3, 0.5], [0.1, 0.6, 0.3]]))
+    new = hmm.mstep_rows(g, old)
+    np.testing.assert_allclose(new[1], old[1])
+    np.testing.assert_allclose(new[0, :2], np.log([0.25, 0.75]), rtol=1e-15)
+    assert new[0, 2] == -np.inf
