@@ -9,6 +9,8 @@ HBM when the timed region starts:
   hmm_bf16    BF16 tensor-core scaled forward, K=256, M=64, 4,096 sequences, lengths
               log-uniform in [50, 5000], one persistent launch
   hmm_adjoint forward + adjoint, K=256, M=64, 1,024 sequences, lengths U{200..2000}
+  hmm_mstep   the re-estimation that follows: softmax-parameterised gradient and
+              Baum-Welch M-step from the adjoint's expected counts
   allpairs    records {pos: float3, mass: float} -> SoA, all-pairs softened gravity, N=65,536
 
 Metric: HMM state-steps per second (K x sum of lengths, counted once for every forward
@@ -118,6 +120,7 @@ def hmm_inputs(cfg, torch, dev):
     d["offsets"] = torch.from_numpy(p["offsets"]).to(dev)
     d["host"] = {"obs": p["obs"], "offsets": p["offsets"], **logs}
     d["K"], d["S"], d["sumT"], d["maxT"] = cfg["K"], cfg["S"], int(p["lengths"].sum()), int(p["lengths"].max())
+    d["M"] = cfg["M"]
     return d
 
 
@@ -223,6 +226,10 @@ class Workload:
                 return api.hmm_adjoint(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"],
                                        max_T=a["maxT"], want_loglik=True)
             out["adj"] = mark("hmm_adjoint", adjoint)
+            g = out["adj"]
+            # the re-estimation that follows the adjoint in a training step
+            out["mstep"] = mark("hmm_mstep", lambda: api.hmm_mstep(a["log_A"], a["log_B"], a["log_pi"], g[0], g[1],
+                                                                   g[2]))
 
         def allpairs():
             x, y, z, m = api.accel_marshal_records(self.aos, self.fields)
@@ -249,7 +256,8 @@ class Workload:
             d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
             gA, gB, gpi, ll = api.hmm_adjoint(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"],
                                               max_T=self.adj["maxT"], want_loglik=True)
-            res += [gA, gB, gpi, ll]
+            th, nw = api.hmm_mstep(d["log_A"], d["log_B"], d["log_pi"], gA, gB, gpi)
+            res += [gA, gB, gpi, ll, *th, *nw]
         aos = host["aos"].to(dev, non_blocking=True)
         x, y, z, mm = api.accel_marshal_records(aos, self.fields)
         res += list(api.pairwise_mapreduce(x, y, z, mm, self.eps))
@@ -309,6 +317,11 @@ def rooflines(W, row_ms, peaks, sm_mhz_max):
     q = W.bf16
     r["hmm_bf16"] = {"bound": "tensor", "achieved": 2 * q["K"] ** 2 * q["sumT"] / (row_ms["hmm_bf16"] * 1e-3) / 1e12,
                      "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+    if W.adj is not None and "hmm_mstep" in row_ms:
+        a = W.adj
+        nb = 16 * (a["K"] * a["K"] + a["K"] * a["M"] + a["K"])      # read log P and g, write two outputs
+        r["hmm_mstep"] = {"bound": "hbm", "achieved": nb / (row_ms["hmm_mstep"] * 1e-3) / 1e9,
+                          "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     if W.adj is not None and "hmm_adjoint" in row_ms:
         a = W.adj
         r["hmm_adjoint"] = {"bound": "alu", "achieved": 6 * a["K"] ** 2 * a["sumT"] / (row_ms["hmm_adjoint"] * 1e-3)

@@ -279,6 +279,28 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
                          float* d_grad_log_pi, void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * hmm_mstep -- re-estimation after hmm_adjoint (textbook HMM training step; the paper has no
+ * HMM; its shape is a map over parameter rows of reductions over the row followed by a map,
+ * Appendix A).  Each parameter is a set of probability rows: the K rows of A (over j), the K
+ * rows of B (over k) and pi.  Inputs: the model (its log parameters, device) and the
+ * gradients of L with respect to log A, log B, log pi read as free parameters, i.e. the
+ * expected counts d_grad_log_* that hmm_adjoint writes (device FP32, same layouts as the
+ * model; counts must be >= 0 for the M-step).  Outputs (device FP32, same layouts, caller
+ * owned; any of the six pointers may be NULL to skip that output):
+ *   d_grad_theta_*  gradient with respect to unconstrained row parameters theta with
+ *                   P = softmax(theta) along each row, taken at theta = log P:
+ *                   g_ij - P_ij sum_j' g_ij'  (each row sums to zero);
+ *   d_new_log_*     Baum-Welch M-step: log(g_ij / sum_j' g_ij'); a row whose counts sum to
+ *                   zero keeps its log P row.
+ * Row reductions in FP64; one warp per row.  Every row of log P needs a finite entry.
+ * Asynchronous on `stream`; errors: INVALID_ARG (null model or gradient), UNSUPPORTED (K, M).
+ */
+accel_status hmm_mstep(const accel_hmm_model* m, const float* d_grad_log_A, const float* d_grad_log_B,
+                       const float* d_grad_log_pi, float* d_grad_theta_A, float* d_grad_theta_B,
+                       float* d_grad_theta_pi, float* d_new_log_A, float* d_new_log_B,
+                       float* d_new_log_pi, void* stream);
+
+/*
  * hmm_autotune -- choose the launch configuration of the BF16 tensor-core forward (column
  * parts per row: 8 or 16 warps; sequence rows per tile: 128, 64 or 32; a tile on one CTA or
  * on a cluster of two CTAs that split the state columns) by timing each

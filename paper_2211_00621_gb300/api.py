@@ -242,6 +242,22 @@ def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | N
     return gA, gB, gpi, ll
 
 
+def hmm_mstep(log_A, log_B, log_pi, grad_log_A, grad_log_B, grad_log_pi, want_grad=True, want_new=True):
+    """Re-estimation after hmm_adjoint, from its gradients (the expected counts):
+    returns (grad_theta, new_log), each a tuple (A, B, pi) of float32 tensors or None --
+    the gradient for row-softmax parameters theta (P = softmax(theta) per row) and the
+    Baum-Welch M-step log parameters."""
+    lib = L.load()
+    _need_cuda(log_A, log_B, log_pi, grad_log_A, grad_log_B, grad_log_pi)
+    m = _model(log_A, log_B, log_pi)
+    gA, gB, gpi = (t.contiguous().to(torch.float32) for t in (grad_log_A, grad_log_B, grad_log_pi))
+    th = tuple(torch.empty_like(t) for t in (gA, gB, gpi)) if want_grad else (None, None, None)
+    nw = tuple(torch.empty_like(t) for t in (gA, gB, gpi)) if want_new else (None, None, None)
+    L.check("hmm_mstep", lib.hmm_mstep(C.byref(m), _ptr(gA), _ptr(gB), _ptr(gpi), _ptr(th[0]), _ptr(th[1]),
+                                       _ptr(th[2]), _ptr(nw[0]), _ptr(nw[1]), _ptr(nw[2]), _stream()))
+    return (th if want_grad else None), (nw if want_new else None)
+
+
 def hmm_autotune(log_A, log_B, log_pi, obs, offsets, precision=L.HMM_BF16_SCALED, cache_path=None, ws=None):
     """Times the BF16 forward's launch configurations on these inputs and keeps the fastest
     for later hmm_forward calls (and in `cache_path`, JSON lines, if given).  Returns
