@@ -640,6 +640,17 @@ def main():
                                               "ratio": row_ms["hmm_adjoint"] / fwd_only,
                                               "workspace_bytes": int(ws_bytes),
                                               "all_alphas_bytes": int(a["sumT"]) * a["K"] * 4}
+    # parallel-in-T forward on few, very long sequences, against the sequential FP32 forward
+    lg = hmm_inputs(synth.CFG_HMM_LONG, torch, dev)
+    long_ms = timed_once(lambda: api.hmm_forward_long(lg["log_A"], lg["log_B"], lg["log_pi"], lg["obs"], lg["offsets"],
+                                                      max_T=lg["maxT"]))
+    seq_ms = timed_once(lambda: api.hmm_forward(lg["log_A"], lg["log_B"], lg["log_pi"], lg["obs"], lg["offsets"],
+                                                api.HMM_FP32_LOG), reps=1)
+    compare["hmm_long_parallel_in_T"] = {
+        "workload": "K=64 M=32, 4 sequences x 250,000 steps", "ms": long_ms, "sequential_fp32_ms": seq_ms,
+        "speedup": seq_ms / long_ms, "state_steps_per_s": lg["K"] * lg["sumT"] / (long_ms * 1e-3),
+        # work of the method: one 64 x 64 x 64 product per step (2 K^3 flop)
+        "TFLOP/s": 2 * lg["K"] ** 3 * lg["sumT"] / (long_ms * 1e-3) / 1e12}
     compare["allpairs_interactions_per_s"] = W.N * W.N / (row_ms["allpairs"] * 1e-3)
     compare["segreduce_plain_form"] = {"ms": plain_form["ms"], "GB/s_equiv": plain_form["GB/s"],
                                        "fused_speedup": plain_form["ms"] / sweep["ms"]}

@@ -279,6 +279,25 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
                          float* d_grad_log_pi, void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * hmm_forward_long -- the same per-sequence log-likelihoods as hmm_forward, computed
+ * parallel-in-T for few, very long sequences.  The forward recursion is the chain of
+ * vector-matrix products alpha_T = (pi o b(o_1)) M_2 ... M_T with M_t = A diag(b(o_t));
+ * because matrix products are associative (the reduce pattern of Appendix A applied to the
+ * sequential loop of Listing 1), each sequence is cut into chunks whose products are formed
+ * in parallel (one K x K x K product per step, FP32, rows rescaled by exact powers of two),
+ * then folded into the vector chunk by chunk.  Depth T / chunks instead of T; work K^3 per
+ * step instead of K^2.
+ *  K <= 64 (UNSUPPORTED otherwise), S <= 65535, every T_s >= 1; max_T >= max_s T_s (it sets
+ *  the number of chunks per sequence).  Arguments and layouts as hmm_forward; d_ws
+ *  256-byte aligned, at least hmm_forward_long_workspace_size bytes (the chunk products:
+ *  16 KB per chunk).  Asynchronous on `stream`.
+ */
+size_t hmm_forward_long_workspace_size(const accel_hmm_model* m, int64_t S, int64_t total_T, int64_t max_T);
+accel_status hmm_forward_long(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets,
+                              int64_t S, int64_t total_T, int64_t max_T, double* d_loglik, void* d_ws,
+                              size_t ws_bytes, void* stream);
+
+/*
  * hmm_mstep -- re-estimation after hmm_adjoint (textbook HMM training step; the paper has no
  * HMM; its shape is a map over parameter rows of reductions over the row followed by a map,
  * Appendix A).  Each parameter is a set of probability rows: the K rows of A (over j), the K

@@ -242,6 +242,25 @@ def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | N
     return gA, gB, gpi, ll
 
 
+def hmm_forward_long(log_A, log_B, log_pi, obs, offsets, max_T: int | None = None, out=None, ws=None):
+    """logL per sequence (float64 [S]) computed parallel-in-T (chunked products of
+    A diag(b(o_t))), for few, very long sequences; K <= 64."""
+    lib = L.load()
+    _need_cuda(log_A, log_B, log_pi, obs, offsets)
+    m = _model(log_A, log_B, log_pi)
+    S = offsets.numel() - 1
+    if max_T is None:
+        max_T = int((offsets[1:] - offsets[:-1]).max().item()) if S else 0
+    need = lib.hmm_forward_long_workspace_size(C.byref(m), S, obs.numel(), max_T)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, obs.device)
+    if out is None:
+        out = torch.empty(S, dtype=torch.float64, device=obs.device)
+    L.check("hmm_forward_long", lib.hmm_forward_long(C.byref(m), _ptr(obs), _ptr(offsets), S, obs.numel(), max_T,
+                                                     _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
 def hmm_mstep(log_A, log_B, log_pi, grad_log_A, grad_log_B, grad_log_pi, want_grad=True, want_new=True):
     """Re-estimation after hmm_adjoint, from its gradients (the expected counts):
     returns (grad_theta, new_log), each a tuple (A, B, pi) of float32 tensors or None --

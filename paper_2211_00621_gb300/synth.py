@@ -135,3 +135,5 @@ CFG_HMM_PLAIN = dict(seed=0, K=64, M=32, S=512, kind="fixed", lo=1000, hi=1000)
 CFG_HMM_BATCHED = dict(seed=0, K=256, M=64, S=4096, kind="loguniform", lo=50, hi=5000)
 CFG_HMM_ADJOINT = dict(seed=0, K=256, M=64, S=1024, kind="uniform", lo=200, hi=2000)
 CFG_ALLPAIRS = dict(seed=0, N=65536, eps=1e-3)
+# few, very long sequences (the parallel-in-T forward); beside the hot-path rows, not in their step
+CFG_HMM_LONG = dict(seed=0, K=64, M=32, S=4, kind="fixed", lo=250000, hi=250000)
