@@ -57,6 +57,25 @@ def unmarshal_ragged(flat: np.ndarray, offsets: np.ndarray) -> list[np.ndarray]:
     return [flat[offsets[s]:offsets[s + 1]].copy() for s in range(len(offsets) - 1)]
 
 
+def marshal_nested(groups: list[list[np.ndarray]]) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """flatten applied twice, [[[T]]] -> (flat, sequence offsets, group offsets): the sequences
+    of all groups in order, as :func:`marshal_ragged`, and goffsets[g+1] = goffsets[g] +
+    (number of sequences in group g), indices into the sequence offsets."""
+    seqs = [s for g in groups for s in g]
+    flat, offsets = marshal_ragged(seqs)
+    G = len(groups)
+    goffsets = np.zeros(G + 1, dtype=np.int64)
+    for g in range(G):
+        goffsets[g + 1] = goffsets[g] + len(groups[g])
+    return flat, offsets, goffsets
+
+
+def unmarshal_nested(flat: np.ndarray, offsets: np.ndarray, goffsets: np.ndarray) -> list[list[np.ndarray]]:
+    """Inverse of :func:`marshal_nested`."""
+    seqs = unmarshal_ragged(flat, offsets)
+    return [seqs[goffsets[g]:goffsets[g + 1]] for g in range(len(goffsets) - 1)]
+
+
 def marshal_records(aos: np.ndarray, fields: list[tuple[int, np.dtype]]) -> list[np.ndarray]:
     """Records {l_i = e_i} (Fig. mexpr-ast) to one array per field (Sec. 3.3).
 

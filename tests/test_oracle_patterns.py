@@ -144,3 +144,36 @@ def test_segreduce_min_mul_builtin():
 def test_float_reduce_within_rounding(dt):
     x = synth.rng(4).standard_normal(1000).astype(dt)
     assert P.reduce_op(P.RED_ADD, x, np.float64) == pytest.approx(math.fsum(x.tolist()), rel=1e-12, abs=1e-12)
+
+
+# ------------------------------------------------------------ two-level flatten (next row 3)
+def _groups(seed, G=7):
+    rng = np.random.default_rng(seed)
+    out = []
+    for g in range(G):
+        n = int(rng.integers(0, 5))                       # empty groups included
+        out.append([rng.integers(-50, 50, size=int(rng.integers(0, 9))).astype(np.int32) for _ in range(n)])
+    return out
+
+
+def test_marshal_nested_roundtrip_and_offsets():
+    groups = _groups(4)
+    flat, off, goff = P.marshal_nested(groups)
+    back = P.unmarshal_nested(flat, off, goff)
+    assert len(back) == len(groups)
+    for a, b in zip(groups, back):
+        assert len(a) == len(b) and all(np.array_equal(x, y) for x, y in zip(a, b))
+    # the flat data is the concatenation of every sequence in order (reduce (++), Listing-1 style)
+    assert np.array_equal(flat, functools.reduce(lambda u, v: np.concatenate([u, v]),
+                                                 [s for g in groups for s in g], np.zeros(0, np.int32)))
+    assert goff[-1] == len(off) - 1 and off[-1] == len(flat)
+
+
+def test_nested_reduce_of_reduces_is_the_nested_python_sum():
+    # map (lam g. reduce (+) 0 (map (lam s. reduce (+) 0 s) g)) via two segmented reduces
+    groups = _groups(5, G=9)
+    flat, off, goff = P.marshal_nested(groups)
+    inner = P.segreduce(P.RED_ADD, P.MAP_IDENTITY, flat, off, np.int64)
+    outer = P.segreduce(P.RED_ADD, P.MAP_IDENTITY, inner, goff, np.int64)
+    expect = [sum(int(v) for s in g for v in s) for g in groups]
+    assert outer.tolist() == expect
