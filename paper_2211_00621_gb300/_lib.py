@@ -52,6 +52,10 @@ SIGNATURES = {
     "accel_launch_count": (C.c_uint64, []),
     "accel_marshal_ragged_workspace_size": (sz, [i64]),
     "accel_marshal_ragged": (i32, [vp, vp, i64, i32, vp, vp, vp, sz, vp]),
+    "accel_marshal_nested_workspace_size": (sz, [i64, i64]),
+    "accel_marshal_nested": (i32, [vp, vp, i64, vp, i64, i32, vp, vp, vp, vp, sz, vp]),
+    "accel_unmarshal_ragged_workspace_size": (sz, [i64]),
+    "accel_unmarshal_ragged": (i32, [vp, i64, vp, i64, i32, vp, vp, sz, vp]),
     "accel_marshal_records": (i32, [vp, i64, i32, i32, vp, vp, vp, i32, vp]),
     "accel_map": (i32, [i32, i32, vp, vp, i32, vp, i64, dbl, vp]),
     "accel_reduce_workspace_size": (sz, [i64, i32]),

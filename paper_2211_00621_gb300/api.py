@@ -102,6 +102,46 @@ def accel_marshal_ragged(seqs, dtype=torch.int32, device="cuda"):
     return accel_marshal_ragged_table(RaggedTable(seqs, dtype), device)
 
 
+def accel_marshal_nested(groups, dtype=torch.int32, device="cuda"):
+    """Flatten [[[T]]] -- a list of groups, each a list of 1-D tensors (CUDA, or pinned CPU) --
+    into (flat data, int64 sequence offsets [S+1], int64 group offsets [G+1] into them)."""
+    lib = L.load()
+    seqs = [t for g in groups for t in g]
+    table = RaggedTable(seqs, dtype)
+    sizes = torch.tensor([len(g) for g in groups] or [0], dtype=torch.int64).pin_memory()
+    G = len(groups)
+    flat = torch.empty(table.total, dtype=dtype, device=device)
+    offsets = torch.empty(table.S + 1, dtype=torch.int64, device=device)
+    goffsets = torch.empty(G + 1, dtype=torch.int64, device=device)
+    ws = _ws(lib.accel_marshal_nested_workspace_size(table.S, G), device)
+    L.check("accel_marshal_nested", lib.accel_marshal_nested(
+        C.c_void_p(table.ptrs.data_ptr()), C.c_void_p(table.lengths.data_ptr()), table.S,
+        C.c_void_p(sizes.data_ptr()), G, _dt(dtype), _ptr(flat), _ptr(offsets), _ptr(goffsets), _ptr(ws), ws.numel(),
+        _stream()))
+    return flat, offsets, goffsets
+
+
+def accel_unmarshal_ragged(flat, offsets, pinned=True):
+    """The inverse of accel_marshal_ragged: a list of S tensors, sequence s = flat[offsets[s]
+    : offsets[s+1]], each in its own (pinned host, or device if pinned=False) buffer written
+    by the kernel.  Synchronizes the stream."""
+    lib = L.load()
+    _need_cuda(flat, offsets)
+    S = offsets.numel() - 1
+    off = offsets.cpu().tolist()
+    if pinned:
+        outs = [torch.empty(off[s + 1] - off[s], dtype=flat.dtype).pin_memory() for s in range(S)]
+    else:
+        outs = [torch.empty(off[s + 1] - off[s], dtype=flat.dtype, device=flat.device) for s in range(S)]
+    ptrs = torch.tensor([o.data_ptr() if o.numel() else 0 for o in outs] or [0], dtype=torch.int64).pin_memory()
+    ws = _ws(lib.accel_unmarshal_ragged_workspace_size(S), flat.device)
+    L.check("accel_unmarshal_ragged", lib.accel_unmarshal_ragged(_ptr(flat), flat.numel(), _ptr(offsets), S,
+                                                                 _dt(flat.dtype), C.c_void_p(ptrs.data_ptr()),
+                                                                 _ptr(ws), ws.numel(), _stream()))
+    torch.cuda.current_stream().synchronize()
+    return outs
+
+
 def accel_marshal_records(aos: torch.Tensor, fields, inverse_from=None):
     """Records -> structure of arrays.  ``aos`` is a CUDA tensor whose rows are records
     (any dtype; the record size is its row size in bytes); ``fields`` = [(byte offset,

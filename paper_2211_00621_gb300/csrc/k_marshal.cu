@@ -4,7 +4,16 @@
 //                              flat data + int64 offsets (flatten, Appendix A).
 //  K2 accel_marshal_records -- a sequence of records {l_i = e_i} stored as an array of
 //                              structures -> one array per field, or back.
+//  accel_marshal_nested     -- [[[T]]] (groups of separately stored sequences) -> flat data,
+//                              int64 offsets of the sequences, int64 offsets of the groups
+//                              into those (two levels of flatten).
+//  accel_unmarshal_ragged   -- the inverse of K1: flat data + offsets -> S separately stored
+//                              destination arrays (device memory or pinned host memory
+//                              written by the kernel directly).
 #include "common.cuh"
+
+#include <cstring>
+#include <vector>
 
 namespace accel {
 namespace marshal {
@@ -107,6 +116,43 @@ __global__ void __launch_bounds__(256) k_gather(const T* const* __restrict__ ptr
     }
 }
 
+// One warp per sequence: dst[s][k] = flat[off[s] + k] (the inverse of k_gather).
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(const T* __restrict__ flat, const int64_t* __restrict__ off, int64_t S,
+                                                T* const* __restrict__ ptrs) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < S; s += nwarps) {
+        const int64_t o = off[s];
+        const int64_t n = off[s + 1] - o;
+        const T* src = flat + o;
+        T* dst = ptrs[s];
+        for (int64_t base = 0; base < n; base += 32 * 8) {
+            T v[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                int64_t k = base + r * 32 + lane;
+                if (k < n) v[r] = src[k];
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                int64_t k = base + r * 32 + lane;
+                if (k < n) dst[k] = v[r];
+            }
+        }
+    }
+}
+
+// A host table into device memory, read before this returns: the bytes are first copied to
+// pageable memory, from which an asynchronous copy is staged by the driver before the call
+// returns (a copy straight from page-locked memory would read it later, in stream order).
+static cudaError_t table_to_device(void* d_dst, const void* h_src, size_t bytes, cudaStream_t st) {
+    std::vector<unsigned char> tmp(bytes);
+    if (bytes) std::memcpy(tmp.data(), h_src, bytes);
+    return cudaMemcpyAsync(d_dst, tmp.data(), bytes, cudaMemcpyHostToDevice, st);
+}
+
 size_t ws_layout(int64_t S, size_t* ptr_off, size_t* len_off, size_t* bsum_off) {
     int64_t nb = (S + kScanThreads - 1) / kScanThreads;
     *ptr_off = kStatusBytes;
@@ -198,8 +244,8 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
     int64_t* d_len = (int64_t*)(ws + lo);
     int64_t* d_bsum = (int64_t*)(ws + bo);
     const void** d_ptrs = (const void**)(ws + po);
-    ACCEL_CUDA_TRY(cudaMemcpyAsync(d_ptrs, h_ptrs, (size_t)S * sizeof(void*), cudaMemcpyHostToDevice, st));
-    ACCEL_CUDA_TRY(cudaMemcpyAsync(d_len, h_lengths, (size_t)S * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    ACCEL_CUDA_TRY(table_to_device(d_ptrs, h_ptrs, (size_t)S * sizeof(void*), st));
+    ACCEL_CUDA_TRY(table_to_device(d_len, h_lengths, (size_t)S * sizeof(int64_t), st));
     int64_t nb = (S + kScanThreads - 1) / kScanThreads;
     k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum);
     k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
@@ -213,6 +259,87 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
     else
         k_gather<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t* const*)d_ptrs, d_offsets, S, (int64_t*)d_flat);
     return after_launch(st, "accel_marshal_ragged", 4);
+}
+
+// offsets[0..n] = exclusive scan of the n host lengths (copied into the workspace first)
+static accel_status scan_lengths(const int64_t* h_len, int64_t n, int64_t* d_off, char* ws, cudaStream_t st) {
+    size_t po, lo, bo;
+    ws_layout(n, &po, &lo, &bo);
+    int64_t* d_len = (int64_t*)(ws + lo);
+    int64_t* d_bsum = (int64_t*)(ws + bo);
+    ACCEL_CUDA_TRY(table_to_device(d_len, h_len, (size_t)n * sizeof(int64_t), st));
+    int64_t nb = (n + kScanThreads - 1) / kScanThreads;
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, n, d_bsum);
+    k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
+    k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, n, d_bsum, d_off);
+    return ACCEL_OK;
+}
+
+size_t accel_marshal_nested_workspace_size(int64_t S, int64_t G) {
+    size_t a, b, c;
+    const size_t x = ws_layout(S < 0 ? 0 : S, &a, &b, &c), y = ws_layout(G < 0 ? 0 : G, &a, &b, &c);
+    return x > y ? x : y;
+}
+
+accel_status accel_marshal_nested(const void* const* h_ptrs, const int64_t* h_lengths, int64_t S,
+                                  const int64_t* h_group_sizes, int64_t G, int32_t dtype, void* d_flat,
+                                  int64_t* d_offsets, int64_t* d_group_offsets, void* d_ws, size_t ws_bytes,
+                                  void* stream) {
+    ACCEL_REQUIRE(G >= 0 && S >= 0, ACCEL_ERR_INVALID_ARG, "accel_marshal_nested: negative size");
+    ACCEL_REQUIRE(d_group_offsets && (G == 0 || h_group_sizes), ACCEL_ERR_INVALID_ARG, "accel_marshal_nested: null pointer");
+    ACCEL_REQUIRE(ws_bytes >= accel_marshal_nested_workspace_size(S, G), ACCEL_ERR_WORKSPACE,
+                  "accel_marshal_nested: workspace %zu < %zu bytes", ws_bytes, accel_marshal_nested_workspace_size(S, G));
+    int64_t total = 0;
+    for (int64_t g = 0; g < G; ++g) {
+        ACCEL_REQUIRE(h_group_sizes[g] >= 0, ACCEL_ERR_SHAPE, "accel_marshal_nested: group size[%lld] < 0", (long long)g);
+        total += h_group_sizes[g];
+    }
+    ACCEL_REQUIRE(total == S, ACCEL_ERR_SHAPE, "accel_marshal_nested: group sizes sum to %lld, not S=%lld",
+                  (long long)total, (long long)S);
+    // inner level: the sequences, as accel_marshal_ragged
+    accel_status r = accel_marshal_ragged(h_ptrs, h_lengths, S, dtype, d_flat, d_offsets, d_ws, ws_bytes, stream);
+    if (r != ACCEL_OK) return r;
+    // outer level: group offsets into the sequence offsets (stream order: after the gather)
+    cudaStream_t st = as_stream(stream);
+    if (G == 0) {
+        ACCEL_CUDA_TRY(cudaMemsetAsync(d_group_offsets, 0, sizeof(int64_t), st));
+        return after_launch(st, "accel_marshal_nested", 0);
+    }
+    r = scan_lengths(h_group_sizes, G, d_group_offsets, (char*)d_ws, st);
+    if (r != ACCEL_OK) return r;
+    return after_launch(st, "accel_marshal_nested", 3);
+}
+
+size_t accel_unmarshal_ragged_workspace_size(int64_t S) {
+    return align_up(kStatusBytes + (size_t)(S > 0 ? S : 0) * sizeof(void*), 256);
+}
+
+accel_status accel_unmarshal_ragged(const void* d_flat, int64_t N, const int64_t* d_offsets, int64_t S, int32_t dtype,
+                                    void* const* h_dst_ptrs, void* d_ws, size_t ws_bytes, void* stream) {
+    ACCEL_REQUIRE(S >= 0 && N >= 0, ACCEL_ERR_INVALID_ARG, "accel_unmarshal_ragged: negative size");
+    ACCEL_REQUIRE(dtype_valid(dtype), ACCEL_ERR_DTYPE, "accel_unmarshal_ragged: bad dtype");
+    ACCEL_REQUIRE(d_offsets && d_ws && (S == 0 || (h_dst_ptrs && d_flat)), ACCEL_ERR_INVALID_ARG,
+                  "accel_unmarshal_ragged: null pointer");
+    ACCEL_REQUIRE(((uintptr_t)d_ws % 256) == 0, ACCEL_ERR_INVALID_ARG, "accel_unmarshal_ragged: d_ws must be 256-byte aligned");
+    ACCEL_REQUIRE(ws_bytes >= accel_unmarshal_ragged_workspace_size(S), ACCEL_ERR_WORKSPACE,
+                  "accel_unmarshal_ragged: workspace %zu < %zu bytes", ws_bytes, accel_unmarshal_ragged_workspace_size(S));
+    if (S == 0) return ok();
+    cudaStream_t st = as_stream(stream);
+    char* ws = (char*)d_ws;
+    if (debug_mode()) {
+        accel_status r = debug_check_offsets(d_offsets, S, N, 0, ws + 0, st);
+        if (r != ACCEL_OK) return r;
+    }
+    void** d_ptrs = (void**)(ws + kStatusBytes);
+    ACCEL_CUDA_TRY(table_to_device(d_ptrs, h_dst_ptrs, (size_t)S * sizeof(void*), st));
+    int64_t blocks = (S + 7) / 8;
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (dtype_size(dtype) == 4)
+        k_scatter<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t*)d_flat, d_offsets, S, (int32_t* const*)d_ptrs);
+    else
+        k_scatter<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t*)d_flat, d_offsets, S, (int64_t* const*)d_ptrs);
+    return after_launch(st, "accel_unmarshal_ragged", 1);
 }
 
 accel_status accel_marshal_records(void* d_aos, int64_t n, int32_t record_bytes, int32_t nfields,
