@@ -128,6 +128,23 @@ def bodies(seed: int, N: int) -> dict:
     return {"pos": pos, "mass": mass, "aos": aos}
 
 
+# ----------------------------------------------------------- angular pair histogram
+def sphere_points(seed: int, N: int) -> np.ndarray:
+    """N points uniform on the unit sphere (normalised Gaussian vectors), float32 [N, 3]."""
+    g = rng(seed)
+    v = g.normal(size=(N, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v.astype(np.float32)
+
+
+def angle_edges(nbins: int, amin_arcmin: float, amax_arcmin: float) -> np.ndarray:
+    """nbins + 1 bin edges for angular separations log-spaced between amin and amax
+    arcminutes, given as their cosines (float32, strictly decreasing)."""
+    k = np.arange(nbins + 1, dtype=np.float64)
+    theta = amin_arcmin * (amax_arcmin / amin_arcmin) ** (k / nbins) * (np.pi / (180.0 * 60.0))
+    return np.cos(theta).astype(np.float32)
+
+
 # ------------------------------------------------------------------------ configs
 # The five workload configurations, by what they are.
 CFG_SEGREDUCE = dict(seed=0, S=4096, len_lo=0, len_hi=256, val_lo=-1000, val_hi=1000)
@@ -137,3 +154,5 @@ CFG_HMM_ADJOINT = dict(seed=0, K=256, M=64, S=1024, kind="uniform", lo=200, hi=2
 CFG_ALLPAIRS = dict(seed=0, N=65536, eps=1e-3)
 # few, very long sequences (the parallel-in-T forward); beside the hot-path rows, not in their step
 CFG_HMM_LONG = dict(seed=0, K=64, M=32, S=4, kind="fixed", lo=250000, hi=250000)
+# all-pairs angular histogram (tpacf shape): 20 log-spaced bins from 1 to 10,000 arcminutes
+CFG_PAIRHIST = dict(seed=0, N=32768, nbins=20, amin=1.0, amax=10000.0)
