@@ -651,6 +651,15 @@ def main():
         "speedup": seq_ms / long_ms, "state_steps_per_s": lg["K"] * lg["sumT"] / (long_ms * 1e-3),
         # work of the method: one 64 x 64 x 64 product per step (2 K^3 flop)
         "TFLOP/s": 2 * lg["K"] ** 3 * lg["sumT"] / (long_ms * 1e-3) / 1e12}
+    # all-pairs angular histogram (tpacf shape) on synthetic sphere points
+    ch = synth.CFG_PAIRHIST
+    pts = torch.from_numpy(synth.sphere_points(ch["seed"], ch["N"])).to(dev)
+    edges = synth.angle_edges(ch["nbins"], ch["amin"], ch["amax"])
+    hist_ms = timed_once(lambda: api.accel_pair_histogram(pts, edges))
+    npairs = ch["N"] * (ch["N"] - 1) // 2
+    compare["pair_histogram_tpacf"] = {"workload": f"N={ch['N']} points, {ch['nbins']} log-spaced bins "
+                                                   f"({ch['amin']:g}-{ch['amax']:g} arcmin), self pairs",
+                                       "ms": hist_ms, "pairs_per_s": npairs / (hist_ms * 1e-3)}
     compare["allpairs_interactions_per_s"] = W.N * W.N / (row_ms["allpairs"] * 1e-3)
     compare["segreduce_plain_form"] = {"ms": plain_form["ms"], "GB/s_equiv": plain_form["GB/s"],
                                        "fused_speedup": plain_form["ms"] / sweep["ms"]}

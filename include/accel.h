@@ -373,6 +373,25 @@ accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int
 accel_status hmm_tuned_config(int32_t K, int32_t M, int64_t S, int32_t* h_split, int32_t* h_rows,
                               int32_t* h_pair);
 
+/*
+ * accel_pair_histogram -- all-pairs histogram of angular separations (the two-point angular
+ * correlation, tpacf, that Table 1 lists among the paper's workloads): a map over point pairs
+ * of a bin lookup, reduced into a histogram.  Points are unit vectors in three float32
+ * arrays (device).  A pair's dot product d = (x_i x_j + y_i y_j) + z_i z_j is formed in FP32
+ * with every product and sum rounded separately (no fused multiply-add); its bin is the
+ * number of edges e_k >= d, for n_edges strictly decreasing float32 edges h_edges (host,
+ * read before return; e.g. cosines of increasing angles): bin 0 holds pairs closer than
+ * the first edge, bin n_edges those beyond the last.
+ *  Self mode (B is A: d_bx == d_ax, d_by == d_ay, d_bz == d_az and NB == NA): the
+ *  unordered pairs i < j of A.  Otherwise cross mode: all NA x NB pairs (i in A, j in B).
+ *  d_hist  device int64 [n_edges + 1], overwritten.  1 <= n_edges <= 31.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG (null, negative, NaN edge), SHAPE (edges
+ * not strictly decreasing), UNSUPPORTED (n_edges).
+ */
+accel_status accel_pair_histogram(const float* d_ax, const float* d_ay, const float* d_az, int64_t NA,
+                                  const float* d_bx, const float* d_by, const float* d_bz, int64_t NB,
+                                  const float* h_edges, int32_t n_edges, int64_t* d_hist, void* stream);
+
 /* ========================================================================= graphs */
 /*
  * Capture a sequence of library calls made on `stream` into an executable CUDA graph and

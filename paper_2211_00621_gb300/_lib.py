@@ -71,6 +71,7 @@ SIGNATURES = {
     "pairwise_mapreduce": (i32, [i32, vp, vp, vp, vp, i64, flt, vp, vp, vp, vp]),
     "hmm_forward_long_workspace_size": (sz, [C.POINTER(accel_hmm_model), i64, i64, i64]),
     "hmm_forward_long": (i32, [C.POINTER(accel_hmm_model), vp, vp, i64, i64, i64, vp, vp, sz, vp]),
+    "accel_pair_histogram": (i32, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, vp]),
     "hmm_mstep": (i32, [C.POINTER(accel_hmm_model), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "hmm_autotune": (i32, [C.POINTER(accel_hmm_model), i32, vp, vp, i64, i64, vp, vp, sz, C.c_char_p, vp, vp]),
     "hmm_tuned_config": (i32, [i32, i32, i64, vp, vp, vp]),

@@ -282,6 +282,22 @@ def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | N
     return gA, gB, gpi, ll
 
 
+def accel_pair_histogram(A, edges, B=None):
+    """Histogram (int64 [len(edges)+1]) of the angular separations of point pairs: A and B
+    are float32 [n, 3] unit vectors (CUDA); edges a strictly decreasing float32 sequence of
+    cosines.  B=None counts the pairs i < j of A, else every pair (i in A, j in B)."""
+    lib = L.load()
+    _need_cuda(A, B)
+    cols = [A[:, k].contiguous() for k in range(3)]
+    bcols = [B[:, k].contiguous() for k in range(3)] if B is not None else cols
+    e = torch.as_tensor(edges, dtype=torch.float32).contiguous().cpu()
+    hist = torch.empty(e.numel() + 1, dtype=torch.int64, device=A.device)
+    L.check("accel_pair_histogram", lib.accel_pair_histogram(
+        _ptr(cols[0]), _ptr(cols[1]), _ptr(cols[2]), A.shape[0], _ptr(bcols[0]), _ptr(bcols[1]), _ptr(bcols[2]),
+        B.shape[0] if B is not None else A.shape[0], C.c_void_p(e.data_ptr()), e.numel(), _ptr(hist), _stream()))
+    return hist
+
+
 def hmm_forward_long(log_A, log_B, log_pi, obs, offsets, max_T: int | None = None, out=None, ws=None):
     """logL per sequence (float64 [S]) computed parallel-in-T (chunked products of
     A diag(b(o_t))), for few, very long sequences; K <= 64."""
