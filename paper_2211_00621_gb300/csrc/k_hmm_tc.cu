@@ -183,6 +183,8 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     const uint32_t idesc = tc::idesc_bf16_f32(MT, K);
     const uint32_t sx_addr = tc::smem_u32(sX), sat_addr = tc::smem_u32(sAT);
     const uint32_t sbo = 16u * (uint32_t)K;
+    const uint64_t adesc0 = tc::smem_desc_noswizzle(sx_addr, 128, sbo);
+    const uint64_t bdesc0 = tc::smem_desc_noswizzle(sat_addr, 128, sbo);
 
     // row bookkeeping, kept by the row's owner thread (part 0)
     const bool owner = part == 0 && has_row;
@@ -272,10 +274,13 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         if (!any) break;
         if (tid == kRows) {              // a thread of column part 1: never a row owner
             tc::tc_fence_after();
-            for (int ks = 0; ks < K / 16; ++ks) {
-                uint64_t ad = tc::smem_desc_noswizzle(sx_addr + ks * 256, 128, sbo);
-                uint64_t bd = tc::smem_desc_noswizzle(sat_addr + ks * 256, 128, sbo);
-                tc::mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            // k-step ks is 256 bytes further: 16 in the descriptors' address field
+            uint64_t ad = adesc0, bd = bdesc0;
+            tc::mma_bf16(tmem, ad, bd, idesc, 0u);
+            for (int ks = 1; ks < K / 16; ++ks) {
+                ad += 16;
+                bd += 16;
+                tc::mma_bf16(tmem, ad, bd, idesc, 1u);
             }
             tc::mma_commit(bar);
         }

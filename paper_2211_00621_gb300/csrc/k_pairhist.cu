@@ -81,14 +81,24 @@ __global__ void __launch_bounds__(kThreads) k_pairhist(HistPrm p) {
         if (has_i) {
             // self mode, diagonal tile: only j > i
             const int jstart = (p.self && ta == tb) ? tid + 1 : 0;
-            for (int jj = jstart; jj < (int)nj; ++jj) {
+            auto bin_of = [&](int jj) {
                 const float d = __fadd_rn(__fadd_rn(__fmul_rn(xi, sx[jj]), __fmul_rn(yi, sy[jj])), __fmul_rn(zi, sz[jj]));
                 int b = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1)
                     if (se[b + step - 1] >= d) b += step;
-                cnt[b][tid] += 1u;
+                return b;
+            };
+            int jj = jstart;
+            // four independent lookups in flight, then their counts
+            for (; jj + 4 <= (int)nj; jj += 4) {
+                const int b0 = bin_of(jj), b1 = bin_of(jj + 1), b2 = bin_of(jj + 2), b3 = bin_of(jj + 3);
+                cnt[b0][tid] += 1u;
+                cnt[b1][tid] += 1u;
+                cnt[b2][tid] += 1u;
+                cnt[b3][tid] += 1u;
             }
+            for (; jj < (int)nj; ++jj) cnt[bin_of(jj)][tid] += 1u;
         }
     }
     __syncthreads();
