@@ -20,10 +20,10 @@
 // vector's own scale as a log2 sum in FP64.
 //
 // States are padded to KP = 64 (zero rows and columns of A, zero emissions); K <= 64.
-// Per step of phase 1 a CTA of 256 threads computes a 64 x 64 x 64 product from shared
-// memory (X stored transposed, A row-major; each thread a 4 x 4 block, float4 loads), scales
-// the columns by the step's emission (prefetched one step ahead), and renormalises its rows
-// with a half-warp max.  FP32 throughout; exponents int32.
+// Per step of phase 1 a CTA of 64 threads computes a 64 x 64 x 64 product from shared
+// memory (X stored transposed, A row-major; each thread an 8 x 8 block from four float4
+// loads per k, packed FP32 FMAs over column pairs), scales the columns by the step's emission (prefetched one step ahead), and
+// renormalises its rows with a max over the row's 8 lanes.  FP32 throughout; exponents int32.
 #include "common.cuh"
 #include "hmm_internal.cuh"
 
@@ -37,7 +37,7 @@ namespace hmm {
 namespace {
 
 constexpr int KP = 64;
-constexpr int kThreads = 256;
+constexpr int kChunkThreads = 64;       // chunk products: 8 x 8 outputs per thread
 
 struct LongPrm {
     const float* Ap;        // [KP][KP] exp(log A), zero padded
@@ -81,14 +81,14 @@ __device__ __forceinline__ void chunk_range(const LongPrm& p, int64_t s, int c, 
     if (t0 > t1) t0 = t1;
 }
 
-__global__ void __launch_bounds__(kThreads) k_long_chunk(LongPrm p) {
+__global__ void __launch_bounds__(kChunkThreads) k_long_chunk(LongPrm p) {
     __shared__ __align__(16) float sA[KP][KP];         // A[k][j]
     __shared__ __align__(16) float sX[2][KP][KP];      // X transposed: sX[b][k][i] = X[i][k]
     const int c = blockIdx.x;
     const int64_t s = blockIdx.y;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    const int i0 = 4 * ty, j0 = 4 * tx;
-    for (int idx = tid; idx < KP * KP / 4; idx += kThreads) {
+    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+    const int i0 = 8 * ty, j0 = 8 * tx;                // this thread's 8 x 8 block of X A
+    for (int idx = tid; idx < KP * KP / 4; idx += kChunkThreads) {
         reinterpret_cast<float4*>(&sA[0][0])[idx] = reinterpret_cast<const float4*>(p.Ap)[idx];
         const int k = (4 * idx) / KP, i = (4 * idx) % KP;    // identity
         reinterpret_cast<float4*>(&sX[0][0][0])[idx] =
@@ -96,61 +96,86 @@ __global__ void __launch_bounds__(kThreads) k_long_chunk(LongPrm p) {
     }
     int64_t o0, t0, t1;
     chunk_range(p, s, c, o0, t0, t1);
-    int32_t erow[4] = {0, 0, 0, 0};
-    float4 bn = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (t0 < t1) bn = *reinterpret_cast<const float4*>(p.BT + (int64_t)p.obs[o0 + t0] * KP + j0);
+    int32_t erow[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float4 bn0 = make_float4(0.f, 0.f, 0.f, 0.f), bn1 = bn0;
+    if (t0 < t1) {
+        const float4* bp = reinterpret_cast<const float4*>(p.BT + (int64_t)p.obs[o0 + t0] * KP + j0);
+        bn0 = bp[0];
+        bn1 = bp[1];
+    }
     __syncthreads();
     int buf = 0;
     for (int64_t t = t0; t < t1; ++t) {
-        float acc[4][4];
+        // packed FMAs over column pairs: (acc[a][2q], acc[a][2q+1]) += x[a] (A[k][2q], A[k][2q+1])
+        float2 acc2[8][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 8; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 8
+            for (int q = 0; q < 4; ++q) acc2[a][q] = make_float2(0.f, 0.f);
+#pragma unroll 4
         for (int k = 0; k < KP; ++k) {
             const float4 xa = *reinterpret_cast<const float4*>(&sX[buf][k][i0]);
-            const float4 ab = *reinterpret_cast<const float4*>(&sA[k][j0]);
-            const float xv[4] = {xa.x, xa.y, xa.z, xa.w}, av[4] = {ab.x, ab.y, ab.z, ab.w};
+            const float4 xb = *reinterpret_cast<const float4*>(&sX[buf][k][i0 + 4]);
+            const float4 aa = *reinterpret_cast<const float4*>(&sA[k][j0]);
+            const float4 ab = *reinterpret_cast<const float4*>(&sA[k][j0 + 4]);
+            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+            const float2 av[4] = {make_float2(aa.x, aa.y), make_float2(aa.z, aa.w), make_float2(ab.x, ab.y),
+                                  make_float2(ab.z, ab.w)};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 8; ++a) {
+                const float2 xx = make_float2(xv[a], xv[a]);
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], av[b], acc[a][b]);
+                for (int q = 0; q < 4; ++q) acc2[a][q] = __ffma2_rn(xx, av[q], acc2[a][q]);
+            }
         }
-        const float bv[4] = {bn.x, bn.y, bn.z, bn.w};
-        if (t + 1 < t1) bn = *reinterpret_cast<const float4*>(p.BT + (int64_t)p.obs[o0 + t + 1] * KP + j0);
+        float acc[8][8];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[a][2 * q] = acc2[a][q].x;
+                acc[a][2 * q + 1] = acc2[a][q].y;
+            }
+        const float bv[8] = {bn0.x, bn0.y, bn0.z, bn0.w, bn1.x, bn1.y, bn1.z, bn1.w};
+        if (t + 1 < t1) {
+            const float4* bp = reinterpret_cast<const float4*>(p.BT + (int64_t)p.obs[o0 + t + 1] * KP + j0);
+            bn0 = bp[0];
+            bn1 = bp[1];
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
             float m = 0.f;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
+            for (int b = 0; b < 8; ++b) {
                 acc[a][b] *= bv[b];
                 m = fmaxf(m, acc[a][b]);
             }
-            // the row's 16 threads are lanes tx of one half-warp
+            // the row's 8 threads are 8 consecutive lanes
 #pragma unroll
-            for (int d = 1; d < 16; d <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+            for (int d = 1; d < 8; d <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
             const int e = m > 0.f ? ilogbf(m) : 0;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = ldexpf(acc[a][b], -e);
+            for (int b = 0; b < 8; ++b) acc[a][b] = ldexpf(acc[a][b], -e);
             erow[a] += e;
         }
         float* dst = &sX[buf ^ 1][0][0];
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
+        for (int b = 0; b < 8; ++b) {
             *reinterpret_cast<float4*>(dst + (j0 + b) * KP + i0) = make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+            *reinterpret_cast<float4*>(dst + (j0 + b) * KP + i0 + 4) = make_float4(acc[4][b], acc[5][b], acc[6][b], acc[7][b]);
+        }
         buf ^= 1;
         __syncthreads();
     }
     const int64_t slot = s * p.nchunk + c;
     float* Xo = p.X + slot * KP * KP;
-    for (int idx = tid; idx < KP * KP; idx += kThreads) {
+    for (int idx = tid; idx < KP * KP; idx += kChunkThreads) {
         const int i = idx / KP, j = idx % KP;
         Xo[idx] = sX[buf][j][i];
     }
     if (tx == 0) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) p.E[slot * KP + i0 + a] = erow[a];
+        for (int a = 0; a < 8; ++a) p.E[slot * KP + i0 + a] = erow[a];
     }
 }
 
@@ -327,7 +352,7 @@ accel_status hmm_forward_long(const accel_hmm_model* m, const int32_t* d_obs, co
     int pg = (int)((nprep + 255) / 256);
     if (pg > 4 * num_sms()) pg = 4 * num_sms();
     k_long_prep<<<pg, 256, 0, st>>>(m->log_A, m->log_B, m->K, m->M, (float*)p.Ap, (float*)p.BT);
-    k_long_chunk<<<dim3((unsigned)nchunk, (unsigned)S), kThreads, 0, st>>>(p);
+    k_long_chunk<<<dim3((unsigned)nchunk, (unsigned)S), kChunkThreads, 0, st>>>(p);
     k_long_combine<<<(unsigned)S, KP, 0, st>>>(p);
     return after_launch(st, "hmm_forward_long", 3);
 }
