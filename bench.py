@@ -415,7 +415,7 @@ def segreduce_sweep(torch, dev, api, S=1 << 20, reps=10, plain=False):
 
 
 PROFILE_CASES = ("segreduce_sweep", "step", "hmm_plain", "hmm_bf16", "hmm_bf16_small", "hmm_adjoint",
-                 "hmm_adjoint_small", "allpairs")
+                 "hmm_adjoint_small", "allpairs", "hmm_long", "hmm_long_small", "pairhist", "pairhist_small")
 
 
 def profile_case(name, reps, torch, dev, tune_cache=None):
@@ -444,6 +444,17 @@ def profile_case(name, reps, torch, dev, tune_cache=None):
             if prec == api.HMM_BF16_SCALED:
                 api.hmm_autotune(h["log_A"], h["log_B"], h["log_pi"], h["obs"], h["offsets"], cache_path=tune_cache)
             fn = lambda: api.hmm_forward(h["log_A"], h["log_B"], h["log_pi"], h["obs"], h["offsets"], prec)
+    elif name in ("hmm_long", "hmm_long_small"):
+        cfg = synth.CFG_HMM_LONG if name == "hmm_long" else dict(synth.CFG_HMM_LONG, lo=20000, hi=20000)
+        h = hmm_inputs(cfg, torch, dev)
+        fn = lambda: api.hmm_forward_long(h["log_A"], h["log_B"], h["log_pi"], h["obs"], h["offsets"],
+                                          max_T=h["maxT"])
+    elif name in ("pairhist", "pairhist_small"):
+        ch = synth.CFG_PAIRHIST
+        n = ch["N"] if name == "pairhist" else 8192
+        pts = torch.from_numpy(synth.sphere_points(ch["seed"], n)).to(dev)
+        edges = synth.angle_edges(ch["nbins"], ch["amin"], ch["amax"])
+        fn = lambda: api.accel_pair_histogram(pts, edges)
     elif name == "allpairs":
         b = synth.bodies(0, synth.CFG_ALLPAIRS["N"])
         aos = torch.from_numpy(b["aos"]).to(dev)
