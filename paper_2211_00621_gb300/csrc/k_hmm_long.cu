@@ -81,16 +81,23 @@ __device__ __forceinline__ void chunk_range(const LongPrm& p, int64_t s, int c, 
     if (t0 > t1) t0 = t1;
 }
 
+// X is stored transposed, row k = column k of X, in 16-byte chunks of 4 entries; chunk q of
+// row k sits at chunk position q ^ xsw(k), so that the 8 rows a warp writes in one store hit
+// different banks (the readers of a row read whole chunks, unaffected).
+__device__ __forceinline__ int xsw(int k) { return (k >> 2) & 7; }
+
 __global__ void __launch_bounds__(kChunkThreads) k_long_chunk(LongPrm p) {
     __shared__ __align__(16) float sA[KP][KP];         // A[k][j]
-    __shared__ __align__(16) float sX[2][KP][KP];      // X transposed: sX[b][k][i] = X[i][k]
+    __shared__ __align__(16) float sX[2][KP][KP];      // X transposed (chunk-swizzled rows)
     const int c = blockIdx.x;
     const int64_t s = blockIdx.y;
     const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
-    const int i0 = 8 * ty, j0 = 8 * tx;                // this thread's 8 x 8 block of X A
+    // this thread's 8 x 8 block of X A: rows i0..i0+7, columns 4tx..4tx+3 and 32+4tx..32+4tx+3
+    // (the two float4 loads of a row of A by a warp then cover all banks once)
+    const int i0 = 8 * ty, jA = 4 * tx, jB = 32 + 4 * tx;
     for (int idx = tid; idx < KP * KP / 4; idx += kChunkThreads) {
         reinterpret_cast<float4*>(&sA[0][0])[idx] = reinterpret_cast<const float4*>(p.Ap)[idx];
-        const int k = (4 * idx) / KP, i = (4 * idx) % KP;    // identity
+        const int k = (4 * idx) / KP, i = 4 * (((4 * idx) % KP / 4) ^ xsw(k));   // identity
         reinterpret_cast<float4*>(&sX[0][0][0])[idx] =
             make_float4(k == i ? 1.f : 0.f, k == i + 1 ? 1.f : 0.f, k == i + 2 ? 1.f : 0.f, k == i + 3 ? 1.f : 0.f);
     }
@@ -99,9 +106,9 @@ __global__ void __launch_bounds__(kChunkThreads) k_long_chunk(LongPrm p) {
     int32_t erow[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     float4 bn0 = make_float4(0.f, 0.f, 0.f, 0.f), bn1 = bn0;
     if (t0 < t1) {
-        const float4* bp = reinterpret_cast<const float4*>(p.BT + (int64_t)p.obs[o0 + t0] * KP + j0);
-        bn0 = bp[0];
-        bn1 = bp[1];
+        const float* bp = p.BT + (int64_t)p.obs[o0 + t0] * KP;
+        bn0 = *reinterpret_cast<const float4*>(bp + jA);
+        bn1 = *reinterpret_cast<const float4*>(bp + jB);
     }
     __syncthreads();
     int buf = 0;
@@ -114,10 +121,11 @@ __global__ void __launch_bounds__(kChunkThreads) k_long_chunk(LongPrm p) {
             for (int q = 0; q < 4; ++q) acc2[a][q] = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int k = 0; k < KP; ++k) {
-            const float4 xa = *reinterpret_cast<const float4*>(&sX[buf][k][i0]);
-            const float4 xb = *reinterpret_cast<const float4*>(&sX[buf][k][i0 + 4]);
-            const float4 aa = *reinterpret_cast<const float4*>(&sA[k][j0]);
-            const float4 ab = *reinterpret_cast<const float4*>(&sA[k][j0 + 4]);
+            const int sk = xsw(k);
+            const float4 xa = *reinterpret_cast<const float4*>(&sX[buf][k][4 * ((2 * ty) ^ sk)]);
+            const float4 xb = *reinterpret_cast<const float4*>(&sX[buf][k][4 * ((2 * ty + 1) ^ sk)]);
+            const float4 aa = *reinterpret_cast<const float4*>(&sA[k][jA]);
+            const float4 ab = *reinterpret_cast<const float4*>(&sA[k][jB]);
             const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
             const float2 av[4] = {make_float2(aa.x, aa.y), make_float2(aa.z, aa.w), make_float2(ab.x, ab.y),
                                   make_float2(ab.z, ab.w)};
@@ -138,9 +146,9 @@ __global__ void __launch_bounds__(kChunkThreads) k_long_chunk(LongPrm p) {
             }
         const float bv[8] = {bn0.x, bn0.y, bn0.z, bn0.w, bn1.x, bn1.y, bn1.z, bn1.w};
         if (t + 1 < t1) {
-            const float4* bp = reinterpret_cast<const float4*>(p.BT + (int64_t)p.obs[o0 + t + 1] * KP + j0);
-            bn0 = bp[0];
-            bn1 = bp[1];
+            const float* bp = p.BT + (int64_t)p.obs[o0 + t + 1] * KP;
+            bn0 = *reinterpret_cast<const float4*>(bp + jA);
+            bn1 = *reinterpret_cast<const float4*>(bp + jB);
         }
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
@@ -161,8 +169,12 @@ __global__ void __launch_bounds__(kChunkThreads) k_long_chunk(LongPrm p) {
         float* dst = &sX[buf ^ 1][0][0];
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            *reinterpret_cast<float4*>(dst + (j0 + b) * KP + i0) = make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
-            *reinterpret_cast<float4*>(dst + (j0 + b) * KP + i0 + 4) = make_float4(acc[4][b], acc[5][b], acc[6][b], acc[7][b]);
+            const int j = b < 4 ? jA + b : jB + b - 4;
+            const int sj = xsw(j);
+            *reinterpret_cast<float4*>(dst + j * KP + 4 * ((2 * ty) ^ sj)) =
+                make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+            *reinterpret_cast<float4*>(dst + j * KP + 4 * ((2 * ty + 1) ^ sj)) =
+                make_float4(acc[4][b], acc[5][b], acc[6][b], acc[7][b]);
         }
         buf ^= 1;
         __syncthreads();
@@ -171,7 +183,7 @@ __global__ void __launch_bounds__(kChunkThreads) k_long_chunk(LongPrm p) {
     float* Xo = p.X + slot * KP * KP;
     for (int idx = tid; idx < KP * KP; idx += kChunkThreads) {
         const int i = idx / KP, j = idx % KP;
-        Xo[idx] = sX[buf][j][i];
+        Xo[idx] = sX[buf][j][4 * ((i >> 2) ^ xsw(j)) + (i & 3)];
     }
     if (tx == 0) {
 #pragma unroll
