@@ -667,16 +667,22 @@ struct MatRegs {
     }
 };
 
-// part[w][g][lane CW + h] = sum_{i in part w} X[g][i] Mx[i][lane CW + h], for the 16 g (the
-// second pass is skipped when the group has at most 8 sequences; its slots are then stale
-// and unused).
+// Rows of the partial sums are stored with their 16-byte chunks permuted: chunk q at chunk
+// position q ^ ((q >> 3) & 1).  The gather reads 8 consecutive floats per thread (16 threads
+// per row); unpermuted, those loads would use half of the banks twice.
+__device__ __forceinline__ int pswz(int q) { return q ^ ((q >> 3) & 1); }
+
+// part[w][g][lane CW + h] = sum_{i in part w} X[g][i] Mx[i][lane CW + h] (chunk-permuted), for
+// the 16 g (the second pass is skipped when the group has at most 8 sequences; its slots are
+// then stale and unused).
 template <int K>
 __device__ __forceinline__ void contract(const MatRegs<K>& m, const float* __restrict__ X, float* __restrict__ part,
                                          int gcount) {
     using S = Sh<K>;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float* xb = X + w * S::IPART;
-    float* pb = part + (w * kG) * S::Kh + lane * S::CW;
+    // this lane's CW columns within a row: chunk (lane CW) / 4, offset (lane CW) % 4
+    float* pb = part + (w * kG) * S::Kh + 4 * pswz((lane * S::CW) >> 2) + ((lane * S::CW) & 3);
 #pragma unroll
     for (int ps = 0; ps < S::NPASS; ++ps) {
         if (ps > 0 && ps * S::GP >= gcount) break;   // (uniform) a group of at most GP sequences
@@ -739,15 +745,31 @@ __device__ __forceinline__ void stv(float* dst, const float (&v)[EC]) {
     }
 }
 
+// EC consecutive floats from column c0 of a chunk-permuted partial-sum row.
+template <int EC>
+__device__ __forceinline__ void ldv_part(const float* __restrict__ row, int c0, float (&v)[EC]) {
+    if constexpr (EC % 4 == 0) {
+#pragma unroll
+        for (int e = 0; e < EC; e += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(row + 4 * pswz((c0 + e) >> 2));
+            v[e] = x.x; v[e + 1] = x.y; v[e + 2] = x.z; v[e + 3] = x.w;
+        }
+    } else {
+        const float2 x = *reinterpret_cast<const float2*>(row + 4 * pswz(c0 >> 2) + (c0 & 3));
+        v[0] = x.x; v[1] = x.y;
+    }
+}
+
 // o = sum over the 8 warps' partials of the thread's epilogue outputs (fixed order).
 template <int K>
 __device__ __forceinline__ void gather(const float* __restrict__ part, int g, int c0, float (&o)[Sh<K>::EC]) {
     using S = Sh<K>;
-    ldv<S::EC>(part + g * S::Kh + c0, o);
+    static_assert(S::EC % 4 == 0 || S::EC == 2, "gather: 2 or a multiple of 4 floats per thread");
+    ldv_part<S::EC>(part + g * S::Kh, c0, o);
 #pragma unroll
     for (int w = 1; w < kNW; ++w) {
         float v[S::EC];
-        ldv<S::EC>(part + (w * kG + g) * S::Kh + c0, v);
+        ldv_part<S::EC>(part + (w * kG + g) * S::Kh, c0, v);
 #pragma unroll
         for (int e = 0; e < S::EC; ++e) o[e] += v[e];
     }
