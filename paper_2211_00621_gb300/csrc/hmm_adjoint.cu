@@ -616,6 +616,14 @@ __device__ void round_bounds_gs(GS& gs, int r) {
 }
 
 // dst[k][c] = BT[k][r Kh + c]
+// Rows of the shared-memory arrays that the epilogue threads address 8 floats at a time
+// (16 threads per row: the vectors X, the emission half-rows, the partial sums, the S_t rows)
+// are stored with their 16-byte chunks permuted: chunk q at chunk position q ^ ((q >> 3) & 1).
+// Unpermuted, those accesses would use half of the banks twice.  (An involution: the same
+// function maps positions back to chunks.)
+__device__ __forceinline__ int pswz(int q) { return q ^ ((q >> 3) & 1); }
+__device__ __forceinline__ int pcol(int col) { return 4 * pswz(col >> 2) + (col & 3); }
+
 template <int K>
 __device__ void load_bt(const float* __restrict__ BT, int M, int r, float* dst) {
     using S = Sh<K>;
@@ -631,7 +639,7 @@ __device__ void load_bt(const float* __restrict__ BT, int M, int r, float* dst) 
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int idx = b0 + e * kT;
-            if (idx < N) *reinterpret_cast<float4*>(dst + 4 * idx) = v[e];
+            if (idx < N) *reinterpret_cast<float4*>(dst + (idx / Q) * S::Kh + 4 * pswz(idx % Q)) = v[e];
         }
     }
 }
@@ -646,19 +654,23 @@ struct MatRegs {
     __device__ void load(const float* __restrict__ Mx, int Kp, int r) {
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const float* base = Mx + (int64_t)(w * S::IPART) * Kp + r * S::Kh + lane * S::CW;
+        const int cb = w * S::IPART / 4;   // first chunk of the warp's part of a vector
 #pragma unroll
         for (int q = 0; q < S::IPART / 2; ++q) {
+            // the contraction reads the vector's chunk positions in order; position q/2 holds
+            // chunk pswz(cb + q/2), so the matrix rows are taken in that order
+            const int lr = 4 * (pswz(cb + (q >> 1)) - cb) + 2 * (q & 1);
             float v0[S::CW], v1[S::CW];
             if constexpr (S::CW == 4) {
-                const float4 x0 = *reinterpret_cast<const float4*>(base + (int64_t)(2 * q) * Kp);
-                const float4 x1 = *reinterpret_cast<const float4*>(base + (int64_t)(2 * q + 1) * Kp);
+                const float4 x0 = *reinterpret_cast<const float4*>(base + (int64_t)lr * Kp);
+                const float4 x1 = *reinterpret_cast<const float4*>(base + (int64_t)(lr + 1) * Kp);
                 v0[0] = x0.x; v0[1] = x0.y; v0[2] = x0.z; v0[3] = x0.w;
                 v1[0] = x1.x; v1[1] = x1.y; v1[2] = x1.z; v1[3] = x1.w;
             } else {
 #pragma unroll
                 for (int h = 0; h < S::CW; ++h) {
-                    v0[h] = base[(int64_t)(2 * q) * Kp + h];
-                    v1[h] = base[(int64_t)(2 * q + 1) * Kp + h];
+                    v0[h] = base[(int64_t)lr * Kp + h];
+                    v1[h] = base[(int64_t)(lr + 1) * Kp + h];
                 }
             }
 #pragma unroll
@@ -666,11 +678,6 @@ struct MatRegs {
         }
     }
 };
-
-// Rows of the partial sums are stored with their 16-byte chunks permuted: chunk q at chunk
-// position q ^ ((q >> 3) & 1).  The gather reads 8 consecutive floats per thread (16 threads
-// per row); unpermuted, those loads would use half of the banks twice.
-__device__ __forceinline__ int pswz(int q) { return q ^ ((q >> 3) & 1); }
 
 // part[w][g][lane CW + h] = sum_{i in part w} X[g][i] Mx[i][lane CW + h] (chunk-permuted), for
 // the 16 g (the second pass is skipped when the group has at most 8 sequences; its slots are
@@ -745,9 +752,9 @@ __device__ __forceinline__ void stv(float* dst, const float (&v)[EC]) {
     }
 }
 
-// EC consecutive floats from column c0 of a chunk-permuted partial-sum row.
+// EC consecutive floats from / to column c0 (a multiple of EC) of a chunk-permuted row.
 template <int EC>
-__device__ __forceinline__ void ldv_part(const float* __restrict__ row, int c0, float (&v)[EC]) {
+__device__ __forceinline__ void ldv_p(const float* __restrict__ row, int c0, float (&v)[EC]) {
     if constexpr (EC % 4 == 0) {
 #pragma unroll
         for (int e = 0; e < EC; e += 4) {
@@ -755,8 +762,18 @@ __device__ __forceinline__ void ldv_part(const float* __restrict__ row, int c0, 
             v[e] = x.x; v[e + 1] = x.y; v[e + 2] = x.z; v[e + 3] = x.w;
         }
     } else {
-        const float2 x = *reinterpret_cast<const float2*>(row + 4 * pswz(c0 >> 2) + (c0 & 3));
+        const float2 x = *reinterpret_cast<const float2*>(row + pcol(c0));
         v[0] = x.x; v[1] = x.y;
+    }
+}
+template <int EC>
+__device__ __forceinline__ void stv_p(float* row, int c0, const float (&v)[EC]) {
+    if constexpr (EC % 4 == 0) {
+#pragma unroll
+        for (int e = 0; e < EC; e += 4)
+            *reinterpret_cast<float4*>(row + 4 * pswz((c0 + e) >> 2)) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+    } else {
+        *reinterpret_cast<float2*>(row + pcol(c0)) = make_float2(v[0], v[1]);
     }
 }
 
@@ -765,11 +782,11 @@ template <int K>
 __device__ __forceinline__ void gather(const float* __restrict__ part, int g, int c0, float (&o)[Sh<K>::EC]) {
     using S = Sh<K>;
     static_assert(S::EC % 4 == 0 || S::EC == 2, "gather: 2 or a multiple of 4 floats per thread");
-    ldv_part<S::EC>(part + g * S::Kh, c0, o);
+    ldv_p<S::EC>(part + g * S::Kh, c0, o);
 #pragma unroll
     for (int w = 1; w < kNW; ++w) {
         float v[S::EC];
-        ldv_part<S::EC>(part + (w * kG + g) * S::Kh, c0, v);
+        ldv_p<S::EC>(part + (w * kG + g) * S::Kh, c0, v);
 #pragma unroll
         for (int e = 0; e < S::EC; ++e) o[e] += v[e];
     }
@@ -811,16 +828,17 @@ using tc::st_async1;
 using tc::st_async2;
 using tc::st_async4;
 
-// N floats at element offset x of the peer's vector buffer (N a multiple of 2)
+// N floats at column c0 of the chunk-permuted row starting at element `row` of the peer's
+// vector buffer (N = 2 or a multiple of 4)
 template <int N>
-__device__ __forceinline__ void st_peer(const Xchg& xc, uint32_t base, int x, const float (&v)[N], uint32_t rbar) {
-    const uint32_t a = base + 4u * (uint32_t)x;
+__device__ __forceinline__ void st_peer(const Xchg& xc, uint32_t base, int row, int c0, const float (&v)[N], uint32_t rbar) {
+    const uint32_t a = base + 4u * (uint32_t)row;
     if constexpr (N % 4 == 0) {
 #pragma unroll
-        for (int e = 0; e < N; e += 4) st_async4(a + 4u * e, make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]), rbar);
+        for (int e = 0; e < N; e += 4)
+            st_async4(a + 16u * (uint32_t)pswz((c0 + e) >> 2), make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]), rbar);
     } else {
-#pragma unroll
-        for (int e = 0; e < N; e += 2) st_async2(a + 4u * e, make_float2(v[e], v[e + 1]), rbar);
+        st_async2(a + 4u * (uint32_t)pcol(c0), make_float2(v[0], v[1]), rbar);
     }
 }
 
@@ -867,16 +885,16 @@ __device__ __forceinline__ void fwd_epilogue(const Views& V, const Xchg& xc, int
                                              int ob, const float (&o)[Sh<K>::EC], float sc) {
     using S = Sh<K>;
     float b[S::EC], v[S::EC];
-    ldv<S::EC>(V.BTh + ob * S::Kh + c0, b);
+    ldv_p<S::EC>(V.BTh + ob * S::Kh, c0, b);
     float ps = 0.f;
 #pragma unroll
     for (int e = 0; e < S::EC; ++e) {
         v[e] = on ? o[e] * sc * b[e] : 0.f;
         ps += v[e];
     }
-    const int x = (nxt * kG + g) * K + r * S::Kh + c0;
-    stv<S::EC>(V.sX + x, v);
-    st_peer<S::EC>(xc, xc.sx_peer, x, v, (nxt ? xc.bar_peer1 : xc.bar_peer0));
+    const int row = (nxt * kG + g) * K;
+    stv_p<S::EC>(V.sX + row, r * S::Kh + c0, v);
+    st_peer<S::EC>(xc, xc.sx_peer, row, r * S::Kh + c0, v, (nxt ? xc.bar_peer1 : xc.bar_peer0));
     publish_sum(ps, V, xc, nxt, r, g);
 }
 
@@ -973,7 +991,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
             E += ex;
             if (due) {
                 float v[S::EC];
-                ldv<S::EC>(V.sX + (cur * kG + g) * K + r * S::Kh + c0, v);
+                ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
 #pragma unroll
                 for (int e = 0; e < S::EC; ++e) v[e] *= sc;
                 stv<S::EC>(p.cp + (base + cp_idx) * K + r * S::Kh + c0, v);
@@ -1035,7 +1053,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
             sv = *reinterpret_cast<const float4*>(p.cp + (gs.seq[gg] * p.Cmax + gs.t0[gg] / gs.C[gg]) * K + cc);
             if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + ((gstart + gg) * p.Cmax) * K + cc) = sv;
         }
-        *reinterpret_cast<float4*>(V.sX + gg * K + cc) = sv;
+        *reinterpret_cast<float4*>(V.sX + gg * K + pcol(cc)) = sv;
     }
     int ob_next = 0;
     if (tid < kG) {
@@ -1063,7 +1081,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
             if (tp < Lg) {
                 if (lead && r == 0) p.ebuf[rowb + tp] = ex;
                 float v[S::EC];
-                ldv<S::EC>(V.sX + (cur * kG + g) * K + r * S::Kh + c0, v);
+                ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
 #pragma unroll
                 for (int e = 0; e < S::EC; ++e) v[e] *= sc;
                 stv<S::EC>(p.P + (rowb + tp) * K + r * S::Kh + c0, v);
@@ -1172,16 +1190,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     auto write_v = [&](int tt, int s, bool active) {
         float v[S::EC], b[S::EC];
         if (active && s >= 0) {
-            ldv<S::EC>(V.BTh + s * S::Kh + c0, b);
+            ldv_p<S::EC>(V.BTh + s * S::Kh, c0, b);
 #pragma unroll
             for (int e = 0; e < S::EC; ++e) v[e] = b[e] * R[e];
         } else {
 #pragma unroll
             for (int e = 0; e < S::EC; ++e) v[e] = 0.f;
         }
-        const int x = ((tt & 1) * kG + g) * K + jc;
-        stv<S::EC>(V.sX + x, v);
-        st_peer<S::EC>(xc, xc.sx_peer, x, v, ((tt & 1) ? xc.bar_peer1 : xc.bar_peer0));
+        const int row = ((tt & 1) * kG + g) * K;
+        stv_p<S::EC>(V.sX + row, jc, v);
+        st_peer<S::EC>(xc, xc.sx_peer, row, jc, v, ((tt & 1) ? xc.bar_peer1 : xc.bar_peer0));
         if (active) {
 #pragma unroll
             for (int e = 0; e < S::EC; ++e) v[e] *= wg;
@@ -1196,17 +1214,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         const bool on = tt < Lg;
         // S_t of the thread's pairs, copied asynchronously into shared memory while the
         // contraction runs (keeps registers free)
-        float* st_mine = V.St + g * S::Kh + c0;
+        float* st_row = V.St + g * S::Kh;      // chunk-permuted like the vectors
         if (on) {
             const float* src = p.P + (rowb + tt) * K + jc;
 #pragma unroll
             for (int e = 0; e < S::EC; e += 2) {
                 if constexpr (S::EC % 4 == 0) {
                     if (e % 4 == 0)
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(st_mine + e)),
-                                     "l"(src + e) : "memory");
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                     ::"r"(tc::smem_u32(st_row + 4 * pswz((c0 + e) >> 2))), "l"(src + e) : "memory");
                 } else {
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(st_mine + e)),
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(st_row + pcol(c0 + e))),
                                  "l"(src + e) : "memory");
                 }
             }
@@ -1216,7 +1234,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         float St[S::EC];
-        if (on) ldv<S::EC>(st_mine, St);
+        if (on) ldv_p<S::EC>(st_row, c0, St);
         if (on) {
             float o[S::EC];
             gather<K>(V.part, g, c0, o);
