@@ -113,10 +113,12 @@ uint64_t accel_launch_count(void);
  *     d_flat[d_offsets[s] + k] = h_ptrs[s][k]                           (k < h_lengths[s])
  *  h_ptrs    host array of S element pointers; each points to device memory or to
  *            page-locked host memory mapped for the device (UVA); may be NULL where the
- *            length is 0.  The array is read before the call returns; the pieces it points
- *            to are read by the kernel in stream order (keep them until the stream has
- *            executed the call).
- *  h_lengths host array of S lengths >= 0.  Read before the call returns.
+ *            length is 0.
+ *  h_lengths host array of S lengths >= 0 (also read on the host, for checks).
+ *            Both tables are copied to the device in stream order: a page-locked table is
+ *            read when the stream reaches the copy, a pageable one before the call returns.
+ *            The tables and the pieces must stay unchanged until the stream has executed
+ *            the call.
  *  dtype     element type of every sequence (4- or 8-byte).
  *  d_flat    device output, sum(lengths) elements; d_offsets device output, S+1 int64.
  *  d_ws      scratch of accel_marshal_ragged_workspace_size(S) bytes (pointer + length
@@ -136,8 +138,8 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
  * d_group_offsets[0..G] (int64): group g's sequences are [d_group_offsets[g],
  * d_group_offsets[g+1]) of d_offsets.  A reduce of reduces is then two accel_segreduce calls
  * (inner segments by d_offsets, then the inner results by d_group_offsets).  Workspace:
- * accel_marshal_nested_workspace_size(S, G) bytes, 256-byte aligned.  Host tables are read
- * before return; asynchronous on `stream`.
+ * accel_marshal_nested_workspace_size(S, G) bytes, 256-byte aligned.  Host tables are copied
+ * in stream order as in accel_marshal_ragged; asynchronous on `stream`.
  */
 size_t accel_marshal_nested_workspace_size(int64_t S, int64_t G);
 accel_status accel_marshal_nested(const void* const* h_ptrs, const int64_t* h_lengths, int64_t S,
@@ -150,9 +152,9 @@ accel_status accel_marshal_nested(const void* const* h_ptrs, const int64_t* h_le
  * the host representation, Sec. 3.3): sequence s of the flat data (N elements of `dtype`,
  * device), elements [d_offsets[s], d_offsets[s+1]), is copied to h_dst_ptrs[s], a
  * caller-owned buffer with room for that many elements in device memory or in pinned host
- * memory (written by the kernel directly; one warp per sequence).  The pointer table is read
- * before return; the copies are asynchronous on `stream` (synchronize before reading host
- * buffers).  Workspace: accel_unmarshal_ragged_workspace_size(S) bytes, 256-byte aligned.
+ * memory (written by the kernel directly; one warp per sequence).  The pointer table is
+ * copied in stream order as in accel_marshal_ragged; the copies are asynchronous on
+ * `stream` (synchronize before reading host buffers).  Workspace: accel_unmarshal_ragged_workspace_size(S) bytes, 256-byte aligned.
  * Debug mode checks the offsets (monotone, offsets[S] == N).
  */
 size_t accel_unmarshal_ragged_workspace_size(int64_t S);

@@ -98,8 +98,13 @@ def accel_marshal_ragged_table(table: RaggedTable, device="cuda", out=None):
 
 def accel_marshal_ragged(seqs, dtype=torch.int32, device="cuda"):
     """Flatten a list of 1-D tensors (CUDA, or pinned CPU readable by the device) into
-    (flat data, int64 offsets) on ``device``."""
-    return accel_marshal_ragged_table(RaggedTable(seqs, dtype), device)
+    (flat data, int64 offsets) on ``device``.  Builds a temporary RaggedTable, so it waits for
+    the copy of its tables (keep a RaggedTable and call accel_marshal_ragged_table to stay
+    asynchronous)."""
+    table = RaggedTable(seqs, dtype)
+    out = accel_marshal_ragged_table(table, device)
+    torch.cuda.current_stream().synchronize()
+    return out
 
 
 def accel_marshal_nested(groups, dtype=torch.int32, device="cuda"):
@@ -118,6 +123,7 @@ def accel_marshal_nested(groups, dtype=torch.int32, device="cuda"):
         C.c_void_p(table.ptrs.data_ptr()), C.c_void_p(table.lengths.data_ptr()), table.S,
         C.c_void_p(sizes.data_ptr()), G, _dt(dtype), _ptr(flat), _ptr(offsets), _ptr(goffsets), _ptr(ws), ws.numel(),
         _stream()))
+    torch.cuda.current_stream().synchronize()        # the temporary pinned tables are read in stream order
     return flat, offsets, goffsets
 
 

@@ -12,9 +12,6 @@
 //                              written by the kernel directly).
 #include "common.cuh"
 
-#include <cstring>
-#include <vector>
-
 namespace accel {
 namespace marshal {
 
@@ -144,13 +141,10 @@ __global__ void __launch_bounds__(256) k_scatter(const T* __restrict__ flat, con
     }
 }
 
-// A host table into device memory, read before this returns: the bytes are first copied to
-// pageable memory, from which an asynchronous copy is staged by the driver before the call
-// returns (a copy straight from page-locked memory would read it later, in stream order).
+// A host table into device memory, in stream order: a page-locked table is read when the
+// stream reaches the copy (keep it until then), a pageable one is staged before this returns.
 static cudaError_t table_to_device(void* d_dst, const void* h_src, size_t bytes, cudaStream_t st) {
-    std::vector<unsigned char> tmp(bytes);
-    if (bytes) std::memcpy(tmp.data(), h_src, bytes);
-    return cudaMemcpyAsync(d_dst, tmp.data(), bytes, cudaMemcpyHostToDevice, st);
+    return cudaMemcpyAsync(d_dst, h_src, bytes, cudaMemcpyHostToDevice, st);
 }
 
 size_t ws_layout(int64_t S, size_t* ptr_off, size_t* len_off, size_t* bsum_off) {
