@@ -67,7 +67,9 @@ struct Prm {
     int32_t* ebuf;      // exponents e_t of the P rows [S][Cmax] (cluster path)
     float* gam;         // weighted posteriors gamma_t of the rows [S][Cmax][K] (cluster path)
     int32_t* osym;      // o_t of each row, -1 for none [S][Cmax] (cluster path)
-    int64_t ncl;        // cluster path: number of sequence groups (2 CTAs each)
+    int64_t ncl;        // cluster path: number of CTA pairs
+    const int64_t* plan;  // cluster path: per pair (start0, size0, start1, size1) of its sequence
+                          // groups (size1 = 0: one group), or null: group_range with ncl groups
 };
 
 __host__ __device__ __forceinline__ int seg_len(int64_t T) {
@@ -559,21 +561,115 @@ struct GS {
 // decreasing length) split into p.ncl contiguous groups of at most 16.  The critical path is
 // the group of the longest sequences, so when there is room the first groups take at most 8
 // (half the contraction work per step) and the rest share the remainder evenly.
-__device__ __forceinline__ void group_range(const Prm& p, int64_t cidx, int64_t& start, int& size) {
+__device__ __forceinline__ void group_range_n(int64_t S, int64_t ngroups, int64_t j, int64_t& start, int& size) {
     int64_t n8 = 0;                                    // leading groups of at most 8
-    if (p.S > 8 * p.ncl) {
-        n8 = (16 * p.ncl - p.S) / 8;
+    if (S > 8 * ngroups) {
+        n8 = (16 * ngroups - S) / 8;
         if (n8 < 0) n8 = 0;
     }
-    if (cidx < n8) {
-        start = 8 * cidx;
+    if (j < n8) {
+        start = 8 * j;
         size = 8;
         return;
     }
-    const int64_t rem = p.S - 8 * n8, m = p.ncl - n8, j = cidx - n8;
+    const int64_t rem = S - 8 * n8, m = ngroups - n8, jj = j - n8;
     const int64_t base = rem / m, extra = rem % m, firstbig = m - extra;
-    start = 8 * n8 + j * base + (j > firstbig ? j - firstbig : 0);
-    size = (int)(base + (j >= firstbig ? 1 : 0));
+    start = 8 * n8 + jj * base + (jj > firstbig ? jj - firstbig : 0);
+    size = (int)(base + (jj >= firstbig ? 1 : 0));
+}
+__device__ __forceinline__ void group_range(const Prm& p, int64_t cidx, int64_t& start, int& size) {
+    group_range_n(p.S, p.ncl, cidx, start, size);
+}
+
+// The sequence groups CTA pair cidx runs, one after the other (1 or 2).
+__device__ __forceinline__ int cluster_groups(const Prm& p, int64_t cidx) {
+    return (p.plan && p.plan[cidx * 4 + 3] > 0) ? 2 : 1;
+}
+__device__ __forceinline__ void cluster_group_range(const Prm& p, int64_t cidx, int gi, int64_t& start, int& size) {
+    if (p.plan) {
+        start = p.plan[cidx * 4 + 2 * gi];
+        size = (int)p.plan[cidx * 4 + 2 * gi + 1];
+    } else {
+        group_range(p, cidx, start, size);
+    }
+}
+
+// ---- group plan.  More groups than CTA pairs lets more of the longest sequences run in
+// groups of 8 (one contraction pass per step instead of two); the surplus groups, the
+// shortest, then share a pair with another group and run after it.  A step of a group of g
+// sequences costs about (0.92 + ceil(g / GP)) contraction passes (measured: a pass of 8
+// sequences ~2,840 cycles at K = 256, the rest of the step ~2,620), so a pair's time is the
+// sum over its groups of T_max(group) x that cost.  One thread per candidate group count
+// nv in [nv_lo, nv_hi] splits the sorted sequences with group_range_n, assigns the groups to
+// the ncl pairs longest-first to the least-loaded pair (at most two per pair), and the
+// candidate with the smallest maximum load writes the plan.
+constexpr int kPlanThreads = 128;
+constexpr int kPlanMaxGroups = 256;
+
+__device__ float plan_eval(const Prm& p, int64_t nv, int gp, int64_t* plan) {
+    float cost[kPlanMaxGroups];
+    int16_t ord[kPlanMaxGroups];
+    float load[kPlanMaxGroups / 2];
+    int8_t cnt[kPlanMaxGroups / 2];
+    for (int64_t j = 0; j < nv; ++j) {
+        int64_t st;
+        int sz;
+        group_range_n(p.S, nv, j, st, sz);
+        const int64_t sq = p.order[st];        // the longest of the group (sorted order)
+        const float T = (float)(p.off[sq + 1] - p.off[sq]);
+        cost[j] = T * (0.92f + (float)((sz + gp - 1) / gp));
+        int k = (int)j;                        // insertion by decreasing cost
+        while (k > 0 && cost[ord[k - 1]] < cost[j]) {
+            ord[k] = ord[k - 1];
+            --k;
+        }
+        ord[k] = (int16_t)j;
+    }
+    for (int64_t c = 0; c < p.ncl; ++c) {
+        load[c] = 0.f;
+        cnt[c] = 0;
+        if (plan) plan[c * 4 + 2] = plan[c * 4 + 3] = 0;
+    }
+    float worst = 0.f;
+    for (int64_t k = 0; k < nv; ++k) {
+        const int j = ord[k];
+        int best = -1;
+        for (int64_t c = 0; c < p.ncl; ++c)
+            if (cnt[c] < 2 && (best < 0 || load[c] < load[best])) best = (int)c;
+        if (best < 0) return INFINITY;
+        if (plan) {
+            int64_t st;
+            int sz;
+            group_range_n(p.S, nv, j, st, sz);
+            plan[best * 4 + 2 * cnt[best]] = st;
+            plan[best * 4 + 2 * cnt[best] + 1] = sz;
+        }
+        load[best] += cost[j];
+        ++cnt[best];
+        worst = fmaxf(worst, load[best]);
+    }
+    return worst;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int64_t nv_lo, int64_t nv_hi, int gp) {
+    __shared__ float s_v[kPlanThreads];
+    __shared__ int s_i[kPlanThreads];
+    const int t = threadIdx.x;
+    const int64_t nv = nv_lo + t;
+    s_v[t] = nv <= nv_hi ? plan_eval(p, nv, gp, nullptr) : INFINITY;
+    s_i[t] = t;
+    __syncthreads();
+    for (int d = kPlanThreads / 2; d > 0; d >>= 1) {
+        if (t < d) {
+            const float a = s_v[t], b = s_v[t + d];
+            if (b < a || (b == a && s_i[t + d] < s_i[t])) {
+                s_v[t] = b;
+                s_i[t] = s_i[t + d];
+            }
+        }
+        __syncthreads();
+    }
+    if (t == s_i[0]) plan_eval(p, nv, gp, plan);
 }
 
 __device__ void load_gs(const Prm& p, GS& gs, int64_t gstart, int gsize) {
@@ -931,9 +1027,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    int64_t gstart;
-    int gsize;
-    group_range(p, cidx, gstart, gsize);
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;    // one thread per sequence
     extern __shared__ __align__(16) char smem[];
@@ -944,76 +1037,84 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     MatRegs<K> m;
     m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
-    load_gs(p, gs, gstart, gsize);
-    __syncthreads();
-    int ob_next = 0;                      // thread g < 16: o_{t+1} for the next symbol write
-    if (tid < kG) {
-        const int64_t T = gs.T[tid], o0 = gs.o0[tid];
-        gs.sym[0][tid] = T > 0 ? p.obs[o0] : 0;
-        gs.sym[1][tid] = T > 1 ? p.obs[o0 + 1] : 0;
-        ob_next = T > 2 ? p.obs[o0 + 2] : 0;
-    }
-    int64_t Tmax = 0;
-#pragma unroll
-    for (int q = 0; q < kG; ++q) Tmax = gs.T[q] > Tmax ? gs.T[q] : Tmax;
-    const int64_t Tg = gs.T[g], base = gs.seq[g] * p.Cmax;
-    const int Cg = gs.C[g];
-    __syncthreads();
-    cl.sync();                            // both CTAs started: shared memory may be written remotely
-    {
-        // t = 0: alpha~_0 = pi o b(o_0)
-        float o[S::EC];
-        ldv<S::EC>(p.pi + r * S::Kh + c0, o);
-        fwd_epilogue<K>(V, xc, r, 0, g, c0, Tg > 0, gs.sym[0][g], o, 1.f);
-    }
-    xchg_finish(xc, 0, xchg_bytes<K>(true), p.status);
-    // the sequence's running exponent sum (used by the lead threads), steps to the next
-    // checkpoint and its index
-    int64_t E = 0;
-    int cp_left = 0, cp_idx = 0;
-    for (int64_t t = 1; t <= Tmax; ++t) {
-        const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
-        const int64_t tp = t - 1;
-        const float c = row_sum(V.red, cur, g);
-        int ex = 0;
-        frexpf(c, &ex);
-        const float sc = ldexpf(1.0f, -ex);
-        if (tp < Tg) {
-            const bool due = cp_left == 0;
-            if (lead && r == 0) {
-                if (due) p.cp_e[base + cp_idx] = ex;
-                if (tp == Tg - 1) {
-                    const int64_t sq = gs.seq[g];
-                    p.clast[sq] = c;
-                    if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E + log((double)c);
+    // the pair's sequence groups, one after the other
+    const int ngr = cluster_groups(p, cidx);
+    for (int gi = 0; gi < ngr; ++gi) {
+        int64_t gstart;
+        int gsize;
+        cluster_group_range(p, cidx, gi, gstart, gsize);
+        load_gs(p, gs, gstart, gsize);
+        __syncthreads();
+        int ob_next = 0;                      // thread g < 16: o_{t+1} for the next symbol write
+        if (tid < kG) {
+            const int64_t T = gs.T[tid], o0 = gs.o0[tid];
+            gs.sym[0][tid] = T > 0 ? p.obs[o0] : 0;
+            gs.sym[1][tid] = T > 1 ? p.obs[o0 + 1] : 0;
+            ob_next = T > 2 ? p.obs[o0 + 2] : 0;
+        }
+        int64_t Tmax = 0;
+    #pragma unroll
+        for (int q = 0; q < kG; ++q) Tmax = gs.T[q] > Tmax ? gs.T[q] : Tmax;
+        const int64_t Tg = gs.T[g], base = gs.seq[g] * p.Cmax;
+        const int Cg = gs.C[g];
+        __syncthreads();
+        cl.sync();                            // both CTAs started: shared memory may be written remotely
+        {
+            // t = 0: alpha~_0 = pi o b(o_0)
+            float o[S::EC];
+            ldv<S::EC>(p.pi + r * S::Kh + c0, o);
+            fwd_epilogue<K>(V, xc, r, 0, g, c0, Tg > 0, gs.sym[0][g], o, 1.f);
+        }
+        xchg_finish(xc, 0, xchg_bytes<K>(true), p.status);
+        // the sequence's running exponent sum (used by the lead threads), steps to the next
+        // checkpoint and its index
+        int64_t E = 0;
+        int cp_left = 0, cp_idx = 0;
+        for (int64_t t = 1; t <= Tmax; ++t) {
+            const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
+            const int64_t tp = t - 1;
+            const float c = row_sum(V.red, cur, g);
+            int ex = 0;
+            frexpf(c, &ex);
+            const float sc = ldexpf(1.0f, -ex);
+            if (tp < Tg) {
+                const bool due = cp_left == 0;
+                if (lead && r == 0) {
+                    if (due) p.cp_e[base + cp_idx] = ex;
+                    if (tp == Tg - 1) {
+                        const int64_t sq = gs.seq[g];
+                        p.clast[sq] = c;
+                        if (p.loglik) p.loglik[sq] = 0.6931471805599453 * (double)E + log((double)c);
+                    }
+                }
+                E += ex;
+                if (due) {
+                    float v[S::EC];
+                    ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
+    #pragma unroll
+                    for (int e = 0; e < S::EC; ++e) v[e] *= sc;
+                    stv<S::EC>(p.cp + (base + cp_idx) * K + r * S::Kh + c0, v);
+                    ++cp_idx;
+                    cp_left = Cg - 1;
+                } else {
+                    --cp_left;
                 }
             }
-            E += ex;
-            if (due) {
-                float v[S::EC];
-                ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
-#pragma unroll
-                for (int e = 0; e < S::EC; ++e) v[e] *= sc;
-                stv<S::EC>(p.cp + (base + cp_idx) * K + r * S::Kh + c0, v);
-                ++cp_idx;
-                cp_left = Cg - 1;
-            } else {
-                --cp_left;
+            if (t == Tmax) break;
+            contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
+            __syncthreads();
+            float o[S::EC];
+            gather<K>(V.part, g, c0, o);
+            fwd_epilogue<K>(V, xc, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
+            if (tid < kG) {
+                gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
+                ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
             }
+            xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
         }
-        if (t == Tmax) break;
-        contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
-        __syncthreads();
-        float o[S::EC];
-        gather<K>(V.part, g, c0, o);
-        fwd_epilogue<K>(V, xc, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
-        if (tid < kG) {
-            gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
-            ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
-        }
-        xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
+        cl.sync();
+        cl.sync();                        // the peer is done with this CTA's shared memory
     }
-    cl.sync();
 }
 
 // ---------------------------------------------------------------- recompute a segment
@@ -1026,9 +1127,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    int64_t gstart;
-    int gsize;
-    group_range(p, cidx, gstart, gsize);
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
@@ -1036,70 +1134,81 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     __shared__ __align__(8) uint64_t s_xbar[2];
     const Views V = make_views(smem, K, p.M, cl, peer);
     Xchg xc = make_xchg(V, s_xbar, peer);
-    load_gs(p, gs, gstart, gsize);
-    __syncthreads();
-    round_bounds_gs(gs, round);
-    __syncthreads();
-    int maxL = 0;
-#pragma unroll
-    for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
-    const int Lg = (int)gs.L[g];
-    const int64_t rowb = (gstart + g) * p.Cmax;
-    // row 0: the checkpoint itself, into the local vector buffer and the P row
-    for (int idx = tid; idx < kG * K / 4; idx += kT) {
-        const int gg = idx / (K / 4), cc = 4 * (idx - gg * (K / 4));
-        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gs.L[gg] > 0) {
-            sv = *reinterpret_cast<const float4*>(p.cp + (gs.seq[gg] * p.Cmax + gs.t0[gg] / gs.C[gg]) * K + cc);
-            if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + ((gstart + gg) * p.Cmax) * K + cc) = sv;
-        }
-        *reinterpret_cast<float4*>(V.sX + gg * K + pcol(cc)) = sv;
-    }
-    int ob_next = 0;
-    if (tid < kG) {
-        const int q = tid;
-        if (gs.L[q] > 0 && r == 0) p.ebuf[(gstart + q) * p.Cmax] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
-        const int64_t b0 = gs.o0[q] + gs.t0[q];
-        gs.sym[1][q] = gs.L[q] > 1 ? p.obs[b0 + 1] : 0;
-        ob_next = gs.L[q] > 2 ? p.obs[b0 + 2] : 0;
-    }
-    if (maxL <= 1) return;                // no remote access made; the peer returns here too
     MatRegs<K> m;
     m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
-    __syncthreads();
-    cl.sync();
-    for (int tt = 1; tt <= maxL; ++tt) {
-        const int cur = (tt - 1) & 1, nxt = tt & 1;
-        float sc = 1.f;
-        if (tt >= 2) {
-            const float c = row_sum(V.red, cur, g);
-            int ex = 0;
-            frexpf(c, &ex);
-            sc = ldexpf(1.0f, -ex);
-            const int tp = tt - 1;
-            if (tp < Lg) {
-                if (lead && r == 0) p.ebuf[rowb + tp] = ex;
-                float v[S::EC];
-                ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
-#pragma unroll
-                for (int e = 0; e < S::EC; ++e) v[e] *= sc;
-                stv<S::EC>(p.P + (rowb + tp) * K + r * S::Kh + c0, v);
-            }
-        }
-        if (tt == maxL) break;
-        contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
+    // the pair's sequence groups, one after the other
+    const int ngr = cluster_groups(p, cidx);
+    for (int gi = 0; gi < ngr; ++gi) {
+        int64_t gstart;
+        int gsize;
+        cluster_group_range(p, cidx, gi, gstart, gsize);
+        load_gs(p, gs, gstart, gsize);
         __syncthreads();
-        float o[S::EC];
-        gather<K>(V.part, g, c0, o);
-        fwd_epilogue<K>(V, xc, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
-        if (tid < kG) {
-            gs.sym[cur][tid] = ob_next;
-            ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
+        round_bounds_gs(gs, round);
+        __syncthreads();
+        int maxL = 0;
+    #pragma unroll
+        for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
+        const int Lg = (int)gs.L[g];
+        const int64_t rowb = (gstart + g) * p.Cmax;
+        // row 0: the checkpoint itself, into the local vector buffer and the P row
+        for (int idx = tid; idx < kG * K / 4; idx += kT) {
+            const int gg = idx / (K / 4), cc = 4 * (idx - gg * (K / 4));
+            float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gs.L[gg] > 0) {
+                sv = *reinterpret_cast<const float4*>(p.cp + (gs.seq[gg] * p.Cmax + gs.t0[gg] / gs.C[gg]) * K + cc);
+                if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + ((gstart + gg) * p.Cmax) * K + cc) = sv;
+            }
+            *reinterpret_cast<float4*>(V.sX + gg * K + pcol(cc)) = sv;
         }
-        xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
+        int ob_next = 0;
+        if (tid < kG) {
+            const int q = tid;
+            if (gs.L[q] > 0 && r == 0) p.ebuf[(gstart + q) * p.Cmax] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
+            const int64_t b0 = gs.o0[q] + gs.t0[q];
+            gs.sym[1][q] = gs.L[q] > 1 ? p.obs[b0 + 1] : 0;
+            ob_next = gs.L[q] > 2 ? p.obs[b0 + 2] : 0;
+        }
+        if (maxL <= 1) {                      // no remote access made; the peer skips it too
+            __syncthreads();                  // (gs is rewritten for the next group)
+            continue;
+        }
+        __syncthreads();
+        cl.sync();
+        for (int tt = 1; tt <= maxL; ++tt) {
+            const int cur = (tt - 1) & 1, nxt = tt & 1;
+            float sc = 1.f;
+            if (tt >= 2) {
+                const float c = row_sum(V.red, cur, g);
+                int ex = 0;
+                frexpf(c, &ex);
+                sc = ldexpf(1.0f, -ex);
+                const int tp = tt - 1;
+                if (tp < Lg) {
+                    if (lead && r == 0) p.ebuf[rowb + tp] = ex;
+                    float v[S::EC];
+                    ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
+    #pragma unroll
+                    for (int e = 0; e < S::EC; ++e) v[e] *= sc;
+                    stv<S::EC>(p.P + (rowb + tp) * K + r * S::Kh + c0, v);
+                }
+            }
+            if (tt == maxL) break;
+            contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
+            __syncthreads();
+            float o[S::EC];
+            gather<K>(V.part, g, c0, o);
+            fwd_epilogue<K>(V, xc, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
+            if (tid < kG) {
+                gs.sym[cur][tid] = ob_next;
+                ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
+            }
+            xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
+        }
+        cl.sync();
+        cl.sync();                        // the peer is done with this CTA's shared memory
     }
-    cl.sync();
 }
 
 // ---------------------------------------------------------------- backward over a segment
@@ -1116,9 +1225,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     const int64_t cidx = blockIdx.x >> 1;
-    int64_t gstart;
-    int gsize;
-    group_range(p, cidx, gstart, gsize);
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
     extern __shared__ __align__(16) char smem[];
@@ -1126,153 +1232,164 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     __shared__ __align__(8) uint64_t s_xbar[2];
     const Views V = make_views(smem, K, p.M, cl, peer);
     Xchg xc = make_xchg(V, s_xbar, peer);
-    load_gs(p, gs, gstart, gsize);
-    __syncthreads();
-    round_bounds_gs(gs, round);
-    __syncthreads();
-    int maxL = 0;
-#pragma unroll
-    for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
-    const int Lg = (int)gs.L[g];
-    const int64_t rowb = (gstart + g) * p.Cmax;
-    const int jc = r * S::Kh + c0;        // first state of the thread's epilogue block
-    if (tid < kG && gs.L[tid] > 0) atomicMax(&p.rows[round], (int32_t)((gstart + tid + 1) * p.Cmax));
-    // rows that must read as zero / carry no symbol: all rows of a sequence whose last
-    // segment was done in the previous round, rows past the segment of an active one
-    if (gs.seq[g] >= 0 && (gs.just_done[g] || Lg > 0)) {
-        float z[S::EC];
-#pragma unroll
-        for (int e = 0; e < S::EC; ++e) z[e] = 0.f;
-        for (int tt = Lg; tt < p.Cmax; ++tt) stv<S::EC>(p.Q + (rowb + tt) * K + jc, z);
-    }
-    if (r == 0 && tid < kG) {
-        const int q = tid;
-        const int64_t rb = (gstart + q) * p.Cmax;
-        const int64_t from = (gs.seq[q] >= 0 && (gs.just_done[q] || gs.L[q] > 0)) ? gs.L[q] : p.Cmax;
-        for (int64_t tt = from; tt < p.Cmax; ++tt) p.osym[rb + tt] = -1;
-    }
-    if (maxL == 0) return;                // no remote access made; the peer returns here too
-    auto sym_at = [&](int q, int tt) -> int {
-        const int64_t t = gs.t0[q] + tt;
-        return (tt <= gs.L[q] && t < gs.T[q] && gs.seq[q] >= 0) ? p.obs[gs.o0[q] + t] : -1;
-    };
-    auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(gstart + q) * p.Cmax + tt] : 0; };
-    int nsym = -1, ne = 0;                // thread q < 16: scalars of step tt-1, loaded one step ahead
-    if (tid < kG) {
-        const int q = tid;
-        gs.sym_end[q] = sym_at(q, maxL);
-        gs.sym[(maxL - 1) & 1][q] = sym_at(q, maxL - 1);
-        gs.eb[(maxL - 1) & 1][q] = e_at(q, maxL - 1);
-        if (maxL >= 2) {
-            nsym = sym_at(q, maxL - 2);
-            ne = e_at(q, maxL - 2);
-        }
-    }
     MatRegs<K> m;
     m.load(p.At, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
-    for (int idx = tid; idx < 2 * kG * K; idx += kT) V.sX[idx] = 0.f;
-    __syncthreads();
-    cl.sync();                            // both CTAs started and zeroed before any remote write
-    const float wg = gs.w[g];
-    const bool last_seg = gs.t0[g] + Lg == gs.T[g];
-    float R[S::EC];                       // R_{t+1} of the thread's (sequence, state) pairs
-    if (Lg > 0 && !last_seg) {
-        ldv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
-    } else {
-#pragma unroll
-        for (int e = 0; e < S::EC; ++e) R[e] = 0.f;
-    }
-    int prev_sym = gs.sym_end[g];
-    // v = b(s) o R for step tt into both CTAs, and the Q row of step tt
-    // (every thread sends its part each step -- zeros for a sequence not in step tt -- so the
-    // peer's expected byte count is constant; the Q row is written only for active steps)
-    auto write_v = [&](int tt, int s, bool active) {
-        float v[S::EC], b[S::EC];
-        if (active && s >= 0) {
-            ldv_p<S::EC>(V.BTh + s * S::Kh, c0, b);
-#pragma unroll
-            for (int e = 0; e < S::EC; ++e) v[e] = b[e] * R[e];
+    // the pair's sequence groups, one after the other
+    const int ngr = cluster_groups(p, cidx);
+    for (int gi = 0; gi < ngr; ++gi) {
+        int64_t gstart;
+        int gsize;
+        cluster_group_range(p, cidx, gi, gstart, gsize);
+        load_gs(p, gs, gstart, gsize);
+        __syncthreads();
+        round_bounds_gs(gs, round);
+        __syncthreads();
+        int maxL = 0;
+    #pragma unroll
+        for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
+        const int Lg = (int)gs.L[g];
+        const int64_t rowb = (gstart + g) * p.Cmax;
+        const int jc = r * S::Kh + c0;        // first state of the thread's epilogue block
+        if (tid < kG && gs.L[tid] > 0) atomicMax(&p.rows[round], (int32_t)((gstart + tid + 1) * p.Cmax));
+        // rows that must read as zero / carry no symbol: all rows of a sequence whose last
+        // segment was done in the previous round, rows past the segment of an active one
+        if (gs.seq[g] >= 0 && (gs.just_done[g] || Lg > 0)) {
+            float z[S::EC];
+    #pragma unroll
+            for (int e = 0; e < S::EC; ++e) z[e] = 0.f;
+            for (int tt = Lg; tt < p.Cmax; ++tt) stv<S::EC>(p.Q + (rowb + tt) * K + jc, z);
+        }
+        if (r == 0 && tid < kG) {
+            const int q = tid;
+            const int64_t rb = (gstart + q) * p.Cmax;
+            const int64_t from = (gs.seq[q] >= 0 && (gs.just_done[q] || gs.L[q] > 0)) ? gs.L[q] : p.Cmax;
+            for (int64_t tt = from; tt < p.Cmax; ++tt) p.osym[rb + tt] = -1;
+        }
+        if (maxL == 0) {                      // no remote access made; the peer skips it too
+            __syncthreads();                  // (gs is rewritten for the next group)
+            continue;
+        }
+        auto sym_at = [&](int q, int tt) -> int {
+            const int64_t t = gs.t0[q] + tt;
+            return (tt <= gs.L[q] && t < gs.T[q] && gs.seq[q] >= 0) ? p.obs[gs.o0[q] + t] : -1;
+        };
+        auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(gstart + q) * p.Cmax + tt] : 0; };
+        int nsym = -1, ne = 0;                // thread q < 16: scalars of step tt-1, loaded one step ahead
+        if (tid < kG) {
+            const int q = tid;
+            gs.sym_end[q] = sym_at(q, maxL);
+            gs.sym[(maxL - 1) & 1][q] = sym_at(q, maxL - 1);
+            gs.eb[(maxL - 1) & 1][q] = e_at(q, maxL - 1);
+            if (maxL >= 2) {
+                nsym = sym_at(q, maxL - 2);
+                ne = e_at(q, maxL - 2);
+            }
+        }
+        for (int idx = tid; idx < 2 * kG * K; idx += kT) V.sX[idx] = 0.f;
+        __syncthreads();
+        cl.sync();                            // both CTAs started and zeroed before any remote write
+        const float wg = gs.w[g];
+        const bool last_seg = gs.t0[g] + Lg == gs.T[g];
+        float R[S::EC];                       // R_{t+1} of the thread's (sequence, state) pairs
+        if (Lg > 0 && !last_seg) {
+            ldv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
         } else {
-#pragma unroll
-            for (int e = 0; e < S::EC; ++e) v[e] = 0.f;
+    #pragma unroll
+            for (int e = 0; e < S::EC; ++e) R[e] = 0.f;
         }
-        const int row = ((tt & 1) * kG + g) * K;
-        stv_p<S::EC>(V.sX + row, jc, v);
-        st_peer<S::EC>(xc, xc.sx_peer, row, jc, v, ((tt & 1) ? xc.bar_peer1 : xc.bar_peer0));
-        if (active) {
-#pragma unroll
-            for (int e = 0; e < S::EC; ++e) v[e] *= wg;
-            stv<S::EC>(p.Q + (rowb + tt) * K + jc, v);
-        }
-    };
-    write_v(maxL - 1, prev_sym, maxL - 1 < Lg);
-    xchg_finish(xc, (maxL - 1) & 1, xchg_bytes<K>(false), p.status);
-    for (int tt = maxL - 1; tt >= 0; --tt) {
-        const int buf = tt & 1;
-        const int sym = gs.sym[buf][g], e_t = gs.eb[buf][g];
-        const bool on = tt < Lg;
-        // S_t of the thread's pairs, copied asynchronously into shared memory while the
-        // contraction runs (keeps registers free)
-        float* st_row = V.St + g * S::Kh;      // chunk-permuted like the vectors
-        if (on) {
-            const float* src = p.P + (rowb + tt) * K + jc;
-#pragma unroll
-            for (int e = 0; e < S::EC; e += 2) {
-                if constexpr (S::EC % 4 == 0) {
-                    if (e % 4 == 0)
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                                     ::"r"(tc::smem_u32(st_row + 4 * pswz((c0 + e) >> 2))), "l"(src + e) : "memory");
-                } else {
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(st_row + pcol(c0 + e))),
-                                 "l"(src + e) : "memory");
+        int prev_sym = gs.sym_end[g];
+        // v = b(s) o R for step tt into both CTAs, and the Q row of step tt
+        // (every thread sends its part each step -- zeros for a sequence not in step tt -- so the
+        // peer's expected byte count is constant; the Q row is written only for active steps)
+        auto write_v = [&](int tt, int s, bool active) {
+            float v[S::EC], b[S::EC];
+            if (active && s >= 0) {
+                ldv_p<S::EC>(V.BTh + s * S::Kh, c0, b);
+    #pragma unroll
+                for (int e = 0; e < S::EC; ++e) v[e] = b[e] * R[e];
+            } else {
+    #pragma unroll
+                for (int e = 0; e < S::EC; ++e) v[e] = 0.f;
+            }
+            const int row = ((tt & 1) * kG + g) * K;
+            stv_p<S::EC>(V.sX + row, jc, v);
+            st_peer<S::EC>(xc, xc.sx_peer, row, jc, v, ((tt & 1) ? xc.bar_peer1 : xc.bar_peer0));
+            if (active) {
+    #pragma unroll
+                for (int e = 0; e < S::EC; ++e) v[e] *= wg;
+                stv<S::EC>(p.Q + (rowb + tt) * K + jc, v);
+            }
+        };
+        write_v(maxL - 1, prev_sym, maxL - 1 < Lg);
+        xchg_finish(xc, (maxL - 1) & 1, xchg_bytes<K>(false), p.status);
+        for (int tt = maxL - 1; tt >= 0; --tt) {
+            const int buf = tt & 1;
+            const int sym = gs.sym[buf][g], e_t = gs.eb[buf][g];
+            const bool on = tt < Lg;
+            // S_t of the thread's pairs, copied asynchronously into shared memory while the
+            // contraction runs (keeps registers free)
+            float* st_row = V.St + g * S::Kh;      // chunk-permuted like the vectors
+            if (on) {
+                const float* src = p.P + (rowb + tt) * K + jc;
+    #pragma unroll
+                for (int e = 0; e < S::EC; e += 2) {
+                    if constexpr (S::EC % 4 == 0) {
+                        if (e % 4 == 0)
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                         ::"r"(tc::smem_u32(st_row + 4 * pswz((c0 + e) >> 2))), "l"(src + e) : "memory");
+                    } else {
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(st_row + pcol(c0 + e))),
+                                     "l"(src + e) : "memory");
+                    }
                 }
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            contract<K>(m, V.sX + buf * kG * K, V.part, gsize);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            float St[S::EC];
+            if (on) ldv_p<S::EC>(st_row, c0, St);
+            if (on) {
+                float o[S::EC];
+                gather<K>(V.part, g, c0, o);
+                const bool trans = prev_sym >= 0;
+                const float down = ldexpf(1.0f, -e_t);
+                const float up = wg * ldexpf(1.0f, e_t);
+                const float cinv = trans ? 0.f : 1.0f / p.clast[gs.seq[g]];
+                float gm[S::EC];
+    #pragma unroll
+                for (int e = 0; e < S::EC; ++e) {
+                    R[e] = trans ? o[e] * down : cinv;
+                    gm[e] = up * St[e] * R[e];
+                }
+                stv<S::EC>(p.gam + (rowb + tt) * K + jc, gm);
+                if (lead && r == 0) p.osym[rowb + tt] = sym;
+            }
+            if (tt > 0) write_v(tt - 1, sym, tt - 1 < Lg);
+            prev_sym = sym;
+            if (tid < kG && tt > 0) {
+                gs.sym[(tt - 1) & 1][tid] = nsym;
+                gs.eb[(tt - 1) & 1][tid] = ne;
+                if (tt >= 2) {
+                    nsym = sym_at(tid, tt - 2);
+                    ne = e_at(tid, tt - 2);
+                }
+            }
+            if (tt > 0) xchg_finish(xc, (tt - 1) & 1, xchg_bytes<K>(false), p.status);
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        contract<K>(m, V.sX + buf * kG * K, V.part, gsize);
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (Lg > 0) stv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
+        // gamma_0 of the sequences that started in this round, summed in a fixed order by one
+        // thread per state (the gam rows written above are visible after the barrier)
         __syncthreads();
-        float St[S::EC];
-        if (on) ldv_p<S::EC>(st_row, c0, St);
-        if (on) {
-            float o[S::EC];
-            gather<K>(V.part, g, c0, o);
-            const bool trans = prev_sym >= 0;
-            const float down = ldexpf(1.0f, -e_t);
-            const float up = wg * ldexpf(1.0f, e_t);
-            const float cinv = trans ? 0.f : 1.0f / p.clast[gs.seq[g]];
-            float gm[S::EC];
-#pragma unroll
-            for (int e = 0; e < S::EC; ++e) {
-                R[e] = trans ? o[e] * down : cinv;
-                gm[e] = up * St[e] * R[e];
-            }
-            stv<S::EC>(p.gam + (rowb + tt) * K + jc, gm);
-            if (lead && r == 0) p.osym[rowb + tt] = sym;
+        for (int cc = tid; cc < S::Kh; cc += kT) {
+            const int j = r * S::Kh + cc;
+            float s = 0.f;
+            for (int q = 0; q < kG; ++q)
+                if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[((gstart + q) * p.Cmax) * K + j];
+            p.pig[cidx * K + j] += s;
         }
-        if (tt > 0) write_v(tt - 1, sym, tt - 1 < Lg);
-        prev_sym = sym;
-        if (tid < kG && tt > 0) {
-            gs.sym[(tt - 1) & 1][tid] = nsym;
-            gs.eb[(tt - 1) & 1][tid] = ne;
-            if (tt >= 2) {
-                nsym = sym_at(tid, tt - 2);
-                ne = e_at(tid, tt - 2);
-            }
-        }
-        if (tt > 0) xchg_finish(xc, (tt - 1) & 1, xchg_bytes<K>(false), p.status);
-    }
-    if (Lg > 0) stv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
-    // gamma_0 of the sequences that started in this round, summed in a fixed order by one
-    // thread per state (the gam rows written above are visible after the barrier)
-    __syncthreads();
-    for (int cc = tid; cc < S::Kh; cc += kT) {
-        const int j = r * S::Kh + cc;
-        float s = 0.f;
-        for (int q = 0; q < kG; ++q)
-            if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[((gstart + q) * p.Cmax) * K + j];
-        p.pig[cidx * K + j] += s;
+        cl.sync();                        // the peer is done with this CTA's shared memory
     }
 }
 
@@ -1293,7 +1410,7 @@ inline Kernels kernels_for(int K) {
 }  // namespace clu
 
 struct Layout {
-    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, order, total;
+    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, plan, order, total;
     int Cmax;
     int64_t ngroups;
     int64_t npig;       // rows of pig: one per group of either path (clusters: up to S)
@@ -1326,6 +1443,7 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.gam = take((size_t)S * L.Cmax * K * 4);
     L.osym = take((size_t)S * L.Cmax * 4);
     L.cntp = take((size_t)(ns_max > kCntSplit ? ns_max : kCntSplit) * K * M * 4);
+    L.plan = take((size_t)(adj::clu::kPlanMaxGroups / 2) * 4 * 8);     // group plan of the CTA pairs
     L.order = o;
     L.total = o + order_ws_bytes(S);
     return L;
@@ -1391,6 +1509,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     p.gam = (float*)(ws + L.gam);
     p.osym = (int32_t*)(ws + L.osym);
     p.ncl = 0;
+    p.plan = nullptr;
     float* cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
     p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = d_weights;
@@ -1429,7 +1548,20 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             // groups: at most 16 sequences each, and at least one pair of CTAs per two SMs
             const int64_t ncl_min = (S + adj::clu::kG - 1) / adj::clu::kG;
             const int64_t ncl_sm = S < (int64_t)(num_sms() / 2) ? S : (int64_t)(num_sms() / 2);
-            p.ncl = ncl_min > ncl_sm ? ncl_min : ncl_sm;
+            if (ncl_min <= 2 * ncl_sm && 2 * ncl_sm <= adj::clu::kPlanMaxGroups) {
+                // one pair per two SMs, each running one or two groups (planned on the device
+                // from the sorted lengths)
+                p.ncl = ncl_sm;
+                const int64_t nv_lo = ncl_min > ncl_sm ? ncl_min : ncl_sm;
+                int64_t nv_hi = 2 * ncl_sm < S ? 2 * ncl_sm : S;
+                if (nv_hi > nv_lo + adj::clu::kPlanThreads - 1) nv_hi = nv_lo + adj::clu::kPlanThreads - 1;
+                int64_t* plan = (int64_t*)(ws + L.plan);
+                adj::clu::k_plan<<<1, adj::clu::kPlanThreads, 0, st>>>(p, plan, nv_lo, nv_hi, K == 256 ? 8 : 16);
+                ++nlaunch;
+                p.plan = plan;
+            } else {
+                p.ncl = ncl_min > ncl_sm ? ncl_min : ncl_sm;
+            }
             const unsigned grid = (unsigned)(2 * p.ncl);
             const adj::clu::Kernels kc = adj::clu::kernels_for(K);
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
