@@ -600,63 +600,43 @@ __device__ __forceinline__ void cluster_group_range(const Prm& p, int64_t cidx, 
 // sequences costs about (0.92 + ceil(g / GP)) contraction passes (measured: a pass of 8
 // sequences ~2,840 cycles at K = 256, the rest of the step ~2,620), so a pair's time is the
 // sum over its groups of T_max(group) x that cost.  One thread per candidate group count
-// nv in [nv_lo, nv_hi] splits the sorted sequences with group_range_n, assigns the groups to
-// the ncl pairs longest-first to the least-loaded pair (at most two per pair), and the
-// candidate with the smallest maximum load writes the plan.
+// nv in [nv_lo, nv_hi] splits the sorted sequences with group_range_n; the first ncl groups
+// (the longest) take one pair each and surplus group ncl + k joins pair ncl - 1 - k (the
+// least loaded first); the candidate with the smallest maximum load writes the plan.
 constexpr int kPlanThreads = 128;
 constexpr int kPlanMaxGroups = 256;
+constexpr int kPlanMaxSeq = 16 * kPlanMaxGroups;
 
-__device__ float plan_eval(const Prm& p, int64_t nv, int gp, int64_t* plan) {
-    float cost[kPlanMaxGroups];
-    int16_t ord[kPlanMaxGroups];
-    float load[kPlanMaxGroups / 2];
-    int8_t cnt[kPlanMaxGroups / 2];
-    for (int64_t j = 0; j < nv; ++j) {
-        int64_t st;
-        int sz;
-        group_range_n(p.S, nv, j, st, sz);
-        const int64_t sq = p.order[st];        // the longest of the group (sorted order)
-        const float T = (float)(p.off[sq + 1] - p.off[sq]);
-        cost[j] = T * (0.92f + (float)((sz + gp - 1) / gp));
-        int k = (int)j;                        // insertion by decreasing cost
-        while (k > 0 && cost[ord[k - 1]] < cost[j]) {
-            ord[k] = ord[k - 1];
-            --k;
-        }
-        ord[k] = (int16_t)j;
-    }
-    for (int64_t c = 0; c < p.ncl; ++c) {
-        load[c] = 0.f;
-        cnt[c] = 0;
-        if (plan) plan[c * 4 + 2] = plan[c * 4 + 3] = 0;
-    }
-    float worst = 0.f;
-    for (int64_t k = 0; k < nv; ++k) {
-        const int j = ord[k];
-        int best = -1;
-        for (int64_t c = 0; c < p.ncl; ++c)
-            if (cnt[c] < 2 && (best < 0 || load[c] < load[best])) best = (int)c;
-        if (best < 0) return INFINITY;
-        if (plan) {
-            int64_t st;
-            int sz;
-            group_range_n(p.S, nv, j, st, sz);
-            plan[best * 4 + 2 * cnt[best]] = st;
-            plan[best * 4 + 2 * cnt[best] + 1] = sz;
-        }
-        load[best] += cost[j];
-        ++cnt[best];
-        worst = fmaxf(worst, load[best]);
-    }
-    return worst;
+__device__ __forceinline__ float plan_cost(const int* sT, int64_t S, int64_t nv, int64_t j, int gp) {
+    int64_t st;
+    int sz;
+    group_range_n(S, nv, j, st, sz);
+    return (float)sT[st] * (0.92f + (float)((sz + gp - 1) / gp));   // sT[st]: the group's longest
 }
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int64_t nv_lo, int64_t nv_hi, int gp) {
+    __shared__ int sT[kPlanMaxSeq];                 // lengths in sorted order
     __shared__ float s_v[kPlanThreads];
     __shared__ int s_i[kPlanThreads];
     const int t = threadIdx.x;
-    const int64_t nv = nv_lo + t;
-    s_v[t] = nv <= nv_hi ? plan_eval(p, nv, gp, nullptr) : INFINITY;
+    for (int64_t q = t; q < p.S; q += kPlanThreads) {
+        const int64_t sq = p.order[q];
+        sT[q] = (int)(p.off[sq + 1] - p.off[sq]);
+    }
+    __syncthreads();
+    const int64_t nv = nv_lo + t, ncl = p.ncl;
+    float worst = INFINITY;
+    if (nv <= nv_hi) {
+        const int64_t extra = nv - ncl;             // 0 <= extra <= ncl
+        worst = 0.f;
+        for (int64_t c = 0; c < ncl; ++c) {
+            float l = plan_cost(sT, p.S, nv, c, gp);
+            const int64_t k = ncl - 1 - c;          // surplus group ncl + k joins pair c
+            if (k < extra) l += plan_cost(sT, p.S, nv, ncl + k, gp);
+            worst = fmaxf(worst, l);
+        }
+    }
+    s_v[t] = worst;
     s_i[t] = t;
     __syncthreads();
     for (int d = kPlanThreads / 2; d > 0; d >>= 1) {
@@ -669,7 +649,23 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int
         }
         __syncthreads();
     }
-    if (t == s_i[0]) plan_eval(p, nv, gp, plan);
+    const int64_t best = nv_lo + s_i[0];
+    const int64_t extra = best - ncl;
+    for (int64_t c = t; c < ncl; c += kPlanThreads) {
+        int64_t st;
+        int sz;
+        group_range_n(p.S, best, c, st, sz);
+        plan[c * 4] = st;
+        plan[c * 4 + 1] = sz;
+        plan[c * 4 + 2] = 0;
+        plan[c * 4 + 3] = 0;
+        const int64_t k = ncl - 1 - c;
+        if (k < extra) {
+            group_range_n(p.S, best, ncl + k, st, sz);
+            plan[c * 4 + 2] = st;
+            plan[c * 4 + 3] = sz;
+        }
+    }
 }
 
 __device__ void load_gs(const Prm& p, GS& gs, int64_t gstart, int gsize) {
@@ -1548,7 +1544,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
             // groups: at most 16 sequences each, and at least one pair of CTAs per two SMs
             const int64_t ncl_min = (S + adj::clu::kG - 1) / adj::clu::kG;
             const int64_t ncl_sm = S < (int64_t)(num_sms() / 2) ? S : (int64_t)(num_sms() / 2);
-            if (ncl_min <= 2 * ncl_sm && 2 * ncl_sm <= adj::clu::kPlanMaxGroups) {
+            if (ncl_min <= 2 * ncl_sm && 2 * ncl_sm <= adj::clu::kPlanMaxGroups && S <= adj::clu::kPlanMaxSeq) {
                 // one pair per two SMs, each running one or two groups (planned on the device
                 // from the sorted lengths)
                 p.ncl = ncl_sm;
