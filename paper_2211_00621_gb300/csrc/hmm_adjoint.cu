@@ -24,8 +24,11 @@
 // Q = w_s b(o_{t+1}) o R_{t+1}, and a split-K GEMM accumulates U += P^T Q, so that
 // xi = A o U at the end.  Storage is O(S sqrt(T_max) K) instead of O(sum_s T_s K).
 //
-// All kernels are FP32 SIMT; the groups of 8 sequences per CTA are taken in order of
-// decreasing length.  Every accumulation has a fixed order, so results are deterministic.
+// The recurrences are FP32 SIMT: for K in {64, 128, 256} on CTA pairs (thread-block clusters)
+// that split the states, each pair running one or two groups of up to 16 length-sorted
+// sequences as planned by k_plan; otherwise one CTA per 8 sequences.  The count
+// contractions of each backward round run on the tensor cores (k_xi_tc.cu).  Every
+// accumulation has a fixed order, so results are deterministic.
 #include "hmm_internal.cuh"
 #include "simt_stream.cuh"
 
@@ -557,10 +560,11 @@ struct GS {
     int sym_end[kG];     // backward: symbol after the segment, -1 if none
 };
 
-// Sorted positions [start, start + size) of group cidx: the S sequences (in order of
-// decreasing length) split into p.ncl contiguous groups of at most 16.  The critical path is
-// the group of the longest sequences, so when there is room the first groups take at most 8
-// (half the contraction work per step) and the rest share the remainder evenly.
+// Sorted positions [start, start + size) of group j when the S sequences (in order of
+// decreasing length) are split into `ngroups` contiguous groups of at most 16 (ngroups >=
+// S / 16).  The longest sequences set the critical path, so when there is room the first
+// groups take 8 (half the contraction work per step) and the rest share the remainder
+// evenly.  Without a plan, CTA pair cidx runs group cidx of p.ncl.
 __device__ __forceinline__ void group_range_n(int64_t S, int64_t ngroups, int64_t j, int64_t& start, int& size) {
     int64_t n8 = 0;                                    // leading groups of at most 8
     if (S > 8 * ngroups) {
