@@ -28,7 +28,10 @@
  *    Workflow" and Appendix B "Dynamic Assumptions"): arguments are validated on the host
  *    and on the device (offsets monotone and in range, symbols < M, rank <= 3, lengths),
  *    the stream is synchronized after the call and device-side errors are returned as
- *    status codes.  With debug mode off ("accelerate mode") only O(1) host checks run.
+ *    status codes.  With debug mode off ("accelerate mode") only O(1) host checks run, and
+ *    errors that only the device can see (a bounded wait that gave up, a sequence longer
+ *    than the max_T a call was sized for) are recorded in a device status word: the
+ *    caller's, registered with accel_set_device_status, and read with accel_sync_status.
  *  - Integers are 64-bit wherever the paper's compiler would use its single int type
  *    (Sec. 5: the compiler always uses 64-bit integers): offsets, sizes, integer results of
  *    maps and reductions computed from int32 data.
@@ -104,6 +107,57 @@ int32_t accel_get_debug(void);
 /* Number of CUDA kernels this library has launched in the process so far (diagnostic;
  * used to count the launches inside a timed region). */
 uint64_t accel_launch_count(void);
+
+/*
+ * accel_alu_rate -- measure one arithmetic rate of the running device at its current clocks
+ * (a measurement utility with no counterpart in the paper: the denominators of the ALU
+ * rooflines reported beside the kernels).  One warm-up launch, then one timed launch
+ * (CUDA events) of 4 CTAs x 512 threads per SM, each thread running 8 independent chains of
+ * 8 x iters dependent operations:
+ *   ACCEL_PROBE_FFMA   FP32 fused multiply-add (counted as 2 flop)
+ *   ACCEL_PROBE_FFMA2  packed FP32 FMA on float pairs (4 flop)
+ *   ACCEL_PROBE_RSQRT  FP32 reciprocal square root (1 op, the special-function unit)
+ *   ACCEL_PROBE_DFMA   FP64 fused multiply-add (2 flop)
+ * *h_rate receives operations per second.  d_scratch: device float32 scratch of 2048 x SM
+ * count elements (written).  Synchronizes `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+#define ACCEL_PROBE_FFMA  0
+#define ACCEL_PROBE_FFMA2 1
+#define ACCEL_PROBE_RSQRT 2
+#define ACCEL_PROBE_DFMA  3
+accel_status accel_alu_rate(int32_t kind, int64_t iters, float* d_scratch, double* h_rate, void* stream);
+
+/*
+ * Device-side status in accelerate mode (the asynchronous counterpart of the paper's
+ * debug-mode runtime checks, Sec. 3.2 and Appendix B "Dynamic Assumptions").
+ *
+ * accel_set_device_status -- register d_status (a caller-owned device int32, set to
+ *   ACCEL_OK = 0 by the caller) for the calls made afterwards on the calling thread; NULL
+ *   unregisters.  Every call that can detect an error on the device (hmm_forward,
+ *   hmm_adjoint; their bounded waits and the adjoint's max_T check) then records it there:
+ *   the FIRST error stays (compare-and-swap from ACCEL_OK), later calls do not clear it.
+ *   Without a registered word each call keeps its status in its own workspace, where only
+ *   debug mode reads it.  Kernels captured into a CUDA graph keep the word they were
+ *   captured with.
+ * accel_sync_status -- synchronize `stream`, return the word's value as the status of this
+ *   call (with a message in accel_last_error()), and set it back to ACCEL_OK when `clear`
+ *   is non-zero.  The word holds the errors of every call issued before this one on
+ *   `stream` (and of calls on other streams that have completed).
+ */
+accel_status accel_set_device_status(int32_t* d_status);
+accel_status accel_sync_status(int32_t* d_status, int32_t clear, void* stream);
+
+/*
+ * accel_set_watchdog_ns -- failure detection for the persistent single-CTA BF16 forward
+ * (hmm_forward, ACCEL_HMM_BF16_SCALED, in the tuned configurations that run one CTA per
+ * tile): a launch that has run longer than budget_ns stops at its next step boundary, after
+ * the step's tensor-core work has completed, and reports ACCEL_ERR_TIMEOUT in its device
+ * status word; its log-likelihoods are then incomplete.  0 (the default) means no limit.
+ * Process-wide; read by each launch when it is issued (a captured graph keeps the value
+ * it was captured with).  The cluster-pair configurations keep only their bounded waits.
+ */
+void accel_set_watchdog_ns(uint64_t budget_ns);
+uint64_t accel_get_watchdog_ns(void);
 
 /* =========================================================== marshaling (Sec. 3.3) */
 /*
@@ -235,8 +289,11 @@ accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, in
  *  clearing between calls.  Calls that overlap on the GPU (other streams, or other host
  *  threads without ordering) race on the array: order them.
  *  Set-up: the first call on a device looks up the array's device address with that device
- *  current and caches it; make that first call before any stream capture begins.
- *  The call itself allocates nothing and frees nothing.
+ *  current and caches it; make that first call before any stream capture begins.  Resetting
+ *  the device (cudaDeviceReset) after that first call is not supported: the cached address
+ *  would belong to the destroyed context.
+ *  The call itself allocates nothing and frees nothing.  Errors are those of accel_segreduce
+ *  (messages name this entry point) and UNSUPPORTED for N beyond the limit.
  */
 accel_status accel_segreduce_noalloc(int32_t op, int32_t fused_map, int32_t in_dtype, int32_t out_dtype,
                                      const void* d_data, int64_t N, const int64_t* d_offsets, int64_t S,
@@ -305,7 +362,10 @@ accel_status hmm_forward(const accel_hmm_model* m, int32_t precision, const int3
  * recomputation of alpha from its checkpoint and the backward (beta) recursion.
  *  d_weights  device float64 [S] or NULL (all ones).
  *  d_loglik   device float64 [S] or NULL: the forward's logL_s.
- *  max_T      the largest sequence length (sizes the checkpoint storage).
+ *  max_T      the largest sequence length (sizes the checkpoint storage; hmm_max_length
+ *             computes it on the device).  A sequence longer than the checkpoints allow is
+ *             skipped and reported as ACCEL_ERR_SHAPE: returned by the call in debug mode,
+ *             else recorded in the device status word (accel_set_device_status).
  *  Outputs are overwritten (not accumulated); d_grad_log_pi may be NULL.
  */
 size_t hmm_adjoint_workspace_size(const accel_hmm_model* m, int64_t S, int64_t total_T, int64_t max_T);
@@ -313,6 +373,14 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
                          int64_t S, int64_t total_T, int64_t max_T, const double* d_weights,
                          double* d_loglik, float* d_grad_log_A, float* d_grad_log_B,
                          float* d_grad_log_pi, void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * hmm_max_length -- *d_max_T = max_s (d_offsets[s+1] - d_offsets[s]) (device int64, caller
+ * owned; 0 when S = 0): the max_T that hmm_adjoint and hmm_forward_long are sized with,
+ * computed on the device (one CTA, asynchronous on `stream`) for callers that do not track
+ * their sequences' lengths on the host.  Errors: INVALID_ARG.
+ */
+accel_status hmm_max_length(const int64_t* d_offsets, int64_t S, int64_t* d_max_T, void* stream);
 
 /*
  * hmm_forward_long -- the same per-sequence log-likelihoods as hmm_forward, computed

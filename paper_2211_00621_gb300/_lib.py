@@ -22,6 +22,7 @@ RED_ADD, RED_MUL, RED_MIN, RED_MAX = range(4)
 LOOP_AXPY, LOOP_SCALE = range(2)
 PAIR_GRAVITY_SOFTENED = 0
 HMM_FP32_LOG, HMM_BF16_SCALED = 0, 1
+PROBE_FFMA, PROBE_FFMA2, PROBE_RSQRT, PROBE_DFMA = range(4)
 MAX_RANK = 3
 
 
@@ -50,6 +51,12 @@ SIGNATURES = {
     "accel_set_debug": (None, [i32]),
     "accel_get_debug": (i32, []),
     "accel_launch_count": (C.c_uint64, []),
+    "accel_set_device_status": (i32, [vp]),
+    "accel_sync_status": (i32, [vp, i32, vp]),
+    "accel_set_watchdog_ns": (None, [C.c_uint64]),
+    "accel_get_watchdog_ns": (C.c_uint64, []),
+    "hmm_max_length": (i32, [vp, i64, vp, vp]),
+    "accel_alu_rate": (i32, [i32, i64, vp, vp, vp]),
     "accel_marshal_ragged_workspace_size": (sz, [i64]),
     "accel_marshal_ragged": (i32, [vp, vp, i64, i32, vp, vp, vp, sz, vp]),
     "accel_marshal_nested_workspace_size": (sz, [i64, i64]),

@@ -55,6 +55,50 @@ def version() -> str:
     return L.load().accel_version().decode()
 
 
+# ------------------------------------------------------- device status (accelerate mode)
+def set_device_status(word: torch.Tensor | None):
+    """Register a device int32 tensor (one element, zero) as the status word of the calls made
+    afterwards on this thread (None unregisters): device-side errors of those calls (a bounded
+    wait that gave up, a sequence longer than max_T) are recorded there, the first one kept."""
+    if word is not None:
+        _need_cuda(word)
+        if word.dtype != torch.int32 or word.numel() < 1:
+            raise TypeError("the status word is a CUDA int32 tensor")
+    L.check("accel_set_device_status", L.load().accel_set_device_status(_ptr(word)))
+
+
+def sync_status(word: torch.Tensor, clear: bool = True):
+    """Synchronize the current stream and raise AccelError if the status word records a
+    device-side error (clearing it first when `clear`)."""
+    _need_cuda(word)
+    L.check("accel_sync_status", L.load().accel_sync_status(_ptr(word), 1 if clear else 0, _stream()))
+
+
+def set_watchdog_ns(budget_ns: int):
+    """Run-time budget of a persistent single-CTA BF16 forward launch (0 = no limit)."""
+    L.load().accel_set_watchdog_ns(int(budget_ns))
+
+
+def alu_rate(kind: int, iters: int = 4096, device="cuda") -> float:
+    """Measured arithmetic rate of the device (operations per second) for one of
+    PROBE_FFMA / PROBE_FFMA2 (FP32 flop), PROBE_RSQRT (MUFU ops), PROBE_DFMA (FP64 flop)."""
+    lib = L.load()
+    n = 2048 * torch.cuda.get_device_properties(device).multi_processor_count
+    scratch = torch.empty(n, dtype=torch.float32, device=device)
+    rate = C.c_double(0.0)
+    L.check("accel_alu_rate", lib.accel_alu_rate(int(kind), int(iters), _ptr(scratch), C.byref(rate), _stream()))
+    return rate.value
+
+
+def hmm_max_length(offsets: torch.Tensor) -> torch.Tensor:
+    """The largest sequence length, max_s offsets[s+1] - offsets[s], as a device int64 [1]
+    (computed by the library, asynchronously)."""
+    _need_cuda(offsets)
+    out = torch.empty(1, dtype=torch.int64, device=offsets.device)
+    L.check("hmm_max_length", L.load().hmm_max_length(_ptr(offsets), offsets.numel() - 1, _ptr(out), _stream()))
+    return out
+
+
 # ------------------------------------------------------------------------ marshaling
 class RaggedTable:
     """Host-side description of a list of sequences: pinned tables of element pointers and
@@ -272,7 +316,7 @@ def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | N
     S = offsets.numel() - 1
     K, M = m.K, m.M
     if max_T is None:
-        max_T = int((offsets[1:] - offsets[:-1]).max().item()) if S else 0
+        max_T = int(hmm_max_length(offsets).item()) if S else 0
     gA = torch.empty(K, K, dtype=torch.float32, device=obs.device)
     gB = torch.empty(K, M, dtype=torch.float32, device=obs.device)
     gpi = torch.empty(K, dtype=torch.float32, device=obs.device)
@@ -312,7 +356,7 @@ def hmm_forward_long(log_A, log_B, log_pi, obs, offsets, max_T: int | None = Non
     m = _model(log_A, log_B, log_pi)
     S = offsets.numel() - 1
     if max_T is None:
-        max_T = int((offsets[1:] - offsets[:-1]).max().item()) if S else 0
+        max_T = int(hmm_max_length(offsets).item()) if S else 0
     need = lib.hmm_forward_long_workspace_size(C.byref(m), S, obs.numel(), max_T)
     if ws is None or ws.numel() < need:
         ws = _ws(need, obs.device)
@@ -401,23 +445,28 @@ class Graph:
 
 
 class HMMLogLik(torch.autograd.Function):
-    """logL[S] = HMMLogLik.apply(log_A, log_B, log_pi, obs, offsets, precision).
+    """logL[S] = HMMLogLik.apply(log_A, log_B, log_pi, obs, offsets, precision, max_T=None).
 
     Backward calls hmm_adjoint with the incoming gradient as per-sequence weights (the
     gradient of sum_s w_s logL_s is linear in w), giving d/d log_A, d/d log_B, d/d log_pi.
     """
 
     @staticmethod
-    def forward(ctx, log_A, log_B, log_pi, obs, offsets, precision=L.HMM_FP32_LOG):
-        ctx.save_for_backward(log_A, log_B, log_pi, obs, offsets)
+    def forward(ctx, log_A, log_B, log_pi, obs, offsets, precision=L.HMM_FP32_LOG, max_T=None):
+        # max_T sizes the adjoint's checkpoints: the caller's value, else the library's device
+        # reduction over the offsets, launched here and read only in backward
+        ctx.max_T = max_T
+        d_max = hmm_max_length(offsets) if max_T is None and offsets.numel() > 1 else None
+        ctx.save_for_backward(log_A, log_B, log_pi, obs, offsets, d_max)
         return hmm_forward(log_A, log_B, log_pi, obs, offsets, precision)
 
     @staticmethod
     def backward(ctx, grad_out):
-        log_A, log_B, log_pi, obs, offsets = ctx.saved_tensors
+        log_A, log_B, log_pi, obs, offsets, d_max = ctx.saved_tensors
+        max_T = ctx.max_T if ctx.max_T is not None else (int(d_max.item()) if d_max is not None else 0)
         gA, gB, gpi, _ = hmm_adjoint(log_A, log_B, log_pi, obs, offsets,
-                                     weights=grad_out.contiguous().to(torch.float64), want_loglik=False)
-        return gA, gB, gpi, None, None, None
+                                     weights=grad_out.contiguous().to(torch.float64), max_T=max_T, want_loglik=False)
+        return gA, gB, gpi, None, None, None, None
 
 
 # ------------------------------------------------------------------------- all-pairs

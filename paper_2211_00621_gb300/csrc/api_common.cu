@@ -11,6 +11,11 @@ namespace accel {
 static thread_local char g_last_error[512] = {0};
 static std::atomic<int> g_debug{0};
 static std::atomic<unsigned long long> g_launches{0};
+static thread_local int32_t* g_status_word = nullptr;     // accel_set_device_status
+static std::atomic<unsigned long long> g_watchdog_ns{0};  // accel_set_watchdog_ns
+
+int32_t* status_word(int32_t* fallback) { return g_status_word ? g_status_word : fallback; }
+uint64_t watchdog_ns() { return g_watchdog_ns.load(std::memory_order_relaxed); }
 
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
@@ -126,6 +131,32 @@ const char* accel_last_error(void) { return accel::g_last_error; }
 void accel_set_debug(int32_t on) { accel::g_debug.store(on ? 1 : 0); }
 int32_t accel_get_debug(void) { return accel::g_debug.load(); }
 uint64_t accel_launch_count(void) { return accel::g_launches.load(); }
+
+accel_status accel_set_device_status(int32_t* d_status) {
+    accel::g_status_word = d_status;
+    return accel::ok();
+}
+
+accel_status accel_sync_status(int32_t* d_status, int32_t clear, void* stream) {
+    using namespace accel;
+    ACCEL_REQUIRE(d_status != nullptr, ACCEL_ERR_INVALID_ARG, "accel_sync_status: null status word");
+    cudaStream_t st = as_stream(stream);
+    int32_t h = 0;
+    ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, d_status, 4, cudaMemcpyDeviceToHost, st));
+    if (clear) ACCEL_CUDA_TRY(cudaMemsetAsync(d_status, 0, 4, st));
+    ACCEL_CUDA_TRY(cudaStreamSynchronize(st));
+    switch (h) {
+        case ACCEL_OK: return ok();
+        case ACCEL_ERR_TIMEOUT:
+            return set_error(h, "device-side status: TIMEOUT (a bounded wait gave up or the watchdog budget ran out)");
+        case ACCEL_ERR_SHAPE:
+            return set_error(h, "device-side status: SHAPE (a sequence longer than the max_T the call was sized for)");
+        default: return set_error(h, "device-side status %d", h);
+    }
+}
+
+void accel_set_watchdog_ns(uint64_t budget_ns) { accel::g_watchdog_ns.store(budget_ns); }
+uint64_t accel_get_watchdog_ns(void) { return accel::g_watchdog_ns.load(); }
 
 }  // extern "C"
 

@@ -150,4 +150,14 @@ accel_status debug_check_symbols(const int32_t* d_obs, int64_t n, int32_t M, voi
 // Bytes every workspace reserves at its start for debug / device status words.
 constexpr size_t kStatusBytes = 256;
 
+// Device status word of a call made on this thread: the word the caller registered with
+// accel_set_device_status, or `fallback` (the call's own word in its workspace) if none.
+int32_t* status_word(int32_t* fallback);
+// Watchdog budget of the persistent single-CTA BF16 forward (accel_set_watchdog_ns; 0 = off).
+uint64_t watchdog_ns();
+
+// Record a device-side error: the first error stays (compare-and-swap from ACCEL_OK), so a
+// word shared by several calls keeps the earliest failure until the caller clears it.
+__device__ __forceinline__ void report_status(int32_t* word, int32_t code) { atomicCAS(word, ACCEL_OK, code); }
+
 }  // namespace accel

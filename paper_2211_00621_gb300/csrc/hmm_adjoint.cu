@@ -96,7 +96,7 @@ __device__ void load_group(const Prm& p, GroupInfo& gi) {
         gi.o0[g] = s >= 0 ? p.off[s] : 0;
         gi.C[g] = s >= 0 ? seg_len(gi.T[g]) : 1;
         if (s >= 0 && gi.C[g] > p.Cmax) {   // longer than max_T: skip, report
-            if (threadIdx.x == 0) atomicExch(p.status, ACCEL_ERR_SHAPE);
+            if (threadIdx.x == 0) report_status(p.status, ACCEL_ERR_SHAPE);
             gi.seq[g] = -1;
             gi.T[g] = 0;
             gi.C[g] = 1;
@@ -154,7 +154,7 @@ __device__ __forceinline__ bool fwd_step(const Prm& p, simt::AStream& as, float*
 }
 
 __device__ __forceinline__ void report_timeout(const Prm& p, simt::AStream& as) {
-    if (threadIdx.x == 0) atomicExch(p.status, ACCEL_ERR_TIMEOUT);
+    if (threadIdx.x == 0) report_status(p.status, ACCEL_ERR_TIMEOUT);
     simt::as_drain(as);
 }
 
@@ -679,7 +679,7 @@ __device__ void load_gs(const Prm& p, GS& gs, int64_t gstart, int gsize) {
         int64_t T = sq >= 0 ? p.off[sq + 1] - p.off[sq] : 0;
         int C = sq >= 0 ? seg_len(T) : 1;
         if (sq >= 0 && C > p.Cmax) {
-            atomicExch(p.status, ACCEL_ERR_SHAPE);
+            report_status(p.status, ACCEL_ERR_SHAPE);
             sq = -1;
             T = 0;
             C = 1;
@@ -952,7 +952,7 @@ __device__ __forceinline__ void xchg_finish(Xchg& xc, int par, uint32_t bytes, i
         if ((i & 255) == 0) {
             const uint64_t now = tc::globaltimer_ns();
             if (i == 0) t0 = now;
-            else if (now - t0 > 2000000000ull) { atomicExch(status, ACCEL_ERR_TIMEOUT); break; }
+            else if (now - t0 > 2000000000ull) { report_status(status, ACCEL_ERR_TIMEOUT); break; }
         }
     }
     xc.phase ^= 1u << par;
@@ -1503,7 +1503,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + kStatusOff, 0, 4, st));
     adj::Prm p;
     p.K = K; p.M = M; p.Cmax = L.Cmax; p.S = S; p.Kp = adj::padK(K);
-    p.status = (int32_t*)(ws + kStatusOff);
+    p.status = status_word((int32_t*)(ws + kStatusOff));
     p.rows = (int32_t*)(ws + L.rows);
     p.ebuf = (int32_t*)(ws + L.ebuf);
     p.gam = (float*)(ws + L.gam);
@@ -1539,6 +1539,9 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.rows, 0, (size_t)L.Cmax * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cntp, 0, (size_t)nsC * K * M * 4, st));
+    // every row starts with no symbol: the rows of a sequence skipped as longer than max_T are
+    // never written by the cluster kernels, and the count kernels index tables by osym
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.osym, 0xff, (size_t)S * L.Cmax * 4, st));
     if (counts_tc) ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.gam, 0, (size_t)S * L.Cmax * K * 4, st));
     if (S > 0) {
         r = order_by_length(d_offsets, S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)S * 4, 256), st);
@@ -1614,7 +1617,7 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     if (r != ACCEL_OK) return r;
     if (debug_mode()) {
         int32_t h = 0;
-        ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, ws + kStatusOff, 4, cudaMemcpyDeviceToHost, st));
+        ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, p.status, 4, cudaMemcpyDeviceToHost, st));
         ACCEL_CUDA_TRY(cudaStreamSynchronize(st));
         if (h == ACCEL_ERR_SHAPE) return set_error(h, "hmm_adjoint: a sequence is longer than max_T=%lld", (long long)max_T);
         if (h != ACCEL_OK) return set_error(h, "hmm_adjoint: device status %d (a bounded wait gave up)", h);

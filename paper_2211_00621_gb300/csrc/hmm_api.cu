@@ -17,11 +17,13 @@ accel_status check_model(const accel_hmm_model* m, const char* who) {
     return ACCEL_OK;
 }
 
-accel_status read_device_status(char* ws, cudaStream_t st) {
+accel_status read_device_status(const int32_t* d_status, cudaStream_t st) {
     int32_t h = 0;
-    ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, ws + kStatusOff, 4, cudaMemcpyDeviceToHost, st));
+    ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, d_status, 4, cudaMemcpyDeviceToHost, st));
     ACCEL_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h != ACCEL_OK) return set_error(h, "device-side status %d (a bounded wait gave up)", h);
+    if (h == ACCEL_ERR_TIMEOUT)
+        return set_error(h, "device-side status TIMEOUT (a bounded wait gave up or the watchdog budget ran out)");
+    if (h != ACCEL_OK) return set_error(h, "device-side status %d", h);
     return ACCEL_OK;
 }
 
@@ -60,13 +62,14 @@ accel_status hmm_forward(const accel_hmm_model* m, int32_t precision, const int3
         if (r != ACCEL_OK) return r;
     }
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + kStatusOff, 0, 4, st));
+    int32_t* dst = status_word((int32_t*)(ws + kStatusOff));
     if (precision == ACCEL_HMM_FP32_LOG) {
-        r = plain_forward(m, d_obs, d_offsets, S, d_loglik, ws + kStatusBytes, (int32_t*)(ws + kStatusOff), st);
+        r = plain_forward(m, d_obs, d_offsets, S, d_loglik, ws + kStatusBytes, dst, st);
     } else {
-        r = tc_forward(m, d_obs, d_offsets, S, d_loglik, ws, (int32_t*)(ws + kStatusOff), st);
+        r = tc_forward(m, d_obs, d_offsets, S, d_loglik, ws, dst, st);
     }
     if (r != ACCEL_OK) return r;
-    if (debug_mode()) return read_device_status(ws, st);
+    if (debug_mode()) return read_device_status(dst, st);
     return ok();
 }
 

@@ -148,6 +148,13 @@ accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int
             total += ms;
         }
         if (r != ACCEL_OK) break;
+        int32_t dev_status = ACCEL_OK;      // a candidate that timed out on the device is an error
+        ACCEL_CUDA_TRY(cudaMemcpy(&dev_status, ws + kStatusOff, 4, cudaMemcpyDeviceToHost));
+        if (dev_status != ACCEL_OK) {
+            r = set_error(dev_status, "hmm_autotune: device-side status %d while timing (split=%d, rows=%d, pair=%d)",
+                          dev_status, c.split, c.rows, c.pair);
+            break;
+        }
         const float ms = total / 2;
         if (ms < best_ms) { best_ms = ms; best = c; }
     }

@@ -65,5 +65,38 @@ accel_status order_by_length(const int64_t* d_off, int64_t S, int32_t* d_order, 
     return ACCEL_OK;
 }
 
+// Largest segment length max_s (off[s+1] - off[s]), one CTA (0 for S = 0).
+__global__ void __launch_bounds__(1024) k_max_len(const int64_t* __restrict__ off, int64_t S,
+                                                  int64_t* __restrict__ out) {
+    __shared__ int64_t s_max[32];
+    int64_t m = 0;
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+        const int64_t len = off[s + 1] - off[s];
+        m = len > m ? len : m;
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        const int64_t o = __shfl_xor_sync(0xffffffffu, m, d);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? s_max[threadIdx.x] : 0;
+        for (int d = 16; d > 0; d >>= 1) {
+            const int64_t o = __shfl_xor_sync(0xffffffffu, m, d);
+            m = o > m ? o : m;
+        }
+        if (threadIdx.x == 0) *out = m;
+    }
+}
+
 }  // namespace hmm
 }  // namespace accel
+
+extern "C" accel_status hmm_max_length(const int64_t* d_offsets, int64_t S, int64_t* d_max_T, void* stream) {
+    using namespace accel;
+    ACCEL_REQUIRE(S >= 0, ACCEL_ERR_INVALID_ARG, "hmm_max_length: negative S");
+    ACCEL_REQUIRE(d_offsets && d_max_T, ACCEL_ERR_INVALID_ARG, "hmm_max_length: null pointer");
+    hmm::k_max_len<<<1, 1024, 0, as_stream(stream)>>>(d_offsets, S, d_max_T);
+    return after_launch(as_stream(stream), "hmm_max_length", 1);
+}

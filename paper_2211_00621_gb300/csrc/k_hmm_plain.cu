@@ -193,7 +193,7 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
         __syncthreads();
         float acc[kG];
         if (!simt::as_matvec<kG>(as, sP, Kp, act, acc)) {
-            if (threadIdx.x == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            if (threadIdx.x == 0) report_status(status, ACCEL_ERR_TIMEOUT);
             simt::as_drain(as);
             return;
         }
@@ -208,7 +208,7 @@ k_plain_cta(const float* __restrict__ Aexp, const float* __restrict__ logB, cons
         __syncthreads();   // sP and s_red reuse
     }
     if (!simt::as_end(as)) {
-        if (threadIdx.x == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+        if (threadIdx.x == 0) report_status(status, ACCEL_ERR_TIMEOUT);
         simt::as_drain(as);
         return;
     }

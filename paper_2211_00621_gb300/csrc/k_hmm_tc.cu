@@ -31,7 +31,9 @@
 //    alpha~_0 = pi o b(o_0) the row's threads write in the next epilogue (so uneven lengths
 //    are packed into one launch).  The row's next symbol is loaded one step ahead, so no
 //    global load sits on the step's critical path.
-// All mbarrier waits are bounded (2 s); on expiry the kernel reports ACCEL_ERR_TIMEOUT.
+// All mbarrier waits are bounded (2 s); on expiry the kernel reports ACCEL_ERR_TIMEOUT.  The
+// single-CTA kernel also has a watchdog on its whole run time (accel_set_watchdog_ns), checked
+// at step boundaries, which stops it cleanly with ACCEL_ERR_TIMEOUT.
 #include "common.cuh"
 #include "hmm_internal.cuh"
 #include "tc_ptx.cuh"
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(128 * NSPLIT, 1)
 k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g_etab,
          const float* __restrict__ log_pi, const int32_t* __restrict__ obs, const int64_t* __restrict__ off,
          int64_t S, const int32_t* __restrict__ order, unsigned long long* __restrict__ next, int rows_active,
-         double* __restrict__ loglik, int32_t* __restrict__ status, TcLayout L) {
+         double* __restrict__ loglik, int32_t* __restrict__ status, uint64_t watchdog_ns, TcLayout L) {
     extern __shared__ __align__(1024) char smem[];
     char* sAT = smem + L.s_at;
     char* sX = smem + L.s_x;
@@ -196,6 +198,11 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
     bool queue_empty = !has_row || row >= rows_active;   // rows past rows_active never take sequences
     volatile uint32_t* s_flag = slot + 1;                 // set by a thread whose wait timed out
     if (tid == 0) *s_flag = 0;
+    // watchdog: when the launch has run longer than watchdog_ns (0 = no limit), thread 0 stops
+    // it at the next step boundary -- after the previous step's MMAs have completed and before
+    // new ones are issued, so no tensor-core work is in flight -- and every thread leaves
+    // through the normal exit that frees the tensor memory
+    const uint64_t t_launch = watchdog_ns != 0 ? tc::globaltimer_ns() : 0;
 
     // emission b(j, ob) for j in [jc, jc+32), FP32, times `scale` (a power of two: exact)
     auto load_emis = [&](int ob, int jc, float (&b)[32], float scale) {
@@ -266,9 +273,10 @@ k_hmm_tc(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g
         // ---- (A) publish X; the MMAs of this iteration
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
+        if (watchdog_ns != 0 && tid == 0 && tc::globaltimer_ns() - t_launch > watchdog_ns) *s_flag = 2;
         const bool any = __syncthreads_or(owner && seq >= 0);
         if (*s_flag != 0) {
-            if (tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            if (tid == 0) report_status(status, ACCEL_ERR_TIMEOUT);
             break;
         }
         if (!any) break;
@@ -583,7 +591,7 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
         tc::tc_fence_before();
         const bool any = __syncthreads_or(owner && seq != -1);
         if (*s_flag != 0 || !any) {
-            if (*s_flag != 0 && tid == 0) atomicExch(status, ACCEL_ERR_TIMEOUT);
+            if (*s_flag != 0 && tid == 0) report_status(status, ACCEL_ERR_TIMEOUT);
             if (iter > 0) xchg_wait(par ^ 1);     // the peer's last stores have landed (bounded)
             break;
         }
@@ -814,7 +822,7 @@ accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, cons
                                : (cfg.rows <= 64 ? k_hmm_tc<2, 64> : k_hmm_tc<2, 128>);
     ACCEL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
     kern<<<grid, 128 * cfg.split, L.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
-                                                      loglik, d_status, L);
+                                                      loglik, d_status, watchdog_ns(), L);
     return after_launch(st, "hmm_forward(bf16 tcgen05)", 5);
 }
 

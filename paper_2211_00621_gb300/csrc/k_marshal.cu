@@ -222,13 +222,17 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
     size_t po, lo, bo;
     size_t need = ws_layout(S, &po, &lo, &bo);
     ACCEL_REQUIRE(ws_bytes >= need, ACCEL_ERR_WORKSPACE, "accel_marshal_ragged: workspace %zu < %zu bytes", ws_bytes, need);
-    int64_t total = 0;
-    for (int64_t s = 0; s < S; ++s) {
-        ACCEL_REQUIRE(h_lengths[s] >= 0, ACCEL_ERR_SHAPE, "accel_marshal_ragged: length[%lld] < 0", (long long)s);
-        ACCEL_REQUIRE(h_lengths[s] == 0 || h_ptrs[s], ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: ptr[%lld] is null", (long long)s);
-        total += h_lengths[s];
+    if (debug_mode()) {
+        // O(S) checks of the host tables only in debug mode (accelerate mode: O(1) checks)
+        int64_t total = 0;
+        for (int64_t s = 0; s < S; ++s) {
+            ACCEL_REQUIRE(h_lengths[s] >= 0, ACCEL_ERR_SHAPE, "accel_marshal_ragged: length[%lld] < 0", (long long)s);
+            ACCEL_REQUIRE(h_lengths[s] == 0 || h_ptrs[s], ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: ptr[%lld] is null",
+                          (long long)s);
+            total += h_lengths[s];
+        }
+        ACCEL_REQUIRE(total == 0 || d_flat, ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: d_flat is null");
     }
-    ACCEL_REQUIRE(total == 0 || d_flat, ACCEL_ERR_INVALID_ARG, "accel_marshal_ragged: d_flat is null");
     cudaStream_t st = as_stream(stream);
     if (S == 0) {
         ACCEL_CUDA_TRY(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), st));

@@ -545,7 +545,8 @@ accel_status accel_segreduce(int32_t op, int32_t fused_map, int32_t in_dtype, in
 // streams, or different host threads without ordering) race on the array.
 // Set-up: the first call on each device looks up the array's device address with
 // cudaGetSymbolAddress while that device is current, and caches it; make that first call
-// before any stream capture begins.
+// before any stream capture begins.  The cached address belongs to the device's context of
+// that moment: resetting the device (cudaDeviceReset) after the first call is not supported.
 // ----------------------------------------------------------------------------------------
 #include <mutex>
 
@@ -596,8 +597,15 @@ accel_status accel_segreduce_noalloc(int32_t op, int32_t fused_map, int32_t in_d
     void* scratch = nullptr;
     accel_status r = segred::noalloc_scratch(&scratch);
     if (r != ACCEL_OK) return r;
-    return accel_segreduce(op, fused_map, in_dtype, out_dtype, d_data, N, d_offsets, S, scalar, d_out, scratch,
-                           segred::kNoAllocScratchBytes, stream);
+    r = accel_segreduce(op, fused_map, in_dtype, out_dtype, d_data, N, d_offsets, S, scalar, d_out, scratch,
+                        segred::kNoAllocScratchBytes, stream);
+    if (r != ACCEL_OK) {
+        // name this entry point in the message of an error found by the shared implementation
+        char msg[400];
+        snprintf(msg, sizeof(msg), "%s", accel_last_error());
+        return set_error(r, "accel_segreduce_noalloc (via %s)", msg);
+    }
+    return r;
 }
 
 }  // extern "C"

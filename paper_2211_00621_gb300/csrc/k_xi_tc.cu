@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
         failed = __syncthreads_or(!ok);
     }
     if (failed) {
-        if (tid == 0) atomicExch(p.status, ACCEL_ERR_TIMEOUT);
+        if (tid == 0) report_status(p.status, ACCEL_ERR_TIMEOUT);
     } else {
         tc::tc_fence_after();
         // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows i of the block), column half w / 4
