@@ -150,11 +150,60 @@ def gradients_batch(p: dict, seqs=None, weights=None, params: dict | None = None
     return np.array(lls), gA, gB, gpi
 
 
+def loglik_scaled_batch(p: dict, seqs=None, params: dict | None = None) -> np.ndarray:
+    """logL of many sequences by the scaled recursion of :func:`forward_scaled`, all
+    sequences advanced together: the forward vectors of the sequences still running at step t
+    are the rows of one matrix X, and the step is one library matrix product X A (each row is
+    that sequence's a^_{t-1} A, rows independent), then the emission o b(o_t) and the
+    division of each row by its sum c_t; logL_s = sum_t log c_t.  Same arithmetic as the
+    per-sequence loop, for sizes where that loop is too slow."""
+    q = params if params is not None else p
+    A, B, pi = q["A"], q["B"], q["pi"]
+    obs, off = p["obs"], p["offsets"]
+    idx = np.arange(len(off) - 1) if seqs is None else np.asarray(list(seqs), dtype=np.int64)
+    T = (off[idx + 1] - off[idx]).astype(np.int64)
+    order = np.argsort(-T, kind="stable")          # longest first: the running set is a prefix
+    sidx, sT, start = idx[order], T[order], off[idx[order]]
+    logL = np.zeros(len(sidx))
+    x = pi[None, :] * B[:, obs[start]].T            # a~_1 = pi o b(o_1)
+    for t in range(int(sT.max()) if len(sT) else 0):
+        n = int(np.count_nonzero(sT > t))
+        if t > 0:
+            x = (x[:n] @ A) * B[:, obs[start[:n] + t]].T
+        c = x.sum(axis=1)
+        x = x / c[:, None]
+        logL[:n] += np.log(c)
+    out = np.empty(len(sidx))
+    out[order] = logL
+    return out
+
+
 def params_from_f32_logs(logs: dict) -> dict:
     """float64 parameters equal to exp of the float32 log inputs (the kernel's inputs)."""
     return {"A": np.exp(logs["log_A"].astype(np.float64)),
             "B": np.exp(logs["log_B"].astype(np.float64)),
             "pi": np.exp(logs["log_pi"].astype(np.float64))}
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to bfloat16 (8 significant bits) to nearest, ties to even, returned
+    as float32: add half a bfloat16 unit (0x7FFF plus the kept part's lowest bit, so that ties
+    go to the even neighbour) to the IEEE bit pattern and clear the 16 low bits.  Finite
+    inputs only."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def params_bf16_from_f32_logs(logs: dict) -> dict:
+    """The parameters as the BF16 tensor-core forward holds them: exp of the float32 logs
+    rounded to float32, then to bfloat16 for A and B (its matrix operand and emission
+    table); pi stays float32 (it enters the first vector in FP32).  float64 arrays."""
+    def r32(v):
+        return np.exp(v.astype(np.float64)).astype(np.float32)
+    return {"A": round_bf16(r32(logs["log_A"])).astype(np.float64),
+            "B": round_bf16(r32(logs["log_B"])).astype(np.float64),
+            "pi": r32(logs["log_pi"]).astype(np.float64)}
 
 
 # ------------------------------------------------------------------------ re-estimation

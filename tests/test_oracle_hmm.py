@@ -241,3 +241,74 @@ def test_mstep_row_without_counts_keeps_its_parameters():
     np.testing.assert_allclose(new[1], old[1])
     np.testing.assert_allclose(new[0, :2], np.log([0.25, 0.75]), rtol=1e-15)
     assert new[0, 2] == -np.inf
+
+
+# ------------------------------------------------------- sequence-batched scaled forward
+@pytest.mark.parametrize("name", ["hmm_k2_t5", "hmm_k3_t4"])
+def test_batched_forward_matches_bruteforce_fixture(name):
+    c = _load(name)
+    obs = c["obs"].astype(np.int32)
+    p = {"A": c["A"], "B": c["B"], "pi": c["pi"], "obs": obs, "offsets": np.array([0, len(obs)], np.int64)}
+    assert hmm.loglik_scaled_batch(p)[0] == pytest.approx(float(c["loglik"]), rel=1e-13)
+
+
+def test_batched_forward_matches_brute_force_on_mixed_lengths():
+    # brute force over every state path for each of several sequences of different lengths
+    # (1 .. 6 steps), all advanced together by the batched form
+    p = synth.hmm_workload(5, 2, 3, 12, "uniform", 1, 6)
+    ll = hmm.loglik_scaled_batch(p)
+    for s in range(12):
+        o = p["obs"][p["offsets"][s]:p["offsets"][s + 1]]
+        assert ll[s] == pytest.approx(brute.loglik(p["A"], p["B"], p["pi"], o), rel=1e-13)
+
+
+@pytest.mark.parametrize("K,M,S,kind,lo,hi", [(7, 5, 40, "uniform", 1, 60), (64, 16, 30, "loguniform", 1, 500),
+                                              (256, 64, 12, "loguniform", 50, 400)])
+def test_batched_forward_matches_per_sequence_forward(K, M, S, kind, lo, hi):
+    p = synth.hmm_workload(K + S, K, M, S, kind, lo, hi)
+    ll = hmm.loglik_scaled_batch(p)
+    ref = hmm.loglik_batch(p, log_space=True)        # the log-space recursion (no shared step)
+    np.testing.assert_allclose(ll, ref, rtol=1e-12)
+    sub = [S - 1, 0, 3]
+    np.testing.assert_allclose(hmm.loglik_scaled_batch(p, seqs=sub), ref[sub], rtol=1e-12)
+
+
+def test_batched_forward_closed_form_uniform_emissions():
+    p = synth.hmm_workload(9, 6, 5, 20, "uniform", 1, 80)
+    p["B"] = np.full((6, 5), 0.2)
+    np.testing.assert_allclose(hmm.loglik_scaled_batch(p), -np.diff(p["offsets"]) * math.log(5), rtol=1e-13)
+
+
+# ------------------------------------------------------------------- bfloat16 rounding
+def test_round_bf16_hand_worked():
+    # bfloat16 keeps 8 significant bits: the unit in the last place at 1.0 is 2^-7
+    x = np.array([1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20, 3.0, -1 - 3 * 2.0 ** -8,
+                  2.0 ** -130], np.float32)
+    want = np.array([1.0, 1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, 3.0, -1 - 2.0 ** -6, 2.0 ** -130], np.float32)
+    # ties to even: 1 + 2^-8 is halfway between 1 (even) and 1 + 2^-7; 1 + 3 2^-8 halfway
+    # between 1 + 2^-7 (odd) and 1 + 2^-6; just above the halfway point rounds up
+    np.testing.assert_array_equal(hmm.round_bf16(x), want)
+
+
+def test_round_bf16_matches_library_conversion():
+    torch = pytest.importorskip("torch")
+    g = synth.rng(8)
+    x = np.concatenate([g.standard_normal(20000), np.exp(g.uniform(-30, 5, 20000)),
+                        # exact halfway points: a bfloat16 value plus half its unit in the last place
+                        (g.integers(1, 255, 2000) * 2.0 + 1) * 2.0 ** -9]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(hmm.round_bf16(x), ref)
+
+
+def test_bf16_parameters_are_the_rounded_exponentials():
+    p = synth.hmm_workload(2, 16, 8, 1, "fixed", 5, 5)
+    logs = synth.hmm_log_inputs_f32(p)
+    q = hmm.params_bf16_from_f32_logs(logs)
+    # every entry has at most 8 significant bits and lies within half a bfloat16 unit
+    for k, lk in (("A", "log_A"), ("B", "log_B")):
+        v = q[k]
+        m, _ = np.frexp(v)
+        assert np.all(m * 2 ** 8 == np.round(m * 2 ** 8))
+        ex = np.exp(logs[lk].astype(np.float64))
+        assert np.all(np.abs(v - ex) <= 2.0 ** -8 * ex * (1 + 1e-6))
+    np.testing.assert_array_equal(q["pi"], np.exp(logs["log_pi"].astype(np.float64)).astype(np.float32))

@@ -55,3 +55,37 @@ def test_subset_matches_full():
     idx = [0, 17, 99]
     np.testing.assert_array_equal(pairwise.accel(b["pos"], b["mass"], 1e-3, idx), full[idx])
     assert pairwise.term_scale(b["pos"], b["mass"], 1e-3, idx).shape == (3,)
+
+
+def test_term_scale_two_bodies_hand_worked():
+    # (0,0,0) m=2 and (3,0,0) m=5, eps=4: r^2 + eps^2 = 9 + 16 = 25, 25^(3/2) = 125; the self
+    # term is zero; each body sees the other's |m_j r / (r^2+eps^2)^(3/2)| = m_j 3 / 125, then
+    # divided by sqrt(N) = sqrt(2)
+    pos = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 0.0]])
+    got = pairwise.term_scale(pos, np.array([2.0, 5.0]), 4.0, [0, 1])
+    np.testing.assert_allclose(got, [0.0848528137423857029, 0.0339411254969542812], rtol=1e-14)
+
+
+def test_term_scale_three_bodies_hand_worked():
+    # a 3-4-5 right triangle, masses 1, 2, 3, eps = 4: the denominators are 25^1.5 = 125,
+    # 32^1.5 = 181.01933598375617 and 41^1.5 = 262.52809373474680; body 0 sums 2*3/125 +
+    # 3*4/181.019..., body 1 1*3/125 + 3*5/262.528..., body 2 1*4/181.019... + 2*5/262.528...,
+    # each divided by sqrt(3)
+    pos = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 0.0], [0.0, 4.0, 0.0]])
+    got = pairwise.term_scale(pos, np.array([1.0, 2.0, 3.0]), 4.0, [0, 1, 2])
+    np.testing.assert_allclose(got, [0.0659860901520891945, 0.0468443199239936631, 0.0347497013859574824],
+                               rtol=1e-14)
+
+
+def test_term_scale_bounds_the_acceleration():
+    # |a_i| <= sum_j |term_ij| (triangle inequality), with equality when every other body lies
+    # on one ray from i (all terms parallel): collinear bodies on one side
+    pos = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [2.5, 0.0, 0.0], [4.0, 0.0, 0.0]])
+    m = np.array([1.0, 2.0, 0.5, 3.0])
+    n = len(m)
+    a0 = np.linalg.norm(pairwise.accel(pos, m, 0.1, [0])[0])
+    np.testing.assert_allclose(pairwise.term_scale(pos, m, 0.1, [0])[0] * np.sqrt(n), a0, rtol=1e-14)
+    b = synth.bodies(4, 50)
+    a = np.linalg.norm(pairwise.accel(b["pos"], b["mass"], 1e-3), axis=1)
+    ts = pairwise.term_scale(b["pos"], b["mass"], 1e-3, range(50)) * np.sqrt(50)
+    assert np.all(a <= ts * (1 + 1e-12))
