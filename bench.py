@@ -15,7 +15,13 @@ HBM when the timed region starts:
 
 Metric: HMM state-steps per second (K x sum of lengths, counted once for every forward
 pass and once for every adjoint pass) over the whole step; per-row times, the segmented
-reduce's GB/s and every kernel's roofline fraction are reported beside it.
+reduce's and the marshal's GB/s at HBM scale and every kernel's roofline fraction are
+reported beside it.  ALU rooflines use the FP32 rate measured in the same run
+(accel_alu_rate); the tensor and HBM ones the measured peaks.
+
+The CPU leg (rank 0, N=1) times the float64 oracle on the host cores -- one worker and one
+worker per allowed core, in each configuration's own unit -- and, from the oracle values it
+computes, states every result's error against the oracle (`errors`).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -41,8 +47,6 @@ from paper_2211_00621_gb300 import synth  # noqa: E402
 METRIC = "HMM fwd+adjoint state-steps/s & seg-reduce GB/s vs plain form, 1 GB300"
 UNIT = "state-steps/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
-N_SM = 152
-FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -305,8 +309,21 @@ def traffic_for(row: str):
     return e.get("dram_bytes_per_launch")
 
 
-def rooflines(W, row_ms, peaks, sm_mhz_max):
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
+def measure_alu(api):
+    """Arithmetic rates measured on this GPU at its running clocks (best of three launches
+    each): FP32 FMA and packed FMA (flop/s), MUFU rsqrt (op/s), FP64 FMA (flop/s)."""
+    L = api.L
+    r = {}
+    for name, kind in (("ffma", L.PROBE_FFMA), ("ffma2", L.PROBE_FFMA2), ("rsqrt", L.PROBE_RSQRT),
+                       ("dfma", L.PROBE_DFMA)):
+        r[name] = max(api.alu_rate(kind, iters=2048 if name != "dfma" else 64) for _ in range(3))
+    r["fp32_tflops"] = max(r["ffma"], r["ffma2"]) / 1e12
+    return r
+
+
+def rooflines(W, row_ms, peaks, fp32_peak):
+    """Per-row roofline: algorithmic work / time against the bounding unit's peak
+    (fp32_peak: the FP32 rate measured in this run, TFLOP/s)."""
     r = {}
     seg_bytes = 4 * W.seg_N * 3 + 8 * (W.seg_S + 1) * 3 + 8 * W.seg_S * 2 + 16 * W.seg_S
     r["segreduce"] = {"bound": "hbm", "achieved": seg_bytes / (row_ms["segreduce"] * 1e-3) / 1e9,
@@ -324,8 +341,12 @@ def rooflines(W, row_ms, peaks, sm_mhz_max):
                           "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     if W.adj is not None and "hmm_adjoint" in row_ms:
         a = W.adj
-        r["hmm_adjoint"] = {"bound": "alu", "achieved": 6 * a["K"] ** 2 * a["sumT"] / (row_ms["hmm_adjoint"] * 1e-3)
-                            / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
+        # 8 K^2 flop per time step: the forward, the checkpoint recomputation, the backward
+        # recursion and the xi accumulation, 2 K^2 each (6 K^2 without the recomputation)
+        sec = row_ms["hmm_adjoint"] * 1e-3
+        r["hmm_adjoint"] = {"bound": "alu", "achieved": 8 * a["K"] ** 2 * a["sumT"] / sec / 1e12,
+                            "peak": fp32_peak, "unit": "TFLOP/s", "flop_per_step": "8 K^2",
+                            "achieved_6K2": 6 * a["K"] ** 2 * a["sumT"] / sec / 1e12}
     r["allpairs"] = {"bound": "alu", "achieved": 20.0 * W.N * W.N / (row_ms["allpairs"] * 1e-3) / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s"}
     for v in r.values():
@@ -334,44 +355,212 @@ def rooflines(W, row_ms, peaks, sm_mhz_max):
 
 
 # ---------------------------------------------------------------------- CPU oracle
-def oracle_sample(seconds: float, seed: int = 0):
-    """Times the oracle (as it stands) on a bounded sample of the HMM rows; returns
-    (state-steps, seconds, description)."""
+# The oracle as it stands, timed on the host cores: each worker process (spawned, so it never
+# inherits a CUDA context) runs one kind of unit for `seconds` and returns (units, seconds).
+#   hmm       random sequences of the three HMM configurations: the forward (K=64 plain and
+#             K=256 batched) or the forward-backward (K=256 adjoint); unit = state-steps, K
+#             per time step and pass (forward-backward counts two passes, as on the GPU)
+#   segreduce the config-1 segmented sum of x*x+1 (the oracle's vectorised form); unit = bytes
+#             of the algorithmic traffic 4 N + 16 S
+#   allpairs  the acceleration of random bodies of the N = 65,536 set; unit = interactions
+def _oracle_units(kind: str, seconds: float, seed: int):
     from oracle import hmm as ohmm
+    from oracle import pairwise as opair
+    from oracle import patterns as op
     g = synth.rng(seed)
-    work, t_total, n_fwd, n_fb = 0, 0.0, 0, 0
-    pl = synth.hmm_workload(**{k: v for k, v in synth.CFG_HMM_PLAIN.items()})
-    bf = synth.hmm_workload(**{k: v for k, v in synth.CFG_HMM_BATCHED.items()})
-    ad = synth.hmm_workload(**{k: v for k, v in synth.CFG_HMM_ADJOINT.items()})
-    pl_par = ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(pl))
-    bf_par = ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(bf))
-    ad_par = ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(ad))
-    t_end = time.perf_counter() + seconds
-    while time.perf_counter() < t_end:
-        for p, par, fb in ((pl, pl_par, False), (bf, bf_par, False), (ad, ad_par, True)):
-            s = int(g.integers(0, p["S"]))
+    units, busy = 0, 0.0
+    if kind == "hmm":
+        cfgs = [(synth.CFG_HMM_PLAIN, False), (synth.CFG_HMM_BATCHED, False), (synth.CFG_HMM_ADJOINT, True)]
+        work = []
+        for c, fb in cfgs:
+            p = synth.hmm_workload(c["seed"], c["K"], c["M"], c["S"], c["kind"], c["lo"], c["hi"])
+            work.append((p, ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(p)), fb))
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            for p, par, fb in work:
+                sq = int(g.integers(0, p["S"]))
+                t0 = time.perf_counter()
+                if fb:
+                    ohmm.gradients_batch(p, seqs=[sq], params=par)
+                else:
+                    ohmm.loglik_batch(p, seqs=[sq], params=par)
+                busy += time.perf_counter() - t0
+                units += (2 if fb else 1) * p["K"] * int(p["lengths"][sq])
+    elif kind == "segreduce":
+        c = synth.CFG_SEGREDUCE
+        data, lengths = synth.ragged_flat_int32(c["seed"], c["S"], c["len_lo"], c["len_hi"], c["val_lo"], c["val_hi"])
+        off = np.zeros(c["S"] + 1, np.int64)
+        np.cumsum(lengths, out=off[1:])
+        nbytes = 4 * len(data) + 16 * c["S"]
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
             t0 = time.perf_counter()
-            if fb:
-                ohmm.gradients_batch(p, seqs=[s], params=par)
-                work += 2 * p["K"] * int(p["lengths"][s])
-                n_fb += 1
-            else:
-                ohmm.loglik_batch(p, seqs=[s], params=par)
-                work += p["K"] * int(p["lengths"][s])
-                n_fwd += 1
-            t_total += time.perf_counter() - t0
-    desc = (f"float64 numpy oracle: {n_fwd} forward passes (random sequences of the K=64 and K=256 configs) and "
-            f"{n_fb} forward-backward passes (K=256 adjoint config), {t_total:.1f} s")
-    return work, t_total, desc
+            op.segreduce_fast(op.RED_ADD, op.MAP_SQ_PLUS_ONE, data, off, np.int64)
+            busy += time.perf_counter() - t0
+            units += nbytes
+    elif kind == "allpairs":
+        b = synth.bodies(synth.CFG_ALLPAIRS["seed"], synth.CFG_ALLPAIRS["N"])
+        pos, mass = b["aos"][:, :3].astype(np.float64), b["aos"][:, 3].astype(np.float64)
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            i = int(g.integers(0, len(mass)))
+            t0 = time.perf_counter()
+            opair.accel(pos, mass, synth.CFG_ALLPAIRS["eps"], [i])
+            busy += time.perf_counter() - t0
+            units += len(mass)
+    else:
+        raise ValueError(kind)
+    return units, busy
 
 
-def oracle_threads():
-    # numpy matrix-vector products at K <= 256 run on one thread in the BLAS builds used here;
-    # report the process's allowed cores as the upper bound only if BLAS threading is on.
-    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        if os.environ.get(var):
-            return int(os.environ[var])
-    return 1
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_rate(kind: str, seconds: float, workers: int, seed: int = 0):
+    """Units per second of `workers` oracle processes running side by side for `seconds`
+    (the sum of the workers' units over the longest worker's busy time)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    old = os.environ.get("OPENBLAS_NUM_THREADS")
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"        # one core per worker (inherited at spawn)
+    try:
+        with ctx.Pool(workers) as pool:
+            res = pool.starmap(_oracle_units, [(kind, seconds, seed + 7919 * k) for k in range(workers)])
+    finally:
+        if old is None:
+            os.environ.pop("OPENBLAS_NUM_THREADS", None)
+        else:
+            os.environ["OPENBLAS_NUM_THREADS"] = old
+    units = sum(u for u, _ in res)
+    busy = max(b for _, b in res)
+    return units / busy, units, busy
+
+
+UNITS = {"hmm": "state-steps/s", "segreduce": "GB/s", "allpairs": "interactions/s"}
+SAMPLES = {"hmm": "random sequences of the K=64 plain and K=256 batched configurations (forward) and of the "
+                  "K=256 adjoint configuration (forward-backward), float64 numpy",
+           "segreduce": "the 4,096-sequence segmented sum of x*x+1 (oracle.patterns.segreduce_fast, int64)",
+           "allpairs": "single bodies of the N=65,536 set against all N (oracle.pairwise.accel, float64)"}
+
+
+def cpu_baseline(seconds_each: float):
+    """The oracle per configuration unit at one core and at every allowed core."""
+    cores = host_cores()
+    out = {}
+    for kind in ("hmm", "segreduce", "allpairs"):
+        r1, _, b1 = oracle_rate(kind, seconds_each, 1, seed=11)
+        rn, _, bn = oracle_rate(kind, seconds_each, cores, seed=13)
+        scale = 1e-9 if kind == "segreduce" else 1.0
+        out[kind] = {"unit": UNITS[kind], "one_core": r1 * scale, "all_cores": rn * scale, "cores": cores,
+                     "sample": SAMPLES[kind] + f", {seconds_each:.0f} s per worker"}
+    return out
+
+
+def _relstats(rel):
+    rel = np.asarray(rel, dtype=np.float64)
+    return {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)), "median": float(np.median(rel)),
+            "n": int(rel.size)}
+
+
+def errors_leg(W, out, api, torch, dev, seed: int = 0):
+    """Every result's error against the float64 oracle, from the outputs of the last timed
+    step (and, for the adjoint, one more untimed call on a subset of sequences): this leg runs
+    the oracle, so it belongs to the CPU leg.  Samples are stated; the tests compare every
+    element."""
+    from oracle import hmm as ohmm
+    from oracle import pairwise as opair
+    from oracle import patterns as op
+    g = synth.rng(seed)
+    e = {}
+    # seg-reduce (config 1): int64, bit-exact
+    c = synth.CFG_SEGREDUCE
+    data, lengths = synth.ragged_flat_int32(c["seed"], c["S"], c["len_lo"], c["len_hi"], c["val_lo"], c["val_hi"])
+    off = np.zeros(c["S"] + 1, np.int64)
+    np.cumsum(lengths, out=off[1:])
+    ref = op.segreduce_fast(op.RED_ADD, op.MAP_SQ_PLUS_ONE, data, off, np.int64)
+    seg, mx = out["seg"]
+    got = seg.cpu().numpy()
+    e["segreduce"] = {"mismatches": int(np.count_nonzero(got != ref)), "max_equal": int(mx.item()) == int(ref.max()),
+                      "n": int(ref.size), "criterion": "bit-exact int64"}
+    # HMM FP32 log-space forward (config 2): every sequence, oracle on the float32-rounded logs
+    cp = synth.CFG_HMM_PLAIN
+    p = synth.hmm_workload(cp["seed"], cp["K"], cp["M"], cp["S"], cp["kind"], cp["lo"], cp["hi"])
+    ref = ohmm.loglik_scaled_batch(p, params=ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(p)))
+    e["hmm_fp32_logL"] = dict(_relstats(np.abs(out["plain"].cpu().numpy() - ref) / np.abs(ref)),
+                              tolerance=1e-5, reading="relative per sequence; oracle on the float32-rounded logs")
+    # HMM BF16 batched forward (config 3): a sample (the 16 longest + 496 random sequences)
+    # under three readings of the reference parameters
+    cb = synth.CFG_HMM_BATCHED
+    p = synth.hmm_workload(cb["seed"], cb["K"], cb["M"], cb["S"], cb["kind"], cb["lo"], cb["hi"])
+    logs = synth.hmm_log_inputs_f32(p)
+    sample = np.unique(np.concatenate([np.argsort(p["lengths"])[-16:], g.choice(cb["S"], 496, replace=False)]))
+    ll = out["bf16"].cpu().numpy()[sample]
+    bf = {}
+    for tag, par in (("original_params", None), ("fp32_rounded_params", ohmm.params_from_f32_logs(logs)),
+                     ("bf16_rounded_params", ohmm.params_bf16_from_f32_logs(logs))):
+        r = ohmm.loglik_scaled_batch(p, seqs=sample, params=par)
+        bf[tag] = _relstats(np.abs(ll - r) / np.abs(r))
+    bf.update(tolerance=1e-3, sample=f"{sample.size} sequences: the 16 longest and random ones",
+              reading="original: total error incl. rounding the parameters; bf16: the BF16 arithmetic alone")
+    e["hmm_bf16_logL"] = bf
+    # adjoint (config 4): the gradient of a subset's summed logL (0/1 weights), entry by entry
+    # against the oracle's expected counts, and against central differences of the oracle
+    if W.adj is not None:
+        ca = synth.CFG_HMM_ADJOINT
+        a = W.adj
+        p = synth.hmm_workload(ca["seed"], ca["K"], ca["M"], ca["S"], ca["kind"], ca["lo"], ca["hi"])
+        par = ohmm.params_from_f32_logs(synth.hmm_log_inputs_f32(p))
+        sub = sorted(set(g.choice(ca["S"], 7, replace=False).tolist() + [int(np.argmax(p["lengths"]))]))
+        w = np.zeros(ca["S"])
+        w[sub] = 1.0
+        gA, gB, gpi, _ = api.hmm_adjoint(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"],
+                                         weights=torch.from_numpy(w).to(dev), max_T=a["maxT"], want_loglik=False)
+        _, rA, rB, rpi = ohmm.gradients_batch(p, seqs=sub, params=par)
+        adj = {}
+        for name, gg, rr in (("log_A", gA, rA), ("log_B", gB, rB), ("log_pi", gpi, rpi)):
+            gg = gg.cpu().numpy().astype(np.float64)
+            rel = np.abs(gg - rr) / np.maximum(np.abs(rr), 1e-300)
+            big = rr > 1e-6 * rr.sum(axis=-1, keepdims=True)     # entries above the row-total floor
+            adj[name] = {"max_entry_rel": float(rel[big].max()), "median_entry_rel": float(np.median(rel[big])),
+                         "rel_frobenius": float(np.linalg.norm(gg - rr) / np.linalg.norm(rr))}
+        # central differences (h = 1e-6) of sum_s logL_s over the subset, float64 oracle
+        h = 1e-6
+        fd_err = []
+        gA_np = gA.cpu().numpy()
+        top = np.argsort(rA, axis=None)[-rA.size // 100:]          # among the largest 1% of entries
+        for q in g.choice(top, 4, replace=False):
+            i, j = (int(x) for x in np.unravel_index(int(q), rA.shape))
+            lo, hi = dict(par), dict(par)
+            lo["A"], hi["A"] = par["A"].copy(), par["A"].copy()
+            hi["A"][i, j] *= np.exp(h)
+            lo["A"][i, j] *= np.exp(-h)
+            fd = (ohmm.loglik_scaled_batch(p, seqs=sub, params=hi).sum()
+                  - ohmm.loglik_scaled_batch(p, seqs=sub, params=lo).sum()) / (2 * h)
+            fd_err.append(abs(gA_np[i, j] - fd) / max(abs(fd), 1e-12))
+        adj["fd_log_A_max_rel"] = float(max(fd_err))
+        adj.update(sample=f"{len(sub)} sequences (0/1 weights), all entries; central differences of 4 of the "
+                          "largest 1% entries of log A",
+                   tolerance="|g - r| <= 1e-4 |r| + 1e-6 row total")
+        e["hmm_adjoint_grad"] = adj
+    # all-pairs (config 5): 256 random bodies
+    ca = synth.CFG_ALLPAIRS
+    b = synth.bodies(ca["seed"], ca["N"])
+    pos, mass = b["aos"][:, :3].astype(np.float64), b["aos"][:, 3].astype(np.float64)
+    idx = np.sort(g.choice(ca["N"], 256, replace=False))
+    ref = opair.accel(pos, mass, ca["eps"], idx)
+    ax, ay, az = out["allpairs"]
+    got = torch.stack([ax, ay, az], 1).cpu().numpy().astype(np.float64)[idx]
+    err = np.linalg.norm(got - ref, axis=1)
+    scale = np.maximum(np.linalg.norm(ref, axis=1), opair.term_scale(pos, mass, ca["eps"], idx))
+    e["allpairs_accel"] = dict(_relstats(err / np.linalg.norm(ref, axis=1)),
+                               criterion_max=float((err / scale).max()), tolerance=1e-4,
+                               sample="256 random bodies", reading="per-body relative; criterion_max = "
+                               "max |a - a_ref| / max(|a_ref|, sum_j |term_ij| / sqrt(N))")
+    return e
 
 
 # ------------------------------------------------------------- single-kernel cases
@@ -414,7 +603,52 @@ def segreduce_sweep(torch, dev, api, S=1 << 20, reps=10, plain=False):
     return {"S": S, "N": int(d.numel()), "ms": ms, "GB/s": nbytes / (ms * 1e-3) / 1e9, "bytes": nbytes}
 
 
-PROFILE_CASES = ("segreduce_sweep", "step", "hmm_plain", "hmm_bf16", "hmm_bf16_small", "hmm_adjoint",
+def marshal_sweep(torch, dev, api, S, reps=10):
+    """accel_marshal_ragged at HBM scale: S int32 sequences with lengths U{0..256} stored as
+    separate pieces in device memory (placed in a shuffled order, so the gather reads
+    scattered addresses) -> flat data + int64 offsets; L2 flushed before each rep.  The
+    call's pointer and length tables (page-locked host memory, copied in stream order) are
+    part of the timed call.  Algorithmic bytes: 8 per element (read + write) + 24 per
+    sequence (the two 8-byte table entries read, one offset written)."""
+    import ctypes as C
+    lib = api.L.load()
+    lengths = synth.ragged_lengths(1, S)
+    N = int(lengths.sum())
+    g = synth.rng(5)
+    perm = g.permutation(S)                      # piece order in the source buffer
+    start = np.zeros(S, np.int64)
+    start[perm] = np.concatenate([[0], np.cumsum(lengths[perm])[:-1]])
+    src = torch.randint(-1000, 1001, (N,), dtype=torch.int32, device=dev)
+    ptrs = torch.from_numpy(src.data_ptr() + 4 * start).pin_memory()
+    lens = torch.from_numpy(lengths.astype(np.int64)).pin_memory()
+    flat = torch.empty(N, dtype=torch.int32, device=dev)
+    offsets = torch.empty(S + 1, dtype=torch.int64, device=dev)
+    ws = torch.empty(lib.accel_marshal_ragged_workspace_size(S), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def run():
+        st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        api.L.check("accel_marshal_ragged", lib.accel_marshal_ragged(
+            C.c_void_p(ptrs.data_ptr()), C.c_void_p(lens.data_ptr()), S, api.L.I32, C.c_void_p(flat.data_ptr()),
+            C.c_void_p(offsets.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(), st))
+    for _ in range(3):
+        run()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    nbytes = 8 * N + 24 * S
+    return {"S": S, "N": N, "ms": ms, "GB/s": nbytes / (ms * 1e-3) / 1e9, "bytes": nbytes}
+
+
+PROFILE_CASES = ("segreduce_sweep", "marshal_sweep", "step", "hmm_plain", "hmm_bf16", "hmm_bf16_small", "hmm_adjoint",
                  "hmm_adjoint_small", "allpairs", "hmm_long", "hmm_long_small", "pairhist", "pairhist_small")
 
 
@@ -426,6 +660,12 @@ def profile_case(name, reps, torch, dev, tune_cache=None):
     if name == "segreduce_sweep":
         d, o = sweep_inputs(torch, dev, 1 << 20)
         fn = lambda: api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, d, o, torch.int64)
+    elif name == "marshal_sweep":
+        # 2^18 sequences (N ~ 33.5M elements): the marshal sweep's middle size, run `reps` times
+        marshal_sweep(torch, dev, api, 1 << 18, reps=reps)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "reps": reps, "ok": True}))
+        return 0
     elif name == "step":
         W = Workload(torch, dev, True)
         W.tune_and_capture(tune_cache)
@@ -482,23 +722,25 @@ def aggregate_ranks(ms_local: float, work_per_rank: float, world: int, allreduce
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    # the reference arm is the oracle, timed as it stands on the host cores
+    # the reference arm is the oracle, timed as it stands on the host cores (one worker per
+    # allowed core), in the line's own unit: HMM state-steps per second
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(args.ref_step_seconds, seed=1000)
-    work, secs = 0, 0.0
-    desc = ""
+        oracle_rate("hmm", min(args.ref_step_seconds, 1.0), cores, seed=1000)
+    units, secs = 0, 0.0
     for k in range(args.steps):
-        w, s, desc = oracle_sample(args.ref_step_seconds, seed=k)
-        work += w
-        secs += s
-    value = work / secs
+        _, u, b = oracle_rate("hmm", args.ref_step_seconds, cores, seed=k)
+        units += u
+        secs += b
+    value = units / secs
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "HMM rows of the hot path (K=64 plain, K=256 batched, K=256 adjoint), "
-                                   "bounded random sample of sequences per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                             "sample": desc + f" per step, {args.steps} steps"},
+            "config": {"workload": "HMM rows of the hot path (K=64 plain, K=256 batched, K=256 adjoint), bounded "
+                                   "random sample of sequences per step, one oracle process per host core"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": SAMPLES["hmm"] + f"; {args.ref_step_seconds:.0f} s per step per worker, "
+                                                        f"{args.steps} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -576,12 +818,13 @@ def main():
     step_ms = []
     launches0 = lib.accel_launch_count()
     barrier()
+    last = None
     for _ in range(args.steps):
         flush.zero_()
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         s.record()
-        W.step(ev)
+        last = W.step(ev)
         e.record()
         e.synchronize()
         step_ms.append(s.elapsed_time(e))
@@ -614,10 +857,15 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e, e2e_value = aggregate_ranks(statistics.median(e2e_ms), work, world, allreduce_max)
 
-    # ---------------- seg-reduce at HBM scale (2^16, 2^18, 2^20 segments; plain form at 2^20)
+    # ---------------- seg-reduce and marshal at HBM scale (2^16, 2^18, 2^20 segments; the
+    # seg-reduce's plain form at 2^20)
     sweeps = [segreduce_sweep(torch, dev, api, S=1 << e) for e in (16, 18, 20)]
     sweep = sweeps[-1]
     plain_form = segreduce_sweep(torch, dev, api, S=1 << 20, plain=True)
+    msweeps = [marshal_sweep(torch, dev, api, S=1 << e) for e in (16, 18, 20)]
+
+    # ---------------- measured ALU rates (the denominators of the "alu" rooflines)
+    alu = measure_alu(api)
 
     # ---------------- reported comparisons (untimed by the step): BF16 vs FP32 forward on the
     # batched input, adjoint vs forward-only on the adjoint input, adjoint memory
@@ -677,17 +925,19 @@ def main():
 
     # ---------------- rooflines
     peaks, peak_src = load_peaks()
-    for sw in sweeps:
+    for sw in sweeps + msweeps:
         sw["frac"] = sw["GB/s"] / peaks["hbm_gbs"]
-    rl = rooflines(W, row_ms, peaks, float(peaks.get("sm_max_mhz", 2070.0)))
+    rl = rooflines(W, row_ms, peaks, alu["fp32_tflops"])
     dom = max((k for k in rl), key=lambda k: row_ms.get(k, 0.0))
     roof = dict(rl[dom])
     roof["kernel"] = dom
     roof["traffic"] = traffic_for(dom)
-    roof["peak_source"] = f"{peak_src} ({'sustained bf16' if roof['bound'] == 'tensor' else roof['bound']})"
+    roof["peak_source"] = {"tensor": f"{peak_src} sustained bf16 (MEASURED_PEAKS.json)",
+                           "hbm": f"{peak_src} HBM copy (MEASURED_PEAKS.json)",
+                           "alu": "measured in this run: FP32 FMA rate (accel_alu_rate, best of FFMA and packed "
+                                  "FFMA2)"}[roof["bound"]]
 
-    rows = {k: {"ms": row_ms[k], "frac": rl[k]["frac"], "achieved": rl[k]["achieved"], "unit": rl[k]["unit"],
-                "bound": rl[k]["bound"]} for k in rl}
+    rows = {k: {kk: v for kk, v in rl[k].items() if kk != "peak"} | {"ms": row_ms[k]} for k in rl}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -699,17 +949,24 @@ def main():
                                    "; all-pairs N=65536",
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
-            "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweeps, "compare": compare,
-            "rows": rows, "roofline": roof,
+            "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweeps, "marshal_sweep": msweeps,
+            "compare": compare, "rows": rows, "roofline": roof,
+            "alu_measured": {"ffma_tflops": alu["ffma"] / 1e12, "ffma2_tflops": alu["ffma2"] / 1e12,
+                             "rsqrt_gops": alu["rsqrt"] / 1e9, "dfma_tflops": alu["dfma"] / 1e12,
+                             "how": "accel_alu_rate: 4 CTAs x 512 threads per SM, 8 independent dependent "
+                                    "chains per thread, CUDA events, running clocks, best of 3"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": int(launches), "clocks": clk,
             "autotune": W.tuned}
 
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        w, s, desc = oracle_sample(args.cpu_seconds)
-        line["cpu_baseline"] = {"value": w / s, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                                "sample": desc}
+        # the CPU leg: the oracle timed on the host cores, and the errors against it
+        per = cpu_baseline(args.cpu_seconds / 6)
+        h = per["hmm"]
+        line["cpu_baseline"] = {"value": h["all_cores"], "unit": UNIT, "cores": h["cores"], "kind": "oracle",
+                                "one_core": h["one_core"], "sample": h["sample"], "per_config": per}
+        line["errors"] = errors_leg(W, last, api, torch, dev)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -2,8 +2,12 @@
 the float64 oracle's forward-backward expected counts, brute-force enumeration and central
 finite differences of the float64 forward.
 
-Tolerance: relative Frobenius 1e-4 per gradient (FP32 arithmetic), against the oracle on
-the same float32-rounded log parameters the kernels receive.
+Tolerance, entry by entry, against the oracle on the same float32-rounded log parameters
+the kernels receive: |g - r| <= 1e-4 |r| + 1e-6 (row total of r).  Every gradient entry is
+a sum of non-negative terms (expected counts), each formed with FP32 relative error, so
+the error is relative to the entry; the row-total term only absorbs entries whose terms
+underflow.  A wrong entry in a rarely visited state's row fails it, which a whole-matrix
+norm would hide.  The relative Frobenius error is printed as a summary.
 """
 import json
 import os
@@ -30,10 +34,17 @@ def _rel_fro(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def _check_grads(got, ref, tol=1e-4):
+def _check_grads(got, ref, rtol=1e-4, row_atol=1e-6):
     for g, r, name in zip(got, ref, ("log_A", "log_B", "log_pi")):
-        e = _rel_fro(g, r)
-        assert e <= tol, f"{name}: relative Frobenius error {e:.3e}"
+        g = np.asarray(g, dtype=np.float64)
+        r = np.asarray(r, dtype=np.float64)
+        tot = r.sum(axis=-1, keepdims=True)               # expected visits of the row's state
+        err = np.abs(g - r)
+        bad = err > rtol * np.abs(r) + row_atol * tot
+        rel = err / np.maximum(np.abs(r), 1e-300)
+        print(f"[adjoint {name}] max entry rel err {rel.max():.3e}, relative Frobenius {_rel_fro(g, r):.3e}")
+        assert not bad.any(), (f"{name}: {int(bad.sum())} entries out of tolerance, worst at "
+                               f"{np.unravel_index(np.argmax(err - rtol * np.abs(r) - row_atol * tot), r.shape)}")
 
 
 @pytest.mark.parametrize("name", ["hmm_k2_t5", "hmm_k3_t4"])

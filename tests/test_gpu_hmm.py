@@ -64,23 +64,65 @@ def test_bf16_tc_more_sequences_than_rows():
     _check(p, acc.HMM_BF16_SCALED, sample=list(range(0, p["S"], 97)) + [p["S"] - 1])
 
 
-def test_bf16_tc_config_sampled():
-    c = synth.CFG_HMM_BATCHED
-    p = synth.hmm_workload(c["seed"], c["K"], c["M"], c["S"], c["kind"], c["lo"], c["hi"])
-    L = p["lengths"]
-    sample = sorted(set(np.argsort(L)[-6:].tolist() + np.argsort(L)[:4].tolist() + list(range(0, c["S"], 331))))
-    _check(p, acc.HMM_BF16_SCALED, sample=sample)
+# ---------------------------------------------------------------------------------------
+# The batched configuration (K=256, M=64, 4,096 sequences, lengths log-uniform in [50, 5000])
+# compared on EVERY sequence.  The float64 oracle is evaluated three ways (once each, shared
+# by the tests below): on the float32-rounded log parameters the library receives (the
+# parity reading); on the original float64 parameters (the total error, parameter rounding
+# included); and on the parameters as the kernel holds them, A and B rounded to bfloat16 (the
+# error of the BF16 arithmetic alone: the alpha tile rounded to BF16 every step).
+_FULL = {}
 
 
-def test_bf16_error_against_original_parameters_reported():
-    # total error (rounding of the parameters to FP32 logs and BF16 included) on a sample
-    c = synth.CFG_HMM_BATCHED
-    p = synth.hmm_workload(c["seed"], c["K"], c["M"], 256, c["kind"], c["lo"], 1000)
+def _batched_full():
+    if not _FULL:
+        c = synth.CFG_HMM_BATCHED
+        p = synth.hmm_workload(c["seed"], c["K"], c["M"], c["S"], c["kind"], c["lo"], c["hi"])
+        logs = synth.hmm_log_inputs_f32(p)
+        _FULL["p"] = p
+        _FULL["fp32_params"] = ohmm.loglik_scaled_batch(p, params=ohmm.params_from_f32_logs(logs))
+        _FULL["original"] = ohmm.loglik_scaled_batch(p)
+        _FULL["bf16_params"] = ohmm.loglik_scaled_batch(p, params=ohmm.params_bf16_from_f32_logs(logs))
+    return _FULL
+
+
+def _rel(ll, ref):
+    return np.abs(ll - ref) / np.abs(ref)
+
+
+def _full_bf16_run(tmp_path=None, force=None):
+    f = _batched_full()
+    p = f["p"]
     logs, t, obs, off = _prep(p)
+    if force is not None:
+        t["obs"], t["off"] = obs, off
+        _force_config(tmp_path, p["K"], p["M"], p["S"], *force[:2], t, pair=force[2])
+    else:
+        api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off)     # the bench's choice
     ll = api.hmm_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off, acc.HMM_BF16_SCALED).cpu().numpy()
-    idx = list(range(0, 256, 16))
-    ref = ohmm.loglik_batch(p, seqs=idx)
-    assert (np.abs(ll[idx] - ref) / np.abs(ref)).max() <= 1e-3
+    assert np.all(np.isfinite(ll))
+    return f, ll
+
+
+def _report(tag, rel):
+    print(f"\n[bf16 logL error, {tag}] max {rel.max():.3e}  p99 {np.percentile(rel, 99):.3e}  "
+          f"median {np.median(rel):.3e}  over {rel.size} sequences")
+
+
+def test_bf16_tc_config_all_sequences_autotuned():
+    f, ll = _full_bf16_run()
+    for tag in ("fp32_params", "original", "bf16_params"):
+        rel = _rel(ll, f[tag])
+        _report(tag, rel)
+        assert rel.max() <= 1e-3, (tag, rel.max())
+
+
+@pytest.mark.parametrize("split,rows,pair", [(2, 128, 0), (4, 64, 1), (4, 32, 1)])
+def test_bf16_tc_config_all_sequences_each_launch_shape(tmp_path, split, rows, pair):
+    f, ll = _full_bf16_run(tmp_path, (split, rows, pair))
+    rel = _rel(ll, f["fp32_params"])
+    _report(f"fp32_params, split={split} rows={rows} pair={pair}", rel)
+    assert rel.max() <= 1e-3
 
 
 def test_bf16_tc_rejects_unsupported_k():
@@ -130,17 +172,6 @@ def test_bf16_tc_cluster_pair(tmp_path, K, split, rows):
     t["obs"], t["off"] = obs, off
     _force_config(tmp_path, K, 40, 700, split, rows, t, pair=1)
     _check(p, acc.HMM_BF16_SCALED)
-
-
-def test_bf16_tc_cluster_pair_batched_config_sampled(tmp_path):
-    c = synth.CFG_HMM_BATCHED
-    p = synth.hmm_workload(c["seed"], c["K"], c["M"], c["S"], c["kind"], c["lo"], c["hi"])
-    logs, t, obs, off = _prep(p)
-    t["obs"], t["off"] = obs, off
-    _force_config(tmp_path, c["K"], c["M"], c["S"], 4, 64, t, pair=1)
-    L = p["lengths"]
-    sample = sorted(set(np.argsort(L)[-6:].tolist() + np.argsort(L)[:4].tolist() + list(range(0, c["S"], 331))))
-    _check(p, acc.HMM_BF16_SCALED, sample=sample)
 
 
 def test_autotune_times_candidates_and_caches(tmp_path):

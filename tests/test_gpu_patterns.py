@@ -252,10 +252,13 @@ def test_segreduce_scaled_sweep_size():
 
 
 # --------------------------------------------------------------------------------- loop
+# every output is compared: n = 100,001 and 100,003 are multiples of neither a warp, a CTA
+# nor the grid stride, so the partial last warp and the grid-stride remainder are checked;
+# n = 3 is a single partial warp
+@pytest.mark.parametrize("n", [100_001, 100_003, 3])
 @pytest.mark.parametrize("dt", [np.int32, np.int64, np.float32, np.float64])
 @pytest.mark.parametrize("body", [op.LOOP_AXPY, op.LOOP_SCALE])
-def test_loop_bodies(dt, body):
-    n = 100_001
+def test_loop_bodies(dt, body, n):
     g = synth.rng(2)
     if np.dtype(dt).kind == "i":
         a, b = g.integers(-1000, 1000, size=(2, n)).astype(dt)
@@ -263,9 +266,21 @@ def test_loop_bodies(dt, body):
         a, b = g.standard_normal((2, n)).astype(dt)
     t0 = _t(a)
     api.accel_loop(body, t0, _t(b), 2.0)
-    ref = op.loop_body(body, a[:3000], b[:3000], 2)
-    got = t0.cpu().numpy()[:3000]
+    ref = op.loop_body(body, a, b, 2)
+    got = t0.cpu().numpy()
+    assert got.shape == ref.shape
     if np.dtype(dt).kind == "i":
         assert np.array_equal(got, ref)
     else:
-        np.testing.assert_allclose(got, ref, rtol=1e-6)
+        # one multiply and one add in the element type: within 1 ulp of the float64 result
+        np.testing.assert_allclose(got, ref, rtol=2 * np.finfo(dt).eps, atol=0)
+
+
+def test_loop_leaves_elements_past_n_untouched():
+    a = np.arange(1000, dtype=np.float32)
+    b = np.ones(1000, dtype=np.float32)
+    t0 = _t(a)
+    api.accel_loop(op.LOOP_AXPY, t0, _t(b), 2.0, n=997)
+    got = t0.cpu().numpy()
+    np.testing.assert_array_equal(got[:997], a[:997] + 2)
+    np.testing.assert_array_equal(got[997:], a[997:])
