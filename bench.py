@@ -154,6 +154,7 @@ class Workload:
         self.with_adjoint = with_adjoint
         self.bf16_graph = None
         self.bf16_out = None
+        self.seg_graph = None
         self.tuned = None
 
     def tune_and_capture(self, tune_cache=None):
@@ -178,6 +179,40 @@ class Workload:
         torch.cuda.synchronize()
         self.bf16_graph = g
         self.tuned["graph_nodes"] = g.nodes()
+        self.capture_seg(side)
+
+    def capture_seg(self, side):
+        """The seg-reduce row (ragged marshal -> fused map + int64 segmented sum -> int64 max,
+        and the loop b = 2a over the flat data) captured into one CUDA graph over buffers
+        allocated once: the config-1 latency without a host round trip per call."""
+        api, torch, dev = self.api, self.torch, self.dev
+        lib = api.L.load()
+        N, S = self.seg_N, self.seg_S
+        b = {"flat": torch.empty(N, dtype=torch.int32, device=dev),
+             "off": torch.empty(S + 1, dtype=torch.int64, device=dev),
+             "ws_m": torch.empty(lib.accel_marshal_ragged_workspace_size(S), dtype=torch.uint8, device=dev),
+             "seg": torch.empty(S, dtype=torch.int64, device=dev),
+             "ws_s": torch.empty(lib.accel_segreduce_workspace_size(N, S), dtype=torch.uint8, device=dev),
+             "max": torch.empty(1, dtype=torch.int64, device=dev),
+             "ws_r": torch.empty(max(lib.accel_reduce_workspace_size(S, api.L.I64), 256), dtype=torch.uint8,
+                                 device=dev),
+             "twice": torch.empty(N, dtype=torch.int32, device=dev)}
+        self.seg_bufs = b
+
+        def body():
+            api.accel_marshal_ragged_table(self.table_dev, out=(b["flat"], b["off"]), ws=b["ws_m"])
+            api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, b["flat"], b["off"], torch.int64, out=b["seg"],
+                                ws=b["ws_s"])
+            api.accel_reduce(api.RED_MAX, b["seg"], out=b["max"], ws=b["ws_r"])
+            api.accel_loop(api.LOOP_SCALE, b["twice"], b["flat"], 2.0)
+        torch.cuda.synchronize()
+        g = api.Graph()
+        n0 = lib.accel_launch_count()
+        g.capture(body, stream=side)
+        self.seg_kernels = int(lib.accel_launch_count() - n0)    # kernels in one replay
+        torch.cuda.synchronize()
+        self.seg_graph = g
+        self.seg_graph_nodes = g.nodes()
 
     def state_steps(self):
         n = self.plain["K"] * self.plain["sumT"] + self.bf16["K"] * self.bf16["sumT"]
@@ -201,6 +236,9 @@ class Workload:
             return r
 
         def seg():
+            if self.seg_graph is not None:
+                self.seg_graph.launch()
+                return self.seg_bufs["seg"], self.seg_bufs["max"]
             flat, off = api.accel_marshal_ragged_table(self.table_dev)
             s = api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, flat, off, torch.int64)
             m = api.accel_reduce(api.RED_MAX, s)
@@ -832,6 +870,8 @@ def main():
     launches = lib.accel_launch_count() - launches0
     if W.bf16_graph is not None:
         launches += 5 * args.steps      # kernels inside each replay of the captured BF16 call
+    if W.seg_graph is not None:
+        launches += W.seg_kernels * args.steps    # ... and of the captured seg-reduce row
     clk = clocks.stop()
     def allreduce_max(x):
         t = torch.tensor([x], device=dev, dtype=torch.float64)

@@ -113,9 +113,12 @@ class RaggedTable:
                 raise TypeError("all sequences must have the same dtype")
             if not s.is_cuda and s.numel() and not s.is_pinned():
                 raise ValueError("host sequences must be in pinned memory")
-        self.ptrs = torch.tensor([s.data_ptr() if s.numel() else 0 for s in self.seqs] or [0],
-                                 dtype=torch.int64).pin_memory()
-        self.lengths = torch.tensor([int(s.numel()) for s in self.seqs] or [0], dtype=torch.int64).pin_memory()
+        # one page-locked buffer [pointers | lengths]: the library copies adjacent tables at once
+        tab = torch.tensor([s.data_ptr() if s.numel() else 0 for s in self.seqs] +
+                           [int(s.numel()) for s in self.seqs] or [0, 0], dtype=torch.int64).pin_memory()
+        n = max(self.S, 1)
+        self.ptrs = tab[:n]
+        self.lengths = tab[n:]
         self.total = int(self.lengths[:self.S].sum().item()) if self.S else 0
 
 
@@ -124,7 +127,7 @@ def ragged_table(seqs, dtype=None):
     return RaggedTable(seqs, dtype)
 
 
-def accel_marshal_ragged_table(table: RaggedTable, device="cuda", out=None):
+def accel_marshal_ragged_table(table: RaggedTable, device="cuda", out=None, ws=None):
     """Flatten the sequences of a RaggedTable into (flat data, int64 offsets) on device."""
     lib = L.load()
     if out is None:
@@ -132,7 +135,9 @@ def accel_marshal_ragged_table(table: RaggedTable, device="cuda", out=None):
         offsets = torch.empty(table.S + 1, dtype=torch.int64, device=device)
     else:
         flat, offsets = out
-    ws = _ws(lib.accel_marshal_ragged_workspace_size(table.S), flat.device if table.total else offsets.device)
+    need = lib.accel_marshal_ragged_workspace_size(table.S)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, flat.device if table.total else offsets.device)
     L.check("accel_marshal_ragged", lib.accel_marshal_ragged(C.c_void_p(table.ptrs.data_ptr()),
                                                              C.c_void_p(table.lengths.data_ptr()), table.S,
                                                              _dt(table.dtype), _ptr(flat), _ptr(offsets), _ptr(ws),
@@ -225,11 +230,14 @@ def accel_map(op: int, x: torch.Tensor, out_dtype=None, y: torch.Tensor | None =
     return out
 
 
-def accel_reduce(op: int, x: torch.Tensor):
+def accel_reduce(op: int, x: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
     lib = L.load()
     _need_cuda(x)
-    out = torch.empty(1, dtype=x.dtype, device=x.device)
-    ws = _ws(lib.accel_reduce_workspace_size(x.numel(), _dt(x)), x.device)
+    if out is None:
+        out = torch.empty(1, dtype=x.dtype, device=x.device)
+    need = lib.accel_reduce_workspace_size(x.numel(), _dt(x))
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, x.device)
     L.check("accel_reduce", lib.accel_reduce(op, _dt(x), _ptr(x), x.numel(), _ptr(out), _ptr(ws), ws.numel(),
                                              _stream()))
     return out

@@ -83,6 +83,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int64_t* __re
     if (i == S - 1) off[S] = p + inc;
 }
 
+// small inputs (S <= kScanSmall): the whole exclusive scan in one CTA, chunk by chunk with a
+// running carry -- one launch instead of three
+constexpr int64_t kScanSmall = 16 * kScanThreads;
+__global__ void __launch_bounds__(kScanThreads) k_scan_one(const int64_t* __restrict__ len, int64_t S,
+                                                            int64_t* __restrict__ off) {
+    __shared__ int64_t s_warp[32];
+    __shared__ int64_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < S; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < S ? len[i] : 0;
+        const int64_t inc = block_incl_scan(v, s_warp);
+        const int64_t carry = s_carry;
+        if (i < S) off[i] = carry + inc - v;
+        if (i == S - 1) off[S] = carry + inc;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) s_carry = carry + inc;
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- ragged gather
 // One warp per sequence (grid-stride over sequences); each lane moves up to 8 elements
 // per round with all loads issued before the stores.
@@ -147,10 +169,12 @@ static cudaError_t table_to_device(void* d_dst, const void* h_src, size_t bytes,
     return cudaMemcpyAsync(d_dst, h_src, bytes, cudaMemcpyHostToDevice, st);
 }
 
+// pointer table, then the length table right after it (so tables that are adjacent on the
+// host travel in one copy), then the scan's block totals
 size_t ws_layout(int64_t S, size_t* ptr_off, size_t* len_off, size_t* bsum_off) {
     int64_t nb = (S + kScanThreads - 1) / kScanThreads;
     *ptr_off = kStatusBytes;
-    *len_off = align_up(*ptr_off + (size_t)S * 8, 256);
+    *len_off = *ptr_off + (size_t)S * 8;
     *bsum_off = align_up(*len_off + (size_t)S * 8, 256);
     return align_up(*bsum_off + (size_t)(nb > 0 ? nb : 1) * 8, 256);
 }
@@ -242,12 +266,23 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
     int64_t* d_len = (int64_t*)(ws + lo);
     int64_t* d_bsum = (int64_t*)(ws + bo);
     const void** d_ptrs = (const void**)(ws + po);
-    ACCEL_CUDA_TRY(table_to_device(d_ptrs, h_ptrs, (size_t)S * sizeof(void*), st));
-    ACCEL_CUDA_TRY(table_to_device(d_len, h_lengths, (size_t)S * sizeof(int64_t), st));
+    if ((const void*)h_lengths == (const void*)(h_ptrs + S)) {
+        // the length table follows the pointer table on the host: one copy
+        ACCEL_CUDA_TRY(table_to_device(d_ptrs, h_ptrs, (size_t)S * 16, st));
+    } else {
+        ACCEL_CUDA_TRY(table_to_device(d_ptrs, h_ptrs, (size_t)S * sizeof(void*), st));
+        ACCEL_CUDA_TRY(table_to_device(d_len, h_lengths, (size_t)S * sizeof(int64_t), st));
+    }
     int64_t nb = (S + kScanThreads - 1) / kScanThreads;
-    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum);
-    k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
-    k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum, d_offsets);
+    int nscan = 1;
+    if (S <= kScanSmall) {
+        k_scan_one<<<1, kScanThreads, 0, st>>>(d_len, S, d_offsets);
+    } else {
+        k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum);
+        k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
+        k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum, d_offsets);
+        nscan = 3;
+    }
     int64_t warps_needed = S;
     int64_t blocks = (warps_needed + 7) / 8;
     int64_t cap = (int64_t)num_sms() * 8;
@@ -256,7 +291,7 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
         k_gather<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t* const*)d_ptrs, d_offsets, S, (int32_t*)d_flat);
     else
         k_gather<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t* const*)d_ptrs, d_offsets, S, (int64_t*)d_flat);
-    return after_launch(st, "accel_marshal_ragged", 4);
+    return after_launch(st, "accel_marshal_ragged", nscan + 1);
 }
 
 // offsets[0..n] = exclusive scan of the n host lengths (copied into the workspace first)
@@ -266,10 +301,16 @@ static accel_status scan_lengths(const int64_t* h_len, int64_t n, int64_t* d_off
     int64_t* d_len = (int64_t*)(ws + lo);
     int64_t* d_bsum = (int64_t*)(ws + bo);
     ACCEL_CUDA_TRY(table_to_device(d_len, h_len, (size_t)n * sizeof(int64_t), st));
+    if (n <= kScanSmall) {
+        k_scan_one<<<1, kScanThreads, 0, st>>>(d_len, n, d_off);
+        count_launches(1);
+        return ACCEL_OK;
+    }
     int64_t nb = (n + kScanThreads - 1) / kScanThreads;
     k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, n, d_bsum);
     k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
     k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, n, d_bsum, d_off);
+    count_launches(3);
     return ACCEL_OK;
 }
 
@@ -305,7 +346,7 @@ accel_status accel_marshal_nested(const void* const* h_ptrs, const int64_t* h_le
     }
     r = scan_lengths(h_group_sizes, G, d_group_offsets, (char*)d_ws, st);
     if (r != ACCEL_OK) return r;
-    return after_launch(st, "accel_marshal_nested", 3);
+    return after_launch(st, "accel_marshal_nested", 0);
 }
 
 size_t accel_unmarshal_ragged_workspace_size(int64_t S) {

@@ -121,16 +121,18 @@ k_reduce_partial(const T* __restrict__ in, int64_t n, typename compute_of<T>::ty
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Pass 2: one CTA combines the partials in index order.
+// Pass 2: one CTA combines the partials in index order.  The int64 result of an int32
+// reduction is narrowed; an empty reduction gives the neutral element of T itself (for an
+// int32 max, INT32_MIN -- not the narrowed int64 neutral element).
 template <typename T, int OP>
 __global__ void __launch_bounds__(kThreads)
-k_reduce_final(const typename compute_of<T>::type* __restrict__ partials, int nparts, T* __restrict__ out) {
+k_reduce_final(const typename compute_of<T>::type* __restrict__ partials, int nparts, int64_t n, T* __restrict__ out) {
     using C = typename compute_of<T>::type;
     __shared__ C smem[kThreads / 32];
     C acc = red_neutral<C>(OP);
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc = red_combine<OP, C>(acc, partials[i]);
     acc = block_reduce<OP, C>(acc, smem);
-    if (threadIdx.x == 0) *out = (T)acc;
+    if (threadIdx.x == 0) *out = n == 0 ? red_neutral<T>(OP) : (T)acc;
 }
 
 static int reduce_grid(int64_t n) {
@@ -203,7 +205,7 @@ accel_status accel_reduce(int32_t op, int32_t dtype, const void* d_in, int64_t n
     ACCEL_DISPATCH_DTYPE(dtype, T, ACCEL_DISPATCH_RED(op, OPC, {
         using C = typename compute_of<T>::type;
         k_reduce_partial<T, OPC><<<grid, kThreads, 0, st>>>((const T*)d_in, n, (C*)partials);
-        k_reduce_final<T, OPC><<<1, kThreads, 0, st>>>((const C*)partials, grid, (T*)d_out);
+        k_reduce_final<T, OPC><<<1, kThreads, 0, st>>>((const C*)partials, grid, n, (T*)d_out);
     }));
     return after_launch(st, "accel_reduce", 2);
 }

@@ -139,6 +139,7 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
     const int ne = (int)((e0 + TE < N) ? TE : N - e0);   // elements in this tile
     const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
     const C nel = red_neutral<C>(OP);
+    const Tout nel_out = red_neutral<Tout>(OP);   // an empty segment: the output type's own neutral
     const C sc = (C)scalar;
 
     // ---- stage the tile (16-byte vectors, coalesced) and the tile's offsets
@@ -190,7 +191,7 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
         }
         int q = a;
         // empty segments positioned at r0 precede q: they are owned here
-        for (int p = q - 1; p >= 0 && rel(p) == r0 && rel(p + 1) == r0; --p) out[lo_b + p] = (Tout)nel;
+        for (int p = q - 1; p >= 0 && rel(p) == r0 && rel(p + 1) == r0; --p) out[lo_b + p] = nel_out;
         int nend = rel_end(q);
         if (nend > r1) {
             // no segment ends among this thread's items: one fused map + fold
@@ -220,7 +221,7 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
                     // end of the data (their key is clamped to N-1)
                     while (lo_b + q < S && (k + 1 < r1 || k + 1 == rN)) {
                         if (!(rel(q) == k + 1 && rel_end(q) == k + 1)) break;
-                        out[lo_b + q] = (Tout)nel;
+                        out[lo_b + q] = nel_out;
                         ++q;
                     }
                     nend = (lo_b + q < S) ? rel_end(q) : TE + 2;
@@ -279,6 +280,37 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
 // prefix array is item-major (item i of thread t at i * kThreads + t), so the stores are
 // conflict-free with constant offsets.  The tile's open segment (if its last element does
 // not end a segment) is handed to the fixup kernel.
+//
+// The kernel is persistent (two CTAs per SM, each taking every gridDim-th tile) and keeps
+// its next tiles in flight while it works on the current one: a ring of kStages shared
+// buffers is filled by asynchronous global->shared copies (cp.async, 16 bytes per thread,
+// written in the swizzled order the threads read), each tile's copies forming one commit
+// group.  A tile's offsets chunk can only be fetched once its segment range [lo[b], lo[b+1])
+// is known, so the lo pairs travel one pipeline depth further ahead, through a small ring
+// of their own: the group that carries tile k's data also carries tile k + kStages - 1's lo
+// pair.  So kStages - 1 tiles (16 KB each) are in flight per CTA at every step.
+constexpr int kStages = 3;
+constexpr int kLoRing = 8;                                   // >= 2 kStages - 1
+constexpr size_t kStageBytes = kTileBytes + (size_t)kOffCap * 8;   // data tile + offsets chunk
+
+template <typename Tin> constexpr size_t segsum_smem_bytes() {
+    return kStages * kStageBytes + (size_t)tile_elems<Tin>() * 8 + 2 * kLoRing * 8 + (kThreads / 32) * 8;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// 16-byte asynchronous copy; bytes past src_bytes (0..16) are zero-filled and not read
+__device__ __forceinline__ void cp_async16(void* s, const void* g, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(s)), "l"(g), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <typename Tin>
 __device__ __forceinline__ uint64_t gmap(int map_op, int64_t x, int64_t sc) {
     switch (map_op) {
@@ -291,112 +323,159 @@ __device__ __forceinline__ uint64_t gmap(int map_op, int64_t x, int64_t sc) {
 }
 
 template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
-         const int64_t* __restrict__ lo_arr, int map_op, double scalar, Tout* __restrict__ out,
+         const int64_t* __restrict__ lo_arr, int64_t ntiles, int map_op, double scalar, Tout* __restrict__ out,
          int64_t* __restrict__ tail_seg, int64_t* __restrict__ tail_val) {
     constexpr int IT = items<Tin>();
     constexpr int TE = tile_elems<Tin>();
-    constexpr int PV = 16 / (int)sizeof(Tin);
-    // the staged tile and, once every thread holds its items, the prefix sums share storage
-    __shared__ __align__(16) uint64_t s_buf[TE];
-    int4* s_data = reinterpret_cast<int4*>(s_buf);  // kVecs 16-byte vectors (16 KB)
-    uint64_t* s_P = s_buf;                          // prefix of the mapped values, item-major
-    __shared__ int32_t s_pos[kOffCap];
-    __shared__ uint64_t s_wtot[kThreads / 32];
+    extern __shared__ __align__(16) char smem[];
+    uint64_t* s_P = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);   // prefix, item-major
+    int64_t* s_lo = reinterpret_cast<int64_t*>(smem + kStages * kStageBytes + (size_t)TE * 8);   // [kLoRing][2]
+    uint64_t* s_wtot = reinterpret_cast<uint64_t*>(s_lo + 2 * kLoRing);
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t b = blockIdx.x;
-    const int64_t e0 = b * TE;
-    const int ne = (int)((e0 + TE < N) ? TE : N - e0);
-    const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
+    const int64_t grid = gridDim.x, c = blockIdx.x;
+    const int64_t mytiles = c < ntiles ? (ntiles - 1 - c) / grid + 1 : 0;
     const int64_t sc = (int64_t)scalar;
-    const bool fast = map_op == ACCEL_MAP_SQ_PLUS_ONE && ne == TE;
+    auto stage_data = [&](int st) { return reinterpret_cast<int4*>(smem + (size_t)st * kStageBytes); };
+    auto stage_off = [&](int st) { return reinterpret_cast<int64_t*>(smem + (size_t)st * kStageBytes + kTileBytes); };
 
-    if (ne == TE) {
-        const int4* src = reinterpret_cast<const int4*>(data + e0);
+    // the lo pair of this CTA's k-th tile into its ring slot (thread 0)
+    auto issue_lo = [&](int64_t k) {
+        if (t == 0 && k < mytiles) {
+            const int64_t b = c + k * grid;
+            int64_t* d = s_lo + 2 * (k % kLoRing);
+            cp_async8(d, lo_arr + b);
+            cp_async8(d + 1, lo_arr + b + 1);
+        }
+    };
+    // the data tile and the offsets chunk of this CTA's k-th tile (its lo pair has arrived)
+    auto issue_tile = [&](int64_t k) {
+        if (k >= mytiles) return;
+        const int st = (int)(k % kStages);
+        const int64_t b = c + k * grid;
+        const int64_t e0 = b * TE;
+        const int64_t nbytes = ((e0 + TE < N) ? (int64_t)TE : N - e0) * (int64_t)sizeof(Tin);
+        const char* src = reinterpret_cast<const char*>(data + e0);
+        int4* dst = stage_data(st);
 #pragma unroll
         for (int r = 0; r < kVecPerThread; ++r) {
-            int v = r * kThreads + t;
-            s_data[swz(v)] = __ldg(src + v);
+            const int v = r * kThreads + t;
+            const int64_t rem = nbytes - 16 * (int64_t)v;
+            const uint32_t sb = rem >= 16 ? 16u : (rem > 0 ? (uint32_t)rem : 0u);
+            cp_async16(dst + swz(v), sb ? src + 16 * (int64_t)v : reinterpret_cast<const char*>(data), sb);
         }
-    } else {
-        Tin* sd = reinterpret_cast<Tin*>(s_data);
-        for (int e = t; e < TE; e += kThreads) sd[swz(e / PV) * PV + e % PV] = e < ne ? data[e0 + e] : Tin(0);
-    }
-    const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
-    const int64_t cnt = last - lo_b + 1;
-    const bool in_smem = cnt <= kOffCap;
-    // segment start relative to the tile, clamped to [0, ne]
-    auto clamp_rel = [&](int64_t x) -> int32_t {
-        const int64_t r = x - e0;
-        return (int32_t)(r < 0 ? 0 : (r > ne ? ne : r));
-    };
-    if (in_smem)
-        for (int i = t; i < cnt; i += kThreads) s_pos[i] = clamp_rel(off[lo_b + i]);
-    __syncthreads();
-    auto rel = [&](int64_t q) -> int32_t { return in_smem ? s_pos[q] : clamp_rel(off[lo_b + q]); };
-
-    // ---- per-thread items and their total
-    const int r0 = t * IT;
-    const int n = max(0, min(IT, ne - r0));
-    int4 raw[kVecPerThread];
-#pragma unroll
-    for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
-    const Tin* xs = reinterpret_cast<const Tin*>(raw);
-    uint64_t run = 0;
-    if (fast) {
-#pragma unroll
-        for (int i = 0; i < IT; ++i) run += (uint64_t)sq_wide(xs[i]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < IT; ++i)
-            if (i < n) run += gmap<Tin>(map_op, (int64_t)xs[i], sc);
-    }
-    // ---- CTA-wide exclusive scan of the thread totals
-    uint64_t inc = run;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += o;
-    }
-    if (lane == 31) s_wtot[warp] = inc;
-    __syncthreads();   // also: every thread has read its items from the staging buffer
-    uint64_t acc = inc - run;
-    for (int w = 0; w < warp; ++w) acc += s_wtot[w];
-    if (fast) {
-#pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            acc += (uint64_t)sq_wide(xs[i]);
-            s_P[i * kThreads + t] = acc;
+        const int64_t lo_b = s_lo[2 * (k % kLoRing)], hi_b = s_lo[2 * (k % kLoRing) + 1];
+        const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
+        const int64_t cnt = last - lo_b + 1;
+        if (cnt <= kOffCap) {
+            int64_t* od = stage_off(st);
+            for (int j = t; j < cnt; j += kThreads) cp_async8(od + j, off + lo_b + j);
         }
-    } else {
-#pragma unroll
-        for (int i = 0; i < IT; ++i)
-            if (i < n) { acc += gmap<Tin>(map_op, (int64_t)xs[i], sc); s_P[i * kThreads + t] = acc; }
-    }
-    __syncthreads();
-
-    // ---- owned segments: sum over [start, end) of the tile = P(end) - P(start), where
-    // P(p) = sum of g over the tile's positions < p
-    auto Pb = [&](int32_t p) -> uint64_t {
-        if (p <= 0) return 0ull;
-        const int k = p - 1;
-        const uint64_t v = s_P[(k % IT) * kThreads + k / IT];
-        return fast ? v + (uint64_t)p : v;
     };
-    const int64_t nown = hi_b - lo_b;
-    for (int64_t q = t; q < nown; q += kThreads) out[lo_b + q] = (Tout)(int64_t)(Pb(rel(q + 1)) - Pb(rel(q)));
-    // ---- the tile's open segment: segment hi_b if it starts at or before the last element
-    if (t == 0) {
-        const int32_t a = (hi_b < S) ? rel(nown) : ne;
-        if (a <= ne - 1) {
-            tail_seg[b] = hi_b;
-            tail_val[b] = (int64_t)(Pb(ne) - Pb(a));
+
+    // prologue: lo pairs of the first kStages - 1 tiles directly, then their copies (group g
+    // holds tile g and the lo pair of tile g + kStages - 1)
+    if (t == 0)
+        for (int64_t k = 0; k < kStages - 1 && k < mytiles; ++k) {
+            const int64_t b = c + k * grid;
+            s_lo[2 * (k % kLoRing)] = lo_arr[b];
+            s_lo[2 * (k % kLoRing) + 1] = lo_arr[b + 1];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kStages - 1; ++k) {
+        issue_lo(k + kStages - 1);
+        issue_tile(k);
+        cp_async_commit();
+    }
+
+    for (int64_t k = 0; k < mytiles; ++k) {
+        cp_async_wait<kStages - 2>();        // this thread's copies of tile k (group k) have landed
+        __syncthreads();                     // ... everyone's; and tile k - 1 is finished with
+        issue_lo(k + 2 * kStages - 2);
+        issue_tile(k + kStages - 1);
+        cp_async_commit();
+
+        const int st = (int)(k % kStages);
+        const int64_t b = c + k * grid;
+        const int64_t e0 = b * TE;
+        const int ne = (int)((e0 + TE < N) ? TE : N - e0);
+        const int64_t lo_b = s_lo[2 * (k % kLoRing)], hi_b = s_lo[2 * (k % kLoRing) + 1];
+        const bool fast = map_op == ACCEL_MAP_SQ_PLUS_ONE && ne == TE;
+        const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
+        const bool in_smem = last - lo_b + 1 <= kOffCap;
+        const int64_t* od = stage_off(st);
+        // segment start relative to the tile, clamped to [0, ne]
+        auto rel = [&](int64_t q) -> int32_t {
+            const int64_t r = (in_smem ? od[q] : off[lo_b + q]) - e0;
+            return (int32_t)(r < 0 ? 0 : (r > ne ? ne : r));
+        };
+
+        // ---- per-thread items and their total
+        const int r0 = t * IT;
+        const int n = max(0, min(IT, ne - r0));
+        int4 raw[kVecPerThread];
+        const int4* sd = stage_data(st);
+#pragma unroll
+        for (int r = 0; r < kVecPerThread; ++r) raw[r] = sd[swz(t * kVecPerThread + r)];
+        const Tin* xs = reinterpret_cast<const Tin*>(raw);
+        uint64_t run = 0;
+        if (fast) {
+#pragma unroll
+            for (int i = 0; i < IT; ++i) run += (uint64_t)sq_wide(xs[i]);
         } else {
-            tail_seg[b] = -1;
+#pragma unroll
+            for (int i = 0; i < IT; ++i)
+                if (i < n) run += gmap<Tin>(map_op, (int64_t)xs[i], sc);
+        }
+        // ---- CTA-wide exclusive scan of the thread totals
+        uint64_t inc = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (lane == 31) s_wtot[warp] = inc;
+        __syncthreads();
+        uint64_t acc = inc - run;
+        for (int w = 0; w < warp; ++w) acc += s_wtot[w];
+        if (fast) {
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                acc += (uint64_t)sq_wide(xs[i]);
+                s_P[i * kThreads + t] = acc;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < IT; ++i)
+                if (i < n) { acc += gmap<Tin>(map_op, (int64_t)xs[i], sc); s_P[i * kThreads + t] = acc; }
+        }
+        __syncthreads();
+
+        // ---- owned segments: sum over [start, end) of the tile = P(end) - P(start), where
+        // P(p) = sum of g over the tile's positions < p
+        auto Pb = [&](int32_t p) -> uint64_t {
+            if (p <= 0) return 0ull;
+            const int kk = p - 1;
+            const uint64_t v = s_P[(kk % IT) * kThreads + kk / IT];
+            return fast ? v + (uint64_t)p : v;
+        };
+        const int64_t nown = hi_b - lo_b;
+        for (int64_t q = t; q < nown; q += kThreads) out[lo_b + q] = (Tout)(int64_t)(Pb(rel(q + 1)) - Pb(rel(q)));
+        // ---- the tile's open segment: segment hi_b if it starts at or before the last element
+        if (t == 0) {
+            const int32_t a = (hi_b < S) ? rel(nown) : ne;
+            if (a <= ne - 1) {
+                tail_seg[b] = hi_b;
+                tail_val[b] = (int64_t)(Pb(ne) - Pb(a));
+            } else {
+                tail_seg[b] = -1;
+            }
         }
     }
+    cp_async_wait<0>();                      // the trailing (empty) groups
 }
 
 // Folds the carry-outs of the tiles preceding b into the first segment b owns, when that
@@ -454,7 +533,7 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
     Tout* out = (Tout*)d_out;
     if (N == 0) {
         Tout nel = 0;
-        ACCEL_DISPATCH_RED(op, OPC, (nel = (Tout)red_neutral<C>(OPC)));
+        ACCEL_DISPATCH_RED(op, OPC, (nel = red_neutral<Tout>(OPC)));
         int g = (int)((S + 255) / 256);
         if (g > 8 * num_sms()) g = 8 * num_sms();
         k_fill<Tout><<<g, 256, 0, st>>>(out, S, nel);
@@ -464,8 +543,13 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
     k_partition_scatter<<<(unsigned)((S + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);
     if constexpr (std::is_integral<C>::value) {
         if (op == ACCEL_RED_ADD) {
-            k_segsum<Tin, Tout><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
-                (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, (int64_t*)tval);
+            const size_t smem = segsum_smem_bytes<Tin>();
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_segsum<Tin, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem));
+            const int64_t cap = 2 * (int64_t)num_sms();
+            const unsigned grid = (unsigned)(L.ntiles < cap ? L.ntiles : cap);
+            k_segsum<Tin, Tout><<<grid, kThreads, smem, st>>>((const Tin*)d_data, N, d_off, S, lo, L.ntiles, map_op,
+                                                              scalar, out, tseg, (int64_t*)tval);
             k_fixup<Tout, ACCEL_RED_ADD><<<(unsigned)((L.ntiles + 255) / 256), 256, 0, st>>>(d_off, lo, L.ntiles, te,
                                                                                             tseg, tval, out);
             return after_launch(st, "accel_segreduce", 3);

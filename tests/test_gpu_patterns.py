@@ -50,6 +50,91 @@ def test_marshal_ragged_int64_and_many_sequences():
     assert np.array_equal(flat.cpu().numpy(), rf)
 
 
+@pytest.mark.parametrize("S", [16 * 1024, 16 * 1024 + 1, 40_000])
+def test_marshal_ragged_scan_paths(S):
+    # S <= 16,384 scans the lengths in one CTA, larger S in three passes; separate (not
+    # adjacent) host tables take two copies
+    seqs = synth.ragged_int32(S, S, 0, 9)
+    pieces = [_t(x) for x in seqs]
+    ptrs = torch.tensor([p.data_ptr() if p.numel() else 0 for p in pieces], dtype=torch.int64).pin_memory()
+    lens = torch.tensor([p.numel() for p in pieces], dtype=torch.int64).pin_memory()
+    lib = api.L.load()
+    total = int(lens.sum())
+    flat = torch.empty(total, dtype=torch.int32, device=DEV)
+    off = torch.empty(S + 1, dtype=torch.int64, device=DEV)
+    ws = torch.empty(lib.accel_marshal_ragged_workspace_size(S), dtype=torch.uint8, device=DEV)
+    import ctypes as C
+    api.L.check("accel_marshal_ragged", lib.accel_marshal_ragged(
+        C.c_void_p(ptrs.data_ptr()), C.c_void_p(lens.data_ptr()), S, api.L.I32, C.c_void_p(flat.data_ptr()),
+        C.c_void_p(off.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(),
+        C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    rf, ro = op.marshal_ragged(seqs)
+    assert np.array_equal(off.cpu().numpy(), ro)
+    assert np.array_equal(flat.cpu().numpy(), rf)
+
+
+def test_marshal_ragged_sweep_size_shuffled_pieces():
+    # 2^20 sequences (lengths U{0..256}, ~134M elements) whose pieces lie in one buffer in a
+    # shuffled order: the HBM-scale marshal the bench times, compared element by element
+    S = 1 << 20
+    data, lengths = synth.ragged_flat_int32(1, S)
+    perm = synth.rng(5).permutation(S)
+    start = np.zeros(S, np.int64)
+    start[perm] = np.concatenate([[0], np.cumsum(lengths[perm])[:-1]])
+    src = np.empty_like(data)
+    ref_off = np.zeros(S + 1, np.int64)
+    np.cumsum(lengths, out=ref_off[1:])
+    for_src = np.repeat(start - ref_off[:-1], lengths) + np.arange(len(data))   # source position of flat k
+    src[for_src] = data
+    d_src = _t(src)
+    table = api.RaggedTable.__new__(api.RaggedTable)
+    table.seqs, table.dtype, table.S = [d_src], torch.int32, S
+    tab = torch.from_numpy(np.concatenate([d_src.data_ptr() + 4 * start, lengths]).astype(np.int64)).pin_memory()
+    table.ptrs, table.lengths, table.total = tab[:S], tab[S:], int(lengths.sum())
+    flat, off = api.accel_marshal_ragged_table(table)
+    torch.cuda.synchronize()
+    assert np.array_equal(off.cpu().numpy(), ref_off)
+    assert np.array_equal(flat.cpu().numpy(), data)
+
+
+def test_seg_row_captured_as_one_graph_replays():
+    # marshal -> fused map + segmented sum -> max -> loop, captured once and replayed twice
+    c = synth.CFG_SEGREDUCE
+    seqs = synth.ragged_int32(c["seed"], c["S"], c["len_lo"], c["len_hi"], c["val_lo"], c["val_hi"])
+    table = api.ragged_table([_t(x) for x in seqs])
+    lib = api.L.load()
+    N, S = table.total, table.S
+    flat = torch.empty(N, dtype=torch.int32, device=DEV)
+    off = torch.empty(S + 1, dtype=torch.int64, device=DEV)
+    seg = torch.empty(S, dtype=torch.int64, device=DEV)
+    mx = torch.empty(1, dtype=torch.int64, device=DEV)
+    twice = torch.empty(N, dtype=torch.int32, device=DEV)
+    ws_m = torch.empty(lib.accel_marshal_ragged_workspace_size(S), dtype=torch.uint8, device=DEV)
+    ws_s = torch.empty(lib.accel_segreduce_workspace_size(N, S), dtype=torch.uint8, device=DEV)
+    ws_r = torch.empty(max(lib.accel_reduce_workspace_size(S, api.L.I64), 256), dtype=torch.uint8, device=DEV)
+
+    def body():
+        api.accel_marshal_ragged_table(table, out=(flat, off), ws=ws_m)
+        api.accel_segreduce(op.RED_ADD, op.MAP_SQ_PLUS_ONE, flat, off, torch.int64, out=seg, ws=ws_s)
+        api.accel_reduce(op.RED_MAX, seg, out=mx, ws=ws_r)
+        api.accel_loop(op.LOOP_SCALE, twice, flat, 2.0)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = api.Graph()
+    g.capture(body, stream=side)
+    rf, ro = op.marshal_ragged(seqs)
+    ref = op.segreduce_fast(op.RED_ADD, op.MAP_SQ_PLUS_ONE, rf, ro, np.int64)
+    for _ in range(2):
+        for t in (flat, seg, mx, twice):
+            t.fill_(-1)
+        torch.cuda.synchronize()
+        g.launch()
+        torch.cuda.synchronize()
+        assert np.array_equal(seg.cpu().numpy(), ref)
+        assert int(mx.item()) == int(ref.max())
+        assert np.array_equal(twice.cpu().numpy(), 2 * rf)
+
+
 def test_marshal_records_fast_path_and_inverse():
     b = synth.bodies(2, 1001)
     aos = _t(b["aos"])
@@ -149,11 +234,14 @@ def test_reduce_float(dt):
     assert api.accel_reduce(op.RED_MAX, _t(x)).item() == float(x.max())
 
 
-def test_reduce_empty_gives_neutral():
-    e = _t(np.zeros(0, np.int64))
-    assert api.accel_reduce(op.RED_ADD, e).item() == 0
-    assert api.accel_reduce(op.RED_MUL, e).item() == 1
-    assert api.accel_reduce(op.RED_MAX, e).item() == np.iinfo(np.int64).min
+@pytest.mark.parametrize("dt", [np.int64, np.int32])
+def test_reduce_empty_gives_neutral(dt):
+    # the neutral element of the result's own type (an int32 reduction runs in int64, but an
+    # empty one gives INT32_MIN / INT32_MAX, not a narrowed int64 value)
+    e = _t(np.zeros(0, dt))
+    for red in (op.RED_ADD, op.RED_MUL, op.RED_MIN, op.RED_MAX):
+        assert api.accel_reduce(red, e).item() == op.neutral(red, dt)
+    assert op.neutral(op.RED_MAX, dt) == np.iinfo(dt).min
 
 
 # ----------------------------------------------------------------------- segreduce
@@ -217,10 +305,22 @@ def test_segreduce_edge_cases(case):
         assert np.array_equal(got, ref)
 
 
-def test_segreduce_no_elements():
+@pytest.mark.parametrize("dout", [np.int64, np.int32])
+def test_segreduce_no_elements(dout):
     off = np.zeros(17, np.int64)
-    got = api.accel_segreduce(op.RED_MIN, op.MAP_IDENTITY, _t(np.zeros(0, np.int32)), _t(off), torch.int64)
-    assert np.array_equal(got.cpu().numpy(), np.full(16, np.iinfo(np.int64).max))
+    for red in (op.RED_MIN, op.RED_MAX, op.RED_MUL):
+        got = api.accel_segreduce(red, op.MAP_IDENTITY, _t(np.zeros(0, np.int32)), _t(off), TORCH_DT[dout])
+        assert np.array_equal(got.cpu().numpy(), np.full(16, op.neutral(red, dout), dtype=dout))
+
+
+@pytest.mark.parametrize("red", [op.RED_MIN, op.RED_MAX, op.RED_ADD])
+def test_segreduce_int32_output_with_empty_segments(red):
+    # an empty segment gives the int32 neutral element, at every position in a tile
+    data, off = _seg_case(40 + red, 3000, 0, 12)
+    got = api.accel_segreduce(red, op.MAP_IDENTITY, _t(data), _t(off), torch.int32).cpu().numpy()
+    ref = op.segreduce(red, op.MAP_IDENTITY, data, off, np.int32)
+    assert np.count_nonzero(np.diff(off) == 0) > 100
+    assert np.array_equal(got, ref)
 
 
 @pytest.mark.parametrize("dts", [(np.float32, np.float32), (np.float32, np.float64), (np.float64, np.float64),
