@@ -168,11 +168,13 @@ uint64_t accel_get_watchdog_ns(void);
  *  h_ptrs    host array of S element pointers; each points to device memory or to
  *            page-locked host memory mapped for the device (UVA); may be NULL where the
  *            length is 0.
- *  h_lengths host array of S lengths >= 0 (also read on the host, for checks).
- *            Both tables are copied to the device in stream order: a page-locked table is
- *            read when the stream reaches the copy, a pageable one before the call returns.
- *            The tables and the pieces must stay unchanged until the stream has executed
- *            the call.
+ *  h_lengths host array of S lengths >= 0 (read on the host too, for checks, in debug
+ *            mode only).  When both tables are page-locked (mapped) host memory the kernels
+ *            read them in place over the host link, when the stream reaches the call;
+ *            otherwise they are copied to the workspace in stream order (a pageable table is
+ *            staged before the call returns; pageable tables cannot be captured into a
+ *            CUDA graph).  The tables and the pieces must stay unchanged until the stream
+ *            has executed the call.
  *  dtype     element type of every sequence (4- or 8-byte).
  *  d_flat    device output, sum(lengths) elements; d_offsets device output, S+1 int64.
  *  d_ws      scratch of accel_marshal_ragged_workspace_size(S) bytes (pointer + length

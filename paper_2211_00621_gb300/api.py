@@ -113,7 +113,7 @@ class RaggedTable:
                 raise TypeError("all sequences must have the same dtype")
             if not s.is_cuda and s.numel() and not s.is_pinned():
                 raise ValueError("host sequences must be in pinned memory")
-        # one page-locked buffer [pointers | lengths]: the library copies adjacent tables at once
+        # one page-locked buffer [pointers | lengths], which the library's kernels read in place
         tab = torch.tensor([s.data_ptr() if s.numel() else 0 for s in self.seqs] +
                            [int(s.numel()) for s in self.seqs] or [0, 0], dtype=torch.int64).pin_memory()
         n = max(self.S, 1)

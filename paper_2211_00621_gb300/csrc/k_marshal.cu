@@ -42,12 +42,14 @@ __device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t* s_warp) {
     return v;
 }
 
-// pass 1: per-block totals of the lengths
+// pass 1: per-block totals of the lengths; `copy` (may be null) receives the lengths read
+// (when they are read from host memory, so the third pass reads them from the device)
 __global__ void __launch_bounds__(kScanThreads) k_scan_blocks(const int64_t* __restrict__ len, int64_t S,
-                                                               int64_t* __restrict__ bsum) {
+                                                               int64_t* __restrict__ bsum, int64_t* __restrict__ copy) {
     __shared__ int64_t s_warp[32];
     int64_t i = blockIdx.x * (int64_t)kScanThreads + threadIdx.x;
     int64_t v = i < S ? len[i] : 0;
+    if (copy && i < S) copy[i] = v;
     v = block_incl_scan(v, s_warp);
     if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = v;
 }
@@ -106,31 +108,57 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int64_t* __rest
 }
 
 // ---------------------------------------------------------------- ragged gather
-// One warp per sequence (grid-stride over sequences); each lane moves up to 8 elements
-// per round with all loads issued before the stores.
+// Each warp takes batches of SPB consecutive sequences (grid-stride over batches): lane l
+// loads the metadata of sequence b0 + l (offset, length, source pointer) with one coalesced
+// load per table -- the pointer table may be page-locked host memory read over the
+// chip-to-chip link -- then the warp copies the batch's sequences two at a time, the loads of
+// both (up to 8 elements per lane each) issued before any store, broadcasting the metadata
+// with shuffles.  SPB (1 .. 32) is chosen by the host so that there are enough batches to
+// fill the device.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gather(const T* const* __restrict__ ptrs, const int64_t* __restrict__ off,
-                                               int64_t S, T* __restrict__ flat) {
+__device__ __forceinline__ void gather_pair(const T* __restrict__ s0, T* __restrict__ d0, int64_t n0,
+                                            const T* __restrict__ s1, T* __restrict__ d1, int64_t n1, int lane) {
+    const int64_t n = n0 > n1 ? n0 : n1;
+    for (int64_t base = 0; base < n; base += 32 * 8) {
+        T v0[8], v1[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int64_t k = base + r * 32 + lane;
+            if (k < n0) v0[r] = s0[k];
+            if (k < n1) v1[r] = s1[k];
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int64_t k = base + r * 32 + lane;
+            if (k < n0) d0[k] = v0[r];
+            if (k < n1) d1[k] = v1[r];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_gather(const T* const* __restrict__ ptrs, const int64_t* __restrict__ off,
+                                               int64_t S, int spb, T* __restrict__ flat) {
     const int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t s = warp; s < S; s += nwarps) {
-        const int64_t o = off[s];
-        const int64_t n = off[s + 1] - o;
-        const T* src = ptrs[s];
-        T* dst = flat + o;
-        for (int64_t base = 0; base < n; base += 32 * 8) {
-            T v[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                int64_t k = base + r * 32 + lane;
-                if (k < n) v[r] = src[k];
-            }
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                int64_t k = base + r * 32 + lane;
-                if (k < n) dst[k] = v[r];
-            }
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b0 = warp * spb; b0 < S; b0 += nwarps * spb) {
+        const int cnt = (int)(S - b0 < spb ? S - b0 : spb);
+        int64_t mo = 0, mn = 0;
+        const T* ms = nullptr;
+        if (lane < cnt) {
+            mo = off[b0 + lane];
+            mn = off[b0 + lane + 1] - mo;
+            ms = ptrs[b0 + lane];
+        }
+        for (int j = 0; j < cnt; j += 2) {
+            const int64_t o0 = __shfl_sync(0xffffffffu, mo, j), n0 = __shfl_sync(0xffffffffu, mn, j);
+            const T* s0 = reinterpret_cast<const T*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(ms), j));
+            const int j1 = j + 1 < cnt ? j + 1 : j;
+            const int64_t o1 = __shfl_sync(0xffffffffu, mo, j1);
+            const int64_t n1 = j + 1 < cnt ? __shfl_sync(0xffffffffu, mn, j1) : 0;
+            const T* s1 = reinterpret_cast<const T*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(ms), j1));
+            gather_pair<T>(s0, flat + o0, n0, s1, flat + o1, n1, lane);
         }
     }
 }
@@ -169,8 +197,19 @@ static cudaError_t table_to_device(void* d_dst, const void* h_src, size_t bytes,
     return cudaMemcpyAsync(d_dst, h_src, bytes, cudaMemcpyHostToDevice, st);
 }
 
-// pointer table, then the length table right after it (so tables that are adjacent on the
-// host travel in one copy), then the scan's block totals
+// The device address of a page-locked (mapped) host table, or null for pageable memory,
+// which must be copied.
+static const void* mapped_host(const void* h) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// pointer table (copied there when the host tables are pageable), the length table (ditto,
+// or the scan's copy of page-locked lengths), then the scan's block totals
 size_t ws_layout(int64_t S, size_t* ptr_off, size_t* len_off, size_t* bsum_off) {
     int64_t nb = (S + kScanThreads - 1) / kScanThreads;
     *ptr_off = kStatusBytes;
@@ -263,34 +302,44 @@ accel_status accel_marshal_ragged(const void* const* h_ptrs, const int64_t* h_le
         return after_launch(st, "accel_marshal_ragged", 0);
     }
     char* ws = (char*)d_ws;
-    int64_t* d_len = (int64_t*)(ws + lo);
+    const int64_t* d_len = (int64_t*)(ws + lo);
     int64_t* d_bsum = (int64_t*)(ws + bo);
-    const void** d_ptrs = (const void**)(ws + po);
-    if ((const void*)h_lengths == (const void*)(h_ptrs + S)) {
-        // the length table follows the pointer table on the host: one copy
-        ACCEL_CUDA_TRY(table_to_device(d_ptrs, h_ptrs, (size_t)S * 16, st));
+    const void* const* d_ptrs = (const void* const*)(ws + po);
+    const void* dp = mapped_host(h_ptrs);
+    const void* dl = mapped_host(h_lengths);
+    if (dp && dl) {
+        // page-locked tables: the kernels read them in place over the host link (no copy)
+        d_ptrs = (const void* const*)dp;
+        d_len = (const int64_t*)dl;
     } else {
-        ACCEL_CUDA_TRY(table_to_device(d_ptrs, h_ptrs, (size_t)S * sizeof(void*), st));
-        ACCEL_CUDA_TRY(table_to_device(d_len, h_lengths, (size_t)S * sizeof(int64_t), st));
+        ACCEL_CUDA_TRY(table_to_device(ws + po, h_ptrs, (size_t)S * sizeof(void*), st));
+        ACCEL_CUDA_TRY(table_to_device(ws + lo, h_lengths, (size_t)S * sizeof(int64_t), st));
     }
     int64_t nb = (S + kScanThreads - 1) / kScanThreads;
     int nscan = 1;
     if (S <= kScanSmall) {
         k_scan_one<<<1, kScanThreads, 0, st>>>(d_len, S, d_offsets);
     } else {
-        k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum);
+        int64_t* dev_len = (int64_t*)(ws + lo);
+        k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum, d_len != dev_len ? dev_len : nullptr);
         k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
-        k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, S, d_bsum, d_offsets);
+        k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(dev_len, S, d_bsum, d_offsets);
         nscan = 3;
     }
-    int64_t warps_needed = S;
-    int64_t blocks = (warps_needed + 7) / 8;
+    // sequences per warp batch: as many as keep every warp slot of the device busy (8 CTAs of
+    // 8 warps per SM), at most 32
+    const int64_t slots = (int64_t)num_sms() * 64;
+    int spb = 1;
+    while (spb < 32 && S / (2 * spb) >= slots) spb *= 2;
+    int64_t blocks = ((S + spb - 1) / spb + 7) / 8;
     int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
     if (dtype_size(dtype) == 4)
-        k_gather<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t* const*)d_ptrs, d_offsets, S, (int32_t*)d_flat);
+        k_gather<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t* const*)d_ptrs, d_offsets, S, spb,
+                                                            (int32_t*)d_flat);
     else
-        k_gather<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t* const*)d_ptrs, d_offsets, S, (int64_t*)d_flat);
+        k_gather<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t* const*)d_ptrs, d_offsets, S, spb,
+                                                            (int64_t*)d_flat);
     return after_launch(st, "accel_marshal_ragged", nscan + 1);
 }
 
@@ -307,7 +356,7 @@ static accel_status scan_lengths(const int64_t* h_len, int64_t n, int64_t* d_off
         return ACCEL_OK;
     }
     int64_t nb = (n + kScanThreads - 1) / kScanThreads;
-    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, n, d_bsum);
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, n, d_bsum, nullptr);
     k_scan_totals<<<1, kScanThreads, 0, st>>>(d_bsum, nb);
     k_scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(d_len, n, d_bsum, d_off);
     count_launches(3);

@@ -50,14 +50,17 @@ def test_marshal_ragged_int64_and_many_sequences():
     assert np.array_equal(flat.cpu().numpy(), rf)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("S", [16 * 1024, 16 * 1024 + 1, 40_000])
-def test_marshal_ragged_scan_paths(S):
-    # S <= 16,384 scans the lengths in one CTA, larger S in three passes; separate (not
-    # adjacent) host tables take two copies
+def test_marshal_ragged_scan_paths(S, pinned):
+    # S <= 16,384 scans the lengths in one CTA, larger S in three passes; page-locked host
+    # tables are read in place by the kernels, pageable ones are copied to the workspace first
     seqs = synth.ragged_int32(S, S, 0, 9)
     pieces = [_t(x) for x in seqs]
-    ptrs = torch.tensor([p.data_ptr() if p.numel() else 0 for p in pieces], dtype=torch.int64).pin_memory()
-    lens = torch.tensor([p.numel() for p in pieces], dtype=torch.int64).pin_memory()
+    ptrs = torch.tensor([p.data_ptr() if p.numel() else 0 for p in pieces], dtype=torch.int64)
+    lens = torch.tensor([p.numel() for p in pieces], dtype=torch.int64)
+    if pinned:
+        ptrs, lens = ptrs.pin_memory(), lens.pin_memory()
     lib = api.L.load()
     total = int(lens.sum())
     flat = torch.empty(total, dtype=torch.int32, device=DEV)
