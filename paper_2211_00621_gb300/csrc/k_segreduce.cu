@@ -270,51 +270,16 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
     }
 }
 
-// Integer sums: a branch-free variant with few instructions per element.  Each thread sums
-// the mapped values of its IT contiguous items (one widening multiply-add per element for
-// the map x*x + 1, whose +1 per element is added as a count), a CTA-wide scan of the thread
-// totals gives every thread's exclusive prefix, and an owned segment's sum is P(end) -
-// P(start) with P(p) the sum of the tile's mapped values before position p.  P is formed
-// only where a segment starts or ends: the prefix of the thread holding position p plus the
-// at most IT - 1 items of that thread before p, read back from the staged tile.  Wrapping
-// 64-bit addition forms a group, so the differences are exact whatever the magnitudes.  The
-// tile's open segment (if its last element does not end a segment) is handed to the fixup
-// kernel.
-//
-// The kernel is persistent (three CTAs per SM, each taking every gridDim-th tile) and keeps
-// its next tiles in flight while it works on the current one: a ring of kStages shared
-// buffers is filled by asynchronous global->shared copies (cp.async, 16 bytes per thread,
-// written in the swizzled order the threads read), each tile's copies forming one commit
-// group.  A tile's offsets chunk can only be fetched once its segment range [lo[b], lo[b+1])
-// is known, so the lo pairs travel one pipeline depth further ahead, through a small ring
-// of their own: the group that carries tile k's data also carries tile k + kStages - 1's lo
-// pair.  So kStages - 1 tiles (16 KB each) are in flight per CTA at every step.
-constexpr int kStages = 3;
-constexpr int kLoRing = 8;                                   // >= 2 kStages - 1
-constexpr int kOffChunk = 512;                               // offsets staged per tile
-constexpr size_t kStageBytes = kTileBytes + (size_t)kOffChunk * 8;   // data tile + offsets chunk
-
-constexpr size_t segsum_smem_bytes() {
-    return kStages * kStageBytes + (size_t)kThreads * 8 + 2 * kLoRing * 8 + (kThreads / 32) * 8;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// 16-byte asynchronous copy; bytes past src_bytes (0..16) are zero-filled and not read
-__device__ __forceinline__ void cp_async16(void* s, const void* g, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(s)), "l"(g), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16_full(void* s, const void* g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* s, const void* g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
+// Integer sums: a branch-free variant with few instructions per element.  The tile's mapped
+// values are prefix-summed across the CTA (each thread scans its IT contiguous items, a
+// CTA-wide scan adds the thread offsets) into shared memory, and every owned segment's sum
+// is P[end-1] - P[start-1].  Wrapping 64-bit addition forms a group, so the differences are
+// exact whatever the magnitudes; every thread does the same work whatever the segment
+// lengths.  For the common map x*x + 1 on a full tile, P' = prefix of x*x is formed with one
+// widening multiply-add per element and P[k] = P'[k] + k + 1 is applied at lookup.  The
+// prefix array is item-major (item i of thread t at i * kThreads + t), so the stores are
+// conflict-free with constant offsets.  The tile's open segment (if its last element does
+// not end a segment) is handed to the fixup kernel.
 template <typename Tin>
 __device__ __forceinline__ uint64_t gmap(int map_op, int64_t x, int64_t sc) {
     switch (map_op) {
@@ -327,174 +292,112 @@ __device__ __forceinline__ uint64_t gmap(int map_op, int64_t x, int64_t sc) {
 }
 
 template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads)
 k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
-         const int64_t* __restrict__ lo_arr, int64_t ntiles, int map_op, double scalar, Tout* __restrict__ out,
+         const int64_t* __restrict__ lo_arr, int map_op, double scalar, Tout* __restrict__ out,
          int64_t* __restrict__ tail_seg, int64_t* __restrict__ tail_val) {
     constexpr int IT = items<Tin>();
     constexpr int TE = tile_elems<Tin>();
     constexpr int PV = 16 / (int)sizeof(Tin);
-    extern __shared__ __align__(16) char smem[];
-    uint64_t* s_tpre = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);   // thread prefixes
-    int64_t* s_lo = reinterpret_cast<int64_t*>(s_tpre + kThreads);                   // [kLoRing][2]
-    uint64_t* s_wtot = reinterpret_cast<uint64_t*>(s_lo + 2 * kLoRing);
+    // the staged tile and, once every thread holds its items, the prefix sums share storage
+    __shared__ __align__(16) uint64_t s_buf[TE];
+    int4* s_data = reinterpret_cast<int4*>(s_buf);  // kVecs 16-byte vectors (16 KB)
+    uint64_t* s_P = s_buf;                          // prefix of the mapped values, item-major
+    __shared__ int32_t s_pos[kOffCap];
+    __shared__ uint64_t s_wtot[kThreads / 32];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t grid = gridDim.x, c = blockIdx.x;
-    const int64_t mytiles = c < ntiles ? (ntiles - 1 - c) / grid + 1 : 0;
+    const int64_t b = blockIdx.x;
+    const int64_t e0 = b * TE;
+    const int ne = (int)((e0 + TE < N) ? TE : N - e0);
+    const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
     const int64_t sc = (int64_t)scalar;
-    auto stage_data = [&](int st) { return reinterpret_cast<int4*>(smem + (size_t)st * kStageBytes); };
-    auto stage_off = [&](int st) { return reinterpret_cast<int64_t*>(smem + (size_t)st * kStageBytes + kTileBytes); };
+    const bool fast = map_op == ACCEL_MAP_SQ_PLUS_ONE && ne == TE;
 
-    // the lo pair of this CTA's k-th tile into its ring slot (thread 0)
-    auto issue_lo = [&](int64_t k) {
-        if (t == 0 && k < mytiles) {
-            const int64_t b = c + k * grid;
-            int64_t* d = s_lo + 2 * (k % kLoRing);
-            cp_async8(d, lo_arr + b);
-            cp_async8(d + 1, lo_arr + b + 1);
-        }
-    };
-    // the data tile and the offsets chunk of this CTA's k-th tile (its lo pair has arrived)
-    auto issue_tile = [&](int64_t k) {
-        if (k >= mytiles) return;
-        const int st = (int)(k % kStages);
-        const int64_t b = c + k * grid;
-        const int64_t e0 = b * TE;
-        const char* src = reinterpret_cast<const char*>(data + e0);
-        int4* dst = stage_data(st);
-        if (e0 + TE <= N) {
+    if (ne == TE) {
+        const int4* src = reinterpret_cast<const int4*>(data + e0);
 #pragma unroll
-            for (int r = 0; r < kVecPerThread; ++r) {
-                const int v = r * kThreads + t;
-                cp_async16_full(dst + swz(v), src + 16 * v);
-            }
-        } else {
-            const int64_t nbytes = (N - e0) * (int64_t)sizeof(Tin);
-#pragma unroll
-            for (int r = 0; r < kVecPerThread; ++r) {
-                const int v = r * kThreads + t;
-                const int64_t rem = nbytes - 16 * (int64_t)v;
-                const uint32_t sb = rem >= 16 ? 16u : (rem > 0 ? (uint32_t)rem : 0u);
-                cp_async16(dst + swz(v), sb ? src + 16 * (int64_t)v : reinterpret_cast<const char*>(data), sb);
-            }
+        for (int r = 0; r < kVecPerThread; ++r) {
+            int v = r * kThreads + t;
+            s_data[swz(v)] = __ldg(src + v);
         }
-        const int64_t lo_b = s_lo[2 * (k % kLoRing)], hi_b = s_lo[2 * (k % kLoRing) + 1];
-        const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
-        const int64_t cnt = last - lo_b + 1;
-        if (cnt <= kOffChunk) {
-            int64_t* od = stage_off(st);
-            for (int j = t; j < cnt; j += kThreads) cp_async8(od + j, off + lo_b + j);
-        }
+    } else {
+        Tin* sd = reinterpret_cast<Tin*>(s_data);
+        for (int e = t; e < TE; e += kThreads) sd[swz(e / PV) * PV + e % PV] = e < ne ? data[e0 + e] : Tin(0);
+    }
+    const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
+    const int64_t cnt = last - lo_b + 1;
+    const bool in_smem = cnt <= kOffCap;
+    // segment start relative to the tile, clamped to [0, ne]
+    auto clamp_rel = [&](int64_t x) -> int32_t {
+        const int64_t r = x - e0;
+        return (int32_t)(r < 0 ? 0 : (r > ne ? ne : r));
     };
-
-    // prologue: lo pairs of the first kStages - 1 tiles directly, then their copies (group g
-    // holds tile g and the lo pair of tile g + kStages - 1)
-    if (t == 0)
-        for (int64_t k = 0; k < kStages - 1 && k < mytiles; ++k) {
-            const int64_t b = c + k * grid;
-            s_lo[2 * (k % kLoRing)] = lo_arr[b];
-            s_lo[2 * (k % kLoRing) + 1] = lo_arr[b + 1];
-        }
+    if (in_smem)
+        for (int i = t; i < cnt; i += kThreads) s_pos[i] = clamp_rel(off[lo_b + i]);
     __syncthreads();
+    auto rel = [&](int64_t q) -> int32_t { return in_smem ? s_pos[q] : clamp_rel(off[lo_b + q]); };
+
+    // ---- per-thread items and their total
+    const int r0 = t * IT;
+    const int n = max(0, min(IT, ne - r0));
+    int4 raw[kVecPerThread];
 #pragma unroll
-    for (int k = 0; k < kStages - 1; ++k) {
-        issue_lo(k + kStages - 1);
-        issue_tile(k);
-        cp_async_commit();
+    for (int r = 0; r < kVecPerThread; ++r) raw[r] = s_data[swz(t * kVecPerThread + r)];
+    const Tin* xs = reinterpret_cast<const Tin*>(raw);
+    uint64_t run = 0;
+    if (fast) {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) run += (uint64_t)sq_wide(xs[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < IT; ++i)
+            if (i < n) run += gmap<Tin>(map_op, (int64_t)xs[i], sc);
     }
-
-    for (int64_t k = 0; k < mytiles; ++k) {
-        cp_async_wait<kStages - 2>();        // this thread's copies of tile k (group k) have landed
-        __syncthreads();                     // ... everyone's; and tile k - 1 is finished with
-        issue_lo(k + 2 * kStages - 2);
-        issue_tile(k + kStages - 1);
-        cp_async_commit();
-
-        const int st = (int)(k % kStages);
-        const int64_t b = c + k * grid;
-        const int64_t e0 = b * TE;
-        const int ne = (int)((e0 + TE < N) ? TE : N - e0);
-        const int64_t lo_b = s_lo[2 * (k % kLoRing)], hi_b = s_lo[2 * (k % kLoRing) + 1];
-        const bool fast = map_op == ACCEL_MAP_SQ_PLUS_ONE && ne == TE;
-        const int64_t last = (hi_b + 1 < S) ? hi_b + 1 : S;
-        const bool in_smem = last - lo_b + 1 <= kOffChunk;
-        const int64_t* od = stage_off(st);
-        const Tin* sd = reinterpret_cast<const Tin*>(stage_data(st));
-        // segment start relative to the tile, clamped to [0, ne]
-        auto rel = [&](int64_t q) -> int32_t {
-            const int64_t r = (in_smem ? od[q] : off[lo_b + q]) - e0;
-            return (int32_t)(r < 0 ? 0 : (r > ne ? ne : r));
-        };
-        auto item = [&](int kk) -> Tin { return sd[swz(kk / PV) * PV + kk % PV]; };
-
-        // ---- per-thread total of the mapped items
-        const int r0 = t * IT;
-        const int n = max(0, min(IT, ne - r0));
-        uint64_t run = 0;
-        {
-            int4 raw[kVecPerThread];
+    // ---- CTA-wide exclusive scan of the thread totals
+    uint64_t inc = run;
 #pragma unroll
-            for (int r = 0; r < kVecPerThread; ++r) raw[r] = stage_data(st)[swz(t * kVecPerThread + r)];
-            const Tin* xs = reinterpret_cast<const Tin*>(raw);
-            if (fast) {
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) s_wtot[warp] = inc;
+    __syncthreads();   // also: every thread has read its items from the staging buffer
+    uint64_t acc = inc - run;
+    for (int w = 0; w < warp; ++w) acc += s_wtot[w];
+    if (fast) {
 #pragma unroll
-                for (int i = 0; i < IT; ++i) run += (uint64_t)sq_wide(xs[i]);
-                run += (uint64_t)IT;
-            } else {
-#pragma unroll
-                for (int i = 0; i < IT; ++i)
-                    if (i < n) run += gmap<Tin>(map_op, (int64_t)xs[i], sc);
-            }
+        for (int i = 0; i < IT; ++i) {
+            acc += (uint64_t)sq_wide(xs[i]);
+            s_P[i * kThreads + t] = acc;
         }
-        // ---- CTA-wide exclusive scan of the thread totals
-        uint64_t inc = run;
+    } else {
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += o;
-        }
-        if (lane == 31) s_wtot[warp] = inc;
-        __syncthreads();
-        uint64_t pre = inc - run, total = 0;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const uint64_t x = s_wtot[w];
-            pre += w < warp ? x : 0ull;
-            total += x;
-        }
-        s_tpre[t] = pre;
-        __syncthreads();
+        for (int i = 0; i < IT; ++i)
+            if (i < n) { acc += gmap<Tin>(map_op, (int64_t)xs[i], sc); s_P[i * kThreads + t] = acc; }
+    }
+    __syncthreads();
 
-        // ---- owned segments: sum over [start, end) of the tile = P(end) - P(start), where
-        // P(p) = sum of g over the tile's positions < p
-        auto P = [&](int32_t p) -> uint64_t {
-            if (p <= 0) return 0ull;
-            if (p >= ne) return total;
-            const int th = p / IT, k0 = th * IT;
-            uint64_t v = s_tpre[th];
-            if (fast) {
-                v += (uint64_t)(p - k0);
-                for (int kk = k0; kk < p; ++kk) v += (uint64_t)sq_wide(item(kk));
-            } else {
-                for (int kk = k0; kk < p; ++kk) v += gmap<Tin>(map_op, (int64_t)item(kk), sc);
-            }
-            return v;
-        };
-        const int64_t nown = hi_b - lo_b;
-        for (int64_t q = t; q < nown; q += kThreads) out[lo_b + q] = (Tout)(int64_t)(P(rel(q + 1)) - P(rel(q)));
-        // ---- the tile's open segment: segment hi_b if it starts at or before the last element
-        if (t == kThreads - 1) {
-            const int32_t a = (hi_b < S) ? rel(nown) : ne;
-            if (a <= ne - 1) {
-                tail_seg[b] = hi_b;
-                tail_val[b] = (int64_t)(total - P(a));
-            } else {
-                tail_seg[b] = -1;
-            }
+    // ---- owned segments: sum over [start, end) of the tile = P(end) - P(start), where
+    // P(p) = sum of g over the tile's positions < p
+    auto Pb = [&](int32_t p) -> uint64_t {
+        if (p <= 0) return 0ull;
+        const int k = p - 1;
+        const uint64_t v = s_P[(k % IT) * kThreads + k / IT];
+        return fast ? v + (uint64_t)p : v;
+    };
+    const int64_t nown = hi_b - lo_b;
+    for (int64_t q = t; q < nown; q += kThreads) out[lo_b + q] = (Tout)(int64_t)(Pb(rel(q + 1)) - Pb(rel(q)));
+    // ---- the tile's open segment: segment hi_b if it starts at or before the last element
+    if (t == 0) {
+        const int32_t a = (hi_b < S) ? rel(nown) : ne;
+        if (a <= ne - 1) {
+            tail_seg[b] = hi_b;
+            tail_val[b] = (int64_t)(Pb(ne) - Pb(a));
+        } else {
+            tail_seg[b] = -1;
         }
     }
-    cp_async_wait<0>();                      // the trailing (empty) groups
 }
 
 // Folds the carry-outs of the tiles preceding b into the first segment b owns, when that
@@ -562,13 +465,8 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
     k_partition_scatter<<<(unsigned)((S + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);
     if constexpr (std::is_integral<C>::value) {
         if (op == ACCEL_RED_ADD) {
-            const size_t smem = segsum_smem_bytes();
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_segsum<Tin, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem));
-            const int64_t cap = 3 * (int64_t)num_sms();
-            const unsigned grid = (unsigned)(L.ntiles < cap ? L.ntiles : cap);
-            k_segsum<Tin, Tout><<<grid, kThreads, smem, st>>>((const Tin*)d_data, N, d_off, S, lo, L.ntiles, map_op,
-                                                              scalar, out, tseg, (int64_t*)tval);
+            k_segsum<Tin, Tout><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
+                (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, (int64_t*)tval);
             k_fixup<Tout, ACCEL_RED_ADD><<<(unsigned)((L.ntiles + 255) / 256), 256, 0, st>>>(d_off, lo, L.ntiles, te,
                                                                                             tseg, tval, out);
             return after_launch(st, "accel_segreduce", 3);
