@@ -428,7 +428,7 @@ accel_status hmm_mstep(const accel_hmm_model* m, const float* d_grad_log_A, cons
 /*
  * hmm_autotune -- choose the launch configuration of the BF16 tensor-core forward (column
  * parts per row: 8 or 16 warps; sequence rows per tile: 128, 64 or 32; a tile on one CTA or
- * on a cluster of two CTAs that split the state columns) by timing each
+ * on a cluster of two or four CTAs that split the state columns) by timing each
  * candidate with CUDA events on these inputs, and remember the fastest for (device, K, M,
  * floor(log2 S)); hmm_forward then launches with it.  `cache_path` (may be NULL) names a
  * file of JSON lines: an entry for the same key is reused without timing, a new result is
@@ -441,7 +441,8 @@ accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int
                           void* d_ws, size_t ws_bytes, const char* cache_path, float* h_best_ms,
                           void* stream);
 /* The configuration hmm_forward(ACCEL_HMM_BF16_SCALED) uses for these sizes: column parts
- * per row, rows per tile, and (h_pair, may be NULL) 1 when a tile runs on a CTA pair. */
+ * per row, rows per tile, and (h_pair, may be NULL) how a tile is split over a thread-block
+ * cluster: 0 one CTA, 1 two CTAs, 2 four CTAs (each holding K/2 or K/4 state columns). */
 accel_status hmm_tuned_config(int32_t K, int32_t M, int64_t S, int32_t* h_split, int32_t* h_rows,
                               int32_t* h_pair);
 

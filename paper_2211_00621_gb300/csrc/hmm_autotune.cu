@@ -1,6 +1,6 @@
 // Autotuner for the BF16 tensor-core HMM forward: picks the launch configuration (column
 // parts per row: 8 or 16 warps; sequence rows per tile: 128, 64 or 32; one CTA per tile or a
-// cluster pair splitting the state columns) by timing every candidate on the caller's inputs
+// cluster of two or four CTAs splitting the state columns) by timing every candidate on the caller's inputs
 // with CUDA events, and remembers the winner per
 // (device, K, M, floor(log2 S)) -- in this process, and optionally in a cache file of JSON
 // lines so later processes skip the timing:
@@ -59,7 +59,7 @@ bool load_from_cache(const char* path, const Key& key, TcConfig* out) {
                        kern, dev, &K, &M, &sl, &split, &rows, &pair, &ms);
         if (n != 9 || strcmp(kern, "hmm_forward_bf16") != 0) continue;
         if (Key(dev, K, M, sl) == key) {
-            *out = TcConfig{split, rows, pair ? 1 : 0};
+            *out = TcConfig{split, rows, pair < 0 ? 0 : (pair > 2 ? 2 : pair)};
             found = true;   // the last matching line wins
         }
     }
@@ -119,12 +119,12 @@ accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int
     cudaStream_t st = as_stream(stream);
     char* ws = (char*)d_ws;
     std::vector<TcConfig> cands;
-    for (int pair : {0, 1})
+    for (int pair : {0, 1, 2})
         for (int split : {4, 2})
             for (int rows : {128, 64, 32}) {
                 if (split == 4 && (m->K / 4) % 32 != 0) continue;
                 if (rows < 128 && (S + rows - 1) / rows <= (S + 127) / 128) continue;   // no more tiles than 128 rows
-                if (pair && !tc_pair_supported(m->K, m->M, rows, split)) continue;
+                if (pair && !tc_cl_supported(m->K, m->M, rows, split, pair == 1 ? 2 : 4)) continue;
                 cands.push_back(TcConfig{split, rows, pair});
             }
     cudaEvent_t e0, e1;

@@ -25,13 +25,14 @@ accel_status plain_forward(const accel_hmm_model* m, const int32_t* obs, const i
 // Launch configuration of the BF16 tensor-core forward, chosen by the autotuner
 // (hmm_autotune.cu): column parts per row (2: 8 warps, 4: 16 warps), sequence rows used per
 // tile (<= 128; fewer rows spread the sequences over more SMs), and whether a tile runs on
-// one CTA or on a cluster of two that split the state columns (pair = 1).
+// one CTA (pair = 0) or on a cluster that splits the state columns: two CTAs (pair = 1) or
+// four (pair = 2).
 struct TcConfig {
     int split;
     int rows;
     int pair;
 };
-bool tc_pair_supported(int K, int M, int rows, int split);
+bool tc_cl_supported(int K, int M, int rows, int split, int nc);
 TcConfig tuned_config(int K, int M, int64_t S);
 
 // BF16 tensor-core scaled forward (k_hmm_tc.cu).

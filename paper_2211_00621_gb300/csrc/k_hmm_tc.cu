@@ -390,18 +390,19 @@ struct PairLayout {
     uint32_t s_at, s_x, x_bytes, s_e, s_rowinfo, s_psum, s_mail, s_bar, s_slot, smem_bytes;
 };
 
-static PairLayout pair_layout(int K, int M, int MT, int NSPLIT) {
+// NC = CTAs of the cluster (2 or 4); each holds KC = K / NC state columns.
+static PairLayout pair_layout(int K, int M, int MT, int NSPLIT, int NC) {
     PairLayout L;
-    const uint32_t KC = (uint32_t)K / 2;
+    const uint32_t KC = (uint32_t)(K / NC);
     uint32_t o = 0;
-    L.s_at = o; o += KC * (uint32_t)K * 2;                 // this CTA's half of A^T (N = K/2 rows)
+    L.s_at = o; o += KC * (uint32_t)K * 2;                 // this CTA's part of A^T (N = K/NC rows)
     L.x_bytes = (uint32_t)MT * (uint32_t)K * 2;
     L.s_x = o;  o += 2 * L.x_bytes;                        // X, one buffer per step parity
-    L.s_e = o;  o += (uint32_t)M * KC * 2;                 // emission columns of this half
+    L.s_e = o;  o += (uint32_t)M * KC * 2;                 // emission columns of this part
     o = (o + 15) & ~15u;
     L.s_rowinfo = o; o += (uint32_t)MT * (uint32_t)sizeof(RowInfo);
-    L.s_psum = o; o += 2 * 2 * (uint32_t)NSPLIT * (uint32_t)MT * 4;   // [parity][cta][part][row]
-    L.s_mail = o; o += 2 * (uint32_t)MT * 4;                          // [parity][row] popped index
+    L.s_psum = o; o += 2 * (uint32_t)NC * (uint32_t)NSPLIT * (uint32_t)MT * 4;   // [parity][cta][part][row]
+    L.s_mail = o; o += 2 * (uint32_t)MT * 4;                                     // [parity][row] popped index
     o = (o + 7) & ~7u;
     L.s_bar = o; o += 3 * 8;                                          // MMA, exchange x 2 parities
     L.s_slot = o; o += 8;
@@ -409,15 +410,17 @@ static PairLayout pair_layout(int K, int M, int MT, int NSPLIT) {
     return L;
 }
 
-bool tc_pair_supported(int K, int M, int rows, int split) {
-    if (K < 128 || K > 256 || K % 64 != 0 || M < 1 || M > 32767 || (split != 2 && split != 4)) return false;
-    if ((K / 2 / split) % 32 != 0) return false;
+bool tc_cl_supported(int K, int M, int rows, int split, int nc) {
+    if (nc != 2 && nc != 4) return false;
+    if (K < 64 * nc || K > 256 || K % 64 != 0 || M < 1 || M > 32767 || (split != 2 && split != 4)) return false;
+    if ((K / nc / split) % 32 != 0) return false;
     const int MT = rows <= 64 ? 64 : 128;
-    return (int)pair_layout(K, M, MT, split).smem_bytes <= max_smem_optin();
+    return (int)pair_layout(K, M, MT, split, nc).smem_bytes <= max_smem_optin();
 }
 
-template <int NSPLIT, int MT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128 * NSPLIT, 1)
+// Launched with a cluster of NC CTAs (cudaLaunchKernelEx, cluster-dimension attribute).
+template <int NSPLIT, int MT, int NC>
+__global__ void __launch_bounds__(128 * NSPLIT, 1)
 k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restrict__ g_etab,
               const float* __restrict__ log_pi, const int32_t* __restrict__ obs, const int64_t* __restrict__ off,
               int64_t S, const int32_t* __restrict__ order, unsigned long long* __restrict__ next, int rows_active,
@@ -425,8 +428,8 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     extern __shared__ __align__(1024) char smem[];
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank(), peer = rank ^ 1;
-    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+    const int rank = (int)cl.block_rank();
+    const int cid = (int)(blockIdx.x / NC), ncl = (int)(gridDim.x / NC);
     char* sAT = smem + L.s_at;
     char* sX = smem + L.s_x;
     char* sE = smem + L.s_e;
@@ -444,7 +447,7 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     constexpr bool HL = MT == 64;
     const int hsel = HL ? lane >> 4 : 0;
     const int row = HL ? 16 * quarter + (lane & 15) : 32 * quarter + lane;
-    const int KC = K / 2;                         // columns of this CTA
+    const int KC = K / NC;                        // columns of this CTA
     const int KH = KC / NSPLIT;                   // columns per part
     const int CPT = HL ? KH / 2 : KH;             // columns per thread
     const int l0 = part * KH;                     // first column of the part, within the half
@@ -486,14 +489,20 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     const uint32_t idesc = tc::idesc_bf16_f32(MT, KC);
     const uint32_t sx_addr = tc::smem_u32(sX), sat_addr = tc::smem_u32(sAT);
     const uint32_t sbo = 16u * (uint32_t)K;
-    const uint32_t rx = tc::cluster_addr(sX, (uint32_t)peer);
-    const uint32_t rpsum = tc::cluster_addr(psum, (uint32_t)peer);
-    const uint32_t rmail = tc::cluster_addr(mail, (uint32_t)peer);
-    const uint32_t rbar0 = tc::cluster_addr(&bar[1], (uint32_t)peer);
-    const uint32_t rbar1 = tc::cluster_addr(&bar[2], (uint32_t)peer);
-    // bytes a CTA receives per step: the peer's half of X, its partial sums, and (CTA 1) the
-    // popped indices
-    const uint32_t xbytes = (uint32_t)(MT * KC * 2 + MT * NSPLIT * 4 + (rank == 1 ? MT * 4 : 0));
+    // the other CTAs of the cluster, d = 1 .. NC-1: CTA (rank + d) % NC
+    uint32_t rx[NC - 1], rpsum[NC - 1], rmail[NC - 1], rbar0[NC - 1], rbar1[NC - 1];
+#pragma unroll
+    for (int d = 1; d < NC; ++d) {
+        const uint32_t pr = (uint32_t)((rank + d) % NC);
+        rx[d - 1] = tc::cluster_addr(sX, pr);
+        rpsum[d - 1] = tc::cluster_addr(psum, pr);
+        rmail[d - 1] = tc::cluster_addr(mail, pr);
+        rbar0[d - 1] = tc::cluster_addr(&bar[1], pr);
+        rbar1[d - 1] = tc::cluster_addr(&bar[2], pr);
+    }
+    // bytes a CTA receives per step: the other CTAs' parts of X and partial sums, and (CTAs
+    // other than 0) the indices CTA 0 popped
+    const uint32_t xbytes = (uint32_t)((NC - 1) * (MT * KC * 2 + MT * NSPLIT * 4) + (rank != 0 ? MT * 4 : 0));
 
     const bool owner = part == 0 && hsel == 0;
     int64_t seq = -1, T = 0, pos = 0, E = 0;     // seq: -1 none, -2 waiting for CTA 0's index
@@ -519,7 +528,7 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     };
     // columns [jc, jc+16) of this half: X = a o bs packed to BF16 into the buffer at xo of both
     // CTAs; returns their sum (a fixed pairwise tree)
-    auto epi16 = [&](const float* a, const float (&bs)[16], int jc, uint32_t xo, uint32_t rb) -> float {
+    auto epi16 = [&](const float* a, const float (&bs)[16], int jc, uint32_t xo, const uint32_t (&rb)[NC - 1]) -> float {
         float part4[4];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -533,7 +542,8 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
             pk.w = pack_bf16(v[6], v[7]);
             const uint32_t co = xo + canon_off(row, rank * KC + jc + 8 * u, K);
             *reinterpret_cast<uint4*>(sX + co) = pk;
-            tc::st_async_u4(rx + co, pk, rb);
+#pragma unroll
+            for (int d = 0; d < NC - 1; ++d) tc::st_async_u4(rx[d] + co, pk, rb[d]);
             part4[2 * u] = (v[0] + v[1]) + (v[2] + v[3]);
             part4[2 * u + 1] = (v[4] + v[5]) + (v[6] + v[7]);
         }
@@ -577,7 +587,7 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
         }
         xph ^= 1u << q;
     };
-    const int ks_own = rank * (KC / 16), ks_peer = (rank ^ 1) * (KC / 16);
+    const int ks_own = rank * (KC / 16);
     // descriptors of k-step 0 of X buffer 0 and of A^T; a k-step is 256 bytes further (16 in
     // the descriptor's address field), a buffer x_bytes
     const uint64_t adesc0 = tc::smem_desc_noswizzle(sx_addr, 128, sbo);
@@ -609,12 +619,16 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
         // the peer's half of X_{t-1}, its row sums and (CTA 1) the indices it popped
         if (iter > 0) xchg_wait(par ^ 1);
         if (tid == kRows) {
-            tc::fence_proxy_async_smem();         // the peer's stores, seen through the barrier, to the tensor core
-            uint64_t ad = xdesc + (uint64_t)(ks_peer * 16), bd = bdesc0 + (uint64_t)(ks_peer * 16);
-            for (int u = 0; u < nks; ++u) {
-                tc::mma_bf16(tmem, ad, bd, idesc, 1u);
-                ad += 16;
-                bd += 16;
+            tc::fence_proxy_async_smem();         // the peers' stores, seen through the barrier, to the tensor core
+#pragma unroll
+            for (int d = 1; d < NC; ++d) {
+                const int ks_peer = ((rank + d) % NC) * (KC / 16);
+                uint64_t ad = xdesc + (uint64_t)(ks_peer * 16), bd = bdesc0 + (uint64_t)(ks_peer * 16);
+                for (int u = 0; u < nks; ++u) {
+                    tc::mma_bf16(tmem, ad, bd, idesc, 1u);
+                    ad += 16;
+                    bd += 16;
+                }
             }
             tc::mma_commit(&bar[0]);
         }
@@ -626,11 +640,11 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
                 if (sq >= 0) start(sq);
                 else idle(-1);
             } else if (seq >= 0) {
-                float s = 0.f;
+                float s = 0.f;                    // the same order in every CTA of the cluster
 #pragma unroll
-                for (int c = 0; c < 2; ++c)
+                for (int c = 0; c < NC; ++c)
 #pragma unroll
-                    for (int q = 0; q < NSPLIT; ++q) s += psum[((pp * 2 + c) * NSPLIT + q) * MT + row];
+                    for (int q = 0; q < NSPLIT; ++q) s += psum[((pp * NC + c) * NSPLIT + q) * MT + row];
                 if (pos == T - 1) {
                     if (rank == 0) {
                         loglik[seq] = 0.6931471805599453 * (double)E + log((double)s);
@@ -657,8 +671,13 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
                 }
             }
         }
-        const uint32_t rb = par ? rbar1 : rbar0;
-        if (rank == 0 && owner) tc::st_async_u1(rmail + 4u * (uint32_t)(par * MT + row), (uint32_t)mail[par * MT + row], rb);
+        uint32_t rb[NC - 1];
+#pragma unroll
+        for (int d = 0; d < NC - 1; ++d) rb[d] = par ? rbar1[d] : rbar0[d];
+        if (rank == 0 && owner)
+#pragma unroll
+            for (int d = 0; d < NC - 1; ++d)
+                tc::st_async_u1(rmail[d] + 4u * (uint32_t)(par * MT + row), (uint32_t)mail[par * MT + row], rb[d]);
         __syncthreads();
         // ---- (B) epilogue of this CTA's columns into buffer par of both CTAs
         const RowInfo ri = rinfo[row];
@@ -718,14 +737,16 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
                 const uint32_t co = xo + canon_off(row, gt + jc, K);
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 *reinterpret_cast<uint4*>(sX + co) = z;
-                tc::st_async_u4(rx + co, z, rb);
+#pragma unroll
+                for (int d = 0; d < NC - 1; ++d) tc::st_async_u4(rx[d] + co, z, rb[d]);
             }
         }
         if (HL) ps += __shfl_xor_sync(0xffffffffu, ps, 16);   // the row's two threads
         if (hsel == 0) {
-            const int idx = ((par * 2 + rank) * NSPLIT + part) * MT + row;
+            const int idx = ((par * NC + rank) * NSPLIT + part) * MT + row;
             psum[idx] = ps;
-            tc::st_async1(rpsum + 4u * (uint32_t)idx, ps, rb);
+#pragma unroll
+            for (int d = 0; d < NC - 1; ++d) tc::st_async1(rpsum[d] + 4u * (uint32_t)idx, ps, rb[d]);
         }
         // the peer's bytes of this step complete the barrier's phase (waited for next step)
         if (tid == 0) tc::mbar_arrive_expect_tx(&bar[1 + par], xbytes);
@@ -736,9 +757,9 @@ k_hmm_tc_pair(int K, int M, const char* __restrict__ g_at, const char* __restric
     cl.sync();                                    // the peer no longer addresses this CTA's shared memory
 }
 
-// Clusters of the pair kernel that fit on the device at once (cached per kernel).
+// Clusters of nc CTAs of a cluster kernel that fit on the device at once (cached per kernel).
 template <typename Kern>
-static int pair_max_clusters(Kern kern, uint32_t smem, int threads) {
+static int pair_max_clusters(Kern kern, uint32_t smem, int threads, int nc) {
     static std::mutex mu;
     static std::map<std::pair<const void*, uint32_t>, int> cache;
     const auto key = std::make_pair(reinterpret_cast<const void*>(kern), smem);
@@ -746,9 +767,16 @@ static int pair_max_clusters(Kern kern, uint32_t smem, int threads) {
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(num_sms() & ~1), 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(num_sms() / nc * nc), 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
         cudaGetLastError();
@@ -758,14 +786,15 @@ static int pair_max_clusters(Kern kern, uint32_t smem, int threads) {
     return n;
 }
 
-static accel_status tc_forward_pair(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
-                                    double* loglik, char* ws, int32_t* d_status, TcConfig cfg, cudaStream_t st) {
+template <int NC>
+static accel_status tc_forward_cluster(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
+                                       double* loglik, char* ws, int32_t* d_status, TcConfig cfg, cudaStream_t st) {
     const int K = mdl->K, M = mdl->M;
-    ACCEL_REQUIRE(tc_pair_supported(K, M, cfg.rows, cfg.split), ACCEL_ERR_UNSUPPORTED,
-                  "hmm_forward(bf16, pair): unsupported configuration (K=%d, M=%d, split=%d, rows=%d)", K, M,
-                  cfg.split, cfg.rows);
+    ACCEL_REQUIRE(tc_cl_supported(K, M, cfg.rows, cfg.split, NC), ACCEL_ERR_UNSUPPORTED,
+                  "hmm_forward(bf16, cluster of %d): unsupported configuration (K=%d, M=%d, split=%d, rows=%d)", NC, K,
+                  M, cfg.split, cfg.rows);
     const int MT = cfg.rows <= 64 ? 64 : 128;
-    const PairLayout P = pair_layout(K, M, MT, cfg.split);
+    const PairLayout P = pair_layout(K, M, MT, cfg.split, NC);
     TcLayout L = tc_layout(K, M, S);
     char* at = ws + L.at_off;
     char* et = ws + L.e_off;
@@ -778,16 +807,29 @@ static accel_status tc_forward_pair(const accel_hmm_model* mdl, const int32_t* o
     k_tc_prep<<<pg, 256, 0, st>>>(mdl->log_A, mdl->log_B, K, M, at, et);
     accel_status r = order_by_length(off, S, order, ws + L.order_scratch_off, st);
     if (r != ACCEL_OK) return r;
-    auto kern = cfg.split == 4 ? (MT == 64 ? k_hmm_tc_pair<4, 64> : k_hmm_tc_pair<4, 128>)
-                               : (MT == 64 ? k_hmm_tc_pair<2, 64> : k_hmm_tc_pair<2, 128>);
+    auto kern = cfg.split == 4 ? (MT == 64 ? k_hmm_tc_pair<4, 64, NC> : k_hmm_tc_pair<4, 128, NC>)
+                               : (MT == 64 ? k_hmm_tc_pair<2, 64, NC> : k_hmm_tc_pair<2, 128, NC>);
     ACCEL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem_bytes));
-    const int maxcl = pair_max_clusters(kern, P.smem_bytes, 128 * cfg.split);
-    ACCEL_REQUIRE(maxcl > 0, ACCEL_ERR_UNSUPPORTED, "hmm_forward(bf16, pair): no cluster of two CTAs fits the device");
+    const int threads = 128 * cfg.split;
+    const int maxcl = pair_max_clusters(kern, P.smem_bytes, threads, NC);
+    ACCEL_REQUIRE(maxcl > 0, ACCEL_ERR_UNSUPPORTED, "hmm_forward(bf16): no cluster of %d CTAs fits the device", NC);
     const int64_t tiles = (S + cfg.rows - 1) / cfg.rows;
     const int ncl = (int)(tiles < maxcl ? tiles : maxcl);
-    kern<<<2 * ncl, 128 * cfg.split, P.smem_bytes, st>>>(K, M, at, et, mdl->log_pi, obs, off, S, order, next, cfg.rows,
-                                                         loglik, d_status, P);
-    return after_launch(st, "hmm_forward(bf16 tcgen05, cluster pair)", 5);
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)NC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3((unsigned)(NC * ncl), 1, 1);
+    lc.blockDim = dim3((unsigned)threads, 1, 1);
+    lc.dynamicSmemBytes = P.smem_bytes;
+    lc.stream = st;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    ACCEL_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, K, M, (const char*)at, (const char*)et, mdl->log_pi, obs, off, S,
+                                      (const int32_t*)order, next, cfg.rows, loglik, d_status, P));
+    return after_launch(st, NC == 2 ? "hmm_forward(bf16 tcgen05, cluster pair)" : "hmm_forward(bf16 tcgen05, cluster of 4)", 5);
 }
 
 accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, const int64_t* off, int64_t S,
@@ -798,9 +840,11 @@ accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, cons
                   "memory (K=%d, M=%d)", K, M);
     if (cfg.split == 4 && (K / 4) % 32 != 0) cfg.split = 2;
     if (cfg.rows < 32 || cfg.rows > kRows) cfg.rows = kRows;
-    if (cfg.pair) {
-        if (tc_pair_supported(K, M, cfg.rows, cfg.split))
-            return tc_forward_pair(mdl, obs, off, S, loglik, ws, d_status, cfg, st);
+    if (cfg.pair == 2 && !tc_cl_supported(K, M, cfg.rows, cfg.split, 4)) cfg.pair = 1;
+    if (cfg.pair == 2) return tc_forward_cluster<4>(mdl, obs, off, S, loglik, ws, d_status, cfg, st);
+    if (cfg.pair == 1) {
+        if (tc_cl_supported(K, M, cfg.rows, cfg.split, 2))
+            return tc_forward_cluster<2>(mdl, obs, off, S, loglik, ws, d_status, cfg, st);
         cfg.pair = 0;
     }
     TcLayout L = tc_layout(K, M, S);

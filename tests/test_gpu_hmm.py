@@ -117,7 +117,7 @@ def test_bf16_tc_config_all_sequences_autotuned():
         assert rel.max() <= 1e-3, (tag, rel.max())
 
 
-@pytest.mark.parametrize("split,rows,pair", [(2, 128, 0), (4, 64, 1), (4, 32, 1)])
+@pytest.mark.parametrize("split,rows,pair", [(2, 128, 0), (4, 64, 1), (4, 32, 1), (2, 64, 2), (2, 32, 2)])
 def test_bf16_tc_config_all_sequences_each_launch_shape(tmp_path, split, rows, pair):
     f, ll = _full_bf16_run(tmp_path, (split, rows, pair))
     rel = _rel(ll, f["fp32_params"])
@@ -171,6 +171,17 @@ def test_bf16_tc_cluster_pair(tmp_path, K, split, rows):
     logs, t, obs, off = _prep(p)
     t["obs"], t["off"] = obs, off
     _force_config(tmp_path, K, 40, 700, split, rows, t, pair=1)
+    _check(p, acc.HMM_BF16_SCALED)
+
+
+# clusters of four CTAs (K/4 = 64 state columns each, MMA N = 64): CTA 0 pops the queue and
+# mails the index to the other three; rows of 128, 64 and 32
+@pytest.mark.parametrize("rows", [128, 64, 32])
+def test_bf16_tc_cluster_of_four(tmp_path, rows):
+    p = synth.hmm_workload(15, 256, 40, 700, "loguniform", 1, 400)
+    logs, t, obs, off = _prep(p)
+    t["obs"], t["off"] = obs, off
+    _force_config(tmp_path, 256, 40, 700, 2, rows, t, pair=2)
     _check(p, acc.HMM_BF16_SCALED)
 
 
