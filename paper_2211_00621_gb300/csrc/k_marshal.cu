@@ -111,34 +111,68 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_one(const int64_t* __rest
 // Each warp takes batches of SPB consecutive sequences (grid-stride over batches): lane l
 // loads the metadata of sequence b0 + l (offset, length, source pointer) with one coalesced
 // load per table -- the pointer table may be page-locked host memory read over the
-// chip-to-chip link -- then the warp copies the batch's sequences two at a time, the loads of
-// both (up to 8 elements per lane each) issued before any store, broadcasting the metadata
-// with shuffles.  SPB (1 .. 32) is chosen by the host so that there are enough batches to
-// fill the device.
+// chip-to-chip link -- then the warp copies the batch's sequences four at a time, the loads of
+// a round issued before any of its stores, broadcasting the metadata with shuffles.  SPB
+// (1 .. 32) is chosen by the host so that there are enough batches to fill the device.
+// Four sequences at a time, in rounds of 128 elements of each: every lane issues its 4 x 4
+// loads before any of the round's stores, so a warp keeps 2 KB (int32) in flight even when
+// the sequences are short.
 template <typename T>
-__device__ __forceinline__ void gather_pair(const T* __restrict__ s0, T* __restrict__ d0, int64_t n0,
-                                            const T* __restrict__ s1, T* __restrict__ d1, int64_t n1, int lane) {
-    const int64_t n = n0 > n1 ? n0 : n1;
-    for (int64_t base = 0; base < n; base += 32 * 8) {
-        T v0[8], v1[8];
+__device__ __forceinline__ void gather_quad(const T* const (&src)[4], T* const (&dst)[4], const int (&n)[4], int lane) {
+    const int nmax = max(max(n[0], n[1]), max(n[2], n[3]));
+    for (int base = 0; base < nmax; base += 32 * 4) {
+        T v[4][4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int64_t k = base + r * 32 + lane;
-            if (k < n0) v0[r] = s0[k];
-            if (k < n1) v1[r] = s1[k];
-        }
+        for (int g = 0; g < 4; ++g)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int64_t k = base + r * 32 + lane;
-            if (k < n0) d0[k] = v0[r];
-            if (k < n1) d1[k] = v1[r];
+            for (int r = 0; r < 4; ++r) {
+                const int k = base + r * 32 + lane;
+                if (k < n[g]) v[g][r] = src[g][k];
+            }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int k = base + r * 32 + lane;
+                if (k < n[g]) dst[g][k] = v[g][r];
+            }
+    }
+}
+
+// One warp copies a batch of cnt <= 32 consecutive sequences whose metadata lane l holds
+// (offset mo, length mn, source ms of sequence l of the batch).
+template <typename T>
+__device__ __forceinline__ void gather_batch(int64_t mo, int64_t mn, const T* ms, int cnt, T* __restrict__ flat,
+                                             int lane) {
+    if (__any_sync(0xffffffffu, mn > (int64_t)INT32_MAX)) {
+        // a sequence longer than 2^31 - 1 elements: the batch one sequence at a time, 64-bit
+        for (int j = 0; j < cnt; ++j) {
+            const int64_t o = __shfl_sync(0xffffffffu, mo, j), ng = __shfl_sync(0xffffffffu, mn, j);
+            const T* sp = reinterpret_cast<const T*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(ms), j));
+            for (int64_t k = lane; k < ng; k += 32) flat[o + k] = sp[k];
         }
+        return;
+    }
+    for (int j = 0; j < cnt; j += 4) {
+        const T* src[4];
+        T* dst[4];
+        int n[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int jj = j + g < cnt ? j + g : j;          // a missing sequence copies nothing
+            const int64_t o = __shfl_sync(0xffffffffu, mo, jj);
+            const int ng = __shfl_sync(0xffffffffu, (int)mn, jj);
+            src[g] = reinterpret_cast<const T*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(ms), jj));
+            dst[g] = flat + o;
+            n[g] = j + g < cnt ? ng : 0;
+        }
+        gather_quad<T>(src, dst, n, lane);
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_gather(const T* const* __restrict__ ptrs, const int64_t* __restrict__ off,
-                                               int64_t S, int spb, T* __restrict__ flat) {
+                                                  int64_t S, int spb, T* __restrict__ flat) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -151,15 +185,7 @@ __global__ void __launch_bounds__(256, 4) k_gather(const T* const* __restrict__ 
             mn = off[b0 + lane + 1] - mo;
             ms = ptrs[b0 + lane];
         }
-        for (int j = 0; j < cnt; j += 2) {
-            const int64_t o0 = __shfl_sync(0xffffffffu, mo, j), n0 = __shfl_sync(0xffffffffu, mn, j);
-            const T* s0 = reinterpret_cast<const T*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(ms), j));
-            const int j1 = j + 1 < cnt ? j + 1 : j;
-            const int64_t o1 = __shfl_sync(0xffffffffu, mo, j1);
-            const int64_t n1 = j + 1 < cnt ? __shfl_sync(0xffffffffu, mn, j1) : 0;
-            const T* s1 = reinterpret_cast<const T*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(ms), j1));
-            gather_pair<T>(s0, flat + o0, n0, s1, flat + o1, n1, lane);
-        }
+        gather_batch<T>(mo, mn, ms, cnt, flat, lane);
     }
 }
 

@@ -51,10 +51,11 @@ def test_marshal_ragged_int64_and_many_sequences():
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-@pytest.mark.parametrize("S", [16 * 1024, 16 * 1024 + 1, 40_000])
+@pytest.mark.parametrize("S", [16 * 1024, 16 * 1024 + 1, 40_000, 200_003])
 def test_marshal_ragged_scan_paths(S, pinned):
-    # S <= 16,384 scans the lengths in one CTA, larger S in three passes; page-locked host
-    # tables are read in place by the kernels, pageable ones are copied to the workspace first
+    # S <= 16,384 scans the lengths in one CTA, larger S in three passes (200,003: more
+    # sequences per warp batch, a partial last batch); page-locked host tables are read in
+    # place by the kernels, pageable ones are copied to the workspace first
     seqs = synth.ragged_int32(S, S, 0, 9)
     pieces = [_t(x) for x in seqs]
     ptrs = torch.tensor([p.data_ptr() if p.numel() else 0 for p in pieces], dtype=torch.int64)
