@@ -248,7 +248,8 @@ accel_status accel_map(int32_t op, int32_t in_dtype, const void* d_in, const voi
 /* ============================================================ reduce (Appendix A) */
 /*
  * accel_reduce -- *d_out = reduce f ne d_in[0..n)  (one element of `dtype`, device).
- *  Deterministic two-pass reduction: per-CTA partials in d_ws, then one combining CTA.
+ *  Deterministic: one CTA for n <= 65,536, else two passes (per-CTA partials in d_ws, then
+ *  one combining CTA).
  *  n == 0 gives ne.  Integer results are exact (wrapping), float results depend on the
  *  (fixed) combination order.
  */

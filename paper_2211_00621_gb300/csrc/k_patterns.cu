@@ -135,6 +135,19 @@ k_reduce_final(const typename compute_of<T>::type* __restrict__ partials, int np
     if (threadIdx.x == 0) *out = n == 0 ? red_neutral<T>(OP) : (T)acc;
 }
 
+// Small inputs (n <= kReduceOne): one CTA reduces everything (one launch instead of two);
+// the same fixed combination order on every call.
+constexpr int64_t kReduceOne = 1 << 16;
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) k_reduce_one(const T* __restrict__ in, int64_t n, T* __restrict__ out) {
+    using C = typename compute_of<T>::type;
+    __shared__ C smem[kThreads / 32];
+    C acc = red_neutral<C>(OP);
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) acc = red_combine<OP, C>(acc, (C)in[i]);
+    acc = block_reduce<OP, C>(acc, smem);
+    if (threadIdx.x == 0) *out = n == 0 ? red_neutral<T>(OP) : (T)acc;
+}
+
 static int reduce_grid(int64_t n) {
     int g = grid_for(n / 4 + 1, kThreads);
     return g > 1024 ? 1024 : g;
@@ -200,7 +213,13 @@ accel_status accel_reduce(int32_t op, int32_t dtype, const void* d_in, int64_t n
     ACCEL_REQUIRE(n >= 0 && d_out && d_ws && (n == 0 || d_in), ACCEL_ERR_INVALID_ARG, "accel_reduce: bad pointer or size");
     ACCEL_REQUIRE(ws_bytes >= accel_reduce_workspace_size(n, dtype), ACCEL_ERR_WORKSPACE, "accel_reduce: workspace too small");
     cudaStream_t st = as_stream(stream);
-    int grid = n == 0 ? 1 : reduce_grid(n);
+    if (n <= kReduceOne) {
+        ACCEL_DISPATCH_DTYPE(dtype, T, ACCEL_DISPATCH_RED(op, OPC, {
+            k_reduce_one<T, OPC><<<1, kThreads, 0, st>>>((const T*)d_in, n, (T*)d_out);
+        }));
+        return after_launch(st, "accel_reduce", 1);
+    }
+    int grid = reduce_grid(n);
     void* partials = (char*)d_ws + kStatusBytes;
     ACCEL_DISPATCH_DTYPE(dtype, T, ACCEL_DISPATCH_RED(op, OPC, {
         using C = typename compute_of<T>::type;

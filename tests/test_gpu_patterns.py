@@ -206,16 +206,18 @@ def test_map_unaligned_and_empty():
 
 
 # ------------------------------------------------------------------------------ reduce
+# n <= 65,536 is reduced by one CTA, larger n in two passes
+@pytest.mark.parametrize("n", [200_003, 65_537, 65_536, 4_097, 1])
 @pytest.mark.parametrize("red", [op.RED_ADD, op.RED_MUL, op.RED_MIN, op.RED_MAX])
 @pytest.mark.parametrize("dt", [np.int32, np.int64])
-def test_reduce_int_bit_exact(red, dt):
-    n = 200_003
+def test_reduce_int_bit_exact(red, dt, n):
     g = synth.rng(red + 11)
     x = g.integers(-5 if red == op.RED_MUL else -10**6, 6 if red == op.RED_MUL else 10**6, size=n).astype(dt)
     got = api.accel_reduce(red, _t(x)).item()
     if red == op.RED_MUL:
-        ref = op.reduce_op(red, x[:2000])          # wrapping product: compare a prefix exactly
-        got = api.accel_reduce(red, _t(x[:2000])).item()
+        m = min(n, 2000)
+        ref = op.reduce_op(red, x[:m])             # wrapping product: compare a prefix exactly
+        got = api.accel_reduce(red, _t(x[:m])).item()
     elif red == op.RED_ADD:
         ref = int(np.sum(x.astype(np.int64)))
         bits = np.dtype(dt).itemsize * 8
