@@ -378,6 +378,26 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
                          float* d_grad_log_pi, void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * hmm_adjoint_forward / hmm_adjoint_backward -- hmm_adjoint in two calls, for a forward pass
+ * whose gradient is taken later (e.g. an autograd function): the forward writes logL_s
+ * (d_loglik, may be NULL) and leaves its saved state -- the ceil(sqrt(T_s)) checkpoints of
+ * alpha, their exponents, the sequence order and grouping -- in d_ws; the backward then runs
+ * the recomputation and the backward recursion from that state and writes the gradients as
+ * hmm_adjoint does.  Both calls take the same model, observations, offsets, sizes and
+ * workspace (hmm_adjoint_workspace_size bytes), and the model's log parameters must not change
+ * in between; the forward does not depend on the weights, and the backward leaves the saved
+ * state intact, so one forward may be followed by several backward calls (other weights).
+ * Results equal hmm_adjoint's.  Errors as hmm_adjoint.
+ */
+accel_status hmm_adjoint_forward(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets,
+                                 int64_t S, int64_t total_T, int64_t max_T, double* d_loglik, void* d_ws,
+                                 size_t ws_bytes, void* stream);
+accel_status hmm_adjoint_backward(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets,
+                                  int64_t S, int64_t total_T, int64_t max_T, const double* d_weights,
+                                  float* d_grad_log_A, float* d_grad_log_B, float* d_grad_log_pi, void* d_ws,
+                                  size_t ws_bytes, void* stream);
+
+/*
  * hmm_max_length -- *d_max_T = max_s (d_offsets[s+1] - d_offsets[s]) (device int64, caller
  * owned; 0 when S = 0): the max_T that hmm_adjoint and hmm_forward_long are sized with,
  * computed on the device (one CTA, asynchronous on `stream`) for callers that do not track

@@ -75,6 +75,8 @@ SIGNATURES = {
     "hmm_forward": (i32, [C.POINTER(accel_hmm_model), i32, vp, vp, i64, i64, vp, vp, sz, vp]),
     "hmm_adjoint_workspace_size": (sz, [C.POINTER(accel_hmm_model), i64, i64, i64]),
     "hmm_adjoint": (i32, [C.POINTER(accel_hmm_model), vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, sz, vp]),
+    "hmm_adjoint_forward": (i32, [C.POINTER(accel_hmm_model), vp, vp, i64, i64, i64, vp, vp, sz, vp]),
+    "hmm_adjoint_backward": (i32, [C.POINTER(accel_hmm_model), vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, sz, vp]),
     "pairwise_mapreduce": (i32, [i32, vp, vp, vp, vp, i64, flt, vp, vp, vp, vp]),
     "hmm_forward_long_workspace_size": (sz, [C.POINTER(accel_hmm_model), i64, i64, i64]),
     "hmm_forward_long": (i32, [C.POINTER(accel_hmm_model), vp, vp, i64, i64, i64, vp, vp, sz, vp]),

@@ -340,6 +340,48 @@ def hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=None, max_T: int | N
     return gA, gB, gpi, ll
 
 
+class AdjointSaved:
+    """The state hmm_adjoint_forward leaves for hmm_adjoint_backward: the workspace (with the
+    checkpoints of alpha) and the sizes it was made for."""
+
+    def __init__(self, ws, S, total_T, max_T):
+        self.ws, self.S, self.total_T, self.max_T = ws, S, total_T, max_T
+
+
+def hmm_adjoint_forward(log_A, log_B, log_pi, obs, offsets, max_T: int | None = None, out=None):
+    """logL (float64 [S]) by the adjoint's checkpointed FP32 forward, and the saved state for
+    hmm_adjoint_backward."""
+    lib = L.load()
+    _need_cuda(log_A, log_B, log_pi, obs, offsets)
+    m = _model(log_A, log_B, log_pi)
+    S = offsets.numel() - 1
+    if max_T is None:
+        max_T = int(hmm_max_length(offsets).item()) if S else 0
+    ll = torch.empty(S, dtype=torch.float64, device=obs.device) if out is None else out
+    ws = _ws(lib.hmm_adjoint_workspace_size(C.byref(m), S, obs.numel(), max_T), obs.device)
+    L.check("hmm_adjoint_forward", lib.hmm_adjoint_forward(C.byref(m), _ptr(obs), _ptr(offsets), S, obs.numel(), max_T,
+                                                           _ptr(ll), _ptr(ws), ws.numel(), _stream()))
+    return ll, AdjointSaved(ws, S, obs.numel(), max_T)
+
+
+def hmm_adjoint_backward(log_A, log_B, log_pi, obs, offsets, saved: AdjointSaved, weights=None):
+    """Gradients (float32 log_A, log_B, log_pi) of sum_s w_s logL_s from the state a previous
+    hmm_adjoint_forward call on the same inputs saved."""
+    lib = L.load()
+    _need_cuda(log_A, log_B, log_pi, obs, offsets, weights)
+    m = _model(log_A, log_B, log_pi)
+    K, M = m.K, m.M
+    gA = torch.empty(K, K, dtype=torch.float32, device=obs.device)
+    gB = torch.empty(K, M, dtype=torch.float32, device=obs.device)
+    gpi = torch.empty(K, dtype=torch.float32, device=obs.device)
+    if weights is not None and weights.dtype != torch.float64:
+        weights = weights.to(torch.float64)
+    L.check("hmm_adjoint_backward", lib.hmm_adjoint_backward(
+        C.byref(m), _ptr(obs), _ptr(offsets), saved.S, saved.total_T, saved.max_T, _ptr(weights), _ptr(gA), _ptr(gB),
+        _ptr(gpi), _ptr(saved.ws), saved.ws.numel(), _stream()))
+    return gA, gB, gpi
+
+
 def accel_pair_histogram(A, edges, B=None):
     """Histogram (int64 [len(edges)+1]) of the angular separations of point pairs: A and B
     are float32 [n, 3] unit vectors (CUDA); edges a strictly decreasing float32 sequence of
@@ -455,15 +497,24 @@ class Graph:
 class HMMLogLik(torch.autograd.Function):
     """logL[S] = HMMLogLik.apply(log_A, log_B, log_pi, obs, offsets, precision, max_T=None).
 
-    Backward calls hmm_adjoint with the incoming gradient as per-sequence weights (the
-    gradient of sum_s w_s logL_s is linear in w), giving d/d log_A, d/d log_B, d/d log_pi.
+    With FP32 precision and a gradient to take, the forward is the adjoint's checkpointed
+    forward (hmm_adjoint_forward), whose saved state the backward uses (hmm_adjoint_backward):
+    the forward recursion runs once.  With BF16 precision the forward runs on the tensor cores
+    and the backward calls hmm_adjoint.  The incoming gradient enters as per-sequence weights
+    (the gradient of sum_s w_s logL_s is linear in w), giving d/d log_A, d/d log_B, d/d log_pi.
     """
 
     @staticmethod
     def forward(ctx, log_A, log_B, log_pi, obs, offsets, precision=L.HMM_FP32_LOG, max_T=None):
+        ctx.saved = None
+        ctx.max_T = max_T
+        needs = any(ctx.needs_input_grad[:3])
+        if precision == L.HMM_FP32_LOG and needs:
+            ll, ctx.saved = hmm_adjoint_forward(log_A, log_B, log_pi, obs, offsets, max_T=max_T)
+            ctx.save_for_backward(log_A, log_B, log_pi, obs, offsets, None)
+            return ll
         # max_T sizes the adjoint's checkpoints: the caller's value, else the library's device
         # reduction over the offsets, launched here and read only in backward
-        ctx.max_T = max_T
         d_max = hmm_max_length(offsets) if max_T is None and offsets.numel() > 1 else None
         ctx.save_for_backward(log_A, log_B, log_pi, obs, offsets, d_max)
         return hmm_forward(log_A, log_B, log_pi, obs, offsets, precision)
@@ -471,9 +522,12 @@ class HMMLogLik(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         log_A, log_B, log_pi, obs, offsets, d_max = ctx.saved_tensors
+        w = grad_out.contiguous().to(torch.float64)
+        if ctx.saved is not None:
+            gA, gB, gpi = hmm_adjoint_backward(log_A, log_B, log_pi, obs, offsets, ctx.saved, weights=w)
+            return gA, gB, gpi, None, None, None, None
         max_T = ctx.max_T if ctx.max_T is not None else (int(d_max.item()) if d_max is not None else 0)
-        gA, gB, gpi, _ = hmm_adjoint(log_A, log_B, log_pi, obs, offsets,
-                                     weights=grad_out.contiguous().to(torch.float64), max_T=max_T, want_loglik=False)
+        gA, gB, gpi, _ = hmm_adjoint(log_A, log_B, log_pi, obs, offsets, weights=w, max_T=max_T, want_loglik=False)
         return gA, gB, gpi, None, None, None, None
 
 

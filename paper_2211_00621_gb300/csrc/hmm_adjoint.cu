@@ -1476,33 +1476,44 @@ size_t hmm_adjoint_workspace_size(const accel_hmm_model* m, int64_t S, int64_t t
     return adj::layout(m->K, m->M, S, max_T).total;
 }
 
-accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets, int64_t S,
-                         int64_t total_T, int64_t max_T, const double* d_weights, double* d_loglik,
-                         float* d_grad_log_A, float* d_grad_log_B, float* d_grad_log_pi, void* d_ws, size_t ws_bytes,
-                         void* stream) {
-    accel_status r = check_model(m, "hmm_adjoint");
+}  // extern "C"
+
+namespace accel {
+namespace hmm {
+namespace adj {
+
+// What both phases of the adjoint derive from the arguments (the same decisions every call).
+struct Plan {
+    Layout L;
+    Prm p;
+    int K, M, nb, nsU, nsC;
+    size_t sm_b, sm_c;
+    bool use_cluster, xi_tc, counts_tc, planned;
+    float* cntp;
+    float* Upart;
+    char* ws;
+};
+
+static accel_status setup(const char* who, const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets,
+                          int64_t S, int64_t total_T, int64_t max_T, void* d_ws, size_t ws_bytes, Plan& P) {
+    accel_status r = check_model(m, who);
     if (r != ACCEL_OK) return r;
-    ACCEL_REQUIRE(S >= 0 && total_T >= 0 && max_T >= 0, ACCEL_ERR_INVALID_ARG, "hmm_adjoint: negative size");
-    ACCEL_REQUIRE(d_offsets && d_ws && d_grad_log_A && d_grad_log_B && (total_T == 0 || d_obs), ACCEL_ERR_INVALID_ARG,
-                  "hmm_adjoint: null pointer");
-    ACCEL_REQUIRE(((uintptr_t)d_ws % 256) == 0, ACCEL_ERR_INVALID_ARG, "hmm_adjoint: d_ws must be 256-byte aligned");
+    ACCEL_REQUIRE(S >= 0 && total_T >= 0 && max_T >= 0, ACCEL_ERR_INVALID_ARG, "%s: negative size", who);
+    ACCEL_REQUIRE(d_offsets && d_ws && (total_T == 0 || d_obs), ACCEL_ERR_INVALID_ARG, "%s: null pointer", who);
+    ACCEL_REQUIRE(((uintptr_t)d_ws % 256) == 0, ACCEL_ERR_INVALID_ARG, "%s: d_ws must be 256-byte aligned", who);
     const int K = m->K, M = m->M;
-    adj::Layout L = adj::layout(K, M, S, max_T);
-    ACCEL_REQUIRE(ws_bytes >= L.total, ACCEL_ERR_WORKSPACE, "hmm_adjoint: workspace %zu < %zu bytes", ws_bytes, L.total);
-    size_t sm_b = adj::smem_bwd(K, M, L.Cmax);
-    ACCEL_REQUIRE(sm_b <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED,
-                  "hmm_adjoint: emission table too large for shared memory (K=%d, M=%d)", K, M);
-    cudaStream_t st = as_stream(stream);
+    P.K = K;
+    P.M = M;
+    P.L = layout(K, M, S, max_T);
+    const Layout& L = P.L;
+    ACCEL_REQUIRE(ws_bytes >= L.total, ACCEL_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", who, ws_bytes, L.total);
+    P.sm_b = smem_bwd(K, M, L.Cmax);
+    ACCEL_REQUIRE(P.sm_b <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED,
+                  "%s: emission table too large for shared memory (K=%d, M=%d)", who, K, M);
     char* ws = (char*)d_ws;
-    if (debug_mode() && S > 0) {
-        r = debug_check_offsets(d_offsets, S, total_T, 1, ws + kDebugScratchOff, st);
-        if (r != ACCEL_OK) return r;
-        r = debug_check_symbols(d_obs, total_T, M, ws + kDebugScratchOff, st);
-        if (r != ACCEL_OK) return r;
-    }
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + kStatusOff, 0, 4, st));
-    adj::Prm p;
-    p.K = K; p.M = M; p.Cmax = L.Cmax; p.S = S; p.Kp = adj::padK(K);
+    P.ws = ws;
+    Prm& p = P.p;
+    p.K = K; p.M = M; p.Cmax = L.Cmax; p.S = S; p.Kp = padK(K);
     p.status = status_word((int32_t*)(ws + kStatusOff));
     p.rows = (int32_t*)(ws + L.rows);
     p.ebuf = (int32_t*)(ws + L.ebuf);
@@ -1510,119 +1521,227 @@ accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const i
     p.osym = (int32_t*)(ws + L.osym);
     p.ncl = 0;
     p.plan = nullptr;
-    float* cntp = (float*)(ws + L.cntp);
+    P.cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
-    p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = d_weights;
+    p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = nullptr;
     p.cp = (float*)(ws + L.cp); p.cp_e = (int32_t*)(ws + L.cp_e); p.clast = (float*)(ws + L.clast);
-    p.loglik = d_loglik; p.P = (float*)(ws + L.P); p.Q = (float*)(ws + L.Q); p.Rc = (float*)(ws + L.Rc);
+    p.loglik = nullptr; p.P = (float*)(ws + L.P); p.Q = (float*)(ws + L.Q); p.Rc = (float*)(ws + L.Rc);
     p.cnt = (float*)(ws + L.cnt); p.pig = (float*)(ws + L.pig);
-    float* Upart = (float*)(ws + L.Upart);
-    int nlaunch = 0;
-    int pg = num_sms() * 4;
-    adj::k_prep<<<pg, 256, 0, st>>>(m->log_A, m->log_B, m->log_pi, K, p.Kp, M, (float*)p.A, (float*)p.At,
-                                    (float*)p.BT, (float*)p.pi);
-    ++nlaunch;
-    const int nb = (K + adj::kTile - 1) / adj::kTile;
-    const size_t sm_c = adj::clu::smem_layout(K, M).total;
+    P.Upart = (float*)(ws + L.Upart);
+    P.nb = (K + kTile - 1) / kTile;
+    P.sm_c = clu::smem_layout(K, M).total;
     // the cluster kernels leave the emission counts to the tensor-core kernel or to k_counts
     // (an [M][256] table in shared memory); otherwise the streaming kernels take the shape
     const bool counts_fit = xi_tc_counts_supported(K, M) || (size_t)M * 256 * 4 <= (size_t)max_smem_optin();
-    const bool use_cluster = S > 0 && adj::clu::cluster_shape_ok(K) && sm_c <= (size_t)max_smem_optin() && counts_fit;
-    const bool xi_tc = use_cluster && xi_tc_supported(K);
-    const bool counts_tc = xi_tc && xi_tc_counts_supported(K, M);
-    const int nsU = xi_tc ? xi_tc_splits(K) : adj::kSplit;
-    const int nsC = counts_tc ? xi_tc_splits(K) : adj::kCntSplit;
+    P.use_cluster = S > 0 && clu::cluster_shape_ok(K) && P.sm_c <= (size_t)max_smem_optin() && counts_fit;
+    P.xi_tc = P.use_cluster && xi_tc_supported(K);
+    P.counts_tc = P.xi_tc && xi_tc_counts_supported(K, M);
+    P.nsU = P.xi_tc ? xi_tc_splits(K) : kSplit;
+    P.nsC = P.counts_tc ? xi_tc_splits(K) : kCntSplit;
+    P.planned = false;
+    if (P.use_cluster) {
+        // groups: at most 16 sequences each, and at least one pair of CTAs per two SMs
+        const int64_t ncl_min = (S + clu::kG - 1) / clu::kG;
+        const int64_t ncl_sm = S < (int64_t)(num_sms() / 2) ? S : (int64_t)(num_sms() / 2);
+        if (ncl_min <= 2 * ncl_sm && 2 * ncl_sm <= clu::kPlanMaxGroups && S <= clu::kPlanMaxSeq) {
+            // one pair per two SMs, each running one or two groups (planned on the device
+            // from the sorted lengths by the forward phase)
+            p.ncl = ncl_sm;
+            p.plan = (int64_t*)(ws + L.plan);
+            P.planned = true;
+        } else {
+            p.ncl = ncl_min > ncl_sm ? ncl_min : ncl_sm;
+        }
+    }
+    return ACCEL_OK;
+}
+
+// Phase 1: parameters prepared, sequences ordered and (cluster path) grouped, the forward pass
+// with its checkpoints and logL.  Everything phase 2 reads stays in the workspace.
+static accel_status run_forward(Plan& P, const accel_hmm_model* m, double* d_loglik, cudaStream_t st, int& nlaunch) {
+    Prm& p = P.p;
+    const Layout& L = P.L;
+    const int K = P.K, M = P.M;
+    char* ws = P.ws;
+    p.loglik = d_loglik;
+    int pg = num_sms() * 4;
+    k_prep<<<pg, 256, 0, st>>>(m->log_A, m->log_B, m->log_pi, K, p.Kp, M, (float*)p.A, (float*)p.At, (float*)p.BT,
+                               (float*)p.pi);
+    ++nlaunch;
+    if (p.S == 0) return ACCEL_OK;
+    accel_status r = order_by_length(p.off, p.S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)p.S * 4, 256), st);
+    if (r != ACCEL_OK) return r;
+    nlaunch += 3;
+    if (P.use_cluster) {
+        if (P.planned) {
+            const int64_t ncl_min = (p.S + clu::kG - 1) / clu::kG;
+            const int64_t ncl_sm = p.ncl;
+            const int64_t nv_lo = ncl_min > ncl_sm ? ncl_min : ncl_sm;
+            int64_t nv_hi = 2 * ncl_sm < p.S ? 2 * ncl_sm : p.S;
+            if (nv_hi > nv_lo + clu::kPlanThreads - 1) nv_hi = nv_lo + clu::kPlanThreads - 1;
+            clu::k_plan<<<1, clu::kPlanThreads, 0, st>>>(p, (int64_t*)p.plan, nv_lo, nv_hi, K == 256 ? 8 : 16);
+            ++nlaunch;
+        }
+        const unsigned grid = (unsigned)(2 * p.ncl);
+        const clu::Kernels kc = clu::kernels_for(K);
+        ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
+        kc.fwd<<<grid, clu::kT, P.sm_c, st>>>(p);
+        ++nlaunch;
+    } else {
+        size_t sm_f = smem_fwd(K, M);
+        ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_forward_cp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f));
+        k_forward_cp<<<(unsigned)L.ngroups, kT, sm_f, st>>>(p);
+        ++nlaunch;
+    }
+    p.loglik = nullptr;
+    return ACCEL_OK;
+}
+
+// Phase 2: the rounds of recomputation and the backward recursion, the count accumulation, and
+// the gradients.  Reads phase 1's checkpoints, order and plan; clears its own accumulators.
+static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad_log_A, float* d_grad_log_B,
+                                 float* d_grad_log_pi, cudaStream_t st, int& nlaunch) {
+    Prm& p = P.p;
+    const Layout& L = P.L;
+    const int K = P.K, M = P.M;
+    const int64_t S = p.S;
+    char* ws = P.ws;
+    p.w = d_weights;
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cnt, 0, (size_t)L.ngroups * K * M * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.pig, 0, (size_t)L.npig * K * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)nsU * K * K * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)P.nsU * K * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.rows, 0, (size_t)L.Cmax * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cntp, 0, (size_t)nsC * K * M * 4, st));
+    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cntp, 0, (size_t)P.nsC * K * M * 4, st));
     // every row starts with no symbol: the rows of a sequence skipped as longer than max_T are
     // never written by the cluster kernels, and the count kernels index tables by osym
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.osym, 0xff, (size_t)S * L.Cmax * 4, st));
-    if (counts_tc) ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.gam, 0, (size_t)S * L.Cmax * K * 4, st));
+    if (P.counts_tc) ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.gam, 0, (size_t)S * L.Cmax * K * 4, st));
     if (S > 0) {
-        r = order_by_length(d_offsets, S, (int32_t*)(ws + L.order), ws + L.order + align_up((size_t)S * 4, 256), st);
-        if (r != ACCEL_OK) return r;
-        nlaunch += 3;
-        if (use_cluster) {
-            // groups: at most 16 sequences each, and at least one pair of CTAs per two SMs
-            const int64_t ncl_min = (S + adj::clu::kG - 1) / adj::clu::kG;
-            const int64_t ncl_sm = S < (int64_t)(num_sms() / 2) ? S : (int64_t)(num_sms() / 2);
-            if (ncl_min <= 2 * ncl_sm && 2 * ncl_sm <= adj::clu::kPlanMaxGroups && S <= adj::clu::kPlanMaxSeq) {
-                // one pair per two SMs, each running one or two groups (planned on the device
-                // from the sorted lengths)
-                p.ncl = ncl_sm;
-                const int64_t nv_lo = ncl_min > ncl_sm ? ncl_min : ncl_sm;
-                int64_t nv_hi = 2 * ncl_sm < S ? 2 * ncl_sm : S;
-                if (nv_hi > nv_lo + adj::clu::kPlanThreads - 1) nv_hi = nv_lo + adj::clu::kPlanThreads - 1;
-                int64_t* plan = (int64_t*)(ws + L.plan);
-                adj::clu::k_plan<<<1, adj::clu::kPlanThreads, 0, st>>>(p, plan, nv_lo, nv_hi, K == 256 ? 8 : 16);
-                ++nlaunch;
-                p.plan = plan;
-            } else {
-                p.ncl = ncl_min > ncl_sm ? ncl_min : ncl_sm;
-            }
+        if (P.use_cluster) {
             const unsigned grid = (unsigned)(2 * p.ncl);
-            const adj::clu::Kernels kc = adj::clu::kernels_for(K);
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c));
-            kc.fwd<<<grid, adj::clu::kT, sm_c, st>>>(p);
-            ++nlaunch;
+            const clu::Kernels kc = clu::kernels_for(K);
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
             const size_t sm_cnt = (size_t)M * 256 * 4;
-            if (!counts_tc) {
+            if (!P.counts_tc) {
                 ACCEL_REQUIRE(sm_cnt <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: M=%d too large", M);
-                ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
+                ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
             }
             const int nbc = (K + 255) / 256;
             for (int round = 0; round < L.Cmax; ++round) {
-                kc.rec<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
-                kc.bwd<<<grid, adj::clu::kT, sm_c, st>>>(p, round);
+                kc.rec<<<grid, clu::kT, P.sm_c, st>>>(p, round);
+                kc.bwd<<<grid, clu::kT, P.sm_c, st>>>(p, round);
                 nlaunch += 2;
-                if (xi_tc) {
-                    r = xi_tc_round(p.P, p.Q, p.gam, p.osym, p.rows + round, K, M, Upart, counts_tc ? cntp : nullptr,
-                                    p.status, st);
+                if (P.xi_tc) {
+                    accel_status r = xi_tc_round(p.P, p.Q, p.gam, p.osym, p.rows + round, K, M, P.Upart,
+                                                 P.counts_tc ? P.cntp : nullptr, p.status, st);
                     if (r != ACCEL_OK) return r;
                     ++nlaunch;
                 } else {
-                    adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
+                    k_gemm_ptq<<<P.nb * P.nb * kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, P.Upart);
                     ++nlaunch;
                 }
-                if (!counts_tc) {
-                    adj::k_counts<<<nbc * adj::kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, cntp);
+                if (!P.counts_tc) {
+                    k_counts<<<nbc * kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, P.cntp);
                     ++nlaunch;
                 }
             }
         } else {
-            size_t sm_f = adj::smem_fwd(K, M);
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_forward_cp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f));
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(adj::k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
-            adj::k_forward_cp<<<(unsigned)L.ngroups, adj::kT, sm_f, st>>>(p);
-            ++nlaunch;
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_b));
             for (int round = 0; round < L.Cmax; ++round) {
-                adj::k_backward_round<<<(unsigned)L.ngroups, adj::kT, sm_b, st>>>(p, round);
-                adj::k_gemm_ptq<<<nb * nb * adj::kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, Upart);
+                k_backward_round<<<(unsigned)L.ngroups, kT, P.sm_b, st>>>(p, round);
+                k_gemm_ptq<<<P.nb * P.nb * kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, P.Upart);
                 nlaunch += 2;
             }
         }
     }
-    adj::k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, Upart, p.cnt, cntp, p.pig, K, M, L.ngroups,
-                                      use_cluster ? p.ncl : L.ngroups, nsU, nsC, d_grad_log_A,
-                                      d_grad_log_B, d_grad_log_pi);
+    int pg = num_sms() * 4;
+    k_finish<<<pg, 256, 0, st>>>(p.A, p.Kp, P.Upart, p.cnt, P.cntp, p.pig, K, M, L.ngroups,
+                                 P.use_cluster ? p.ncl : L.ngroups, P.nsU, P.nsC, d_grad_log_A, d_grad_log_B,
+                                 d_grad_log_pi);
     ++nlaunch;
-    r = after_launch(st, "hmm_adjoint", nlaunch);
+    return ACCEL_OK;
+}
+
+static accel_status debug_checks(const Plan& P, const int64_t* d_offsets, const int32_t* d_obs, int64_t total_T,
+                                 cudaStream_t st) {
+    if (!debug_mode() || P.p.S == 0) return ACCEL_OK;
+    accel_status r = debug_check_offsets(d_offsets, P.p.S, total_T, 1, P.ws + kDebugScratchOff, st);
+    if (r != ACCEL_OK) return r;
+    return debug_check_symbols(d_obs, total_T, P.M, P.ws + kDebugScratchOff, st);
+}
+
+static accel_status finish_call(const char* who, const Plan& P, int64_t max_T, cudaStream_t st, int nlaunch) {
+    accel_status r = after_launch(st, who, nlaunch);
     if (r != ACCEL_OK) return r;
     if (debug_mode()) {
         int32_t h = 0;
-        ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, p.status, 4, cudaMemcpyDeviceToHost, st));
+        ACCEL_CUDA_TRY(cudaMemcpyAsync(&h, P.p.status, 4, cudaMemcpyDeviceToHost, st));
         ACCEL_CUDA_TRY(cudaStreamSynchronize(st));
-        if (h == ACCEL_ERR_SHAPE) return set_error(h, "hmm_adjoint: a sequence is longer than max_T=%lld", (long long)max_T);
-        if (h != ACCEL_OK) return set_error(h, "hmm_adjoint: device status %d (a bounded wait gave up)", h);
+        if (h == ACCEL_ERR_SHAPE) return set_error(h, "%s: a sequence is longer than max_T=%lld", who, (long long)max_T);
+        if (h != ACCEL_OK) return set_error(h, "%s: device status %d (a bounded wait gave up)", who, h);
     }
     return ok();
+}
+
+}  // namespace adj
+}  // namespace hmm
+}  // namespace accel
+
+extern "C" {
+
+accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets, int64_t S,
+                         int64_t total_T, int64_t max_T, const double* d_weights, double* d_loglik,
+                         float* d_grad_log_A, float* d_grad_log_B, float* d_grad_log_pi, void* d_ws, size_t ws_bytes,
+                         void* stream) {
+    adj::Plan P;
+    accel_status r = adj::setup("hmm_adjoint", m, d_obs, d_offsets, S, total_T, max_T, d_ws, ws_bytes, P);
+    if (r != ACCEL_OK) return r;
+    ACCEL_REQUIRE(d_grad_log_A && d_grad_log_B, ACCEL_ERR_INVALID_ARG, "hmm_adjoint: null pointer");
+    cudaStream_t st = as_stream(stream);
+    r = adj::debug_checks(P, d_offsets, d_obs, total_T, st);
+    if (r != ACCEL_OK) return r;
+    ACCEL_CUDA_TRY(cudaMemsetAsync(P.ws + kStatusOff, 0, 4, st));
+    int nlaunch = 0;
+    r = adj::run_forward(P, m, d_loglik, st, nlaunch);
+    if (r != ACCEL_OK) return r;
+    r = adj::run_backward(P, d_weights, d_grad_log_A, d_grad_log_B, d_grad_log_pi, st, nlaunch);
+    if (r != ACCEL_OK) return r;
+    return adj::finish_call("hmm_adjoint", P, max_T, st, nlaunch);
+}
+
+accel_status hmm_adjoint_forward(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets, int64_t S,
+                                 int64_t total_T, int64_t max_T, double* d_loglik, void* d_ws, size_t ws_bytes,
+                                 void* stream) {
+    adj::Plan P;
+    accel_status r = adj::setup("hmm_adjoint_forward", m, d_obs, d_offsets, S, total_T, max_T, d_ws, ws_bytes, P);
+    if (r != ACCEL_OK) return r;
+    cudaStream_t st = as_stream(stream);
+    r = adj::debug_checks(P, d_offsets, d_obs, total_T, st);
+    if (r != ACCEL_OK) return r;
+    ACCEL_CUDA_TRY(cudaMemsetAsync(P.ws + kStatusOff, 0, 4, st));
+    int nlaunch = 0;
+    r = adj::run_forward(P, m, d_loglik, st, nlaunch);
+    if (r != ACCEL_OK) return r;
+    return adj::finish_call("hmm_adjoint_forward", P, max_T, st, nlaunch);
+}
+
+accel_status hmm_adjoint_backward(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets, int64_t S,
+                                  int64_t total_T, int64_t max_T, const double* d_weights, float* d_grad_log_A,
+                                  float* d_grad_log_B, float* d_grad_log_pi, void* d_ws, size_t ws_bytes,
+                                  void* stream) {
+    adj::Plan P;
+    accel_status r = adj::setup("hmm_adjoint_backward", m, d_obs, d_offsets, S, total_T, max_T, d_ws, ws_bytes, P);
+    if (r != ACCEL_OK) return r;
+    ACCEL_REQUIRE(d_grad_log_A && d_grad_log_B, ACCEL_ERR_INVALID_ARG, "hmm_adjoint_backward: null pointer");
+    cudaStream_t st = as_stream(stream);
+    ACCEL_CUDA_TRY(cudaMemsetAsync(P.ws + kStatusOff, 0, 4, st));
+    int nlaunch = 0;
+    r = adj::run_backward(P, d_weights, d_grad_log_A, d_grad_log_B, d_grad_log_pi, st, nlaunch);
+    if (r != ACCEL_OK) return r;
+    return adj::finish_call("hmm_adjoint_backward", P, max_T, st, nlaunch);
 }
 
 }  // extern "C"

@@ -180,3 +180,34 @@ def test_single_step_sequences_and_debug_max_T():
         assert e.value.status == 2
     finally:
         api.set_debug(False)
+
+
+# ------------------------------------------------- forward -> adjoint hand-off (saved state)
+@pytest.mark.parametrize("K,M,S,lo,hi", [(256, 64, 24, 200, 2000), (37, 11, 13, 1, 130), (64, 8, 200, 5, 60)])
+def test_split_forward_backward_equals_one_call(K, M, S, lo, hi):
+    # hmm_adjoint_forward + hmm_adjoint_backward compute exactly what hmm_adjoint does (the same
+    # kernels in the same order), and one saved state serves two backward calls with other weights
+    p = synth.hmm_workload(K + 2 * S, K, M, S, "uniform", lo, hi)
+    logs, t, obs, off = _dev(p)
+    ll, saved = api.hmm_adjoint_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off)
+    for seed in (1, 2):
+        w = torch.from_numpy(synth.rng(seed).uniform(0.0, 2.0, size=S)).to(DEV)
+        g2 = api.hmm_adjoint_backward(t["log_A"], t["log_B"], t["log_pi"], obs, off, saved, weights=w)
+        g1 = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w)
+        for a, b in zip(g2, g1[:3]):
+            assert torch.equal(a, b)
+        assert torch.equal(ll, g1[3])
+
+
+def test_autograd_fp32_uses_one_forward_pass():
+    # with FP32 precision the autograd forward is the adjoint's checkpointed forward: its logL
+    # matches the log-space kernel and the oracle, and the backward matches the oracle
+    p = synth.hmm_workload(9, 64, 16, 30, "uniform", 20, 300)
+    logs, t, obs, off = _dev(p)
+    lA = t["log_A"].clone().requires_grad_(True)
+    ll = api.HMMLogLik.apply(lA, t["log_B"], t["log_pi"], obs, off)
+    ref_ll = api.hmm_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off)
+    assert torch.max(torch.abs(ll.detach() - ref_ll) / torch.abs(ref_ll)).item() <= 1e-5
+    ll.sum().backward()
+    _, rA, _, _ = ohmm.gradients_batch(p, params=ohmm.params_from_f32_logs(logs))
+    np.testing.assert_allclose(lA.grad.cpu().numpy(), rA, rtol=1e-4, atol=1e-6 * rA.sum(axis=1, keepdims=True).max())
