@@ -183,8 +183,9 @@ class Workload:
 
     def capture_seg(self, side):
         """The seg-reduce row (ragged marshal -> fused map + int64 segmented sum -> int64 max,
-        and the loop b = 2a over the flat data) captured into one CUDA graph over buffers
-        allocated once: the config-1 latency without a host round trip per call."""
+        and the loop b = 2a over the flat data, a parallel branch after the marshal) captured
+        into one CUDA graph over buffers allocated once: the config-1 latency without a host
+        round trip per call."""
         api, torch, dev = self.api, self.torch, self.dev
         lib = api.L.load()
         N, S = self.seg_N, self.seg_S
@@ -199,12 +200,23 @@ class Workload:
              "twice": torch.empty(N, dtype=torch.int32, device=dev)}
         self.seg_bufs = b
 
+        fork = torch.cuda.Stream()
+
         def body():
+            cur = torch.cuda.current_stream()
             api.accel_marshal_ragged_table(self.table_dev, out=(b["flat"], b["off"]), ws=b["ws_m"])
+            # the loop over the flat data does not depend on the reductions: a parallel branch
+            e0 = torch.cuda.Event()
+            e0.record(cur)
+            fork.wait_event(e0)
+            with torch.cuda.stream(fork):
+                api.accel_loop(api.LOOP_SCALE, b["twice"], b["flat"], 2.0)
             api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, b["flat"], b["off"], torch.int64, out=b["seg"],
                                 ws=b["ws_s"])
             api.accel_reduce(api.RED_MAX, b["seg"], out=b["max"], ws=b["ws_r"])
-            api.accel_loop(api.LOOP_SCALE, b["twice"], b["flat"], 2.0)
+            e1 = torch.cuda.Event()
+            e1.record(fork)
+            cur.wait_event(e1)
         torch.cuda.synchronize()
         g = api.Graph()
         n0 = lib.accel_launch_count()
