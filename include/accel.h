@@ -510,6 +510,14 @@ accel_status accel_graph_node_count(accel_graph g, int64_t* out);
  *     a_i = sum_j m_j (p_j - p_i) / (|p_j - p_i|^2 + eps^2)^(3/2)      (G = 1, FP32)
  *  d_x, d_y, d_z, d_m  device float32 [n] (structure of arrays, e.g. from
  *                      accel_marshal_records); outputs d_ax, d_ay, d_az float32 [n].
+ *  eps                 softening length, > 0 and finite with eps^-3 <= FLT_MAX / 4
+ *                      (eps >= about 1e-13); otherwise ACCEL_ERR_INVALID_ARG.  The j = i
+ *                      term is 0 * m_i eps^-3: it is 0 while m_i eps^-3 is finite in FP32.
+ *  Order of the sum (deterministic for a given n on a given device): the j range is split
+ *  into P contiguous parts (P in {1, 2, 4, 8}, chosen from n and the device's SM count);
+ *  within a part, the j's of each quarter of every 512-body tile are summed by parity, the
+ *  two parities added, then the four quarters in order; then the P parts in order.
+ *  One kernel launch (a thread-block cluster of P CTAs per 64 bodies).
  */
 accel_status pairwise_mapreduce(int32_t op, const float* d_x, const float* d_y, const float* d_z,
                                 const float* d_m, int64_t n, float eps, float* d_ax, float* d_ay,

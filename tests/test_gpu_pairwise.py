@@ -33,8 +33,10 @@ def _check(b, eps, idx):
     return a
 
 
-@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 1000, 4099])
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 511, 512, 513, 1000, 1025, 3000, 4099, 9001])
 def test_small_all_bodies(n):
+    # n < 2,048 runs one CTA per 64 bodies; 3,000, 4,099 and 9,001 split the j range over
+    # clusters of 2, 4 and 8 CTAs
     b = synth.bodies(n, n)
     _check(b, 1e-3, list(range(n)))
 
@@ -57,3 +59,27 @@ def test_two_body_closed_form():
     r2 = float(d @ d) + 1e-6
     np.testing.assert_allclose(a[0], 3.0 * d / r2 ** 1.5, rtol=2e-6)
     np.testing.assert_allclose(a[1], -2.0 * d / r2 ** 1.5, rtol=2e-6)
+
+
+@pytest.mark.parametrize("eps", [0.0, -1e-3, float("nan"), float("inf"), 1e-14])
+def test_eps_outside_its_range_is_rejected(eps):
+    # eps^-3 must be finite in FP32 (the j = i term is 0 * m_i eps^-3); nothing is launched
+    b = synth.bodies(0, 8)
+    with pytest.raises(RuntimeError, match="eps"):
+        _run(b, eps)
+
+
+def test_ragged_pointer_offsets():
+    # inputs that start at an element offset (not 16-byte aligned): the j tiles are loaded
+    # element by element, so any float alignment is accepted
+    b = synth.bodies(5, 1001)
+    aos = torch.from_numpy(b["aos"]).to(DEV)
+    x, y, z, m = api.accel_marshal_records(aos, [(0, F32), (4, F32), (8, F32), (12, F32)])
+    sub = [v[1:] for v in (x, y, z, m)]
+    ax, ay, az = api.pairwise_mapreduce(*sub, 1e-3)
+    a = torch.stack([ax, ay, az], 1).cpu().numpy().astype(np.float64)
+    pos, mass = b["aos"][1:, :3], b["aos"][1:, 3]
+    idx = list(range(1000))
+    ref = opair.accel(pos, mass, 1e-3, idx)
+    scale = np.maximum(np.linalg.norm(ref, axis=1), opair.term_scale(pos, mass, 1e-3, idx))
+    assert np.all(np.linalg.norm(a - ref, axis=1) <= 1e-4 * scale)
