@@ -938,16 +938,21 @@ __device__ __forceinline__ void st_peer(const Xchg& xc, uint32_t base, int row, 
     }
 }
 
-// End of a step's writes of parity par: local visibility, then the peer's `bytes`.  A wait
-// that gives up (2 s) records ACCEL_ERR_TIMEOUT; the kernel then finishes its bounded
-// loops with unusable values, and the caller sees the status.
-__device__ __forceinline__ void xchg_finish(Xchg& xc, int par, uint32_t bytes, int32_t* status) {
+// End of a step's writes of parity par: local visibility, then the peer's `bytes`.  Only the
+// threads with `wait` set -- the warps whose part of the next contraction reads the peer's
+// half of the vectors -- wait for them; the other warps start the next contraction on the
+// local half at once, which hides the exchange latency behind their work.  Everything else a
+// thread reads of the peer's data (the row sums) it reads after the contraction's CTA
+// barrier, which the waiting warps pass only after their wait.  A wait that gives up (2 s)
+// records ACCEL_ERR_TIMEOUT; the kernel then finishes its bounded loops with unusable
+// values, and the caller sees the status.
+__device__ __forceinline__ void xchg_finish(Xchg& xc, int par, uint32_t bytes, int32_t* status, bool wait) {
     __syncthreads();
     uint64_t* bar = par ? &xc.bar[1] : &xc.bar[0];
     if (threadIdx.x == 0) tc::mbar_arrive_expect_tx(bar, bytes);
     const uint32_t ph = (xc.phase >> par) & 1u;
     uint64_t t0 = 0;
-    for (uint32_t i = 0;; ++i) {
+    for (uint32_t i = 0; wait; ++i) {
         if (mbar_try_wait_cluster(bar, ph)) break;
         if ((i & 255) == 0) {
             const uint64_t now = tc::globaltimer_ns();
@@ -957,6 +962,10 @@ __device__ __forceinline__ void xchg_finish(Xchg& xc, int par, uint32_t bytes, i
     }
     xc.phase ^= 1u << par;
 }
+
+// Whether the calling thread's warp reads the peer's half of the vectors in the contraction
+// (warp w takes rows w K/8 .. of the matrix, so warps [4r, 4r + 4) read CTA r's half).
+__device__ __forceinline__ bool reads_peer_half(int rank) { return (int)(threadIdx.x >> 5) / (kNW / 2) != rank; }
 
 // Sum over the 16 threads of a sequence (a half warp), published as slot (rank) of parity
 // par in both CTAs.
@@ -1029,6 +1038,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     const int64_t cidx = blockIdx.x >> 1;
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;    // one thread per sequence
+    const bool peer_half = reads_peer_half(r);
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
     __shared__ __align__(8) uint64_t s_xbar[2];
@@ -1065,7 +1075,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
             ldv<S::EC>(p.pi + r * S::Kh + c0, o);
             fwd_epilogue<K>(V, xc, r, 0, g, c0, Tg > 0, gs.sym[0][g], o, 1.f);
         }
-        xchg_finish(xc, 0, xchg_bytes<K>(true), p.status);
+        xchg_finish(xc, 0, xchg_bytes<K>(true), p.status, peer_half);
         // the sequence's running exponent sum (used by the lead threads), steps to the next
         // checkpoint and its index
         int64_t E = 0;
@@ -1073,6 +1083,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
         for (int64_t t = 1; t <= Tmax; ++t) {
             const int cur = (int)((t - 1) & 1), nxt = (int)(t & 1);
             const int64_t tp = t - 1;
+            if (t < Tmax) contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
+            __syncthreads();                  // partials complete; the peer's half of X_{t-1} and
+                                              // its row sums visible to every thread
             const float c = row_sum(V.red, cur, g);
             int ex = 0;
             frexpf(c, &ex);
@@ -1101,8 +1114,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
                 }
             }
             if (t == Tmax) break;
-            contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
-            __syncthreads();
             float o[S::EC];
             gather<K>(V.part, g, c0, o);
             fwd_epilogue<K>(V, xc, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
@@ -1110,7 +1121,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
                 gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
                 ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
             }
-            xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
+            xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status, peer_half);
         }
         cl.sync();
         cl.sync();                        // the peer is done with this CTA's shared memory
@@ -1129,6 +1140,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     const int64_t cidx = blockIdx.x >> 1;
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
+    const bool peer_half = reads_peer_half(r);
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
     __shared__ __align__(8) uint64_t s_xbar[2];
@@ -1178,6 +1190,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
         cl.sync();
         for (int tt = 1; tt <= maxL; ++tt) {
             const int cur = (tt - 1) & 1, nxt = tt & 1;
+            if (tt < maxL) contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
+            __syncthreads();                  // partials complete; the peer's half of X_{tt-1} and
+                                              // its row sums visible to every thread
             float sc = 1.f;
             if (tt >= 2) {
                 const float c = row_sum(V.red, cur, g);
@@ -1195,8 +1210,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
                 }
             }
             if (tt == maxL) break;
-            contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
-            __syncthreads();
             float o[S::EC];
             gather<K>(V.part, g, c0, o);
             fwd_epilogue<K>(V, xc, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
@@ -1204,7 +1217,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
                 gs.sym[cur][tid] = ob_next;
                 ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
             }
-            xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status);
+            xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status, peer_half);
         }
         cl.sync();
         cl.sync();                        // the peer is done with this CTA's shared memory
@@ -1227,6 +1240,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     const int64_t cidx = blockIdx.x >> 1;
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
+    const bool peer_half = reads_peer_half(r);
     extern __shared__ __align__(16) char smem[];
     __shared__ GS gs;
     __shared__ __align__(8) uint64_t s_xbar[2];
@@ -1322,7 +1336,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             }
         };
         write_v(maxL - 1, prev_sym, maxL - 1 < Lg);
-        xchg_finish(xc, (maxL - 1) & 1, xchg_bytes<K>(false), p.status);
+        xchg_finish(xc, (maxL - 1) & 1, xchg_bytes<K>(false), p.status, peer_half);
         for (int tt = maxL - 1; tt >= 0; --tt) {
             const int buf = tt & 1;
             const int sym = gs.sym[buf][g], e_t = gs.eb[buf][g];
@@ -1376,7 +1390,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
                     ne = e_at(tid, tt - 2);
                 }
             }
-            if (tt > 0) xchg_finish(xc, (tt - 1) & 1, xchg_bytes<K>(false), p.status);
+            if (tt > 0) xchg_finish(xc, (tt - 1) & 1, xchg_bytes<K>(false), p.status, peer_half);
         }
         if (Lg > 0) stv<S::EC>(p.Rc + gs.seq[g] * K + jc, R);
         // gamma_0 of the sequences that started in this round, summed in a fixed order by one

@@ -211,3 +211,22 @@ def test_autograd_fp32_uses_one_forward_pass():
     ll.sum().backward()
     _, rA, _, _ = ohmm.gradients_batch(p, params=ohmm.params_from_f32_logs(logs))
     np.testing.assert_allclose(lA.grad.cpu().numpy(), rA, rtol=1e-4, atol=1e-6 * rA.sum(axis=1, keepdims=True).max())
+
+
+@pytest.mark.parametrize("K,M,S,lo,hi", [(64, 8, 200, 5, 60), (128, 16, 100, 10, 300)])
+def test_repeated_calls_are_bit_identical(K, M, S, lo, hi):
+    # many equal lengths (ties in the length sort); the workspace of each call is a fresh
+    # allocation whose stale contents differ, so nothing may depend on them or on timing
+    p = synth.hmm_workload(K + 3 * S, K, M, S, "uniform", lo, hi)
+    logs, t, obs, off = _dev(p)
+    w = torch.from_numpy(synth.rng(3).uniform(0.0, 2.0, size=S)).to(DEV)
+    ref = None
+    for rep in range(4):
+        junk = torch.rand(1 << 24, device=DEV) * rep      # changes what stale memory holds
+        del junk
+        g = [x.clone() for x in api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w)[:4]]
+        if ref is None:
+            ref = g
+        else:
+            for a, b in zip(g, ref):
+                assert torch.equal(a, b)
