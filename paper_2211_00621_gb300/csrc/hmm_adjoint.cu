@@ -71,8 +71,15 @@ struct Prm {
     float* gam;         // weighted posteriors gamma_t of the rows [S][Cmax][K] (cluster path)
     int32_t* osym;      // o_t of each row, -1 for none [S][Cmax] (cluster path)
     int64_t ncl;        // cluster path: number of CTA pairs
-    const int64_t* plan;  // cluster path: per pair (start0, size0, start1, size1) of its sequence
-                          // groups (size1 = 0: one group), or null: group_range with ncl groups
+    const int64_t* plan;  // cluster path: per pass (the forward, then round 0, 1, ...) and per pair
+                          // (start0, size0, start1, size1) of its sequence groups (size1 = 0: one
+                          // group), or null: group_range with ncl groups
+    // cluster path, per round r: the sorted positions of the sequences with a segment in round
+    // r (rlist[r][i], in sorted order), the first row of each in the round's row buffers
+    // (rrow[r][i]: rows are packed, each sequence taking its segment length), and their number
+    const int32_t* rlist;
+    const int32_t* rrow;
+    const int32_t* rcount;
 };
 
 __host__ __device__ __forceinline__ int seg_len(int64_t T) {
@@ -558,6 +565,7 @@ struct GS {
     int sym[2][kG];      // per step parity: the step's symbol (see the kernels)
     int eb[2][kG];       // per step parity: e_t (backward)
     int sym_end[kG];     // backward: symbol after the segment, -1 if none
+    int32_t rowb[kG];    // rounds: the sequence's first row in the round's row buffers
 };
 
 // Sorted positions [start, start + size) of group j when the S sequences (in order of
@@ -581,62 +589,94 @@ __device__ __forceinline__ void group_range_n(int64_t S, int64_t ngroups, int64_
     start = 8 * n8 + jj * base + (jj > firstbig ? jj - firstbig : 0);
     size = (int)(base + (jj >= firstbig ? 1 : 0));
 }
-__device__ __forceinline__ void group_range(const Prm& p, int64_t cidx, int64_t& start, int& size) {
-    group_range_n(p.S, p.ncl, cidx, start, size);
-}
 
-// The sequence groups CTA pair cidx runs, one after the other (1 or 2).
-__device__ __forceinline__ int cluster_groups(const Prm& p, int64_t cidx) {
-    return (p.plan && p.plan[cidx * 4 + 3] > 0) ? 2 : 1;
+// The sequence groups CTA pair cidx runs in pass `pass` (0: the forward; 1 + r: round r), one
+// after the other (1 or 2).  Groups are ranges of the pass's sequence list (the forward: all
+// sorted positions; round r: rlist[r]) of n entries.
+__device__ __forceinline__ const int64_t* pass_plan(const Prm& p, int pass) {
+    return p.plan ? p.plan + (int64_t)pass * p.ncl * 4 : nullptr;
 }
-__device__ __forceinline__ void cluster_group_range(const Prm& p, int64_t cidx, int gi, int64_t& start, int& size) {
-    if (p.plan) {
-        start = p.plan[cidx * 4 + 2 * gi];
-        size = (int)p.plan[cidx * 4 + 2 * gi + 1];
+__device__ __forceinline__ int cluster_groups(const Prm& p, int pass, int64_t cidx) {
+    const int64_t* pl = pass_plan(p, pass);
+    return (pl && pl[cidx * 4 + 3] > 0) ? 2 : 1;
+}
+__device__ __forceinline__ void cluster_group_range(const Prm& p, int pass, int64_t n, int64_t cidx, int gi,
+                                                    int64_t& start, int& size) {
+    const int64_t* pl = pass_plan(p, pass);
+    if (pl) {
+        start = pl[cidx * 4 + 2 * gi];
+        size = (int)pl[cidx * 4 + 2 * gi + 1];
     } else {
-        group_range(p, cidx, start, size);
+        group_range_n(n, p.ncl, cidx, start, size);
     }
 }
 
-// ---- group plan.  More groups than CTA pairs lets more of the longest sequences run in
+// ---- group plans.  More groups than CTA pairs lets more of the longest sequences run in
 // groups of 8 (one contraction pass per step instead of two); the surplus groups, the
 // shortest, then share a pair with another group and run after it.  A step of a group of g
 // sequences costs about (0.92 + ceil(g / GP)) contraction passes (measured: a pass of 8
-// sequences ~2,840 cycles at K = 256, the rest of the step ~2,620), so a pair's time is the
-// sum over its groups of T_max(group) x that cost.  One thread per candidate group count
-// nv in [nv_lo, nv_hi] splits the sorted sequences with group_range_n; the first ncl groups
-// (the longest) take one pair each and surplus group ncl + k joins pair ncl - 1 - k (the
-// least loaded first); the candidate with the smallest maximum load writes the plan.
+// sequences ~2,840 cycles at K = 256, the rest of the step ~2,620), so a pair's time in a pass
+// is the sum over its groups of (the group's longest step count) x that cost.  One plan per
+// pass: the forward (step counts T over all sequences) and every backward round r (step
+// counts = the segment lengths of round r over the sequences that have one).  The rounds need
+// their own plans: segment lengths grow like sqrt(T), so a grouping balanced for T leaves the
+// pairs that run two groups of short sequences as the slowest of every round.
+// One CTA per pass, one thread per candidate group count nv in [nv_lo, nv_hi]: it splits the
+// pass's list with group_range_n; the first ncl groups (the longest) take one pair each and
+// surplus group ncl + k joins pair ncl - 1 - k (the least loaded first); the candidate with
+// the smallest maximum load writes the plan.
 constexpr int kPlanThreads = 128;
 constexpr int kPlanMaxGroups = 256;
 constexpr int kPlanMaxSeq = 16 * kPlanMaxGroups;
 
-__device__ __forceinline__ float plan_cost(const int* sT, int64_t S, int64_t nv, int64_t j, int gp) {
-    int64_t st;
-    int sz;
-    group_range_n(S, nv, j, st, sz);
-    return (float)sT[st] * (0.92f + (float)((sz + gp - 1) / gp));   // sT[st]: the group's longest
+// step count of the sequence with T steps in pass `pass` (0: T; 1 + r: its round-r segment)
+__host__ __device__ __forceinline__ int64_t pass_steps(int64_t T, int pass) {
+    if (pass == 0) return T;
+    if (T <= 0) return 0;
+    const int64_t C = seg_len(T), n = (T + C - 1) / C, k = n - pass;   // segment n - 1 - r
+    if (k < 0) return 0;
+    const int64_t t1 = (k + 1) * C < T ? (k + 1) * C : T;
+    return t1 - k * C;
 }
 
-__global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int64_t nv_lo, int64_t nv_hi, int gp) {
-    __shared__ int sT[kPlanMaxSeq];                 // lengths in sorted order
+__device__ __forceinline__ float plan_cost(const int* sL, int64_t n, int64_t nv, int64_t j, int gp) {
+    if (j >= nv) return 0.f;
+    int64_t st;
+    int sz;
+    group_range_n(n, nv, j, st, sz);
+    int mx = 0;
+    for (int i = 0; i < sz; ++i) mx = sL[st + i] > mx ? sL[st + i] : mx;
+    return sz > 0 ? (float)mx * (0.92f + (float)((sz + gp - 1) / gp)) : 0.f;
+}
+
+// Block b plans pass b into plan[b][ncl][4].
+__global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int gp) {
+    __shared__ int sL[kPlanMaxSeq];                 // step counts in list order
     __shared__ float s_v[kPlanThreads];
     __shared__ int s_i[kPlanThreads];
-    const int t = threadIdx.x;
-    for (int64_t q = t; q < p.S; q += kPlanThreads) {
+    const int t = threadIdx.x, pass = blockIdx.x;
+    const int64_t n = pass == 0 ? p.S : p.rcount[pass - 1];
+    for (int64_t i = t; i < n; i += kPlanThreads) {
+        const int64_t q = pass == 0 ? i : p.rlist[(int64_t)(pass - 1) * p.S + i];
         const int64_t sq = p.order[q];
-        sT[q] = (int)(p.off[sq + 1] - p.off[sq]);
+        sL[i] = (int)pass_steps(p.off[sq + 1] - p.off[sq], pass);
     }
     __syncthreads();
-    const int64_t nv = nv_lo + t, ncl = p.ncl;
+    const int64_t ncl = p.ncl;
+    int64_t* pl = plan + (int64_t)pass * ncl * 4;
+    const int64_t lo16 = (n + 15) / 16;
+    const int64_t nv_lo = lo16 > (ncl < n ? ncl : n) ? lo16 : (ncl < n ? ncl : n);
+    int64_t nv_hi = 2 * ncl < n ? 2 * ncl : n;
+    if (nv_hi > nv_lo + kPlanThreads - 1) nv_hi = nv_lo + kPlanThreads - 1;
+    const int64_t nv = nv_lo + t;
     float worst = INFINITY;
-    if (nv <= nv_hi) {
-        const int64_t extra = nv - ncl;             // 0 <= extra <= ncl
+    if (n > 0 && nv <= nv_hi) {
+        const int64_t extra = nv > ncl ? nv - ncl : 0;   // 0 <= extra <= ncl
         worst = 0.f;
         for (int64_t c = 0; c < ncl; ++c) {
-            float l = plan_cost(sT, p.S, nv, c, gp);
+            float l = plan_cost(sL, n, nv, c, gp);
             const int64_t k = ncl - 1 - c;          // surplus group ncl + k joins pair c
-            if (k < extra) l += plan_cost(sT, p.S, nv, ncl + k, gp);
+            if (k < extra) l += plan_cost(sL, n, nv, ncl + k, gp);
             worst = fmaxf(worst, l);
         }
     }
@@ -654,28 +694,94 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int
         __syncthreads();
     }
     const int64_t best = nv_lo + s_i[0];
-    const int64_t extra = best - ncl;
+    const int64_t extra = best > ncl ? best - ncl : 0;
     for (int64_t c = t; c < ncl; c += kPlanThreads) {
-        int64_t st;
-        int sz;
-        group_range_n(p.S, best, c, st, sz);
-        plan[c * 4] = st;
-        plan[c * 4 + 1] = sz;
-        plan[c * 4 + 2] = 0;
-        plan[c * 4 + 3] = 0;
+        int64_t st = 0;
+        int sz = 0;
+        if (n > 0 && c < best) group_range_n(n, best, c, st, sz);
+        pl[c * 4] = st;
+        pl[c * 4 + 1] = sz;
+        pl[c * 4 + 2] = 0;
+        pl[c * 4 + 3] = 0;
         const int64_t k = ncl - 1 - c;
-        if (k < extra) {
-            group_range_n(p.S, best, ncl + k, st, sz);
-            plan[c * 4 + 2] = st;
-            plan[c * 4 + 3] = sz;
+        if (n > 0 && k < extra) {
+            group_range_n(n, best, ncl + k, st, sz);
+            pl[c * 4 + 2] = st;
+            pl[c * 4 + 3] = sz;
         }
     }
 }
 
-__device__ void load_gs(const Prm& p, GS& gs, int64_t gstart, int gsize) {
+// Round lists: block r writes rlist[r] (the sorted positions with a segment in round r, in
+// sorted order), rrow[r] (their first rows: the exclusive prefix sum of the segment lengths),
+// rcount[r] and rows[r] (the round's total rows).  Sequences longer than the workspace was
+// sized for are left out (the forward reports them).
+constexpr int kListThreads = 1024;
+__global__ void __launch_bounds__(kListThreads) k_round_lists(Prm p, int32_t* rlist, int32_t* rrow, int32_t* rcount) {
+    __shared__ int32_t s_n[32], s_l[32];
+    const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int32_t base_n = 0, base_rows = 0;
+    for (int64_t q0 = 0; q0 < p.S; q0 += kListThreads) {
+        const int64_t q = q0 + tid;
+        int32_t L = 0;
+        if (q < p.S) {
+            const int64_t sq = p.order[q];
+            const int64_t T = p.off[sq + 1] - p.off[sq];
+            if (seg_len(T) <= p.Cmax) L = (int32_t)pass_steps(T, 1 + r);
+        }
+        const int32_t a = L > 0 ? 1 : 0;
+        // block-wide inclusive scans of a and L (warps, then the warp totals)
+        int32_t sa = a, sl = L;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t va = __shfl_up_sync(0xffffffffu, sa, d), vl = __shfl_up_sync(0xffffffffu, sl, d);
+            if (lane >= d) { sa += va; sl += vl; }
+        }
+        if (lane == 31) { s_n[warp] = sa; s_l[warp] = sl; }
+        __syncthreads();
+        if (warp == 0) {
+            int32_t wa = s_n[lane], wl = s_l[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t va = __shfl_up_sync(0xffffffffu, wa, d), vl = __shfl_up_sync(0xffffffffu, wl, d);
+                if (lane >= d) { wa += va; wl += vl; }
+            }
+            s_n[lane] = wa;
+            s_l[lane] = wl;
+        }
+        __syncthreads();
+        const int32_t pa = (warp > 0 ? s_n[warp - 1] : 0) + sa - a;   // exclusive
+        const int32_t pl = (warp > 0 ? s_l[warp - 1] : 0) + sl - L;
+        if (a) {
+            rlist[(int64_t)r * p.S + base_n + pa] = (int32_t)q;
+            rrow[(int64_t)r * p.S + base_n + pa] = base_rows + pl;
+        }
+        base_n += s_n[31];
+        base_rows += s_l[31];
+        __syncthreads();                      // s_n / s_l are rewritten by the next chunk
+    }
+    if (tid == 0) {
+        rcount[r] = base_n;
+        p.rows[r] = base_rows;
+    }
+}
+
+// Group state of entries [gstart, gstart + gsize) of the pass's list: round < 0, the forward
+// (sorted positions); else round `round` (rlist / rrow of the round).
+__device__ void load_gs(const Prm& p, GS& gs, int round, int64_t gstart, int gsize) {
     const int g = threadIdx.x;
     if (g < kG) {
-        int64_t sq = g < gsize ? p.order[gstart + g] : -1;
+        int64_t pos = -1;
+        gs.rowb[g] = 0;
+        if (g < gsize) {
+            if (round < 0) {
+                pos = gstart + g;
+            } else {
+                pos = p.rlist[(int64_t)round * p.S + gstart + g];
+                gs.rowb[g] = p.rrow[(int64_t)round * p.S + gstart + g];
+            }
+        }
+        int64_t sq = pos >= 0 ? p.order[pos] : -1;
         int64_t T = sq >= 0 ? p.off[sq + 1] - p.off[sq] : 0;
         int C = sq >= 0 ? seg_len(T) : 1;
         if (sq >= 0 && C > p.Cmax) {
@@ -1048,12 +1154,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
     m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
     // the pair's sequence groups, one after the other
-    const int ngr = cluster_groups(p, cidx);
+    const int ngr = cluster_groups(p, 0, cidx);
     for (int gi = 0; gi < ngr; ++gi) {
         int64_t gstart;
         int gsize;
-        cluster_group_range(p, cidx, gi, gstart, gsize);
-        load_gs(p, gs, gstart, gsize);
+        cluster_group_range(p, 0, p.S, cidx, gi, gstart, gsize);
+        load_gs(p, gs, -1, gstart, gsize);
         __syncthreads();
         int ob_next = 0;                      // thread g < 16: o_{t+1} for the next symbol write
         if (tid < kG) {
@@ -1150,12 +1256,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
     // the pair's sequence groups, one after the other
-    const int ngr = cluster_groups(p, cidx);
+    const int64_t nlist = p.rcount[round];
+    const int ngr = cluster_groups(p, 1 + round, cidx);
     for (int gi = 0; gi < ngr; ++gi) {
         int64_t gstart;
         int gsize;
-        cluster_group_range(p, cidx, gi, gstart, gsize);
-        load_gs(p, gs, gstart, gsize);
+        cluster_group_range(p, 1 + round, nlist, cidx, gi, gstart, gsize);
+        load_gs(p, gs, round, gstart, gsize);
         __syncthreads();
         round_bounds_gs(gs, round);
         __syncthreads();
@@ -1163,21 +1270,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
     #pragma unroll
         for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
         const int Lg = (int)gs.L[g];
-        const int64_t rowb = (gstart + g) * p.Cmax;
+        const int64_t rowb = gs.rowb[g];
         // row 0: the checkpoint itself, into the local vector buffer and the P row
         for (int idx = tid; idx < kG * K / 4; idx += kT) {
             const int gg = idx / (K / 4), cc = 4 * (idx - gg * (K / 4));
             float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gs.L[gg] > 0) {
                 sv = *reinterpret_cast<const float4*>(p.cp + (gs.seq[gg] * p.Cmax + gs.t0[gg] / gs.C[gg]) * K + cc);
-                if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + ((gstart + gg) * p.Cmax) * K + cc) = sv;
+                if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + (int64_t)gs.rowb[gg] * K + cc) = sv;
             }
             *reinterpret_cast<float4*>(V.sX + gg * K + pcol(cc)) = sv;
         }
         int ob_next = 0;
         if (tid < kG) {
             const int q = tid;
-            if (gs.L[q] > 0 && r == 0) p.ebuf[(gstart + q) * p.Cmax] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
+            if (gs.L[q] > 0 && r == 0) p.ebuf[gs.rowb[q]] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
             const int64_t b0 = gs.o0[q] + gs.t0[q];
             gs.sym[1][q] = gs.L[q] > 1 ? p.obs[b0 + 1] : 0;
             ob_next = gs.L[q] > 2 ? p.obs[b0 + 2] : 0;
@@ -1250,12 +1357,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     m.load(p.At, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
     // the pair's sequence groups, one after the other
-    const int ngr = cluster_groups(p, cidx);
+    const int64_t nlist = p.rcount[round];
+    const int ngr = cluster_groups(p, 1 + round, cidx);
     for (int gi = 0; gi < ngr; ++gi) {
         int64_t gstart;
         int gsize;
-        cluster_group_range(p, cidx, gi, gstart, gsize);
-        load_gs(p, gs, gstart, gsize);
+        cluster_group_range(p, 1 + round, nlist, cidx, gi, gstart, gsize);
+        load_gs(p, gs, round, gstart, gsize);
         __syncthreads();
         round_bounds_gs(gs, round);
         __syncthreads();
@@ -1263,23 +1371,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     #pragma unroll
         for (int q = 0; q < kG; ++q) maxL = gs.L[q] > maxL ? (int)gs.L[q] : maxL;
         const int Lg = (int)gs.L[g];
-        const int64_t rowb = (gstart + g) * p.Cmax;
+        const int64_t rowb = gs.rowb[g];
         const int jc = r * S::Kh + c0;        // first state of the thread's epilogue block
-        if (tid < kG && gs.L[tid] > 0) atomicMax(&p.rows[round], (int32_t)((gstart + tid + 1) * p.Cmax));
-        // rows that must read as zero / carry no symbol: all rows of a sequence whose last
-        // segment was done in the previous round, rows past the segment of an active one
-        if (gs.seq[g] >= 0 && (gs.just_done[g] || Lg > 0)) {
-            float z[S::EC];
-    #pragma unroll
-            for (int e = 0; e < S::EC; ++e) z[e] = 0.f;
-            for (int tt = Lg; tt < p.Cmax; ++tt) stv<S::EC>(p.Q + (rowb + tt) * K + jc, z);
-        }
-        if (r == 0 && tid < kG) {
-            const int q = tid;
-            const int64_t rb = (gstart + q) * p.Cmax;
-            const int64_t from = (gs.seq[q] >= 0 && (gs.just_done[q] || gs.L[q] > 0)) ? gs.L[q] : p.Cmax;
-            for (int64_t tt = from; tt < p.Cmax; ++tt) p.osym[rb + tt] = -1;
-        }
+        // (the round's rows are packed: every row below rows[round] belongs to a step of a
+        // sequence in the round and is written below, so no row needs clearing)
         if (maxL == 0) {                      // no remote access made; the peer skips it too
             __syncthreads();                  // (gs is rewritten for the next group)
             continue;
@@ -1288,7 +1383,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             const int64_t t = gs.t0[q] + tt;
             return (tt <= gs.L[q] && t < gs.T[q] && gs.seq[q] >= 0) ? p.obs[gs.o0[q] + t] : -1;
         };
-        auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(gstart + q) * p.Cmax + tt] : 0; };
+        auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(int64_t)gs.rowb[q] + tt] : 0; };
         int nsym = -1, ne = 0;                // thread q < 16: scalars of step tt-1, loaded one step ahead
         if (tid < kG) {
             const int q = tid;
@@ -1400,7 +1495,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             const int j = r * S::Kh + cc;
             float s = 0.f;
             for (int q = 0; q < kG; ++q)
-                if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[((gstart + q) * p.Cmax) * K + j];
+                if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[(int64_t)gs.rowb[q] * K + j];
             p.pig[cidx * K + j] += s;
         }
         cl.sync();                        // the peer is done with this CTA's shared memory
@@ -1424,7 +1519,8 @@ inline Kernels kernels_for(int K) {
 }  // namespace clu
 
 struct Layout {
-    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, plan, order, total;
+    size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, plan, rlist, rrow,
+        rcount, order, total;
     int Cmax;
     int64_t ngroups;
     int64_t npig;       // rows of pig: one per group of either path (clusters: up to S)
@@ -1457,7 +1553,11 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.gam = take((size_t)S * L.Cmax * K * 4);
     L.osym = take((size_t)S * L.Cmax * 4);
     L.cntp = take((size_t)(ns_max > kCntSplit ? ns_max : kCntSplit) * K * M * 4);
-    L.plan = take((size_t)(adj::clu::kPlanMaxGroups / 2) * 4 * 8);     // group plan of the CTA pairs
+    // group plans of the CTA pairs: the forward and every round
+    L.plan = take((size_t)(L.Cmax + 1) * (adj::clu::kPlanMaxGroups / 2) * 4 * 8);
+    L.rlist = take((size_t)L.Cmax * S * 4);
+    L.rrow = take((size_t)L.Cmax * S * 4);
+    L.rcount = take((size_t)L.Cmax * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
     return L;
@@ -1521,6 +1621,8 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     P.L = layout(K, M, S, max_T);
     const Layout& L = P.L;
     ACCEL_REQUIRE(ws_bytes >= L.total, ACCEL_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", who, ws_bytes, L.total);
+    ACCEL_REQUIRE(S * (int64_t)L.Cmax <= (int64_t)INT32_MAX, ACCEL_ERR_UNSUPPORTED,
+                  "%s: S x ceil(sqrt(max_T)) = %lld rows exceeds 2^31-1", who, (long long)(S * (int64_t)L.Cmax));
     P.sm_b = smem_bwd(K, M, L.Cmax);
     ACCEL_REQUIRE(P.sm_b <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED,
                   "%s: emission table too large for shared memory (K=%d, M=%d)", who, K, M);
@@ -1535,6 +1637,9 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     p.osym = (int32_t*)(ws + L.osym);
     p.ncl = 0;
     p.plan = nullptr;
+    p.rlist = (int32_t*)(ws + L.rlist);
+    p.rrow = (int32_t*)(ws + L.rrow);
+    p.rcount = (int32_t*)(ws + L.rcount);
     P.cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
     p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = nullptr;
@@ -1587,13 +1692,13 @@ static accel_status run_forward(Plan& P, const accel_hmm_model* m, double* d_log
     if (r != ACCEL_OK) return r;
     nlaunch += 3;
     if (P.use_cluster) {
+        // the backward rounds' sequence lists and packed row offsets (they depend on the
+        // lengths only, so they belong to the saved state), then the plans of every pass
+        clu::k_round_lists<<<(unsigned)L.Cmax, clu::kListThreads, 0, st>>>(p, (int32_t*)p.rlist, (int32_t*)p.rrow,
+                                                                          (int32_t*)p.rcount);
+        ++nlaunch;
         if (P.planned) {
-            const int64_t ncl_min = (p.S + clu::kG - 1) / clu::kG;
-            const int64_t ncl_sm = p.ncl;
-            const int64_t nv_lo = ncl_min > ncl_sm ? ncl_min : ncl_sm;
-            int64_t nv_hi = 2 * ncl_sm < p.S ? 2 * ncl_sm : p.S;
-            if (nv_hi > nv_lo + clu::kPlanThreads - 1) nv_hi = nv_lo + clu::kPlanThreads - 1;
-            clu::k_plan<<<1, clu::kPlanThreads, 0, st>>>(p, (int64_t*)p.plan, nv_lo, nv_hi, K == 256 ? 8 : 16);
+            clu::k_plan<<<(unsigned)(L.Cmax + 1), clu::kPlanThreads, 0, st>>>(p, (int64_t*)p.plan, K == 256 ? 8 : 16);
             ++nlaunch;
         }
         const unsigned grid = (unsigned)(2 * p.ncl);
@@ -1624,14 +1729,15 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cnt, 0, (size_t)L.ngroups * K * M * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.pig, 0, (size_t)L.npig * K * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Upart, 0, (size_t)P.nsU * K * K * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.rows, 0, (size_t)L.Cmax * 4, st));
     ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.cntp, 0, (size_t)P.nsC * K * M * 4, st));
-    // every row starts with no symbol: the rows of a sequence skipped as longer than max_T are
-    // never written by the cluster kernels, and the count kernels index tables by osym
-    ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.osym, 0xff, (size_t)S * L.Cmax * 4, st));
-    if (P.counts_tc) ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.gam, 0, (size_t)S * L.Cmax * K * 4, st));
+    if (!P.use_cluster) {
+        // the streaming kernels keep Cmax row slots per sequence and clear the ones they
+        // leave; the cluster path packs each round's rows (all written in the round) and its
+        // row counts were set by the forward phase
+        ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.P, 0, (size_t)S * L.Cmax * K * 4, st));
+        ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.Q, 0, (size_t)S * L.Cmax * K * 4, st));
+        ACCEL_CUDA_TRY(cudaMemsetAsync(ws + L.rows, 0, (size_t)L.Cmax * 4, st));
+    }
     if (S > 0) {
         if (P.use_cluster) {
             const unsigned grid = (unsigned)(2 * p.ncl);
