@@ -165,13 +165,14 @@ class Workload:
         api, torch = self.api, self.torch
         q = self.bf16
         ms, cfg = api.hmm_autotune(q["log_A"], q["log_B"], q["log_pi"], q["obs"], q["offsets"], cache_path=tune_cache)
-        self.tuned = {"split": cfg[0], "rows": cfg[1], "pair": cfg[2], "best_ms": ms}
+        self.tuned = {"split": cfg[0], "rows": cfg[1], "pair": cfg[2], "units": cfg[3], "best_ms": ms}
         lib = api.L.load()
         m = api._model(q["log_A"], q["log_B"], q["log_pi"])
         nb = lib.hmm_forward_workspace_size(C.byref(m), q["S"], q["obs"].numel(), api.HMM_BF16_SCALED)
         self.bf16_ws = torch.empty(nb, dtype=torch.uint8, device=self.dev)
         self.bf16_out = torch.empty(q["S"], dtype=torch.float64, device=self.dev)
         side = torch.cuda.Stream()
+        self.side = torch.cuda.Stream()     # the overlapped BF16 row of a step
         torch.cuda.synchronize()
         g = api.Graph()
         g.capture(lambda: api.hmm_forward(q["log_A"], q["log_B"], q["log_pi"], q["obs"], q["offsets"],
@@ -232,9 +233,23 @@ class Workload:
             n += 2 * self.adj["K"] * self.adj["sumT"]
         return n
 
-    # one step, device-resident inputs; `ev` collects per-row (start, end) events
+    # one step, device-resident inputs.  With `ev` (per-row (start, end) events) the rows run one
+    # after another on the current stream, so each row's time is its own.  Without it the
+    # step overlaps independent rows: the batched BF16 forward -- a latency-bound persistent
+    # launch whose CTAs fill the register files of the SMs they hold and leave the others
+    # idle -- runs on a second stream while the seg-reduce, plain FP32 and all-pairs rows run
+    # on the rest of the GPU; the adjoint and the re-estimation, which want every SM, follow.
     def step(self, ev=None):
         api, torch = self.api, self.torch
+        overlap = ev is None and self.bf16_graph is not None
+        cur = torch.cuda.current_stream()
+        if overlap:
+            e_in = torch.cuda.Event()
+            e_in.record(cur)
+            self.side.wait_event(e_in)
+            self.bf16_graph.launch(stream=self.side)
+            e_bf16 = torch.cuda.Event()
+            e_bf16.record(self.side)
 
         def mark(name, fn):
             if ev is None:
@@ -264,7 +279,14 @@ class Workload:
         out["plain"] = mark("hmm_plain", lambda: api.hmm_forward(p["log_A"], p["log_B"], p["log_pi"], p["obs"],
                                                                  p["offsets"], api.HMM_FP32_LOG))
         q = self.bf16
-        if self.bf16_graph is not None:
+        if overlap:
+            def allpairs_row():
+                x, y, z, m = api.accel_marshal_records(self.aos, self.fields)
+                return api.pairwise_mapreduce(x, y, z, m, self.eps)
+            out["allpairs"] = allpairs_row()
+            cur.wait_event(e_bf16)
+            out["bf16"] = self.bf16_out
+        elif self.bf16_graph is not None:
             def bf16():
                 self.bf16_graph.launch()
                 return self.bf16_out
@@ -285,10 +307,11 @@ class Workload:
             out["mstep"] = mark("hmm_mstep", lambda: api.hmm_mstep(a["log_A"], a["log_B"], a["log_pi"], g[0], g[1],
                                                                    g[2]))
 
-        def allpairs():
-            x, y, z, m = api.accel_marshal_records(self.aos, self.fields)
-            return api.pairwise_mapreduce(x, y, z, m, self.eps)
-        out["allpairs"] = mark("allpairs", allpairs)
+        if not overlap:
+            def allpairs():
+                x, y, z, m = api.accel_marshal_records(self.aos, self.fields)
+                return api.pairwise_mapreduce(x, y, z, m, self.eps)
+            out["allpairs"] = mark("allpairs", allpairs)
         return out
 
     # end-to-end step: inputs copied from pinned host memory, results read back
@@ -301,10 +324,25 @@ class Workload:
         s = api.accel_segreduce(api.RED_ADD, api.MAP_SQ_PLUS_ONE, flat, off, torch.int64)
         m = api.accel_reduce(api.RED_MAX, s)
         res += [s, m]
-        for name, prec in (("plain", api.HMM_FP32_LOG), ("bf16", api.HMM_BF16_SCALED)):
-            h = host[name]
+        # the BF16 row on the second stream, beside the rows that follow (as in step())
+        e_in = torch.cuda.Event()
+        e_in.record(st)
+        self.side.wait_event(e_in)
+        with torch.cuda.stream(self.side):
+            h = host["bf16"]
             d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
-            res.append(api.hmm_forward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"], prec))
+            r_bf16 = api.hmm_forward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"], api.HMM_BF16_SCALED)
+            e_bf16 = torch.cuda.Event()
+            e_bf16.record(self.side)
+        h = host["plain"]
+        d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
+        res.append(api.hmm_forward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"], api.HMM_FP32_LOG))
+        aos = host["aos"].to(dev, non_blocking=True)
+        x, y, z, mm = api.accel_marshal_records(aos, self.fields)
+        res += list(api.pairwise_mapreduce(x, y, z, mm, self.eps))
+        st.wait_event(e_bf16)
+        r_bf16.record_stream(st)
+        res.append(r_bf16)
         if self.adj is not None:
             h = host["adj"]
             d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
@@ -312,9 +350,6 @@ class Workload:
                                               max_T=self.adj["maxT"], want_loglik=True)
             th, nw = api.hmm_mstep(d["log_A"], d["log_B"], d["log_pi"], gA, gB, gpi)
             res += [gA, gB, gpi, ll, *th, *nw]
-        aos = host["aos"].to(dev, non_blocking=True)
-        x, y, z, mm = api.accel_marshal_records(aos, self.fields)
-        res += list(api.pairwise_mapreduce(x, y, z, mm, self.eps))
         outs = [torch.empty(r.shape, dtype=r.dtype, pin_memory=True) for r in res]
         for o, r in zip(outs, res):
             o.copy_(r, non_blocking=True)
@@ -874,7 +909,7 @@ def main():
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         s.record()
-        last = W.step(ev)
+        last = W.step()
         e.record()
         e.synchronize()
         step_ms.append(s.elapsed_time(e))
@@ -890,6 +925,11 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    # per-row times: the same step with its rows one after another (untimed by the step)
+    for _ in range(3):
+        flush.zero_()
+        W.step(ev)
+    torch.cuda.synchronize()
     row_ms = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
     work = W.state_steps()
     ms, value = aggregate_ranks(sum(step_ms) / len(step_ms), work, world, allreduce_max)
@@ -1000,6 +1040,10 @@ def main():
                                    "T U[200,2000]" + ("" if with_adj else " (adjoint not built: skipped)") +
                                    "; all-pairs N=65536",
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
+                       "schedule": "two streams: the batched BF16 forward (a CUDA graph of its 5 kernels) "
+                                   "beside the seg-reduce, plain FP32 and all-pairs rows, then the adjoint "
+                                   "and the re-estimation; per-row times in `rows` come from the same "
+                                   "step run row after row",
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
             "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweeps, "marshal_sweep": msweeps,
             "compare": compare, "rows": rows, "roofline": roof,

@@ -450,8 +450,10 @@ accel_status hmm_mstep(const accel_hmm_model* m, const float* d_grad_log_A, cons
  * hmm_autotune -- choose the launch configuration of the BF16 tensor-core forward (column
  * parts per row: 8 or 16 warps; sequence rows per tile: 128, 64 or 32; a tile on one CTA or
  * on a cluster of two or four CTAs that split the state columns) by timing each
- * candidate with CUDA events on these inputs, and remember the fastest for (device, K, M,
- * floor(log2 S)); hmm_forward then launches with it.  `cache_path` (may be NULL) names a
+ * candidate with CUDA events on these inputs, then the number of persistent work units of
+ * the fastest (the fewest of all that fit, 3/4, 1/2, 3/8 and 1/4 of them within 1 % of its
+ * time, so that a latency-bound forward leaves SMs free for other streams), and remember the
+ * result for (device, K, M, floor(log2 S)); hmm_forward then launches with it.  `cache_path` (may be NULL) names a
  * file of JSON lines: an entry for the same key is reused without timing, a new result is
  * appended.  Arguments as hmm_forward (d_loglik receives the last timed run's result).
  * Synchronizes the stream.  h_best_ms (may be NULL) receives the best time (0 when taken from
@@ -462,10 +464,12 @@ accel_status hmm_autotune(const accel_hmm_model* m, int32_t precision, const int
                           void* d_ws, size_t ws_bytes, const char* cache_path, float* h_best_ms,
                           void* stream);
 /* The configuration hmm_forward(ACCEL_HMM_BF16_SCALED) uses for these sizes: column parts
- * per row, rows per tile, and (h_pair, may be NULL) how a tile is split over a thread-block
- * cluster: 0 one CTA, 1 two CTAs, 2 four CTAs (each holding K/2 or K/4 state columns). */
+ * per row, rows per tile, (h_pair, may be NULL) how a tile is split over a thread-block
+ * cluster: 0 one CTA, 1 two CTAs, 2 four CTAs (each holding K/2 or K/4 state columns), and
+ * (h_units, may be NULL) the persistent work units launched (CTAs or clusters; 0: all that
+ * fit). */
 accel_status hmm_tuned_config(int32_t K, int32_t M, int64_t S, int32_t* h_split, int32_t* h_rows,
-                              int32_t* h_pair);
+                              int32_t* h_pair, int32_t* h_units);
 
 /*
  * accel_pair_histogram -- all-pairs histogram of angular separations (the two-point angular

@@ -83,7 +83,7 @@ SIGNATURES = {
     "accel_pair_histogram": (i32, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, vp]),
     "hmm_mstep": (i32, [C.POINTER(accel_hmm_model), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "hmm_autotune": (i32, [C.POINTER(accel_hmm_model), i32, vp, vp, i64, i64, vp, vp, sz, C.c_char_p, vp, vp]),
-    "hmm_tuned_config": (i32, [i32, i32, i64, vp, vp, vp]),
+    "hmm_tuned_config": (i32, [i32, i32, i64, vp, vp, vp, vp]),
     "accel_graph_begin": (i32, [vp]),
     "accel_graph_end": (i32, [vp, vp]),
     "accel_graph_launch": (i32, [vp, vp]),

@@ -436,8 +436,9 @@ def hmm_mstep(log_A, log_B, log_pi, grad_log_A, grad_log_B, grad_log_pi, want_gr
 def hmm_autotune(log_A, log_B, log_pi, obs, offsets, precision=L.HMM_BF16_SCALED, cache_path=None, ws=None):
     """Times the BF16 forward's launch configurations on these inputs and keeps the fastest
     for later hmm_forward calls (and in `cache_path`, JSON lines, if given).  Returns
-    (best ms or 0.0 if cached, (split, rows, pair)); pair = 1 when a tile of sequences runs
-    on a cluster of two CTAs that split the state columns."""
+    (best ms or 0.0 if cached, (split, rows, pair, units)); pair = 1 (2) when a tile of
+    sequences runs on a cluster of two (four) CTAs that split the state columns; units = the
+    persistent CTAs or clusters launched (0: all that fit)."""
     lib = L.load()
     m = _model(log_A, log_B, log_pi)
     S = offsets.numel() - 1
@@ -449,9 +450,10 @@ def hmm_autotune(log_A, log_B, log_pi, obs, offsets, precision=L.HMM_BF16_SCALED
     path = cache_path.encode() if cache_path else None
     L.check("hmm_autotune", lib.hmm_autotune(C.byref(m), precision, _ptr(obs), _ptr(offsets), S, obs.numel(),
                                              _ptr(out), _ptr(ws), ws.numel(), path, C.byref(best), _stream()))
-    split, rows, pair = C.c_int32(0), C.c_int32(0), C.c_int32(0)
-    L.check("hmm_tuned_config", lib.hmm_tuned_config(m.K, m.M, S, C.byref(split), C.byref(rows), C.byref(pair)))
-    return best.value, (split.value, rows.value, pair.value)
+    split, rows, pair, units = C.c_int32(0), C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    L.check("hmm_tuned_config", lib.hmm_tuned_config(m.K, m.M, S, C.byref(split), C.byref(rows), C.byref(pair),
+                                                     C.byref(units)))
+    return best.value, (split.value, rows.value, pair.value, units.value)
 
 
 class Graph:

@@ -31,6 +31,7 @@ struct TcConfig {
     int split;
     int rows;
     int pair;
+    int units;      // persistent work units launched (CTAs, or clusters when pair > 0); 0: all that fit
 };
 bool tc_cl_supported(int K, int M, int rows, int split, int nc);
 TcConfig tuned_config(int K, int M, int64_t S);

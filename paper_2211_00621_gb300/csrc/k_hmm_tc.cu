@@ -814,7 +814,8 @@ static accel_status tc_forward_cluster(const accel_hmm_model* mdl, const int32_t
     const int maxcl = pair_max_clusters(kern, P.smem_bytes, threads, NC);
     ACCEL_REQUIRE(maxcl > 0, ACCEL_ERR_UNSUPPORTED, "hmm_forward(bf16): no cluster of %d CTAs fits the device", NC);
     const int64_t tiles = (S + cfg.rows - 1) / cfg.rows;
-    const int ncl = (int)(tiles < maxcl ? tiles : maxcl);
+    int ncl = (int)(tiles < maxcl ? tiles : maxcl);
+    if (cfg.units > 0 && cfg.units < ncl) ncl = cfg.units;
     cudaLaunchConfig_t lc = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -861,6 +862,7 @@ accel_status tc_forward_cfg(const accel_hmm_model* mdl, const int32_t* obs, cons
     if (r != ACCEL_OK) return r;
     int64_t tiles = (S + cfg.rows - 1) / cfg.rows;
     int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+    if (cfg.units > 0 && cfg.units < grid) grid = cfg.units;
     // rows <= 64 per CTA: M = 64 tiles
     auto kern = cfg.split == 4 ? (cfg.rows <= 64 ? k_hmm_tc<4, 64> : k_hmm_tc<4, 128>)
                                : (cfg.rows <= 64 ? k_hmm_tc<2, 64> : k_hmm_tc<2, 128>);

@@ -140,17 +140,21 @@ def test_single_step_sequences():
         _check(p, prec)
 
 
-def _force_config(tmp_path, K, M, S, split, rows, t, pair=0):
+def _force_config(tmp_path, K, M, S, split, rows, t, pair=0, units=None):
     import json as _json
     path = str(tmp_path / "tune.jsonl")
     sl = 0
     while (1 << (sl + 1)) <= S:
         sl += 1
+    entry = {"kernel": "hmm_forward_bf16", "device": torch.cuda.get_device_name(), "K": K, "M": M,
+             "S_log2": sl, "split": split, "rows": rows, "pair": pair}
+    if units is not None:                  # lines without "units" launch all units
+        entry["units"] = units
+    entry["ms"] = 1.0
     with open(path, "w") as f:
-        f.write(_json.dumps({"kernel": "hmm_forward_bf16", "device": torch.cuda.get_device_name(), "K": K, "M": M,
-                             "S_log2": sl, "split": split, "rows": rows, "pair": pair, "ms": 1.0}) + "\n")
+        f.write(_json.dumps(entry) + "\n")
     ms, cfg = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], t["obs"], t["off"], cache_path=path)
-    assert ms == 0.0 and cfg == (split, rows, pair)
+    assert ms == 0.0 and cfg == (split, rows, pair, units or 0)
 
 
 @pytest.mark.parametrize("split,rows", [(2, 128), (4, 128), (4, 32), (2, 64), (4, 64), (2, 32)])
@@ -191,7 +195,7 @@ def test_autotune_times_candidates_and_caches(tmp_path):
     logs, t, obs, off = _prep(p)
     path = str(tmp_path / "tune.jsonl")
     ms, cfg = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off, cache_path=path)
-    assert ms > 0.0 and cfg[0] in (2, 4) and cfg[1] in (32, 64, 128) and cfg[2] in (0, 1)
+    assert ms > 0.0 and cfg[0] in (2, 4) and cfg[1] in (32, 64, 128) and cfg[2] in (0, 1, 2) and cfg[3] >= 0
     with open(path) as f:
         assert "hmm_forward_bf16" in f.read()
     ms2, cfg2 = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off, cache_path=path)
@@ -221,3 +225,14 @@ def test_graph_capture_replays_the_persistent_launch():
         g.launch()
         torch.cuda.synchronize()
         assert torch.equal(out, direct)
+
+
+# fewer persistent work units than fit (the autotuner's choice for a latency-bound mix): the
+# queue hands every tile to one of the launched CTAs / clusters all the same
+@pytest.mark.parametrize("pair,units", [(0, 1), (0, 5), (1, 1), (1, 3), (2, 2)])
+def test_bf16_tc_fewer_work_units(tmp_path, pair, units):
+    p = synth.hmm_workload(16, 256, 40, 700, "loguniform", 1, 400)
+    logs, t, obs, off = _prep(p)
+    t["obs"], t["off"] = obs, off
+    _force_config(tmp_path, 256, 40, 700, 2, 64, t, pair=pair, units=units)
+    _check(p, acc.HMM_BF16_SCALED)

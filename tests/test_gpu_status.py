@@ -138,7 +138,7 @@ def _force_single_cta(tmp_path, K, M, S, t, obs, off, split=2, rows=64):
         f.write(json.dumps({"kernel": "hmm_forward_bf16", "device": torch.cuda.get_device_name(), "K": K, "M": M,
                             "S_log2": sl, "split": split, "rows": rows, "pair": 0, "ms": 1.0}) + "\n")
     ms, cfg = api.hmm_autotune(t["log_A"], t["log_B"], t["log_pi"], obs, off, cache_path=path)
-    assert ms == 0.0 and cfg == (split, rows, 0)
+    assert ms == 0.0 and cfg == (split, rows, 0, 0)
 
 
 def test_watchdog_stops_single_cta_bf16_forward_with_timeout(status_word, tmp_path):
