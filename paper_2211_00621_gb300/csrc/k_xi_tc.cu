@@ -17,11 +17,17 @@
 // hi_a hi_b + hi_a lo_b + lo_a hi_b; the dropped lo_a lo_b term is below 2^-21 relative.
 // The one-hot operand needs no split.
 //
-// Operands are staged by all 256 threads (coalesced global loads, split, 16-byte shared
-// stores into the no-swizzle K-major canonical layout: core matrices of 8 rows x 4 values),
-// up to three stages deep; the loads of the next two chunks are in flight (in registers)
-// while the current chunk is split and stored.  One thread issues the MMAs of a stage and commits them
-// to the stage's mbarrier, which the threads wait on (bounded) before they refill it.
+// Operand path of a chunk of kKC = 16 reduction rows: the chunk's rows of Q (all K columns:
+// one contiguous bulk copy, completing on the raw tile's mbarrier) and of P and Gamma (the
+// CTA's 128 columns: 16-byte cp.async pieces, one commit group per chunk) go into a raw
+// shared-memory tile kRawStages chunks ahead; all 256 threads then split the raw values into
+// the hi / lo operand blocks of a split stage (the no-swizzle K-major canonical layout: core
+// matrices of 8 rows x 4 values) and build the one-hot block, and one thread issues the
+// chunk's MMAs and commits them to the split stage's mbarrier, which the threads wait on
+// (bounded) before they refill that stage.  The rows are the round's packed rows, read once
+// from global memory per CTA with no per-element address arithmetic; thread 0 keeps the
+// rows of the next kPrefetch chunks on their way into L2, so that the copies into the raw
+// tiles, only kRawStages chunks ahead for lack of shared memory, wait on L2 and not on DRAM.
 #include "hmm_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -30,9 +36,13 @@ namespace hmm {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kSplitThreads = 512;      // warps 0-15: copies, operand split, epilogue
+constexpr int kThreads = kSplitThreads + 32;   // + warp 16: issues the MMAs
+constexpr int kColParts = kSplitThreads / 128; // epilogue: column parts per TMEM lane quarter
 constexpr int kKC = 16;                 // reduction rows per stage
-constexpr int kMaxStages = 3;
+constexpr int kMaxStages = 3;          // split stages
+constexpr int kRawStages = 2;          // raw tiles (bulk-copy targets)
+constexpr int kPrefetch = 6;           // chunks brought into L2 ahead
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Instruction descriptor, kind::tf32: TF32 A and B (K-major), FP32 accumulator, M x N.
@@ -67,6 +77,7 @@ struct XiPrm {
     const int32_t* osym;
     const int32_t* rows_r;
     int K, M, Mp, nib, nsplit, stages;
+    uint32_t raw_bytes;                   // one raw tile: Q [kKC][K], P and Gamma [kKC][128]
     uint32_t tmem_cols;
     float* Upart;                         // [nsplit][K][K]
     float* cntp;                          // [nsplit][K][M] (null: counts not taken here)
@@ -110,113 +121,75 @@ __device__ __forceinline__ void put_split(char* hi, char* lo, int n, int kq, flo
     *reinterpret_cast<float4*>(lo + off) = l;
 }
 
-// Column `col` of rows row0 + 4kq .. +3 of a [rows][K] buffer, zero past r1 or past K.
-__device__ __forceinline__ float4 load4(const float* __restrict__ X, int K, int64_t row0, int kq, int64_t r1,
-                                        int col) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (col < K) {
-        const int64_t r = row0 + 4 * kq;
-        if (r + 0 < r1) v.x = X[(r + 0) * K + col];
-        if (r + 1 < r1) v.y = X[(r + 1) * K + col];
-        if (r + 2 < r1) v.z = X[(r + 2) * K + col];
-        if (r + 3 < r1) v.w = X[(r + 3) * K + col];
-    }
-    return v;
-}
-
-// The operand values one thread stages per chunk: the index e of each group is the thread's
-// e-th slot idx = tid + e * 256 of the block's (column, row quad) pairs.
-template <int K, bool CNT>
-struct Frag {
-    static constexpr int NA = 128 * (kKC / 4) / kThreads;        // P^T and Gamma^T groups
-    static constexpr int NB = K * (kKC / 4) / kThreads;          // Q^T groups
-    float4 a[NA], g[CNT ? NA : 1], b[NB];
-    int4 o;                                                      // osym of the thread's H row quad
+// Byte offsets inside a raw tile.
+struct RawLayout {
+    uint32_t q, pp, g;
 };
-
-template <int K, bool CNT>
-__device__ __forceinline__ void frag_load(Frag<K, CNT>& f, const XiPrm& p, int64_t row0, int64_t r1, int icol0,
-                                          bool valid) {
-    using F = Frag<K, CNT>;
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int e = 0; e < F::NA; ++e) {
-        const int idx = tid + e * kThreads, n = idx % 128, kq = idx / 128;
-        f.a[e] = valid ? load4(p.P, K, row0, kq, r1, icol0 + n) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (CNT) f.g[e] = valid ? load4(p.G, K, row0, kq, r1, icol0 + n) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int e = 0; e < F::NB; ++e) {
-        const int idx = tid + e * kThreads, n = idx % K, kq = idx / K;
-        f.b[e] = valid ? load4(p.Q, K, row0, kq, r1, n) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    if (CNT) {
-        // H: thread tid takes row quad tid % 4 for the columns tid / 4 + 64 m (see frag_store)
-        const int kq = tid & 3;
-        const int64_t r = row0 + 4 * kq;
-        f.o.x = (valid && r + 0 < r1) ? p.osym[r + 0] : -1;
-        f.o.y = (valid && r + 1 < r1) ? p.osym[r + 1] : -1;
-        f.o.z = (valid && r + 2 < r1) ? p.osym[r + 2] : -1;
-        f.o.w = (valid && r + 3 < r1) ? p.osym[r + 3] : -1;
-    }
+__host__ __device__ inline RawLayout raw_layout(int K, bool counts) {
+    RawLayout r;
+    r.q = 0;
+    r.pp = (uint32_t)kKC * K * 4;
+    r.g = r.pp + kKC * 128 * 4;
+    (void)counts;
+    return r;
+}
+__host__ __device__ inline uint32_t raw_tile_bytes(int K, bool counts) {
+    return (uint32_t)kKC * K * 4 + kKC * 128 * 4 * (counts ? 2u : 1u);
 }
 
-template <int K, bool CNT>
-__device__ __forceinline__ void frag_store(const Frag<K, CNT>& f, char* st, const StageLayout& sl, int icol0, int Mp) {
-    using F = Frag<K, CNT>;
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int e = 0; e < F::NA; ++e) {
-        const int idx = tid + e * kThreads, n = idx % 128, kq = idx / 128;
-        if (icol0 + n >= K) continue;
-        put_split(st + sl.a_hi, st + sl.a_lo, n, kq, f.a[e]);
-        if (CNT) put_split(st + sl.g_hi, st + sl.g_lo, n, kq, f.g[e]);
-    }
-#pragma unroll
-    for (int e = 0; e < F::NB; ++e) {
-        const int idx = tid + e * kThreads, n = idx % K, kq = idx / K;
-        put_split(st + sl.b_hi, st + sl.b_lo, n, kq, f.b[e]);
-    }
-    if (CNT) {
-        // quad kq = tid % 4, columns n = tid / 4 + 64 m (m < Mp / 64)
-        const int kq = tid & 3;
-        for (int n = tid >> 2; n < Mp; n += kThreads / 4) {
-            float4 v;
-            v.x = f.o.x == n ? 1.f : 0.f;
-            v.y = f.o.y == n ? 1.f : 0.f;
-            v.z = f.o.z == n ? 1.f : 0.f;
-            v.w = f.o.w == n ? 1.f : 0.f;
-            *reinterpret_cast<float4*>(st + sl.h + canon(n, kq)) = v;
-        }
-    }
+// Four reduction rows (4kq .. 4kq+3) of column n of a raw tile with row stride `ld` floats;
+// rows at or past nrow read as zero (the last chunk of a range).
+__device__ __forceinline__ float4 raw4(const float* t, int ld, int n, int kq, int nrow) {
+    const int r = 4 * kq;
+    float4 v;
+    v.x = r + 0 < nrow ? t[(r + 0) * ld + n] : 0.f;
+    v.y = r + 1 < nrow ? t[(r + 1) * ld + n] : 0.f;
+    v.z = r + 2 < nrow ? t[(r + 2) * ld + n] : 0.f;
+    v.w = r + 3 < nrow ? t[(r + 3) * ld + n] : 0.f;
+    return v;
 }
 
 template <int K, bool CNT>
 __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     extern __shared__ __align__(1024) char smem[];
-    __shared__ __align__(8) uint64_t s_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t s_bar[kMaxStages];     // split stage s: its MMAs done
+    __shared__ __align__(8) uint64_t s_full[kMaxStages];    // split stage s: operands written
+    __shared__ __align__(8) uint64_t s_raw[kRawStages];     // raw tile r: its Q rows arrived
     __shared__ uint32_t s_tmem;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ int s_fail;
+    __shared__ int64_t s_committed;       // chunks whose MMAs the MMA warp committed
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool splitter = tid < kSplitThreads;
     const int ib = blockIdx.x % p.nib, sp = blockIdx.x / p.nib;
     const int64_t rows = *p.rows_r;
     const int64_t r0 = rows * sp / p.nsplit, r1 = rows * (sp + 1) / p.nsplit;
     if (r0 >= r1) return;                 // uniform over the CTA; nothing allocated yet
     const int Mp = p.Mp, NS = p.stages;
     const StageLayout sl = stage_layout(K, Mp, CNT);
+    const RawLayout rl = raw_layout(K, CNT);
+    char* const raw0 = smem + (size_t)NS * sl.bytes;
+    const int icol0 = ib * 128;
+    const int ncols = K - icol0 < 128 ? K - icol0 : 128;     // valid i columns of the block
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) tc::mbar_init(&s_bar[s], 1);
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&s_bar[s], 1);
+            tc::mbar_init(&s_full[s], kSplitThreads);
+        }
+        for (int r = 0; r < kRawStages; ++r) tc::mbar_init(&s_raw[r], 1);
         tc::fence_mbar_init();
+        s_fail = 0;
+        s_committed = 0;
     }
     if (warp == 0) {
         tc::tmem_alloc(&s_tmem, p.tmem_cols);
         tc::tmem_relinquish();
     }
     // rows of the i block past K stay zero in every stage
-    if (K - ib * 128 < 128) {
+    if (ncols < 128 && splitter) {
         for (int s = 0; s < NS; ++s)
-            for (int idx = tid; idx < 128 * kKC / 4; idx += kThreads) {
+            for (int idx = tid; idx < 128 * kKC / 4; idx += kSplitThreads) {
                 const int n = idx % 128, kq = idx / 128;
-                if (ib * 128 + n < K) continue;
+                if (n < ncols) continue;
                 char* st = smem + (size_t)s * sl.bytes;
                 const uint32_t off = canon(n, kq);
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -232,103 +205,230 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t idU = idesc_tf32_f32(128, K), idC = idesc_tf32_f32(128, CNT ? Mp : 16);
     const int64_t nchunks = (r1 - r0 + kKC - 1) / kKC;
-    const int icol0 = ib * 128;
     bool failed = false;
-    // register ring of three chunks: chunk c is split and stored while the loads of chunks
-    // c+1 and c+2 are in flight
-    Frag<K, CNT> f0, f1, f2;
-    frag_load<K, CNT>(f0, p, r0, r1, icol0, true);
-    frag_load<K, CNT>(f1, p, r0 + kKC, r1, icol0, 1 < nchunks);
-    auto chunk = [&](int64_t c, const Frag<K, CNT>& cur, Frag<K, CNT>& ahead) -> bool {
-        const int s = (int)(c % NS);
-        char* st = smem + (size_t)s * sl.bytes;
-        frag_load<K, CNT>(ahead, p, r0 + (c + 2) * kKC, r1, icol0, c + 2 < nchunks);
-        if (c >= NS) {
-            const uint32_t par = (uint32_t)((c / NS - 1) & 1);
-            const bool ok = tc::mbar_wait_bounded(&s_bar[s], par, kWaitNs);
-            if (__syncthreads_or(!ok)) return false;
-        }
-        frag_store<K, CNT>(cur, st, sl, icol0, Mp);
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc::tc_fence_after();
-            const uint32_t base = tc::smem_u32(st);
+    int64_t c = 0, issued = 0;
+    if (!splitter) {
+        // ---- the last warp: lane 0 issues each chunk's MMAs once its operands are written
+        if (lane == 0) {
+            const uint32_t idU = idesc_tf32_f32(128, K), idC = idesc_tf32_f32(128, CNT ? Mp : 16);
             const uint32_t sbo = kKC / 4 * 128;
+            for (int64_t q = 0; q < nchunks; ++q) {
+                const int s = (int)(q % NS);
+                if (!tc::mbar_wait_bounded(&s_full[s], (uint32_t)((q / NS) & 1), kWaitNs)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t base = tc::smem_u32(smem + (size_t)s * sl.bytes);
 #pragma unroll
-            for (int ks = 0; ks < kKC / 8; ++ks) {
-                const uint32_t koff = (uint32_t)ks * 256;   // 8 reduction rows = two core matrices
-                const uint64_t ah = tc::smem_desc_noswizzle(base + sl.a_hi + koff, 128, sbo);
-                const uint64_t al = tc::smem_desc_noswizzle(base + sl.a_lo + koff, 128, sbo);
-                const uint64_t bh = tc::smem_desc_noswizzle(base + sl.b_hi + koff, 128, sbo);
-                const uint64_t bl = tc::smem_desc_noswizzle(base + sl.b_lo + koff, 128, sbo);
-                const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-                mma_tf32(tmem, ah, bh, idU, acc0);
-                mma_tf32(tmem, ah, bl, idU, 1u);
-                mma_tf32(tmem, al, bh, idU, 1u);
-                if (CNT) {
-                    const uint64_t gh = tc::smem_desc_noswizzle(base + sl.g_hi + koff, 128, sbo);
-                    const uint64_t gl = tc::smem_desc_noswizzle(base + sl.g_lo + koff, 128, sbo);
-                    const uint64_t hh = tc::smem_desc_noswizzle(base + sl.h + koff, 128, sbo);
-                    mma_tf32(tmem + (uint32_t)K, gh, hh, idC, acc0);
-                    mma_tf32(tmem + (uint32_t)K, gl, hh, idC, 1u);
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    const uint32_t koff = (uint32_t)ks * 256;   // 8 reduction rows = two core matrices
+                    const uint64_t ah = tc::smem_desc_noswizzle(base + sl.a_hi + koff, 128, sbo);
+                    const uint64_t al = tc::smem_desc_noswizzle(base + sl.a_lo + koff, 128, sbo);
+                    const uint64_t bh = tc::smem_desc_noswizzle(base + sl.b_hi + koff, 128, sbo);
+                    const uint64_t bl = tc::smem_desc_noswizzle(base + sl.b_lo + koff, 128, sbo);
+                    const uint32_t acc0 = (q > 0 || ks > 0) ? 1u : 0u;
+                    mma_tf32(tmem, ah, bh, idU, acc0);
+                    mma_tf32(tmem, ah, bl, idU, 1u);
+                    mma_tf32(tmem, al, bh, idU, 1u);
+                    if (CNT) {
+                        const uint64_t gh = tc::smem_desc_noswizzle(base + sl.g_hi + koff, 128, sbo);
+                        const uint64_t gl = tc::smem_desc_noswizzle(base + sl.g_lo + koff, 128, sbo);
+                        const uint64_t hh = tc::smem_desc_noswizzle(base + sl.h + koff, 128, sbo);
+                        mma_tf32(tmem + (uint32_t)K, gh, hh, idC, acc0);
+                        mma_tf32(tmem + (uint32_t)K, gl, hh, idC, 1u);
+                    }
+                }
+                tc::mma_commit(&s_bar[s]);
+                s_committed = q + 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- the other warps: copies and operand split
+        // the copies of chunk q into raw tile q % kRawStages: thread 0 copies the Q rows (one
+        // contiguous bulk copy, completing on the tile's mbarrier); every splitter copies
+        // 16-byte pieces of the chunk's P and Gamma rows (the CTA's 128 columns) with
+        // cp.async and commits them as one group -- an empty group past the last chunk, so
+        // that "all but the newest kRawStages - 1 groups complete" means "chunk q complete"
+        auto issue_q = [&](int64_t q) {
+            const int rs = (int)(q % kRawStages);
+            char* raw = raw0 + (size_t)rs * p.raw_bytes;
+            const int64_t row0 = r0 + q * kKC;
+            const int nrow = (int)(r1 - row0 < kKC ? r1 - row0 : kKC);
+            tc::mbar_arrive_expect_tx(&s_raw[rs], (uint32_t)nrow * K * 4);
+            tc::bulk_g2s(raw + rl.q, p.Q + row0 * K, (uint32_t)nrow * K * 4, &s_raw[rs]);
+            // and the whole rows of P, Q and Gamma of chunk q + kPrefetch into L2 (full rows are
+            // contiguous; the other i block of the same rows reads the rest)
+            const int64_t pq = q + kPrefetch;
+            if (pq < nchunks) {
+                const int64_t prow0 = r0 + pq * kKC;
+                const uint32_t bytes = (uint32_t)(r1 - prow0 < kKC ? r1 - prow0 : kKC) * K * 4;
+                tc::bulk_prefetch_l2(p.Q + prow0 * K, bytes);
+                tc::bulk_prefetch_l2(p.P + prow0 * K, bytes);
+                if (CNT) tc::bulk_prefetch_l2(p.G + prow0 * K, bytes);
+            }
+        };
+        auto issue_pg = [&](int64_t q) {
+            if (q < nchunks) {
+                const int rs = (int)(q % kRawStages);
+                char* raw = raw0 + (size_t)rs * p.raw_bytes;
+                const int64_t row0 = r0 + q * kKC;
+                const int nrow = (int)(r1 - row0 < kKC ? r1 - row0 : kKC);
+#pragma unroll
+                for (int idx = tid; idx < kKC * 32; idx += kSplitThreads) {
+                    const int rr = idx >> 5, col = 4 * (idx & 31);
+                    if (rr < nrow && col < ncols) {
+                        const uint32_t off = (uint32_t)(rr * 128 + col) * 4;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                     ::"r"(tc::smem_u32(raw + rl.pp + off)), "l"(p.P + (row0 + rr) * K + icol0 + col)
+                                     : "memory");
+                        if (CNT)
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                         ::"r"(tc::smem_u32(raw + rl.g + off)), "l"(p.G + (row0 + rr) * K + icol0 + col)
+                                         : "memory");
+                    }
                 }
             }
-            tc::mma_commit(&s_bar[s]);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (tid == 0)
+            for (int64_t q = 0; q < kPrefetch && q < nchunks; ++q) {
+                const int64_t prow0 = r0 + q * kKC;
+                const uint32_t bytes = (uint32_t)(r1 - prow0 < kKC ? r1 - prow0 : kKC) * K * 4;
+                tc::bulk_prefetch_l2(p.Q + prow0 * K, bytes);
+                tc::bulk_prefetch_l2(p.P + prow0 * K, bytes);
+                if (CNT) tc::bulk_prefetch_l2(p.G + prow0 * K, bytes);
+            }
+        for (; issued < kRawStages; ++issued) {
+            if (tid == 0 && issued < nchunks) issue_q(issued);
+            issue_pg(issued);
         }
-        return true;
-    };
-    for (int64_t c = 0; c < nchunks; c += 3) {
-        if (!chunk(c, f0, f2)) { failed = true; break; }
-        if (c + 1 >= nchunks) break;
-        if (!chunk(c + 1, f1, f0)) { failed = true; break; }
-        if (c + 2 >= nchunks) break;
-        if (!chunk(c + 2, f2, f1)) { failed = true; break; }
+        for (; c < nchunks; ++c) {
+            const int s = (int)(c % NS), rs = (int)(c % kRawStages);
+            char* st = smem + (size_t)s * sl.bytes;
+            const char* raw = raw0 + (size_t)rs * p.raw_bytes;
+            const int64_t row0 = r0 + c * kKC;
+            const int nrow = (int)(r1 - row0 < kKC ? r1 - row0 : kKC);
+            int4 o = make_int4(-1, -1, -1, -1);   // osym of the thread's H row quad tid % 4
+            if (CNT) {
+                const int64_t r = row0 + 4 * (tid & 3);
+                if (r + 0 < r1) o.x = p.osym[r + 0];
+                if (r + 1 < r1) o.y = p.osym[r + 1];
+                if (r + 2 < r1) o.z = p.osym[r + 2];
+                if (r + 3 < r1) o.w = p.osym[r + 3];
+            }
+            bool ok = tc::mbar_wait_bounded(&s_raw[rs], (uint32_t)((c / kRawStages) & 1), kWaitNs);
+            if (ok && c >= NS) ok = tc::mbar_wait_bounded(&s_bar[s], (uint32_t)((c / NS - 1) & 1), kWaitNs);
+            static_assert(kRawStages == 2, "the cp.async group count below assumes two raw tiles");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this thread's pieces of chunk c
+            if (tc::bar_or_n(1, kSplitThreads, !ok)) {             // every splitter's pieces visible
+                failed = true;
+                break;
+            }
+            // split the raw tile into the stage's hi / lo operand blocks
+            const float* rq = reinterpret_cast<const float*>(raw + rl.q);
+            const float* rp = reinterpret_cast<const float*>(raw + rl.pp);
+            const float* rg = reinterpret_cast<const float*>(raw + rl.g);
+#pragma unroll
+            for (int idx = tid; idx < 128 * (kKC / 4); idx += kSplitThreads) {
+                const int n = idx % 128, kq = idx / 128;
+                if (n >= ncols) continue;
+                put_split(st + sl.a_hi, st + sl.a_lo, n, kq, raw4(rp, 128, n, kq, nrow));
+                if (CNT) put_split(st + sl.g_hi, st + sl.g_lo, n, kq, raw4(rg, 128, n, kq, nrow));
+            }
+#pragma unroll
+            for (int idx = tid; idx < K * (kKC / 4); idx += kSplitThreads) {
+                const int n = idx % K, kq = idx / K;
+                put_split(st + sl.b_hi, st + sl.b_lo, n, kq, raw4(rq, K, n, kq, nrow));
+            }
+            if (CNT) {
+                // quad kq = tid % 4, columns n = tid / 4 + 64 m (m < Mp / 64)
+                const int kq = tid & 3;
+                for (int n = tid >> 2; n < Mp; n += kSplitThreads / 4) {
+                    float4 v;
+                    v.x = o.x == n ? 1.f : 0.f;
+                    v.y = o.y == n ? 1.f : 0.f;
+                    v.z = o.z == n ? 1.f : 0.f;
+                    v.w = o.w == n ? 1.f : 0.f;
+                    *reinterpret_cast<float4*>(st + sl.h + canon(n, kq)) = v;
+                }
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&s_full[s]);                       // the MMA warp may issue chunk c
+            tc::bar_sync_n(2, kSplitThreads);                  // raw tile rs read by every splitter
+            if (tid == 0 && issued < nchunks) issue_q(issued); // chunk c + kRawStages into tile rs
+            issue_pg(issued++);
+        }
+        if (failed) s_fail = 1;
     }
-    if (!failed) {
+    __syncthreads();                      // the MMA warp is done issuing
+    failed = s_fail != 0;
+    if (!failed && tid == 0) {
         // the last commit covers every MMA issued before it
         const int64_t cl = nchunks - 1;
-        const bool ok = tc::mbar_wait_bounded(&s_bar[cl % NS], (uint32_t)((cl / NS) & 1), kWaitNs);
-        failed = __syncthreads_or(!ok);
+        if (!tc::mbar_wait_bounded(&s_bar[cl % NS], (uint32_t)((cl / NS) & 1), kWaitNs)) s_fail = 1;
     }
+    if (failed && tid == 0) {
+        // a wait gave up: let the Q copies already issued land and the MMAs already committed
+        // finish (each wait bounded) before the tensor memory and the CTA go away
+        for (int64_t q = c; q < issued && q < nchunks; ++q)
+            tc::mbar_wait_bounded(&s_raw[q % kRawStages], (uint32_t)((q / kRawStages) & 1), kWaitNs);
+        const int64_t nc = s_committed;
+        if (nc > 0) tc::mbar_wait_bounded(&s_bar[(nc - 1) % NS], (uint32_t)(((nc - 1) / NS) & 1), kWaitNs);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    failed = s_fail != 0;
     if (failed) {
         if (tid == 0) report_status(p.status, ACCEL_ERR_TIMEOUT);
-    } else {
+    } else if (splitter) {
         tc::tc_fence_after();
-        // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows i of the block), column half w / 4
-        const int q = warp & 3, half = warp >> 2;
-        const int i = icol0 + 32 * q + (tid & 31);
+        // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows i of the block) and the 32-column
+        // pieces w / 4, w / 4 + kColParts, ...; each piece: its partial sums loaded first,
+        // then added and stored
+        const int q = warp & 3, part = warp >> 2;
+        const int i = icol0 + 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
         float* U = p.Upart + (int64_t)sp * K * K;
 #pragma unroll 1
-        for (int j0 = half * (K / 2); j0 < (half + 1) * (K / 2); j0 += 32) {
+        for (int j0 = 32 * part; j0 < K; j0 += 32 * kColParts) {
             uint32_t v[32];
             tc::tmem_ld32(lane_base + (uint32_t)j0, v);
             if (i < K) {
-                float* dst = U + (int64_t)i * K + j0;
+                float4* dst = reinterpret_cast<float4*>(U + (int64_t)i * K + j0);
+                float4 d[8];
 #pragma unroll
-                for (int e = 0; e < 32; e += 4) {
-                    float4 d = *reinterpret_cast<float4*>(dst + e);
-                    d.x += __uint_as_float(v[e]);
-                    d.y += __uint_as_float(v[e + 1]);
-                    d.z += __uint_as_float(v[e + 2]);
-                    d.w += __uint_as_float(v[e + 3]);
-                    *reinterpret_cast<float4*>(dst + e) = d;
+                for (int e = 0; e < 8; ++e) d[e] = dst[e];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    d[e].x += __uint_as_float(v[4 * e]);
+                    d[e].y += __uint_as_float(v[4 * e + 1]);
+                    d[e].z += __uint_as_float(v[4 * e + 2]);
+                    d[e].w += __uint_as_float(v[4 * e + 3]);
                 }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) dst[e] = d[e];
             }
         }
         if (CNT) {
             float* Cn = p.cntp + (int64_t)sp * K * p.M;
+            // 32-column pieces of the Mp count columns, one per column part in turn
 #pragma unroll 1
-            for (int k0 = half * (Mp / 2); k0 < (half + 1) * (Mp / 2); k0 += 32) {
+            for (int k0 = 32 * part; k0 < Mp; k0 += 32 * kColParts) {
                 uint32_t v[32];
                 tc::tmem_ld32(lane_base + (uint32_t)(K + k0), v);
-                if (i < K)
+                if (i < K) {
+                    float* dst = Cn + (int64_t)i * p.M + k0;
+                    const int nk = p.M - k0 < 32 ? p.M - k0 : 32;
+                    float d[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) d[e] = e < nk ? dst[e] : 0.f;
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
-                        if (k0 + e < p.M) Cn[(int64_t)i * p.M + k0 + e] += __uint_as_float(v[e]);
+                        if (e < nk) dst[e] = d[e] + __uint_as_float(v[e]);
+                }
             }
         }
     }
@@ -364,13 +464,16 @@ accel_status xi_tc_round(const float* P, const float* Q, const float* G, const i
     while ((int)cols < need_cols) cols <<= 1;
     p.tmem_cols = cols;
     const StageLayout sl = stage_layout(K, p.Mp, counts);
+    p.raw_bytes = raw_tile_bytes(K, counts);
+    const size_t raw_total = (size_t)kRawStages * p.raw_bytes;
     const int optin = max_smem_optin();
     int stages = kMaxStages;
-    while (stages > 2 && (size_t)stages * sl.bytes + 1024 > (size_t)optin) --stages;
-    ACCEL_REQUIRE((size_t)stages * sl.bytes + 1024 <= (size_t)optin, ACCEL_ERR_UNSUPPORTED,
+    while (stages > 2 && (size_t)stages * sl.bytes + raw_total + 1024 > (size_t)optin) --stages;
+    ACCEL_REQUIRE((size_t)stages * sl.bytes + raw_total + 1024 <= (size_t)optin, ACCEL_ERR_UNSUPPORTED,
                   "hmm_adjoint: count/transition stages do not fit in shared memory (K=%d, M=%d)", K, M);
     p.stages = stages;
-    const size_t smem = (size_t)stages * sl.bytes + 1024;   // + alignment slack of the dynamic block
+    // + alignment slack of the dynamic block
+    const size_t smem = (size_t)stages * sl.bytes + raw_total + 1024;
     void (*kern)(XiPrm) = nullptr;
     switch (K) {
         case 64: kern = counts ? k_xi_tc<64, true> : k_xi_tc<64, false>; break;
