@@ -426,6 +426,43 @@ __global__ void k_fill(Tout* __restrict__ out, int64_t S, Tout v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) out[i] = v;
 }
 
+// Small inputs (N <= kWarpPathMaxN elements, segments of at most 4,096 elements on
+// average): one warp per segment, straight from the offsets -- one launch instead of three (partition, tiles, fix-up).  At these sizes the
+// call's time is its launches, not its bytes, and the tiled kernel's load balance buys
+// nothing.  Lane l folds elements off[s] + l, + 32, ... in order (warp loads of 32
+// consecutive elements), then the 32 lane values combine in a fixed butterfly: the result
+// is deterministic (bit-exact for integers; for floats a fixed order, not the tiled one).
+constexpr int64_t kWarpPathMaxN = int64_t(1) << 20;
+
+template <typename Tin, typename Tout, int OP>
+__global__ void __launch_bounds__(kThreads)
+k_segreduce_warp(const Tin* __restrict__ data, const int64_t* __restrict__ off, int64_t S, int map_op,
+                 double scalar, Tout* __restrict__ out) {
+    using C = typename compute_of<Tout>::type;
+    const C sc = (C)scalar;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t s = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; s < S; s += nw) {
+        const int64_t a = off[s], b = off[s + 1];
+        C acc = red_neutral<C>(OP);
+        bool done = false;
+        if constexpr (OP == ACCEL_RED_ADD && std::is_integral<C>::value) {
+            if (map_op == ACCEL_MAP_SQ_PLUS_ONE) {
+                // x*x of the input is exact in 64 bits; only the running sum wraps
+                uint64_t u = 0;
+                for (int64_t k = a + lane; k < b; k += 32) u += (uint64_t)sq_wide(data[k]) + 1u;
+                acc = (C)u;
+                done = true;
+            }
+        }
+        if (!done)
+            for (int64_t k = a + lane; k < b; k += 32) acc = red_combine<OP, C>(acc, map_one<C>(map_op, (C)data[k], sc));
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc = red_combine<OP, C>(acc, (C)__shfl_xor_sync(0xffffffffu, acc, d));
+        if (lane == 0) out[s] = b > a ? (Tout)acc : red_neutral<Tout>(OP);
+    }
+}
+
 struct Layout {
     int64_t ntiles;
     size_t lo_off, seg_off, val_off, total;
@@ -460,6 +497,15 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
         if (g > 8 * num_sms()) g = 8 * num_sms();
         k_fill<Tout><<<g, 256, 0, st>>>(out, S, nel);
         return after_launch(st, "accel_segreduce(fill)", 1);
+    }
+    if (N <= kWarpPathMaxN && N <= 4096 * S) {
+        int64_t g = (S + kThreads / 32 - 1) / (kThreads / 32);
+        if (g > 8 * (int64_t)num_sms()) g = 8 * (int64_t)num_sms();
+        ACCEL_DISPATCH_RED(op, OPC, {
+            k_segreduce_warp<Tin, Tout, OPC><<<(unsigned)g, kThreads, 0, st>>>((const Tin*)d_data, d_off, S, map_op,
+                                                                                scalar, out);
+        });
+        return after_launch(st, "accel_segreduce", 1);
     }
     int64_t te = tile_elems<Tin>();
     k_partition_scatter<<<(unsigned)((S + 1 + 255) / 256), 256, 0, st>>>(d_off, S, N, te, L.ntiles, lo);

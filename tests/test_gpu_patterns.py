@@ -278,19 +278,51 @@ def test_segreduce_config_bit_exact_and_max():
     assert int(seg.sum().item()) == int(np.sum(rf.astype(np.int64) ** 2 + 1))
 
 
+# Inputs of at most 2^20 elements (segments of at most 4,096 elements on average) take the
+# one-warp-per-segment kernel; larger ones the tiled kernels.  PATH "tiled" appends a segment
+# of 2^20 + 1 zeros after the case, which sends the same segments through the tiled kernels;
+# the appended segment's result is checked on its own.
+PATHS = ["warp", "tiled"]
+TAIL = (1 << 20) + 1
+
+
+def _with_tail(data, off, path):
+    if path == "warp":
+        return data, off
+    data2 = np.concatenate([data, np.zeros(TAIL, data.dtype)])
+    off2 = np.concatenate([off, [off[-1] + TAIL]]).astype(np.int64)
+    return data2, off2
+
+
+def _tail_value(red, fmap, scalar=0.0):
+    g0 = {op.MAP_IDENTITY: 0, op.MAP_SQ_PLUS_ONE: 1, op.MAP_NEG: 0, op.MAP_ABS: 0, op.MAP_SCALE: 0}[fmap]
+    return {op.RED_ADD: g0 * TAIL, op.RED_MUL: g0, op.RED_MIN: g0, op.RED_MAX: g0}[red]
+
+
+def _segreduce_path(red, fmap, data, off, dt, path, scalar=0.0):
+    d2, o2 = _with_tail(data, off, path)
+    got = api.accel_segreduce(red, fmap, _t(d2), _t(o2), dt, scalar=scalar).cpu().numpy()
+    if path == "tiled":
+        assert got[-1] == _tail_value(red, fmap, scalar)
+        got = got[:-1]
+    return got
+
+
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("red", [op.RED_ADD, op.RED_MUL, op.RED_MIN, op.RED_MAX])
 @pytest.mark.parametrize("fmap", [op.MAP_IDENTITY, op.MAP_SQ_PLUS_ONE, op.MAP_NEG, op.MAP_ABS, op.MAP_SCALE])
-def test_segreduce_ops_small(red, fmap):
+def test_segreduce_ops_small(red, fmap, path):
     data, off = _seg_case(red * 10 + fmap, 300, 0, 60)
     if red == op.RED_MUL:
         data = (data % 5).astype(np.int32)
-    got = api.accel_segreduce(red, fmap, _t(data), _t(off), torch.int64, scalar=-2.0).cpu().numpy()
+    got = _segreduce_path(red, fmap, data, off, torch.int64, path, scalar=-2.0)
     ref = op.segreduce(red, fmap, data, off, np.int64, scalar=-2.0)
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("case", ["one_long", "all_empty_tail", "unit_lengths", "empty_runs", "spanning_tiles"])
-def test_segreduce_edge_cases(case):
+def test_segreduce_edge_cases(case, path):
     g = synth.rng(1)
     if case == "one_long":            # one segment spanning many tiles
         lengths = np.array([100_003])
@@ -306,7 +338,7 @@ def test_segreduce_edge_cases(case):
     np.cumsum(lengths, out=off[1:])
     data = g.integers(-1000, 1001, size=int(off[-1])).astype(np.int32)
     for red in (op.RED_ADD, op.RED_MAX):
-        got = api.accel_segreduce(red, op.MAP_SQ_PLUS_ONE, _t(data), _t(off), torch.int64).cpu().numpy()
+        got = _segreduce_path(red, op.MAP_SQ_PLUS_ONE, data, off, torch.int64, path)
         ref = op.segreduce_fast(red, op.MAP_SQ_PLUS_ONE, data, off, np.int64)
         assert np.array_equal(got, ref)
 
@@ -319,22 +351,24 @@ def test_segreduce_no_elements(dout):
         assert np.array_equal(got.cpu().numpy(), np.full(16, op.neutral(red, dout), dtype=dout))
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("red", [op.RED_MIN, op.RED_MAX, op.RED_ADD])
-def test_segreduce_int32_output_with_empty_segments(red):
+def test_segreduce_int32_output_with_empty_segments(red, path):
     # an empty segment gives the int32 neutral element, at every position in a tile
     data, off = _seg_case(40 + red, 3000, 0, 12)
-    got = api.accel_segreduce(red, op.MAP_IDENTITY, _t(data), _t(off), torch.int32).cpu().numpy()
+    got = _segreduce_path(red, op.MAP_IDENTITY, data, off, torch.int32, path)
     ref = op.segreduce(red, op.MAP_IDENTITY, data, off, np.int32)
     assert np.count_nonzero(np.diff(off) == 0) > 100
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("dts", [(np.float32, np.float32), (np.float32, np.float64), (np.float64, np.float64),
                                  (np.int64, np.int64), (np.int64, np.int32), (np.int32, np.int32)])
-def test_segreduce_dtypes(dts):
+def test_segreduce_dtypes(dts, path):
     din, dout = dts
     data, off = _seg_case(77, 2000, 0, 500, din)
-    got = api.accel_segreduce(op.RED_ADD, op.MAP_SQ_PLUS_ONE, _t(data), _t(off), TORCH_DT[dout]).cpu().numpy()
+    got = _segreduce_path(op.RED_ADD, op.MAP_SQ_PLUS_ONE, data, off, TORCH_DT[dout], path)
     if np.dtype(dout).kind == "i":
         ref = op.segreduce(op.RED_ADD, op.MAP_SQ_PLUS_ONE, data, off, dout)
         assert np.array_equal(got, ref)
