@@ -1624,8 +1624,6 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     ACCEL_REQUIRE(S * (int64_t)L.Cmax <= (int64_t)INT32_MAX, ACCEL_ERR_UNSUPPORTED,
                   "%s: S x ceil(sqrt(max_T)) = %lld rows exceeds 2^31-1", who, (long long)(S * (int64_t)L.Cmax));
     P.sm_b = smem_bwd(K, M, L.Cmax);
-    ACCEL_REQUIRE(P.sm_b <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED,
-                  "%s: emission table too large for shared memory (K=%d, M=%d)", who, K, M);
     char* ws = (char*)d_ws;
     P.ws = ws;
     Prm& p = P.p;
@@ -1653,10 +1651,13 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     // (an [M][256] table in shared memory); otherwise the streaming kernels take the shape
     const bool counts_fit = xi_tc_counts_supported(K, M) || (size_t)M * 256 * 4 <= (size_t)max_smem_optin();
     P.use_cluster = S > 0 && clu::cluster_shape_ok(K) && P.sm_c <= (size_t)max_smem_optin() && counts_fit;
+    // the streaming kernels hold the whole emission table in shared memory
+    ACCEL_REQUIRE(P.use_cluster || S == 0 || P.sm_b <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED,
+                  "%s: emission table too large for shared memory (K=%d, M=%d)", who, K, M);
     P.xi_tc = P.use_cluster && xi_tc_supported(K);
     P.counts_tc = P.xi_tc && xi_tc_counts_supported(K, M);
-    P.nsU = P.xi_tc ? xi_tc_splits(K) : kSplit;
-    P.nsC = P.counts_tc ? xi_tc_splits(K) : kCntSplit;
+    P.nsU = P.xi_tc ? xi_tc_partials(K, M, P.counts_tc) : kSplit;
+    P.nsC = P.counts_tc ? xi_tc_partials(K, M, true) : kCntSplit;
     P.planned = false;
     if (P.use_cluster) {
         // groups: at most 16 sequences each, and at least one pair of CTAs per two SMs

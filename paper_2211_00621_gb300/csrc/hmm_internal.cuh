@@ -46,13 +46,15 @@ bool tc_supported(int K, int M);
 
 // Tensor-core (TF32, hi/lo split) accumulation of the adjoint's transition and emission
 // counts over the row buffers of one backward round (k_xi_tc.cu):
-//   Upart[split] += P^T Q over rows [0, *rows_r), and, when cntp is not null,
-//   cntp[split][i][k] += sum_rows G[row][i] [osym[row] == k].
-// The rows are divided into xi_tc_splits(K) contiguous ranges, one partial each.
+//   Upart[g] += P^T Q over rows [0, *rows_r), and, when cntp is not null,
+//   cntp[g][i][k] += sum_rows G[row][i] [osym[row] == k].
+// The rows are divided into xi_tc_splits(K) contiguous ranges; clusters of consecutive
+// ranges add their sums together, so there are xi_tc_partials(K) partials g.
 constexpr int kXiSplitMax = 160;
 bool xi_tc_supported(int K);
 bool xi_tc_counts_supported(int K, int M);
-int xi_tc_splits(int K);
+int xi_tc_splits(int K, int M, bool counts);
+int xi_tc_partials(int K, int M, bool counts);   // partials the splits leave (one per cluster)
 accel_status xi_tc_round(const float* P, const float* Q, const float* G, const int32_t* osym, const int32_t* rows_r,
                          int K, int M, float* Upart, float* cntp, int32_t* status, cudaStream_t st);
 

@@ -31,6 +31,12 @@
 #include "hmm_internal.cuh"
 #include "tc_ptx.cuh"
 
+#include <cooperative_groups.h>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
+
 namespace accel {
 namespace hmm {
 
@@ -39,6 +45,7 @@ namespace {
 constexpr int kSplitThreads = 512;      // warps 0-15: copies, operand split, epilogue
 constexpr int kThreads = kSplitThreads + 32;   // + warp 16: issues the MMAs
 constexpr int kColParts = kSplitThreads / 128; // epilogue: column parts per TMEM lane quarter
+constexpr int kCluster = 4;            // CTAs of consecutive row ranges of one i block
 constexpr int kKC = 16;                 // reduction rows per stage
 constexpr int kMaxStages = 3;          // split stages
 constexpr int kRawStages = 2;          // raw tiles (bulk-copy targets)
@@ -78,6 +85,7 @@ struct XiPrm {
     const int32_t* rows_r;
     int K, M, Mp, nib, nsplit, stages;
     uint32_t raw_bytes;                   // one raw tile: Q [kKC][K], P and Gamma [kKC][128]
+    int two_phase;                        // epilogue: U and the counts staged one after the other
     uint32_t tmem_cols;
     float* Upart;                         // [nsplit][K][K]
     float* cntp;                          // [nsplit][K][M] (null: counts not taken here)
@@ -160,10 +168,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     __shared__ int64_t s_committed;       // chunks whose MMAs the MMA warp committed
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool splitter = tid < kSplitThreads;
-    const int ib = blockIdx.x % p.nib, sp = blockIdx.x / p.nib;
+    // cluster cid = (i block ib, split group sg); its rank crank takes split sp of the rows
+    const int cid = (int)blockIdx.x / kCluster, crank = (int)blockIdx.x % kCluster;
+    const int ib = cid % p.nib, sg = cid / p.nib, sp = sg * kCluster + crank;
     const int64_t rows = *p.rows_r;
+    if (rows == 0) return;                // uniform over the grid; nothing allocated yet
     const int64_t r0 = rows * sp / p.nsplit, r1 = rows * (sp + 1) / p.nsplit;
-    if (r0 >= r1) return;                 // uniform over the CTA; nothing allocated yet
+    const bool has_rows = r0 < r1;        // a rank without rows still joins the cluster's sums
     const int Mp = p.Mp, NS = p.stages;
     const StageLayout sl = stage_layout(K, Mp, CNT);
     const RawLayout rl = raw_layout(K, CNT);
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const int64_t nchunks = (r1 - r0 + kKC - 1) / kKC;
+    const int64_t nchunks = has_rows ? (r1 - r0 + kKC - 1) / kKC : 0;
     bool failed = false;
     int64_t c = 0, issued = 0;
     if (!splitter) {
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     }
     __syncthreads();                      // the MMA warp is done issuing
     failed = s_fail != 0;
-    if (!failed && tid == 0) {
+    if (!failed && tid == 0 && nchunks > 0) {
         // the last commit covers every MMA issued before it
         const int64_t cl = nchunks - 1;
         if (!tc::mbar_wait_bounded(&s_bar[cl % NS], (uint32_t)((cl / NS) & 1), kWaitNs)) s_fail = 1;
@@ -381,56 +392,121 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     failed = s_fail != 0;
-    if (failed) {
-        if (tid == 0) report_status(p.status, ACCEL_ERR_TIMEOUT);
-    } else if (splitter) {
-        tc::tc_fence_after();
-        // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows i of the block) and the 32-column
-        // pieces w / 4, w / 4 + kColParts, ...; each piece: its partial sums loaded first,
-        // then added and stored
-        const int q = warp & 3, part = warp >> 2;
-        const int i = icol0 + 32 * q + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-        float* U = p.Upart + (int64_t)sp * K * K;
+    if (failed && tid == 0) report_status(p.status, ACCEL_ERR_TIMEOUT);
+    // ---- epilogue.  Each CTA stages its accumulators in its own (now idle) shared memory --
+    // zeros for a rank without rows or after a failed wait, so that every rank still takes
+    // both cluster barriers -- then rank r adds the cluster's kCluster blocks for rows
+    // [32 r, 32 r + 32) of the i block through distributed shared memory, in rank order, and
+    // adds the sums into the cluster's partial: one read-modify-write of the partials per
+    // cluster instead of one per CTA.
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    constexpr int ULD = K + 4;            // staging row strides (floats): 16-byte stores, 4 wavefronts
+    const int CLD = Mp + 4;
+    float* stU = reinterpret_cast<float*>(smem);
+    // U and the counts are staged together when both fit, else one after the other in the
+    // same area (two rounds of the two barriers)
+    const bool two_phase = CNT && p.two_phase;
+    float* stC = two_phase ? stU : stU + 128 * ULD;
+    const bool live = !failed && has_rows;
+    for (int ph = 0; ph < (two_phase ? 2 : 1); ++ph) {
+        const bool do_u = !two_phase || ph == 0, do_c = CNT && (!two_phase || ph == 1);
+        if (splitter) {
+            const int q = warp & 3, part = warp >> 2;
+            const int row = 32 * q + lane;
+            const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+            if (live) tc::tc_fence_after();
 #pragma unroll 1
-        for (int j0 = 32 * part; j0 < K; j0 += 32 * kColParts) {
-            uint32_t v[32];
-            tc::tmem_ld32(lane_base + (uint32_t)j0, v);
-            if (i < K) {
-                float4* dst = reinterpret_cast<float4*>(U + (int64_t)i * K + j0);
-                float4 d[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) d[e] = dst[e];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    d[e].x += __uint_as_float(v[4 * e]);
-                    d[e].y += __uint_as_float(v[4 * e + 1]);
-                    d[e].z += __uint_as_float(v[4 * e + 2]);
-                    d[e].w += __uint_as_float(v[4 * e + 3]);
-                }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) dst[e] = d[e];
-            }
-        }
-        if (CNT) {
-            float* Cn = p.cntp + (int64_t)sp * K * p.M;
-            // 32-column pieces of the Mp count columns, one per column part in turn
-#pragma unroll 1
-            for (int k0 = 32 * part; k0 < Mp; k0 += 32 * kColParts) {
+            for (int j0 = 32 * part; do_u && j0 < K; j0 += 32 * kColParts) {
                 uint32_t v[32];
-                tc::tmem_ld32(lane_base + (uint32_t)(K + k0), v);
-                if (i < K) {
-                    float* dst = Cn + (int64_t)i * p.M + k0;
-                    const int nk = p.M - k0 < 32 ? p.M - k0 : 32;
-                    float d[32];
+                if (live) {
+                    tc::tmem_ld32(lane_base + (uint32_t)j0, v);
+                } else {
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) d[e] = e < nk ? dst[e] : 0.f;
+                    for (int e = 0; e < 32; ++e) v[e] = 0u;
+                }
+                float4* dst = reinterpret_cast<float4*>(stU + row * ULD + j0);
 #pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (e < nk) dst[e] = d[e] + __uint_as_float(v[e]);
+                for (int e = 0; e < 8; ++e)
+                    dst[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                         __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+            }
+            if (do_c) {
+#pragma unroll 1
+                for (int k0 = 32 * part; k0 < Mp; k0 += 32 * kColParts) {
+                    uint32_t v[32];
+                    if (live) {
+                        tc::tmem_ld32(lane_base + (uint32_t)(K + k0), v);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) v[e] = 0u;
+                    }
+                    float4* dst = reinterpret_cast<float4*>(stC + row * CLD + k0);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        dst[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                             __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
                 }
             }
         }
+        cluster.sync();                       // every rank's block staged
+        if (splitter) {
+            const int rb = 32 * crank;        // this rank's rows of the block
+            constexpr int NQ = K / 4;         // float4 per row
+            constexpr int UIT = (32 * NQ + kSplitThreads - 1) / kSplitThreads;
+            float* U = p.Upart + (int64_t)sg * K * K;
+            if (do_u) {
+            float4 acc[UIT], cur[UIT];
+#pragma unroll
+            for (int it = 0; it < UIT; ++it) {
+                const int idx = tid + it * kSplitThreads, rr = idx / NQ, c4 = idx % NQ;
+                acc[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (idx < 32 * NQ && icol0 + rb + rr < K) {
+#pragma unroll
+                    for (int c = 0; c < kCluster; ++c) {
+                        const float4 b = reinterpret_cast<const float4*>(cluster.map_shared_rank(stU, c) + (rb + rr) * ULD)[c4];
+                        acc[it].x += b.x; acc[it].y += b.y; acc[it].z += b.z; acc[it].w += b.w;
+                    }
+                    cur[it] = reinterpret_cast<const float4*>(U + (int64_t)(icol0 + rb + rr) * K)[c4];
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < UIT; ++it) {
+                const int idx = tid + it * kSplitThreads, rr = idx / NQ, c4 = idx % NQ;
+                if (idx < 32 * NQ && icol0 + rb + rr < K) {
+                    float4 d = cur[it];
+                    d.x += acc[it].x; d.y += acc[it].y; d.z += acc[it].z; d.w += acc[it].w;
+                    reinterpret_cast<float4*>(U + (int64_t)(icol0 + rb + rr) * K)[c4] = d;
+                }
+            }
+            }
+            if (do_c) {
+                const int M = p.M;
+                float* Cn = p.cntp + (int64_t)sg * K * M;
+                // batches of four entries per thread: their loads first, then their stores
+                constexpr int CB = 4;
+                for (int base = tid; base < 32 * M; base += CB * kSplitThreads) {
+                    float cacc[CB], ccur[CB];
+#pragma unroll
+                    for (int it = 0; it < CB; ++it) {
+                        const int idx = base + it * kSplitThreads, rr = idx / M, k = idx % M;
+                        cacc[it] = 0.f;
+                        ccur[it] = 0.f;
+                        if (idx < 32 * M && icol0 + rb + rr < K) {
+#pragma unroll
+                            for (int c = 0; c < kCluster; ++c) cacc[it] += cluster.map_shared_rank(stC, c)[(rb + rr) * CLD + k];
+                            ccur[it] = Cn[(int64_t)(icol0 + rb + rr) * M + k];
+                        }
+                    }
+#pragma unroll
+                    for (int it = 0; it < CB; ++it) {
+                        const int idx = base + it * kSplitThreads, rr = idx / M, k = idx % M;
+                        if (idx < 32 * M && icol0 + rb + rr < K) Cn[(int64_t)(icol0 + rb + rr) * M + k] = ccur[it] + cacc[it];
+                    }
+                }
+            }
+        }
+        cluster.sync();                       // no CTA leaves while a peer still reads its staging
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -444,11 +520,77 @@ int xi_counts_cols(int M) { return (M + 63) / 64 * 64; }
 bool xi_tc_supported(int K) { return K == 64 || K == 128 || K == 256; }
 bool xi_tc_counts_supported(int K, int M) { return xi_tc_supported(K) && K + xi_counts_cols(M) <= 512 && xi_counts_cols(M) <= 256; }
 
-int xi_tc_splits(int K) {
+namespace {
+// Dynamic shared memory of a launch (stages, raw tiles, at least the epilogue's staging).
+// Dynamic shared memory of a launch: the split stages and raw tiles (+ alignment slack of
+// the block), at least the epilogue's staging of the accumulators -- U and the counts
+// together if that fits, else one after the other (*two_phase).
+size_t xi_smem_bytes(int K, int Mp, bool counts, int* stages_out, bool* two_phase) {
+    const StageLayout sl = stage_layout(K, Mp, counts);
+    const size_t raw_total = (size_t)kRawStages * raw_tile_bytes(K, counts);
+    const size_t optin = (size_t)max_smem_optin();
+    int stages = kMaxStages;
+    while (stages > 2 && (size_t)stages * sl.bytes + raw_total + 1024 > optin) --stages;
+    if (stages_out) *stages_out = stages;
+    size_t smem = (size_t)stages * sl.bytes + raw_total + 1024;
+    const size_t su = (size_t)128 * (K + 4) * 4, sc = counts ? (size_t)128 * (Mp + 4) * 4 : 0;
+    const bool two = su + sc + 1024 > optin;
+    if (two_phase) *two_phase = two;
+    const size_t staging = (two ? (su > sc ? su : sc) : su + sc) + 1024;
+    return smem < staging ? staging : smem;
+}
+
+void (*xi_kernel(int K, bool counts))(XiPrm) {
+    switch (K) {
+        case 64: return counts ? k_xi_tc<64, true> : k_xi_tc<64, false>;
+        case 128: return counts ? k_xi_tc<128, true> : k_xi_tc<128, false>;
+        default: return counts ? k_xi_tc<256, true> : k_xi_tc<256, false>;
+    }
+}
+}  // namespace
+
+// Row splits of a launch: one CTA per split and i block, in whole clusters, no more CTAs
+// than are resident at once (clusters of four fit 144 of 152 SMs: a second wave of the last
+// clusters would double the call).
+int xi_tc_splits(int K, int M, bool counts) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int Mp = counts ? xi_counts_cols(M) : 0;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(dev, K, Mp, counts ? 1 : 0);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
     const int nib = (K + 127) / 128;
     int n = num_sms() / nib;
-    return n < 1 ? 1 : (n > kXiSplitMax ? kXiSplitMax : n);
+    void (*kern)(XiPrm) = xi_kernel(K, counts);
+    const size_t smem = xi_smem_bytes(K, Mp, counts, nullptr, nullptr);
+    int maxcl = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.gridDim = dim3((unsigned)(kCluster * nib), 1, 1);
+        lc.blockDim = dim3(kThreads, 1, 1);
+        lc.dynamicSmemBytes = smem;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&maxcl, kern, &lc) != cudaSuccess) maxcl = 0;
+    }
+    cudaGetLastError();
+    if (maxcl > 0 && maxcl * kCluster / nib < n) n = maxcl * kCluster / nib;
+    n = n > kXiSplitMax ? kXiSplitMax : n;
+    n = n / kCluster * kCluster;                  // whole clusters
+    if (n < kCluster) n = kCluster;
+    cache[key] = n;
+    return n;
 }
+
+int xi_tc_partials(int K, int M, bool counts) { return xi_tc_splits(K, M, counts) / kCluster; }
 
 accel_status xi_tc_round(const float* P, const float* Q, const float* G, const int32_t* osym, const int32_t* rows_r,
                          int K, int M, float* Upart, float* cntp, int32_t* status, cudaStream_t st) {
@@ -457,31 +599,35 @@ accel_status xi_tc_round(const float* P, const float* Q, const float* G, const i
     p.P = P; p.Q = Q; p.G = G; p.osym = osym; p.rows_r = rows_r;
     p.K = K; p.M = M; p.Mp = counts ? xi_counts_cols(M) : 0;
     p.nib = (K + 127) / 128;
-    p.nsplit = xi_tc_splits(K);
+    p.nsplit = xi_tc_splits(K, M, counts);
     p.Upart = Upart; p.cntp = cntp; p.status = status;
     const int need_cols = K + p.Mp;
     uint32_t cols = 32;
     while ((int)cols < need_cols) cols <<= 1;
     p.tmem_cols = cols;
-    const StageLayout sl = stage_layout(K, p.Mp, counts);
     p.raw_bytes = raw_tile_bytes(K, counts);
-    const size_t raw_total = (size_t)kRawStages * p.raw_bytes;
-    const int optin = max_smem_optin();
-    int stages = kMaxStages;
-    while (stages > 2 && (size_t)stages * sl.bytes + raw_total + 1024 > (size_t)optin) --stages;
-    ACCEL_REQUIRE((size_t)stages * sl.bytes + raw_total + 1024 <= (size_t)optin, ACCEL_ERR_UNSUPPORTED,
+    int stages = 2;
+    bool two = false;
+    const size_t smem = xi_smem_bytes(K, p.Mp, counts, &stages, &two);
+    p.two_phase = two ? 1 : 0;
+    ACCEL_REQUIRE(smem <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED,
                   "hmm_adjoint: count/transition stages do not fit in shared memory (K=%d, M=%d)", K, M);
     p.stages = stages;
-    // + alignment slack of the dynamic block
-    const size_t smem = (size_t)stages * sl.bytes + raw_total + 1024;
-    void (*kern)(XiPrm) = nullptr;
-    switch (K) {
-        case 64: kern = counts ? k_xi_tc<64, true> : k_xi_tc<64, false>; break;
-        case 128: kern = counts ? k_xi_tc<128, true> : k_xi_tc<128, false>; break;
-        default: kern = counts ? k_xi_tc<256, true> : k_xi_tc<256, false>; break;
-    }
+    void (*kern)(XiPrm) = xi_kernel(K, counts);
     ACCEL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)(p.nib * p.nsplit), kThreads, smem, st>>>(p);
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3((unsigned)(p.nib * p.nsplit), 1, 1);
+    lc.blockDim = dim3(kThreads, 1, 1);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    ACCEL_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, p));
     return ACCEL_OK;
 }
 

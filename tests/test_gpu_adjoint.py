@@ -69,7 +69,7 @@ def test_bruteforce_fixture(name):
 # cluster groups of 2-3 and 15-16 sequences.
 @pytest.mark.parametrize("K,M,S,lo,hi", [(8, 5, 20, 1, 50), (37, 11, 13, 1, 130), (64, 32, 9, 100, 400),
                                          (64, 7, 40, 1, 200), (128, 200, 10, 20, 120), (64, 300, 6, 1, 90),
-                                         (256, 100, 5, 30, 90), (128, 16, 35, 1, 60),
+                                         (256, 100, 5, 30, 90), (256, 200, 6, 20, 80), (128, 16, 35, 1, 60),
                                          (64, 8, 200, 5, 60), (64, 8, 1500, 2, 12)])
 def test_small_models_against_oracle(K, M, S, lo, hi):
     p = synth.hmm_workload(K * 3 + S, K, M, S, "uniform", lo, hi)
