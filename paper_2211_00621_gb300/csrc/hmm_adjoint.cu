@@ -82,6 +82,23 @@ struct Prm {
     const int32_t* rcount;
 };
 
+// The scale exponent of a row sum c: c = m 2^e with m in [0.5, 1) (the frexp convention),
+// read from the IEEE-754 exponent field of a normal c; zero, subnormal and non-finite c take
+// frexpf.  pow2_scale(e) = 2^-e, built from the field where that is a normal float.  Both
+// give exactly what frexpf / ldexpf give, at a few integer instructions on the per-step path.
+__device__ __forceinline__ int scale_exp(float c) {
+    const int f = (int)((__float_as_uint(c) >> 23) & 0xffu);
+    if (f == 0 || f == 0xff) {
+        int e = 0;
+        frexpf(c, &e);
+        return e;
+    }
+    return f - 126;
+}
+__device__ __forceinline__ float pow2_scale(int e) {     // 2^-e
+    return (e > -127 && e < 127) ? __uint_as_float((uint32_t)(127 - e) << 23) : ldexpf(1.0f, -e);
+}
+
 __host__ __device__ __forceinline__ int seg_len(int64_t T) {
     int c = (int)ceil(sqrt((double)T));
     while ((int64_t)c * c < T) ++c;
@@ -1193,9 +1210,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
             __syncthreads();                  // partials complete; the peer's half of X_{t-1} and
                                               // its row sums visible to every thread
             const float c = row_sum(V.red, cur, g);
-            int ex = 0;
-            frexpf(c, &ex);
-            const float sc = ldexpf(1.0f, -ex);
+            const int ex = scale_exp(c);
+            const float sc = pow2_scale(ex);
+            if (t < Tmax) {
+                float o[S::EC];
+                gather<K>(V.part, g, c0, o);
+                fwd_epilogue<K>(V, xc, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
+                if (tid < kG) {
+                    gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
+                    ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
+                }
+            }
+            // the bookkeeping of step t-1, off the path to the exchange: X_t is on its way; the
+            // checkpoint reads this CTA's half of X_{t-1}, which the peer never writes
             if (tp < Tg) {
                 const bool due = cp_left == 0;
                 if (lead && r == 0) {
@@ -1220,13 +1247,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
                 }
             }
             if (t == Tmax) break;
-            float o[S::EC];
-            gather<K>(V.part, g, c0, o);
-            fwd_epilogue<K>(V, xc, r, nxt, g, c0, t < Tg, gs.sym[nxt][g], o, sc);
-            if (tid < kG) {
-                gs.sym[cur][tid] = ob_next;   // o_{t+1}, read at step t+1 (parity of t+1 == cur)
-                ob_next = t + 2 < gs.T[tid] ? p.obs[gs.o0[tid] + t + 2] : 0;
-            }
             xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status, peer_half);
         }
         cl.sync();
@@ -1300,30 +1320,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
             if (tt < maxL) contract<K>(m, V.sX + cur * kG * K, V.part, gsize);
             __syncthreads();                  // partials complete; the peer's half of X_{tt-1} and
                                               // its row sums visible to every thread
+            int ex = 0;
             float sc = 1.f;
             if (tt >= 2) {
-                const float c = row_sum(V.red, cur, g);
-                int ex = 0;
-                frexpf(c, &ex);
-                sc = ldexpf(1.0f, -ex);
-                const int tp = tt - 1;
-                if (tp < Lg) {
-                    if (lead && r == 0) p.ebuf[rowb + tp] = ex;
-                    float v[S::EC];
-                    ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
-    #pragma unroll
-                    for (int e = 0; e < S::EC; ++e) v[e] *= sc;
-                    stv<S::EC>(p.P + (rowb + tp) * K + r * S::Kh + c0, v);
+                ex = scale_exp(row_sum(V.red, cur, g));
+                sc = pow2_scale(ex);
+            }
+            if (tt < maxL) {
+                float o[S::EC];
+                gather<K>(V.part, g, c0, o);
+                fwd_epilogue<K>(V, xc, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
+                if (tid < kG) {
+                    gs.sym[cur][tid] = ob_next;
+                    ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
                 }
             }
-            if (tt == maxL) break;
-            float o[S::EC];
-            gather<K>(V.part, g, c0, o);
-            fwd_epilogue<K>(V, xc, r, nxt, g, c0, tt < Lg, gs.sym[nxt][g], o, sc);
-            if (tid < kG) {
-                gs.sym[cur][tid] = ob_next;
-                ob_next = tt + 2 < gs.L[tid] ? p.obs[gs.o0[tid] + gs.t0[tid] + tt + 2] : 0;
+            // the P row of step tt-1, off the path to the exchange: X_tt is on its way; the row
+            // is this CTA's half of X_{tt-1}, which the peer never writes
+            if (tt >= 2 && tt - 1 < Lg) {
+                const int tp = tt - 1;
+                if (lead && r == 0) p.ebuf[rowb + tp] = ex;
+                float v[S::EC];
+                ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
+    #pragma unroll
+                for (int e = 0; e < S::EC; ++e) v[e] *= sc;
+                stv<S::EC>(p.P + (rowb + tp) * K + r * S::Kh + c0, v);
             }
+            if (tt == maxL) break;
             xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status, peer_half);
         }
         cl.sync();
@@ -1463,8 +1486,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
                 float o[S::EC];
                 gather<K>(V.part, g, c0, o);
                 const bool trans = prev_sym >= 0;
-                const float down = ldexpf(1.0f, -e_t);
-                const float up = wg * ldexpf(1.0f, e_t);
+                const float down = pow2_scale(e_t);
+                const float up = wg * pow2_scale(-e_t);
                 const float cinv = trans ? 0.f : 1.0f / p.clast[gs.seq[g]];
                 float gm[S::EC];
     #pragma unroll
