@@ -18,7 +18,10 @@
 //    fixup kernel that folds the preceding tiles' carry-outs in tile order.
 #include "common.cuh"
 
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 namespace accel {
 namespace segred {
@@ -53,6 +56,17 @@ __global__ void k_partition_scatter(const int64_t* __restrict__ off, int64_t S, 
     const int64_t tprev = s == 0 ? -1 : seg_key(off, s - 1, N) / tile;
     const int64_t tcur = s == S ? ntiles : seg_key(off, s, N) / tile;
     for (int64_t b = tprev + 1; b <= tcur; ++b) lo[b] = s;
+}
+
+// Bring the 16 KB tile `b` into L2 ahead of its CTA (full tiles only; no completion to wait
+// for).  A CTA prefetches the tile about half a wave of resident CTAs ahead of its own, so
+// the CTA that later takes it finds it in L2: more bytes in flight than the resident CTAs'
+// own loads alone.
+template <typename Tin>
+__device__ __forceinline__ void prefetch_tile(const Tin* data, int64_t N, int64_t b) {
+    constexpr int64_t TE = kTileBytes / (int64_t)sizeof(Tin);
+    if ((b + 1) * TE <= N)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(data + b * TE), "r"((uint32_t)kTileBytes) : "memory");
 }
 
 template <typename C> struct KV { int32_t k; C v; };
@@ -124,7 +138,7 @@ template <typename Tin, typename Tout, int OP>
 __global__ void __launch_bounds__(kThreads)
 k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
             const int64_t* __restrict__ lo_arr, int map_op, double scalar, Tout* __restrict__ out,
-            int64_t* __restrict__ tail_seg, typename compute_of<Tout>::type* __restrict__ tail_val) {
+            int64_t* __restrict__ tail_seg, typename compute_of<Tout>::type* __restrict__ tail_val, int64_t pf) {
     using C = typename compute_of<Tout>::type;
     constexpr int IT = items<Tin>();
     constexpr int TE = tile_elems<Tin>();
@@ -138,6 +152,7 @@ k_segreduce(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__
     const int64_t e0 = b * TE;
     const int ne = (int)((e0 + TE < N) ? TE : N - e0);   // elements in this tile
     const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
+    if (t == 0 && pf > 0) prefetch_tile(data, N, b + pf);
     const C nel = red_neutral<C>(OP);
     const Tout nel_out = red_neutral<Tout>(OP);   // an empty segment: the output type's own neutral
     const C sc = (C)scalar;
@@ -295,7 +310,7 @@ template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kThreads)
 k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ off, int64_t S,
          const int64_t* __restrict__ lo_arr, int map_op, double scalar, Tout* __restrict__ out,
-         int64_t* __restrict__ tail_seg, int64_t* __restrict__ tail_val) {
+         int64_t* __restrict__ tail_seg, int64_t* __restrict__ tail_val, int64_t pf) {
     constexpr int IT = items<Tin>();
     constexpr int TE = tile_elems<Tin>();
     constexpr int PV = 16 / (int)sizeof(Tin);
@@ -313,6 +328,7 @@ k_segsum(const Tin* __restrict__ data, int64_t N, const int64_t* __restrict__ of
     const int64_t lo_b = lo_arr[b], hi_b = lo_arr[b + 1];
     const int64_t sc = (int64_t)scalar;
     const bool fast = map_op == ACCEL_MAP_SQ_PLUS_ONE && ne == TE;
+    if (t == 0 && pf > 0) prefetch_tile(data, N, b + pf);
 
     if (ne == TE) {
         const int4* src = reinterpret_cast<const int4*>(data + e0);
@@ -480,6 +496,28 @@ static Layout layout(int64_t N, int64_t S, size_t in_size) {
     return L;
 }
 
+// Tiles half a wave ahead: half the CTAs resident at once on the device (measured at 2^20
+// segments: half a wave 3,452 GB/s, one wave 3,409, two waves 3,342, none 3,187).
+template <typename KernT>
+static int64_t prefetch_distance(KernT kern) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int64_t> cache;   // per device and kernel
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_pair(dev, (const void*)kern);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    const int64_t d = (int64_t)per_sm * num_sms() / 2;
+    cache[key] = d;
+    return d;
+}
+
 template <typename Tin, typename Tout>
 static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t N, const int64_t* d_off,
                         int64_t S, double scalar, void* d_out, void* d_ws, cudaStream_t st) {
@@ -512,7 +550,8 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
     if constexpr (std::is_integral<C>::value) {
         if (op == ACCEL_RED_ADD) {
             k_segsum<Tin, Tout><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
-                (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, (int64_t*)tval);
+                (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, (int64_t*)tval,
+                prefetch_distance(k_segsum<Tin, Tout>));
             k_fixup<Tout, ACCEL_RED_ADD><<<(unsigned)((L.ntiles + 255) / 256), 256, 0, st>>>(d_off, lo, L.ntiles, te,
                                                                                             tseg, tval, out);
             return after_launch(st, "accel_segreduce", 3);
@@ -520,7 +559,8 @@ static accel_status run(int32_t op, int32_t map_op, const void* d_data, int64_t 
     }
     ACCEL_DISPATCH_RED(op, OPC, {
         k_segreduce<Tin, Tout, OPC><<<(unsigned)L.ntiles, kThreads, 0, st>>>(
-            (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, tval);
+            (const Tin*)d_data, N, d_off, S, lo, map_op, scalar, out, tseg, tval,
+            prefetch_distance(k_segreduce<Tin, Tout, OPC>));
         k_fixup<Tout, OPC><<<(unsigned)((L.ntiles + 255) / 256), 256, 0, st>>>(d_off, lo, L.ntiles, te, tseg, tval, out);
     });
     return after_launch(st, "accel_segreduce", 3);
