@@ -173,6 +173,8 @@ class Workload:
         self.bf16_out = torch.empty(q["S"], dtype=torch.float64, device=self.dev)
         side = torch.cuda.Stream()
         self.side = torch.cuda.Stream()     # the overlapped BF16 row of a step
+        self.side2 = torch.cuda.Stream()    # ... and the adjoint's forward phase
+        self.n_sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
         torch.cuda.synchronize()
         g = api.Graph()
         g.capture(lambda: api.hmm_forward(q["log_A"], q["log_B"], q["log_pi"], q["obs"], q["offsets"],
@@ -237,8 +239,37 @@ class Workload:
     # after another on the current stream, so each row's time is its own.  Without it the
     # step overlaps independent rows: the batched BF16 forward -- a latency-bound persistent
     # launch whose CTAs fill the register files of the SMs they hold and leave the others
-    # idle -- runs on a second stream while the seg-reduce, plain FP32 and all-pairs rows run
-    # on the rest of the GPU; the adjoint and the re-estimation, which want every SM, follow.
+    # idle -- runs on a second stream; the adjoint's forward phase runs on a third within the
+    # SMs the BF16 launch leaves (accel_set_sm_budget), and the seg-reduce, plain FP32 and
+    # all-pairs rows on the main stream take what is free; the adjoint's backward rounds and
+    # the re-estimation, which want every SM, follow.
+    def adj_budget(self):
+        units = (self.tuned or {}).get("units", 0)
+        nc = 2 if (self.tuned or {}).get("pair", 0) == 1 else 4 if (self.tuned or {}).get("pair", 0) == 2 else 1
+        free = self.n_sms - units * nc
+        return free if units > 0 and free > 0 else 0
+
+    def adj_forward_side(self, cur, adj_inputs):
+        """The adjoint's forward phase on the third stream within the free SMs; returns
+        (logL, saved state, event)."""
+        api, torch = self.api, self.torch
+        a = adj_inputs
+        e_in = torch.cuda.Event()
+        e_in.record(cur)
+        self.side2.wait_event(e_in)
+        with torch.cuda.stream(self.side2):
+            api.set_sm_budget(self.adj_budget())
+            try:
+                ll, saved = api.hmm_adjoint_forward(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"],
+                                                    max_T=self.adj["maxT"])
+            finally:
+                api.set_sm_budget(0)
+            e_af = torch.cuda.Event()
+            e_af.record(self.side2)
+        ll.record_stream(cur)
+        saved.ws.record_stream(cur)
+        return ll, saved, e_af
+
     def step(self, ev=None):
         api, torch = self.api, self.torch
         overlap = ev is None and self.bf16_graph is not None
@@ -250,6 +281,8 @@ class Workload:
             self.bf16_graph.launch(stream=self.side)
             e_bf16 = torch.cuda.Event()
             e_bf16.record(self.side)
+            if self.adj is not None:
+                adj_ll, adj_saved, e_af = self.adj_forward_side(cur, self.adj)
 
         def mark(name, fn):
             if ev is None:
@@ -301,7 +334,12 @@ class Workload:
                 # one pass: the adjoint's checkpointed forward returns logL, then the backward
                 return api.hmm_adjoint(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"],
                                        max_T=a["maxT"], want_loglik=True)
-            out["adj"] = mark("hmm_adjoint", adjoint)
+            if overlap:
+                cur.wait_event(e_af)
+                g3 = api.hmm_adjoint_backward(a["log_A"], a["log_B"], a["log_pi"], a["obs"], a["offsets"], adj_saved)
+                out["adj"] = (*g3, adj_ll)
+            else:
+                out["adj"] = mark("hmm_adjoint", adjoint)
             g = out["adj"]
             # the re-estimation that follows the adjoint in a training step
             out["mstep"] = mark("hmm_mstep", lambda: api.hmm_mstep(a["log_A"], a["log_B"], a["log_pi"], g[0], g[1],
@@ -334,6 +372,14 @@ class Workload:
             r_bf16 = api.hmm_forward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"], api.HMM_BF16_SCALED)
             e_bf16 = torch.cuda.Event()
             e_bf16.record(self.side)
+        if self.adj is not None:
+            # the adjoint's inputs and forward phase on the third stream (as in step())
+            self.side2.wait_event(e_in)
+            with torch.cuda.stream(self.side2):
+                dadj = {k: v.to(dev, non_blocking=True) for k, v in host["adj"].items()}
+            adj_ll, adj_saved, e_af = self.adj_forward_side(st, dadj)
+            for v in dadj.values():
+                v.record_stream(st)
         h = host["plain"]
         d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
         res.append(api.hmm_forward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"], api.HMM_FP32_LOG))
@@ -344,12 +390,12 @@ class Workload:
         r_bf16.record_stream(st)
         res.append(r_bf16)
         if self.adj is not None:
-            h = host["adj"]
-            d = {k: v.to(dev, non_blocking=True) for k, v in h.items()}
-            gA, gB, gpi, ll = api.hmm_adjoint(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"],
-                                              max_T=self.adj["maxT"], want_loglik=True)
+            st.wait_event(e_af)
+            d = dadj
+            gA, gB, gpi = api.hmm_adjoint_backward(d["log_A"], d["log_B"], d["log_pi"], d["obs"], d["offsets"],
+                                                   adj_saved)
             th, nw = api.hmm_mstep(d["log_A"], d["log_B"], d["log_pi"], gA, gB, gpi)
-            res += [gA, gB, gpi, ll, *th, *nw]
+            res += [gA, gB, gpi, adj_ll, *th, *nw]
         outs = [torch.empty(r.shape, dtype=r.dtype, pin_memory=True) for r in res]
         for o, r in zip(outs, res):
             o.copy_(r, non_blocking=True)
@@ -1040,10 +1086,12 @@ def main():
                                    "T U[200,2000]" + ("" if with_adj else " (adjoint not built: skipped)") +
                                    "; all-pairs N=65536",
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
-                       "schedule": "two streams: the batched BF16 forward (a CUDA graph of its 5 kernels) "
-                                   "beside the seg-reduce, plain FP32 and all-pairs rows, then the adjoint "
-                                   "and the re-estimation; per-row times in `rows` come from the same "
-                                   "step run row after row",
+                       "schedule": "three streams: the batched BF16 forward (a CUDA graph of its 5 kernels, "
+                                   "its tuned persistent units) beside the adjoint's forward phase within the "
+                                   "SMs it leaves (accel_set_sm_budget) and the seg-reduce, plain FP32 and "
+                                   "all-pairs rows; then the adjoint's backward phase (every SM) and the "
+                                   "re-estimation; per-row times in `rows` come from the same step run row "
+                                   "after row",
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
             "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweeps, "marshal_sweep": msweeps,
             "compare": compare, "rows": rows, "roofline": roof,

@@ -159,6 +159,18 @@ accel_status accel_sync_status(int32_t* d_status, int32_t clear, void* stream);
 void accel_set_watchdog_ns(uint64_t budget_ns);
 uint64_t accel_get_watchdog_ns(void);
 
+/*
+ * accel_set_sm_budget -- the most SMs the forward recursion of hmm_adjoint /
+ * hmm_adjoint_forward may occupy (its persistent CTA-pair launch, K in {64, 128, 256} with
+ * planned groups), so that it can run beside another stream's persistent kernel instead of
+ * waiting for the whole GPU: the launch takes min(n, #SMs) / 2 pairs, but at least enough to
+ * hold every sequence in two groups of 16.  0 (the default) means every SM.  The backward
+ * rounds always use every SM.  Results do not depend on it (each sequence's forward
+ * arithmetic is the same in any group).  Per host thread; read when a call is issued.
+ */
+void accel_set_sm_budget(int32_t n_sms);
+int32_t accel_get_sm_budget(void);
+
 /* =========================================================== marshaling (Sec. 3.3) */
 /*
  * accel_marshal_ragged -- flatten a host list of S sequences (Appendix A `flatten`,

@@ -18,7 +18,7 @@ from ._lib import (  # noqa: F401
 
 _API = {"accel_marshal_ragged", "accel_marshal_ragged_table", "accel_marshal_nested", "accel_unmarshal_ragged", "ragged_table", "accel_marshal_records", "accel_map", "accel_reduce", "accel_segreduce",
         "accel_loop", "hmm_forward", "hmm_forward_long", "hmm_adjoint", "hmm_mstep", "hmm_autotune", "Graph", "HMMLogLik", "pairwise_mapreduce", "accel_pair_histogram",
-        "set_debug", "version", "set_device_status", "sync_status", "set_watchdog_ns", "hmm_max_length", "alu_rate",
+        "set_debug", "version", "set_device_status", "sync_status", "set_watchdog_ns", "set_sm_budget", "get_sm_budget", "hmm_max_length", "alu_rate",
         "hmm_adjoint_forward", "hmm_adjoint_backward"}
 
 

@@ -55,6 +55,8 @@ SIGNATURES = {
     "accel_sync_status": (i32, [vp, i32, vp]),
     "accel_set_watchdog_ns": (None, [C.c_uint64]),
     "accel_get_watchdog_ns": (C.c_uint64, []),
+    "accel_set_sm_budget": (None, [C.c_int32]),
+    "accel_get_sm_budget": (C.c_int32, []),
     "hmm_max_length": (i32, [vp, i64, vp, vp]),
     "accel_alu_rate": (i32, [i32, i64, vp, vp, vp]),
     "accel_marshal_ragged_workspace_size": (sz, [i64]),

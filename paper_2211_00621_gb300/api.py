@@ -79,6 +79,15 @@ def set_watchdog_ns(budget_ns: int):
     L.load().accel_set_watchdog_ns(int(budget_ns))
 
 
+def set_sm_budget(n_sms: int):
+    """Most SMs the adjoint's forward recursion may occupy on this host thread (0 = all)."""
+    L.load().accel_set_sm_budget(int(n_sms))
+
+
+def get_sm_budget() -> int:
+    return int(L.load().accel_get_sm_budget())
+
+
 def alu_rate(kind: int, iters: int = 4096, device="cuda") -> float:
     """Measured arithmetic rate of the device (operations per second) for one of
     PROBE_FFMA / PROBE_FFMA2 (FP32 flop), PROBE_RSQRT (MUFU ops), PROBE_DFMA (FP64 flop)."""

@@ -16,6 +16,8 @@ static std::atomic<unsigned long long> g_watchdog_ns{0};  // accel_set_watchdog_
 
 int32_t* status_word(int32_t* fallback) { return g_status_word ? g_status_word : fallback; }
 uint64_t watchdog_ns() { return g_watchdog_ns.load(std::memory_order_relaxed); }
+static thread_local int32_t g_sm_budget = 0;                 // accel_set_sm_budget
+int32_t sm_budget() { return g_sm_budget; }
 
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
@@ -157,6 +159,8 @@ accel_status accel_sync_status(int32_t* d_status, int32_t clear, void* stream) {
 
 void accel_set_watchdog_ns(uint64_t budget_ns) { accel::g_watchdog_ns.store(budget_ns); }
 uint64_t accel_get_watchdog_ns(void) { return accel::g_watchdog_ns.load(); }
+void accel_set_sm_budget(int32_t n_sms) { accel::g_sm_budget = n_sms < 0 ? 0 : n_sms; }
+int32_t accel_get_sm_budget(void) { return accel::g_sm_budget; }
 
 }  // extern "C"
 

@@ -155,6 +155,8 @@ constexpr size_t kStatusBytes = 256;
 int32_t* status_word(int32_t* fallback);
 // Watchdog budget of the persistent single-CTA BF16 forward (accel_set_watchdog_ns; 0 = off).
 uint64_t watchdog_ns();
+// SM budget of the adjoint's forward recursion on this host thread (accel_set_sm_budget; 0 = all).
+int32_t sm_budget();
 
 // Record a device-side error: the first error stays (compare-and-swap from ACCEL_OK), so a
 // word shared by several calls keeps the earliest failure until the caller clears it.

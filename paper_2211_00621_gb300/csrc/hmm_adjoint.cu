@@ -70,7 +70,8 @@ struct Prm {
     int32_t* ebuf;      // exponents e_t of the P rows [S][Cmax] (cluster path)
     float* gam;         // weighted posteriors gamma_t of the rows [S][Cmax][K] (cluster path)
     int32_t* osym;      // o_t of each row, -1 for none [S][Cmax] (cluster path)
-    int64_t ncl;        // cluster path: number of CTA pairs
+    int64_t ncl;        // cluster path: number of CTA pairs (the backward rounds; the plans' stride)
+    int64_t ncl_fwd;    // cluster path: CTA pairs of the forward recursion (<= ncl; the SM budget)
     const int64_t* plan;  // cluster path: per pass (the forward, then round 0, 1, ...) and per pair
                           // (start0, size0, start1, size1) of its sequence groups (size1 = 0: one
                           // group), or null: group_range with ncl groups
@@ -624,7 +625,7 @@ __device__ __forceinline__ void cluster_group_range(const Prm& p, int pass, int6
         start = pl[cidx * 4 + 2 * gi];
         size = (int)pl[cidx * 4 + 2 * gi + 1];
     } else {
-        group_range_n(n, p.ncl, cidx, start, size);
+        group_range_n(n, pass == 0 ? p.ncl_fwd : p.ncl, cidx, start, size);
     }
 }
 
@@ -679,8 +680,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int
         sL[i] = (int)pass_steps(p.off[sq + 1] - p.off[sq], pass);
     }
     __syncthreads();
-    const int64_t ncl = p.ncl;
-    int64_t* pl = plan + (int64_t)pass * ncl * 4;
+    const int64_t ncl = pass == 0 ? p.ncl_fwd : p.ncl;   // pairs of this pass
+    int64_t* pl = plan + (int64_t)pass * p.ncl * 4;
     const int64_t lo16 = (n + 15) / 16;
     const int64_t nv_lo = lo16 > (ncl < n ? ncl : n) ? lo16 : (ncl < n ? ncl : n);
     int64_t nv_hi = 2 * ncl < n ? 2 * ncl : n;
@@ -1657,6 +1658,7 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     p.gam = (float*)(ws + L.gam);
     p.osym = (int32_t*)(ws + L.osym);
     p.ncl = 0;
+    p.ncl_fwd = 0;
     p.plan = nullptr;
     p.rlist = (int32_t*)(ws + L.rlist);
     p.rrow = (int32_t*)(ws + L.rrow);
@@ -1688,12 +1690,21 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
         const int64_t ncl_sm = S < (int64_t)(num_sms() / 2) ? S : (int64_t)(num_sms() / 2);
         if (ncl_min <= 2 * ncl_sm && 2 * ncl_sm <= clu::kPlanMaxGroups && S <= clu::kPlanMaxSeq) {
             // one pair per two SMs, each running one or two groups (planned on the device
-            // from the sorted lengths by the forward phase)
+            // from the sorted lengths by the forward phase); the forward recursion within the
+            // SM budget, with at least the pairs that hold every sequence in two groups
             p.ncl = ncl_sm;
+            p.ncl_fwd = ncl_sm;
+            const int64_t budget = sm_budget();
+            if (budget > 0 && budget / 2 < ncl_sm) {
+                const int64_t need = (ncl_min + 1) / 2;
+                p.ncl_fwd = budget / 2 > need ? budget / 2 : need;
+                if (p.ncl_fwd < 1) p.ncl_fwd = 1;
+            }
             p.plan = (int64_t*)(ws + L.plan);
             P.planned = true;
         } else {
             p.ncl = ncl_min > ncl_sm ? ncl_min : ncl_sm;
+            p.ncl_fwd = p.ncl;
         }
     }
     return ACCEL_OK;
@@ -1725,7 +1736,7 @@ static accel_status run_forward(Plan& P, const accel_hmm_model* m, double* d_log
             clu::k_plan<<<(unsigned)(L.Cmax + 1), clu::kPlanThreads, 0, st>>>(p, (int64_t*)p.plan, K == 256 ? 8 : 16);
             ++nlaunch;
         }
-        const unsigned grid = (unsigned)(2 * p.ncl);
+        const unsigned grid = (unsigned)(2 * p.ncl_fwd);
         const clu::Kernels kc = clu::kernels_for(K);
         ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
         kc.fwd<<<grid, clu::kT, P.sm_c, st>>>(p);

@@ -230,3 +230,26 @@ def test_repeated_calls_are_bit_identical(K, M, S, lo, hi):
         else:
             for a, b in zip(g, ref):
                 assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("budget", [40, 8])
+def test_sm_budget_gives_identical_results(budget):
+    # the forward recursion on fewer SMs (more groups per CTA pair) computes every sequence
+    # with the same arithmetic: logL, checkpoints and gradients are bit-identical
+    p = synth.hmm_workload(77, 256, 64, 200, "uniform", 50, 500)
+    logs, t, obs, off = _dev(p)
+    w = torch.from_numpy(synth.rng(7).uniform(0.0, 2.0, size=200)).to(DEV)
+    ref = [x.clone() for x in api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w)[:4]]
+    try:
+        api.set_sm_budget(budget)
+        assert api.get_sm_budget() == budget
+        got = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w)[:4]
+        ll, saved = api.hmm_adjoint_forward(t["log_A"], t["log_B"], t["log_pi"], obs, off)
+    finally:
+        api.set_sm_budget(0)
+    g2 = api.hmm_adjoint_backward(t["log_A"], t["log_B"], t["log_pi"], obs, off, saved, weights=w)
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    for a, b in zip(g2, ref[:3]):
+        assert torch.equal(a, b)
+    assert torch.equal(ll, ref[3])
