@@ -72,15 +72,23 @@ struct Prm {
     int32_t* osym;      // o_t of each row, -1 for none [S][Cmax] (cluster path)
     int64_t ncl;        // cluster path: number of CTA pairs (the backward rounds; the plans' stride)
     int64_t ncl_fwd;    // cluster path: CTA pairs of the forward recursion (<= ncl; the SM budget)
-    const int64_t* plan;  // cluster path: per pass (the forward, then round 0, 1, ...) and per pair
-                          // (start0, size0, start1, size1) of its sequence groups (size1 = 0: one
-                          // group), or null: group_range with ncl groups
+    const int64_t* plan;  // cluster path: per pass (0: the forward; 1 + r: the backward of round r;
+                          // 1 + Cmax + r: the recomputation of round r) and per pair (start0,
+                          // size0, start1, size1) of its sequence groups (size1 = 0: one group),
+                          // or null: group_range with ncl groups
     // cluster path, per round r: the sorted positions of the sequences with a segment in round
     // r (rlist[r][i], in sorted order), the first row of each in the round's row buffers
     // (rrow[r][i]: rows are packed, each sequence taking its segment length), and their number
     const int32_t* rlist;
     const int32_t* rrow;
     const int32_t* rcount;
+    // cluster path: odd rounds' P rows and exponents (even rounds use P and ebuf), so one
+    // launch may recompute round r + 1 while it runs the backward of round r
+    float* P2;
+    int32_t* ebuf2;
+    // cluster path with plans: per backward launch l (the backward of round l - 1 beside the
+    // recomputation of round l), the CTA pairs given to the backward; the rest recompute
+    const int32_t* split;
 };
 
 // The scale exponent of a row sum c: c = m 2^e with m in [0.5, 1) (the frexp convention),
@@ -608,12 +616,17 @@ __device__ __forceinline__ void group_range_n(int64_t S, int64_t ngroups, int64_
     size = (int)(base + (jj >= firstbig ? 1 : 0));
 }
 
-// The sequence groups CTA pair cidx runs in pass `pass` (0: the forward; 1 + r: round r), one
-// after the other (1 or 2).  Groups are ranges of the pass's sequence list (the forward: all
-// sorted positions; round r: rlist[r]) of n entries.
+// The sequence groups CTA pair cidx runs in pass `pass` (0: the forward; 1 + r: the backward
+// of round r; 1 + Cmax + r: the recomputation of round r), one after the other (1 or 2).
+// Groups are ranges of the pass's sequence list (the forward: all sorted positions; round r:
+// rlist[r]) of n entries.
 __device__ __forceinline__ const int64_t* pass_plan(const Prm& p, int pass) {
     return p.plan ? p.plan + (int64_t)pass * p.ncl * 4 : nullptr;
 }
+// The P rows and exponents of round r: even rounds in P / ebuf, odd rounds in P2 / ebuf2 (a
+// launch recomputes round r + 1 while its backward of round r reads round r's rows).
+__device__ __forceinline__ float* round_P(const Prm& p, int round) { return (round & 1) ? p.P2 : p.P; }
+__device__ __forceinline__ int32_t* round_e(const Prm& p, int round) { return (round & 1) ? p.ebuf2 : p.ebuf; }
 __device__ __forceinline__ int cluster_groups(const Prm& p, int pass, int64_t cidx) {
     const int64_t* pl = pass_plan(p, pass);
     return (pl && pl[cidx * 4 + 3] > 0) ? 2 : 1;
@@ -634,18 +647,37 @@ __device__ __forceinline__ void cluster_group_range(const Prm& p, int pass, int6
 // shortest, then share a pair with another group and run after it.  A step of a group of g
 // sequences costs about (0.92 + ceil(g / GP)) contraction passes (measured: a pass of 8
 // sequences ~2,840 cycles at K = 256, the rest of the step ~2,620), so a pair's time in a pass
-// is the sum over its groups of (the group's longest step count) x that cost.  One plan per
-// pass: the forward (step counts T over all sequences) and every backward round r (step
-// counts = the segment lengths of round r over the sequences that have one).  The rounds need
-// their own plans: segment lengths grow like sqrt(T), so a grouping balanced for T leaves the
-// pairs that run two groups of short sequences as the slowest of every round.
-// One CTA per pass, one thread per candidate group count nv in [nv_lo, nv_hi]: it splits the
-// pass's list with group_range_n; the first ncl groups (the longest) take one pair each and
-// surplus group ncl + k joins pair ncl - 1 - k (the least loaded first); the candidate with
-// the smallest maximum load writes the plan.
-constexpr int kPlanThreads = 128;
+// is the sum over its groups of (the group's longest step count) x that cost.  A plan of nv
+// groups on c pairs gives the first c groups (the longest) one pair each, and surplus group
+// c + k joins pair c - 1 - k (the least loaded first); the group count with the smallest
+// maximum load wins.
+//
+// One plan per pass: the forward (step counts T over all sequences) and, for every round r,
+// the backward and the recomputation (step counts = the segment lengths of round r over the
+// sequences that have one).  Segment lengths grow like sqrt(T), so a grouping balanced for T
+// would leave the pairs that run two groups of short sequences as the slowest of every round.
+//
+// The backward of round r and the recomputation of round r + 1 are independent, so they share
+// one launch (backward launch r + 1).  Either they run side by side, the backward on nb pairs
+// and the recomputation on the other ncl - nb, or each on all ncl pairs, the recomputation's
+// pairs starting as the backward's finish.  The planner takes the split with the smallest
+// estimated time: the larger of the two passes' maximum loads side by side, their sum
+// otherwise (a backward step costs about 1.14 recomputation steps, measured at K = 256).  One
+// pass alone on all pairs has to round 13-14 sequences a pair up to two contraction passes a
+// step; two passes side by side can use groups of 16 and balance what is left between them.
+//
+// One CTA per launch (block 0: the forward).  The step counts of a pass's list sit in shared
+// memory with their maxima over 2, 4, 8 and 16 consecutive entries, so a group's cost is two
+// reads.  Candidate splits: every nb for ncl <= 32, else the multiples of 4 and then the three
+// on each side of the best of them; per candidate and pass, one warp task per 32 group counts.
+constexpr int kPlanThreads = 1024;
 constexpr int kPlanMaxGroups = 256;
 constexpr int kPlanMaxSeq = 16 * kPlanMaxGroups;
+constexpr int kPlanMaxCand = 40;
+constexpr int kPlanLevels = 5;
+constexpr float kBwdStepCost = 1.14f;
+
+__host__ __device__ inline size_t plan_smem_bytes() { return (size_t)2 * kPlanLevels * kPlanMaxSeq * 4; }
 
 // step count of the sequence with T steps in pass `pass` (0: T; 1 + r: its round-r segment)
 __host__ __device__ __forceinline__ int64_t pass_steps(int64_t T, int pass) {
@@ -657,76 +689,223 @@ __host__ __device__ __forceinline__ int64_t pass_steps(int64_t T, int pass) {
     return t1 - k * C;
 }
 
-__device__ __forceinline__ float plan_cost(const int* sL, int64_t n, int64_t nv, int64_t j, int gp) {
-    if (j >= nv) return 0.f;
-    int64_t st;
-    int sz;
-    group_range_n(n, nv, j, st, sz);
-    int mx = 0;
-    for (int i = 0; i < sz; ++i) mx = sL[st + i] > mx ? sL[st + i] : mx;
-    return sz > 0 ? (float)mx * (0.92f + (float)((sz + gp - 1) / gp)) : 0.f;
+// A pass's list in shared memory: lv[k][i] = max of the step counts of entries i .. i + 2^k - 1.
+struct PlanList {
+    int* lv[kPlanLevels];
+    int64_t n;
+};
+
+// max over entries [st, st + sz), 1 <= sz < 32: two overlapping windows of the level below sz
+__device__ __forceinline__ int list_max(const PlanList& t, int st, int sz) {
+    const int k = 31 - __clz(sz);
+    const int a = t.lv[k][st], b = t.lv[k][st + sz - (1 << k)];
+    return a > b ? a : b;
 }
 
-// Block b plans pass b into plan[b][ncl][4].
-__global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int gp) {
-    __shared__ int sL[kPlanMaxSeq];                 // step counts in list order
-    __shared__ float s_v[kPlanThreads];
-    __shared__ int s_i[kPlanThreads];
-    const int t = threadIdx.x, pass = blockIdx.x;
-    const int64_t n = pass == 0 ? p.S : p.rcount[pass - 1];
-    for (int64_t i = t; i < n; i += kPlanThreads) {
-        const int64_t q = pass == 0 ? i : p.rlist[(int64_t)(pass - 1) * p.S + i];
-        const int64_t sq = p.order[q];
-        sL[i] = (int)pass_steps(p.off[sq + 1] - p.off[sq], pass);
+// group_range_n(n, nv, .) with its divisions done once per group count
+struct Groups {
+    int64_t n8, base, firstbig;
+};
+__device__ __forceinline__ Groups groups_of(int64_t n, int64_t nv) {
+    Groups g;
+    g.n8 = 0;
+    if (n > 8 * nv) {
+        g.n8 = (16 * nv - n) / 8;
+        if (g.n8 < 0) g.n8 = 0;
     }
-    __syncthreads();
-    const int64_t ncl = pass == 0 ? p.ncl_fwd : p.ncl;   // pairs of this pass
-    int64_t* pl = plan + (int64_t)pass * p.ncl * 4;
-    const int64_t lo16 = (n + 15) / 16;
-    const int64_t nv_lo = lo16 > (ncl < n ? ncl : n) ? lo16 : (ncl < n ? ncl : n);
-    int64_t nv_hi = 2 * ncl < n ? 2 * ncl : n;
-    if (nv_hi > nv_lo + kPlanThreads - 1) nv_hi = nv_lo + kPlanThreads - 1;
-    const int64_t nv = nv_lo + t;
-    float worst = INFINITY;
-    if (n > 0 && nv <= nv_hi) {
-        const int64_t extra = nv > ncl ? nv - ncl : 0;   // 0 <= extra <= ncl
-        worst = 0.f;
-        for (int64_t c = 0; c < ncl; ++c) {
-            float l = plan_cost(sL, n, nv, c, gp);
-            const int64_t k = ncl - 1 - c;          // surplus group ncl + k joins pair c
-            if (k < extra) l += plan_cost(sL, n, nv, ncl + k, gp);
-            worst = fmaxf(worst, l);
+    const int64_t rem = n - 8 * g.n8, m = nv - g.n8;
+    g.base = rem / m;
+    g.firstbig = m - rem % m;
+    return g;
+}
+__device__ __forceinline__ float group_cost(const PlanList& t, const Groups& g, int64_t j, int gp) {
+    int st, sz;
+    if (j < g.n8) {
+        st = (int)(8 * j);
+        sz = 8;
+    } else {
+        const int64_t jj = j - g.n8;
+        st = (int)(8 * g.n8 + jj * g.base + (jj > g.firstbig ? jj - g.firstbig : 0));
+        sz = (int)(g.base + (jj >= g.firstbig ? 1 : 0));
+    }
+    return sz > 0 ? (float)list_max(t, st, sz) * (0.92f + (float)((sz + gp - 1) / gp)) : 0.f;
+}
+
+// the largest pair load of nv groups of the list's n > 0 entries on c pairs
+__device__ float plan_worst(const PlanList& t, int64_t c, int64_t nv, int gp) {
+    const Groups g = groups_of(t.n, nv);
+    const int64_t extra = nv > c ? nv - c : 0;
+    float worst = 0.f;
+    for (int64_t q = 0; q < c && q < nv; ++q) {
+        float l = group_cost(t, g, q, gp);
+        const int64_t k = c - 1 - q;
+        if (k < extra) l += group_cost(t, g, c + k, gp);
+        worst = fmaxf(worst, l);
+    }
+    return worst;
+}
+
+// candidate group counts of n > 0 entries on c > 0 pairs: groups of at most 16, at most two
+// groups a pair, at most 128 candidates (lo > hi: none)
+__device__ __forceinline__ void nv_range(int64_t n, int64_t c, int64_t& lo, int64_t& hi) {
+    const int64_t lo16 = (n + 15) / 16, m = c < n ? c : n;
+    lo = lo16 > m ? lo16 : m;
+    hi = 2 * c < n ? 2 * c : n;
+    if (hi > lo + 127) hi = lo + 127;
+}
+
+// plan entries [0, stride) of one pass: nv groups on pairs [0, c), the rest empty
+__device__ void write_plan(const PlanList& t, int64_t* pl, int64_t stride, int64_t c, int64_t nv) {
+    const int64_t extra = nv > c ? nv - c : 0;
+    for (int64_t q = threadIdx.x; q < stride; q += blockDim.x) {
+        int64_t st = 0;
+        int sz = 0;
+        if (t.n > 0 && q < c && q < nv) group_range_n(t.n, nv, q, st, sz);
+        pl[q * 4] = st;
+        pl[q * 4 + 1] = sz;
+        pl[q * 4 + 2] = 0;
+        pl[q * 4 + 3] = 0;
+        const int64_t k = c - 1 - q;
+        if (t.n > 0 && q < c && k < extra) {
+            group_range_n(t.n, nv, c + k, st, sz);
+            pl[q * 4 + 2] = st;
+            pl[q * 4 + 3] = sz;
         }
     }
-    s_v[t] = worst;
-    s_i[t] = t;
+}
+
+// Block 0 plans the forward on ncl_fwd pairs.  Block 1 + l plans backward launch l (l in
+// [0, Cmax]): the backward of round l - 1 (list 0, if l >= 1) and the recomputation of round l
+// (list 1, if l < Cmax), and writes split[2 l] = the backward's pairs, split[2 l + 1] = the
+// recomputation's.
+__global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int32_t* split, int gp) {
+    extern __shared__ __align__(16) int s_lv[];          // [2][kPlanLevels][kPlanMaxSeq]
+    __shared__ float s_w[2][kPlanMaxCand][4];
+    __shared__ int64_t s_nv[2][kPlanMaxCand][4];
+    __shared__ int s_cb[kPlanMaxCand], s_cc[kPlanMaxCand];
+    __shared__ int s_ncand;
+    __shared__ float s_bf;
+    __shared__ int s_bcb, s_bcc;
+    __shared__ int64_t s_bnv[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int blk = blockIdx.x, l = blk - 1;
+    const bool fwd = blk == 0;
+    const int rnd[2] = {fwd ? -1 : l - 1, (!fwd && l < p.Cmax) ? l : -1};
+    const int64_t ncl = fwd ? p.ncl_fwd : p.ncl;
+    PlanList t[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+#pragma unroll
+        for (int v = 0; v < kPlanLevels; ++v) t[k].lv[v] = s_lv + (k * kPlanLevels + v) * kPlanMaxSeq;
+        t[k].n = fwd ? (k == 0 ? p.S : 0) : (rnd[k] >= 0 ? p.rcount[rnd[k]] : 0);
+    }
+    for (int k = 0; k < 2; ++k) {
+        for (int64_t i = tid; i < t[k].n; i += kPlanThreads) {
+            const int64_t q = fwd ? i : p.rlist[(int64_t)rnd[k] * p.S + i];
+            const int64_t sq = p.order[q];
+            t[k].lv[0][i] = (int)pass_steps(p.off[sq + 1] - p.off[sq], fwd ? 0 : 1 + rnd[k]);
+        }
+    }
     __syncthreads();
-    for (int d = kPlanThreads / 2; d > 0; d >>= 1) {
-        if (t < d) {
-            const float a = s_v[t], b = s_v[t + d];
-            if (b < a || (b == a && s_i[t + d] < s_i[t])) {
-                s_v[t] = b;
-                s_i[t] = s_i[t + d];
+    for (int v = 1; v < kPlanLevels; ++v) {
+        const int h = 1 << (v - 1);
+        for (int k = 0; k < 2; ++k)
+            for (int64_t i = tid; i + 2 * h <= t[k].n; i += kPlanThreads) {
+                const int a = t[k].lv[v - 1][i], b = t[k].lv[v - 1][i + h];
+                t[k].lv[v][i] = a > b ? a : b;
+            }
+        __syncthreads();
+    }
+    const bool both = !fwd && rnd[0] >= 0 && rnd[1] >= 0;
+    const int step = ncl <= 32 ? 1 : 4;
+    if (tid == 0) {
+        s_bf = INFINITY;
+        s_bcb = (int)ncl;
+        s_bcc = fwd ? 0 : (int)ncl;
+        s_bnv[0] = s_bnv[1] = 0;
+    }
+    for (int phase = 0; phase < 2; ++phase) {
+        if (tid == 0) {
+            int nc = 0;
+            if (phase == 0) {
+                if (fwd) {
+                    s_cb[nc] = (int)ncl; s_cc[nc++] = 0;
+                } else if (!both) {
+                    s_cb[nc] = rnd[0] >= 0 ? (int)ncl : 0;
+                    s_cc[nc++] = rnd[1] >= 0 ? (int)ncl : 0;
+                } else {
+                    s_cb[nc] = (int)ncl; s_cc[nc++] = (int)ncl;          // each on all pairs
+                    s_cb[nc] = (int)ncl; s_cc[nc++] = 0;                 // (an empty list)
+                    for (int nb = step; nb < ncl; nb += step) { s_cb[nc] = nb; s_cc[nc++] = (int)ncl - nb; }
+                }
+            } else if (both && step > 1 && s_bcb + s_bcc == ncl) {
+                for (int nb = s_bcb - step + 1; nb < s_bcb + step; ++nb)
+                    if (nb >= 1 && nb < ncl && nb % step != 0) { s_cb[nc] = nb; s_cc[nc++] = (int)ncl - nb; }
+            }
+            s_ncand = nc;
+        }
+        __syncthreads();
+        const int nc = s_ncand;
+        for (int task = warp; task < 2 * nc * 4; task += kPlanThreads / 32) {
+            const int k = task / (nc * 4), j = (task >> 2) % nc, q = task & 3;
+            const int64_t c = k == 0 ? s_cb[j] : s_cc[j], n = t[k].n;
+            float w = INFINITY;
+            int64_t nv = 0;
+            if (n == 0) {
+                if (q == 0 && lane == 0) w = 0.f;
+            } else if (c > 0) {
+                int64_t lo, hi;
+                nv_range(n, c, lo, hi);
+                nv = lo + 32 * q + lane;
+                if (nv <= hi) w = plan_worst(t[k], c, nv, gp);
+            }
+            // the smallest load, the fewest groups on a tie
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const float ow = __shfl_down_sync(0xffffffffu, w, d);
+                const int64_t onv = __shfl_down_sync(0xffffffffu, nv, d);
+                if (ow < w || (ow == w && onv < nv)) { w = ow; nv = onv; }
+            }
+            if (lane == 0) {
+                s_w[k][j][q] = w;
+                s_nv[k][j][q] = nv;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int j = 0; j < nc; ++j) {
+                float w2[2];
+                int64_t v2[2];
+                for (int k = 0; k < 2; ++k) {
+                    w2[k] = s_w[k][j][0];
+                    v2[k] = s_nv[k][j][0];
+                    for (int q = 1; q < 4; ++q)
+                        if (s_w[k][j][q] < w2[k]) { w2[k] = s_w[k][j][q]; v2[k] = s_nv[k][j][q]; }
+                }
+                const float wb = kBwdStepCost * w2[0], wc = w2[1];
+                const float f = s_cb[j] + s_cc[j] <= ncl ? fmaxf(wb, wc) : wb + wc;
+                if (f < s_bf) {
+                    s_bf = f;
+                    s_bcb = s_cb[j];
+                    s_bcc = s_cc[j];
+                    s_bnv[0] = v2[0];
+                    s_bnv[1] = v2[1];
+                }
             }
         }
         __syncthreads();
     }
-    const int64_t best = nv_lo + s_i[0];
-    const int64_t extra = best > ncl ? best - ncl : 0;
-    for (int64_t c = t; c < ncl; c += kPlanThreads) {
-        int64_t st = 0;
-        int sz = 0;
-        if (n > 0 && c < best) group_range_n(n, best, c, st, sz);
-        pl[c * 4] = st;
-        pl[c * 4 + 1] = sz;
-        pl[c * 4 + 2] = 0;
-        pl[c * 4 + 3] = 0;
-        const int64_t k = ncl - 1 - c;
-        if (n > 0 && k < extra) {
-            group_range_n(n, best, ncl + k, st, sz);
-            pl[c * 4 + 2] = st;
-            pl[c * 4 + 3] = sz;
-        }
+    // every launch has a feasible candidate: each list alone fits on all ncl pairs
+    const int64_t stride = p.ncl;
+    if (fwd) {
+        write_plan(t[0], plan, stride, s_bcb, s_bnv[0]);
+        return;
+    }
+    if (rnd[0] >= 0) write_plan(t[0], plan + (int64_t)(1 + rnd[0]) * stride * 4, stride, s_bcb, s_bnv[0]);
+    if (rnd[1] >= 0) write_plan(t[1], plan + (int64_t)(1 + p.Cmax + rnd[1]) * stride * 4, stride, s_bcc, s_bnv[1]);
+    if (tid == 0) {
+        split[2 * l] = s_bcb;
+        split[2 * l + 1] = s_bcc;
     }
 }
 
@@ -1259,30 +1438,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_fwd_cl(Prm 
 // S_t for t in the round's segment into the P rows (normalised), e_t into ebuf; the same
 // step structure as the forward, starting from the checkpoint row (e = its stored
 // exponent, scale 1).
+// (the groups of CTA pair cidx of the recomputation pass of round `round`; m holds A)
 template <int K>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm p, int round) {
+__device__ __forceinline__ void rec_groups(const Prm& p, int round, int64_t cidx, cg::cluster_group& cl,
+                                           const Views& V, Xchg& xc, const MatRegs<K>& m, GS& gs) {
     using S = Sh<K>;
-    cg::cluster_group cl = cg::this_cluster();
-    const int r = (int)cl.block_rank(), peer = r ^ 1;
-    const int64_t cidx = blockIdx.x >> 1;
+    const int r = (int)cl.block_rank();
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
     const bool peer_half = reads_peer_half(r);
-    extern __shared__ __align__(16) char smem[];
-    __shared__ GS gs;
-    __shared__ __align__(8) uint64_t s_xbar[2];
-    const Views V = make_views(smem, K, p.M, cl, peer);
-    Xchg xc = make_xchg(V, s_xbar, peer);
-    MatRegs<K> m;
-    m.load(p.A, p.Kp, r);
-    load_bt<K>(p.BT, p.M, r, V.BTh);
+    float* const Pw = round_P(p, round);
+    int32_t* const ew = round_e(p, round);
     // the pair's sequence groups, one after the other
+    const int pass = 1 + p.Cmax + round;
     const int64_t nlist = p.rcount[round];
-    const int ngr = cluster_groups(p, 1 + round, cidx);
+    const int ngr = cluster_groups(p, pass, cidx);
     for (int gi = 0; gi < ngr; ++gi) {
         int64_t gstart;
         int gsize;
-        cluster_group_range(p, 1 + round, nlist, cidx, gi, gstart, gsize);
+        cluster_group_range(p, pass, nlist, cidx, gi, gstart, gsize);
         load_gs(p, gs, round, gstart, gsize);
         __syncthreads();
         round_bounds_gs(gs, round);
@@ -1298,14 +1472,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
             float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gs.L[gg] > 0) {
                 sv = *reinterpret_cast<const float4*>(p.cp + (gs.seq[gg] * p.Cmax + gs.t0[gg] / gs.C[gg]) * K + cc);
-                if (cc / S::Kh == r) *reinterpret_cast<float4*>(p.P + (int64_t)gs.rowb[gg] * K + cc) = sv;
+                if (cc / S::Kh == r) *reinterpret_cast<float4*>(Pw + (int64_t)gs.rowb[gg] * K + cc) = sv;
             }
             *reinterpret_cast<float4*>(V.sX + gg * K + pcol(cc)) = sv;
         }
         int ob_next = 0;
         if (tid < kG) {
             const int q = tid;
-            if (gs.L[q] > 0 && r == 0) p.ebuf[gs.rowb[q]] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
+            if (gs.L[q] > 0 && r == 0) ew[gs.rowb[q]] = p.cp_e[gs.seq[q] * p.Cmax + gs.t0[q] / gs.C[q]];
             const int64_t b0 = gs.o0[q] + gs.t0[q];
             gs.sym[1][q] = gs.L[q] > 1 ? p.obs[b0 + 1] : 0;
             ob_next = gs.L[q] > 2 ? p.obs[b0 + 2] : 0;
@@ -1340,12 +1514,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
             // is this CTA's half of X_{tt-1}, which the peer never writes
             if (tt >= 2 && tt - 1 < Lg) {
                 const int tp = tt - 1;
-                if (lead && r == 0) p.ebuf[rowb + tp] = ex;
+                if (lead && r == 0) ew[rowb + tp] = ex;
                 float v[S::EC];
                 ldv_p<S::EC>(V.sX + (cur * kG + g) * K, r * S::Kh + c0, v);
     #pragma unroll
                 for (int e = 0; e < S::EC; ++e) v[e] *= sc;
-                stv<S::EC>(p.P + (rowb + tp) * K + r * S::Kh + c0, v);
+                stv<S::EC>(Pw + (rowb + tp) * K + r * S::Kh + c0, v);
             }
             if (tt == maxL) break;
             xchg_finish(xc, nxt, xchg_bytes<K>(true), p.status, peer_half);
@@ -1363,30 +1537,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm 
 // registers of the thread that owns the (sequence, state) pair.
 //   sym(tt) = o_{t0+tt} if t0+tt < T and tt <= L, else -1: the epilogue symbol o_t of an
 //   active step and the symbol of v_t; sym(tt+1) >= 0 says whether step tt is a transition.
+// (the groups of CTA pair cidx of the backward pass of round `round`; m holds A^T)
 template <int K>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm p, int round) {
+__device__ __forceinline__ void bwd_groups(const Prm& p, int round, int64_t cidx, cg::cluster_group& cl,
+                                           const Views& V, Xchg& xc, const MatRegs<K>& m, GS& gs) {
     using S = Sh<K>;
-    cg::cluster_group cl = cg::this_cluster();
-    const int r = (int)cl.block_rank(), peer = r ^ 1;
-    const int64_t cidx = blockIdx.x >> 1;
+    const int r = (int)cl.block_rank();
     const int tid = threadIdx.x, g = tid >> 4, c0 = (tid & 15) * S::EC;
     const bool lead = (tid & 15) == 0;
     const bool peer_half = reads_peer_half(r);
-    extern __shared__ __align__(16) char smem[];
-    __shared__ GS gs;
-    __shared__ __align__(8) uint64_t s_xbar[2];
-    const Views V = make_views(smem, K, p.M, cl, peer);
-    Xchg xc = make_xchg(V, s_xbar, peer);
-    MatRegs<K> m;
-    m.load(p.At, p.Kp, r);
-    load_bt<K>(p.BT, p.M, r, V.BTh);
+    const float* const Pr = round_P(p, round);
+    const int32_t* const er = round_e(p, round);
     // the pair's sequence groups, one after the other
+    const int pass = 1 + round;
     const int64_t nlist = p.rcount[round];
-    const int ngr = cluster_groups(p, 1 + round, cidx);
+    const int ngr = cluster_groups(p, pass, cidx);
     for (int gi = 0; gi < ngr; ++gi) {
         int64_t gstart;
         int gsize;
-        cluster_group_range(p, 1 + round, nlist, cidx, gi, gstart, gsize);
+        cluster_group_range(p, pass, nlist, cidx, gi, gstart, gsize);
         load_gs(p, gs, round, gstart, gsize);
         __syncthreads();
         round_bounds_gs(gs, round);
@@ -1407,7 +1576,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             const int64_t t = gs.t0[q] + tt;
             return (tt <= gs.L[q] && t < gs.T[q] && gs.seq[q] >= 0) ? p.obs[gs.o0[q] + t] : -1;
         };
-        auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? p.ebuf[(int64_t)gs.rowb[q] + tt] : 0; };
+        auto e_at = [&](int q, int tt) -> int { return tt < gs.L[q] ? er[(int64_t)gs.rowb[q] + tt] : 0; };
         int nsym = -1, ne = 0;                // thread q < 16: scalars of step tt-1, loaded one step ahead
         if (tid < kG) {
             const int q = tid;
@@ -1464,7 +1633,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
             // contraction runs (keeps registers free)
             float* st_row = V.St + g * S::Kh;      // chunk-permuted like the vectors
             if (on) {
-                const float* src = p.P + (rowb + tt) * K + jc;
+                const float* src = Pr + (rowb + tt) * K + jc;
     #pragma unroll
                 for (int e = 0; e < S::EC; e += 2) {
                     if constexpr (S::EC % 4 == 0) {
@@ -1526,17 +1695,45 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm 
     }
 }
 
+// One launch of the backward phase (see k_plan): CTA pairs [0, nb) run the backward of round
+// rb, pairs [rbase, rbase + nr) the recomputation of round rc (rb, rc < 0: none).  nb < 0
+// takes nb and nr from the plan of backward launch rb + 1.  rbase = nb when both fit side by
+// side on the ncl pairs, else ncl: the recomputation's pairs start as the backward's finish.
+template <int K>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_round_cl(Prm p, int rb, int rc, int nb, int nr) {
+    if (nb < 0) {
+        nb = p.split[2 * (rb + 1)];
+        nr = p.split[2 * (rb + 1) + 1];
+    }
+    const int64_t rbase = (int64_t)nb + nr <= p.ncl ? nb : p.ncl;
+    const int64_t pair = blockIdx.x >> 1;
+    const bool bwd = rb >= 0 && pair < nb;
+    const bool rec = !bwd && rc >= 0 && pair >= rbase && pair < rbase + nr;
+    if (!bwd && !rec) return;             // both CTAs of the pair leave, before any remote access
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank(), peer = r ^ 1;
+    extern __shared__ __align__(16) char smem[];
+    __shared__ GS gs;
+    __shared__ __align__(8) uint64_t s_xbar[2];
+    const Views V = make_views(smem, K, p.M, cl, peer);
+    Xchg xc = make_xchg(V, s_xbar, peer);
+    MatRegs<K> m;
+    m.load(bwd ? p.At : p.A, p.Kp, r);
+    load_bt<K>(p.BT, p.M, r, V.BTh);
+    if (bwd) bwd_groups<K>(p, rb, pair, cl, V, xc, m, gs);
+    else rec_groups<K>(p, rc, pair - rbase, cl, V, xc, m, gs);
+}
+
 struct Kernels {
     void (*fwd)(Prm);
-    void (*rec)(Prm, int);
-    void (*bwd)(Prm, int);
+    void (*round)(Prm, int, int, int, int);
 };
 
 inline Kernels kernels_for(int K) {
     switch (K) {
-        case 64: return Kernels{k_fwd_cl<64>, k_rec_cl<64>, k_bwd_cl<64>};
-        case 128: return Kernels{k_fwd_cl<128>, k_rec_cl<128>, k_bwd_cl<128>};
-        default: return Kernels{k_fwd_cl<256>, k_rec_cl<256>, k_bwd_cl<256>};
+        case 64: return Kernels{k_fwd_cl<64>, k_round_cl<64>};
+        case 128: return Kernels{k_fwd_cl<128>, k_round_cl<128>};
+        default: return Kernels{k_fwd_cl<256>, k_round_cl<256>};
     }
 }
 
@@ -1544,7 +1741,7 @@ inline Kernels kernels_for(int K) {
 
 struct Layout {
     size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, plan, rlist, rrow,
-        rcount, order, total;
+        rcount, P2, ebuf2, split, order, total;
     int Cmax;
     int64_t ngroups;
     int64_t npig;       // rows of pig: one per group of either path (clusters: up to S)
@@ -1577,11 +1774,16 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.gam = take((size_t)S * L.Cmax * K * 4);
     L.osym = take((size_t)S * L.Cmax * 4);
     L.cntp = take((size_t)(ns_max > kCntSplit ? ns_max : kCntSplit) * K * M * 4);
-    // group plans of the CTA pairs: the forward and every round
-    L.plan = take((size_t)(L.Cmax + 1) * (adj::clu::kPlanMaxGroups / 2) * 4 * 8);
+    // group plans of the CTA pairs: the forward, and every round's backward and recomputation
+    L.plan = take((size_t)(2 * L.Cmax + 1) * (adj::clu::kPlanMaxGroups / 2) * 4 * 8);
     L.rlist = take((size_t)L.Cmax * S * 4);
     L.rrow = take((size_t)L.Cmax * S * 4);
     L.rcount = take((size_t)L.Cmax * 4);
+    // cluster path: the odd rounds' P rows and exponents, and each backward launch's split
+    const bool clu_rows = adj::clu::cluster_shape_ok(K);
+    L.P2 = take(clu_rows ? (size_t)S * L.Cmax * K * 4 : 0);
+    L.ebuf2 = take(clu_rows ? (size_t)S * L.Cmax * 4 : 0);
+    L.split = take((size_t)(L.Cmax + 1) * 2 * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
     return L;
@@ -1663,6 +1865,9 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     p.rlist = (int32_t*)(ws + L.rlist);
     p.rrow = (int32_t*)(ws + L.rrow);
     p.rcount = (int32_t*)(ws + L.rcount);
+    p.P2 = (float*)(ws + L.P2);
+    p.ebuf2 = (int32_t*)(ws + L.ebuf2);
+    p.split = nullptr;
     P.cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
     p.obs = d_obs; p.off = d_offsets; p.order = (int32_t*)(ws + L.order); p.w = nullptr;
@@ -1701,6 +1906,7 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
                 if (p.ncl_fwd < 1) p.ncl_fwd = 1;
             }
             p.plan = (int64_t*)(ws + L.plan);
+            p.split = (int32_t*)(ws + L.split);
             P.planned = true;
         } else {
             p.ncl = ncl_min > ncl_sm ? ncl_min : ncl_sm;
@@ -1733,7 +1939,10 @@ static accel_status run_forward(Plan& P, const accel_hmm_model* m, double* d_log
                                                                           (int32_t*)p.rcount);
         ++nlaunch;
         if (P.planned) {
-            clu::k_plan<<<(unsigned)(L.Cmax + 1), clu::kPlanThreads, 0, st>>>(p, (int64_t*)p.plan, K == 256 ? 8 : 16);
+            const size_t sm_plan = clu::plan_smem_bytes();
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(clu::k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plan));
+            clu::k_plan<<<(unsigned)(L.Cmax + 2), clu::kPlanThreads, sm_plan, st>>>(p, (int64_t*)p.plan,
+                                                                                   (int32_t*)p.split, K == 256 ? 8 : 16);
             ++nlaunch;
         }
         const unsigned grid = (unsigned)(2 * p.ncl_fwd);
@@ -1775,32 +1984,51 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
     }
     if (S > 0) {
         if (P.use_cluster) {
-            const unsigned grid = (unsigned)(2 * p.ncl);
             const clu::Kernels kc = clu::kernels_for(K);
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
             const size_t sm_cnt = (size_t)M * 256 * 4;
             if (!P.counts_tc) {
                 ACCEL_REQUIRE(sm_cnt <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: M=%d too large", M);
                 ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
             }
             const int nbc = (K + 255) / 256;
-            for (int round = 0; round < L.Cmax; ++round) {
-                kc.rec<<<grid, clu::kT, P.sm_c, st>>>(p, round);
-                kc.bwd<<<grid, clu::kT, P.sm_c, st>>>(p, round);
-                nlaunch += 2;
+            // the counts of a round, once its backward has written its rows
+            auto counts = [&](int round) -> accel_status {
+                const float* Pr = (round & 1) ? p.P2 : p.P;
                 if (P.xi_tc) {
-                    accel_status r = xi_tc_round(p.P, p.Q, p.gam, p.osym, p.rows + round, K, M, P.Upart,
+                    accel_status r = xi_tc_round(Pr, p.Q, p.gam, p.osym, p.rows + round, K, M, P.Upart,
                                                  P.counts_tc ? P.cntp : nullptr, p.status, st);
                     if (r != ACCEL_OK) return r;
-                    ++nlaunch;
                 } else {
-                    k_gemm_ptq<<<P.nb * P.nb * kSplit, 256, 0, st>>>(p.P, p.Q, p.rows + round, K, P.Upart);
-                    ++nlaunch;
+                    k_gemm_ptq<<<P.nb * P.nb * kSplit, 256, 0, st>>>(Pr, p.Q, p.rows + round, K, P.Upart);
                 }
+                ++nlaunch;
                 if (!P.counts_tc) {
                     k_counts<<<nbc * kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, P.cntp);
                     ++nlaunch;
+                }
+                return ACCEL_OK;
+            };
+            if (P.planned) {
+                // launch l: the backward of round l - 1 beside the recomputation of round l, on
+                // the pairs the plan gives each (up to 2 ncl pairs when they run one after the other)
+                const unsigned grid = (unsigned)(4 * p.ncl);
+                for (int l = 0; l <= L.Cmax; ++l) {
+                    kc.round<<<grid, clu::kT, P.sm_c, st>>>(p, l - 1, l < L.Cmax ? l : -1, -1, -1);
+                    ++nlaunch;
+                    if (l >= 1) {
+                        accel_status r = counts(l - 1);
+                        if (r != ACCEL_OK) return r;
+                    }
+                }
+            } else {
+                const unsigned grid = (unsigned)(2 * p.ncl);
+                for (int round = 0; round < L.Cmax; ++round) {
+                    kc.round<<<grid, clu::kT, P.sm_c, st>>>(p, -1, round, 0, (int)p.ncl);
+                    kc.round<<<grid, clu::kT, P.sm_c, st>>>(p, round, -1, (int)p.ncl, 0);
+                    nlaunch += 2;
+                    accel_status r = counts(round);
+                    if (r != ACCEL_OK) return r;
                 }
             }
         } else {

@@ -66,11 +66,15 @@ def test_bruteforce_fixture(name):
 # K in {64, 128, 256} with a small enough emission table take the cluster kernels and the
 # tensor-core count accumulation (emission counts there up to 256 padded symbols, else the
 # SIMT count kernel); other shapes take the streaming kernels.  S = 200 and 1500 give
-# cluster groups of 2-3 and 15-16 sequences.
+# cluster groups of 2-3 and 15-16 sequences.  With plans (S <= 32 pairs' worth), a round's
+# backward and the next round's recomputation share a launch: side by side on disjoint CTA
+# pairs when both fit (S = 200, 1500), else each on all pairs one after the other
+# (S = 2400 on 76 pairs); S = 3000 has no plans (separate launches, groups by position).
 @pytest.mark.parametrize("K,M,S,lo,hi", [(8, 5, 20, 1, 50), (37, 11, 13, 1, 130), (64, 32, 9, 100, 400),
                                          (64, 7, 40, 1, 200), (128, 200, 10, 20, 120), (64, 300, 6, 1, 90),
                                          (256, 100, 5, 30, 90), (256, 200, 6, 20, 80), (128, 16, 35, 1, 60),
-                                         (64, 8, 200, 5, 60), (64, 8, 1500, 2, 12)])
+                                         (64, 8, 200, 5, 60), (64, 8, 1500, 2, 12), (64, 8, 2400, 20, 60),
+                                         (64, 8, 3000, 2, 12)])
 def test_small_models_against_oracle(K, M, S, lo, hi):
     p = synth.hmm_workload(K * 3 + S, K, M, S, "uniform", lo, hi)
     logs, t, obs, off = _dev(p)
