@@ -317,8 +317,7 @@ class Workload:
                 x, y, z, m = api.accel_marshal_records(self.aos, self.fields)
                 return api.pairwise_mapreduce(x, y, z, m, self.eps)
             out["allpairs"] = allpairs_row()
-            cur.wait_event(e_bf16)
-            out["bf16"] = self.bf16_out
+            out["bf16"] = self.bf16_out         # joined at the end of the step
         elif self.bf16_graph is not None:
             def bf16():
                 self.bf16_graph.launch()
@@ -344,6 +343,10 @@ class Workload:
             # the re-estimation that follows the adjoint in a training step
             out["mstep"] = mark("hmm_mstep", lambda: api.hmm_mstep(a["log_A"], a["log_B"], a["log_pi"], g[0], g[1],
                                                                    g[2]))
+        if overlap:
+            # the adjoint's backward phase starts when its forward phase ends, on the SMs the
+            # BF16 forward leaves until it finishes
+            cur.wait_event(e_bf16)
 
         if not overlap:
             def allpairs():
@@ -386,9 +389,6 @@ class Workload:
         aos = host["aos"].to(dev, non_blocking=True)
         x, y, z, mm = api.accel_marshal_records(aos, self.fields)
         res += list(api.pairwise_mapreduce(x, y, z, mm, self.eps))
-        st.wait_event(e_bf16)
-        r_bf16.record_stream(st)
-        res.append(r_bf16)
         if self.adj is not None:
             st.wait_event(e_af)
             d = dadj
@@ -396,6 +396,9 @@ class Workload:
                                                    adj_saved)
             th, nw = api.hmm_mstep(d["log_A"], d["log_B"], d["log_pi"], gA, gB, gpi)
             res += [gA, gB, gpi, adj_ll, *th, *nw]
+        st.wait_event(e_bf16)
+        r_bf16.record_stream(st)
+        res.append(r_bf16)
         outs = [torch.empty(r.shape, dtype=r.dtype, pin_memory=True) for r in res]
         for o, r in zip(outs, res):
             o.copy_(r, non_blocking=True)
@@ -1089,8 +1092,9 @@ def main():
                        "schedule": "three streams: the batched BF16 forward (a CUDA graph of its 5 kernels, "
                                    "its tuned persistent units) beside the adjoint's forward phase within the "
                                    "SMs it leaves (accel_set_sm_budget) and the seg-reduce, plain FP32 and "
-                                   "all-pairs rows; then the adjoint's backward phase (every SM) and the "
-                                   "re-estimation; per-row times in `rows` come from the same step run row "
+                                   "all-pairs rows; the adjoint's backward phase and the re-estimation as "
+                                   "soon as its forward phase ends (on the SMs the BF16 forward leaves, then "
+                                   "on every SM); per-row times in `rows` come from the same step run row "
                                    "after row",
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
             "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweeps, "marshal_sweep": msweeps,

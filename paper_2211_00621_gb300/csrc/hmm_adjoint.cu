@@ -669,7 +669,7 @@ __device__ __forceinline__ void cluster_group_range(const Prm& p, int pass, int6
 // One CTA per launch (block 0: the forward).  The step counts of a pass's list sit in shared
 // memory with their maxima over 2, 4, 8 and 16 consecutive entries, so a group's cost is two
 // reads.  Candidate splits: every nb for ncl <= 32, else the multiples of 4 and then the three
-// on each side of the best of them; per candidate and pass, one warp task per 32 group counts.
+// on each side of the best of them; one thread per (pass, candidate, group count).
 constexpr int kPlanThreads = 1024;
 constexpr int kPlanMaxGroups = 256;
 constexpr int kPlanMaxSeq = 16 * kPlanMaxGroups;
@@ -689,56 +689,61 @@ __host__ __device__ __forceinline__ int64_t pass_steps(int64_t T, int pass) {
     return t1 - k * C;
 }
 
-// A pass's list in shared memory: lv[k][i] = max of the step counts of entries i .. i + 2^k - 1.
+// A pass's list in shared memory: level k (lv(k)[i]) = max of the step counts of entries
+// i .. i + 2^k - 1.
 struct PlanList {
-    int* lv[kPlanLevels];
+    int* lv0;
     int64_t n;
+    __device__ __forceinline__ int* lv(int k) const { return lv0 + k * kPlanMaxSeq; }
 };
 
 // max over entries [st, st + sz), 1 <= sz < 32: two overlapping windows of the level below sz
 __device__ __forceinline__ int list_max(const PlanList& t, int st, int sz) {
     const int k = 31 - __clz(sz);
-    const int a = t.lv[k][st], b = t.lv[k][st + sz - (1 << k)];
+    const int* v = t.lv(k);
+    const int a = v[st], b = v[st + sz - (1 << k)];
     return a > b ? a : b;
 }
 
-// group_range_n(n, nv, .) with its divisions done once per group count
+// group_range_n(n, nv, .) with its divisions done once per group count (n <= kPlanMaxSeq and
+// nv <= kPlanMaxGroups: 32-bit arithmetic)
 struct Groups {
-    int64_t n8, base, firstbig;
+    int n8, base, firstbig;
 };
-__device__ __forceinline__ Groups groups_of(int64_t n, int64_t nv) {
+__device__ __forceinline__ Groups groups_of(int n, int nv) {
     Groups g;
     g.n8 = 0;
     if (n > 8 * nv) {
         g.n8 = (16 * nv - n) / 8;
         if (g.n8 < 0) g.n8 = 0;
     }
-    const int64_t rem = n - 8 * g.n8, m = nv - g.n8;
+    const int rem = n - 8 * g.n8, m = nv - g.n8;
     g.base = rem / m;
     g.firstbig = m - rem % m;
     return g;
 }
-__device__ __forceinline__ float group_cost(const PlanList& t, const Groups& g, int64_t j, int gp) {
+__device__ __forceinline__ float group_cost(const PlanList& t, const Groups& g, int j, int gp) {
     int st, sz;
     if (j < g.n8) {
-        st = (int)(8 * j);
+        st = 8 * j;
         sz = 8;
     } else {
-        const int64_t jj = j - g.n8;
-        st = (int)(8 * g.n8 + jj * g.base + (jj > g.firstbig ? jj - g.firstbig : 0));
-        sz = (int)(g.base + (jj >= g.firstbig ? 1 : 0));
+        const int jj = j - g.n8;
+        st = 8 * g.n8 + jj * g.base + (jj > g.firstbig ? jj - g.firstbig : 0);
+        sz = g.base + (jj >= g.firstbig ? 1 : 0);
     }
     return sz > 0 ? (float)list_max(t, st, sz) * (0.92f + (float)((sz + gp - 1) / gp)) : 0.f;
 }
 
 // the largest pair load of nv groups of the list's n > 0 entries on c pairs
-__device__ float plan_worst(const PlanList& t, int64_t c, int64_t nv, int gp) {
-    const Groups g = groups_of(t.n, nv);
-    const int64_t extra = nv > c ? nv - c : 0;
+__device__ float plan_worst(const PlanList& t, int c, int nv, int gp) {
+    const Groups g = groups_of((int)t.n, nv);
+    const int extra = nv > c ? nv - c : 0;
+    const int nq = c < nv ? c : nv;
     float worst = 0.f;
-    for (int64_t q = 0; q < c && q < nv; ++q) {
+    for (int q = 0; q < nq; ++q) {
         float l = group_cost(t, g, q, gp);
-        const int64_t k = c - 1 - q;
+        const int k = c - 1 - q;
         if (k < extra) l += group_cost(t, g, c + k, gp);
         worst = fmaxf(worst, l);
     }
@@ -780,40 +785,44 @@ __device__ void write_plan(const PlanList& t, int64_t* pl, int64_t stride, int64
 // recomputation's.
 __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int32_t* split, int gp) {
     extern __shared__ __align__(16) int s_lv[];          // [2][kPlanLevels][kPlanMaxSeq]
-    __shared__ float s_w[2][kPlanMaxCand][4];
-    __shared__ int64_t s_nv[2][kPlanMaxCand][4];
+    __shared__ uint64_t s_key[2][kPlanMaxCand];
+    __shared__ int s_lo[2][kPlanMaxCand];
+    __shared__ int s_cnt[2 * kPlanMaxCand + 1];
     __shared__ int s_cb[kPlanMaxCand], s_cc[kPlanMaxCand];
     __shared__ int s_ncand;
     __shared__ float s_bf;
     __shared__ int s_bcb, s_bcc;
     __shared__ int64_t s_bnv[2];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int blk = blockIdx.x, l = blk - 1;
     const bool fwd = blk == 0;
     const int rnd[2] = {fwd ? -1 : l - 1, (!fwd && l < p.Cmax) ? l : -1};
     const int64_t ncl = fwd ? p.ncl_fwd : p.ncl;
-    PlanList t[2];
-#pragma unroll
+    // list k of the two passes (0: the forward or the backward; 1: the recomputation)
+    auto list = [&](int k) -> PlanList {
+        PlanList t;
+        t.lv0 = s_lv + k * kPlanLevels * kPlanMaxSeq;
+        t.n = fwd ? (k == 0 ? p.S : 0) : (rnd[k] >= 0 ? p.rcount[rnd[k]] : 0);
+        return t;
+    };
     for (int k = 0; k < 2; ++k) {
-#pragma unroll
-        for (int v = 0; v < kPlanLevels; ++v) t[k].lv[v] = s_lv + (k * kPlanLevels + v) * kPlanMaxSeq;
-        t[k].n = fwd ? (k == 0 ? p.S : 0) : (rnd[k] >= 0 ? p.rcount[rnd[k]] : 0);
-    }
-    for (int k = 0; k < 2; ++k) {
-        for (int64_t i = tid; i < t[k].n; i += kPlanThreads) {
+        const PlanList t = list(k);
+        for (int64_t i = tid; i < t.n; i += kPlanThreads) {
             const int64_t q = fwd ? i : p.rlist[(int64_t)rnd[k] * p.S + i];
             const int64_t sq = p.order[q];
-            t[k].lv[0][i] = (int)pass_steps(p.off[sq + 1] - p.off[sq], fwd ? 0 : 1 + rnd[k]);
+            t.lv0[i] = (int)pass_steps(p.off[sq + 1] - p.off[sq], fwd ? 0 : 1 + rnd[k]);
         }
     }
     __syncthreads();
     for (int v = 1; v < kPlanLevels; ++v) {
         const int h = 1 << (v - 1);
-        for (int k = 0; k < 2; ++k)
-            for (int64_t i = tid; i + 2 * h <= t[k].n; i += kPlanThreads) {
-                const int a = t[k].lv[v - 1][i], b = t[k].lv[v - 1][i + h];
-                t[k].lv[v][i] = a > b ? a : b;
+        for (int k = 0; k < 2; ++k) {
+            const PlanList t = list(k);
+            for (int64_t i = tid; i + 2 * h <= t.n; i += kPlanThreads) {
+                const int a = t.lv(v - 1)[i], b = t.lv(v - 1)[i + h];
+                t.lv(v)[i] = a > b ? a : b;
             }
+        }
         __syncthreads();
     }
     const bool both = !fwd && rnd[0] >= 0 && rnd[1] >= 0;
@@ -846,30 +855,42 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int
         }
         __syncthreads();
         const int nc = s_ncand;
-        for (int task = warp; task < 2 * nc * 4; task += kPlanThreads / 32) {
-            const int k = task / (nc * 4), j = (task >> 2) % nc, q = task & 3;
-            const int64_t c = k == 0 ? s_cb[j] : s_cc[j], n = t[k].n;
-            float w = INFINITY;
-            int64_t nv = 0;
-            if (n == 0) {
-                if (q == 0 && lane == 0) w = 0.f;
-            } else if (c > 0) {
-                int64_t lo, hi;
-                nv_range(n, c, lo, hi);
-                nv = lo + 32 * q + lane;
-                if (nv <= hi) w = plan_worst(t[k], c, nv, gp);
+        // per problem (pass k, candidate j): its group-count range, its first item, and the
+        // best (load, group count) so far as one 64-bit key (load bits above the count: the
+        // loads are non-negative, so integer order is value order, ties to the fewest groups)
+        if (tid < 2 * nc) {
+            const int k = tid / nc, j = tid - k * nc;
+            const int64_t c = k == 0 ? s_cb[j] : s_cc[j], n = list(k).n;
+            int64_t lo = 0, hi = -1;
+            uint64_t key = (uint64_t)__float_as_uint(INFINITY) << 32;
+            if (n == 0) key = 0;
+            else if (c > 0) nv_range(n, c, lo, hi);
+            s_lo[k][j] = (int)lo;
+            s_cnt[tid] = hi >= lo ? (int)(hi - lo + 1) : 0;
+            s_key[k][j] = key;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int i = 0; i < 2 * nc; ++i) {
+                const int c = s_cnt[i];
+                s_cnt[i] = acc;
+                acc += c;
             }
-            // the smallest load, the fewest groups on a tie
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                const float ow = __shfl_down_sync(0xffffffffu, w, d);
-                const int64_t onv = __shfl_down_sync(0xffffffffu, nv, d);
-                if (ow < w || (ow == w && onv < nv)) { w = ow; nv = onv; }
-            }
-            if (lane == 0) {
-                s_w[k][j][q] = w;
-                s_nv[k][j][q] = nv;
-            }
+            s_cnt[2 * nc] = acc;
+        }
+        __syncthreads();
+        // one thread per item (problem, group count)
+        const int nitems = s_cnt[2 * nc];
+        for (int it = tid; it < nitems; it += kPlanThreads) {
+            int pi = 0;
+            while (s_cnt[pi + 1] <= it) ++pi;
+            const int k = pi / nc, j = pi - k * nc;
+            const int c = k == 0 ? s_cb[j] : s_cc[j];
+            const int nv = s_lo[k][j] + (it - s_cnt[pi]);
+            const float w = plan_worst(list(k), c, nv, gp);
+            atomicMin((unsigned long long*)&s_key[k][j],
+                      (unsigned long long)(((uint64_t)__float_as_uint(w) << 32) | (uint32_t)nv));
         }
         __syncthreads();
         if (tid == 0) {
@@ -877,10 +898,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int
                 float w2[2];
                 int64_t v2[2];
                 for (int k = 0; k < 2; ++k) {
-                    w2[k] = s_w[k][j][0];
-                    v2[k] = s_nv[k][j][0];
-                    for (int q = 1; q < 4; ++q)
-                        if (s_w[k][j][q] < w2[k]) { w2[k] = s_w[k][j][q]; v2[k] = s_nv[k][j][q]; }
+                    w2[k] = __uint_as_float((uint32_t)(s_key[k][j] >> 32));
+                    v2[k] = (int64_t)(s_key[k][j] & 0xffffffffu);
                 }
                 const float wb = kBwdStepCost * w2[0], wc = w2[1];
                 const float f = s_cb[j] + s_cc[j] <= ncl ? fmaxf(wb, wc) : wb + wc;
@@ -898,11 +917,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Prm p, int64_t* plan, int
     // every launch has a feasible candidate: each list alone fits on all ncl pairs
     const int64_t stride = p.ncl;
     if (fwd) {
-        write_plan(t[0], plan, stride, s_bcb, s_bnv[0]);
+        write_plan(list(0), plan, stride, s_bcb, s_bnv[0]);
         return;
     }
-    if (rnd[0] >= 0) write_plan(t[0], plan + (int64_t)(1 + rnd[0]) * stride * 4, stride, s_bcb, s_bnv[0]);
-    if (rnd[1] >= 0) write_plan(t[1], plan + (int64_t)(1 + p.Cmax + rnd[1]) * stride * 4, stride, s_bcc, s_bnv[1]);
+    if (rnd[0] >= 0) write_plan(list(0), plan + (int64_t)(1 + rnd[0]) * stride * 4, stride, s_bcb, s_bnv[0]);
+    if (rnd[1] >= 0) write_plan(list(1), plan + (int64_t)(1 + p.Cmax + rnd[1]) * stride * 4, stride, s_bcc, s_bnv[1]);
     if (tid == 0) {
         split[2 * l] = s_bcb;
         split[2 * l + 1] = s_bcc;
