@@ -33,7 +33,9 @@
 #include "simt_stream.cuh"
 
 #include <cooperative_groups.h>
+#include <map>
 #include <math.h>
+#include <vector>
 
 namespace accel {
 namespace hmm {
@@ -82,10 +84,16 @@ struct Prm {
     const int32_t* rlist;
     const int32_t* rrow;
     const int32_t* rcount;
-    // cluster path: odd rounds' P rows and exponents (even rounds use P and ebuf), so one
-    // launch may recompute round r + 1 while it runs the backward of round r
+    // cluster path: more row buffers, so that one launch may recompute round r + 1 while it
+    // runs the backward of round r, and the counts of round r may run beside the launch of
+    // rounds r + 1 / r + 2: P rows of round r in P, P2, P3 (r mod 3); exponents in ebuf,
+    // ebuf2 and Q, gamma and symbol rows in Q / Q2, gam / gam2, osym / osym2 (r mod 2)
     float* P2;
+    float* P3;
     int32_t* ebuf2;
+    float* Q2;
+    float* gam2;
+    int32_t* osym2;
     // cluster path with plans: per backward launch l (the backward of round l - 1 beside the
     // recomputation of round l), the CTA pairs given to the backward; the rest recompute
     const int32_t* split;
@@ -623,10 +631,15 @@ __device__ __forceinline__ void group_range_n(int64_t S, int64_t ngroups, int64_
 __device__ __forceinline__ const int64_t* pass_plan(const Prm& p, int pass) {
     return p.plan ? p.plan + (int64_t)pass * p.ncl * 4 : nullptr;
 }
-// The P rows and exponents of round r: even rounds in P / ebuf, odd rounds in P2 / ebuf2 (a
-// launch recomputes round r + 1 while its backward of round r reads round r's rows).
-__device__ __forceinline__ float* round_P(const Prm& p, int round) { return (round & 1) ? p.P2 : p.P; }
-__device__ __forceinline__ int32_t* round_e(const Prm& p, int round) { return (round & 1) ? p.ebuf2 : p.ebuf; }
+// The row buffers of round r on the cluster path (see Prm).
+__host__ __device__ __forceinline__ float* round_P(const Prm& p, int r) {
+    const int k = r % 3;
+    return k == 0 ? p.P : k == 1 ? p.P2 : p.P3;
+}
+__host__ __device__ __forceinline__ int32_t* round_e(const Prm& p, int r) { return (r & 1) ? p.ebuf2 : p.ebuf; }
+__host__ __device__ __forceinline__ float* round_Q(const Prm& p, int r) { return (r & 1) ? p.Q2 : p.Q; }
+__host__ __device__ __forceinline__ float* round_gam(const Prm& p, int r) { return (r & 1) ? p.gam2 : p.gam; }
+__host__ __device__ __forceinline__ int32_t* round_osym(const Prm& p, int r) { return (r & 1) ? p.osym2 : p.osym; }
 __device__ __forceinline__ int cluster_groups(const Prm& p, int pass, int64_t cidx) {
     const int64_t* pl = pass_plan(p, pass);
     return (pl && pl[cidx * 4 + 3] > 0) ? 2 : 1;
@@ -1567,6 +1580,9 @@ __device__ __forceinline__ void bwd_groups(const Prm& p, int round, int64_t cidx
     const bool peer_half = reads_peer_half(r);
     const float* const Pr = round_P(p, round);
     const int32_t* const er = round_e(p, round);
+    float* const Qw = round_Q(p, round);
+    float* const Gw = round_gam(p, round);
+    int32_t* const Ow = round_osym(p, round);
     // the pair's sequence groups, one after the other
     const int pass = 1 + round;
     const int64_t nlist = p.rcount[round];
@@ -1639,7 +1655,7 @@ __device__ __forceinline__ void bwd_groups(const Prm& p, int round, int64_t cidx
             if (active) {
     #pragma unroll
                 for (int e = 0; e < S::EC; ++e) v[e] *= wg;
-                stv<S::EC>(p.Q + (rowb + tt) * K + jc, v);
+                stv<S::EC>(Qw + (rowb + tt) * K + jc, v);
             }
         };
         write_v(maxL - 1, prev_sym, maxL - 1 < Lg);
@@ -1684,8 +1700,8 @@ __device__ __forceinline__ void bwd_groups(const Prm& p, int round, int64_t cidx
                     R[e] = trans ? o[e] * down : cinv;
                     gm[e] = up * St[e] * R[e];
                 }
-                stv<S::EC>(p.gam + (rowb + tt) * K + jc, gm);
-                if (lead && r == 0) p.osym[rowb + tt] = sym;
+                stv<S::EC>(Gw + (rowb + tt) * K + jc, gm);
+                if (lead && r == 0) Ow[rowb + tt] = sym;
             }
             if (tt > 0) write_v(tt - 1, sym, tt - 1 < Lg);
             prev_sym = sym;
@@ -1707,7 +1723,7 @@ __device__ __forceinline__ void bwd_groups(const Prm& p, int round, int64_t cidx
             const int j = r * S::Kh + cc;
             float s = 0.f;
             for (int q = 0; q < kG; ++q)
-                if (gs.L[q] > 0 && gs.t0[q] == 0) s += p.gam[(int64_t)gs.rowb[q] * K + j];
+                if (gs.L[q] > 0 && gs.t0[q] == 0) s += Gw[(int64_t)gs.rowb[q] * K + j];
             p.pig[cidx * K + j] += s;
         }
         cl.sync();                        // the peer is done with this CTA's shared memory
@@ -1760,7 +1776,7 @@ inline Kernels kernels_for(int K) {
 
 struct Layout {
     size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, plan, rlist, rrow,
-        rcount, P2, ebuf2, split, order, total;
+        rcount, P2, P3, ebuf2, Q2, gam2, osym2, split, order, total;
     int Cmax;
     int64_t ngroups;
     int64_t npig;       // rows of pig: one per group of either path (clusters: up to S)
@@ -1798,10 +1814,15 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     L.rlist = take((size_t)L.Cmax * S * 4);
     L.rrow = take((size_t)L.Cmax * S * 4);
     L.rcount = take((size_t)L.Cmax * 4);
-    // cluster path: the odd rounds' P rows and exponents, and each backward launch's split
+    // cluster path: the further row buffers of the rounds, and each backward launch's split
     const bool clu_rows = adj::clu::cluster_shape_ok(K);
-    L.P2 = take(clu_rows ? (size_t)S * L.Cmax * K * 4 : 0);
-    L.ebuf2 = take(clu_rows ? (size_t)S * L.Cmax * 4 : 0);
+    const size_t rowsK = clu_rows ? (size_t)S * L.Cmax * K * 4 : 0, rows1 = clu_rows ? (size_t)S * L.Cmax * 4 : 0;
+    L.P2 = take(rowsK);
+    L.P3 = take(rowsK);
+    L.ebuf2 = take(rows1);
+    L.Q2 = take(rowsK);
+    L.gam2 = take(rowsK);
+    L.osym2 = take(rows1);
     L.split = take((size_t)(L.Cmax + 1) * 2 * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
@@ -1885,7 +1906,11 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     p.rrow = (int32_t*)(ws + L.rrow);
     p.rcount = (int32_t*)(ws + L.rcount);
     p.P2 = (float*)(ws + L.P2);
+    p.P3 = (float*)(ws + L.P3);
     p.ebuf2 = (int32_t*)(ws + L.ebuf2);
+    p.Q2 = (float*)(ws + L.Q2);
+    p.gam2 = (float*)(ws + L.gam2);
+    p.osym2 = (int32_t*)(ws + L.osym2);
     p.split = nullptr;
     P.cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
@@ -1979,6 +2004,41 @@ static accel_status run_forward(Plan& P, const accel_hmm_model* m, double* d_log
     return ACCEL_OK;
 }
 
+// The backward phase's two streams on the cluster path, created once per host thread and
+// device (non-blocking, so they order only against the caller's stream through events).
+struct BwdStreams {
+    cudaStream_t hi = nullptr, lo = nullptr;
+};
+static accel_status bwd_streams(BwdStreams& out) {
+    thread_local std::map<int, BwdStreams> cache;
+    int dev = 0;
+    ACCEL_CUDA_TRY(cudaGetDevice(&dev));
+    auto it = cache.find(dev);
+    if (it == cache.end()) {
+        int least = 0, greatest = 0;
+        ACCEL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        BwdStreams s;
+        ACCEL_CUDA_TRY(cudaStreamCreateWithPriority(&s.hi, cudaStreamNonBlocking, greatest));
+        ACCEL_CUDA_TRY(cudaStreamCreateWithPriority(&s.lo, cudaStreamNonBlocking, least));
+        it = cache.emplace(dev, s).first;
+    }
+    out = it->second;
+    return ACCEL_OK;
+}
+
+// Events of one call, destroyed when it returns (the waits already enqueued still hold).
+struct EventSet {
+    std::vector<cudaEvent_t> ev;
+    cudaError_t make(cudaEvent_t& e) {
+        const cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r == cudaSuccess) ev.push_back(e);
+        return r;
+    }
+    ~EventSet() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
 // Phase 2: the rounds of recomputation and the backward recursion, the count accumulation, and
 // the gradients.  Reads phase 1's checkpoints, order and plan; clears its own accumulators.
 static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad_log_A, float* d_grad_log_B,
@@ -2011,21 +2071,50 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
                 ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
             }
             const int nbc = (K + 255) / 256;
+            // Two streams of this thread's phase: the round launches at the highest priority,
+            // the counts at the lowest.  The counts of round r run beside the launches that
+            // follow (their rows are in other buffers), and the launch that writes round r's
+            // buffers again waits for them; the caller's stream waits for both at the end.
+            BwdStreams bs;
+            accel_status rs = bwd_streams(bs);
+            if (rs != ACCEL_OK) return rs;
+            EventSet ev;
+            cudaEvent_t e_fork;
+            ACCEL_CUDA_TRY(ev.make(e_fork));
+            ACCEL_CUDA_TRY(cudaEventRecord(e_fork, st));
+            ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, e_fork, 0));
+            ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.lo, e_fork, 0));
+            std::vector<cudaEvent_t> done((size_t)L.Cmax, nullptr);
             // the counts of a round, once its backward has written its rows
             auto counts = [&](int round) -> accel_status {
-                const float* Pr = (round & 1) ? p.P2 : p.P;
+                cudaEvent_t e_rows;
+                ACCEL_CUDA_TRY(ev.make(e_rows));
+                ACCEL_CUDA_TRY(cudaEventRecord(e_rows, bs.hi));
+                ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.lo, e_rows, 0));
+                const float* Pr = clu::round_P(p, round);
+                const float* Qr = clu::round_Q(p, round);
+                const float* Gr = clu::round_gam(p, round);
+                const int32_t* Or = clu::round_osym(p, round);
                 if (P.xi_tc) {
-                    accel_status r = xi_tc_round(Pr, p.Q, p.gam, p.osym, p.rows + round, K, M, P.Upart,
-                                                 P.counts_tc ? P.cntp : nullptr, p.status, st);
+                    accel_status r = xi_tc_round(Pr, Qr, Gr, Or, p.rows + round, K, M, P.Upart,
+                                                 P.counts_tc ? P.cntp : nullptr, p.status, bs.lo);
                     if (r != ACCEL_OK) return r;
                 } else {
-                    k_gemm_ptq<<<P.nb * P.nb * kSplit, 256, 0, st>>>(Pr, p.Q, p.rows + round, K, P.Upart);
+                    k_gemm_ptq<<<P.nb * P.nb * kSplit, 256, 0, bs.lo>>>(Pr, Qr, p.rows + round, K, P.Upart);
                 }
                 ++nlaunch;
                 if (!P.counts_tc) {
-                    k_counts<<<nbc * kCntSplit, 256, sm_cnt, st>>>(p.gam, p.osym, p.rows + round, K, M, P.cntp);
+                    k_counts<<<nbc * kCntSplit, 256, sm_cnt, bs.lo>>>(Gr, Or, p.rows + round, K, M, P.cntp);
                     ++nlaunch;
                 }
+                ACCEL_CUDA_TRY(ev.make(done[round]));
+                ACCEL_CUDA_TRY(cudaEventRecord(done[round], bs.lo));
+                return ACCEL_OK;
+            };
+            // before writing round t's Q / gamma / symbol rows (and round t + 1's P rows): the
+            // counts of round t - 2 have read them
+            auto wait_counts = [&](int round) -> accel_status {
+                if (round >= 0) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, done[round], 0));
                 return ACCEL_OK;
             };
             if (P.planned) {
@@ -2033,23 +2122,34 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
                 // the pairs the plan gives each (up to 2 ncl pairs when they run one after the other)
                 const unsigned grid = (unsigned)(4 * p.ncl);
                 for (int l = 0; l <= L.Cmax; ++l) {
-                    kc.round<<<grid, clu::kT, P.sm_c, st>>>(p, l - 1, l < L.Cmax ? l : -1, -1, -1);
+                    accel_status r = wait_counts(l - 3);
+                    if (r != ACCEL_OK) return r;
+                    kc.round<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, l - 1, l < L.Cmax ? l : -1, -1, -1);
                     ++nlaunch;
                     if (l >= 1) {
-                        accel_status r = counts(l - 1);
+                        r = counts(l - 1);
                         if (r != ACCEL_OK) return r;
                     }
                 }
             } else {
                 const unsigned grid = (unsigned)(2 * p.ncl);
                 for (int round = 0; round < L.Cmax; ++round) {
-                    kc.round<<<grid, clu::kT, P.sm_c, st>>>(p, -1, round, 0, (int)p.ncl);
-                    kc.round<<<grid, clu::kT, P.sm_c, st>>>(p, round, -1, (int)p.ncl, 0);
+                    accel_status r = wait_counts(round - 2);
+                    if (r != ACCEL_OK) return r;
+                    kc.round<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, -1, round, 0, (int)p.ncl);
+                    kc.round<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, round, -1, (int)p.ncl, 0);
                     nlaunch += 2;
-                    accel_status r = counts(round);
+                    r = counts(round);
                     if (r != ACCEL_OK) return r;
                 }
             }
+            cudaEvent_t e_hi, e_lo;
+            ACCEL_CUDA_TRY(ev.make(e_hi));
+            ACCEL_CUDA_TRY(ev.make(e_lo));
+            ACCEL_CUDA_TRY(cudaEventRecord(e_hi, bs.hi));
+            ACCEL_CUDA_TRY(cudaEventRecord(e_lo, bs.lo));
+            ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_hi, 0));
+            ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_lo, 0));
         } else {
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_b));
             for (int round = 0; round < L.Cmax; ++round) {
