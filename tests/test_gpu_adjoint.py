@@ -257,3 +257,29 @@ def test_sm_budget_gives_identical_results(budget):
     for a, b in zip(g2, ref[:3]):
         assert torch.equal(a, b)
     assert torch.equal(ll, ref[3])
+
+
+@pytest.mark.parametrize("K,M,S,lo,hi", [(64, 8, 200, 5, 60), (256, 64, 40, 50, 300)])
+def test_adjoint_captured_in_a_cuda_graph_replays_bit_identical(K, M, S, lo, hi):
+    # the backward phase forks to its own two streams and joins the caller's stream again with
+    # events, so a whole call captures into a CUDA graph; replays give the eager results
+    p = synth.hmm_workload(K + 5 * S, K, M, S, "uniform", lo, hi)
+    logs, t, obs, off = _dev(p)
+    max_T = int(p["lengths"].max())
+    w = torch.from_numpy(synth.rng(9).uniform(0.5, 2.0, size=S)).to(DEV)
+    ref = [x.clone() for x in api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w,
+                                              max_T=max_T)[:4]]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):                      # warm-up on a non-default stream
+        api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w, max_T=max_T)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        out = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w, max_T=max_T)
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(out[:4], ref):
+            assert torch.equal(a, b)
