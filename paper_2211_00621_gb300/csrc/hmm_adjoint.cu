@@ -1121,7 +1121,9 @@ __device__ __forceinline__ void contract(const MatRegs<K>& m, const float* __res
     const float* xb = X + w * S::IPART;
     // this lane's CW columns within a row: chunk (lane CW) / 4, offset (lane CW) % 4
     float* pb = part + (w * kG) * S::Kh + 4 * pswz((lane * S::CW) >> 2) + ((lane * S::CW) & 3);
-#pragma unroll
+    // the passes are not unrolled: one copy of the unrolled pass body keeps the kernels' hot
+    // code small enough for the instruction caches
+#pragma unroll 1
     for (int ps = 0; ps < S::NPASS; ++ps) {
         if (ps > 0 && ps * S::GP >= gcount) break;   // (uniform) a group of at most GP sequences
         float2 acc[S::GP][S::CW];
