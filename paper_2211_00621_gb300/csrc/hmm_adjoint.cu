@@ -1732,21 +1732,15 @@ __device__ __forceinline__ void bwd_groups(const Prm& p, int round, int64_t cidx
     }
 }
 
-// One launch of the backward phase (see k_plan): CTA pairs [0, nb) run the backward of round
-// rb, pairs [rbase, rbase + nr) the recomputation of round rc (rb, rc < 0: none).  nb < 0
-// takes nb and nr from the plan of backward launch rb + 1.  rbase = nb when both fit side by
-// side on the ncl pairs, else ncl: the recomputation's pairs start as the backward's finish.
+// The recomputation of round `round` and the backward of round `round`, each on the CTA pairs
+// its pass was planned for (see k_plan): np >= 0 pairs from the host, else from the plan --
+// backward launch l holds the backward of round l - 1 (split[2 l] pairs) beside the
+// recomputation of round l (split[2 l + 1] pairs), as two kernels on two streams.  Pairs past
+// the count leave at once (both CTAs of a pair alike, before any remote access).
 template <int K>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_round_cl(Prm p, int rb, int rc, int nb, int nr) {
-    if (nb < 0) {
-        nb = p.split[2 * (rb + 1)];
-        nr = p.split[2 * (rb + 1) + 1];
-    }
-    const int64_t rbase = (int64_t)nb + nr <= p.ncl ? nb : p.ncl;
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_rec_cl(Prm p, int round, int np) {
     const int64_t pair = blockIdx.x >> 1;
-    const bool bwd = rb >= 0 && pair < nb;
-    const bool rec = !bwd && rc >= 0 && pair >= rbase && pair < rbase + nr;
-    if (!bwd && !rec) return;             // both CTAs of the pair leave, before any remote access
+    if (pair >= (np >= 0 ? (int64_t)np : (int64_t)p.split[2 * round + 1])) return;
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank(), peer = r ^ 1;
     extern __shared__ __align__(16) char smem[];
@@ -1755,22 +1749,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_round_cl(Pr
     const Views V = make_views(smem, K, p.M, cl, peer);
     Xchg xc = make_xchg(V, s_xbar, peer);
     MatRegs<K> m;
-    m.load(bwd ? p.At : p.A, p.Kp, r);
+    m.load(p.A, p.Kp, r);
     load_bt<K>(p.BT, p.M, r, V.BTh);
-    if (bwd) bwd_groups<K>(p, rb, pair, cl, V, xc, m, gs);
-    else rec_groups<K>(p, rc, pair - rbase, cl, V, xc, m, gs);
+    rec_groups<K>(p, round, pair, cl, V, xc, m, gs);
+}
+
+template <int K>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kT, 1) k_bwd_cl(Prm p, int round, int np) {
+    const int64_t pair = blockIdx.x >> 1;
+    if (pair >= (np >= 0 ? (int64_t)np : (int64_t)p.split[2 * (round + 1)])) return;
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank(), peer = r ^ 1;
+    extern __shared__ __align__(16) char smem[];
+    __shared__ GS gs;
+    __shared__ __align__(8) uint64_t s_xbar[2];
+    const Views V = make_views(smem, K, p.M, cl, peer);
+    Xchg xc = make_xchg(V, s_xbar, peer);
+    MatRegs<K> m;
+    m.load(p.At, p.Kp, r);
+    load_bt<K>(p.BT, p.M, r, V.BTh);
+    bwd_groups<K>(p, round, pair, cl, V, xc, m, gs);
 }
 
 struct Kernels {
     void (*fwd)(Prm);
-    void (*round)(Prm, int, int, int, int);
+    void (*rec)(Prm, int, int);
+    void (*bwd)(Prm, int, int);
 };
 
 inline Kernels kernels_for(int K) {
     switch (K) {
-        case 64: return Kernels{k_fwd_cl<64>, k_round_cl<64>};
-        case 128: return Kernels{k_fwd_cl<128>, k_round_cl<128>};
-        default: return Kernels{k_fwd_cl<256>, k_round_cl<256>};
+        case 64: return Kernels{k_fwd_cl<64>, k_rec_cl<64>, k_bwd_cl<64>};
+        case 128: return Kernels{k_fwd_cl<128>, k_rec_cl<128>, k_bwd_cl<128>};
+        default: return Kernels{k_fwd_cl<256>, k_rec_cl<256>, k_bwd_cl<256>};
     }
 }
 
@@ -2006,10 +2017,11 @@ static accel_status run_forward(Plan& P, const accel_hmm_model* m, double* d_log
     return ACCEL_OK;
 }
 
-// The backward phase's two streams on the cluster path, created once per host thread and
-// device (non-blocking, so they order only against the caller's stream through events).
+// The backward phase's streams on the cluster path, created once per host thread and device
+// (non-blocking, so they order only against the caller's stream through events): the
+// backward passes and the recomputations at the highest priority, the counts at the lowest.
 struct BwdStreams {
-    cudaStream_t hi = nullptr, lo = nullptr;
+    cudaStream_t hi = nullptr, hi2 = nullptr, lo = nullptr;
 };
 static accel_status bwd_streams(BwdStreams& out) {
     thread_local std::map<int, BwdStreams> cache;
@@ -2021,6 +2033,7 @@ static accel_status bwd_streams(BwdStreams& out) {
         ACCEL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         BwdStreams s;
         ACCEL_CUDA_TRY(cudaStreamCreateWithPriority(&s.hi, cudaStreamNonBlocking, greatest));
+        ACCEL_CUDA_TRY(cudaStreamCreateWithPriority(&s.hi2, cudaStreamNonBlocking, greatest));
         ACCEL_CUDA_TRY(cudaStreamCreateWithPriority(&s.lo, cudaStreamNonBlocking, least));
         it = cache.emplace(dev, s).first;
     }
@@ -2066,17 +2079,21 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
     if (S > 0) {
         if (P.use_cluster) {
             const clu::Kernels kc = clu::kernels_for(K);
-            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
+            ACCEL_CUDA_TRY(cudaFuncSetAttribute(kc.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_c));
             const size_t sm_cnt = (size_t)M * 256 * 4;
             if (!P.counts_tc) {
                 ACCEL_REQUIRE(sm_cnt <= (size_t)max_smem_optin(), ACCEL_ERR_UNSUPPORTED, "hmm_adjoint: M=%d too large", M);
                 ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cnt));
             }
             const int nbc = (K + 255) / 256;
-            // Two streams of this thread's phase: the round launches at the highest priority,
-            // the counts at the lowest.  The counts of round r run beside the launches that
-            // follow (their rows are in other buffers), and the launch that writes round r's
-            // buffers again waits for them; the caller's stream waits for both at the end.
+            // Three streams of this thread's phase: the backward passes (hi) and the
+            // recomputations (hi2) at the highest priority, the counts (lo) at the lowest.  The
+            // backward of round l - 1 runs beside the recomputation of round l on the CTA pairs
+            // the plan splits between them; the counts of round r run beside what follows
+            // (their rows are in other buffers).  Before a pass writes a buffer again, it waits
+            // for the last reader of the round that used it; the caller's stream waits for all
+            // three at the end.
             BwdStreams bs;
             accel_status rs = bwd_streams(bs);
             if (rs != ACCEL_OK) return rs;
@@ -2085,14 +2102,13 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
             ACCEL_CUDA_TRY(ev.make(e_fork));
             ACCEL_CUDA_TRY(cudaEventRecord(e_fork, st));
             ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, e_fork, 0));
+            ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, e_fork, 0));
             ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.lo, e_fork, 0));
-            std::vector<cudaEvent_t> done((size_t)L.Cmax, nullptr);
+            const size_t nr = (size_t)L.Cmax;
+            std::vector<cudaEvent_t> e_rec(nr, nullptr), e_bwd(nr, nullptr), done(nr, nullptr);
             // the counts of a round, once its backward has written its rows
             auto counts = [&](int round) -> accel_status {
-                cudaEvent_t e_rows;
-                ACCEL_CUDA_TRY(ev.make(e_rows));
-                ACCEL_CUDA_TRY(cudaEventRecord(e_rows, bs.hi));
-                ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.lo, e_rows, 0));
+                ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.lo, e_bwd[round], 0));
                 const float* Pr = clu::round_P(p, round);
                 const float* Qr = clu::round_Q(p, round);
                 const float* Gr = clu::round_gam(p, round);
@@ -2113,44 +2129,44 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
                 ACCEL_CUDA_TRY(cudaEventRecord(done[round], bs.lo));
                 return ACCEL_OK;
             };
-            // before writing round t's Q / gamma / symbol rows (and round t + 1's P rows): the
-            // counts of round t - 2 have read them
-            auto wait_counts = [&](int round) -> accel_status {
-                if (round >= 0) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, done[round], 0));
-                return ACCEL_OK;
-            };
-            if (P.planned) {
-                // launch l: the backward of round l - 1 beside the recomputation of round l, on
-                // the pairs the plan gives each (up to 2 ncl pairs when they run one after the other)
-                const unsigned grid = (unsigned)(4 * p.ncl);
-                for (int l = 0; l <= L.Cmax; ++l) {
-                    accel_status r = wait_counts(l - 3);
-                    if (r != ACCEL_OK) return r;
-                    kc.round<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, l - 1, l < L.Cmax ? l : -1, -1, -1);
+            // with plans each pass takes its pairs from the plan; without, all ncl pairs
+            const int np = P.planned ? -1 : (int)p.ncl;
+            const unsigned grid = (unsigned)(2 * p.ncl);
+            for (int l = 0; l <= L.Cmax; ++l) {
+                if (l >= 1) {
+                    // the backward of round l - 1: after its recomputation; its Q / gamma /
+                    // symbol buffers were last read by the counts of round l - 3
+                    const int rb = l - 1;
+                    ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, e_rec[rb], 0));
+                    if (rb >= 2) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, done[rb - 2], 0));
+                    kc.bwd<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, rb, np);
                     ++nlaunch;
-                    if (l >= 1) {
-                        r = counts(l - 1);
-                        if (r != ACCEL_OK) return r;
-                    }
+                    ACCEL_CUDA_TRY(ev.make(e_bwd[rb]));
+                    ACCEL_CUDA_TRY(cudaEventRecord(e_bwd[rb], bs.hi));
+                    accel_status r = counts(rb);
+                    if (r != ACCEL_OK) return r;
                 }
-            } else {
-                const unsigned grid = (unsigned)(2 * p.ncl);
-                for (int round = 0; round < L.Cmax; ++round) {
-                    accel_status r = wait_counts(round - 2);
-                    if (r != ACCEL_OK) return r;
-                    kc.round<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, -1, round, 0, (int)p.ncl);
-                    kc.round<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, round, -1, (int)p.ncl, 0);
-                    nlaunch += 2;
-                    r = counts(round);
-                    if (r != ACCEL_OK) return r;
+                if (l < L.Cmax) {
+                    // the recomputation of round l: its P rows' buffer was last read by the
+                    // backward and the counts of round l - 3, its exponents' by the backward of
+                    // round l - 2
+                    if (l >= 3) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, done[l - 3], 0));
+                    if (l >= 2) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, e_bwd[l - 2], 0));
+                    kc.rec<<<grid, clu::kT, P.sm_c, bs.hi2>>>(p, l, np);
+                    ++nlaunch;
+                    ACCEL_CUDA_TRY(ev.make(e_rec[l]));
+                    ACCEL_CUDA_TRY(cudaEventRecord(e_rec[l], bs.hi2));
                 }
             }
-            cudaEvent_t e_hi, e_lo;
+            cudaEvent_t e_hi, e_hi2, e_lo;
             ACCEL_CUDA_TRY(ev.make(e_hi));
+            ACCEL_CUDA_TRY(ev.make(e_hi2));
             ACCEL_CUDA_TRY(ev.make(e_lo));
             ACCEL_CUDA_TRY(cudaEventRecord(e_hi, bs.hi));
+            ACCEL_CUDA_TRY(cudaEventRecord(e_hi2, bs.hi2));
             ACCEL_CUDA_TRY(cudaEventRecord(e_lo, bs.lo));
             ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_hi, 0));
+            ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_hi2, 0));
             ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_lo, 0));
         } else {
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_b));
