@@ -382,6 +382,12 @@ accel_status hmm_forward(const accel_hmm_model* m, int32_t precision, const int3
  *             skipped and reported as ACCEL_ERR_SHAPE: returned by the call in debug mode,
  *             else recorded in the device status word (accel_set_device_status).
  *  Outputs are overwritten (not accumulated); d_grad_log_pi may be NULL.
+ *  Streams: the work is ordered after what `stream` already holds, and what `stream` enqueues
+ *  next runs after it.  On K = 64, 128 or 256 the backward part runs on three streams the
+ *  library creates once per host thread and device (the backward and recomputation passes at
+ *  the highest stream priority, the count kernels at the lowest).  It forks from `stream`
+ *  and joins it again through events, so a capture of `stream` into a CUDA graph takes the
+ *  whole call.  Two host threads calling at once each use their own streams.
  */
 size_t hmm_adjoint_workspace_size(const accel_hmm_model* m, int64_t S, int64_t total_T, int64_t max_T);
 accel_status hmm_adjoint(const accel_hmm_model* m, const int32_t* d_obs, const int64_t* d_offsets,
