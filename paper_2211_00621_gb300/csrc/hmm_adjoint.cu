@@ -46,6 +46,10 @@ constexpr int kG = 8;       // sequences per CTA
 constexpr int kTile = 64;   // GEMM tile of U
 constexpr int kSplit = 16;  // GEMM split over rows
 
+// cluster path: row buffers of the rounds (see Prm)
+constexpr int kPBufs = 4;      // P rows: rounds r mod 4
+constexpr int kQBufs = 3;      // Q, gamma and symbol rows: rounds r mod 3
+
 struct Prm {
     int K, M, Cmax;
     int64_t S;
@@ -85,20 +89,15 @@ struct Prm {
     const int32_t* rrow;
     const int32_t* rcount;
     // cluster path: more row buffers, so that the recomputation of round r + 1 may run
-    // beside the backward of round r, and the counts of round r beside the passes of the two
-    // rounds after it: P rows of round r in P, P2, P3, P4 (r mod 4); exponents in ebuf, ebuf2
-    // (r mod 2); Q, gamma and symbol rows in Q / Q2 / Q3, gam / gam2 / gam3, osym / osym2 /
-    // osym3 (r mod 3)
-    float* P2;
-    float* P3;
-    float* P4;
+    // beside the backward of round r, and the counts of round r beside the passes of the
+    // rounds after it: P rows of round r in Pb[r mod kPBufs] (Pb[0] = P); exponents in ebuf,
+    // ebuf2 (r mod 2); Q, gamma and symbol rows in Qb / Gb / Ob[r mod kQBufs] (the first
+    // ones Q, gam, osym)
+    float* Pb[kPBufs];
     int32_t* ebuf2;
-    float* Q2;
-    float* Q3;
-    float* gam2;
-    float* gam3;
-    int32_t* osym2;
-    int32_t* osym3;
+    float* Qb[kQBufs];
+    float* Gb[kQBufs];
+    int32_t* Ob[kQBufs];
     // cluster path with plans: per backward launch l (the backward of round l - 1 beside the
     // recomputation of round l), the CTA pairs given to the backward; the rest recompute
     const int32_t* split;
@@ -637,25 +636,11 @@ __device__ __forceinline__ const int64_t* pass_plan(const Prm& p, int pass) {
     return p.plan ? p.plan + (int64_t)pass * p.ncl * 4 : nullptr;
 }
 // The row buffers of round r on the cluster path (see Prm).
-constexpr int kPBufs = 4;      // P row buffers (rounds r mod 4)
-constexpr int kQBufs = 3;      // Q, gamma and symbol row buffers (rounds r mod 3)
-__host__ __device__ __forceinline__ float* round_P(const Prm& p, int r) {
-    const int k = r % kPBufs;
-    return k == 0 ? p.P : k == 1 ? p.P2 : k == 2 ? p.P3 : p.P4;
-}
+__host__ __device__ __forceinline__ float* round_P(const Prm& p, int r) { return p.Pb[r % kPBufs]; }
 __host__ __device__ __forceinline__ int32_t* round_e(const Prm& p, int r) { return (r & 1) ? p.ebuf2 : p.ebuf; }
-__host__ __device__ __forceinline__ float* round_Q(const Prm& p, int r) {
-    const int k = r % kQBufs;
-    return k == 0 ? p.Q : k == 1 ? p.Q2 : p.Q3;
-}
-__host__ __device__ __forceinline__ float* round_gam(const Prm& p, int r) {
-    const int k = r % kQBufs;
-    return k == 0 ? p.gam : k == 1 ? p.gam2 : p.gam3;
-}
-__host__ __device__ __forceinline__ int32_t* round_osym(const Prm& p, int r) {
-    const int k = r % kQBufs;
-    return k == 0 ? p.osym : k == 1 ? p.osym2 : p.osym3;
-}
+__host__ __device__ __forceinline__ float* round_Q(const Prm& p, int r) { return p.Qb[r % kQBufs]; }
+__host__ __device__ __forceinline__ float* round_gam(const Prm& p, int r) { return p.Gb[r % kQBufs]; }
+__host__ __device__ __forceinline__ int32_t* round_osym(const Prm& p, int r) { return p.Ob[r % kQBufs]; }
 __device__ __forceinline__ int cluster_groups(const Prm& p, int pass, int64_t cidx) {
     const int64_t* pl = pass_plan(p, pass);
     return (pl && pl[cidx * 4 + 3] > 0) ? 2 : 1;
@@ -1805,7 +1790,7 @@ inline Kernels kernels_for(int K) {
 
 struct Layout {
     size_t A, At, BT, pi, cp, cp_e, clast, P, Q, Rc, cnt, pig, Upart, rows, ebuf, gam, osym, cntp, plan, rlist, rrow,
-        rcount, P2, P3, P4, ebuf2, Q2, Q3, gam2, gam3, osym2, osym3, split, order, total;
+        rcount, Pb[kPBufs], ebuf2, Qb[kQBufs], Gb[kQBufs], Ob[kQBufs], split, order, total;
     int Cmax;
     int64_t ngroups;
     int64_t npig;       // rows of pig: one per group of either path (clusters: up to S)
@@ -1846,16 +1831,17 @@ static Layout layout(int K, int M, int64_t S, int64_t max_T) {
     // cluster path: the further row buffers of the rounds, and each backward launch's split
     const bool clu_rows = adj::clu::cluster_shape_ok(K);
     const size_t rowsK = clu_rows ? (size_t)S * L.Cmax * K * 4 : 0, rows1 = clu_rows ? (size_t)S * L.Cmax * 4 : 0;
-    L.P2 = take(rowsK);
-    L.P3 = take(rowsK);
-    L.P4 = take(rowsK);
+    L.Pb[0] = L.P;
+    L.Qb[0] = L.Q;
+    L.Gb[0] = L.gam;
+    L.Ob[0] = L.osym;
+    for (int k = 1; k < kPBufs; ++k) L.Pb[k] = take(rowsK);
     L.ebuf2 = take(rows1);
-    L.Q2 = take(rowsK);
-    L.Q3 = take(rowsK);
-    L.gam2 = take(rowsK);
-    L.gam3 = take(rowsK);
-    L.osym2 = take(rows1);
-    L.osym3 = take(rows1);
+    for (int k = 1; k < kQBufs; ++k) {
+        L.Qb[k] = take(rowsK);
+        L.Gb[k] = take(rowsK);
+        L.Ob[k] = take(rows1);
+    }
     L.split = take((size_t)(L.Cmax + 1) * 2 * 4);
     L.order = o;
     L.total = o + order_ws_bytes(S);
@@ -1938,16 +1924,13 @@ static accel_status setup(const char* who, const accel_hmm_model* m, const int32
     p.rlist = (int32_t*)(ws + L.rlist);
     p.rrow = (int32_t*)(ws + L.rrow);
     p.rcount = (int32_t*)(ws + L.rcount);
-    p.P2 = (float*)(ws + L.P2);
-    p.P3 = (float*)(ws + L.P3);
-    p.P4 = (float*)(ws + L.P4);
+    for (int k = 0; k < kPBufs; ++k) p.Pb[k] = (float*)(ws + L.Pb[k]);
     p.ebuf2 = (int32_t*)(ws + L.ebuf2);
-    p.Q2 = (float*)(ws + L.Q2);
-    p.Q3 = (float*)(ws + L.Q3);
-    p.gam2 = (float*)(ws + L.gam2);
-    p.gam3 = (float*)(ws + L.gam3);
-    p.osym2 = (int32_t*)(ws + L.osym2);
-    p.osym3 = (int32_t*)(ws + L.osym3);
+    for (int k = 0; k < kQBufs; ++k) {
+        p.Qb[k] = (float*)(ws + L.Qb[k]);
+        p.Gb[k] = (float*)(ws + L.Gb[k]);
+        p.Ob[k] = (int32_t*)(ws + L.Ob[k]);
+    }
     p.split = nullptr;
     P.cntp = (float*)(ws + L.cntp);
     p.A = (float*)(ws + L.A); p.At = (float*)(ws + L.At); p.BT = (float*)(ws + L.BT); p.pi = (float*)(ws + L.pi);
@@ -2162,7 +2145,7 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
                     // symbol buffers were last read by the counts of round l - 1 - kQBufs
                     const int rb = l - 1;
                     ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, e_rec[rb], 0));
-                    if (rb >= clu::kQBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, done[rb - clu::kQBufs], 0));
+                    if (rb >= kQBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, done[rb - kQBufs], 0));
                     kc.bwd<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, rb, np);
                     ++nlaunch;
                     ACCEL_CUDA_TRY(ev.make(e_bwd[rb]));
@@ -2174,7 +2157,7 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
                     // the recomputation of round l: its P rows' buffer was last read by the
                     // backward and the counts of round l - kPBufs, its exponents' by the
                     // backward of round l - 2
-                    if (l >= clu::kPBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, done[l - clu::kPBufs], 0));
+                    if (l >= kPBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, done[l - kPBufs], 0));
                     if (l >= 2) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, e_bwd[l - 2], 0));
                     kc.rec<<<grid, clu::kT, P.sm_c, bs.hi2>>>(p, l, np);
                     ++nlaunch;
