@@ -283,3 +283,71 @@ def test_adjoint_captured_in_a_cuda_graph_replays_bit_identical(K, M, S, lo, hi)
         torch.cuda.synchronize()
         for a, b in zip(out[:4], ref):
             assert torch.equal(a, b)
+
+
+def test_adjoint_orders_with_the_callers_stream():
+    # on a side stream: a long kernel, then the weights written, then the call, then the
+    # gradients read -- all enqueued back to back with no host synchronisation.  The backward's
+    # own streams fork from the caller's stream after the weights are written and join it
+    # before the gradients are read, so the results equal a call on settled inputs.
+    K, M, S = 128, 16, 120
+    p = synth.hmm_workload(606, K, M, S, "uniform", 20, 200)
+    logs, t, obs, off = _dev(p)
+    max_T = int(p["lengths"].max())
+    w_host = synth.rng(12).uniform(0.5, 2.0, size=S)
+    w_ref = torch.from_numpy(w_host).to(DEV)
+    ref = [x.clone() for x in api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w_ref,
+                                              max_T=max_T)[:3]]
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    big = torch.randn(4096, 4096, device=DEV)
+    w = torch.zeros(S, dtype=torch.float64, device=DEV)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(4):
+            big = big @ big / 64.0                     # keeps the stream busy for a while
+        w.copy_(w_ref)
+        g = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, weights=w, max_T=max_T)[:3]
+        got = [x.clone() for x in g]
+    torch.cuda.synchronize()
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+
+
+def test_adjoint_from_two_host_threads_at_once():
+    # each host thread gets the backward's streams of its own; two calls in flight at once
+    # on two streams give the results of the same calls one after the other
+    import threading
+    cases = []
+    for seed, (K, M, S) in enumerate([(64, 8, 150), (256, 64, 30)]):
+        p = synth.hmm_workload(700 + seed, K, M, S, "uniform", 30, 250)
+        logs, t, obs, off = _dev(p)
+        cases.append((t, obs, off, int(p["lengths"].max())))
+    ref = []
+    for t, obs, off, mt in cases:
+        ref.append([x.clone() for x in api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, max_T=mt)[:4]])
+    torch.cuda.synchronize()
+    out = [None, None]
+    errs = []
+
+    def run(i):
+        try:
+            t, obs, off, mt = cases[i]
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for _ in range(3):
+                    g = api.hmm_adjoint(t["log_A"], t["log_B"], t["log_pi"], obs, off, max_T=mt)[:4]
+                out[i] = [x.clone() for x in g]
+            s.synchronize()
+        except Exception as e:                      # surfaced below
+            errs.append(e)
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errs, errs
+    for got, r in zip(out, ref):
+        for a, b in zip(got, r):
+            assert torch.equal(a, b)
