@@ -17,17 +17,16 @@
 // hi_a hi_b + hi_a lo_b + lo_a hi_b; the dropped lo_a lo_b term is below 2^-21 relative.
 // The one-hot operand needs no split.
 //
-// Operand path of a chunk of kKC = 16 reduction rows: the chunk's rows of Q (all K columns:
-// one contiguous bulk copy, completing on the raw tile's mbarrier) and of P and Gamma (the
-// CTA's 128 columns: 16-byte cp.async pieces, one commit group per chunk) go into a raw
-// shared-memory tile kRawStages chunks ahead; all 256 threads then split the raw values into
-// the hi / lo operand blocks of a split stage (the no-swizzle K-major canonical layout: core
-// matrices of 8 rows x 4 values) and build the one-hot block, and one thread issues the
-// chunk's MMAs and commits them to the split stage's mbarrier, which the threads wait on
+// Operand path of a chunk of kKC = 16 reduction rows: 512 splitter threads load the chunk's
+// rows of Q (all K columns) and of P and Gamma (the CTA's 128 columns) straight from global
+// memory, four rows of one column per piece (warp loads of 32 consecutive columns), and write
+// their hi / lo parts into the operand blocks of a split stage (the no-swizzle K-major
+// canonical layout: core matrices of 8 rows x 4 values) together with the one-hot block.  The
+// stage's mbarrier counts the 512 splitters; one thread of a seventeenth warp then issues the
+// chunk's MMAs and commits them to the stage's second mbarrier, which the splitters wait on
 // (bounded) before they refill that stage.  The rows are the round's packed rows, read once
-// from global memory per CTA with no per-element address arithmetic; thread 0 keeps the
-// rows of the next kPrefetch chunks on their way into L2, so that the copies into the raw
-// tiles, only kRawStages chunks ahead for lack of shared memory, wait on L2 and not on DRAM.
+// per CTA; thread 0 keeps the rows of the next kPrefetch chunks on their way into L2, so the
+// splitters' loads wait on L2, not on DRAM.
 #include "hmm_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -42,13 +41,12 @@ namespace hmm {
 
 namespace {
 
-constexpr int kSplitThreads = 512;      // warps 0-15: copies, operand split, epilogue
+constexpr int kSplitThreads = 512;      // warps 0-15: loads, operand split, epilogue
 constexpr int kThreads = kSplitThreads + 32;   // + warp 16: issues the MMAs
 constexpr int kColParts = kSplitThreads / 128; // epilogue: column parts per TMEM lane quarter
 constexpr int kCluster = 4;            // CTAs of consecutive row ranges of one i block
 constexpr int kKC = 16;                 // reduction rows per stage
 constexpr int kMaxStages = 3;          // split stages
-constexpr int kRawStages = 2;          // raw tiles (bulk-copy targets)
 constexpr int kPrefetch = 6;           // chunks brought into L2 ahead
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -84,7 +82,6 @@ struct XiPrm {
     const int32_t* osym;
     const int32_t* rows_r;
     int K, M, Mp, nib, nsplit, stages;
-    uint32_t raw_bytes;                   // one raw tile: Q [kKC][K], P and Gamma [kKC][128]
     int two_phase;                        // epilogue: U and the counts staged one after the other
     uint32_t tmem_cols;
     float* Upart;                         // [nsplit][K][K]
@@ -129,40 +126,11 @@ __device__ __forceinline__ void put_split(char* hi, char* lo, int n, int kq, flo
     *reinterpret_cast<float4*>(lo + off) = l;
 }
 
-// Byte offsets inside a raw tile.
-struct RawLayout {
-    uint32_t q, pp, g;
-};
-__host__ __device__ inline RawLayout raw_layout(int K, bool counts) {
-    RawLayout r;
-    r.q = 0;
-    r.pp = (uint32_t)kKC * K * 4;
-    r.g = r.pp + kKC * 128 * 4;
-    (void)counts;
-    return r;
-}
-__host__ __device__ inline uint32_t raw_tile_bytes(int K, bool counts) {
-    return (uint32_t)kKC * K * 4 + kKC * 128 * 4 * (counts ? 2u : 1u);
-}
-
-// Four reduction rows (4kq .. 4kq+3) of column n of a raw tile with row stride `ld` floats;
-// rows at or past nrow read as zero (the last chunk of a range).
-__device__ __forceinline__ float4 raw4(const float* t, int ld, int n, int kq, int nrow) {
-    const int r = 4 * kq;
-    float4 v;
-    v.x = r + 0 < nrow ? t[(r + 0) * ld + n] : 0.f;
-    v.y = r + 1 < nrow ? t[(r + 1) * ld + n] : 0.f;
-    v.z = r + 2 < nrow ? t[(r + 2) * ld + n] : 0.f;
-    v.w = r + 3 < nrow ? t[(r + 3) * ld + n] : 0.f;
-    return v;
-}
-
 template <int K, bool CNT>
 __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     extern __shared__ __align__(1024) char smem[];
     __shared__ __align__(8) uint64_t s_bar[kMaxStages];     // split stage s: its MMAs done
     __shared__ __align__(8) uint64_t s_full[kMaxStages];    // split stage s: operands written
-    __shared__ __align__(8) uint64_t s_raw[kRawStages];     // raw tile r: its Q rows arrived
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
     __shared__ int64_t s_committed;       // chunks whose MMAs the MMA warp committed
@@ -177,8 +145,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     const bool has_rows = r0 < r1;        // a rank without rows still joins the cluster's sums
     const int Mp = p.Mp, NS = p.stages;
     const StageLayout sl = stage_layout(K, Mp, CNT);
-    const RawLayout rl = raw_layout(K, CNT);
-    char* const raw0 = smem + (size_t)NS * sl.bytes;
     const int icol0 = ib * 128;
     const int ncols = K - icol0 < 128 ? K - icol0 : 128;     // valid i columns of the block
     if (tid == 0) {
@@ -186,7 +152,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
             tc::mbar_init(&s_bar[s], 1);
             tc::mbar_init(&s_full[s], kSplitThreads);
         }
-        for (int r = 0; r < kRawStages; ++r) tc::mbar_init(&s_raw[r], 1);
         tc::fence_mbar_init();
         s_fail = 0;
         s_committed = 0;
@@ -218,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
     const uint32_t tmem = s_tmem;
     const int64_t nchunks = has_rows ? (r1 - r0 + kKC - 1) / kKC : 0;
     bool failed = false;
-    int64_t c = 0, issued = 0;
+    int64_t c = 0;
     if (!splitter) {
         // ---- the last warp: lane 0 issues each chunk's MMAs once its operands are written
         if (lane == 0) {
@@ -257,105 +222,88 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
         }
         __syncwarp();
     } else {
-        // ---- the other warps: copies and operand split
-        // the copies of chunk q into raw tile q % kRawStages: thread 0 copies the Q rows (one
-        // contiguous bulk copy, completing on the tile's mbarrier); every splitter copies
-        // 16-byte pieces of the chunk's P and Gamma rows (the CTA's 128 columns) with
-        // cp.async and commits them as one group -- an empty group past the last chunk, so
-        // that "all but the newest kRawStages - 1 groups complete" means "chunk q complete"
-        auto issue_q = [&](int64_t q) {
-            const int rs = (int)(q % kRawStages);
-            char* raw = raw0 + (size_t)rs * p.raw_bytes;
+        // ---- the other warps: the operand split, straight from global memory.  Each splitter
+        // loads its pieces of chunk c (four rows of one column per piece; the rows are on
+        // their way into L2, thread 0 bringing them kPrefetch chunks ahead) and writes their
+        // hi / lo parts into the chunk's stage; the stage's mbarrier counts the 512 splitters
+        // before the MMA warp issues, and a splitter refills a stage once its MMAs completed.
+        constexpr int QI = (K * 4 + kSplitThreads - 1) / kSplitThreads;   // Q pieces per splitter
+        const int pn = tid % 128, pkq = tid / 128;    // the P / Gamma piece: column pn, rows 4 pkq ..
+        const bool pin = pn < ncols;
+        auto load4 = [&](const float* base, int n, int kq, int64_t row0, int nrow) -> float4 {
+            const int r = 4 * kq;
+            const float* src = base + (row0 + r) * K + n;
+            float4 v;
+            v.x = r + 0 < nrow ? __ldcg(src) : 0.f;
+            v.y = r + 1 < nrow ? __ldcg(src + K) : 0.f;
+            v.z = r + 2 < nrow ? __ldcg(src + 2 * K) : 0.f;
+            v.w = r + 3 < nrow ? __ldcg(src + 3 * K) : 0.f;
+            return v;
+        };
+        auto prefetch = [&](int64_t q) {
+            const int64_t prow0 = r0 + q * kKC;
+            const uint32_t bytes = (uint32_t)(r1 - prow0 < kKC ? r1 - prow0 : kKC) * K * 4;
+            tc::bulk_prefetch_l2(p.Q + prow0 * K, bytes);
+            tc::bulk_prefetch_l2(p.P + prow0 * K, bytes);
+            if (CNT) tc::bulk_prefetch_l2(p.G + prow0 * K, bytes);
+        };
+        // this splitter's pieces of chunk q (all loads issued before the first use)
+        struct Pieces {
+            float4 p, g, q[QI];
+            int4 o;                       // osym of the thread's H row quad tid % 4
+        };
+        auto load = [&](Pieces& v, int64_t q) {
             const int64_t row0 = r0 + q * kKC;
             const int nrow = (int)(r1 - row0 < kKC ? r1 - row0 : kKC);
-            tc::mbar_arrive_expect_tx(&s_raw[rs], (uint32_t)nrow * K * 4);
-            tc::bulk_g2s(raw + rl.q, p.Q + row0 * K, (uint32_t)nrow * K * 4, &s_raw[rs]);
-            // and the whole rows of P, Q and Gamma of chunk q + kPrefetch into L2 (full rows are
-            // contiguous; the other i block of the same rows reads the rest)
-            const int64_t pq = q + kPrefetch;
-            if (pq < nchunks) {
-                const int64_t prow0 = r0 + pq * kKC;
-                const uint32_t bytes = (uint32_t)(r1 - prow0 < kKC ? r1 - prow0 : kKC) * K * 4;
-                tc::bulk_prefetch_l2(p.Q + prow0 * K, bytes);
-                tc::bulk_prefetch_l2(p.P + prow0 * K, bytes);
-                if (CNT) tc::bulk_prefetch_l2(p.G + prow0 * K, bytes);
-            }
-        };
-        auto issue_pg = [&](int64_t q) {
-            if (q < nchunks) {
-                const int rs = (int)(q % kRawStages);
-                char* raw = raw0 + (size_t)rs * p.raw_bytes;
-                const int64_t row0 = r0 + q * kKC;
-                const int nrow = (int)(r1 - row0 < kKC ? r1 - row0 : kKC);
+            v.p = pin ? load4(p.P + icol0, pn, pkq, row0, nrow) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v.g = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (CNT && pin) v.g = load4(p.G + icol0, pn, pkq, row0, nrow);
 #pragma unroll
-                for (int idx = tid; idx < kKC * 32; idx += kSplitThreads) {
-                    const int rr = idx >> 5, col = 4 * (idx & 31);
-                    if (rr < nrow && col < ncols) {
-                        const uint32_t off = (uint32_t)(rr * 128 + col) * 4;
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                                     ::"r"(tc::smem_u32(raw + rl.pp + off)), "l"(p.P + (row0 + rr) * K + icol0 + col)
-                                     : "memory");
-                        if (CNT)
-                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                                         ::"r"(tc::smem_u32(raw + rl.g + off)), "l"(p.G + (row0 + rr) * K + icol0 + col)
-                                         : "memory");
-                    }
-                }
+            for (int i = 0; i < QI; ++i) {
+                const int idx = tid + i * kSplitThreads;
+                v.q[i] = idx < K * 4 ? load4(p.Q, idx % K, idx / K, row0, nrow) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        if (tid == 0)
-            for (int64_t q = 0; q < kPrefetch && q < nchunks; ++q) {
-                const int64_t prow0 = r0 + q * kKC;
-                const uint32_t bytes = (uint32_t)(r1 - prow0 < kKC ? r1 - prow0 : kKC) * K * 4;
-                tc::bulk_prefetch_l2(p.Q + prow0 * K, bytes);
-                tc::bulk_prefetch_l2(p.P + prow0 * K, bytes);
-                if (CNT) tc::bulk_prefetch_l2(p.G + prow0 * K, bytes);
-            }
-        for (; issued < kRawStages; ++issued) {
-            if (tid == 0 && issued < nchunks) issue_q(issued);
-            issue_pg(issued);
-        }
-        for (; c < nchunks; ++c) {
-            const int s = (int)(c % NS), rs = (int)(c % kRawStages);
-            char* st = smem + (size_t)s * sl.bytes;
-            const char* raw = raw0 + (size_t)rs * p.raw_bytes;
-            const int64_t row0 = r0 + c * kKC;
-            const int nrow = (int)(r1 - row0 < kKC ? r1 - row0 : kKC);
-            int4 o = make_int4(-1, -1, -1, -1);   // osym of the thread's H row quad tid % 4
+            v.o = make_int4(-1, -1, -1, -1);
             if (CNT) {
                 const int64_t r = row0 + 4 * (tid & 3);
-                if (r + 0 < r1) o.x = p.osym[r + 0];
-                if (r + 1 < r1) o.y = p.osym[r + 1];
-                if (r + 2 < r1) o.z = p.osym[r + 2];
-                if (r + 3 < r1) o.w = p.osym[r + 3];
+                if (r + 0 < r1) v.o.x = p.osym[r + 0];
+                if (r + 1 < r1) v.o.y = p.osym[r + 1];
+                if (r + 2 < r1) v.o.z = p.osym[r + 2];
+                if (r + 3 < r1) v.o.w = p.osym[r + 3];
             }
-            bool ok = tc::mbar_wait_bounded(&s_raw[rs], (uint32_t)((c / kRawStages) & 1), kWaitNs);
-            if (ok && c >= NS) ok = tc::mbar_wait_bounded(&s_bar[s], (uint32_t)((c / NS - 1) & 1), kWaitNs);
-            static_assert(kRawStages == 2, "the cp.async group count below assumes two raw tiles");
-            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this thread's pieces of chunk c
-            if (tc::bar_or_n(1, kSplitThreads, !ok)) {             // every splitter's pieces visible
-                failed = true;
-                break;
+        };
+        if (tid == 0)
+            for (int64_t q = 0; q < kPrefetch && q < nchunks; ++q) prefetch(q);
+        // the pieces of chunk c + 1 load while chunk c is split
+        Pieces cur, nxt;
+        if (nchunks > 0) load(cur, 0);
+        for (; c < nchunks; ++c) {
+            const int s = (int)(c % NS);
+            char* st = smem + (size_t)s * sl.bytes;
+            if (tid == 0 && c + kPrefetch < nchunks) prefetch(c + kPrefetch);
+            if (c + 1 < nchunks) load(nxt, c + 1);
+            const float4 vp = cur.p, vg = cur.g;
+            const int4 o = cur.o;
+            // the stage's previous MMAs (chunk c - NS) have completed
+            if (c >= NS) {
+                const bool ok = *reinterpret_cast<volatile int*>(&s_fail) == 0 &&
+                                tc::mbar_wait_bounded(&s_bar[s], (uint32_t)((c / NS - 1) & 1), kWaitNs);
+                if (!ok) {
+                    failed = true;
+                    break;
+                }
             }
-            // split the raw tile into the stage's hi / lo operand blocks
-            const float* rq = reinterpret_cast<const float*>(raw + rl.q);
-            const float* rp = reinterpret_cast<const float*>(raw + rl.pp);
-            const float* rg = reinterpret_cast<const float*>(raw + rl.g);
+            if (pin) {
+                put_split(st + sl.a_hi, st + sl.a_lo, pn, pkq, vp);
+                if (CNT) put_split(st + sl.g_hi, st + sl.g_lo, pn, pkq, vg);
+            }
 #pragma unroll
-            for (int idx = tid; idx < 128 * (kKC / 4); idx += kSplitThreads) {
-                const int n = idx % 128, kq = idx / 128;
-                if (n >= ncols) continue;
-                put_split(st + sl.a_hi, st + sl.a_lo, n, kq, raw4(rp, 128, n, kq, nrow));
-                if (CNT) put_split(st + sl.g_hi, st + sl.g_lo, n, kq, raw4(rg, 128, n, kq, nrow));
-            }
-#pragma unroll
-            for (int idx = tid; idx < K * (kKC / 4); idx += kSplitThreads) {
-                const int n = idx % K, kq = idx / K;
-                put_split(st + sl.b_hi, st + sl.b_lo, n, kq, raw4(rq, K, n, kq, nrow));
+            for (int i = 0; i < QI; ++i) {
+                const int idx = tid + i * kSplitThreads;
+                if (idx < K * 4) put_split(st + sl.b_hi, st + sl.b_lo, idx % K, idx / K, cur.q[i]);
             }
             if (CNT) {
-                // quad kq = tid % 4, columns n = tid / 4 + 64 m (m < Mp / 64)
+                // quad kq = tid % 4, columns n = tid / 4 + 128 m (m < Mp / 128)
                 const int kq = tid & 3;
                 for (int n = tid >> 2; n < Mp; n += kSplitThreads / 4) {
                     float4 v;
@@ -368,9 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
             }
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&s_full[s]);                       // the MMA warp may issue chunk c
-            tc::bar_sync_n(2, kSplitThreads);                  // raw tile rs read by every splitter
-            if (tid == 0 && issued < nchunks) issue_q(issued); // chunk c + kRawStages into tile rs
-            issue_pg(issued++);
+            cur = nxt;
         }
         if (failed) s_fail = 1;
     }
@@ -382,14 +328,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_xi_tc(XiPrm p) {
         if (!tc::mbar_wait_bounded(&s_bar[cl % NS], (uint32_t)((cl / NS) & 1), kWaitNs)) s_fail = 1;
     }
     if (failed && tid == 0) {
-        // a wait gave up: let the Q copies already issued land and the MMAs already committed
-        // finish (each wait bounded) before the tensor memory and the CTA go away
-        for (int64_t q = c; q < issued && q < nchunks; ++q)
-            tc::mbar_wait_bounded(&s_raw[q % kRawStages], (uint32_t)((q / kRawStages) & 1), kWaitNs);
+        // a wait gave up: let the MMAs already committed finish (bounded) before the tensor
+        // memory and the CTA go away
         const int64_t nc = s_committed;
         if (nc > 0) tc::mbar_wait_bounded(&s_bar[(nc - 1) % NS], (uint32_t)(((nc - 1) / NS) & 1), kWaitNs);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     failed = s_fail != 0;
     if (failed && tid == 0) report_status(p.status, ACCEL_ERR_TIMEOUT);
@@ -521,18 +464,16 @@ bool xi_tc_supported(int K) { return K == 64 || K == 128 || K == 256; }
 bool xi_tc_counts_supported(int K, int M) { return xi_tc_supported(K) && K + xi_counts_cols(M) <= 512 && xi_counts_cols(M) <= 256; }
 
 namespace {
-// Dynamic shared memory of a launch (stages, raw tiles, at least the epilogue's staging).
-// Dynamic shared memory of a launch: the split stages and raw tiles (+ alignment slack of
-// the block), at least the epilogue's staging of the accumulators -- U and the counts
-// together if that fits, else one after the other (*two_phase).
+// Dynamic shared memory of a launch: the split stages (as many as fit, at most kMaxStages;
+// + alignment slack of the block), at least the epilogue's staging of the accumulators -- U
+// and the counts together if that fits, else one after the other (*two_phase).
 size_t xi_smem_bytes(int K, int Mp, bool counts, int* stages_out, bool* two_phase) {
     const StageLayout sl = stage_layout(K, Mp, counts);
-    const size_t raw_total = (size_t)kRawStages * raw_tile_bytes(K, counts);
     const size_t optin = (size_t)max_smem_optin();
     int stages = kMaxStages;
-    while (stages > 2 && (size_t)stages * sl.bytes + raw_total + 1024 > optin) --stages;
+    while (stages > 2 && (size_t)stages * sl.bytes + 1024 > optin) --stages;
     if (stages_out) *stages_out = stages;
-    size_t smem = (size_t)stages * sl.bytes + raw_total + 1024;
+    size_t smem = (size_t)stages * sl.bytes + 1024;
     const size_t su = (size_t)128 * (K + 4) * 4, sc = counts ? (size_t)128 * (Mp + 4) * 4 : 0;
     const bool two = su + sc + 1024 > optin;
     if (two_phase) *two_phase = two;
@@ -605,7 +546,6 @@ accel_status xi_tc_round(const float* P, const float* Q, const float* G, const i
     uint32_t cols = 32;
     while ((int)cols < need_cols) cols <<= 1;
     p.tmem_cols = cols;
-    p.raw_bytes = raw_tile_bytes(K, counts);
     int stages = 2;
     bool two = false;
     const size_t smem = xi_smem_bytes(K, p.Mp, counts, &stages, &two);
