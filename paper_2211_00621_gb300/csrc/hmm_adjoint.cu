@@ -27,8 +27,10 @@
 // The recurrences are FP32 SIMT: for K in {64, 128, 256} on CTA pairs (thread-block clusters)
 // that split the states, each pair running one or two groups of up to 16 length-sorted
 // sequences as planned by k_plan; otherwise one CTA per 8 sequences.  The count
-// contractions of each backward round run on the tensor cores (k_xi_tc.cu).  Every
-// accumulation has a fixed order, so results are deterministic.
+// contractions of each backward round run on the tensor cores (k_xi_tc.cu).  On the cluster
+// path the backward of round r, the recomputation of round r + 1 and the counts of earlier
+// rounds run at the same time on three streams, each round's rows in buffers of its own.
+// Every accumulation has a fixed order, so results are deterministic.
 #include "hmm_internal.cuh"
 #include "simt_stream.cuh"
 
@@ -671,10 +673,10 @@ __device__ __forceinline__ void cluster_group_range(const Prm& p, int pass, int6
 // sequences that have one).  Segment lengths grow like sqrt(T), so a grouping balanced for T
 // would leave the pairs that run two groups of short sequences as the slowest of every round.
 //
-// The backward of round r and the recomputation of round r + 1 are independent, so they share
-// one launch (backward launch r + 1).  Either they run side by side, the backward on nb pairs
-// and the recomputation on the other ncl - nb, or each on all ncl pairs, the recomputation's
-// pairs starting as the backward's finish.  The planner takes the split with the smallest
+// The backward of round r and the recomputation of round r + 1 are independent, so they run
+// at the same time (backward launch r + 1: k_bwd_cl and k_rec_cl on two streams).  Either they
+// run side by side, the backward on nb pairs and the recomputation on the other ncl - nb, or
+// each on all ncl pairs, sharing them.  The planner takes the split with the smallest
 // estimated time: the larger of the two passes' maximum loads side by side, their sum
 // otherwise (a backward step costs about 1.14 recomputation steps, measured at K = 256).  One
 // pass alone on all pairs has to round 13-14 sequences a pair up to two contraction passes a
