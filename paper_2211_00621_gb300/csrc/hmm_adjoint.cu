@@ -678,9 +678,10 @@ __device__ __forceinline__ void cluster_group_range(const Prm& p, int pass, int6
 // run side by side, the backward on nb pairs and the recomputation on the other ncl - nb, or
 // each on all ncl pairs, sharing them.  The planner takes the split with the smallest
 // estimated time: the larger of the two passes' maximum loads side by side, their sum
-// otherwise (a backward step costs about 1.14 recomputation steps, measured at K = 256).  One
-// pass alone on all pairs has to round 13-14 sequences a pair up to two contraction passes a
-// step; two passes side by side can use groups of 16 and balance what is left between them.
+// otherwise (a backward step weighs 1.05 recomputation steps: measured fastest among
+// 0.95-1.25 at K = 256 with the two passes running side by side).  One pass alone on all
+// pairs has to round 13-14 sequences a pair up to two contraction passes a step; two passes
+// side by side can use groups of 16 and balance what is left between them.
 //
 // One CTA per launch (block 0: the forward).  The step counts of a pass's list sit in shared
 // memory with their maxima over 2, 4, 8 and 16 consecutive entries, so a group's cost is two
@@ -691,7 +692,7 @@ constexpr int kPlanMaxGroups = 256;
 constexpr int kPlanMaxSeq = 16 * kPlanMaxGroups;
 constexpr int kPlanMaxCand = 40;
 constexpr int kPlanLevels = 5;
-constexpr float kBwdStepCost = 1.14f;
+constexpr float kBwdStepCost = 1.05f;
 
 __host__ __device__ inline size_t plan_smem_bytes() { return (size_t)2 * kPlanLevels * kPlanMaxSeq * 4; }
 
