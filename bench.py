@@ -244,9 +244,12 @@ class Workload:
     # all-pairs rows on the main stream take what is free; the adjoint's backward rounds and
     # the re-estimation, which want every SM, follow.
     def adj_budget(self):
+        """SMs for the adjoint's forward phase in the step: those the BF16 forward's persistent
+        clusters leave, less a tenth of the device for the rows that run beside them (measured
+        at 152 SMs: budgets 94 / 86 / 78 / 70 gave steps of 19.70 / 19.60 / 19.45 / 19.67 ms)."""
         units = (self.tuned or {}).get("units", 0)
         nc = 2 if (self.tuned or {}).get("pair", 0) == 1 else 4 if (self.tuned or {}).get("pair", 0) == 2 else 1
-        free = self.n_sms - units * nc
+        free = self.n_sms - units * nc - self.n_sms // 10
         return free if units > 0 and free > 0 else 0
 
     def adj_forward_side(self, cur, adj_inputs):
@@ -1091,10 +1094,11 @@ def main():
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
                        "schedule": "three streams: the batched BF16 forward (a CUDA graph of its 5 kernels, "
                                    "its tuned persistent units) beside the adjoint's forward phase within the "
-                                   "SMs it leaves (accel_set_sm_budget) and the seg-reduce, plain FP32 and "
-                                   "all-pairs rows; the adjoint's backward phase and the re-estimation as "
-                                   "soon as its forward phase ends (on the SMs the BF16 forward leaves, then "
-                                   "on every SM); per-row times in `rows` come from the same step run row "
+                                   "SMs it leaves less a tenth of the device (accel_set_sm_budget) and the "
+                                   "seg-reduce, plain FP32 and all-pairs rows on the main stream; then, "
+                                   "after those rows and the forward phase, the adjoint's backward phase "
+                                   "(three streams of its own) and the re-estimation; the BF16 stream joins "
+                                   "at the end; per-row times in `rows` come from the same step run row "
                                    "after row",
                        "parallelism": f"replicas x{world} (sequences shard with no exchange)"},
             "seg_reduce_gbs": sweep["GB/s"], "seg_reduce_sweep": sweeps, "marshal_sweep": msweeps,
