@@ -2142,42 +2142,46 @@ static accel_status run_backward(Plan& P, const double* d_weights, float* d_grad
             // with plans each pass takes its pairs from the plan; without, all ncl pairs
             const int np = P.planned ? -1 : (int)p.ncl;
             const unsigned grid = (unsigned)(2 * p.ncl);
-            for (int l = 0; l <= L.Cmax; ++l) {
-                if (l >= 1) {
-                    // the backward of round l - 1: after its recomputation; its Q / gamma /
-                    // symbol buffers were last read by the counts of round l - 1 - kQBufs
-                    const int rb = l - 1;
-                    ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, e_rec[rb], 0));
-                    if (rb >= kQBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, done[rb - kQBufs], 0));
-                    kc.bwd<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, rb, np);
-                    ++nlaunch;
-                    ACCEL_CUDA_TRY(ev.make(e_bwd[rb]));
-                    ACCEL_CUDA_TRY(cudaEventRecord(e_bwd[rb], bs.hi));
-                    accel_status r = counts(rb);
-                    if (r != ACCEL_OK) return r;
+            auto passes = [&]() -> accel_status {
+                for (int l = 0; l <= L.Cmax; ++l) {
+                    if (l >= 1) {
+                        // the backward of round l - 1: after its recomputation; its Q / gamma /
+                        // symbol buffers were last read by the counts of round l - 1 - kQBufs
+                        const int rb = l - 1;
+                        ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, e_rec[rb], 0));
+                        if (rb >= kQBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi, done[rb - kQBufs], 0));
+                        kc.bwd<<<grid, clu::kT, P.sm_c, bs.hi>>>(p, rb, np);
+                        ++nlaunch;
+                        ACCEL_CUDA_TRY(ev.make(e_bwd[rb]));
+                        ACCEL_CUDA_TRY(cudaEventRecord(e_bwd[rb], bs.hi));
+                        accel_status r = counts(rb);
+                        if (r != ACCEL_OK) return r;
+                    }
+                    if (l < L.Cmax) {
+                        // the recomputation of round l: its P rows' buffer was last read by the
+                        // backward and the counts of round l - kPBufs, its exponents' by the
+                        // backward of round l - 2
+                        if (l >= kPBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, done[l - kPBufs], 0));
+                        if (l >= 2) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, e_bwd[l - 2], 0));
+                        kc.rec<<<grid, clu::kT, P.sm_c, bs.hi2>>>(p, l, np);
+                        ++nlaunch;
+                        ACCEL_CUDA_TRY(ev.make(e_rec[l]));
+                        ACCEL_CUDA_TRY(cudaEventRecord(e_rec[l], bs.hi2));
+                    }
                 }
-                if (l < L.Cmax) {
-                    // the recomputation of round l: its P rows' buffer was last read by the
-                    // backward and the counts of round l - kPBufs, its exponents' by the
-                    // backward of round l - 2
-                    if (l >= kPBufs) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, done[l - kPBufs], 0));
-                    if (l >= 2) ACCEL_CUDA_TRY(cudaStreamWaitEvent(bs.hi2, e_bwd[l - 2], 0));
-                    kc.rec<<<grid, clu::kT, P.sm_c, bs.hi2>>>(p, l, np);
-                    ++nlaunch;
-                    ACCEL_CUDA_TRY(ev.make(e_rec[l]));
-                    ACCEL_CUDA_TRY(cudaEventRecord(e_rec[l], bs.hi2));
-                }
+                return ACCEL_OK;
+            };
+            const accel_status rp = passes();
+            // the caller's stream waits for all three streams, also after an error on the way,
+            // so that nothing enqueued so far outlives the call's ordering
+            cudaEvent_t e_join[3];
+            cudaStream_t own[3] = {bs.hi, bs.hi2, bs.lo};
+            for (int k = 0; k < 3; ++k) {
+                ACCEL_CUDA_TRY(ev.make(e_join[k]));
+                ACCEL_CUDA_TRY(cudaEventRecord(e_join[k], own[k]));
+                ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_join[k], 0));
             }
-            cudaEvent_t e_hi, e_hi2, e_lo;
-            ACCEL_CUDA_TRY(ev.make(e_hi));
-            ACCEL_CUDA_TRY(ev.make(e_hi2));
-            ACCEL_CUDA_TRY(ev.make(e_lo));
-            ACCEL_CUDA_TRY(cudaEventRecord(e_hi, bs.hi));
-            ACCEL_CUDA_TRY(cudaEventRecord(e_hi2, bs.hi2));
-            ACCEL_CUDA_TRY(cudaEventRecord(e_lo, bs.lo));
-            ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_hi, 0));
-            ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_hi2, 0));
-            ACCEL_CUDA_TRY(cudaStreamWaitEvent(st, e_lo, 0));
+            if (rp != ACCEL_OK) return rp;
         } else {
             ACCEL_CUDA_TRY(cudaFuncSetAttribute(k_backward_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.sm_b));
             for (int round = 0; round < L.Cmax; ++round) {
